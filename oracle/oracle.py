@@ -1,0 +1,303 @@
+"""ctypes front end of the FP64 C oracle (mg_oracle.c).
+
+Test infrastructure only (see the package docstring).  Every function takes and
+returns numpy float64 arrays; grids are ``[n, n]`` with row index = y, column = x,
+and stencil fields / per-point kernels are ``[9, n, n]`` with tap k = 3*(di+1)+(dj+1).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mg_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C99, -O2, no machine-specific flags)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "mg_oracle.h"))
+    ):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=c99", "-D_DEFAULT_SOURCE", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+        )
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        L = _lib
+        L.or_mg_create.restype = ctypes.c_void_p
+        L.or_mg_create.argtypes = [ctypes.c_int, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        for name in ("or_mg_destroy",):
+            getattr(L, name).argtypes = [ctypes.c_void_p]
+        L.or_mg_levels.argtypes = [ctypes.c_void_p]
+        L.or_mg_n.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.or_mg_get_field.argtypes = [ctypes.c_void_p, ctypes.c_int, _D]
+        L.or_mg_get_kernels.argtypes = [ctypes.c_void_p, ctypes.c_int, _D]
+        L.or_mg_set_kernels.argtypes = [ctypes.c_void_p, ctypes.c_int, _D]
+        L.or_mg_set_jacobi.argtypes = [ctypes.c_void_p, ctypes.c_double]
+        L.or_mg_set_cnn.argtypes = [ctypes.c_void_p, _D, ctypes.c_double, ctypes.c_int]
+        L.or_mg_vcycle.argtypes = [ctypes.c_void_p, _D, _D]
+        L.or_mg_solve.argtypes = [ctypes.c_void_p, _D, _D, ctypes.c_double, ctypes.c_int, _D]
+        L.or_bf16.restype = ctypes.c_double
+        L.or_bf16.argtypes = [ctypes.c_double]
+        L.or_twogrid_loss.restype = ctypes.c_double
+        L.or_twogrid_loss.argtypes = [ctypes.c_int, _D, _D, ctypes.c_int, _D, _D]
+        L.or_cholesky.argtypes = [ctypes.c_int, _D]
+        L.or_cholesky_solve.argtypes = [ctypes.c_int, _D, _D]
+        L.or_q1_rotated_stencil.argtypes = [ctypes.c_double, ctypes.c_double, _D]
+        L.or_fd_rotated_stencil.argtypes = [ctypes.c_double, ctypes.c_double, _D]
+        L.or_hypernet_forward.argtypes = [ctypes.c_int, _D, _D, ctypes.c_double, ctypes.c_int, _D]
+        L.or_hypernet_backward.argtypes = [ctypes.c_int, _D, _D, ctypes.c_double, ctypes.c_int, _D, _D]
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_D)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+# ---------------------------------------------------------------- discretisations
+def q1_rotated_stencil(eps: float, theta: float) -> np.ndarray:
+    s = np.zeros(9)
+    lib().or_q1_rotated_stencil(float(eps), float(theta), _p(s))
+    return s.reshape(3, 3)
+
+
+def fd_rotated_stencil(xi: float, theta: float) -> np.ndarray:
+    s = np.zeros(9)
+    lib().or_fd_rotated_stencil(float(xi), float(theta), _p(s))
+    return s.reshape(3, 3)
+
+
+def fe_q1_field(n: int, kxx, kxy, kyy) -> np.ndarray:
+    """Q1 field; kxx/kxy/kyy scalars (constant tensor) or [(n+1),(n+1)] cell arrays."""
+    per_cell = int(np.ndim(kxx) > 0)
+    kxx, kxy, kyy = (_f64(np.atleast_1d(v)) for v in (kxx, kxy, kyy))
+    st = np.zeros((9, n, n))
+    lib().or_fe_q1_field(n, _p(kxx), _p(kxy), _p(kyy), per_cell, _p(st))
+    return st
+
+
+def paper9_field(n: int, g_cells) -> np.ndarray:
+    g = _f64(g_cells)
+    assert g.shape == (n + 1, n + 1)
+    st = np.zeros((9, n, n))
+    lib().or_paper9_field(n, _p(g), _p(st))
+    return st
+
+
+def varcoef5_field(n: int, a_cells) -> np.ndarray:
+    a = _f64(a_cells)
+    assert a.shape == (n + 1, n + 1)
+    st = np.zeros((9, n, n))
+    lib().or_varcoef5_field(n, _p(a), _p(st))
+    return st
+
+
+def const_field(n: int, s) -> np.ndarray:
+    s = _f64(np.asarray(s).reshape(9))
+    st = np.zeros((9, n, n))
+    lib().or_const_field(n, _p(s), _p(st))
+    return st
+
+
+# ---------------------------------------------------------------- operators
+def apply(st: np.ndarray, x) -> np.ndarray:
+    n = st.shape[1]
+    st, x = _f64(st), _f64(x)
+    y = np.zeros((n, n))
+    lib().or_apply(n, _p(st), _p(x), _p(y))
+    return y
+
+
+def restrict(r) -> np.ndarray:
+    r = _f64(r)
+    n = r.shape[0]
+    rc = np.zeros(((n - 1) // 2, (n - 1) // 2))
+    lib().or_restrict(n, _p(r), _p(rc))
+    return rc
+
+
+def prolong(ec, n: int) -> np.ndarray:
+    ec = _f64(ec)
+    e = np.zeros((n, n))
+    lib().or_prolong_add(n, _p(ec), _p(e))
+    return e
+
+
+def rap(st) -> np.ndarray:
+    st = _f64(st)
+    n = st.shape[1]
+    nc = (n - 1) // 2
+    stc = np.zeros((9, nc, nc))
+    lib().or_rap(n, _p(st), _p(stc))
+    return stc
+
+
+def dense_matrix(st) -> np.ndarray:
+    st = _f64(st)
+    n = st.shape[1]
+    A = np.zeros((n * n, n * n))
+    lib().or_dense_matrix(n, _p(st), _p(A))
+    return A
+
+
+# ---------------------------------------------------------------- smoothers
+def jacobi_kernels(st, omega: float = 2.0 / 3.0) -> np.ndarray:
+    st = _f64(st)
+    n = st.shape[1]
+    W = np.zeros((9, n, n))
+    lib().or_jacobi_kernels(n, _p(st), ctypes.c_double(omega), _p(W))
+    return W
+
+
+def apply_H(W, v) -> np.ndarray:
+    W, v = _f64(W), _f64(v)
+    n = v.shape[0]
+    y = np.zeros((n, n))
+    lib().or_apply_H(n, _p(W), _p(v), _p(y))
+    return y
+
+
+def apply_HT(W, v) -> np.ndarray:
+    W, v = _f64(W), _f64(v)
+    n = v.shape[0]
+    y = np.zeros((n, n))
+    lib().or_apply_HT(n, _p(W), _p(v), _p(y))
+    return y
+
+
+def smooth(st, W, f, u, nsteps: int = 1) -> np.ndarray:
+    st, W, f = _f64(st), _f64(W), _f64(f)
+    u = _f64(u).copy()
+    n = st.shape[1]
+    lib().or_smooth(n, _p(st), _p(W), _p(f), _p(u), nsteps)
+    return u
+
+
+def gauss_seidel(st, f, u) -> np.ndarray:
+    st, f = _f64(st), _f64(f)
+    u = _f64(u).copy()
+    lib().or_gauss_seidel(st.shape[1], _p(st), _p(f), _p(u))
+    return u
+
+
+def bf16(v: float) -> float:
+    return lib().or_bf16(float(v))
+
+
+# ---------------------------------------------------------------- multigrid
+class Multigrid:
+    """Galerkin hierarchy + V-cycle (Algorithm 1) + solve, all FP64."""
+
+    def __init__(self, st0, coarsest_n: int = 3, nu1: int = 1, nu2: int = 1):
+        st0 = _f64(st0)
+        self.h = lib().or_mg_create(st0.shape[1], _p(st0), coarsest_n, nu1, nu2)
+        if not self.h:
+            raise ValueError("coarsest operator is not SPD")
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().or_mg_destroy(self.h)
+            self.h = None
+
+    @property
+    def levels(self) -> int:
+        return lib().or_mg_levels(self.h)
+
+    def n(self, level: int) -> int:
+        return lib().or_mg_n(self.h, level)
+
+    def field(self, level: int) -> np.ndarray:
+        n = self.n(level)
+        st = np.zeros((9, n, n))
+        lib().or_mg_get_field(self.h, level, _p(st))
+        return st
+
+    def kernels(self, level: int) -> np.ndarray:
+        n = self.n(level)
+        W = np.zeros((9, n, n))
+        lib().or_mg_get_kernels(self.h, level, _p(W))
+        return W
+
+    def set_kernels(self, level: int, W) -> None:
+        W = _f64(W)
+        lib().or_mg_set_kernels(self.h, level, _p(W))
+
+    def set_jacobi(self, omega: float = 2.0 / 3.0) -> None:
+        lib().or_mg_set_jacobi(self.h, ctypes.c_double(omega))
+
+    def set_cnn(self, params, omega: float = 2.0 / 3.0, bf16: bool = False) -> None:
+        params = _f64(params)
+        assert params.size == hypernet_nparams()
+        lib().or_mg_set_cnn(self.h, _p(params), ctypes.c_double(omega), int(bf16))
+
+    def vcycle(self, b, x) -> np.ndarray:
+        b = _f64(b)
+        x = _f64(x).copy()
+        lib().or_mg_vcycle(self.h, _p(b), _p(x))
+        return x
+
+    def solve(self, b, x0=None, rtol: float = 1e-8, max_cycles: int = 1000):
+        b = _f64(b)
+        x = np.zeros_like(b) if x0 is None else _f64(x0).copy()
+        hist = np.zeros(max_cycles + 1)
+        k = lib().or_mg_solve(self.h, _p(b), _p(x), ctypes.c_double(rtol), max_cycles, _p(hist))
+        return x, hist[: k + 1]
+
+
+# ---------------------------------------------------------------- network + loss
+def hypernet_nparams() -> int:
+    return lib().or_hypernet_nparams()
+
+
+def hypernet_forward(st, params, omega: float = 2.0 / 3.0, bf16: bool = False) -> np.ndarray:
+    st, params = _f64(st), _f64(params)
+    n = st.shape[1]
+    W = np.zeros((9, n, n))
+    lib().or_hypernet_forward(n, _p(st), _p(params), ctypes.c_double(omega), int(bf16), _p(W))
+    return W
+
+
+def hypernet_backward(st, params, dW, omega: float = 2.0 / 3.0, bf16: bool = False) -> np.ndarray:
+    st, params, dW = _f64(st), _f64(params), _f64(dW)
+    n = st.shape[1]
+    g = np.zeros(params.size)
+    lib().or_hypernet_backward(n, _p(st), _p(params), ctypes.c_double(omega), int(bf16), _p(dW), _p(g))
+    return g
+
+
+def twogrid_loss(st, W, z, want_grad: bool = False):
+    """Loss (1/Z) sum_j ||S C S z_j||^2 / n and, optionally, dLoss/dW."""
+    st, W, z = _f64(st), _f64(W), _f64(z)
+    n = st.shape[1]
+    nz = z.shape[0]
+    dW = np.zeros((9, n, n)) if want_grad else None
+    loss = lib().or_twogrid_loss(n, _p(st), _p(W), nz, _p(z), _p(dW) if want_grad else None)
+    return (loss, dW) if want_grad else loss
+
+
+def cnn_loss_and_grad(st, params, z, omega: float = 2.0 / 3.0, bf16: bool = False):
+    """Loss of one problem as a function of the network parameters, with its gradient."""
+    W = hypernet_forward(st, params, omega, bf16)
+    loss, dW = twogrid_loss(st, W, z, want_grad=True)
+    return loss, hypernet_backward(st, params, dW, omega, bf16)
