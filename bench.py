@@ -1,0 +1,357 @@
+#!/usr/bin/env python3
+"""Benchmark: batched multigrid solves to 1e-8 relative residual on GB300.
+
+Workload (per GPU): 16 rotated anisotropic Q1 problems on a 1023 x 1023 interior grid,
+eps log-uniform in [1e-3, 1], theta uniform in [0, pi], rhs uniform[-1, 1] from seeds,
+zero initial guess, V(1,1) cycles to ||b - A x|| / ||b|| < 1e-8, smoother = the trained
+stencil-to-smoother network when its parameters are available, else weighted Jacobi;
+the Jacobi-smoothed solve of the same batch is timed beside it.
+
+One step = one solve of the whole batch.  value = Mdof-sweeps/s = sum over problems and
+smoothed levels of n_l^2 * (nu1 + nu2) * cycles / time.  Inputs are resident in HBM for
+the device-timed number; `e2e` repeats it through the public API from pinned host
+buffers with the copies inside the timed region.  `--impl reference` times the FP64 CPU
+oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solve time to 1e-8 rel. residual, CNN vs Jacobi smoother; Mdof-sweeps/s; HBM %"
+UNIT = "Mdof-sweeps/s"
+N_DEFAULT, NPROB_DEFAULT = 1023, 16
+RTOL = 1e-8
+MAX_CYCLES = 20000
+WEIGHTS = os.path.join(ROOT, "paper_2102_12071_gb300", "weights", "cnn_rotated.npy")
+# algorithmic bytes per fine dof per launch (FP32, constant stencil)
+BYTES_PER_DOF = {0: 16.0, 1: 9.0, 2: 25.0}
+KERNEL_NAMES = {0: "k_residual", 1: "k_down(level 0)", 2: "k_up(level 0, x update)", 3: "k_tail", 4: "k_down(l>=1)",
+                5: "k_up(l>=1)"}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def sweeps_per_cycle(sizes):
+    """Mdof-sweeps of one V(1,1) cycle: every smoothed level is swept twice."""
+    return sum(2 * s * s for s in sizes[:-1]) / 1e6
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [v.strip() for v in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx = max(mx, float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ workload
+def make_batch(rank: int, n: int, nprob: int):
+    from paper_2102_12071_gb300 import inputs
+
+    params = inputs.rotated_params(inputs.SEED_PARAMS + rank, nprob)
+    import numpy as np
+
+    b = np.stack([inputs.rhs_uniform(inputs.SEED_RHS + rank * nprob + i, n) for i in range(nprob)])
+    return params, b
+
+
+def load_weights():
+    if not os.path.exists(WEIGHTS):
+        return None
+    import numpy as np
+    import torch
+
+    return torch.from_numpy(np.load(WEIGHTS).astype(np.float32))
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    """FP64 CPU oracle on a bounded sample: a fixed number of V(1,1) cycles on one problem."""
+    import numpy as np
+
+    import oracle as O
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    params, b = make_batch(0, args.n, 1)
+    eps, theta = params[0]
+    st = O.const_field(args.n, np.float32(O.q1_rotated_stencil(eps, theta)).astype(np.float64))
+    mg = O.Multigrid(st)
+    sizes = [mg.n(l) for l in range(mg.levels)]
+    bb = b[0].astype(np.float64)
+    cycles = args.ref_cycles
+    for _ in range(args.warmup):
+        mg.solve(bb, rtol=0.0, max_cycles=cycles)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        mg.solve(bb, rtol=0.0, max_cycles=cycles)
+    dt = time.perf_counter() - t0
+    value = sweeps_per_cycle(sizes) * cycles * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"rotated anisotropic Q1, {args.n}x{args.n}, V(1,1) Jacobi, bounded sample "
+                               f"of {cycles} cycles on 1 of {args.nprob} problems", "n": args.n},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{cycles} V(1,1) cycles of one {args.n}^2 problem per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(n: int, budget_s: float = 12.0):
+    import numpy as np
+
+    import oracle as O
+
+    params, b = make_batch(0, n, 1)
+    eps, theta = params[0]
+    st = O.const_field(n, np.float32(O.q1_rotated_stencil(eps, theta)).astype(np.float64))
+    mg = O.Multigrid(st)
+    sizes = [mg.n(l) for l in range(mg.levels)]
+    bb = b[0].astype(np.float64)
+    t0 = time.perf_counter()
+    mg.solve(bb, rtol=0.0, max_cycles=1)
+    one = max(time.perf_counter() - t0, 1e-3)
+    cycles = max(1, min(200, int(budget_s / one)))
+    t0 = time.perf_counter()
+    mg.solve(bb, rtol=0.0, max_cycles=cycles)
+    dt = time.perf_counter() - t0
+    return {"value": sweeps_per_cycle(sizes) * cycles / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{cycles} V(1,1) Jacobi cycles of one {n}^2 problem (FP64, single thread)"}
+
+
+# ------------------------------------------------------------------ our arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--nprob", type=int, default=NPROB_DEFAULT)
+    ap.add_argument("--ref-cycles", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--roofline-cycles", type=int, default=30)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    __graft_entry__.build()
+    from paper_2102_12071_gb300 import binding as B, solver as S
+
+    n, nprob = args.n, args.nprob
+    params, b_host = make_batch(rank, n, nprob)
+    problems = [S.rotated(n, e, t) for e, t in params]
+    weights = load_weights()
+    arms = {"jacobi": S.MultigridSolver(problems, "jacobi")}
+    if weights is not None:
+        arms["cnn"] = S.MultigridSolver(problems, "cnn", net_params=weights.cuda())
+    headline = "cnn" if "cnn" in arms else "jacobi"
+    sizes = arms["jacobi"].sizes
+    b = torch.from_numpy(b_host).cuda().contiguous()
+    shape = b.shape
+    x_hi = torch.zeros(shape, device="cuda")
+    x_lo = torch.zeros(shape, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def one_solve(arm):
+        x_hi.zero_()
+        x_lo.zero_()
+        _, _, _, cyc, st = arms[arm].solve(b, x_hi, x_lo, rtol=RTOL, max_cycles=MAX_CYCLES, history=False)
+        return cyc, st
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    results = {}
+    for arm in arms:
+        for _ in range(args.warmup):
+            one_solve(arm)
+    launches0 = {arm: B.mg_profile_read(arms[arm].ctx, -1)[1] for arm in arms}
+    with ClockSampler(local) as clk:
+        for arm in arms:
+            barrier()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            cyc_all = []
+            for _ in range(args.steps):
+                cyc, st = one_solve(arm)
+                cyc_all.append(cyc.copy())
+            e1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+            ms = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+            cyc = cyc_all[-1]
+            sweeps = sum(sweeps_per_cycle(sizes) * int(c) for c in cyc)
+            results[arm] = {"ms_per_step": ms, "cycles": [int(c) for c in cyc], "converged": int(st) == 0,
+                            "mdof_sweeps_per_s": sweeps * world / (ms / 1e3)}
+    clocks = clk.summary()
+    launches = sum(B.mg_profile_read(arms[a].ctx, -1)[1] - launches0[a] for a in arms)
+
+    # ---- dominant-kernel roofline: fixed-cycle run with every problem active, event-timed
+    peak, peak_kind = peaks()
+    ctx = arms[headline].ctx
+    B.mg_profile_enable(ctx, True)
+    x_hi.zero_()
+    x_lo.zero_()
+    arms[headline].solve(b, x_hi, x_lo, rtol=0.0, max_cycles=args.roofline_cycles, history=False)
+    torch.cuda.synchronize()
+    prof = {c: B.mg_profile_read(ctx, c) for c in range(6)}
+    B.mg_profile_enable(ctx, False)
+    total_ms = sum(v[0] for v in prof.values())
+    dom = max((0, 1, 2), key=lambda c: prof[c][0])
+    dom_ms, dom_n = prof[dom]
+    algo_bytes = BYTES_PER_DOF[dom] * nprob * n * n
+    achieved = algo_bytes / (dom_ms / dom_n / 1e3) / 1e9 if dom_n else None
+    cycle_bytes = (16 + 9 + 25) * nprob * n * n + sum((9 + 13) * nprob * s * s for s in sizes[1:-1] if s > 63)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "kernel": KERNEL_NAMES[dom], "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": algo_bytes,
+                "kernel_share": {KERNEL_NAMES[c]: round(prof[c][0] / total_ms, 4) for c in prof if total_ms},
+                "cycle_hbm_frac": (cycle_bytes * args.roofline_cycles / (total_ms / 1e3) / 1e9) / peak}
+
+    # ---- end to end through the public API from pinned host buffers
+    hb = torch.from_numpy(b_host).pin_memory()
+    hx0 = torch.zeros(shape).pin_memory()
+    hout_hi, hout_lo = torch.empty(shape).pin_memory(), torch.empty(shape).pin_memory()
+    db, dxh, dxl = torch.empty_like(b), torch.empty_like(b), torch.empty_like(b)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    cyc_e2e = None
+    for _ in range(args.steps):
+        db.copy_(hb, non_blocking=True)
+        dxh.copy_(hx0, non_blocking=True)
+        dxl.copy_(hx0, non_blocking=True)
+        _, _, _, cyc_e2e, _ = arms[headline].solve(db, dxh, dxl, rtol=RTOL, max_cycles=MAX_CYCLES, history=False)
+        hout_hi.copy_(dxh, non_blocking=True)
+        hout_lo.copy_(dxl, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps)
+    e2e_val = sum(sweeps_per_cycle(sizes) * int(c) for c in cyc_e2e) * world / e2e_s
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    cpu = None if args.no_cpu_baseline else cpu_baseline(n)
+    head = results[headline]
+    line = {
+        "metric": METRIC, "value": head["mdof_sweeps_per_s"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{nprob} rotated anisotropic Q1 problems per GPU, {n}x{n}, eps log-U[1e-3,1], "
+                               f"theta U[0,pi], V(1,1) to 1e-8 ({headline} smoother)",
+                   "n": n, "nprob_per_gpu": nprob, "smoother": headline, "rtol": RTOL,
+                   "l2": "inputs larger than L2 (batch working set ~%d MB)" % (nprob * n * n * 4 * 7 // 2 ** 20)},
+        "solve": {arm: {"ms_per_step": r["ms_per_step"], "cycles": r["cycles"], "converged": r["converged"],
+                        "mdof_sweeps_per_s": r["mdof_sweeps_per_s"]} for arm, r in results.items()},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 3 * b.numel() * 4,
+                "d2h_bytes_per_step": 2 * b.numel() * 4, "ms_per_step": e2e_s * 1e3},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if "cnn" in results:
+        line["cnn_vs_jacobi_time"] = results["jacobi"]["ms_per_step"] / results["cnn"]["ms_per_step"]
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,222 @@
+/*
+ * mgcnn.h -- C ABI of the GB300 (sm_103a) learned-smoother multigrid library.
+ *
+ * Method: Huang, Li & Xi, "Learning optimal multigrid smoothers via neural networks"
+ * (arXiv 2102.12071).  The library solves A u = f (Sec. 2, eq. Au=f; A symmetric positive
+ * definite) on n x n interior grids of the unit square with homogeneous Dirichlet
+ * boundaries by V-cycles (Algorithm 1) whose smoother is either weighted Jacobi
+ * (Sec. 2.1) or the action H = M^{-1} produced per point by a convolutional network from
+ * the operator stencil (Sec. 4.2), and it evaluates and differentiates the two-grid
+ * convergence loss that trains that network (Sec. 3.2, eq. twogrid, Thm. sbound).
+ *
+ * Conventions shared by every entry point
+ *   Grids      n x n interior points, n = 2^m - 1 (3 <= n <= 8191), row-major:
+ *              element (i, j) at offset i*n + j, row i = y (north = +y), column j = x.
+ *              Batched grids are contiguous [nprob][n][n].
+ *   Stencils   9 coefficients, tap k = 3*(di+1) + (dj+1) is the coefficient of
+ *              u(i+di, j+dj) in row (i, j) of A; k = 4 is the diagonal.  A stencil field
+ *              is [9][n][n] (one stencil per point); taps that couple to points outside
+ *              the interior must be zero (the field is exactly the rows of A).
+ *   Kernels    per-point smoothing kernels use the stencil-field layout:
+ *              (H v)(p) = sum_k W[k][p] * v(p + d_k), v = 0 outside the interior.
+ *   Memory     every pointer documented "device" must point to memory of the current
+ *              CUDA device; the caller owns every buffer, including the workspace.  The
+ *              library allocates no device memory; a context is a small host struct.
+ *              Buffers must stay valid until the work queued on the stream completes.
+ *   Streams    `stream` is a cudaStream_t (NULL = the legacy default stream).  All
+ *              device work of a call is queued on it.  One context must not be used
+ *              from two streams at once.
+ *   Errors     every call returns an mg_status and never aborts; mg_last_error() gives
+ *              a thread-local message for the last failing call.  A CUDA error is
+ *              reported as MG_ERR_CUDA.
+ */
+#ifndef MGCNN_H
+#define MGCNN_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MG_OK = 0,
+  MG_ERR_INVALID_ARG = 1,   /* a size, pointer, kind or option is out of range        */
+  MG_ERR_WORKSPACE = 2,     /* workspace too small or misaligned (needs 256 B)         */
+  MG_ERR_CUDA = 3,          /* a CUDA runtime call or kernel launch failed             */
+  MG_ERR_NOT_CONVERGED = 4, /* mg_solve hit max_cycles before rtol (results valid)     */
+  MG_ERR_NUMERIC = 5,       /* NaN/Inf residual or a non-SPD coarsest operator         */
+  MG_ERR_TIMEOUT = 6,       /* reserved for bounded device-side waits                  */
+  MG_ERR_UNSUPPORTED = 7    /* valid request outside what this build implements        */
+} mg_status;
+
+/* Operator of one problem (Sec. 3.1 eq. constant, Sec. 4 eq. vcoeff, Sec. 6.1 eq. pde). */
+typedef enum {
+  /* -div(K grad u), K = R(theta) diag(1, eps) R(theta)^T constant (the rotated anisotropic
+     Laplacian of Sec. 6.1 with conductivity eps), bilinear (Q1) finite elements:
+     9-point constant stencil.  Uses eps (> 0) and theta; data must be NULL. */
+  MG_PROBLEM_ROTATED = 0,
+  /* constant 9-point stencil given by the caller: data = HOST float[9] (tap layout above). */
+  MG_PROBLEM_STENCIL = 1,
+  /* -div(a grad u) with a constant per cell, 5-point stencil whose edge weights are the
+     mean of the two cells sharing the edge: data = DEVICE float[(n+1)*(n+1)], cell (ci, cj)
+     spans mesh rows ci..ci+1 and columns cj..cj+1 (interior unknown (i,j) = mesh node
+     (i+1, j+1)); values must be positive. */
+  MG_PROBLEM_VARCOEF5 = 2,
+  /* per-point 9-point stencil field given by the caller: data = DEVICE float[9*n*n]. */
+  MG_PROBLEM_FIELD = 3
+} mg_problem_kind;
+
+typedef struct {
+  int n;              /* interior points per side, 2^m - 1                          */
+  int kind;           /* mg_problem_kind                                            */
+  double eps;         /* MG_PROBLEM_ROTATED: conductivity (eps in (0, 1] typical)   */
+  double theta;       /* MG_PROBLEM_ROTATED: angle of anisotropy, radians           */
+  const float* data;  /* see mg_problem_kind; copied during mg_setup                */
+} mg_problem;
+
+typedef enum {
+  MG_SMOOTH_JACOBI = 0, /* weighted Jacobi, H = omega D^{-1} (Sec. 2.1)              */
+  MG_SMOOTH_CNN = 1     /* per-point 3x3 kernels from the stencil network (Sec. 4.2)  */
+} mg_smoother_kind;
+
+typedef struct {
+  int smoother;     /* mg_smoother_kind                                               */
+  int nu1, nu2;     /* pre-/post-smoothing steps per level; this build supports 1, 1  */
+  float omega;      /* Jacobi weight (2/3 in the paper, Sec. 6.1); also the Jacobi part
+                       of the network output W = (omega*delta + NN)/D                   */
+  int coarsest_n;   /* stop coarsening at this size (this build: 3)                  */
+  int conv_bf16;    /* 1: network weights and activations rounded to bfloat16, FP32
+                       accumulation; 0: FP32 throughout                                 */
+} mg_options;
+
+typedef struct mg_ctx mg_ctx;
+typedef struct mg_train_ctx mg_train_ctx;
+
+/* ---------------------------------------------------------------- hierarchy ---- */
+
+/* Bytes of device workspace mg_setup needs for this batch (0 if the arguments are
+   invalid; mg_last_error() says why).  All problems of one batch must share n and be
+   either all constant-stencil (ROTATED/STENCIL) or all per-point (VARCOEF5/FIELD). */
+size_t mg_workspace_size(const mg_problem* problems, int nprob, const mg_options* opts);
+
+/* Builds the multigrid hierarchy of Algorithm 1 for nprob problems on `stream`:
+   level-0 stencils (Sec. 6.1 eq. pde / Sec. 4), Galerkin coarse operators P^T A P
+   (Sec. 2.2) with full coarsening and bilinear P (Sec. 6.1, Fig. full_coarsening) down to
+   coarsest_n, the FP64 Cholesky factor of the coarsest operator, and -- for
+   MG_SMOOTH_CNN -- the per-point smoothing kernels of every smoothed level from the
+   network with parameters net_params (DEVICE float[mg_net_nparams()], read during this
+   call only; NULL for Jacobi).  workspace: DEVICE, >= mg_workspace_size bytes, 256-byte
+   aligned, owned by the caller and used exclusively by this context until mg_destroy.
+   On success *out receives a host handle. */
+mg_status mg_setup(const mg_problem* problems, int nprob, const mg_options* opts,
+                   const float* net_params, void* workspace, size_t ws_bytes,
+                   void* stream, mg_ctx** out);
+
+/* Releases the host handle (the workspace stays the caller's). NULL is ignored. */
+void mg_destroy(mg_ctx* ctx);
+
+int mg_num_levels(const mg_ctx* ctx);          /* levels including the coarsest      */
+int mg_level_n(const mg_ctx* ctx, int level);  /* side of level `level`, 0 if invalid */
+
+/* Copies the stencil field of (prob, level) to out (DEVICE float[9*n_l*n_l]). */
+mg_status mg_get_stencil(const mg_ctx* ctx, int prob, int level, float* out, void* stream);
+
+/* Copies the per-point smoothing kernels H of (prob, level) to out (DEVICE
+   float[9*n_l*n_l]), expanded to one 3x3 kernel per point (Jacobi: omega/D at tap 4). */
+mg_status mg_get_kernels(const mg_ctx* ctx, int prob, int level, float* out, void* stream);
+
+/* Weighted-Jacobi or CNN smoothing on one level of one problem (eq. iteration):
+   nsteps times u <- u + H (f - A u).  f, u: DEVICE float[n_l*n_l].  Uses the context's
+   level-`level` work vectors as scratch. */
+mg_status mg_smoother_apply(mg_ctx* ctx, int prob, int level, const float* f, float* u,
+                            int nsteps, void* stream);
+
+/* ------------------------------------------------------------------ solving ---- */
+
+/* One V-cycle (Algorithm 1) on every problem: x <- x + V(b - A x), where the iterate
+   x = x_hi + x_lo is an unevaluated float-float pair so the outer residual can reach 1e-8.
+   b, x_hi: DEVICE float[nprob*n*n]; x_lo: DEVICE float[nprob*n*n] or NULL (then x_lo is
+   taken as zero and not written); rel_res: DEVICE float[nprob] or NULL, receives
+   ||b - A x||_2 / ||b||_2 after the cycle.  The cycle runs on the error equation A e = r
+   in FP32; the outer residual is evaluated in compensated (float-float) arithmetic. */
+mg_status mg_vcycle(mg_ctx* ctx, const float* b, float* x_hi, float* x_lo, float* rel_res,
+                    void* stream);
+
+/* Repeats V-cycles until ||b - A x||_2 / ||b||_2 < rtol (the stopping rule of Sec. 6.1,
+   evaluation metrics) or max_cycles cycles, per problem.  b, x_hi, x_lo as for mg_vcycle
+   (x_hi holds the initial guess; x_lo NULL means a zero low part kept in the workspace).
+   hist: HOST double[nprob*(max_cycles+1)] or NULL; row p receives the relative residual
+   after 0, 1, ... cycles (entries past cycles[p] are left untouched).  cycles: HOST
+   int[nprob] or NULL, receives the cycle count per problem.  Blocks the calling thread
+   until `stream` has finished the solve.  Returns MG_ERR_NOT_CONVERGED if any problem
+   stopped at max_cycles, MG_ERR_NUMERIC on a NaN/Inf residual. */
+mg_status mg_solve(mg_ctx* ctx, const float* b, float* x_hi, float* x_lo, double rtol,
+                   int max_cycles, double* hist, int* cycles, void* stream);
+
+/* ------------------------------------------------------------ network (a3) ---- */
+
+/* Number of network parameters: 3x3 convolutions 9->7->5->3 (no bias) and the layer
+   from the 3x3 window of the 3-channel map (27 inputs) to the 9 kernel taps
+   (Sec. 4.2 and the layer sizes of Sec. 6.2).  Layout: w1[7][9][3][3], w2[5][7][3][3],
+   w3[3][5][3][3], wf[9][3][3][3]; LeakyReLU slope 0.01 after each convolution. */
+int mg_net_nparams(void);
+
+/* Network inference on nprob stencil fields (DEVICE float[nprob][9][n][n]): per point,
+   input channel c = st[c]/st[4] (zero outside the grid), output kernel
+   W = (omega*delta_4 + NN)/st[4] written to W (DEVICE float[nprob][9][n][n]).
+   params: DEVICE float[mg_net_nparams()]. */
+mg_status mg_net_forward(int n, int nprob, const float* fields, const float* params,
+                         float omega, int conv_bf16, float* W, void* stream);
+
+/* --------------------------------------------------------- training (a11-a12) ---- */
+
+/* Bytes of device workspace for mg_train_setup (0 on invalid arguments). */
+size_t mg_train_workspace_size(const mg_problem* problems, int nprob, int nvec,
+                               const mg_options* opts);
+
+/* Prepares a training batch of nprob problems (all of one size n >= 7, any kinds of
+   mg_problem_kind), nvec random vectors each: stencil fields, the two-grid Galerkin
+   operator P^T A P and its FP64 banded Cholesky factor.  workspace: DEVICE, caller-owned. */
+mg_status mg_train_setup(const mg_problem* problems, int nprob, int nvec,
+                         const mg_options* opts, void* workspace, size_t ws_bytes,
+                         void* stream, mg_train_ctx** out);
+
+void mg_train_destroy(mg_train_ctx* ctx);
+
+/* Loss and gradient of the two-grid convergence objective (eq. twogrid with one pre- and
+   one post-smoothing step, eq. overalltrain with u_* = 0, Thm. sbound):
+     loss = (1/nprob) sum_b (1/nvec) sum_j || S C S z_bj ||^2 / n^2,
+     S = I - H A,  C = I - P (P^T A P)^{-1} P^T A,
+   with H the network's per-point kernels for problem b.  z: DEVICE float[nprob][nvec][n][n]
+   (the random vectors, supplied by the caller), params: DEVICE float[mg_net_nparams()],
+   grad_out: DEVICE float[mg_net_nparams()] (overwritten with dloss/dparams; may be NULL),
+   loss_out: DEVICE float[1]. */
+mg_status mg_train_step(mg_train_ctx* ctx, const float* params, const float* z,
+                        float* grad_out, float* loss_out, void* stream);
+
+/* ------------------------------------------------------------ measurement ---- */
+
+/* Optional CUDA-event timing of individual kernel launches on the launching stream, for
+   measurement tools; solving does not need it.  mg_profile_enable resets all counters and
+   turns timing on (enable != 0) or off.  Timings are collected whenever mg_solve
+   synchronises and by mg_profile_read (which requires the stream to be idle).
+   kernel_class: 0 outer residual, 1 down-sweep of level 0, 2 up-sweep of level 0 (with the
+   iterate update), 3 one-CTA coarse tail / small-problem solve, 4 down-sweeps of levels >= 1,
+   5 up-sweeps of levels >= 1; -1 returns in *launches the number of kernels this context
+   launched since the last reset (timing or not). */
+mg_status mg_profile_enable(mg_ctx* ctx, int enable);
+mg_status mg_profile_read(mg_ctx* ctx, int kernel_class, double* total_ms, long long* launches);
+
+/* ------------------------------------------------------------------- misc ---- */
+
+/* Interior Q1 stencil of MG_PROBLEM_ROTATED, rounded to float (host, no device work). */
+mg_status mg_rotated_stencil(double eps, double theta, float out[9]);
+
+const char* mg_status_string(mg_status s);
+const char* mg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MGCNN_H */

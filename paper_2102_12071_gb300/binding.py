@@ -1,0 +1,226 @@
+"""Thin ctypes binding of libmgcnn.so (C ABI in include/mgcnn.h).
+
+Argument marshalling only: every computation runs in the CUDA library.  Device arrays
+are torch CUDA tensors (float32, contiguous); streams default to torch's current stream.
+Loading fails loudly if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libmgcnn.so")
+
+MG_OK, MG_ERR_INVALID_ARG, MG_ERR_WORKSPACE, MG_ERR_CUDA, MG_ERR_NOT_CONVERGED, MG_ERR_NUMERIC, \
+    MG_ERR_TIMEOUT, MG_ERR_UNSUPPORTED = range(8)
+MG_PROBLEM_ROTATED, MG_PROBLEM_STENCIL, MG_PROBLEM_VARCOEF5, MG_PROBLEM_FIELD = range(4)
+MG_SMOOTH_JACOBI, MG_SMOOTH_CNN = 0, 1
+
+
+class mg_problem(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("kind", ctypes.c_int), ("eps", ctypes.c_double),
+                ("theta", ctypes.c_double), ("data", ctypes.c_void_p)]
+
+
+class mg_options(ctypes.Structure):
+    _fields_ = [("smoother", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
+                ("omega", ctypes.c_float), ("coarsest_n", ctypes.c_int), ("conv_bf16", ctypes.c_int)]
+
+
+class MGError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {msg} (status {status})")
+        self.status = status
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def lib() -> ctypes.CDLL:
+    """Load libmgcnn.so; raises if it is missing (no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built; run __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "mg_workspace_size": (ctypes.c_size_t, [ctypes.POINTER(mg_problem), ctypes.c_int, ctypes.POINTER(mg_options)]),
+        "mg_setup": (ctypes.c_int, [ctypes.POINTER(mg_problem), ctypes.c_int, ctypes.POINTER(mg_options), _P, _P,
+                                    ctypes.c_size_t, _P, ctypes.POINTER(_P)]),
+        "mg_destroy": (None, [_P]),
+        "mg_num_levels": (ctypes.c_int, [_P]),
+        "mg_level_n": (ctypes.c_int, [_P, ctypes.c_int]),
+        "mg_get_stencil": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P]),
+        "mg_get_kernels": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P]),
+        "mg_smoother_apply": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
+        "mg_vcycle": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+        "mg_solve": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_double, ctypes.c_int, _P, _P, _P]),
+        "mg_net_nparams": (ctypes.c_int, []),
+        "mg_net_forward": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_float, ctypes.c_int, _P, _P]),
+        "mg_train_workspace_size": (ctypes.c_size_t, [ctypes.POINTER(mg_problem), ctypes.c_int, ctypes.c_int,
+                                                      ctypes.POINTER(mg_options)]),
+        "mg_train_setup": (ctypes.c_int, [ctypes.POINTER(mg_problem), ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(mg_options), _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)]),
+        "mg_train_destroy": (None, [_P]),
+        "mg_train_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+        "mg_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
+        "mg_profile_read": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_longlong)]),
+        "mg_rotated_stencil": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_float)]),
+        "mg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "mg_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def check(status: int, where: str) -> int:
+    if status not in (MG_OK,):
+        raise MGError(status, where, lib().mg_last_error().decode())
+    return status
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream
+    import torch
+
+    return torch.cuda.current_stream().cuda_stream
+
+
+def problems_array(problems: list[dict]):
+    arr = (mg_problem * len(problems))()
+    keep = []
+    for k, p in enumerate(problems):
+        arr[k].n = p["n"]
+        arr[k].kind = p["kind"]
+        arr[k].eps = p.get("eps", 0.0)
+        arr[k].theta = p.get("theta", 0.0)
+        data = p.get("data")
+        if data is None:
+            arr[k].data = None
+        elif isinstance(data, int):
+            arr[k].data = data
+        elif hasattr(data, "data_ptr"):
+            arr[k].data = data.data_ptr()
+            keep.append(data)
+        else:  # host stencil: 9 floats
+            buf = (ctypes.c_float * 9)(*[float(v) for v in data])
+            keep.append(buf)
+            arr[k].data = ctypes.cast(buf, ctypes.c_void_p)
+    return arr, keep
+
+
+def options(smoother: int = MG_SMOOTH_JACOBI, omega: float = 2.0 / 3.0, coarsest_n: int = 3,
+            conv_bf16: int = 0) -> mg_options:
+    return mg_options(smoother, 1, 1, omega, coarsest_n, conv_bf16)
+
+
+def mg_workspace_size(probs, nprob: int, opts: mg_options) -> int:
+    return lib().mg_workspace_size(probs, nprob, ctypes.byref(opts))
+
+
+def mg_setup(probs, nprob: int, opts: mg_options, net_params, workspace, ws_bytes: int, stream=None) -> int:
+    out = _P()
+    check(lib().mg_setup(probs, nprob, ctypes.byref(opts), _ptr(net_params), _ptr(workspace), ws_bytes,
+                         _stream(stream), ctypes.byref(out)), "mg_setup")
+    return out.value
+
+
+def mg_destroy(ctx: int) -> None:
+    lib().mg_destroy(ctx)
+
+
+def mg_num_levels(ctx: int) -> int:
+    return lib().mg_num_levels(ctx)
+
+
+def mg_level_n(ctx: int, level: int) -> int:
+    return lib().mg_level_n(ctx, level)
+
+
+def mg_get_stencil(ctx, prob, level, out, stream=None):
+    check(lib().mg_get_stencil(ctx, prob, level, _ptr(out), _stream(stream)), "mg_get_stencil")
+
+
+def mg_get_kernels(ctx, prob, level, out, stream=None):
+    check(lib().mg_get_kernels(ctx, prob, level, _ptr(out), _stream(stream)), "mg_get_kernels")
+
+
+def mg_smoother_apply(ctx, prob, level, f, u, nsteps=1, stream=None):
+    check(lib().mg_smoother_apply(ctx, prob, level, _ptr(f), _ptr(u), nsteps, _stream(stream)), "mg_smoother_apply")
+
+
+def mg_vcycle(ctx, b, x_hi, x_lo=None, rel_res=None, stream=None):
+    check(lib().mg_vcycle(ctx, _ptr(b), _ptr(x_hi), _ptr(x_lo), _ptr(rel_res), _stream(stream)), "mg_vcycle")
+
+
+def mg_solve(ctx, b, x_hi, x_lo, rtol, max_cycles, hist=None, cycles=None, stream=None) -> int:
+    """hist: numpy float64 [nprob, max_cycles+1] or None; cycles: numpy int32 [nprob] or None.
+    Returns the status (MG_OK or MG_ERR_NOT_CONVERGED); other failures raise."""
+    hp = hist.ctypes.data if hist is not None else None
+    cp = cycles.ctypes.data if cycles is not None else None
+    st = lib().mg_solve(ctx, _ptr(b), _ptr(x_hi), _ptr(x_lo), float(rtol), int(max_cycles), hp, cp,
+                        _stream(stream))
+    if st not in (MG_OK, MG_ERR_NOT_CONVERGED):
+        check(st, "mg_solve")
+    return st
+
+
+def mg_net_nparams() -> int:
+    return lib().mg_net_nparams()
+
+
+def mg_net_forward(n, nprob, fields, params, omega, conv_bf16, W, stream=None):
+    check(lib().mg_net_forward(n, nprob, _ptr(fields), _ptr(params), float(omega), int(conv_bf16), _ptr(W),
+                               _stream(stream)), "mg_net_forward")
+
+
+def mg_train_workspace_size(probs, nprob, nvec, opts) -> int:
+    return lib().mg_train_workspace_size(probs, nprob, nvec, ctypes.byref(opts))
+
+
+def mg_train_setup(probs, nprob, nvec, opts, workspace, ws_bytes, stream=None) -> int:
+    out = _P()
+    check(lib().mg_train_setup(probs, nprob, nvec, ctypes.byref(opts), _ptr(workspace), ws_bytes, _stream(stream),
+                               ctypes.byref(out)), "mg_train_setup")
+    return out.value
+
+
+def mg_train_destroy(ctx) -> None:
+    lib().mg_train_destroy(ctx)
+
+
+def mg_train_step(ctx, params, z, grad_out, loss_out, stream=None):
+    check(lib().mg_train_step(ctx, _ptr(params), _ptr(z), _ptr(grad_out), _ptr(loss_out), _stream(stream)),
+          "mg_train_step")
+
+
+def mg_profile_enable(ctx, enable: bool) -> None:
+    check(lib().mg_profile_enable(ctx, int(enable)), "mg_profile_enable")
+
+
+def mg_profile_read(ctx, kernel_class: int) -> tuple[float, int]:
+    ms = ctypes.c_double()
+    n = ctypes.c_longlong()
+    check(lib().mg_profile_read(ctx, kernel_class, ctypes.byref(ms), ctypes.byref(n)), "mg_profile_read")
+    return ms.value, n.value
+
+
+def mg_rotated_stencil(eps: float, theta: float):
+    out = (ctypes.c_float * 9)()
+    check(lib().mg_rotated_stencil(float(eps), float(theta), out), "mg_rotated_stencil")
+    return list(out)

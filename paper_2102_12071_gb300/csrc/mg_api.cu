@@ -1,0 +1,451 @@
+// mg_api.cu -- host side of the C ABI declared in include/mgcnn.h.
+//
+// Validates arguments, carves the caller's workspace, records the device descriptors of
+// the hierarchy and queues the kernels of mg_setup.cu, mg_cycle.cu and mg_net.cu on the
+// caller's stream.  It never allocates device memory and never aborts.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "mg_internal.h"
+#include "mgcnn.h"
+
+using namespace mg;
+
+static thread_local char g_err[512] = "";
+
+static mg_status fail(mg_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+#define CK(call)                                                                               \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) return fail(MG_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));  \
+  } while (0)
+
+// ------------------------------------------------------------------ planning
+namespace {
+
+struct Plan {
+  int nprob = 0, n0 = 0, L = 0, lstar = 0, sk = SK_CONST, hk = HK_JACOBI, tail_solve = 0;
+  int nl[MG_MAXL] = {0};
+  int ntiles_max = 0;
+  size_t bytes = 0;
+};
+
+bool is_pow2m1(int n) { return n >= 1 && ((n + 1) & n) == 0; }
+
+mg_status make_plan(const mg_problem* probs, int nprob, const mg_options* o, Plan& P) {
+  if (!probs || nprob <= 0 || !o) return fail(MG_ERR_INVALID_ARG, "problems/options missing or nprob <= 0");
+  if (nprob > 65535) return fail(MG_ERR_INVALID_ARG, "nprob %d > 65535", nprob);
+  if (o->smoother != MG_SMOOTH_JACOBI && o->smoother != MG_SMOOTH_CNN)
+    return fail(MG_ERR_INVALID_ARG, "unknown smoother %d", o->smoother);
+  if (o->nu1 != 1 || o->nu2 != 1) return fail(MG_ERR_UNSUPPORTED, "only nu1 = nu2 = 1 is implemented");
+  if (o->coarsest_n != 3 && o->coarsest_n != 7) return fail(MG_ERR_UNSUPPORTED, "coarsest_n must be 3 or 7");
+  if (!(o->omega > 0.f) || !(o->omega < 2.f)) return fail(MG_ERR_INVALID_ARG, "omega must be in (0, 2)");
+  const int n = probs[0].n;
+  if (!is_pow2m1(n) || n < o->coarsest_n || n > 8191)
+    return fail(MG_ERR_INVALID_ARG, "n = %d must be 2^m - 1 in [coarsest_n, 8191]", n);
+  int nconst = 0;
+  for (int p = 0; p < nprob; ++p) {
+    const mg_problem& q = probs[p];
+    if (q.n != n) return fail(MG_ERR_UNSUPPORTED, "all problems of a batch must share n (problem %d)", p);
+    switch (q.kind) {
+      case MG_PROBLEM_ROTATED:
+        if (!(q.eps > 0.0) || !isfinite(q.theta)) return fail(MG_ERR_INVALID_ARG, "problem %d: eps must be > 0", p);
+        ++nconst;
+        break;
+      case MG_PROBLEM_STENCIL:
+        if (!q.data) return fail(MG_ERR_INVALID_ARG, "problem %d: stencil pointer is NULL", p);
+        ++nconst;
+        break;
+      case MG_PROBLEM_VARCOEF5:
+      case MG_PROBLEM_FIELD:
+        if (!q.data) return fail(MG_ERR_INVALID_ARG, "problem %d: device data pointer is NULL", p);
+        break;
+      default:
+        return fail(MG_ERR_INVALID_ARG, "problem %d: unknown kind %d", p, q.kind);
+    }
+  }
+  if (nconst != 0 && nconst != nprob)
+    return fail(MG_ERR_UNSUPPORTED, "a batch mixes constant-stencil and per-point problems");
+  P.nprob = nprob;
+  P.n0 = n;
+  P.sk = nconst ? SK_CONST : SK_FIELD;
+  P.hk = o->smoother == MG_SMOOTH_JACOBI ? HK_JACOBI : (P.sk == SK_CONST ? HK_TABLE : HK_FIELD);
+  int m = n, L = 0;
+  P.nl[L++] = m;
+  while (m > o->coarsest_n) {
+    m = (m - 1) / 2;
+    if (L >= MG_MAXL) return fail(MG_ERR_INVALID_ARG, "too many levels");
+    P.nl[L++] = m;
+  }
+  P.L = L;
+  P.lstar = 0;
+  while (P.lstar < L && P.nl[P.lstar] > MG_TAIL_N) ++P.lstar;
+  P.tail_solve = P.lstar == 0;
+  const int nt = tiles_per_side(n);
+  P.ntiles_max = nt * nt;
+  if (tail_smem_bytes(P.nl, P.lstar, L, P.hk) > 200 * 1024) return fail(MG_ERR_UNSUPPORTED, "tail does not fit in shared memory");
+  return MG_OK;
+}
+
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base((char*)b) {}
+  template <class T>
+  T* take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    T* p = base ? (T*)(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+}  // namespace
+
+struct mg_ctx {
+  Plan plan;
+  mg_options opts;
+  CycleArgs args;
+  std::vector<ProbDev> h_probs;
+  std::vector<ProbState> h_state;
+  float* xlo_ws = nullptr;
+  int* d_fail = nullptr;
+  NetJob* d_jobs = nullptr;
+  Profiler prof;
+};
+
+// Workspace layout; with base == nullptr only the size is computed.
+static size_t carve(const Plan& P, const mg_options& o, void* base, mg_ctx* ctx) {
+  Carver c(base);
+  ProbDev* probs = c.take<ProbDev>(P.nprob);
+  ProbState* state = c.take<ProbState>(P.nprob);
+  float* partials = c.take<float>((size_t)P.nprob * P.ntiles_max);
+  float* xlo = c.take<float>((size_t)P.nprob * P.n0 * P.n0);
+  int* fail_flag = c.take<int>(4);
+  NetJob* jobs = c.take<NetJob>((size_t)P.nprob * P.L);
+  std::vector<ProbDev> hp(ctx ? P.nprob : 0);
+  for (int p = 0; p < P.nprob; ++p) {
+    ProbDev d;
+    memset(&d, 0, sizeof(d));
+    for (int l = 0; l < P.L; ++l) {
+      const int n = P.nl[l];
+      const size_t nn = (size_t)n * n;
+      LevelDev& v = d.lv[l];
+      v.n = n;
+      v.T = n < MG_PROXY ? n : MG_PROXY;
+      v.r = c.take<float>(nn);
+      v.e = c.take<float>(nn);
+      if (P.sk == SK_FIELD) v.st = c.take<float>(9 * nn);
+      if (l < P.L - 1) {
+        if (P.hk == HK_FIELD) v.W = c.take<float>(9 * nn);
+        else if (P.hk == HK_TABLE) v.W = c.take<float>((size_t)9 * v.T * v.T);
+      }
+    }
+    d.m = P.nl[P.L - 1] * P.nl[P.L - 1];
+    d.chol = c.take<double>((size_t)d.m * d.m);
+    if (ctx) hp[p] = d;
+  }
+  if (ctx) {
+    ctx->h_probs.swap(hp);
+    ctx->args.probs = probs;
+    ctx->args.state = state;
+    ctx->args.partials = partials;
+    ctx->xlo_ws = xlo;
+    ctx->d_fail = fail_flag;
+    ctx->d_jobs = jobs;
+  }
+  (void)o;
+  return c.off + 256;
+}
+
+static void rotated_stencil(double eps, double theta, double s[9]) {
+  // Q1 element stiffness of -div(K grad u), K = [[a, b], [b, c]] (closed form)
+  const double cs = cos(theta), sn = sin(theta);
+  const double a = cs * cs + eps * sn * sn, c = sn * sn + eps * cs * cs, b = cs * sn * (1.0 - eps);
+  const double corner = -(a + c) / 6.0;
+  s[0] = corner - b / 2;  s[1] = (a - 2 * c) / 3;  s[2] = corner + b / 2;
+  s[3] = (c - 2 * a) / 3; s[4] = 4 * (a + c) / 3;  s[5] = (c - 2 * a) / 3;
+  s[6] = corner + b / 2;  s[7] = (a - 2 * c) / 3;  s[8] = corner - b / 2;
+}
+
+extern "C" {
+
+mg_status mg_rotated_stencil(double eps, double theta, float out[9]) {
+  if (!out || !(eps > 0.0)) return fail(MG_ERR_INVALID_ARG, "mg_rotated_stencil: bad arguments");
+  double s[9];
+  rotated_stencil(eps, theta, s);
+  for (int k = 0; k < 9; ++k) out[k] = (float)s[k];
+  return MG_OK;
+}
+
+size_t mg_workspace_size(const mg_problem* problems, int nprob, const mg_options* opts) {
+  Plan P;
+  if (make_plan(problems, nprob, opts, P) != MG_OK) return 0;
+  return carve(P, *opts, nullptr, nullptr);
+}
+
+int mg_net_nparams(void) { return MG_NPARAMS; }
+
+mg_status mg_setup(const mg_problem* problems, int nprob, const mg_options* opts, const float* net_params,
+                   void* workspace, size_t ws_bytes, void* stream, mg_ctx** out) {
+  if (!out) return fail(MG_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  Plan P;
+  mg_status st = make_plan(problems, nprob, opts, P);
+  if (st != MG_OK) return st;
+  if (opts->smoother == MG_SMOOTH_CNN && !net_params) return fail(MG_ERR_INVALID_ARG, "CNN smoother needs net_params");
+  const size_t need = carve(P, *opts, nullptr, nullptr);
+  if (!workspace || ws_bytes < need) return fail(MG_ERR_WORKSPACE, "workspace needs %zu bytes, got %zu", need, ws_bytes);
+  if (((uintptr_t)workspace & 255) != 0) return fail(MG_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  mg_ctx* ctx = new mg_ctx();
+  ctx->plan = P;
+  ctx->opts = *opts;
+  carve(P, *opts, workspace, ctx);
+  CycleArgs& a = ctx->args;
+  a.ntiles_max = P.ntiles_max;
+  a.nprob = P.nprob;
+  a.n0 = P.n0;
+  a.L = P.L;
+  a.lstar = P.lstar;
+  for (int l = 0; l < MG_MAXL; ++l) a.nl[l] = P.nl[l];
+  a.sk = P.sk;
+  a.hk = P.hk;
+  a.omega = opts->omega;
+  a.stream = s;
+  a.prof = &ctx->prof;
+  ctx->h_state.resize(P.nprob);
+  // level-0 stencils
+  for (int p = 0; p < nprob; ++p) {
+    const mg_problem& q = problems[p];
+    LevelDev& v = ctx->h_probs[p].lv[0];
+    if (q.kind == MG_PROBLEM_ROTATED) {
+      double sd[9];
+      rotated_stencil(q.eps, q.theta, sd);
+      for (int k = 0; k < 9; ++k) v.s[k] = (float)sd[k];
+    } else if (q.kind == MG_PROBLEM_STENCIL) {
+      for (int k = 0; k < 9; ++k) v.s[k] = q.data[k];
+    }
+    if (P.sk == SK_CONST && !(v.s[4] > 0.f)) {
+      delete ctx;
+      return fail(MG_ERR_INVALID_ARG, "problem %d: stencil diagonal must be positive", p);
+    }
+  }
+  mg_status rc = MG_OK;
+  auto run = [&]() -> mg_status {
+    CK(cudaMemcpyAsync(a.probs, ctx->h_probs.data(), sizeof(ProbDev) * P.nprob, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(ctx->d_fail, 0, sizeof(int), s));
+    if (P.sk == SK_FIELD) {
+      const size_t nn = (size_t)P.n0 * P.n0;
+      for (int p = 0; p < nprob; ++p) {
+        float* f0 = ctx->h_probs[p].lv[0].st;
+        if (problems[p].kind == MG_PROBLEM_VARCOEF5) CK(launch_varcoef5(P.n0, 1, problems[p].data, 0, f0, 0, s));
+        else CK(cudaMemcpyAsync(f0, problems[p].data, 9 * nn * sizeof(float), cudaMemcpyDeviceToDevice, s));
+      }
+      for (int l = 0; l + 1 < P.L; ++l) CK(launch_rap_field(a.probs, P.nprob, l, P.nl[l + 1], s));
+    } else {
+      CK(launch_rap_const(a.probs, P.nprob, P.L, s));
+    }
+    CK(launch_coarsest_factor(a.probs, P.nprob, P.L, P.sk, ctx->d_fail, s));
+    if (P.hk != HK_JACOBI && P.L > 1) {
+      std::vector<NetJob> jobs;
+      int nmax = 0;
+      for (int p = 0; p < nprob; ++p)
+        for (int l = 0; l + 1 < P.L; ++l) {
+          const LevelDev& v = ctx->h_probs[p].lv[l];
+          NetJob J;
+          J.st = P.sk == SK_FIELD ? v.st : nullptr;
+          J.s = P.sk == SK_CONST ? &a.probs[p].lv[l].s[0] : nullptr;  // device address
+          J.W = v.W;
+          J.n = P.sk == SK_FIELD ? v.n : v.T;
+          J.pad_ = 0;
+          nmax = J.n > nmax ? J.n : nmax;
+          jobs.push_back(J);
+        }
+      CK(cudaMemcpyAsync(ctx->d_jobs, jobs.data(), sizeof(NetJob) * jobs.size(), cudaMemcpyHostToDevice, s));
+      CK(launch_net_forward(ctx->d_jobs, (int)jobs.size(), nmax, net_params, opts->omega, opts->conv_bf16, s));
+      // the host vector must outlive the asynchronous copy
+      CK(cudaStreamSynchronize(s));
+    }
+    int failed = 0;
+    CK(cudaMemcpyAsync(&failed, ctx->d_fail, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (failed) return fail(MG_ERR_NUMERIC, "coarsest operator is not positive definite");
+    return MG_OK;
+  };
+  rc = run();
+  if (rc != MG_OK) {
+    delete ctx;
+    return rc;
+  }
+  *out = ctx;
+  return MG_OK;
+}
+
+void mg_destroy(mg_ctx* ctx) { delete ctx; }
+
+int mg_num_levels(const mg_ctx* ctx) { return ctx ? ctx->plan.L : 0; }
+
+int mg_level_n(const mg_ctx* ctx, int level) {
+  if (!ctx || level < 0 || level >= ctx->plan.L) return 0;
+  return ctx->plan.nl[level];
+}
+
+mg_status mg_get_stencil(const mg_ctx* ctx, int prob, int level, float* out, void* stream) {
+  if (!ctx || !out || prob < 0 || prob >= ctx->plan.nprob || level < 0 || level >= ctx->plan.L)
+    return fail(MG_ERR_INVALID_ARG, "mg_get_stencil: bad arguments");
+  CK(launch_expand_stencil(ctx->args.probs, prob, level, ctx->plan.nl[level], ctx->plan.sk, out, (cudaStream_t)stream));
+  return MG_OK;
+}
+
+mg_status mg_get_kernels(const mg_ctx* ctx, int prob, int level, float* out, void* stream) {
+  if (!ctx || !out || prob < 0 || prob >= ctx->plan.nprob || level < 0 || level >= ctx->plan.L - 1)
+    return fail(MG_ERR_INVALID_ARG, "mg_get_kernels: bad arguments (smoothed levels are 0..L-2)");
+  CK(launch_expand_kernels(ctx->args.probs, prob, level, ctx->plan.nl[level], ctx->plan.sk, ctx->plan.hk,
+                           ctx->opts.omega, out, (cudaStream_t)stream));
+  return MG_OK;
+}
+
+mg_status mg_smoother_apply(mg_ctx* ctx, int prob, int level, const float* f, float* u, int nsteps, void* stream) {
+  if (!ctx || !f || !u || prob < 0 || prob >= ctx->plan.nprob || level < 0 || level >= ctx->plan.L - 1 || nsteps < 0)
+    return fail(MG_ERR_INVALID_ARG, "mg_smoother_apply: bad arguments (smoothed levels are 0..L-2)");
+  CycleArgs a = ctx->args;
+  a.stream = (cudaStream_t)stream;
+  CK(launch_smoother(a, prob, level, f, u, nsteps));
+  return MG_OK;
+}
+
+mg_status mg_vcycle(mg_ctx* ctx, const float* b, float* x_hi, float* x_lo, float* rel_res, void* stream) {
+  if (!ctx || !b || !x_hi) return fail(MG_ERR_INVALID_ARG, "mg_vcycle: ctx, b and x_hi are required");
+  CycleArgs a = ctx->args;
+  a.stream = (cudaStream_t)stream;
+  const int big = 1 << 30;
+  CK(cudaMemsetAsync(a.state, 0, sizeof(ProbState) * a.nprob, a.stream));
+  CK(launch_bnorm(a, b));
+  if (ctx->plan.tail_solve) {
+    CK(launch_tail_solve(a, b, x_hi, x_lo, -1.f, big, 1, 1));
+  } else {
+    CK(launch_residual(a, b, x_hi, x_lo, -1.f, big));
+    CK(launch_cycle(a, x_hi, x_lo));
+    CK(launch_residual(a, b, x_hi, x_lo, -1.f, big));
+  }
+  if (rel_res) CK(launch_copy_rel(a.state, rel_res, a.nprob, a.stream));
+  return MG_OK;
+}
+
+mg_status mg_solve(mg_ctx* ctx, const float* b, float* x_hi, float* x_lo, double rtol, int max_cycles, double* hist,
+                   int* cycles, void* stream) {
+  if (!ctx || !b || !x_hi) return fail(MG_ERR_INVALID_ARG, "mg_solve: ctx, b and x_hi are required");
+  if (max_cycles < 0 || max_cycles > 100000000) return fail(MG_ERR_INVALID_ARG, "max_cycles out of range");
+  CycleArgs a = ctx->args;
+  a.stream = (cudaStream_t)stream;
+  const Plan& P = ctx->plan;
+  float* xlo = x_lo;
+  if (!xlo) {
+    xlo = ctx->xlo_ws;
+    CK(cudaMemsetAsync(xlo, 0, sizeof(float) * (size_t)P.nprob * P.n0 * P.n0, a.stream));
+  }
+  CK(cudaMemsetAsync(a.state, 0, sizeof(ProbState) * a.nprob, a.stream));
+  CK(launch_bnorm(a, b));
+  std::vector<int> seen(P.nprob, 0);
+  const float frtol = (float)rtol;
+  int G = 16;
+  for (;;) {
+    if (P.tail_solve) {
+      CK(launch_tail_solve(a, b, x_hi, xlo, frtol, max_cycles, G, 0));
+    } else {
+      for (int c = 0; c < G; ++c) {
+        CK(launch_residual(a, b, x_hi, xlo, frtol, max_cycles));
+        CK(launch_cycle(a, x_hi, xlo));
+      }
+    }
+    CK(cudaMemcpyAsync(ctx->h_state.data(), a.state, sizeof(ProbState) * P.nprob, cudaMemcpyDeviceToHost, a.stream));
+    CK(cudaStreamSynchronize(a.stream));
+    ctx->prof.collect();
+    int active = 0;
+    for (int p = 0; p < P.nprob; ++p) {
+      const ProbState& S = ctx->h_state[p];
+      if (hist)
+        for (int k = seen[p]; k < S.iter; ++k) hist[(size_t)p * (max_cycles + 1) + k] = S.hist[k % MG_HRING];
+      seen[p] = S.iter;
+      active += S.active;
+    }
+    if (!active) break;
+    G = G < 128 ? 2 * G : 128;
+  }
+  mg_status rc = MG_OK;
+  for (int p = 0; p < P.nprob; ++p) {
+    const ProbState& S = ctx->h_state[p];
+    if (cycles) cycles[p] = S.cycles;
+    if (S.status == 3) rc = MG_ERR_NUMERIC;
+    else if (S.status == 2 && rc == MG_OK) rc = MG_ERR_NOT_CONVERGED;
+  }
+  if (rc == MG_ERR_NUMERIC) fail(rc, "non-finite residual");
+  else if (rc == MG_ERR_NOT_CONVERGED) fail(rc, "max_cycles reached before rtol");
+  return rc;
+}
+
+mg_status mg_net_forward(int n, int nprob, const float* fields, const float* params, float omega, int conv_bf16,
+                         float* W, void* stream) {
+  if (n < 1 || n > 8191 || nprob < 1 || nprob > 65535 || !fields || !params || !W)
+    return fail(MG_ERR_INVALID_ARG, "mg_net_forward: bad arguments");
+  NetBatch B;
+  B.st = fields;
+  B.W = W;
+  B.stride = (size_t)9 * n * n;
+  B.n = n;
+  B.pad_ = 0;
+  CK(launch_net_forward_batch(B, nprob, params, omega, conv_bf16, (cudaStream_t)stream));
+  return MG_OK;
+}
+
+mg_status mg_profile_enable(mg_ctx* ctx, int enable) {
+  if (!ctx) return fail(MG_ERR_INVALID_ARG, "mg_profile_enable: ctx is NULL");
+  ctx->prof.reset();
+  ctx->prof.on = enable != 0;
+  return MG_OK;
+}
+
+mg_status mg_profile_read(mg_ctx* ctx, int kernel_class, double* total_ms, long long* launches) {
+  if (!ctx || kernel_class < -1 || kernel_class >= PK_NCLASS)
+    return fail(MG_ERR_INVALID_ARG, "mg_profile_read: bad arguments");
+  ctx->prof.collect();
+  if (kernel_class == -1) {
+    if (launches) *launches = ctx->prof.launches;
+    if (total_ms) *total_ms = 0.0;
+    return MG_OK;
+  }
+  if (total_ms) *total_ms = ctx->prof.ms[kernel_class];
+  if (launches) *launches = ctx->prof.count[kernel_class];
+  return MG_OK;
+}
+
+const char* mg_status_string(mg_status s) {
+  switch (s) {
+    case MG_OK: return "ok";
+    case MG_ERR_INVALID_ARG: return "invalid argument";
+    case MG_ERR_WORKSPACE: return "workspace too small or misaligned";
+    case MG_ERR_CUDA: return "CUDA error";
+    case MG_ERR_NOT_CONVERGED: return "not converged";
+    case MG_ERR_NUMERIC: return "numerical failure";
+    case MG_ERR_TIMEOUT: return "timeout";
+    case MG_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char* mg_last_error(void) { return g_err; }
+
+}  // extern "C"

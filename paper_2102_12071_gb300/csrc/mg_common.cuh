@@ -1,0 +1,92 @@
+// mg_common.cuh -- device-side data layout and helpers shared by the sm_103a kernels.
+//
+// Layout in HBM (all carved from the caller's workspace, 256-byte aligned):
+//   per problem p and level l: r_l, e_l            float[n_l*n_l]
+//   per-point stencil fields (FIELD problems)      float[9][n_l][n_l]
+//   per-point smoothing kernels (CNN, FIELD)       float[9][n_l][n_l]
+//   kernel class tables (CNN, constant stencils)   float[9][T][T], T = min(n_l, 11)
+//   coarsest FP64 Cholesky factor                  double[m][m], m = n_L^2
+//   ProbDev descriptors, ProbState control blocks, per-CTA norm partials.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define MG_MAXL 14
+#define MG_HRING 256          // ring of relative residuals per problem (>= cycles per chunk)
+#define MG_TAIL_N 63          // levels at or below this size run in one CTA per problem
+#define MG_NET_MARGIN 5       // points closer than this to an edge get their own kernel class
+#define MG_PROXY (2 * MG_NET_MARGIN + 1)  // proxy grid side for constant-stencil inference
+#define MG_NPARAMS 1260
+
+enum { SK_CONST = 0, SK_FIELD = 1 };                 // stencil storage
+enum { HK_JACOBI = 0, HK_TABLE = 1, HK_FIELD = 2 };  // smoother storage
+
+struct LevelDev {
+  int n;
+  int T;               // class-table side (HK_TABLE)
+  float* r;            // residual / right-hand side of the error equation on this level
+  float* e;            // correction on this level
+  float* st;           // SK_FIELD: stencil field [9][n][n]
+  float* W;            // HK_TABLE: [9][T][T]; HK_FIELD: [9][n][n]
+  float s[9];          // SK_CONST: stencil of this level (Galerkin product of the finer one)
+  float pad_[3];
+};
+
+struct ProbDev {
+  LevelDev lv[MG_MAXL];
+  double* chol;        // coarsest operator, dense lower Cholesky factor, m x m
+  int m;               // n_L^2
+  int pad_[3];
+};
+
+struct ProbState {
+  float bb_hi, bb_lo;  // ||b||^2 as a float-float pair
+  float rel;           // last relative residual
+  int active;          // 1 while this problem still iterates
+  int iter;            // number of residual evaluations done in this solve
+  int cycles;          // V-cycles whose correction has been applied
+  int status;          // 0 running, 1 converged, 2 hit max cycles, 3 non-finite residual
+  unsigned int counter;  // last-CTA detection for the norm reduction
+  float hist[MG_HRING];  // hist[k % MG_HRING] = relative residual after k cycles
+};
+
+// ---------------------------------------------------------------- float-float
+// Error-free transformations (Knuth's TwoSum; FMA-based TwoProduct, Dekker 1971).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  e = b - (s - a);
+}
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float bhi, float blo) {
+  float s, e;
+  two_sum(hi, bhi, s, e);
+  e += lo + blo;
+  fast_two_sum(s, e, hi, lo);
+}
+
+// --------------------------------------------------------------- class tables
+// Points at distance >= MG_NET_MARGIN from both edges of a constant-stencil grid see the
+// same network input in their whole receptive field, so they share one kernel; nearer
+// points get one class per distance.  T = min(n, MG_PROXY); for n <= MG_PROXY the map is
+// the identity.
+__device__ __forceinline__ int kclass(int i, int n, int T) {
+  if (i < MG_NET_MARGIN) return i;
+  const int d = n - 1 - i;
+  if (d < MG_NET_MARGIN) return T - 1 - d;
+  return MG_NET_MARGIN;
+}
+
+__device__ __forceinline__ bool in_grid(int i, int j, int n) {
+  return (unsigned)i < (unsigned)n && (unsigned)j < (unsigned)n;
+}
+
+// warp-level sum
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}

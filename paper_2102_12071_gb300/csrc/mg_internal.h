@@ -1,0 +1,121 @@
+// mg_internal.h -- launchers shared between the C-ABI layer and the kernel files.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include <vector>
+
+#include "mg_common.cuh"
+
+namespace mg {
+
+// Kernel classes timed by the optional event profiler.
+enum { PK_RESIDUAL = 0, PK_DOWN0 = 1, PK_UP0 = 2, PK_TAIL = 3, PK_DOWN = 4, PK_UP = 5, PK_NCLASS = 6 };
+
+// CUDA-event timing of individual launches on the launching stream; events are reused
+// after each collect() (called once the stream has been synchronised).
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> cls;
+  int used = 0;
+  double ms[PK_NCLASS] = {};
+  long long count[PK_NCLASS] = {};
+  long long launches = 0;  // every kernel launch, profiled or not
+
+  void begin(int c, cudaStream_t s) {
+    if (!on) return;
+    if ((int)cls.size() <= used) {
+      cudaEvent_t a, b;
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      ev.push_back(a);
+      ev.push_back(b);
+      cls.push_back(0);
+    }
+    cls[used] = c;
+    cudaEventRecord(ev[2 * used], s);
+  }
+  void end(cudaStream_t s) {
+    if (!on) return;
+    cudaEventRecord(ev[2 * used + 1], s);
+    ++used;
+  }
+  void collect() {
+    for (int i = 0; i < used; ++i) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]) == cudaSuccess) {
+        ms[cls[i]] += t;
+        count[cls[i]] += 1;
+      }
+    }
+    used = 0;
+  }
+  void reset() {
+    collect();
+    for (int c = 0; c < PK_NCLASS; ++c) { ms[c] = 0; count[c] = 0; }
+    launches = 0;
+  }
+  ~Profiler() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+};
+
+struct CycleArgs {
+  ProbDev* probs;
+  ProbState* state;
+  float* partials;
+  int ntiles_max;
+  int nprob, n0, L, lstar;
+  int nl[MG_MAXL];
+  int sk, hk;
+  float omega;
+  cudaStream_t stream;
+  Profiler* prof;
+};
+
+// one network evaluation: a stencil field (st) or a constant stencil (s) on an n x n grid
+struct NetJob {
+  const float* st;
+  const float* s;
+  float* W;
+  int n;
+  int pad_;
+};
+
+// a uniform batch of stencil fields [nfields][9][n][n] -> kernels [nfields][9][n][n]
+struct NetBatch {
+  const float* st;
+  float* W;
+  size_t stride;
+  int n;
+  int pad_;
+};
+
+int tiles_per_side(int n);
+size_t tail_smem_bytes(const int* nl, int l0, int L, int hk);
+
+cudaError_t launch_bnorm(const CycleArgs& a, const float* b);
+cudaError_t launch_residual(const CycleArgs& a, const float* b, const float* xhi, const float* xlo, float rtol,
+                            int max_cycles);
+cudaError_t launch_cycle(const CycleArgs& a, float* xhi, float* xlo);
+cudaError_t launch_tail_solve(const CycleArgs& a, const float* b, float* xhi, float* xlo, float rtol, int max_cycles,
+                              int budget, int final_residual);
+cudaError_t launch_smoother(const CycleArgs& a, int p, int l, const float* f, float* u, int nsteps);
+
+cudaError_t launch_varcoef5(int n, int nprob, const float* cells, size_t cells_stride, float* field,
+                            size_t field_stride, cudaStream_t s);
+cudaError_t launch_rap_field(ProbDev* probs, int nprob, int l, int nc, cudaStream_t s);
+cudaError_t launch_rap_const(ProbDev* probs, int nprob, int L, cudaStream_t s);
+cudaError_t launch_coarsest_factor(ProbDev* probs, int nprob, int L, int sk, int* fail, cudaStream_t s);
+cudaError_t launch_expand_stencil(const ProbDev* probs, int p, int l, int n, int sk, float* out, cudaStream_t s);
+cudaError_t launch_expand_kernels(const ProbDev* probs, int p, int l, int n, int sk, int hk, float omega, float* out,
+                                  cudaStream_t s);
+
+cudaError_t launch_net_forward(const NetJob* jobs_dev, int njobs, int nmax, const float* params, float omega, int bf16,
+                               cudaStream_t s);
+cudaError_t launch_net_forward_batch(const NetBatch& batch, int nfields, const float* params, float omega, int bf16,
+                                     cudaStream_t s);
+cudaError_t launch_copy_rel(const ProbState* state, float* rel, int nprob, cudaStream_t s);
+
+}  // namespace mg

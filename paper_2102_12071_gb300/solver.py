@@ -1,0 +1,106 @@
+"""User-facing wrapper: owns the torch-allocated workspace of one multigrid context.
+
+All computation runs in libmgcnn.so through ``binding``; torch supplies device memory
+and the stream.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+
+def rotated(n: int, eps: float, theta: float) -> dict:
+    return {"n": n, "kind": B.MG_PROBLEM_ROTATED, "eps": float(eps), "theta": float(theta)}
+
+
+def stencil(n: int, s) -> dict:
+    return {"n": n, "kind": B.MG_PROBLEM_STENCIL, "data": [float(v) for v in np.asarray(s).reshape(9)]}
+
+
+def varcoef5(n: int, cells: torch.Tensor) -> dict:
+    assert cells.is_cuda and cells.dtype == torch.float32 and cells.shape == (n + 1, n + 1)
+    return {"n": n, "kind": B.MG_PROBLEM_VARCOEF5, "data": cells.contiguous()}
+
+
+def field(n: int, st: torch.Tensor) -> dict:
+    assert st.is_cuda and st.dtype == torch.float32 and st.shape == (9, n, n)
+    return {"n": n, "kind": B.MG_PROBLEM_FIELD, "data": st.contiguous()}
+
+
+class MultigridSolver:
+    """Hierarchy + V-cycle solver for a batch of same-size problems on one GPU."""
+
+    def __init__(self, problems: list[dict], smoother: str = "jacobi", net_params: torch.Tensor | None = None,
+                 omega: float = 2.0 / 3.0, conv_bf16: bool = False, coarsest_n: int = 3, device="cuda",
+                 stream=None):
+        self.nprob = len(problems)
+        self.n = problems[0]["n"]
+        self.device = torch.device(device)
+        self.stream = stream
+        self._probs, self._keep = B.problems_array(problems)
+        kind = B.MG_SMOOTH_CNN if smoother == "cnn" else B.MG_SMOOTH_JACOBI
+        self.opts = B.options(kind, omega, coarsest_n, int(conv_bf16))
+        size = B.mg_workspace_size(self._probs, self.nprob, self.opts)
+        if size == 0:
+            raise B.MGError(B.MG_ERR_INVALID_ARG, "mg_workspace_size", B.lib().mg_last_error().decode())
+        self.workspace = torch.empty(size, dtype=torch.uint8, device=self.device)
+        if net_params is not None:
+            net_params = net_params.to(self.device, torch.float32).contiguous()
+        self.ctx = B.mg_setup(self._probs, self.nprob, self.opts, net_params, self.workspace, size, stream)
+        self.levels = B.mg_num_levels(self.ctx)
+        self.sizes = [B.mg_level_n(self.ctx, l) for l in range(self.levels)]
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            B.mg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        self.close()
+
+    # ------------------------------------------------------------ inspection
+    def stencil_field(self, prob: int, level: int) -> torch.Tensor:
+        n = self.sizes[level]
+        out = torch.empty((9, n, n), dtype=torch.float32, device=self.device)
+        B.mg_get_stencil(self.ctx, prob, level, out, self.stream)
+        return out
+
+    def kernels(self, prob: int, level: int) -> torch.Tensor:
+        n = self.sizes[level]
+        out = torch.empty((9, n, n), dtype=torch.float32, device=self.device)
+        B.mg_get_kernels(self.ctx, prob, level, out, self.stream)
+        return out
+
+    # ------------------------------------------------------------ solving
+    def smooth(self, prob: int, level: int, f: torch.Tensor, u: torch.Tensor, nsteps: int = 1) -> None:
+        B.mg_smoother_apply(self.ctx, prob, level, f, u, nsteps, self.stream)
+
+    def vcycle(self, b: torch.Tensor, x_hi: torch.Tensor, x_lo: torch.Tensor | None = None,
+               rel: torch.Tensor | None = None) -> None:
+        B.mg_vcycle(self.ctx, b, x_hi, x_lo, rel, self.stream)
+
+    def solve(self, b: torch.Tensor, x_hi: torch.Tensor | None = None, x_lo: torch.Tensor | None = None,
+              rtol: float = 1e-8, max_cycles: int = 1000, history: bool = True):
+        """Returns (x_hi, x_lo, hist [nprob, max_cycles+1] float64 (nan past the end), cycles, status)."""
+        shape = (self.nprob, self.n, self.n)
+        assert b.shape == shape and b.dtype == torch.float32 and b.is_contiguous()
+        if x_hi is None:
+            x_hi = torch.zeros(shape, dtype=torch.float32, device=self.device)
+        if x_lo is None:
+            x_lo = torch.zeros(shape, dtype=torch.float32, device=self.device)
+        hist = np.full((self.nprob, max_cycles + 1), np.nan) if history else None
+        cycles = np.zeros(self.nprob, dtype=np.int32)
+        st = B.mg_solve(self.ctx, b, x_hi, x_lo, rtol, max_cycles, hist, cycles, self.stream)
+        return x_hi, x_lo, hist, cycles, st
+
+
+def net_forward(fields: torch.Tensor, params: torch.Tensor, omega: float = 2.0 / 3.0,
+                conv_bf16: bool = False) -> torch.Tensor:
+    """Per-point smoothing kernels for a batch of stencil fields [nprob, 9, n, n]."""
+    nprob, nine, n, _ = fields.shape
+    assert nine == 9
+    W = torch.empty_like(fields)
+    B.mg_net_forward(n, nprob, fields.contiguous(), params.contiguous(), omega, int(conv_bf16), W)
+    return W

@@ -1,0 +1,176 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle.
+
+Tolerances: per-cycle relative residual within 1e-5 relative; asymptotic convergence
+factor within 1e-3; element-wise FP32 results within a few ulps of the stencil width.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2102_12071_gb300 import binding as B
+from paper_2102_12071_gb300 import inputs
+from paper_2102_12071_gb300 import solver as S
+
+pytestmark = pytest.mark.gpu
+
+HIST_RTOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2102_12071_gb300 import build
+
+    build.build()
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def oracle_rotated(n, eps, theta):
+    return O.const_field(n, f32(O.q1_rotated_stencil(eps, theta)))
+
+
+def _cmp_hist(gh, oh, tol=HIST_RTOL, upto=None):
+    k = min(len(oh), np.count_nonzero(~np.isnan(gh)))
+    if upto:
+        k = min(k, upto)
+    rel = np.abs(gh[:k] - oh[:k]) / oh[:k]
+    assert rel.max() <= tol, (rel.max(), int(rel.argmax()), gh[:k][rel.argmax()], oh[:k][rel.argmax()])
+    return k
+
+
+def test_hierarchy_stencils_match_oracle():
+    n = 255
+    eps, theta = 0.01, math.pi / 6
+    mg = S.MultigridSolver([S.rotated(n, eps, theta)])
+    om = O.Multigrid(oracle_rotated(n, eps, theta))
+    assert mg.sizes == [om.n(l) for l in range(om.levels)] == [255, 127, 63, 31, 15, 7, 3]
+    for l in range(mg.levels):
+        g = mg.stencil_field(0, l).cpu().double().numpy()
+        np.testing.assert_array_equal(g, f32(om.field(l)))  # Galerkin-invariant Q1: bit-exact
+        if l < mg.levels - 1:
+            np.testing.assert_allclose(mg.kernels(0, l).cpu().double().numpy(), O.jacobi_kernels(om.field(l)),
+                                       rtol=2e-7, atol=0)
+
+
+@pytest.mark.parametrize("n", [3, 7, 63])
+def test_c1_jacobi_solve_matches_oracle(n):
+    """63 x 63 (C1): eps = 0.01, theta = pi/6, V(1,1) Jacobi, 5 levels, rhs U[-1,1] seed 0."""
+    eps, theta = 0.01, math.pi / 6
+    b = inputs.rhs_uniform(0, n)
+    mg = S.MultigridSolver([S.rotated(n, eps, theta)])
+    x_hi, x_lo, gh, cyc, st = mg.solve(torch.from_numpy(b).cuda()[None].contiguous(), rtol=1e-8, max_cycles=500)
+    assert st == B.MG_OK
+    om = O.Multigrid(oracle_rotated(n, eps, theta))
+    xo, oh = om.solve(f32(b), rtol=1e-8, max_cycles=500)
+    assert abs(int(cyc[0]) - (len(oh) - 1)) <= 1
+    _cmp_hist(gh[0], oh)
+    assert gh[0][cyc[0]] < 1e-8
+    # the float-float iterate is the oracle's solution, and its true residual (FP64) is < 1e-8
+    x = x_hi[0].double().cpu().numpy() + x_lo[0].double().cpu().numpy()
+    st0 = oracle_rotated(n, eps, theta)
+    true_rel = np.linalg.norm(f32(b) - O.apply(st0, x)) / np.linalg.norm(f32(b))
+    assert true_rel < 1.0001e-8 and abs(true_rel - gh[0][cyc[0]]) <= 1e-3 * gh[0][cyc[0]] + 1e-12
+    if n == 63:
+        assert 195 <= cyc[0] <= 207
+        # asymptotic factor over the last 50 cycles
+        fg = (gh[0][cyc[0]] / gh[0][cyc[0] - 50]) ** (1 / 50)
+        fo = (oh[-1] / oh[-51]) ** (1 / 50)
+        assert abs(fg - fo) <= 1e-3 * fo
+
+
+@pytest.mark.parametrize("n,cycles", [(255, 60), (1023, 4)])
+def test_large_grid_jacobi_history_matches_oracle(n, cycles):
+    """Tiled kernels (k_residual/k_down/k_up) plus the one-CTA tail; 1023 is the bench size."""
+    eps, theta = 0.05, 1.1
+    b = inputs.rhs_uniform(1000, n)
+    mg = S.MultigridSolver([S.rotated(n, eps, theta)])
+    _, _, gh, cyc, st = mg.solve(torch.from_numpy(b).cuda()[None].contiguous(), rtol=0.0, max_cycles=cycles)
+    assert st == B.MG_ERR_NOT_CONVERGED and cyc[0] == cycles
+    om = O.Multigrid(oracle_rotated(n, eps, theta))
+    _, oh = om.solve(f32(b), rtol=0.0, max_cycles=cycles)
+    assert _cmp_hist(gh[0], oh) == cycles + 1
+
+
+def test_vcycle_elementwise_matches_oracle():
+    """One cycle from a random iterate: x_new element-wise vs the oracle (FP32 cycle on the
+    error equation, so the difference is bounded by FP32 rounding of the correction)."""
+    n = 127
+    rng = np.random.default_rng(5)
+    eps, theta = 0.2, 2.2
+    b = rng.uniform(-1, 1, (n, n)).astype(np.float32)
+    x = rng.uniform(-1, 1, (n, n)).astype(np.float32)
+    mg = S.MultigridSolver([S.rotated(n, eps, theta)])
+    xh = torch.from_numpy(x).cuda()[None].contiguous()
+    xl = torch.zeros_like(xh)
+    rel = torch.zeros(1, device="cuda")
+    mg.vcycle(torch.from_numpy(b).cuda()[None].contiguous(), xh, xl, rel)
+    got = (xh.double() + xl.double()).cpu().numpy()[0]
+    om = O.Multigrid(oracle_rotated(n, eps, theta))
+    want = om.vcycle(f32(b), f32(x))
+    corr = want - f32(x)
+    assert np.abs(got - want).max() <= 1e-5 * np.abs(corr).max()
+    st0 = oracle_rotated(n, eps, theta)
+    want_rel = np.linalg.norm(f32(b) - O.apply(st0, want)) / np.linalg.norm(f32(b))
+    assert abs(rel.item() - want_rel) <= 1e-5 * want_rel
+
+
+def test_smoother_apply_matches_oracle():
+    n = 63
+    rng = np.random.default_rng(6)
+    mg = S.MultigridSolver([S.rotated(n, 0.3, 0.4)])
+    om = O.Multigrid(oracle_rotated(n, 0.3, 0.4))
+    for level in (0, 1):
+        nl = mg.sizes[level]
+        f = rng.standard_normal((nl, nl)).astype(np.float32)
+        u = rng.standard_normal((nl, nl)).astype(np.float32)
+        ug = torch.from_numpy(u).cuda().contiguous()
+        mg.smooth(0, level, torch.from_numpy(f).cuda().contiguous(), ug, nsteps=3)
+        want = O.smooth(om.field(level), om.kernels(level), f32(f), f32(u), 3)
+        np.testing.assert_allclose(ug.double().cpu().numpy(), want, rtol=0, atol=2e-5 * np.abs(want).max())
+
+
+def test_batch_equals_single_problems():
+    """16 instances of the bench family (eps log-uniform, theta uniform) at 255^2: each
+    problem's history in the batch equals its own single-problem solve bit for bit."""
+    n = 255
+    params = inputs.rotated_params(inputs.SEED_PARAMS, 16)
+    b = torch.from_numpy(np.stack([inputs.rhs_uniform(inputs.SEED_RHS + i, n) for i in range(16)])).cuda()
+    mg = S.MultigridSolver([S.rotated(n, e, t) for e, t in params])
+    _, _, gh, cyc, _ = mg.solve(b.contiguous(), rtol=1e-8, max_cycles=40)
+    for i in (0, 7, 15):
+        one = S.MultigridSolver([S.rotated(n, *params[i])])
+        _, _, h1, c1, _ = one.solve(b[i:i + 1].contiguous(), rtol=1e-8, max_cycles=40)
+        assert c1[0] == cyc[i]
+        np.testing.assert_array_equal(h1[0][: c1[0] + 1], gh[i][: cyc[i] + 1])
+
+
+def test_solve_status_codes():
+    n = 63
+    mg = S.MultigridSolver([S.rotated(n, 0.01, 0.5)])
+    b = torch.from_numpy(inputs.rhs_uniform(3, n)).cuda()[None].contiguous()
+    _, _, h, c, st = mg.solve(b, rtol=1e-8, max_cycles=5)
+    assert st == B.MG_ERR_NOT_CONVERGED and c[0] == 5 and np.all(np.isnan(h[0][6:]))
+    bad = b.clone()
+    bad[0, 3, 3] = float("nan")
+    with pytest.raises(B.MGError) as ei:
+        mg.solve(bad, rtol=1e-8, max_cycles=5)
+    assert ei.value.status == B.MG_ERR_NUMERIC
+    # the context stays usable after an error
+    _, _, _, c, st = mg.solve(b, rtol=1e-8, max_cycles=400)
+    assert st == B.MG_OK and c[0] > 10
+
+
+def test_warm_start_continues_history():
+    """x_lo carries the float-float low part between calls: 10 + 10 cycles == 20 cycles."""
+    n = 255
+    mg = S.MultigridSolver([S.rotated(n, 0.1, 0.3)])
+    b = torch.from_numpy(inputs.rhs_uniform(4, n)).cuda()[None].contiguous()
+    _, _, h20, _, _ = mg.solve(b, rtol=0, max_cycles=20)
+    xh, xl, _, _, _ = mg.solve(b, rtol=0, max_cycles=10)
+    _, _, h10, _, _ = mg.solve(b, xh, xl, rtol=0, max_cycles=10)
+    np.testing.assert_allclose(h10[0][1:], h20[0][11:], rtol=1e-6)
