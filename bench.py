@@ -189,6 +189,25 @@ def cpu_baseline(n: int, budget_s: float = 12.0):
             "sample": f"{cycles} V(1,1) Jacobi cycles of one {n}^2 problem (FP64, single thread)"}
 
 
+def run_profile_case(args):
+    """Set up the benchmark batch and run a fixed number of cycles, nothing else."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2102_12071_gb300 import solver as S
+
+    params, b_host = make_batch(0, args.n, args.nprob)
+    problems = [S.rotated(args.n, e, t) for e, t in params]
+    w = load_weights()
+    kind = args.smoother if args.smoother != "auto" else ("cnn" if w is not None else "jacobi")
+    mg = S.MultigridSolver(problems, kind, net_params=w.cuda() if kind == "cnn" else None)
+    b = torch.from_numpy(b_host).cuda().contiguous()
+    mg.solve(b, rtol=0.0, max_cycles=args.profile_cycles, history=False)
+    torch.cuda.synchronize()
+
+
 # ------------------------------------------------------------------ our arm
 def main():
     ap = argparse.ArgumentParser()
@@ -201,9 +220,14 @@ def main():
     ap.add_argument("--ref-cycles", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--roofline-cycles", type=int, default=30)
+    ap.add_argument("--profile-cycles", type=int, default=0,
+                    help="only set up the batch and run this many V-cycles (for profiler captures)")
+    ap.add_argument("--smoother", default="auto", choices=["auto", "jacobi", "cnn"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_cycles:
+        return run_profile_case(args)
 
     import numpy as np
     import torch

@@ -117,5 +117,11 @@ cudaError_t launch_net_forward(const NetJob* jobs_dev, int njobs, int nmax, cons
 cudaError_t launch_net_forward_batch(const NetBatch& batch, int nfields, const float* params, float omega, int bf16,
                                      cudaStream_t s);
 cudaError_t launch_copy_rel(const ProbState* state, float* rel, int nprob, cudaStream_t s);
+int net_backward_ctas(int n, int nfields);
+cudaError_t launch_net_backward(const NetBatch& batch, int nfields, const float* dW, const float* params, int bf16,
+                                float* partials, float scale, float* grad, cudaStream_t s);
+
+// records the thread-local error text of the C ABI and returns `status`
+int api_fail(int status, const char* fmt, ...);
 
 }  // namespace mg

@@ -120,6 +120,149 @@ __global__ void __launch_bounds__(NET_THREADS) k_net_forward(const NetJob* __res
   }
 }
 
+// ------------------------------------------------------------------ backward
+// Gradient of sum_{k,p} dW[k][p] W[k][p] with respect to the parameters, for a uniform
+// batch of fields.  Each CTA recomputes the forward pass of its 16 x 16 output tile (with
+// halo) and back-propagates the paths that end in its own outputs; summed over tiles this
+// is the full gradient.  Rounding to bfloat16 is passed straight through.  Per-CTA
+// parameter gradients go to partials[cta][MG_NPARAMS] (deterministic reduction after).
+constexpr int BW_SMEM_FLOATS = 2 * MG_NPARAMS + 9 * S0 * S0 + 7 * S1 * S1 + 5 * S2 * S2 + 3 * S3 * S3 +
+                               9 * OT * OT + 3 * S3 * S3 + 5 * S2 * S2 + 7 * S1 * S1;
+
+// weight gradient of a conv layer: gw[o][c][ky][kx] = sum_{y,x in so x so} dz[o][y][x] in[c][y+ky][x+kx]
+template <int CIN, int COUT>
+__device__ __forceinline__ void conv_wgrad(const float* dz, int so, const float* in, int si, float* gw) {
+  for (int t = threadIdx.x; t < COUT * CIN * 9; t += NET_THREADS) {
+    const int o = t / (CIN * 9), c = (t / 9) % CIN, ky = (t % 9) / 3, kx = t % 3;
+    const float* d = dz + o * so * so;
+    const float* a = in + c * si * si + ky * si + kx;
+    float acc = 0.f;
+    for (int y = 0; y < so; ++y)
+      for (int x = 0; x < so; ++x) acc = fmaf(d[y * so + x], a[y * si + x], acc);
+    gw[t] = acc;
+  }
+}
+
+// input gradient of a conv layer: din[c][y'] = sum_{o,ky,kx} w[o][c][ky][kx] dz[o][y'-ky], then
+// times the activation derivative of the layer below (lrelu'(z) from the sign of its output)
+// and the domain mask.
+template <int CIN, int COUT>
+__device__ __forceinline__ void conv_igrad(const float* w, const float* dz, int so, const float* act, int si,
+                                           float* dact, int gy0, int gx0, int n) {
+  for (int t = threadIdx.x; t < CIN * si * si; t += NET_THREADS) {
+    const int c = t / (si * si), pos = t % (si * si);
+    const int y = pos / si, x = pos % si;
+    float acc = 0.f;
+    if (in_grid(gy0 + y, gx0 + x, n)) {
+#pragma unroll
+      for (int o = 0; o < COUT; ++o)
+#pragma unroll
+        for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+          for (int kx = 0; kx < 3; ++kx) {
+            const int yy = y - ky, xx = x - kx;
+            if (yy >= 0 && yy < so && xx >= 0 && xx < so)
+              acc = fmaf(w[((o * CIN + c) * 3 + ky) * 3 + kx], dz[o * so * so + yy * so + xx], acc);
+          }
+      acc *= act[t] > 0.f ? 1.f : 0.01f;
+    }
+    dact[t] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(NET_THREADS) k_net_backward(NetBatch batch, const float* __restrict__ dWall,
+                                                              const float* __restrict__ params, int bf16,
+                                                              float* __restrict__ partials) {
+  extern __shared__ float sm[];
+  float* w = sm;
+  float* gw = w + MG_NPARAMS;
+  float* a0 = gw + MG_NPARAMS;
+  float* a1 = a0 + 9 * S0 * S0;
+  float* a2 = a1 + 7 * S1 * S1;
+  float* a3 = a2 + 5 * S2 * S2;
+  float* dout = a3 + 3 * S3 * S3;
+  float* dz3 = dout + 9 * OT * OT;
+  float* dz2 = dz3 + 3 * S3 * S3;
+  float* dz1 = dz2 + 5 * S2 * S2;
+  NetJob J;
+  J.st = batch.st + blockIdx.y * batch.stride;
+  J.s = nullptr;
+  J.n = batch.n;
+  const float* dW = dWall + blockIdx.y * batch.stride;
+  const int n = J.n;
+  const int ntx = (n + OT - 1) / OT;
+  const int cta = blockIdx.y * gridDim.x + blockIdx.x;
+  float* out = partials + (size_t)cta * MG_NPARAMS;
+  if ((int)blockIdx.x >= ntx * ntx) {
+    for (int t = threadIdx.x; t < MG_NPARAMS; t += NET_THREADS) out[t] = 0.f;
+    return;
+  }
+  const int oy = (blockIdx.x / ntx) * OT, ox = (blockIdx.x % ntx) * OT;
+  for (int t = threadIdx.x; t < MG_NPARAMS; t += NET_THREADS) w[t] = rnd_bf16(params[t], bf16);
+  for (int t = threadIdx.x; t < S0 * S0; t += NET_THREADS) {
+    const int i = oy - 4 + t / S0, j = ox - 4 + t % S0;
+    if (in_grid(i, j, n)) {
+      const float d = job_tap(J, 4, i, j);
+#pragma unroll
+      for (int c = 0; c < 9; ++c) a0[c * S0 * S0 + t] = rnd_bf16(job_tap(J, c, i, j) / d, bf16);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 9; ++c) a0[c * S0 * S0 + t] = 0.f;
+    }
+  }
+  // dL/d(out) = dW / diag on the tile's outputs
+  const size_t nn = (size_t)n * n;
+  for (int t = threadIdx.x; t < 9 * OT * OT; t += NET_THREADS) {
+    const int o = t / (OT * OT), pos = t % (OT * OT);
+    const int i = oy + pos / OT, j = ox + pos % OT;
+    dout[t] = in_grid(i, j, n) ? dW[o * nn + (size_t)i * n + j] / job_tap(J, 4, i, j) : 0.f;
+  }
+  __syncthreads();
+  conv_layer<9, 7>(w + OFF_W1, a0, S0, a1, S1, oy - 3, ox - 3, n, bf16);
+  __syncthreads();
+  conv_layer<7, 5>(w + OFF_W2, a1, S1, a2, S2, oy - 2, ox - 2, n, bf16);
+  __syncthreads();
+  conv_layer<5, 3>(w + OFF_W3, a2, S2, a3, S3, oy - 1, ox - 1, n, bf16);
+  __syncthreads();
+  conv_wgrad<3, 9>(dout, OT, a3, S3, gw + OFF_WF);
+  conv_igrad<3, 9>(w + OFF_WF, dout, OT, a3, S3, dz3, oy - 1, ox - 1, n);
+  __syncthreads();
+  conv_wgrad<5, 3>(dz3, S3, a2, S2, gw + OFF_W3);
+  conv_igrad<5, 3>(w + OFF_W3, dz3, S3, a2, S2, dz2, oy - 2, ox - 2, n);
+  __syncthreads();
+  conv_wgrad<7, 5>(dz2, S2, a1, S1, gw + OFF_W2);
+  conv_igrad<7, 5>(w + OFF_W2, dz2, S2, a1, S1, dz1, oy - 3, ox - 3, n);
+  __syncthreads();
+  conv_wgrad<9, 7>(dz1, S1, a0, S0, gw + OFF_W1);
+  __syncthreads();
+  for (int t = threadIdx.x; t < MG_NPARAMS; t += NET_THREADS) out[t] = gw[t];
+}
+
+__global__ void k_reduce_params(const float* __restrict__ partials, int ncta, float scale, float* __restrict__ g) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= MG_NPARAMS) return;
+  float hi = 0.f, lo = 0.f;
+  for (int c = 0; c < ncta; ++c) ff_add(hi, lo, partials[(size_t)c * MG_NPARAMS + t], 0.f);
+  g[t] = scale * (hi + lo);
+}
+
+int net_backward_ctas(int n, int nfields) {
+  const int ntx = (n + OT - 1) / OT;
+  return ntx * ntx * nfields;
+}
+
+cudaError_t launch_net_backward(const NetBatch& batch, int nfields, const float* dW, const float* params, int bf16,
+                                float* partials, float scale, float* grad, cudaStream_t s) {
+  const int ntx = (batch.n + OT - 1) / OT;
+  dim3 grid(ntx * ntx, nfields);
+  const size_t smem = (size_t)BW_SMEM_FLOATS * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(k_net_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_net_backward<<<grid, NET_THREADS, smem, s>>>(batch, dW, params, bf16, partials);
+  k_reduce_params<<<(MG_NPARAMS + 127) / 128, 128, 0, s>>>(partials, ntx * ntx * nfields, scale, grad);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_net_forward(const NetJob* jobs_dev, int njobs, int nmax, const float* params, float omega, int bf16,
                                cudaStream_t s) {
   const int ntx = (nmax + OT - 1) / OT;

@@ -1,17 +1,580 @@
-// mg_train.cu -- training-loss kernels (placeholder until the adjoint kernels land).
+// mg_train.cu -- the convergence-theory training loss and its adjoint (Sec. 3.2).
+//
+// For problem b and random vector z_bj (Thm. sbound), with S = I - H A and the two-grid
+// coarse correction C = I - P (P^T A P)^{-1} P^T A (eq. twogrid, one pre- and one
+// post-smoothing step):
+//   e0 = z,  v0 = A e0,  e1 = e0 - H v0,  e2 = C e1,  v2 = A e2,  e3 = e2 - H v2,
+//   loss = (1/B) sum_b (1/Z) sum_j ||e3||^2 / n^2.
+// Adjoint: g3 = 2 e3 / (n^2 Z B); dW_p[k] -= g3(p) v2(p+d_k); g2 = g3 - A H^T g3;
+//          g1 = g2 - A P (P^T A P)^{-1} P^T g2; dW_p[k] -= g1(p) v0(p+d_k);
+// then dW -> d(params) through the network (mg_net.cu).
+//
+// All problems of a batch share n, so every kernel runs over (problem, vector, point) in
+// one launch; the data of a 64 x 32 batch at 63^2 (~16 MB per vector set) stays in L2.
+// The two-grid coarse operator is solved exactly in FP64 by a banded Cholesky factor
+// (bandwidth n_c + 1 <= 32): this is the coarsest-level direct solve of the two-grid
+// hierarchy, the one place FP64 is used.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
 #include "mg_internal.h"
 #include "mgcnn.h"
 
-struct mg_train_ctx {
-  int unused;
+namespace mg {
+
+constexpr int TT = 256;
+
+__device__ __forceinline__ float appA(const float* __restrict__ st, const float* __restrict__ v, int n, int i, int j) {
+  const size_t nn = (size_t)n * n;
+  const int q = i * n + j;
+  float acc = 0.f;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const int ii = i + k / 3 - 1, jj = j + k % 3 - 1;
+    if (in_grid(ii, jj, n)) acc = fmaf(st[k * nn + q], v[ii * n + jj], acc);
+  }
+  return acc;
+}
+
+// (H^T v)(y) = sum_k W_{y - d_k}[k] v(y - d_k)
+__device__ __forceinline__ float appHT(const float* __restrict__ W, const float* __restrict__ v, int n, int i, int j) {
+  const size_t nn = (size_t)n * n;
+  float acc = 0.f;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const int ii = i - (k / 3 - 1), jj = j - (k % 3 - 1);
+    if (in_grid(ii, jj, n)) acc = fmaf(W[k * nn + ii * n + jj], v[ii * n + jj], acc);
+  }
+  return acc;
+}
+
+struct TrainDims {
+  int n, nc, B, Z, w;  // w = band width of the coarse factor
+  size_t nn, nnc;
 };
 
+// vector index: blockIdx.y = b*Z + j; points: blockIdx.x * TT + threadIdx.x
+#define T_PROLOGUE                                           \
+  const int vec = blockIdx.y, b = vec / D.Z;                 \
+  const int q = blockIdx.x * TT + threadIdx.x;               \
+  if (q >= (int)D.nn) return;                                \
+  const int i = q / D.n, j = q % D.n;                        \
+  const size_t off = (size_t)vec * D.nn;                     \
+  const float* st = fields + (size_t)b * 9 * D.nn;           \
+  (void)i; (void)j; (void)st;
+
+// out = A in
+__global__ void k_t_applyA(TrainDims D, const float* __restrict__ fields, const float* __restrict__ in,
+                           float* __restrict__ out) {
+  T_PROLOGUE
+  out[off + q] = appA(st, in + off, D.n, i, j);
+}
+
+// out = x - H v
+__global__ void k_t_xmHv(TrainDims D, const float* __restrict__ fields, const float* __restrict__ Wall,
+                         const float* __restrict__ x, const float* __restrict__ v, float* __restrict__ out) {
+  T_PROLOGUE
+  const float* W = Wall + (size_t)b * 9 * D.nn;
+  const float* vv = v + off;
+  float acc = 0.f;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const int ii = i + k / 3 - 1, jj = j + k % 3 - 1;
+    if (in_grid(ii, jj, D.n)) acc = fmaf(W[k * D.nn + q], vv[ii * D.n + jj], acc);
+  }
+  out[off + q] = x[off + q] - acc;
+}
+
+// out = x - A v
+__global__ void k_t_xmAv(TrainDims D, const float* __restrict__ fields, const float* __restrict__ x,
+                         const float* __restrict__ v, float* __restrict__ out) {
+  T_PROLOGUE
+  out[off + q] = x[off + q] - appA(st, v + off, D.n, i, j);
+}
+
+// out = H^T v
+__global__ void k_t_HT(TrainDims D, const float* __restrict__ fields, const float* __restrict__ Wall,
+                       const float* __restrict__ v, float* __restrict__ out) {
+  T_PROLOGUE
+  out[off + q] = appHT(Wall + (size_t)b * 9 * D.nn, v + off, D.n, i, j);
+}
+
+// coarse rc = P^T (A v) if withA, else P^T v  (one thread per coarse point)
+__global__ void k_t_restrict(TrainDims D, const float* __restrict__ fields, const float* __restrict__ v, int withA,
+                             float* __restrict__ rc) {
+  const int vec = blockIdx.y, b = vec / D.Z;
+  const int Q = blockIdx.x * TT + threadIdx.x;
+  if (Q >= (int)D.nnc) return;
+  const int I = Q / D.nc, J = Q % D.nc;
+  const float* st = fields + (size_t)b * 9 * D.nn;
+  const float* vv = v + (size_t)vec * D.nn;
+  float acc = 0.f;
+  for (int di = -1; di <= 1; ++di)
+    for (int dj = -1; dj <= 1; ++dj) {
+      const int fi = 2 * I + 1 + di, fj = 2 * J + 1 + dj;
+      const float val = withA ? appA(st, vv, D.n, fi, fj) : vv[fi * D.n + fj];
+      acc = fmaf((di ? 0.5f : 1.f) * (dj ? 0.5f : 1.f), val, acc);
+    }
+  rc[(size_t)vec * D.nnc + Q] = acc;
+}
+
+// out = x - P xc  (P bilinear)
+__global__ void k_t_xmP(TrainDims D, const float* __restrict__ x, const float* __restrict__ xc,
+                        float* __restrict__ out) {
+  const int vec = blockIdx.y;
+  const int q = blockIdx.x * TT + threadIdx.x;
+  if (q >= (int)D.nn) return;
+  const int i = q / D.n, j = q % D.n;
+  const float* c = xc + (size_t)vec * D.nnc;
+  float v = 0.f;
+  for (int di = -1; di <= 1; ++di)
+    for (int dj = -1; dj <= 1; ++dj) {
+      const int fi = i + di, fj = j + dj;
+      if ((fi & 1) && (fj & 1)) {
+        const int I = (fi - 1) >> 1, J = (fj - 1) >> 1;
+        if (in_grid(I, J, D.nc)) v += (di ? 0.5f : 1.f) * (dj ? 0.5f : 1.f) * c[I * D.nc + J];
+      }
+    }
+  out[(size_t)vec * D.nn + q] = x[(size_t)vec * D.nn + q] - v;
+}
+
+// per-vector sum of squares (one CTA per vector) and g3 = scale * e3
+__global__ void k_t_loss(TrainDims D, const float* __restrict__ e3, float scale, float* __restrict__ g3,
+                         float* __restrict__ partial) {
+  const int vec = blockIdx.x;
+  const float* e = e3 + (size_t)vec * D.nn;
+  float* g = g3 + (size_t)vec * D.nn;
+  float acc = 0.f;
+  for (int q = threadIdx.x; q < (int)D.nn; q += TT) {
+    const float v = e[q];
+    acc = fmaf(v, v, acc);
+    g[q] = scale * v;
+  }
+  __shared__ float ws[TT / 32];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s = 0.f;
+    for (int k = 0; k < TT / 32; ++k) s += ws[k];
+    partial[vec] = s;
+  }
+}
+
+__global__ void k_t_loss_total(const float* __restrict__ partial, int nvecs, float scale, float* __restrict__ loss) {
+  float hi = 0.f, lo = 0.f;
+  for (int t = threadIdx.x; t < nvecs; t += 32) ff_add(hi, lo, partial[t], 0.f);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
+    ff_add(hi, lo, oh, ol);
+  }
+  if (threadIdx.x == 0) *loss = scale * (hi + lo);
+}
+
+// dW_p[k] = -sum_j ( g3_j(p) v2_j(p+d_k) + g1_j(p) v0_j(p+d_k) )   (one thread per (b, p))
+__global__ void k_t_dW(TrainDims D, const float* __restrict__ g3, const float* __restrict__ v2,
+                       const float* __restrict__ g1, const float* __restrict__ v0, float* __restrict__ dW) {
+  const int b = blockIdx.y;
+  const int q = blockIdx.x * TT + threadIdx.x;
+  if (q >= (int)D.nn) return;
+  const int i = q / D.n, j = q % D.n;
+  float acc[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) acc[k] = 0.f;
+  for (int z = 0; z < D.Z; ++z) {
+    const size_t off = ((size_t)b * D.Z + z) * D.nn;
+    const float a3 = g3[off + q], a1 = g1[off + q];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const int ii = i + k / 3 - 1, jj = j + k % 3 - 1;
+      if (in_grid(ii, jj, D.n)) {
+        const int r = ii * D.n + jj;
+        acc[k] = fmaf(a3, v2[off + r], acc[k]);
+        acc[k] = fmaf(a1, v0[off + r], acc[k]);
+      }
+    }
+  }
+  float* out = dW + (size_t)b * 9 * D.nn;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) out[k * D.nn + q] = -acc[k];
+}
+
+// ---------------------------------------------------------------- coarse solve
+// Banded Cholesky of the Galerkin coarse operator, right-looking, one CTA per problem.
+// band[(r)*(w+1) + d] holds L(r, r-d), d = 0..w.  A(r, r-d) comes from the coarse field.
+__global__ void k_t_band_factor(TrainDims D, const float* __restrict__ cfields, double* __restrict__ band,
+                                int* __restrict__ fail) {
+  const int b = blockIdx.x;
+  const int nc = D.nc, m = nc * nc, w = D.w, ld = w + 1;
+  const float* cst = cfields + (size_t)b * 9 * D.nnc;
+  double* L = band + (size_t)b * m * ld;
+  // fill the lower band of A: row r = (I, J), column c = r - d
+  for (int t = threadIdx.x; t < m * ld; t += blockDim.x) {
+    const int r = t / ld, d = t % ld;
+    const int c = r - d;
+    double v = 0.0;
+    if (c >= 0) {
+      const int I = r / nc, J = r % nc, I2 = c / nc, J2 = c % nc;
+      const int di = I2 - I, dj = J2 - J;
+      if (di >= -1 && di <= 1 && dj >= -1 && dj <= 1) v = (double)cst[(3 * (di + 1) + dj + 1) * D.nnc + r];
+    }
+    L[t] = v;
+  }
+  __syncthreads();
+  __shared__ double piv;
+  for (int k = 0; k < m; ++k) {
+    if (threadIdx.x == 0) {
+      const double d = L[(size_t)k * ld];
+      if (!(d > 0.0)) atomicExch(fail, 1);
+      piv = d > 0.0 ? sqrt(d) : 1.0;
+      L[(size_t)k * ld] = piv;
+    }
+    __syncthreads();
+    // column k below the diagonal: rows k+1 .. k+w
+    for (int t = threadIdx.x; t < w; t += blockDim.x) {
+      const int r = k + 1 + t;
+      if (r < m) L[(size_t)r * ld + (r - k)] /= piv;
+    }
+    __syncthreads();
+    // trailing update: A(r, c) -= L(r, k) L(c, k) for k < c <= r <= k+w
+    for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
+      const int r = k + 1 + t / w, c = k + 1 + t % w;
+      if (c <= r && r < m) L[(size_t)r * ld + (r - c)] -= L[(size_t)r * ld + (r - k)] * L[(size_t)c * ld + (c - k)];
+    }
+    __syncthreads();
+  }
+}
+
+// After factorisation: the diagonal slot holds 1/L(i,i) and ut[(i)*(w+1) + d] = L(i+d, i)
+// (the band transposed, so the backward sweep reads rows contiguously).
+__global__ void k_t_band_finish(TrainDims D, double* __restrict__ band, double* __restrict__ ut) {
+  const int b = blockIdx.y;
+  const int m = D.nc * D.nc, ld = D.w + 1;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m * ld) return;
+  const int i = t / ld, d = t % ld;
+  double* L = band + (size_t)b * m * ld;
+  double* U = ut + (size_t)b * m * ld;
+  U[t] = (d > 0 && i + d < m) ? L[(size_t)(i + d) * ld + d] : (d == 0 ? 1.0 / L[(size_t)i * ld] : 0.0);
+}
+
+__global__ void k_t_band_invdiag(TrainDims D, double* __restrict__ band) {
+  const int b = blockIdx.y;
+  const int m = D.nc * D.nc, ld = D.w + 1;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  double* L = band + (size_t)b * m * ld;
+  L[(size_t)i * ld] = 1.0 / L[(size_t)i * ld];
+}
+
+// x = A_c^{-1} rhs, one warp per right-hand side: forward substitution with L, then
+// backward substitution with L^T, FP64 throughout; lane t keeps the (t+1)-th most recent
+// unknown so each step is one warp-wide dot product of length w <= 32.
+__global__ void k_t_band_solve(TrainDims D, const double* __restrict__ band, const double* __restrict__ ut,
+                               const float* __restrict__ rhs, double* __restrict__ ybuf, float* __restrict__ x,
+                               int nvecs) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= nvecs) return;
+  const int b = warp / D.Z;
+  const int m = D.nc * D.nc, w = D.w, ld = w + 1;
+  const double* L = band + (size_t)b * m * ld;
+  const double* U = ut + (size_t)b * m * ld;
+  const float* r = rhs + (size_t)warp * D.nnc;
+  double* y = ybuf + (size_t)warp * m;
+  float* out = x + (size_t)warp * D.nnc;
+  const int d = lane + 1;
+  double hist = 0.0;
+  double lnext = (d <= w) ? L[d] : 0.0;
+  for (int i = 0; i < m; ++i) {
+    const double lcur = lnext;
+    if (i + 1 < m) lnext = (d <= w) ? L[(size_t)(i + 1) * ld + d] : 0.0;
+    double p = (d <= w && i - d >= 0) ? lcur * hist : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+    const double yi = ((double)r[i] - p) * L[(size_t)i * ld];
+    const double prev = __shfl_up_sync(0xffffffffu, hist, 1);
+    hist = lane == 0 ? yi : prev;
+    if (lane == 0) y[i] = yi;
+  }
+  __syncwarp();
+  hist = 0.0;
+  double unext = (d <= w) ? U[(size_t)(m - 1) * ld + d] : 0.0;
+  for (int i = m - 1; i >= 0; --i) {
+    const double ucur = unext;
+    if (i > 0) unext = (d <= w) ? U[(size_t)(i - 1) * ld + d] : 0.0;
+    double p = (d <= w && i + d < m) ? ucur * hist : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+    const double xi = (y[i] - p) * U[(size_t)i * ld];
+    const double prev = __shfl_up_sync(0xffffffffu, hist, 1);
+    hist = lane == 0 ? xi : prev;
+    if (lane == 0) out[i] = (float)xi;
+  }
+}
+
+// constant stencils expanded to truncated fields
+__global__ void k_t_const_field(TrainDims D, const float* __restrict__ s9, float* __restrict__ fields) {
+  const int b = blockIdx.y;
+  const int q = blockIdx.x * TT + threadIdx.x;
+  if (q >= (int)D.nn) return;
+  const int i = q / D.n, j = q % D.n;
+  const float* s = s9 + 9 * b;
+  float* st = fields + (size_t)b * 9 * D.nn;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) st[k * D.nn + q] = in_grid(i + k / 3 - 1, j + k % 3 - 1, D.n) ? s[k] : 0.f;
+}
+
+}  // namespace mg
+
+namespace mg {
+// out = P xc
+__global__ void k_t_P(TrainDims D, const float* __restrict__ xc, float* __restrict__ out) {
+  const int vec = blockIdx.y;
+  const int q = blockIdx.x * TT + threadIdx.x;
+  if (q >= (int)D.nn) return;
+  const int i = q / D.n, j = q % D.n;
+  const float* c = xc + (size_t)vec * D.nnc;
+  float v = 0.f;
+  for (int di = -1; di <= 1; ++di)
+    for (int dj = -1; dj <= 1; ++dj) {
+      const int fi = i + di, fj = j + dj;
+      if ((fi & 1) && (fj & 1)) {
+        const int I = (fi - 1) >> 1, J = (fj - 1) >> 1;
+        if (in_grid(I, J, D.nc)) v += (di ? 0.5f : 1.f) * (dj ? 0.5f : 1.f) * c[I * D.nc + J];
+      }
+    }
+  out[(size_t)vec * D.nn + q] = v;
+}
+}  // namespace mg
+
+using namespace mg;
+
+struct mg_train_ctx {
+  TrainDims D;
+  int bf16 = 0;
+  float omega = 2.f / 3.f;
+  float* s9 = nullptr;
+  float* fields = nullptr;
+  float* cfields = nullptr;
+  float* W = nullptr;
+  float* dW = nullptr;
+  ProbDev* probs = nullptr;
+  double* band = nullptr;
+  double* ut = nullptr;
+  double* ybuf = nullptr;
+  float *v0 = nullptr, *e1 = nullptr, *e2 = nullptr, *v2 = nullptr, *g3 = nullptr, *t = nullptr, *g2 = nullptr,
+        *g1 = nullptr, *rc = nullptr, *xc = nullptr;
+  float* loss_partial = nullptr;
+  float* param_partial = nullptr;
+  int* fail = nullptr;
+  int ncta_bw = 0;
+  std::vector<float> h_s9;
+  std::vector<ProbDev> h_probs;
+};
+
+namespace {
+
+mg_status train_dims(const mg_problem* probs, int nprob, int nvec, const mg_options* o, TrainDims& D, int& is_const) {
+  if (!probs || nprob < 1 || nvec < 1 || !o) return (mg_status)api_fail(MG_ERR_INVALID_ARG, "training: bad arguments");
+  if ((long long)nprob * nvec > 65535) return (mg_status)api_fail(MG_ERR_INVALID_ARG, "nprob * nvec must be <= 65535");
+  if (!(o->omega > 0.f) || !(o->omega < 2.f)) return (mg_status)api_fail(MG_ERR_INVALID_ARG, "omega must be in (0, 2)");
+  const int n = probs[0].n;
+  if (n != 7 && n != 15 && n != 31 && n != 63)
+    return (mg_status)api_fail(MG_ERR_UNSUPPORTED, "training grids must be 7, 15, 31 or 63 (got %d)", n);
+  int nconst = 0;
+  for (int p = 0; p < nprob; ++p) {
+    if (probs[p].n != n) return (mg_status)api_fail(MG_ERR_UNSUPPORTED, "all training problems must share n");
+    const int k = probs[p].kind;
+    if (k == MG_PROBLEM_ROTATED) {
+      if (!(probs[p].eps > 0.0)) return (mg_status)api_fail(MG_ERR_INVALID_ARG, "problem %d: eps must be > 0", p);
+      ++nconst;
+    } else if (k == MG_PROBLEM_STENCIL) {
+      if (!probs[p].data) return (mg_status)api_fail(MG_ERR_INVALID_ARG, "problem %d: NULL stencil", p);
+      ++nconst;
+    } else if (k == MG_PROBLEM_VARCOEF5 || k == MG_PROBLEM_FIELD) {
+      if (!probs[p].data) return (mg_status)api_fail(MG_ERR_INVALID_ARG, "problem %d: NULL data", p);
+    } else {
+      return (mg_status)api_fail(MG_ERR_INVALID_ARG, "problem %d: unknown kind", p);
+    }
+  }
+  if (nconst != 0 && nconst != nprob)
+    return (mg_status)api_fail(MG_ERR_UNSUPPORTED, "a training batch mixes constant and per-point problems");
+  is_const = nconst > 0;
+  D.n = n;
+  D.nc = (n - 1) / 2;
+  D.B = nprob;
+  D.Z = nvec;
+  D.w = D.nc + 1;
+  D.nn = (size_t)n * n;
+  D.nnc = (size_t)D.nc * D.nc;
+  return MG_OK;
+}
+
+template <class T>
+T* take(char* base, size_t& off, size_t count) {
+  off = (off + 255) & ~(size_t)255;
+  T* p = base ? (T*)(base + off) : nullptr;
+  off += count * sizeof(T);
+  return p;
+}
+
+size_t train_carve(const TrainDims& D, void* basev, mg_train_ctx* c) {
+  char* base = (char*)basev;
+  size_t off = 0;
+  const size_t BZ = (size_t)D.B * D.Z, m = D.nnc, ld = D.w + 1;
+  mg_train_ctx tmp;
+  mg_train_ctx& x = c ? *c : tmp;
+  x.s9 = take<float>(base, off, 9 * (size_t)D.B);
+  x.fields = take<float>(base, off, 9 * D.nn * D.B);
+  x.cfields = take<float>(base, off, 9 * D.nnc * D.B);
+  x.W = take<float>(base, off, 9 * D.nn * D.B);
+  x.dW = take<float>(base, off, 9 * D.nn * D.B);
+  x.probs = take<ProbDev>(base, off, D.B);
+  x.band = take<double>(base, off, m * ld * D.B);
+  x.ut = take<double>(base, off, m * ld * D.B);
+  x.ybuf = take<double>(base, off, m * BZ);
+  float** vecs[] = {&x.v0, &x.e1, &x.e2, &x.v2, &x.g3, &x.t, &x.g2, &x.g1};
+  for (float** v : vecs) *v = take<float>(base, off, D.nn * BZ);
+  x.rc = take<float>(base, off, D.nnc * BZ);
+  x.xc = take<float>(base, off, D.nnc * BZ);
+  x.loss_partial = take<float>(base, off, BZ);
+  x.ncta_bw = net_backward_ctas(D.n, D.B);
+  x.param_partial = take<float>(base, off, (size_t)x.ncta_bw * MG_NPARAMS);
+  x.fail = take<int>(base, off, 4);
+  return off + 256;
+}
+
+}  // namespace
+
+#define TCK(call)                                                                                       \
+  do {                                                                                                  \
+    cudaError_t e_ = (call);                                                                            \
+    if (e_ != cudaSuccess) return (mg_status)api_fail(MG_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
 extern "C" {
-size_t mg_train_workspace_size(const mg_problem*, int, int, const mg_options*) { return 0; }
-mg_status mg_train_setup(const mg_problem*, int, int, const mg_options*, void*, size_t, void*, mg_train_ctx** out) {
-  if (out) *out = nullptr;
-  return MG_ERR_UNSUPPORTED;
+
+size_t mg_train_workspace_size(const mg_problem* problems, int nprob, int nvec, const mg_options* opts) {
+  TrainDims D;
+  int is_const = 0;
+  if (train_dims(problems, nprob, nvec, opts, D, is_const) != MG_OK) return 0;
+  return train_carve(D, nullptr, nullptr);
 }
+
+mg_status mg_train_setup(const mg_problem* problems, int nprob, int nvec, const mg_options* opts, void* workspace,
+                         size_t ws_bytes, void* stream, mg_train_ctx** out) {
+  if (!out) return (mg_status)api_fail(MG_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  TrainDims D;
+  int is_const = 0;
+  mg_status st = train_dims(problems, nprob, nvec, opts, D, is_const);
+  if (st != MG_OK) return st;
+  const size_t need = train_carve(D, nullptr, nullptr);
+  if (!workspace || ws_bytes < need)
+    return (mg_status)api_fail(MG_ERR_WORKSPACE, "training workspace needs %zu bytes, got %zu", need, ws_bytes);
+  if (((uintptr_t)workspace & 255) != 0) return (mg_status)api_fail(MG_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  mg_train_ctx* c = new mg_train_ctx();
+  c->D = D;
+  c->bf16 = opts->conv_bf16;
+  c->omega = opts->omega;
+  train_carve(D, workspace, c);
+  auto run = [&]() -> mg_status {
+    const dim3 gp((unsigned)((D.nn + TT - 1) / TT), D.B);
+    if (is_const) {
+      c->h_s9.resize(9 * (size_t)D.B);
+      for (int p = 0; p < D.B; ++p) {
+        float* s9 = &c->h_s9[9 * (size_t)p];
+        if (problems[p].kind == MG_PROBLEM_ROTATED) {
+          if (mg_rotated_stencil(problems[p].eps, problems[p].theta, s9) != MG_OK) return MG_ERR_INVALID_ARG;
+        } else {
+          for (int k = 0; k < 9; ++k) s9[k] = problems[p].data[k];
+        }
+      }
+      TCK(cudaMemcpyAsync(c->s9, c->h_s9.data(), sizeof(float) * 9 * D.B, cudaMemcpyHostToDevice, s));
+      k_t_const_field<<<gp, TT, 0, s>>>(D, c->s9, c->fields);
+    } else {
+      for (int p = 0; p < D.B; ++p) {
+        float* f = c->fields + (size_t)p * 9 * D.nn;
+        if (problems[p].kind == MG_PROBLEM_VARCOEF5) TCK(launch_varcoef5(D.n, 1, problems[p].data, 0, f, 0, s));
+        else TCK(cudaMemcpyAsync(f, problems[p].data, sizeof(float) * 9 * D.nn, cudaMemcpyDeviceToDevice, s));
+      }
+    }
+    // two-level descriptors to reuse the Galerkin kernel
+    c->h_probs.assign(D.B, ProbDev());
+    for (int p = 0; p < D.B; ++p) {
+      ProbDev& d = c->h_probs[p];
+      memset(&d, 0, sizeof(d));
+      d.lv[0].n = D.n;
+      d.lv[0].st = c->fields + (size_t)p * 9 * D.nn;
+      d.lv[1].n = D.nc;
+      d.lv[1].st = c->cfields + (size_t)p * 9 * D.nnc;
+    }
+    TCK(cudaMemcpyAsync(c->probs, c->h_probs.data(), sizeof(ProbDev) * D.B, cudaMemcpyHostToDevice, s));
+    TCK(launch_rap_field(c->probs, D.B, 0, D.nc, s));
+    TCK(cudaMemsetAsync(c->fail, 0, sizeof(int), s));
+    k_t_band_factor<<<D.B, 256, 0, s>>>(D, c->cfields, c->band, c->fail);
+    const int m = D.nc * D.nc, ld = D.w + 1;
+    k_t_band_finish<<<dim3((m * ld + 255) / 256, D.B), 256, 0, s>>>(D, c->band, c->ut);
+    k_t_band_invdiag<<<dim3((m + 255) / 256, D.B), 256, 0, s>>>(D, c->band);
+    TCK(cudaGetLastError());
+    return MG_OK;
+  };
+  st = run();
+  if (st != MG_OK) {
+    delete c;
+    return st;
+  }
+  *out = c;
+  return MG_OK;
+}
+
 void mg_train_destroy(mg_train_ctx* ctx) { delete ctx; }
-mg_status mg_train_step(mg_train_ctx*, const float*, const float*, float*, float*, void*) { return MG_ERR_UNSUPPORTED; }
+
+mg_status mg_train_step(mg_train_ctx* c, const float* params, const float* z, float* grad_out, float* loss_out,
+                        void* stream) {
+  if (!c || !params || !z || !loss_out) return (mg_status)api_fail(MG_ERR_INVALID_ARG, "mg_train_step: bad arguments");
+  const TrainDims& D = c->D;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int BZ = D.B * D.Z;
+  const dim3 gv((unsigned)((D.nn + TT - 1) / TT), BZ), gc((unsigned)((D.nnc + TT - 1) / TT), BZ);
+  const int solve_blocks = (BZ * 32 + 127) / 128;
+  const float inv = 1.f / ((float)D.nn * D.Z * D.B);
+  NetBatch nb;
+  nb.st = c->fields;
+  nb.W = c->W;
+  nb.stride = 9 * D.nn;
+  nb.n = D.n;
+  nb.pad_ = 0;
+  TCK(launch_net_forward_batch(nb, D.B, params, c->omega, c->bf16, s));
+  // forward: e1 = S z, e2 = C e1, e3 = S e2
+  k_t_applyA<<<gv, TT, 0, s>>>(D, c->fields, z, c->v0);
+  k_t_xmHv<<<gv, TT, 0, s>>>(D, c->fields, c->W, z, c->v0, c->e1);
+  k_t_restrict<<<gc, TT, 0, s>>>(D, c->fields, c->e1, 1, c->rc);
+  k_t_band_solve<<<solve_blocks, 128, 0, s>>>(D, c->band, c->ut, c->rc, c->ybuf, c->xc, BZ);
+  k_t_xmP<<<gv, TT, 0, s>>>(D, c->e1, c->xc, c->e2);
+  k_t_applyA<<<gv, TT, 0, s>>>(D, c->fields, c->e2, c->v2);
+  k_t_xmHv<<<gv, TT, 0, s>>>(D, c->fields, c->W, c->e2, c->v2, c->g3);
+  k_t_loss<<<BZ, TT, 0, s>>>(D, c->g3, 2.f * inv, c->g3, c->loss_partial);
+  k_t_loss_total<<<1, 32, 0, s>>>(c->loss_partial, BZ, inv, loss_out);
+  TCK(cudaGetLastError());
+  if (!grad_out) return MG_OK;
+  // adjoint
+  k_t_HT<<<gv, TT, 0, s>>>(D, c->fields, c->W, c->g3, c->t);
+  k_t_xmAv<<<gv, TT, 0, s>>>(D, c->fields, c->g3, c->t, c->g2);
+  k_t_restrict<<<gc, TT, 0, s>>>(D, c->fields, c->g2, 0, c->rc);
+  k_t_band_solve<<<solve_blocks, 128, 0, s>>>(D, c->band, c->ut, c->rc, c->ybuf, c->xc, BZ);
+  k_t_P<<<gv, TT, 0, s>>>(D, c->xc, c->t);
+  k_t_xmAv<<<gv, TT, 0, s>>>(D, c->fields, c->g2, c->t, c->g1);
+  k_t_dW<<<dim3((unsigned)((D.nn + TT - 1) / TT), D.B), TT, 0, s>>>(D, c->g3, c->v2, c->g1, c->v0, c->dW);
+  TCK(cudaGetLastError());
+  TCK(launch_net_backward(nb, D.B, c->dW, params, c->bf16, c->param_partial, 1.f, grad_out, s));
+  return MG_OK;
 }
+
+}  // extern "C"

@@ -1,0 +1,163 @@
+"""Training of the stencil-to-smoother network on the two-grid convergence loss.
+
+Sec. 3.2 trains the smoother by minimising the error left by the multigrid cycle on
+random initial errors (eq. overalltrain with u_* = 0); Thm. sbound makes the mean of
+||E z||^2 over Gaussian z an estimate of ||E||_F^2.  Here E = S C S is the two-grid error
+propagation (eq. twogrid, one pre- and one post-smoothing step), evaluated together with
+its exact gradient by mg_train_step in the CUDA library.  This module only draws the
+problems and vectors, calls the library and applies Adam (Sec. 6: Adam, learning rate
+1e-3) to the ~1.3 k network parameters.
+"""
+from __future__ import annotations
+
+import math
+import os
+
+import numpy as np
+import torch
+
+from . import binding as B
+from . import inputs
+
+NPARAMS = 1260
+LAYERS = [(7, 9), (5, 7), (3, 5), (9, 3)]  # (out, in) channels of the 3x3 layers
+
+
+def init_params(seed: int = 0) -> torch.Tensor:
+    """Convolutions: uniform with the LeakyReLU Kaiming bound; the output layer is zero, so
+    the network starts exactly at weighted Jacobi (W = omega/D) with live gradients."""
+    g = torch.Generator().manual_seed(seed)
+    parts = []
+    for k, (co, ci) in enumerate(LAYERS):
+        if k == len(LAYERS) - 1:
+            parts.append(torch.zeros(co * ci * 9))
+        else:
+            bound = math.sqrt(6.0 / ((1 + 0.01 ** 2) * ci * 9))
+            parts.append((torch.rand(co * ci * 9, generator=g) * 2 - 1) * bound)
+    p = torch.cat(parts)
+    assert p.numel() == NPARAMS
+    return p
+
+
+class TwoGridBatch:
+    """Device workspace + context for one training batch of same-size problems."""
+
+    def __init__(self, problems: list[dict], nvec: int, omega: float = 2.0 / 3.0, conv_bf16: bool = False,
+                 workspace: torch.Tensor | None = None):
+        self.n = problems[0]["n"]
+        self.nprob = len(problems)
+        self.nvec = nvec
+        self._probs, self._keep = B.problems_array(problems)
+        self.opts = B.options(B.MG_SMOOTH_CNN, omega, 3, int(conv_bf16))
+        size = B.mg_train_workspace_size(self._probs, self.nprob, nvec, self.opts)
+        if size == 0:
+            raise B.MGError(B.MG_ERR_INVALID_ARG, "mg_train_workspace_size", B.lib().mg_last_error().decode())
+        if workspace is None or workspace.numel() < size:
+            workspace = torch.empty(size, dtype=torch.uint8, device="cuda")
+        self.workspace = workspace
+        self.ctx = B.mg_train_setup(self._probs, self.nprob, nvec, self.opts, workspace, size)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            B.mg_train_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        self.close()
+
+    def loss_and_grad(self, params: torch.Tensor, z: torch.Tensor, want_grad: bool = True):
+        assert z.shape == (self.nprob, self.nvec, self.n, self.n) and z.is_contiguous()
+        loss = torch.empty(1, device="cuda")
+        grad = torch.empty(NPARAMS, device="cuda") if want_grad else None
+        B.mg_train_step(self.ctx, params.contiguous(), z, grad, loss)
+        return loss, grad
+
+
+class TwoGridLoss(torch.autograd.Function):
+    """loss = mean_b mean_j ||S C S z_bj||^2 / n^2 as a differentiable function of the
+    network parameters; the backward pass is the library's hand-written adjoint."""
+
+    @staticmethod
+    def forward(ctx, params, z, batch):
+        loss, grad = batch.loss_and_grad(params.detach(), z, want_grad=params.requires_grad)
+        ctx.save_for_backward(grad if grad is not None else torch.zeros(0, device=params.device))
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, gout):
+        (grad,) = ctx.saved_tensors
+        return gout * grad, None, None
+
+
+class Trainer:
+    """Adam on the two-grid loss over freshly drawn rotated anisotropic problems."""
+
+    def __init__(self, sizes=(31, 63), per_size: int = 32, nvec: int = 32, omega: float = 2.0 / 3.0,
+                 conv_bf16: bool = True, lr: float = 1e-3, seed: int = 0, eps_range=(1e-3, 1.0)):
+        self.sizes = sizes
+        self.per_size = per_size
+        self.nvec = nvec
+        self.omega = omega
+        self.conv_bf16 = conv_bf16
+        self.eps_range = eps_range
+        self.params = init_params(seed).cuda().requires_grad_(True)
+        self.opt = torch.optim.Adam([self.params], lr=lr)
+        self.gen = torch.Generator(device="cuda").manual_seed(inputs.SEED_TRAIN + seed)
+        self._ws = {}
+        self.step_count = 0
+
+    def problems(self, step: int, n: int) -> list[dict]:
+        params = inputs.rotated_params(inputs.SEED_TRAIN + 7919 * step + n, self.per_size, *self.eps_range)
+        return [{"n": n, "kind": B.MG_PROBLEM_ROTATED, "eps": e, "theta": t} for e, t in params]
+
+    def loss(self, step: int) -> torch.Tensor:
+        total = 0.0
+        for n in self.sizes:
+            probs = self.problems(step, n)
+            ws = self._ws.get(n)
+            batch = TwoGridBatch(probs, self.nvec, self.omega, self.conv_bf16, ws)
+            self._ws[n] = batch.workspace
+            z = torch.randn((self.per_size, self.nvec, n, n), generator=self.gen, device="cuda")
+            total = total + TwoGridLoss.apply(self.params, z, batch)
+        return total / len(self.sizes)
+
+    def step(self) -> float:
+        self.opt.zero_grad(set_to_none=True)
+        loss = self.loss(self.step_count)
+        loss.backward()
+        self.opt.step()
+        self.step_count += 1
+        return float(loss.detach())
+
+    def save(self, path: str) -> None:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        np.save(path, self.params.detach().cpu().numpy().astype(np.float32))
+
+
+def main():
+    import argparse
+    import time
+
+    ap = argparse.ArgumentParser(description="train the stencil-to-smoother network on the GPU")
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights",
+                                                   "cnn_rotated.npy"))
+    ap.add_argument("--fp32-conv", action="store_true")
+    args = ap.parse_args()
+    from . import build
+
+    build.build()
+    tr = Trainer(lr=args.lr, seed=args.seed, conv_bf16=not args.fp32_conv)
+    t0 = time.time()
+    for s in range(args.steps):
+        l = tr.step()
+        if s % 50 == 0 or s == args.steps - 1:
+            print(f"step {s:5d} loss {l:.6f} ({time.time() - t0:.1f} s)", flush=True)
+    tr.save(args.out)
+    print("saved", args.out)
+
+
+if __name__ == "__main__":
+    main()

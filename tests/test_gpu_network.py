@@ -1,0 +1,184 @@
+"""GPU parity of the learned part: network inference, the CNN-smoothed V-cycle and the
+two-grid training loss with its gradient, all through the C ABI against the FP64 oracle.
+
+Tolerances: FP32 network path element-wise rtol 2e-5 (a few ulps through ~100-term dot
+products); gradients 1e-4 relative; bfloat16 mode checked against the oracle's own
+bfloat16 emulation where the two roundings agree, and as a whole against the FP32 result.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2102_12071_gb300 import binding as B
+from paper_2102_12071_gb300 import inputs
+from paper_2102_12071_gb300 import solver as S
+from paper_2102_12071_gb300 import train as T
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2102_12071_gb300 import build
+
+    build.build()
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def small_net(seed=0, scale=0.05):
+    """Random network whose smoother stays convergent: Kaiming convolutions, small output layer."""
+    p = T.init_params(seed).numpy()
+    p[-243:] = np.random.default_rng(seed).standard_normal(243) * scale
+    return p.astype(np.float32)
+
+
+def varcoef_field(n, seed):
+    a = inputs.grf_cells(seed, n)
+    return f32(O.varcoef5_field(n, f32(a)))
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+def test_net_forward_matches_oracle(bf16):
+    n = 45  # three 16-point tiles with a ragged last one
+    fields = np.stack([varcoef_field(n, 10), f32(O.const_field(n, O.q1_rotated_stencil(0.02, 0.9)))])
+    p = small_net(1, 0.3)
+    Wg = S.net_forward(torch.from_numpy(fields.astype(np.float32)).cuda(), torch.from_numpy(p).cuda(),
+                       2.0 / 3.0, bf16).double().cpu().numpy()
+    for k in range(2):
+        Wo = O.hypernet_forward(fields[k], f32(p), 2.0 / 3.0, bf16)
+        scale = np.abs(Wo).max()
+        if not bf16:
+            np.testing.assert_allclose(Wg[k], Wo, rtol=2e-5, atol=2e-6 * scale)
+        else:
+            # the two sides round FP32 (kernel) and FP64 (oracle) pre-activations to bfloat16;
+            # they agree except where a value sits within an FP32 ulp of a rounding boundary
+            err = np.abs(Wg[k] - Wo)
+            assert np.mean(err <= 2e-5 * scale) > 0.99
+            assert err.max() <= 2e-2 * scale
+
+
+@pytest.mark.parametrize("n", [31, 127])
+def test_cnn_kernels_match_oracle_on_every_level(n):
+    """Constant stencils use kernel class tables on a proxy grid; expanded, they must equal
+    the network evaluated on each level's full field (FP32 network)."""
+    eps, theta = 0.03, 2.0
+    p = small_net(2)
+    mg = S.MultigridSolver([S.rotated(n, eps, theta)], "cnn", torch.from_numpy(p).cuda())
+    om = O.Multigrid(O.const_field(n, f32(O.q1_rotated_stencil(eps, theta))))
+    for l in range(mg.levels - 1):
+        Wg = mg.kernels(0, l).double().cpu().numpy()
+        Wo = O.hypernet_forward(om.field(l), f32(p))
+        np.testing.assert_allclose(Wg, Wo, rtol=2e-5, atol=2e-6 * np.abs(Wo).max())
+
+
+@pytest.mark.parametrize("n,cycles", [(63, 60), (255, 25)])
+def test_cnn_solve_history_matches_oracle(n, cycles):
+    eps, theta = 0.05, 0.7
+    p = small_net(3)
+    b = inputs.rhs_uniform(7, n)
+    mg = S.MultigridSolver([S.rotated(n, eps, theta)], "cnn", torch.from_numpy(p).cuda())
+    _, _, gh, cyc, _ = mg.solve(torch.from_numpy(b).cuda()[None].contiguous(), rtol=0.0, max_cycles=cycles)
+    om = O.Multigrid(O.const_field(n, f32(O.q1_rotated_stencil(eps, theta))))
+    om.set_cnn(f32(p))
+    _, oh = om.solve(f32(b), rtol=0.0, max_cycles=cycles)
+    assert cyc[0] == cycles
+    rel = np.abs(gh[0][: cycles + 1] - oh) / oh
+    assert rel.max() <= 1e-5, rel.max()
+
+
+def test_cnn_solve_varcoef_field_path():
+    """Per-point kernels (variable coefficients): setup, RAP fields and the CNN solve."""
+    n = 127
+    a = inputs.grf_cells(11, n)
+    p = small_net(4)
+    mg = S.MultigridSolver([S.varcoef5(n, torch.from_numpy(a).cuda())], "cnn", torch.from_numpy(p).cuda())
+    st0 = O.varcoef5_field(n, f32(a))
+    om = O.Multigrid(f32(st0))
+    for l in range(mg.levels):
+        g = mg.stencil_field(0, l).double().cpu().numpy()
+        np.testing.assert_allclose(g, om.field(l), rtol=0, atol=4e-7 * np.abs(om.field(l)).max())
+    om.set_cnn(f32(p))
+    b = inputs.rhs_uniform(8, n)
+    _, _, gh, cyc, _ = mg.solve(torch.from_numpy(b).cuda()[None].contiguous(), rtol=0.0, max_cycles=20)
+    _, oh = om.solve(f32(b), rtol=0.0, max_cycles=20)
+    rel = np.abs(gh[0][:21] - oh) / oh
+    assert rel.max() <= 1e-5, rel.max()
+
+
+def _train_batch(n, nprob, nvec, seed, bf16=False):
+    params = inputs.rotated_params(seed, nprob)
+    probs = [{"n": n, "kind": B.MG_PROBLEM_ROTATED, "eps": e, "theta": t} for e, t in params]
+    z = inputs.gaussian_vectors(seed + 1, nprob * nvec, n).reshape(nprob, nvec, n, n)
+    return params, probs, z, T.TwoGridBatch(probs, nvec, 2.0 / 3.0, bf16)
+
+
+@pytest.mark.parametrize("n", [15, 31])
+def test_train_step_matches_oracle_loss_and_gradient(n):
+    """C3 check at 15 x 15 (and 31 x 31): loss and dloss/dparams vs the FP64 oracle."""
+    nprob, nvec = 3, 4
+    params, probs, z, batch = _train_batch(n, nprob, nvec, 40 + n)
+    p = small_net(5, 0.1)
+    loss, grad = batch.loss_and_grad(torch.from_numpy(p).cuda(), torch.from_numpy(z).cuda().contiguous())
+    lo, go = 0.0, np.zeros(p.size)
+    for k, (e, t) in enumerate(params):
+        st = O.const_field(n, f32(O.q1_rotated_stencil(e, t)))
+        l1, g1 = O.cnn_loss_and_grad(st, f32(p), f32(z[k]))
+        lo += l1 / nprob
+        go += g1 / nprob
+    assert abs(loss.item() - lo) <= 1e-5 * lo
+    g = grad.double().cpu().numpy()
+    assert np.linalg.norm(g - go) <= 1e-4 * np.linalg.norm(go)
+    big = np.abs(go) > 1e-2 * np.abs(go).max()
+    np.testing.assert_allclose(g[big], go[big], rtol=1e-3)
+
+
+def test_train_step_gradient_matches_finite_differences_on_gpu_loss():
+    """The library's adjoint against central differences of the library's own loss (FP32
+    loss, so the step is large and the check loose); the FP64 FD check is the oracle's."""
+    n = 15
+    _, _, z, batch = _train_batch(n, 2, 4, 77)
+    p = small_net(6, 0.1).astype(np.float64)
+    zt = torch.from_numpy(z).cuda().contiguous()
+    _, grad = batch.loss_and_grad(torch.from_numpy(p.astype(np.float32)).cuda(), zt)
+    g = grad.double().cpu().numpy()
+    d = np.random.default_rng(0).standard_normal(p.size)
+    h = 1e-2 / np.linalg.norm(d)
+    lp, _ = batch.loss_and_grad(torch.from_numpy((p + h * d).astype(np.float32)).cuda(), zt, False)
+    lm, _ = batch.loss_and_grad(torch.from_numpy((p - h * d).astype(np.float32)).cuda(), zt, False)
+    fd = (lp.item() - lm.item()) / (2 * h)
+    assert abs(fd - g @ d) <= 2e-2 * abs(g @ d)
+
+
+def test_bf16_training_loss_close_to_fp32():
+    n = 31
+    _, probs, z, b32 = _train_batch(n, 4, 4, 90, bf16=False)
+    b16 = T.TwoGridBatch(probs, 4, 2.0 / 3.0, True)
+    p = torch.from_numpy(small_net(7, 0.1)).cuda()
+    zt = torch.from_numpy(z).cuda().contiguous()
+    l32, g32 = b32.loss_and_grad(p, zt)
+    l16, g16 = b16.loss_and_grad(p, zt)
+    assert abs(l16.item() - l32.item()) <= 1e-2 * l32.item()
+    cos = torch.dot(g16, g32) / (g16.norm() * g32.norm())
+    assert cos.item() > 0.99
+
+
+def test_autograd_function_and_adam_step_reduce_loss():
+    _, _, z, batch = _train_batch(31, 8, 8, 123)
+    zt = torch.from_numpy(z).cuda().contiguous()
+    tr = T.Trainer(sizes=(31,), per_size=8, nvec=8, conv_bf16=False, lr=1e-3, seed=0)
+    # the autograd path returns the library's adjoint
+    p = tr.params.detach().clone().requires_grad_(True)
+    T.TwoGridLoss.apply(p, zt, batch).backward()
+    _, g = batch.loss_and_grad(p.detach(), zt)
+    torch.testing.assert_close(p.grad, g)
+    l0 = batch.loss_and_grad(tr.params.detach(), zt, False)[0].item()
+    for _ in range(40):
+        tr.step()
+    l1 = batch.loss_and_grad(tr.params.detach(), zt, False)[0].item()
+    assert l1 < l0
