@@ -195,6 +195,37 @@ void mg_train_destroy(mg_train_ctx* ctx);
 mg_status mg_train_step(mg_train_ctx* ctx, const float* params, const float* z,
                         float* grad_out, float* loss_out, void* stream);
 
+/* ------------------------------------------------- solving without a workspace ---- */
+
+/* Limits of mg_solve_small_static: its scratch is a fixed device array of
+   MG_STATIC_SCRATCH_BYTES inside the library, enough for MG_STATIC_MAX_PROBLEMS problems
+   of at most MG_STATIC_MAX_N points per side. */
+#define MG_STATIC_MAX_PROBLEMS 16
+#define MG_STATIC_MAX_N 63
+#define MG_STATIC_SCRATCH_BYTES (512 * 1024)
+
+/* The paper has no counterpart to this call; it exists for callers that cannot allocate
+   device memory: plugins whose host framework's caching allocator owns the GPU memory,
+   control loops with a fixed memory budget that must not risk an allocation failure while
+   running, and latency-bound code that cannot pay for cudaMalloc/cudaFree (they may
+   synchronise the device).  It performs what mg_workspace_size + mg_setup + mg_solve do
+   for a batch of small constant-stencil problems (MG_PROBLEM_ROTATED or MG_PROBLEM_STENCIL,
+   all of one size n = 2^m - 1 <= MG_STATIC_MAX_N, at most MG_STATIC_MAX_PROBLEMS of them)
+   with weighted-Jacobi V(1,1) cycles down to a 3x3 grid, but allocates nothing: its
+   scratch is a device array of MG_STATIC_SCRATCH_BYTES compiled into the library, held by
+   every GPU that loads the library until the process exits.  Larger requests fail with
+   MG_ERR_INVALID_ARG (other smoothers or options: MG_ERR_UNSUPPORTED).
+   Arguments, outputs and return codes are those of mg_solve (b, x_hi, x_lo DEVICE
+   [nprob][n][n], x_lo may be NULL; hist, cycles HOST or NULL); opts must ask for
+   MG_SMOOTH_JACOBI, nu1 = nu2 = 1, coarsest_n = 3.  The first call on a device looks up
+   the array's device address on the current device, so make it before any stream
+   capture.  Every call reuses the same array and resets what must start from zero; calls
+   whose GPU work overlaps (two threads, or two streams) race on it and must be serialised
+   by the caller.  Blocks the calling thread until the solve has finished. */
+mg_status mg_solve_small_static(const mg_problem* problems, int nprob, const mg_options* opts,
+                                const float* b, float* x_hi, float* x_lo, double rtol,
+                                int max_cycles, double* hist, int* cycles, void* stream);
+
 /* ------------------------------------------------------------ measurement ---- */
 
 /* Optional CUDA-event timing of individual kernel launches on the launching stream, for

@@ -66,6 +66,8 @@ def lib() -> ctypes.CDLL:
                                           ctypes.POINTER(mg_options), _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)]),
         "mg_train_destroy": (None, [_P]),
         "mg_train_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+        "mg_solve_small_static": (ctypes.c_int, [ctypes.POINTER(mg_problem), ctypes.c_int, ctypes.POINTER(mg_options),
+                                                 _P, _P, _P, ctypes.c_double, ctypes.c_int, _P, _P, _P]),
         "mg_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
         "mg_profile_read": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_longlong)]),
@@ -177,6 +179,18 @@ def mg_solve(ctx, b, x_hi, x_lo, rtol, max_cycles, hist=None, cycles=None, strea
                         _stream(stream))
     if st not in (MG_OK, MG_ERR_NOT_CONVERGED):
         check(st, "mg_solve")
+    return st
+
+
+def mg_solve_small_static(probs, nprob, opts, b, x_hi, x_lo, rtol, max_cycles, hist=None, cycles=None,
+                          stream=None) -> int:
+    """Workspace-free solve of small constant-stencil batches (see include/mgcnn.h)."""
+    hp = hist.ctypes.data if hist is not None else None
+    cp = cycles.ctypes.data if cycles is not None else None
+    st = lib().mg_solve_small_static(probs, nprob, ctypes.byref(opts), _ptr(b), _ptr(x_hi), _ptr(x_lo), float(rtol),
+                                     int(max_cycles), hp, cp, _stream(stream))
+    if st not in (MG_OK, MG_ERR_NOT_CONVERGED):
+        check(st, "mg_solve_small_static")
     return st
 
 
