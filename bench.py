@@ -189,6 +189,46 @@ def cpu_baseline(n: int, budget_s: float = 12.0):
             "sample": f"{cycles} V(1,1) Jacobi cycles of one {n}^2 problem (FP64, single thread)"}
 
 
+def run_varcoef(args, rank):
+    """Variable-coefficient diffusion -div(a grad u), a = exp(GRF), 5-point stencil: one
+    problem of side args.varcoef_n solved to 1e-8 with the CNN and with Jacobi (C4)."""
+    import numpy as np
+    import torch
+
+    from paper_2102_12071_gb300 import inputs, solver as S
+
+    n = args.varcoef_n
+    cells = torch.from_numpy(inputs.grf_cells(inputs.SEED_GRF + rank, n)).cuda()
+    b = torch.from_numpy(inputs.rhs_uniform(inputs.SEED_RHS + 500 + rank, n)).cuda()[None].contiguous()
+    w = None
+    for name in ("cnn_varcoef.npy", "cnn_rotated.npy"):
+        path = os.path.join(os.path.dirname(WEIGHTS), name)
+        if os.path.exists(path):
+            w = torch.from_numpy(np.load(path).astype(np.float32)).cuda()
+            wname = name
+            break
+    out = {"n": n, "problem": "GRF a = exp(g), unit variance, correlation length 1/16, 5-point", "rtol": RTOL}
+    kinds = ["jacobi"] + (["cnn"] if w is not None else [])
+    for kind in kinds:
+        mg = S.MultigridSolver([S.varcoef5(n, cells)], kind, net_params=w if kind == "cnn" else None)
+        for _ in range(2):
+            mg.solve(b, rtol=RTOL, max_cycles=MAX_CYCLES, history=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, _, _, cyc, st = mg.solve(b, rtol=RTOL, max_cycles=MAX_CYCLES, history=False)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[kind] = {"ms": ms, "cycles": int(cyc[0]), "converged": int(st) == 0,
+                     "mdof_sweeps_per_s": sweeps_per_cycle(mg.sizes) * int(cyc[0]) / (ms / 1e3)}
+        mg.close()
+    if w is not None:
+        out["weights"] = wname
+        out["cnn_vs_jacobi_time"] = out["jacobi"]["ms"] / out["cnn"]["ms"]
+    return out
+
+
 def run_profile_case(args):
     """Set up the benchmark batch and run a fixed number of cycles, nothing else."""
     import torch
@@ -223,6 +263,7 @@ def main():
     ap.add_argument("--profile-cycles", type=int, default=0,
                     help="only set up the batch and run this many V-cycles (for profiler captures)")
     ap.add_argument("--smoother", default="auto", choices=["auto", "jacobi", "cnn"])
+    ap.add_argument("--varcoef-n", type=int, default=1023, help="side of the GRF problem (0: skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -313,6 +354,18 @@ def main():
     arms[headline].solve(b, x_hi, x_lo, rtol=0.0, max_cycles=args.roofline_cycles, history=False)
     torch.cuda.synchronize()
     prof = {c: B.mg_profile_read(ctx, c) for c in range(6)}
+    # the same headline solve to 1e-8 with every launch event-timed: kernel time by class
+    # against the solve's wall time (the gap is launch and synchronisation overhead)
+    B.mg_profile_enable(ctx, True)
+    x_hi.zero_()
+    x_lo.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    arms[headline].solve(b, x_hi, x_lo, rtol=RTOL, max_cycles=MAX_CYCLES, history=False)
+    torch.cuda.synchronize()
+    wall_ms = (time.perf_counter() - t0) * 1e3
+    solve_prof = {KERNEL_NAMES[c]: round(B.mg_profile_read(ctx, c)[0], 3) for c in range(6)}
+    solve_launches = {KERNEL_NAMES[c]: B.mg_profile_read(ctx, c)[1] for c in range(6)}
     B.mg_profile_enable(ctx, False)
     total_ms = sum(v[0] for v in prof.values())
     dom = max((0, 1, 2), key=lambda c: prof[c][0])
@@ -325,7 +378,10 @@ def main():
                 "kernel": KERNEL_NAMES[dom], "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": algo_bytes,
                 "kernel_share": {KERNEL_NAMES[c]: round(prof[c][0] / total_ms, 4) for c in prof if total_ms},
-                "cycle_hbm_frac": (cycle_bytes * args.roofline_cycles / (total_ms / 1e3) / 1e9) / peak}
+                "cycle_hbm_frac": (cycle_bytes * args.roofline_cycles / (total_ms / 1e3) / 1e9) / peak,
+                "solve_breakdown": {"wall_ms_individual_launches": round(wall_ms, 3),
+                                    "kernel_ms": solve_prof, "launches": solve_launches,
+                                    "kernel_ms_total": round(sum(solve_prof.values()), 3)}}
 
     # ---- end to end through the public API from pinned host buffers
     hb = torch.from_numpy(b_host).pin_memory()
@@ -347,6 +403,7 @@ def main():
     e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps)
     e2e_val = sum(sweeps_per_cycle(sizes) * int(c) for c in cyc_e2e) * world / e2e_s
 
+    varcoef = run_varcoef(args, rank) if args.varcoef_n else None
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -369,6 +426,7 @@ def main():
                 "d2h_bytes_per_step": 2 * b.numel() * 4, "ms_per_step": e2e_s * 1e3},
         "gpu_launches": int(launches),
         "clocks": clocks,
+        "varcoef": varcoef,
     }
     if "cnn" in results:
         line["cnn_vs_jacobi_time"] = results["jacobi"]["ms_per_step"] / results["cnn"]["ms_per_step"]

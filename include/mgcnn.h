@@ -21,7 +21,9 @@
  *              (H v)(p) = sum_k W[k][p] * v(p + d_k), v = 0 outside the interior.
  *   Memory     every pointer documented "device" must point to memory of the current
  *              CUDA device; the caller owns every buffer, including the workspace.  The
- *              library allocates no device memory; a context is a small host struct.
+ *              library allocates no device buffers; a context is a host struct that may
+ *              also hold CUDA graphs of one V-cycle and a private capture stream (their
+ *              runtime state is released by mg_destroy).
  *              Buffers must stay valid until the work queued on the stream completes.
  *   Streams    `stream` is a cudaStream_t (NULL = the legacy default stream).  All
  *              device work of a call is queued on it.  One context must not be used
@@ -46,7 +48,7 @@ typedef enum {
   MG_ERR_CUDA = 3,          /* a CUDA runtime call or kernel launch failed             */
   MG_ERR_NOT_CONVERGED = 4, /* mg_solve hit max_cycles before rtol (results valid)     */
   MG_ERR_NUMERIC = 5,       /* NaN/Inf residual or a non-SPD coarsest operator         */
-  MG_ERR_TIMEOUT = 6,       /* reserved for bounded device-side waits                  */
+  MG_ERR_TIMEOUT = 6,       /* a bounded device-side wait for tile copies expired      */
   MG_ERR_UNSUPPORTED = 7    /* valid request outside what this build implements        */
 } mg_status;
 
@@ -103,7 +105,7 @@ size_t mg_workspace_size(const mg_problem* problems, int nprob, const mg_options
 /* Builds the multigrid hierarchy of Algorithm 1 for nprob problems on `stream`:
    level-0 stencils (Sec. 6.1 eq. pde / Sec. 4), Galerkin coarse operators P^T A P
    (Sec. 2.2) with full coarsening and bilinear P (Sec. 6.1, Fig. full_coarsening) down to
-   coarsest_n, the FP64 Cholesky factor of the coarsest operator, and -- for
+   coarsest_n, the FP64 inverse of the coarsest operator, and -- for
    MG_SMOOTH_CNN -- the per-point smoothing kernels of every smoothed level from the
    network with parameters net_params (DEVICE float[mg_net_nparams()], read during this
    call only; NULL for Jacobi).  workspace: DEVICE, >= mg_workspace_size bytes, 256-byte

@@ -103,7 +103,8 @@ mg_status make_plan(const mg_problem* probs, int nprob, const mg_options* o, Pla
   P.tail_solve = P.lstar == 0;
   const int nt = tiles_per_side(n);
   P.ntiles_max = nt * nt;
-  if (tail_smem_bytes(P.nl, P.lstar, L, P.hk) > 200 * 1024) return fail(MG_ERR_UNSUPPORTED, "tail does not fit in shared memory");
+  if (tail_smem_bytes(P.nl, P.lstar, L, P.hk) > MG_TAIL_SMEM_MAX)
+    return fail(MG_ERR_UNSUPPORTED, "tail does not fit in shared memory");
   return MG_OK;
 }
 
@@ -131,10 +132,75 @@ struct mg_ctx {
   float* xlo_ws = nullptr;
   int* d_fail = nullptr;
   NetJob* d_jobs = nullptr;
+  int* d_active = nullptr;      // compacted list of problems still iterating
+  std::vector<int> h_active;
+  LevelArrays arrays;
+  TileMaps maps;
   Profiler prof;
+  // one captured V-cycle (residual + every level kernel) per compacted launch size
+  struct CycleGraph {
+    int nactive, max_cycles;
+    float rtol;
+    cudaGraphExec_t exec;
+    long long nodes;
+  };
+  std::vector<CycleGraph> graphs;
+  cudaStream_t capture_stream = nullptr;
+  ~mg_ctx() {
+    for (CycleGraph& g : graphs) cudaGraphExecDestroy(g.exec);
+    if (capture_stream) cudaStreamDestroy(capture_stream);
+  }
 };
 
-// Workspace layout; with base == nullptr only the size is computed.
+// The executable graph of one cycle for the current launch size, captured on a private
+// stream the first time it is needed and replayed on the caller's stream afterwards.
+static mg_status cycle_graph(mg_ctx* ctx, const CycleArgs& a, float rtol, int max_cycles, cudaGraphExec_t* out,
+                             long long* nodes) {
+  const int nact = a.active ? a.nactive : 0;
+  for (const mg_ctx::CycleGraph& g : ctx->graphs)
+    if (g.nactive == nact && g.rtol == rtol && g.max_cycles == max_cycles) {
+      *out = g.exec;
+      *nodes = g.nodes;
+      return MG_OK;
+    }
+  if (!ctx->capture_stream) CK(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+  CK(prepare_tail(a));
+  CycleArgs c = a;
+  c.stream = ctx->capture_stream;
+  c.pdl = true;
+  const long long before = ctx->prof.launches;
+  CK(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e1 = launch_residual(c, rtol, max_cycles);
+  cudaError_t e2 = e1 == cudaSuccess ? launch_cycle(c) : e1;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e3 = cudaStreamEndCapture(c.stream, &graph);
+  if (e2 != cudaSuccess || e3 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return fail(MG_ERR_CUDA, "capturing the cycle graph: %s", cudaGetErrorString(e2 != cudaSuccess ? e2 : e3));
+  }
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t e4 = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e4 != cudaSuccess) return fail(MG_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e4));
+  mg_ctx::CycleGraph g;
+  g.nactive = nact;
+  g.rtol = rtol;
+  g.max_cycles = max_cycles;
+  g.exec = exec;
+  g.nodes = ctx->prof.launches - before;
+  ctx->prof.launches = before;
+  ctx->graphs.push_back(g);
+  *out = exec;
+  *nodes = g.nodes;
+  return MG_OK;
+}
+
+// row pitch of level vectors: a multiple of 32 floats (128-byte rows, TMA-aligned)
+static int pitch_of(int n) { return (n + 31) & ~31; }
+
+// Workspace layout; with base == nullptr only the size is computed.  Level vectors are
+// level-major: r and e of all problems of a level form one pitched [nprob][n][pitch]
+// array, the unit of the TMA tensor maps.
 static size_t carve(const Plan& P, const mg_options& o, void* base, mg_ctx* ctx) {
   Carver c(base);
   ProbDev* probs = c.take<ProbDev>(P.nprob);
@@ -142,7 +208,23 @@ static size_t carve(const Plan& P, const mg_options& o, void* base, mg_ctx* ctx)
   float* partials = c.take<float>((size_t)P.nprob * P.ntiles_max);
   float* xlo = c.take<float>((size_t)P.nprob * P.n0 * P.n0);
   int* fail_flag = c.take<int>(4);
+  int* active = c.take<int>(P.nprob);
   NetJob* jobs = c.take<NetJob>((size_t)P.nprob * P.L);
+  LevelArrays A;
+  memset(&A, 0, sizeof(A));
+  for (int l = 0; l < P.L; ++l) {
+    A.n[l] = P.nl[l];
+    A.pitch[l] = pitch_of(P.nl[l]);
+    const size_t sz = (size_t)P.nprob * A.n[l] * A.pitch[l];
+    A.r[l] = c.take<float>(sz);
+    A.e[l] = c.take<float>(sz);
+  }
+  if (P.lstar > 0) {
+    const size_t sz = (size_t)P.nprob * A.n[0] * A.pitch[0];
+    A.xh0 = c.take<float>(sz);
+    A.xl0 = c.take<float>(sz);
+    A.b0 = c.take<float>(sz);
+  }
   std::vector<ProbDev> hp(ctx ? P.nprob : 0);
   for (int p = 0; p < P.nprob; ++p) {
     ProbDev d;
@@ -153,8 +235,9 @@ static size_t carve(const Plan& P, const mg_options& o, void* base, mg_ctx* ctx)
       LevelDev& v = d.lv[l];
       v.n = n;
       v.T = n < MG_PROXY ? n : MG_PROXY;
-      v.r = c.take<float>(nn);
-      v.e = c.take<float>(nn);
+      v.pitch = A.pitch[l];
+      v.r = A.r[l] ? A.r[l] + (size_t)p * n * A.pitch[l] : nullptr;
+      v.e = A.e[l] ? A.e[l] + (size_t)p * n * A.pitch[l] : nullptr;
       if (P.sk == SK_FIELD) v.st = c.take<float>(9 * nn);
       if (l < P.L - 1) {
         if (P.hk == HK_FIELD) v.W = c.take<float>(9 * nn);
@@ -170,9 +253,13 @@ static size_t carve(const Plan& P, const mg_options& o, void* base, mg_ctx* ctx)
     ctx->args.probs = probs;
     ctx->args.state = state;
     ctx->args.partials = partials;
+    ctx->args.xh0 = A.xh0;
+    ctx->args.xl0 = A.xl0;
+    ctx->arrays = A;
     ctx->xlo_ws = xlo;
     ctx->d_fail = fail_flag;
     ctx->d_jobs = jobs;
+    ctx->d_active = active;
   }
   (void)o;
   return c.off + 256;
@@ -234,7 +321,15 @@ mg_status mg_setup(const mg_problem* problems, int nprob, const mg_options* opts
   a.omega = opts->omega;
   a.stream = s;
   a.prof = &ctx->prof;
+  a.active = nullptr;
+  a.nactive = 0;
+  a.pdl = false;
+  a.maps = &ctx->maps;
   ctx->h_state.resize(P.nprob);
+  if (P.lstar > 0 && !build_tile_maps(ctx->maps, ctx->arrays, P.nprob, P.lstar)) {
+    delete ctx;
+    return fail(MG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the level arrays");
+  }
   // level-0 stencils
   for (int p = 0; p < nprob; ++p) {
     const mg_problem& q = problems[p];
@@ -345,9 +440,15 @@ mg_status mg_vcycle(mg_ctx* ctx, const float* b, float* x_hi, float* x_lo, float
   if (ctx->plan.tail_solve) {
     CK(launch_tail_solve(a, b, x_hi, x_lo, -1.f, big, 1, 1));
   } else {
-    CK(launch_residual(a, b, x_hi, x_lo, -1.f, big));
-    CK(launch_cycle(a, x_hi, x_lo));
-    CK(launch_residual(a, b, x_hi, x_lo, -1.f, big));
+    const LevelArrays& A = ctx->arrays;
+    CK(launch_pack(b, A.b0, A.n[0], A.pitch[0], a.nprob, a.stream));
+    CK(launch_pack(x_hi, A.xh0, A.n[0], A.pitch[0], a.nprob, a.stream));
+    CK(launch_pack(x_lo, A.xl0, A.n[0], A.pitch[0], a.nprob, a.stream));
+    CK(launch_residual(a, -1.f, big));
+    CK(launch_cycle(a));
+    CK(launch_residual(a, -1.f, big));
+    CK(launch_unpack(A.xh0, x_hi, A.n[0], A.pitch[0], a.nprob, a.stream));
+    if (x_lo) CK(launch_unpack(A.xl0, x_lo, A.n[0], A.pitch[0], a.nprob, a.stream));
   }
   if (rel_res) CK(launch_copy_rel(a.state, rel_res, a.nprob, a.stream));
   return MG_OK;
@@ -361,9 +462,17 @@ mg_status mg_solve(mg_ctx* ctx, const float* b, float* x_hi, float* x_lo, double
   a.stream = (cudaStream_t)stream;
   const Plan& P = ctx->plan;
   float* xlo = x_lo;
-  if (!xlo) {
-    xlo = ctx->xlo_ws;
-    CK(cudaMemsetAsync(xlo, 0, sizeof(float) * (size_t)P.nprob * P.n0 * P.n0, a.stream));
+  const LevelArrays& A = ctx->arrays;
+  if (P.tail_solve) {
+    if (!xlo) {
+      xlo = ctx->xlo_ws;
+      CK(cudaMemsetAsync(xlo, 0, sizeof(float) * (size_t)P.nprob * P.n0 * P.n0, a.stream));
+    }
+  } else {
+    // the tiled path iterates on pitched copies (TMA-aligned rows) and copies x back at the end
+    CK(launch_pack(b, A.b0, A.n[0], A.pitch[0], a.nprob, a.stream));
+    CK(launch_pack(x_hi, A.xh0, A.n[0], A.pitch[0], a.nprob, a.stream));
+    CK(launch_pack(x_lo, A.xl0, A.n[0], A.pitch[0], a.nprob, a.stream));
   }
   CK(cudaMemsetAsync(a.state, 0, sizeof(ProbState) * a.nprob, a.stream));
   CK(launch_bnorm(a, b));
@@ -373,34 +482,57 @@ mg_status mg_solve(mg_ctx* ctx, const float* b, float* x_hi, float* x_lo, double
   for (;;) {
     if (P.tail_solve) {
       CK(launch_tail_solve(a, b, x_hi, xlo, frtol, max_cycles, G, 0));
-    } else {
+    } else if (ctx->prof.on) {  // event timing needs individual launches
       for (int c = 0; c < G; ++c) {
-        CK(launch_residual(a, b, x_hi, xlo, frtol, max_cycles));
-        CK(launch_cycle(a, x_hi, xlo));
+        CK(launch_residual(a, frtol, max_cycles));
+        CK(launch_cycle(a));
       }
+    } else {
+      cudaGraphExec_t exec;
+      long long nodes = 0;
+      mg_status gs = cycle_graph(ctx, a, frtol, max_cycles, &exec, &nodes);
+      if (gs != MG_OK) return gs;
+      for (int c = 0; c < G; ++c) CK(cudaGraphLaunch(exec, a.stream));
+      ctx->prof.launches += nodes * G;
     }
     CK(cudaMemcpyAsync(ctx->h_state.data(), a.state, sizeof(ProbState) * P.nprob, cudaMemcpyDeviceToHost, a.stream));
     CK(cudaStreamSynchronize(a.stream));
     ctx->prof.collect();
     int active = 0;
+    ctx->h_active.clear();
     for (int p = 0; p < P.nprob; ++p) {
       const ProbState& S = ctx->h_state[p];
       if (hist)
         for (int k = seen[p]; k < S.iter; ++k) hist[(size_t)p * (max_cycles + 1) + k] = S.hist[k % MG_HRING];
       seen[p] = S.iter;
       active += S.active;
+      if (S.active) ctx->h_active.push_back(p);
     }
     if (!active) break;
+    // later chunks launch CTAs only for the problems still iterating
+    if (active < a.nprob && active != a.nactive) {
+      CK(cudaMemcpyAsync(ctx->d_active, ctx->h_active.data(), sizeof(int) * active, cudaMemcpyHostToDevice,
+                         a.stream));
+      a.active = ctx->d_active;
+      a.nactive = active;
+    }
     G = G < 128 ? 2 * G : 128;
+  }
+  if (!P.tail_solve) {
+    CK(launch_unpack(A.xh0, x_hi, A.n[0], A.pitch[0], a.nprob, a.stream));
+    if (x_lo) CK(launch_unpack(A.xl0, x_lo, A.n[0], A.pitch[0], a.nprob, a.stream));
+    CK(cudaStreamSynchronize(a.stream));
   }
   mg_status rc = MG_OK;
   for (int p = 0; p < P.nprob; ++p) {
     const ProbState& S = ctx->h_state[p];
     if (cycles) cycles[p] = S.cycles;
-    if (S.status == 3) rc = MG_ERR_NUMERIC;
+    if (S.status == 4) rc = MG_ERR_TIMEOUT;
+    else if (S.status == 3 && rc != MG_ERR_TIMEOUT) rc = MG_ERR_NUMERIC;
     else if (S.status == 2 && rc == MG_OK) rc = MG_ERR_NOT_CONVERGED;
   }
-  if (rc == MG_ERR_NUMERIC) fail(rc, "non-finite residual");
+  if (rc == MG_ERR_TIMEOUT) fail(rc, "a bounded wait for tile copies expired");
+  else if (rc == MG_ERR_NUMERIC) fail(rc, "non-finite residual");
   else if (rc == MG_ERR_NOT_CONVERGED) fail(rc, "max_cycles reached before rtol");
   return rc;
 }

@@ -1,11 +1,11 @@
 // mg_common.cuh -- device-side data layout and helpers shared by the sm_103a kernels.
 //
 // Layout in HBM (all carved from the caller's workspace, 256-byte aligned):
-//   per problem p and level l: r_l, e_l            float[n_l*n_l]
+//   per level l, all problems: r_l, e_l            float[nprob][n_l][pitch_l] (128-byte rows)
 //   per-point stencil fields (FIELD problems)      float[9][n_l][n_l]
 //   per-point smoothing kernels (CNN, FIELD)       float[9][n_l][n_l]
 //   kernel class tables (CNN, constant stencils)   float[9][T][T], T = min(n_l, 11)
-//   coarsest FP64 Cholesky factor                  double[m][m], m = n_L^2
+//   coarsest FP64 inverse                          double[m][m], m = n_L^2
 //   ProbDev descriptors, ProbState control blocks, per-CTA norm partials.
 #pragma once
 #include <cuda_runtime.h>
@@ -14,6 +14,7 @@
 #define MG_MAXL 14
 #define MG_HRING 256          // ring of relative residuals per problem (>= cycles per chunk)
 #define MG_TAIL_N 63          // levels at or below this size run in one CTA per problem
+#define MG_TAIL_SMEM_MAX (200 * 1024)  // dynamic shared memory limit of the tail kernels
 #define MG_NET_MARGIN 5       // points closer than this to an edge get their own kernel class
 #define MG_PROXY (2 * MG_NET_MARGIN + 1)  // proxy grid side for constant-stencil inference
 #define MG_NPARAMS 1260
@@ -24,17 +25,26 @@ enum { HK_JACOBI = 0, HK_TABLE = 1, HK_FIELD = 2 };  // smoother storage
 struct LevelDev {
   int n;
   int T;               // class-table side (HK_TABLE)
-  float* r;            // residual / right-hand side of the error equation on this level
-  float* e;            // correction on this level
+  float* r;            // residual / right-hand side of the error equation, [n][pitch]
+  float* e;            // correction on this level, [n][pitch]
   float* st;           // SK_FIELD: stencil field [9][n][n]
   float* W;            // HK_TABLE: [9][T][T]; HK_FIELD: [9][n][n]
   float s[9];          // SK_CONST: stencil of this level (Galerkin product of the finer one)
-  float pad_[3];
+  int pitch;           // row pitch of r and e in floats (multiple of 32: 128-byte rows)
+  float pad_[2];
 };
+
+#define MG_DISPATCH(SKv, HKv, CALL)                                                                        \
+  do {                                                                                                     \
+    if ((SKv) == SK_CONST && (HKv) == HK_JACOBI) { constexpr int SK_ = SK_CONST, HK_ = HK_JACOBI; CALL; }  \
+    else if ((SKv) == SK_CONST && (HKv) == HK_TABLE) { constexpr int SK_ = SK_CONST, HK_ = HK_TABLE; CALL; } \
+    else if ((SKv) == SK_FIELD && (HKv) == HK_JACOBI) { constexpr int SK_ = SK_FIELD, HK_ = HK_JACOBI; CALL; } \
+    else { constexpr int SK_ = SK_FIELD, HK_ = HK_FIELD; CALL; }                                           \
+  } while (0)
 
 struct ProbDev {
   LevelDev lv[MG_MAXL];
-  double* chol;        // coarsest operator, dense lower Cholesky factor, m x m
+  double* chol;        // coarsest operator, dense FP64 inverse, m x m
   int m;               // n_L^2
   int pad_[3];
 };
@@ -45,7 +55,8 @@ struct ProbState {
   int active;          // 1 while this problem still iterates
   int iter;            // number of residual evaluations done in this solve
   int cycles;          // V-cycles whose correction has been applied
-  int status;          // 0 running, 1 converged, 2 hit max cycles, 3 non-finite residual
+  int status;          // 0 running, 1 converged, 2 hit max cycles, 3 non-finite residual,
+                       // 4 a bounded wait for tile copies expired
   unsigned int counter;  // last-CTA detection for the norm reduction
   float hist[MG_HRING];  // hist[k % MG_HRING] = relative residual after k cycles
 };

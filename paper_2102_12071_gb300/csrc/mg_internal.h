@@ -1,5 +1,6 @@
 // mg_internal.h -- launchers shared between the C-ABI layer and the kernel files.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 
@@ -61,6 +62,28 @@ struct Profiler {
   }
 };
 
+// TMA descriptors of the tiled level kernels (mg_tiles.cu); every map is a 3-D tensor
+// {x, y, problem} over one pitched level array of the whole batch.
+struct ResMaps {
+  CUtensorMap xh, xl, b;
+};
+struct UpMaps {
+  CUtensorMap e, r, ec, xh, xl;
+};
+struct TileMaps {
+  ResMaps res;
+  CUtensorMap down[MG_MAXL];
+  UpMaps up[MG_MAXL];
+};
+
+// base pointers of the pitched level arrays (all problems of a level contiguous)
+struct LevelArrays {
+  int n[MG_MAXL], pitch[MG_MAXL];
+  float* r[MG_MAXL];
+  float* e[MG_MAXL];
+  float *xh0, *xl0, *b0;  // the iterate pair and right-hand side, pitched like level 0
+};
+
 struct CycleArgs {
   ProbDev* probs;
   ProbState* state;
@@ -72,6 +95,11 @@ struct CycleArgs {
   float omega;
   cudaStream_t stream;
   Profiler* prof;
+  const int* active;  // device list of the problems cycle launches cover (nullptr: all)
+  int nactive;
+  const TileMaps* maps;  // host copy of the tensor maps (tiled levels)
+  float *xh0, *xl0;      // pitched iterate pair of the tiled path
+  bool pdl;              // launch the cycle chain with programmatic dependencies
 };
 
 // one network evaluation: a stencil field (st) or a constant stencil (s) on an n x n grid
@@ -92,13 +120,39 @@ struct NetBatch {
   int pad_;
 };
 
+// Launch with programmatic stream serialisation: the kernel may be scheduled before the
+// previous kernel on the stream finishes; it must call griddepcontrol.wait before reading
+// anything that kernel writes (all cycle kernels do).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
+}
+
 int tiles_per_side(int n);
 size_t tail_smem_bytes(const int* nl, int l0, int L, int hk);
 
 cudaError_t launch_bnorm(const CycleArgs& a, const float* b);
-cudaError_t launch_residual(const CycleArgs& a, const float* b, const float* xhi, const float* xlo, float rtol,
-                            int max_cycles);
-cudaError_t launch_cycle(const CycleArgs& a, float* xhi, float* xlo);
+// tiled path (mg_tiles.cu): residual of the pitched iterate, and one V-cycle below it
+cudaError_t launch_residual(const CycleArgs& a, float rtol, int max_cycles);
+cudaError_t launch_cycle(const CycleArgs& a);
+bool build_tile_maps(TileMaps& maps, const LevelArrays& arrays, int nprob, int lstar);
+cudaError_t launch_pack(const float* src, float* dst, int n, int pitch, int nprob, cudaStream_t s);
+cudaError_t launch_unpack(const float* src, float* dst, int n, int pitch, int nprob, cudaStream_t s);
+// one-CTA coarse tail from level a.lstar (mg_cycle.cu); prepare_tail sets its launch
+// attributes (call it outside stream capture)
+cudaError_t launch_tail(const CycleArgs& a);
+cudaError_t prepare_tail(const CycleArgs& a);
 cudaError_t launch_tail_solve(const CycleArgs& a, const float* b, float* xhi, float* xlo, float rtol, int max_cycles,
                               int budget, int final_residual);
 cudaError_t launch_smoother(const CycleArgs& a, int p, int l, const float* f, float* u, int nsteps);

@@ -1,6 +1,6 @@
 // mg_setup.cu -- hierarchy set-up kernels: level-0 stencils, Galerkin coarse operators
 // P^T A P (Sec. 2.2) under full coarsening with bilinear P (Sec. 6.1), and the FP64
-// Cholesky factor of the coarsest operator (the direct solve of Algorithm 1).
+// inverse of the coarsest operator (the direct solve of Algorithm 1).
 #include "mg_common.cuh"
 #include "mg_internal.h"
 
@@ -87,11 +87,17 @@ __global__ void k_rap_field(const ProbDev* __restrict__ probs, int l) {
 __global__ void k_rap_const(ProbDev* __restrict__ probs, int nprob, int L) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nprob) return;
+  // The recursion is carried in float-float and only rounded for storage: the weights
+  // P(x,I) P(y,J) are powers of two, so every product is exact, and no level inherits the
+  // rounding of the level above.  (That matters because bilinear P sums to 4 around a coarse
+  // point, so the Galerkin product multiplies a stencil's row sum by 4 per level and would
+  // amplify each level's FP32 rounding of the near-zero row sum by 4 per level below it.)
+  float sh[9], sl[9];
+  for (int k = 0; k < 9; ++k) { sh[k] = probs[p].lv[0].s[k]; sl[k] = 0.f; }
   for (int l = 0; l + 1 < L; ++l) {
-    float s[9], c[9], lo[9];
-    for (int k = 0; k < 9; ++k) { s[k] = probs[p].lv[l].s[k]; c[k] = 0.f; lo[k] = 0.f; }
-    // coarse point at fine origin 0 (coarse centres on even fine indices); exact products,
-    // float-float sums: a Q1 stencil reproduces itself bit for bit
+    float c[9], lo[9];
+    for (int k = 0; k < 9; ++k) { c[k] = 0.f; lo[k] = 0.f; }
+    // coarse point at fine origin 0 (coarse centres on even fine indices)
     for (int ai = -1; ai <= 1; ++ai)
       for (int aj = -1; aj <= 1; ++aj) {
         const float px = pw(ai, aj);
@@ -99,15 +105,23 @@ __global__ void k_rap_const(ProbDev* __restrict__ probs, int nprob, int L) {
           const int yi = ai + k / 3 - 1, yj = aj + k % 3 - 1;
           for (int kc = 0; kc < 9; ++kc) {
             const float py = pw(yi - 2 * (kc / 3 - 1), yj - 2 * (kc % 3 - 1));
-            if (py != 0.f) ff_add(c[kc], lo[kc], px * py * s[k], 0.f);
+            if (py != 0.f) {
+              ff_add(c[kc], lo[kc], px * py * sh[k], 0.f);
+              ff_add(c[kc], lo[kc], px * py * sl[k], 0.f);
+            }
           }
         }
       }
-    for (int k = 0; k < 9; ++k) probs[p].lv[l + 1].s[k] = c[k] + lo[k];
+    for (int k = 0; k < 9; ++k) {
+      sh[k] = c[k];
+      sl[k] = lo[k];
+      probs[p].lv[l + 1].s[k] = c[k] + lo[k];
+    }
   }
 }
 
-// Dense FP64 Cholesky factor of the coarsest operator (m = n_L^2 <= 64), one thread per problem.
+// Dense FP64 inverse of the coarsest operator (m = n_L^2 <= 64), one thread per problem; the
+// coarsest solve of Algorithm 1 is then one FP64 matrix-vector product.
 __global__ void k_coarsest_factor(ProbDev* __restrict__ probs, int nprob, int L, int sk, int* __restrict__ fail) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nprob) return;
@@ -123,20 +137,22 @@ __global__ void k_coarsest_factor(ProbDev* __restrict__ probs, int nprob, int L,
         const float a = sk == SK_CONST ? C.s[k] : C.st[(size_t)k * m + i * n + j];
         A[(i * n + j) * m + ii * n + jj] += (double)a;
       }
+  // in-place Gauss-Jordan inversion; all pivots of an SPD matrix are positive
   for (int k = 0; k < m; ++k) {
-    double d = A[k * m + k];
-    for (int t = 0; t < k; ++t) d -= A[k * m + t] * A[k * m + t];
-    if (!(d > 0.0)) { atomicExch(fail, 1); return; }
-    d = sqrt(d);
-    A[k * m + k] = d;
-    for (int i = k + 1; i < m; ++i) {
-      double v = A[i * m + k];
-      for (int t = 0; t < k; ++t) v -= A[i * m + t] * A[k * m + t];
-      A[i * m + k] = v / d;
+    const double piv = A[k * m + k];
+    if (!(piv > 0.0)) {
+      atomicExch(fail, 1);
+      return;
+    }
+    A[k * m + k] = 1.0;
+    for (int j = 0; j < m; ++j) A[k * m + j] /= piv;
+    for (int i = 0; i < m; ++i) {
+      if (i == k) continue;
+      const double f = A[i * m + k];
+      A[i * m + k] = 0.0;
+      for (int j = 0; j < m; ++j) A[i * m + j] -= f * A[k * m + j];
     }
   }
-  for (int i = 0; i < m; ++i)
-    for (int j = i + 1; j < m; ++j) A[i * m + j] = 0.0;
 }
 
 // Stencil field of (p, l) expanded to [9][n][n] (couplings across the boundary zero).

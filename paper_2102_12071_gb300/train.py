@@ -93,33 +93,44 @@ class Trainer:
     """Adam on the two-grid loss over freshly drawn rotated anisotropic problems."""
 
     def __init__(self, sizes=(31, 63), per_size: int = 32, nvec: int = 32, omega: float = 2.0 / 3.0,
-                 conv_bf16: bool = True, lr: float = 1e-3, seed: int = 0, eps_range=(1e-3, 1.0)):
+                 conv_bf16: bool = True, lr: float = 1e-3, seed: int = 0, eps_range=(1e-3, 1.0),
+                 families=("rotated",)):
         self.sizes = sizes
         self.per_size = per_size
         self.nvec = nvec
         self.omega = omega
         self.conv_bf16 = conv_bf16
         self.eps_range = eps_range
+        self.families = families
         self.params = init_params(seed).cuda().requires_grad_(True)
         self.opt = torch.optim.Adam([self.params], lr=lr)
         self.gen = torch.Generator(device="cuda").manual_seed(inputs.SEED_TRAIN + seed)
         self._ws = {}
         self.step_count = 0
 
-    def problems(self, step: int, n: int) -> list[dict]:
-        params = inputs.rotated_params(inputs.SEED_TRAIN + 7919 * step + n, self.per_size, *self.eps_range)
-        return [{"n": n, "kind": B.MG_PROBLEM_ROTATED, "eps": e, "theta": t} for e, t in params]
+    def problems(self, step: int, n: int, family: str = "rotated") -> list[dict]:
+        seed = inputs.SEED_TRAIN + 7919 * step + n
+        if family == "rotated":
+            params = inputs.rotated_params(seed, self.per_size, *self.eps_range)
+            return [{"n": n, "kind": B.MG_PROBLEM_ROTATED, "eps": e, "theta": t} for e, t in params]
+        # variable coefficients a = exp(g), g a unit-variance Gaussian random field (Sec. 6.2)
+        return [{"n": n, "kind": B.MG_PROBLEM_VARCOEF5,
+                 "data": torch.from_numpy(inputs.grf_cells(seed * 64 + k, n)).cuda()}
+                for k in range(self.per_size)]
 
     def loss(self, step: int) -> torch.Tensor:
         total = 0.0
-        for n in self.sizes:
-            probs = self.problems(step, n)
-            ws = self._ws.get(n)
-            batch = TwoGridBatch(probs, self.nvec, self.omega, self.conv_bf16, ws)
-            self._ws[n] = batch.workspace
-            z = torch.randn((self.per_size, self.nvec, n, n), generator=self.gen, device="cuda")
-            total = total + TwoGridLoss.apply(self.params, z, batch)
-        return total / len(self.sizes)
+        count = 0
+        for family in self.families:
+            for n in self.sizes:
+                probs = self.problems(step, n, family)
+                key = (family, n)
+                batch = TwoGridBatch(probs, self.nvec, self.omega, self.conv_bf16, self._ws.get(key))
+                self._ws[key] = batch.workspace
+                z = torch.randn((self.per_size, self.nvec, n, n), generator=self.gen, device="cuda")
+                total = total + TwoGridLoss.apply(self.params, z, batch)
+                count += 1
+        return total / count
 
     def step(self) -> float:
         self.opt.zero_grad(set_to_none=True)
@@ -145,11 +156,13 @@ def main():
     ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights",
                                                    "cnn_rotated.npy"))
     ap.add_argument("--fp32-conv", action="store_true")
+    ap.add_argument("--families", default="rotated", help="comma list of rotated,varcoef")
     args = ap.parse_args()
     from . import build
 
     build.build()
-    tr = Trainer(lr=args.lr, seed=args.seed, conv_bf16=not args.fp32_conv)
+    tr = Trainer(lr=args.lr, seed=args.seed, conv_bf16=not args.fp32_conv,
+                 families=tuple(f.strip() for f in args.families.split(",")))
     t0 = time.time()
     for s in range(args.steps):
         l = tr.step()

@@ -102,8 +102,10 @@ def test_cnn_solve_varcoef_field_path():
     om = O.Multigrid(f32(st0))
     for l in range(mg.levels):
         g = mg.stencil_field(0, l).double().cpu().numpy()
-        # FP32 storage per level, FP64 recursion in the oracle: a few ulps per level
-        np.testing.assert_allclose(g, om.field(l), rtol=0, atol=4 * (l + 1) * 2.0 ** -24 * np.abs(om.field(l)).max())
+        # Per-point Galerkin fields are rounded to FP32 on every level.  Bilinear P sums to 4
+        # around a coarse point, so P^T A P multiplies a stencil's row sum by 4; the rounding
+        # of a level's (near-zero) row sum therefore grows by 4 per level below it.
+        np.testing.assert_allclose(g, om.field(l), rtol=0, atol=4 * 4.0 ** l * 2.0 ** -24 * np.abs(om.field(l)).max())
     om.set_cnn(f32(p))
     b = inputs.rhs_uniform(8, n)
     _, _, gh, cyc, _ = mg.solve(torch.from_numpy(b).cuda()[None].contiguous(), rtol=0.0, max_cycles=20)
