@@ -3,7 +3,7 @@
 // The tiled levels (n_l > MG_TAIL_N) are in mg_tiles.cu.  This file holds
 //   k_bnorm      ||b||^2 per problem (float-float) and the reset of the stopping state;
 //   k_tail       levels with n_l <= MG_TAIL_N in one CTA per problem, down to the FP64
-//                coarsest solve and back up (Algorithm 1 lines 3-9);
+//                coarsest solve and back up (Algorithm 1, recursion to the coarsest solve and back);
 //   k_tail_solve whole solves of small problems (n_0 <= MG_TAIL_N) in one CTA each:
 //                compensated residual, stopping test, V-cycle, float-float update;
 //   k_level_*    the standalone smoother of mg_smoother_apply.
@@ -20,8 +20,8 @@
 
 namespace mg {
 
-constexpr int TB = 32;        // fine tile side of k_residual / k_down / k_up
-constexpr int NT = 256;       // threads per CTA of the tiled kernels
+constexpr int TB = 32;        // fine tile side of the norm kernel
+constexpr int NT = 256;       // threads per CTA of the norm kernel
 constexpr int TAIL_THREADS = 512;
 
 template <int SK>
@@ -45,7 +45,10 @@ __global__ void __launch_bounds__(NT) k_bnorm(const ProbDev* __restrict__ probs,
   float acc = 0.f;
   for (int t = threadIdx.x; t < TB * TB; t += NT) {
     const int i = R0 + t / TB, j = C0 + t % TB;
-    if (in_grid(i, j, n)) { const float v = bp[(size_t)i * n + j]; acc = fmaf(v, v, acc); }
+    if (in_grid(i, j, n)) {
+      const float v = bp[(size_t)i * n + j];
+      acc = fmaf(v, v, acc);
+    }
   }
   float hi, lo;
   if (block_partial_and_last<NT>(acc, partials + (size_t)p * ntiles_max, &state[p].counter, ntiles, tile, hi, lo)) {
@@ -61,19 +64,22 @@ __global__ void __launch_bounds__(NT) k_bnorm(const ProbDev* __restrict__ probs,
 }
 
 // ------------------------------------------------------------------ tail
-// Levels l0 .. L-1 of one problem in one CTA with every vector in shared memory.
+// Levels l0 .. L-1 of one problem in one CTA with every vector in shared memory.  Each
+// level vector is stored with a one-point ring of zeros (side n+2), so stencil, smoother
+// and transfer taps need no bounds checks: the ring is the Dirichlet exterior.
 struct TailLayout {
-  int off_r[MG_MAXL], off_e[MG_MAXL], off_w[MG_MAXL];
-  int off_t, total;
+  int off_r[MG_MAXL], off_e[MG_MAXL], off_t[MG_MAXL], off_w[MG_MAXL];
+  int total;
 };
 
 __host__ __device__ inline void tail_layout(const int* nl, int l0, int L, int hk, TailLayout& t) {
   int o = 0;
   for (int l = l0; l < L; ++l) {
-    t.off_r[l] = o; o += nl[l] * nl[l];
-    t.off_e[l] = o; o += nl[l] * nl[l];
+    const int m = nl[l] + 2;
+    t.off_r[l] = o; o += m * m;
+    t.off_e[l] = o; o += m * m;
+    t.off_t[l] = o; o += m * m;
   }
-  t.off_t = o; o += nl[l0] * nl[l0];
   for (int l = l0; l < L; ++l) {
     t.off_w[l] = o;
     if (hk == HK_TABLE && l < L - 1) {
@@ -84,120 +90,163 @@ __host__ __device__ inline void tail_layout(const int* nl, int l0, int L, int hk
   t.total = o;
 }
 
+// A v at (i, j); c points at v(i, j) inside a ring-padded array of row stride m
 template <int SK>
-__device__ __forceinline__ float tail_A(const LevelDev& L, const float* s, const float* v, int n, int i, int j) {
-  float acc = 0.f;
-#pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    const int ii = i + k / 3 - 1, jj = j + k % 3 - 1;
-    const float a = (SK == SK_CONST) ? s[k] : __ldg(L.st + (size_t)k * n * n + (size_t)i * n + j);
-    const float x = in_grid(ii, jj, n) ? v[ii * n + jj] : 0.f;
-    acc = (k == 0) ? a * x : fmaf(a, x, acc);
+__device__ __forceinline__ float pad_A(const LevelDev& L, const float* s, const float* c, int m, int n, int i, int j) {
+  if (SK == SK_CONST) {
+    float acc = s[4] * c[0];
+    acc = fmaf(s[0], c[-m - 1], acc);
+    acc = fmaf(s[1], c[-m], acc);
+    acc = fmaf(s[2], c[-m + 1], acc);
+    acc = fmaf(s[3], c[-1], acc);
+    acc = fmaf(s[5], c[1], acc);
+    acc = fmaf(s[6], c[m - 1], acc);
+    acc = fmaf(s[7], c[m], acc);
+    acc = fmaf(s[8], c[m + 1], acc);
+    return acc;
   }
+  const size_t nn = (size_t)n * n;
+  const float* a = L.st + (size_t)i * n + j;
+  float acc = __ldg(a + 4 * nn) * c[0];
+  acc = fmaf(__ldg(a), c[-m - 1], acc);
+  acc = fmaf(__ldg(a + nn), c[-m], acc);
+  acc = fmaf(__ldg(a + 2 * nn), c[-m + 1], acc);
+  acc = fmaf(__ldg(a + 3 * nn), c[-1], acc);
+  acc = fmaf(__ldg(a + 5 * nn), c[1], acc);
+  acc = fmaf(__ldg(a + 6 * nn), c[m - 1], acc);
+  acc = fmaf(__ldg(a + 7 * nn), c[m], acc);
+  acc = fmaf(__ldg(a + 8 * nn), c[m + 1], acc);
   return acc;
 }
 
+// H v at (i, j) on a ring-padded array; wi holds the interior network kernel of the level
 template <int SK, int HK>
-__device__ __forceinline__ float tail_H(const LevelDev& L, const float* s, const float* wtab, float omega,
-                                        const float* v, int n, int i, int j) {
+__device__ __forceinline__ float pad_H(const LevelDev& L, const float* s, const float* wtab, const float* wi,
+                                       float omega, const float* c, int m, int n, int i, int j) {
   if (HK == HK_JACOBI) {
     const float d = (SK == SK_CONST) ? s[4] : __ldg(L.st + 4 * (size_t)n * n + (size_t)i * n + j);
-    return omega * v[i * n + j] / d;
+    return omega * c[0] / d;
   }
   const float* w;
   int stride;
   if (HK == HK_TABLE) {
-    const int T = L.T;
-    w = wtab + kclass(i, n, T) * T + kclass(j, n, T);
-    stride = T * T;
+    const int T = L.T, M = MG_NET_MARGIN;
+    if (T == MG_PROXY && i >= M && i < n - M && j >= M && j < n - M) {
+      w = wi;
+      stride = 1;
+    } else {
+      w = wtab + kclass(i, n, T) * T + kclass(j, n, T);
+      stride = T * T;
+    }
   } else {
     w = L.W + (size_t)i * n + j;
     stride = n * n;
   }
-  float acc = 0.f;
-#pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    const int ii = i + k / 3 - 1, jj = j + k % 3 - 1;
-    const float x = in_grid(ii, jj, n) ? v[ii * n + jj] : 0.f;
-    acc = fmaf(w[k * stride], x, acc);
-  }
+  float acc = w[4 * stride] * c[0];
+  acc = fmaf(w[0], c[-m - 1], acc);
+  acc = fmaf(w[stride], c[-m], acc);
+  acc = fmaf(w[2 * stride], c[-m + 1], acc);
+  acc = fmaf(w[3 * stride], c[-1], acc);
+  acc = fmaf(w[5 * stride], c[1], acc);
+  acc = fmaf(w[6 * stride], c[m - 1], acc);
+  acc = fmaf(w[7 * stride], c[m], acc);
+  acc = fmaf(w[8 * stride], c[m + 1], acc);
   return acc;
 }
 
-// Down and up sweeps from level l0 with r_{l0} already in shared memory; leaves e_{l0}.
-// Loops run warp-per-row, lane-per-column (no integer division); the coarsest level is one
-// FP64 product with the precomputed inverse of A_L (one thread per unknown).
-#define TAIL_FOR(nside) \
+// interior points of level side n, warp per row and lane per column (no integer division)
+#define TAIL_FOR(nside)                          \
   for (int i = warp; i < (nside); i += nwarps) \
     for (int j = lane; j < (nside); j += 32)
 
+// Down and up sweeps from level l0 with r_{l0} already in shared memory; leaves e_{l0}.
+// The coarsest level is one FP64 product with the precomputed inverse of A_L.
 template <int SK, int HK>
-__device__ void tail_cycle(const ProbDev& P, float* sm, const TailLayout& lay, const float (*sc)[9], int l0,
-                           int L, float omega) {
+__device__ void tail_cycle(const ProbDev& P, float* sm, const TailLayout& lay, const float (*sc)[9],
+                           const float (*wi)[9], int l0, int L, float omega) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   for (int l = l0; l < L - 1; ++l) {
     const LevelDev& Lv = P.lv[l];
-    const int n = Lv.n, nc = P.lv[l + 1].n;
+    const int n = Lv.n, m = n + 2, nc = P.lv[l + 1].n, mc = nc + 2;
     float* r = sm + lay.off_r[l];
     float* e = sm + lay.off_e[l];
-    float* t = sm + lay.off_t;
+    float* t = sm + lay.off_t[l];
     const float* w = sm + lay.off_w[l];
-    TAIL_FOR(n) e[i * n + j] = tail_H<SK, HK>(Lv, sc[l], w, omega, r, n, i, j);
+    TAIL_FOR(n) {
+      const int q = (i + 1) * m + j + 1;
+      e[q] = pad_H<SK, HK>(Lv, sc[l], w, wi[l], omega, r + q, m, n, i, j);
+    }
     __syncthreads();
-    TAIL_FOR(n) t[i * n + j] = r[i * n + j] - tail_A<SK>(Lv, sc[l], e, n, i, j);
+    TAIL_FOR(n) {
+      const int q = (i + 1) * m + j + 1;
+      t[q] = r[q] - pad_A<SK>(Lv, sc[l], e + q, m, n, i, j);
+    }
     __syncthreads();
     float* rc = sm + lay.off_r[l + 1];
     for (int I = warp; I < nc; I += nwarps)
-      for (int J = lane; J < nc; J += 32) rc[I * nc + J] = restrict_at(t + (2 * I + 1) * n + 2 * J + 1, n);
+      for (int J = lane; J < nc; J += 32) rc[(I + 1) * mc + J + 1] = restrict_at(t + (2 * I + 2) * m + 2 * J + 2, m);
     __syncthreads();
   }
   {
+    const int nL = P.lv[L - 1].n, mL = nL + 2, mm = P.m;
     const float* r = sm + lay.off_r[L - 1];
     float* e = sm + lay.off_e[L - 1];
-    const int m = P.m;
-    if ((int)threadIdx.x < m) {
-      const double* Ai = P.chol + threadIdx.x * m;
+    if ((int)threadIdx.x < mm) {
+      const double* Ai = P.chol + threadIdx.x * mm;
       double acc = 0.0;
-      for (int k = 0; k < m; ++k) acc = fma(Ai[k], (double)r[k], acc);
-      e[threadIdx.x] = (float)acc;
+      for (int k = 0; k < mm; ++k) acc = fma(Ai[k], (double)r[(k / nL + 1) * mL + k % nL + 1], acc);
+      e[(threadIdx.x / nL + 1) * mL + threadIdx.x % nL + 1] = (float)acc;
     }
     __syncthreads();
   }
   for (int l = L - 2; l >= l0; --l) {
     const LevelDev& Lv = P.lv[l];
-    const int n = Lv.n, nc = P.lv[l + 1].n;
+    const int n = Lv.n, m = n + 2, mc = P.lv[l + 1].n + 2;
     float* r = sm + lay.off_r[l];
     float* e = sm + lay.off_e[l];
-    float* t = sm + lay.off_t;
+    float* t = sm + lay.off_t[l];
     const float* ec = sm + lay.off_e[l + 1];
     const float* w = sm + lay.off_w[l];
+    TAIL_FOR(n) e[(i + 1) * m + j + 1] += prolong_at(i, j, ec, -1, -1, mc);
+    __syncthreads();
     TAIL_FOR(n) {
-      float v = 0.f;
-      for (int di = -1; di <= 1; ++di)
-        for (int dj = -1; dj <= 1; ++dj) {
-          const int fi = i + di, fj = j + dj;  // candidate coarse centre 2I+1
-          if ((fi & 1) && (fj & 1)) {
-            const int I = (fi - 1) >> 1, J = (fj - 1) >> 1;
-            if (in_grid(I, J, nc)) v += (di ? 0.5f : 1.f) * (dj ? 0.5f : 1.f) * ec[I * nc + J];
-          }
-        }
-      e[i * n + j] += v;
+      const int q = (i + 1) * m + j + 1;
+      t[q] = r[q] - pad_A<SK>(Lv, sc[l], e + q, m, n, i, j);
     }
     __syncthreads();
-    TAIL_FOR(n) t[i * n + j] = r[i * n + j] - tail_A<SK>(Lv, sc[l], e, n, i, j);
-    __syncthreads();
-    TAIL_FOR(n) e[i * n + j] += tail_H<SK, HK>(Lv, sc[l], w, omega, t, n, i, j);
+    TAIL_FOR(n) {
+      const int q = (i + 1) * m + j + 1;
+      e[q] += pad_H<SK, HK>(Lv, sc[l], w, wi[l], omega, t + q, m, n, i, j);
+    }
     __syncthreads();
   }
 }
 
+// Zero rings, stencil constants, class tables and interior kernels of levels l0 .. L-1.
 template <int SK, int HK>
-__device__ void tail_prologue(const ProbDev& P, float* sm, const TailLayout& lay, float (*sc)[9], int l0, int L) {
+__device__ void tail_prologue(const ProbDev& P, float* sm, const TailLayout& lay, float (*sc)[9], float (*wi)[9],
+                              int l0, int L) {
   for (int l = l0; l < L; ++l) {
+    const int m = P.lv[l].n + 2;
+    const int offs[3] = {lay.off_r[l], lay.off_e[l], lay.off_t[l]};
+    for (int a = 0; a < 3; ++a) {
+      float* v = sm + offs[a];
+      for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        v[k] = 0.f;
+        v[(m - 1) * m + k] = 0.f;
+        v[k * m] = 0.f;
+        v[k * m + m - 1] = 0.f;
+      }
+    }
     if (SK == SK_CONST && threadIdx.x < 9) sc[l][threadIdx.x] = P.lv[l].s[threadIdx.x];
     if (HK == HK_TABLE && l < L - 1) {
-      const int cnt = 9 * P.lv[l].T * P.lv[l].T;
+      const int T = P.lv[l].T;
+      const int cnt = 9 * T * T;
       for (int t = threadIdx.x; t < cnt; t += blockDim.x) sm[lay.off_w[l] + t] = P.lv[l].W[t];
+      if (threadIdx.x < 9 && T == MG_PROXY) {
+        const int M = MG_NET_MARGIN;
+        wi[l][threadIdx.x] = P.lv[l].W[threadIdx.x * T * T + M * T + M];
+      }
     }
   }
 }
@@ -208,27 +257,28 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail(const ProbDev* __restrict
                                                        float omega, const int* __restrict__ act) {
   extern __shared__ float sm[];
   __shared__ float sc[MG_MAXL][9];
+  __shared__ float wi[MG_MAXL][9];
+  __shared__ TailLayout lay;
   pdl_trigger();
   const int p = act ? act[blockIdx.x] : blockIdx.x;
   const ProbDev& P = probs[p];
-  __shared__ TailLayout lay;
   if (threadIdx.x == 0) {
     int nl[MG_MAXL];
     for (int l = 0; l < L; ++l) nl[l] = P.lv[l].n;
     tail_layout(nl, l0, L, HK, lay);
   }
   __syncthreads();
-  tail_prologue<SK, HK>(P, sm, lay, sc, l0, L);
+  tail_prologue<SK, HK>(P, sm, lay, sc, wi, l0, L);
   pdl_wait();
   if (!state[p].active) return;
-  const int n = P.lv[l0].n;
+  const int n = P.lv[l0].n, m = n + 2, pitch = P.lv[l0].pitch;
   float* r = sm + lay.off_r[l0];
-  const int pitch = P.lv[l0].pitch;
-  for (int q = threadIdx.x; q < n * n; q += blockDim.x) r[q] = P.lv[l0].r[(q / n) * pitch + q % n];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  TAIL_FOR(n) r[(i + 1) * m + j + 1] = P.lv[l0].r[(size_t)i * pitch + j];
   __syncthreads();
-  tail_cycle<SK, HK>(P, sm, lay, sc, l0, L, omega);
+  tail_cycle<SK, HK>(P, sm, lay, sc, wi, l0, L, omega);
   const float* e = sm + lay.off_e[l0];
-  for (int q = threadIdx.x; q < n * n; q += blockDim.x) P.lv[l0].e[(q / n) * pitch + q % n] = e[q];
+  TAIL_FOR(n) P.lv[l0].e[(size_t)i * pitch + j] = e[(i + 1) * m + j + 1];
 }
 
 // Whole solves of small problems: up to `budget` iterations of (residual, test, V-cycle,
@@ -242,34 +292,36 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_solve(const ProbDev* __re
                                                              const int* __restrict__ act) {
   extern __shared__ float sm[];
   __shared__ float sc[MG_MAXL][9];
+  __shared__ float wi[MG_MAXL][9];
   __shared__ float wh[TAIL_THREADS / 32], wl[TAIL_THREADS / 32];
+  __shared__ TailLayout lay;
   __shared__ int go;
   const int p = act ? act[blockIdx.x] : blockIdx.x;
   if (!state[p].active) return;
   const ProbDev& P = probs[p];
-  __shared__ TailLayout lay;
   if (threadIdx.x == 0) {
     int nl[MG_MAXL];
     for (int l = 0; l < L; ++l) nl[l] = P.lv[l].n;
     tail_layout(nl, 0, L, HK, lay);
   }
   __syncthreads();
-  tail_prologue<SK, HK>(P, sm, lay, sc, 0, L);
+  tail_prologue<SK, HK>(P, sm, lay, sc, wi, 0, L);
   const LevelDev& L0 = P.lv[0];
-  const int n = L0.n;
+  const int n = L0.n, m = n + 2;
   const size_t nn = (size_t)n * n;
   const float* bp = b + p * nn;
   float* xh = xhi + p * nn;
   float* xl = xlo ? xlo + p * nn : nullptr;
   float* r = sm + lay.off_r[0];
   const float* e = sm + lay.off_e[0];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   __syncthreads();
   for (int it = 0; it <= budget; ++it) {
     if (it == budget && !final_residual) break;
     // residual of the current iterate (compensated), its norm and the stopping test
     float acc = 0.f;
-    for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
-      const int i = q / n, j = q % n;
+    TAIL_FOR(n) {
+      const int q = i * n + j;
       float hi = bp[q], lo = 0.f;
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
@@ -285,32 +337,37 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_solve(const ProbDev* __re
         if (xl) lo = fmaf(-a, xl[ii * n + jj], lo);
       }
       const float rv = hi + lo;
-      r[q] = rv;
+      r[(i + 1) * m + j + 1] = rv;
       acc = fmaf(rv, rv, acc);
     }
     acc = warp_sum(acc);
-    if ((threadIdx.x & 31) == 0) { wh[threadIdx.x >> 5] = acc; wl[threadIdx.x >> 5] = 0.f; }
+    if (lane == 0) {
+      wh[warp] = acc;
+      wl[warp] = 0.f;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
       float hi = 0.f, lo = 0.f;
-      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) ff_add(hi, lo, wh[k], wl[k]);
+      for (int k = 0; k < nwarps; ++k) ff_add(hi, lo, wh[k], wl[k]);
       decide(state[p], hi, lo, rtol, max_cycles);
       go = state[p].active && it < budget;
     }
     __syncthreads();
     if (!go) break;
-    tail_cycle<SK, HK>(P, sm, lay, sc, 0, L, omega);
+    tail_cycle<SK, HK>(P, sm, lay, sc, wi, 0, L, omega);
     // x += e_0 (float-float)
-    for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
+    TAIL_FOR(n) {
+      const int q = i * n + j;
+      const float ev = e[(i + 1) * m + j + 1];
       if (xl) {
         float hi = xh[q], lo = xl[q], sum, err;
-        two_sum(hi, e[q], sum, err);
+        two_sum(hi, ev, sum, err);
         err += lo;
         fast_two_sum(sum, err, hi, lo);
         xh[q] = hi;
         xl[q] = lo;
       } else {
-        xh[q] += e[q];
+        xh[q] += ev;
       }
     }
     __syncthreads();
@@ -318,7 +375,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_solve(const ProbDev* __re
 }
 
 // ------------------------------------------------------- standalone smoother
-// t = f - A u into the level's r vector (one thread per point)
+// t = f - A u into the level's r vector (dense scratch, one thread per point)
 template <int SK>
 __global__ void k_level_residual(const ProbDev* __restrict__ probs, int p, int l, const float* __restrict__ f,
                                  const float* __restrict__ u) {
@@ -348,7 +405,23 @@ __global__ void k_level_smooth(const ProbDev* __restrict__ probs, int p, int l, 
   if (q >= n * n) return;
   float s[9];
   load_stencil<SK>(L, s);
-  u[q] += tail_H<SK, HK>(L, s, L.W, omega, L.r, n, q / n, q % n);
+  const int i = q / n, j = q % n;
+  const float* t = L.r;
+  if (HK == HK_JACOBI) {
+    const float d = (SK == SK_CONST) ? s[4] : L.st[4 * (size_t)n * n + q];
+    u[q] += omega * t[q] / d;
+    return;
+  }
+  float acc = 0.f;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const int ii = i + k / 3 - 1, jj = j + k % 3 - 1;
+    float w;
+    if (HK == HK_TABLE) w = L.W[k * L.T * L.T + kclass(i, n, L.T) * L.T + kclass(j, n, L.T)];
+    else w = L.W[(size_t)k * n * n + q];
+    acc = fmaf(w, in_grid(ii, jj, n) ? t[ii * n + jj] : 0.f, acc);
+  }
+  u[q] += acc;
 }
 
 // ---------------------------------------------------------------- launchers
@@ -404,8 +477,8 @@ cudaError_t launch_tail(const CycleArgs& a) {
   a.prof->begin(PK_TAIL, a.stream);
   const ProbDev* probs = a.probs;
   const ProbState* state = a.state;
-  MG_DISPATCH(a.sk, a.hk, (e = launch_pdl(a.pdl, k_tail<SK_, HK_>, dim3(nlaunch(a)), dim3(TAIL_THREADS), smem, a.stream,
-                                          probs, state, ls, L, a.omega, a.active)));
+  MG_DISPATCH(a.sk, a.hk, (e = launch_pdl(a.pdl, k_tail<SK_, HK_>, dim3(nlaunch(a)), dim3(TAIL_THREADS), smem,
+                                          a.stream, probs, state, ls, L, a.omega, a.active)));
   a.prof->end(a.stream);
   return e;
 }

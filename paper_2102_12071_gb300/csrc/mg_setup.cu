@@ -17,20 +17,19 @@ __global__ void k_varcoef5_field(int n, const float* __restrict__ cells, float* 
   float* st = field + p * field_stride;
   const int i = q / n, j = q % n, m = n + 1;
   const size_t nn = (size_t)n * n;
-  const float wE = 0.5f * (a[i * m + j + 1] + a[(i + 1) * m + j + 1]);
-  const float wW = 0.5f * (a[i * m + j] + a[(i + 1) * m + j]);
-  const float wN = 0.5f * (a[(i + 1) * m + j] + a[(i + 1) * m + j + 1]);
-  const float wS = 0.5f * (a[i * m + j] + a[i * m + j + 1]);
-  // centre = correctly rounded sum of the four weights (compensated summation)
-  float hi = wE, lo = 0.f;
-  ff_add(hi, lo, wW, 0.f);
-  ff_add(hi, lo, wN, 0.f);
-  ff_add(hi, lo, wS, 0.f);
+  // edge weights and centre in FP64 (exact for cells within a factor 2^28 of each other),
+  // each rounded once to FP32
+  const double dE = 0.5 * ((double)a[i * m + j + 1] + (double)a[(i + 1) * m + j + 1]);
+  const double dW = 0.5 * ((double)a[i * m + j] + (double)a[(i + 1) * m + j]);
+  const double dN = 0.5 * ((double)a[(i + 1) * m + j] + (double)a[(i + 1) * m + j + 1]);
+  const double dS = 0.5 * ((double)a[i * m + j] + (double)a[i * m + j + 1]);
+  const float wE = (float)dE, wW = (float)dW, wN = (float)dN, wS = (float)dS;
+  const float centre = (float)(dE + dW + dN + dS);
   st[0 * nn + q] = 0.f;
   st[1 * nn + q] = i > 0 ? -wS : 0.f;
   st[2 * nn + q] = 0.f;
   st[3 * nn + q] = j > 0 ? -wW : 0.f;
-  st[4 * nn + q] = hi + lo;
+  st[4 * nn + q] = centre;
   st[5 * nn + q] = j + 1 < n ? -wE : 0.f;
   st[6 * nn + q] = 0.f;
   st[7 * nn + q] = i + 1 < n ? -wN : 0.f;

@@ -7,8 +7,8 @@
 // multiple of 32 floats (128-byte rows) and all problems of a level are one 3-D tensor
 // {x, y, problem}, so one tensor map serves the whole batch.
 //   k_residual  r = b - A (x_hi + x_lo), compensated (float-float), ||r||^2, stopping test
-//   k_down(l)   e = H r, s = r - A e, r_{l+1} = P^T s         (Algorithm 1 lines 1-2)
-//   k_up(l)     e1 = e + P e_{l+1}, e = e1 + H (r - A e1)      (Algorithm 1 lines 8-9);
+//   k_down(l)   e = H r, s = r - A e, r_{l+1} = P^T s         (Algorithm 1, pre-smoothing and restriction)
+//   k_up(l)     e1 = e + P e_{l+1}, e = e1 + H (r - A e1)      (Algorithm 1, correction and post-smoothing);
 //               on level 0 the correction is added to the float-float iterate.
 #include <cudaTypedefs.h>
 
@@ -188,10 +188,9 @@ __global__ void __launch_bounds__(NT) k_down(const __grid_constant__ CUtensorMap
   }
   __syncthreads();
   if (!tile_wait(&bar, state[p])) return;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // pre-smoothing from zero: e = H r on rows/cols R0-1 .. R0+33
-  for (int ti = warp; ti < ES_DN; ti += NW)
-    for (int tj = lane; tj < ES_DN; tj += 32) {
+  for (int t = threadIdx.x; t < ES_DN * ES_DN; t += NT) {
+      const int ti = t / ES_DN, tj = t - ti * ES_DN;
       const int i = R0 - 1 + ti, j = C0 - 1 + tj;
       float v = 0.f;
       if (in_grid(i, j, n)) {
@@ -202,8 +201,8 @@ __global__ void __launch_bounds__(NT) k_down(const __grid_constant__ CUtensorMap
     }
   __syncthreads();
   // s = r - A e on rows/cols R0 .. R0+32, written over r
-  for (int ti = warp; ti <= TB; ti += NW)
-    for (int tj = lane; tj <= TB; tj += 32) {
+  for (int t = threadIdx.x; t < (TB + 1) * (TB + 1); t += NT) {
+      const int ti = t / (TB + 1), tj = t - ti * (TB + 1);
       const int i = R0 + ti, j = C0 + tj;
       float* rp = rs + (ti + 2) * XW + tj + 4;
       float v = 0.f;
@@ -263,16 +262,16 @@ __global__ void __launch_bounds__(NT) k_up(const __grid_constant__ UpMaps M, con
   (void)nc;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // e1 = e + P e_c on rows/cols R0-2 .. R0+33 (zero outside the grid)
-  for (int ti = warp; ti < TB + 4; ti += NW)
-    for (int tj = lane; tj < TB + 4; tj += 32) {
+  for (int t = threadIdx.x; t < (TB + 4) * (TB + 4); t += NT) {
+      const int ti = t / (TB + 4), tj = t - ti * (TB + 4);
       const int i = R0 - 2 + ti, j = C0 - 2 + tj;
       float* ep = es + ti * XW + tj + 2;
       *ep = in_grid(i, j, n) ? *ep + prolong_at(i, j, ecs, I0, J0, EC_W) : 0.f;
     }
   __syncthreads();
   // t = r - A e1 on rows/cols R0-1 .. R0+32
-  for (int ti = warp; ti < TB + 2; ti += NW)
-    for (int tj = lane; tj < TB + 2; tj += 32) {
+  for (int t = threadIdx.x; t < (TB + 2) * (TB + 2); t += NT) {
+      const int ti = t / (TB + 2), tj = t - ti * (TB + 2);
       const int i = R0 - 1 + ti, j = C0 - 1 + tj;
       float* rp = rs + ti * XW + tj + 3;
       *rp = in_grid(i, j, n) ? *rp - stencil_apply<SK>(L, s, i, j, es + (ti + 1) * XW + tj + 3, XW) : 0.f;

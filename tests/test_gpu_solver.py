@@ -89,7 +89,7 @@ def test_c1_jacobi_solve_matches_oracle(n):
         assert abs(fg - fo) <= 1e-3 * fo
 
 
-@pytest.mark.parametrize("n,cycles", [(255, 60), (1023, 4)])
+@pytest.mark.parametrize("n,cycles", [(127, 40), (255, 60), (1023, 4)])
 def test_large_grid_jacobi_history_matches_oracle(n, cycles):
     """Tiled kernels (k_residual/k_down/k_up) plus the one-CTA tail; 1023 is the bench size."""
     eps, theta = 0.05, 1.1
@@ -180,3 +180,34 @@ def test_warm_start_continues_history():
     xh, xl, _, _, _ = mg.solve(b, rtol=0, max_cycles=10)
     _, _, h10, _, _ = mg.solve(b, xh, xl, rtol=0, max_cycles=10)
     np.testing.assert_allclose(h10[0][1:], h20[0][11:], rtol=1e-6)
+
+
+def test_varcoef_field_path_at_bench_size_matches_oracle():
+    """Per-point (variable-coefficient) stencils at 1023 x 1023 with the tiled kernels:
+    stencil field of level 0 bit-exact and the first cycles of the history."""
+    n, cycles = 1023, 3
+    a = inputs.grf_cells(inputs.SEED_GRF, n)
+    mg = S.MultigridSolver([S.varcoef5(n, torch.from_numpy(a).cuda())])
+    st0 = O.varcoef5_field(n, f32(a))
+    np.testing.assert_array_equal(mg.stencil_field(0, 0).double().cpu().numpy(), f32(st0))
+    b = inputs.rhs_uniform(9, n)
+    _, _, gh, cyc, _ = mg.solve(torch.from_numpy(b).cuda()[None].contiguous(), rtol=0.0, max_cycles=cycles)
+    _, oh = O.Multigrid(f32(st0)).solve(f32(b), rtol=0.0, max_cycles=cycles)
+    assert _cmp_hist(gh[0], oh) == cycles + 1
+
+
+def test_vcycle_without_low_part_on_tiled_path():
+    """x_lo = NULL: the iterate is plain FP32 (the low part is taken as zero, not returned)."""
+    n = 255
+    rng = np.random.default_rng(12)
+    b = rng.uniform(-1, 1, (n, n)).astype(np.float32)
+    mg = S.MultigridSolver([S.rotated(n, 0.3, 0.9)])
+    xh = torch.zeros((1, n, n), device="cuda")
+    rel = torch.zeros(1, device="cuda")
+    for _ in range(3):
+        mg.vcycle(torch.from_numpy(b).cuda()[None].contiguous(), xh, None, rel)
+    om = O.Multigrid(oracle_rotated(n, 0.3, 0.9))
+    x = np.zeros((n, n))
+    for _ in range(3):
+        x = om.vcycle(f32(b), x)
+    assert np.abs(xh[0].double().cpu().numpy() - x).max() <= 1e-5 * np.abs(x).max()
