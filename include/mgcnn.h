@@ -90,6 +90,12 @@ typedef struct {
   int coarsest_n;   /* stop coarsening at this size (this build: 3)                  */
   int conv_bf16;    /* 1: network weights and activations rounded to bfloat16, FP32
                        accumulation; 0: FP32 throughout                                 */
+  int cluster_tail; /* 1: the levels of side <= 127 below the finest run in one cluster of
+                       8 CTAs per problem with every vector in shared memory, where the
+                       device can hold such a cluster; 0: the levels of side <= 63 run in
+                       one CTA per problem and the levels above in tiled kernels.  Both
+                       compute the same cycle; the choice only changes how it is laid out
+                       on the GPU.  Problems of side <= 63 always run in one CTA each.   */
 } mg_options;
 
 typedef struct mg_ctx mg_ctx;

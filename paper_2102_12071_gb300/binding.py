@@ -25,7 +25,8 @@ class mg_problem(ctypes.Structure):
 
 class mg_options(ctypes.Structure):
     _fields_ = [("smoother", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
-                ("omega", ctypes.c_float), ("coarsest_n", ctypes.c_int), ("conv_bf16", ctypes.c_int)]
+                ("omega", ctypes.c_float), ("coarsest_n", ctypes.c_int), ("conv_bf16", ctypes.c_int),
+                ("cluster_tail", ctypes.c_int)]
 
 
 class MGError(RuntimeError):
@@ -127,8 +128,8 @@ def problems_array(problems: list[dict]):
 
 
 def options(smoother: int = MG_SMOOTH_JACOBI, omega: float = 2.0 / 3.0, coarsest_n: int = 3,
-            conv_bf16: int = 0) -> mg_options:
-    return mg_options(smoother, 1, 1, omega, coarsest_n, conv_bf16)
+            conv_bf16: int = 0, cluster_tail: int = 1) -> mg_options:
+    return mg_options(smoother, 1, 1, omega, coarsest_n, conv_bf16, cluster_tail)
 
 
 def mg_workspace_size(probs, nprob: int, opts: mg_options) -> int:

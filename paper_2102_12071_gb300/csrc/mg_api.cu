@@ -45,6 +45,8 @@ namespace {
 
 struct Plan {
   int nprob = 0, n0 = 0, L = 0, lstar = 0, sk = SK_CONST, hk = HK_JACOBI, tail_solve = 0;
+  int ctail = 0;    // levels >= lstar in one CTA cluster per problem
+  int lstar1 = 0;   // first level of the one-CTA tail (the fallback of the cluster tail)
   int nl[MG_MAXL] = {0};
   int ntiles_max = 0;
   size_t bytes = 0;
@@ -100,11 +102,20 @@ mg_status make_plan(const mg_problem* probs, int nprob, const mg_options* o, Pla
   P.L = L;
   P.lstar = 0;
   while (P.lstar < L && P.nl[P.lstar] > MG_TAIL_N) ++P.lstar;
+  P.lstar1 = P.lstar;
   P.tail_solve = P.lstar == 0;
   const int nt = tiles_per_side(n);
   P.ntiles_max = nt * nt;
   if (tail_smem_bytes(P.nl, P.lstar, L, P.hk) > MG_TAIL_SMEM_MAX)
     return fail(MG_ERR_UNSUPPORTED, "tail does not fit in shared memory");
+  if (!P.tail_solve && o->cluster_tail) {
+    int ls = 1;  // the finest level stays tiled: it carries the outer residual and update
+    while (ls < L && P.nl[ls] > MG_CT_N) ++ls;
+    if (ls < L && P.nl[ls] > MG_CT_SOLO && ctail_smem_bytes(P.nl, ls, L, P.hk) <= MG_CT_SMEM_MAX) {
+      P.lstar = ls;
+      P.ctail = 1;
+    }
+  }
   return MG_OK;
 }
 
@@ -137,7 +148,7 @@ struct mg_ctx {
   LevelArrays arrays;
   TileMaps maps;
   Profiler prof;
-  // one captured V-cycle (residual + every level kernel) per compacted launch size
+  // captured cycles (residual + every level kernel) per compacted launch size
   struct CycleGraph {
     int nactive, max_cycles;
     float rtol;
@@ -152,8 +163,11 @@ struct mg_ctx {
   }
 };
 
-// The executable graph of one cycle for the current launch size, captured on a private
-// stream the first time it is needed and replayed on the caller's stream afterwards.
+// cycles per executable graph; every chunk of the solve loop is a multiple of it
+constexpr int kGraphCycles = 16;
+
+// The executable graph of kGraphCycles cycles for the current launch size, captured on a
+// private stream the first time it is needed and replayed on the caller's stream afterwards.
 static mg_status cycle_graph(mg_ctx* ctx, const CycleArgs& a, float rtol, int max_cycles, cudaGraphExec_t* out,
                              long long* nodes) {
   const int nact = a.active ? a.nactive : 0;
@@ -170,8 +184,11 @@ static mg_status cycle_graph(mg_ctx* ctx, const CycleArgs& a, float rtol, int ma
   c.pdl = true;
   const long long before = ctx->prof.launches;
   CK(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e1 = launch_residual(c, rtol, max_cycles);
-  cudaError_t e2 = e1 == cudaSuccess ? launch_cycle(c) : e1;
+  cudaError_t e2 = cudaSuccess;
+  for (int k = 0; k < kGraphCycles && e2 == cudaSuccess; ++k) {
+    e2 = launch_residual(c, rtol, max_cycles);
+    if (e2 == cudaSuccess) e2 = launch_cycle(c);
+  }
   cudaGraph_t graph = nullptr;
   cudaError_t e3 = cudaStreamEndCapture(c.stream, &graph);
   if (e2 != cudaSuccess || e3 != cudaSuccess) {
@@ -305,6 +322,10 @@ mg_status mg_setup(const mg_problem* problems, int nprob, const mg_options* opts
   if (!workspace || ws_bytes < need) return fail(MG_ERR_WORKSPACE, "workspace needs %zu bytes, got %zu", need, ws_bytes);
   if (((uintptr_t)workspace & 255) != 0) return fail(MG_ERR_WORKSPACE, "workspace must be 256-byte aligned");
   cudaStream_t s = (cudaStream_t)stream;
+  if (P.ctail && !ctail_supported(P.sk, P.hk, ctail_smem_bytes(P.nl, P.lstar, P.L, P.hk))) {
+    P.ctail = 0;  // the device cannot hold the cluster: one CTA per problem below MG_TAIL_N
+    P.lstar = P.lstar1;
+  }
   mg_ctx* ctx = new mg_ctx();
   ctx->plan = P;
   ctx->opts = *opts;
@@ -315,6 +336,7 @@ mg_status mg_setup(const mg_problem* problems, int nprob, const mg_options* opts
   a.n0 = P.n0;
   a.L = P.L;
   a.lstar = P.lstar;
+  a.ctail = P.ctail;
   for (int l = 0; l < MG_MAXL; ++l) a.nl[l] = P.nl[l];
   a.sk = P.sk;
   a.hk = P.hk;
@@ -492,8 +514,8 @@ mg_status mg_solve(mg_ctx* ctx, const float* b, float* x_hi, float* x_lo, double
       long long nodes = 0;
       mg_status gs = cycle_graph(ctx, a, frtol, max_cycles, &exec, &nodes);
       if (gs != MG_OK) return gs;
-      for (int c = 0; c < G; ++c) CK(cudaGraphLaunch(exec, a.stream));
-      ctx->prof.launches += nodes * G;
+      for (int c = 0; c < G; c += kGraphCycles) CK(cudaGraphLaunch(exec, a.stream));
+      ctx->prof.launches += nodes * (G / kGraphCycles);
     }
     CK(cudaMemcpyAsync(ctx->h_state.data(), a.state, sizeof(ProbState) * P.nprob, cudaMemcpyDeviceToHost, a.stream));
     CK(cudaStreamSynchronize(a.stream));

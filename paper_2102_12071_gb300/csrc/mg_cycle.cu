@@ -16,6 +16,7 @@
 #include "mg_internal.h"
 #include "mg_ops.cuh"
 #include "mg_reduce.cuh"
+#include "mg_tail.cuh"
 #include "mg_tma.cuh"
 
 namespace mg {
@@ -64,193 +65,6 @@ __global__ void __launch_bounds__(NT) k_bnorm(const ProbDev* __restrict__ probs,
 }
 
 // ------------------------------------------------------------------ tail
-// Levels l0 .. L-1 of one problem in one CTA with every vector in shared memory.  Each
-// level vector is stored with a one-point ring of zeros (side n+2), so stencil, smoother
-// and transfer taps need no bounds checks: the ring is the Dirichlet exterior.
-struct TailLayout {
-  int off_r[MG_MAXL], off_e[MG_MAXL], off_t[MG_MAXL], off_w[MG_MAXL];
-  int total;
-};
-
-__host__ __device__ inline void tail_layout(const int* nl, int l0, int L, int hk, TailLayout& t) {
-  int o = 0;
-  for (int l = l0; l < L; ++l) {
-    const int m = nl[l] + 2;
-    t.off_r[l] = o; o += m * m;
-    t.off_e[l] = o; o += m * m;
-    t.off_t[l] = o; o += m * m;
-  }
-  for (int l = l0; l < L; ++l) {
-    t.off_w[l] = o;
-    if (hk == HK_TABLE && l < L - 1) {
-      const int T = nl[l] < MG_PROXY ? nl[l] : MG_PROXY;
-      o += 9 * T * T;
-    }
-  }
-  t.total = o;
-}
-
-// A v at (i, j); c points at v(i, j) inside a ring-padded array of row stride m
-template <int SK>
-__device__ __forceinline__ float pad_A(const LevelDev& L, const float* s, const float* c, int m, int n, int i, int j) {
-  if (SK == SK_CONST) {
-    float acc = s[4] * c[0];
-    acc = fmaf(s[0], c[-m - 1], acc);
-    acc = fmaf(s[1], c[-m], acc);
-    acc = fmaf(s[2], c[-m + 1], acc);
-    acc = fmaf(s[3], c[-1], acc);
-    acc = fmaf(s[5], c[1], acc);
-    acc = fmaf(s[6], c[m - 1], acc);
-    acc = fmaf(s[7], c[m], acc);
-    acc = fmaf(s[8], c[m + 1], acc);
-    return acc;
-  }
-  const size_t nn = (size_t)n * n;
-  const float* a = L.st + (size_t)i * n + j;
-  float acc = __ldg(a + 4 * nn) * c[0];
-  acc = fmaf(__ldg(a), c[-m - 1], acc);
-  acc = fmaf(__ldg(a + nn), c[-m], acc);
-  acc = fmaf(__ldg(a + 2 * nn), c[-m + 1], acc);
-  acc = fmaf(__ldg(a + 3 * nn), c[-1], acc);
-  acc = fmaf(__ldg(a + 5 * nn), c[1], acc);
-  acc = fmaf(__ldg(a + 6 * nn), c[m - 1], acc);
-  acc = fmaf(__ldg(a + 7 * nn), c[m], acc);
-  acc = fmaf(__ldg(a + 8 * nn), c[m + 1], acc);
-  return acc;
-}
-
-// H v at (i, j) on a ring-padded array; wi holds the interior network kernel of the level
-template <int SK, int HK>
-__device__ __forceinline__ float pad_H(const LevelDev& L, const float* s, const float* wtab, const float* wi,
-                                       float omega, const float* c, int m, int n, int i, int j) {
-  if (HK == HK_JACOBI) {
-    const float d = (SK == SK_CONST) ? s[4] : __ldg(L.st + 4 * (size_t)n * n + (size_t)i * n + j);
-    return omega * c[0] / d;
-  }
-  const float* w;
-  int stride;
-  if (HK == HK_TABLE) {
-    const int T = L.T, M = MG_NET_MARGIN;
-    if (T == MG_PROXY && i >= M && i < n - M && j >= M && j < n - M) {
-      w = wi;
-      stride = 1;
-    } else {
-      w = wtab + kclass(i, n, T) * T + kclass(j, n, T);
-      stride = T * T;
-    }
-  } else {
-    w = L.W + (size_t)i * n + j;
-    stride = n * n;
-  }
-  float acc = w[4 * stride] * c[0];
-  acc = fmaf(w[0], c[-m - 1], acc);
-  acc = fmaf(w[stride], c[-m], acc);
-  acc = fmaf(w[2 * stride], c[-m + 1], acc);
-  acc = fmaf(w[3 * stride], c[-1], acc);
-  acc = fmaf(w[5 * stride], c[1], acc);
-  acc = fmaf(w[6 * stride], c[m - 1], acc);
-  acc = fmaf(w[7 * stride], c[m], acc);
-  acc = fmaf(w[8 * stride], c[m + 1], acc);
-  return acc;
-}
-
-// interior points of level side n, warp per row and lane per column (no integer division)
-#define TAIL_FOR(nside)                          \
-  for (int i = warp; i < (nside); i += nwarps) \
-    for (int j = lane; j < (nside); j += 32)
-
-// Down and up sweeps from level l0 with r_{l0} already in shared memory; leaves e_{l0}.
-// The coarsest level is one FP64 product with the precomputed inverse of A_L.
-template <int SK, int HK>
-__device__ void tail_cycle(const ProbDev& P, float* sm, const TailLayout& lay, const float (*sc)[9],
-                           const float (*wi)[9], int l0, int L, float omega) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  for (int l = l0; l < L - 1; ++l) {
-    const LevelDev& Lv = P.lv[l];
-    const int n = Lv.n, m = n + 2, nc = P.lv[l + 1].n, mc = nc + 2;
-    float* r = sm + lay.off_r[l];
-    float* e = sm + lay.off_e[l];
-    float* t = sm + lay.off_t[l];
-    const float* w = sm + lay.off_w[l];
-    TAIL_FOR(n) {
-      const int q = (i + 1) * m + j + 1;
-      e[q] = pad_H<SK, HK>(Lv, sc[l], w, wi[l], omega, r + q, m, n, i, j);
-    }
-    __syncthreads();
-    TAIL_FOR(n) {
-      const int q = (i + 1) * m + j + 1;
-      t[q] = r[q] - pad_A<SK>(Lv, sc[l], e + q, m, n, i, j);
-    }
-    __syncthreads();
-    float* rc = sm + lay.off_r[l + 1];
-    for (int I = warp; I < nc; I += nwarps)
-      for (int J = lane; J < nc; J += 32) rc[(I + 1) * mc + J + 1] = restrict_at(t + (2 * I + 2) * m + 2 * J + 2, m);
-    __syncthreads();
-  }
-  {
-    const int nL = P.lv[L - 1].n, mL = nL + 2, mm = P.m;
-    const float* r = sm + lay.off_r[L - 1];
-    float* e = sm + lay.off_e[L - 1];
-    if ((int)threadIdx.x < mm) {
-      const double* Ai = P.chol + threadIdx.x * mm;
-      double acc = 0.0;
-      for (int k = 0; k < mm; ++k) acc = fma(Ai[k], (double)r[(k / nL + 1) * mL + k % nL + 1], acc);
-      e[(threadIdx.x / nL + 1) * mL + threadIdx.x % nL + 1] = (float)acc;
-    }
-    __syncthreads();
-  }
-  for (int l = L - 2; l >= l0; --l) {
-    const LevelDev& Lv = P.lv[l];
-    const int n = Lv.n, m = n + 2, mc = P.lv[l + 1].n + 2;
-    float* r = sm + lay.off_r[l];
-    float* e = sm + lay.off_e[l];
-    float* t = sm + lay.off_t[l];
-    const float* ec = sm + lay.off_e[l + 1];
-    const float* w = sm + lay.off_w[l];
-    TAIL_FOR(n) e[(i + 1) * m + j + 1] += prolong_at(i, j, ec, -1, -1, mc);
-    __syncthreads();
-    TAIL_FOR(n) {
-      const int q = (i + 1) * m + j + 1;
-      t[q] = r[q] - pad_A<SK>(Lv, sc[l], e + q, m, n, i, j);
-    }
-    __syncthreads();
-    TAIL_FOR(n) {
-      const int q = (i + 1) * m + j + 1;
-      e[q] += pad_H<SK, HK>(Lv, sc[l], w, wi[l], omega, t + q, m, n, i, j);
-    }
-    __syncthreads();
-  }
-}
-
-// Zero rings, stencil constants, class tables and interior kernels of levels l0 .. L-1.
-template <int SK, int HK>
-__device__ void tail_prologue(const ProbDev& P, float* sm, const TailLayout& lay, float (*sc)[9], float (*wi)[9],
-                              int l0, int L) {
-  for (int l = l0; l < L; ++l) {
-    const int m = P.lv[l].n + 2;
-    const int offs[3] = {lay.off_r[l], lay.off_e[l], lay.off_t[l]};
-    for (int a = 0; a < 3; ++a) {
-      float* v = sm + offs[a];
-      for (int k = threadIdx.x; k < m; k += blockDim.x) {
-        v[k] = 0.f;
-        v[(m - 1) * m + k] = 0.f;
-        v[k * m] = 0.f;
-        v[k * m + m - 1] = 0.f;
-      }
-    }
-    if (SK == SK_CONST && threadIdx.x < 9) sc[l][threadIdx.x] = P.lv[l].s[threadIdx.x];
-    if (HK == HK_TABLE && l < L - 1) {
-      const int T = P.lv[l].T;
-      const int cnt = 9 * T * T;
-      for (int t = threadIdx.x; t < cnt; t += blockDim.x) sm[lay.off_w[l] + t] = P.lv[l].W[t];
-      if (threadIdx.x < 9 && T == MG_PROXY) {
-        const int M = MG_NET_MARGIN;
-        wi[l][threadIdx.x] = P.lv[l].W[threadIdx.x * T * T + M * T + M];
-      }
-    }
-  }
-}
-
 template <int SK, int HK>
 __global__ void __launch_bounds__(TAIL_THREADS) k_tail(const ProbDev* __restrict__ probs,
                                                        const ProbState* __restrict__ state, int l0, int L,
@@ -409,7 +223,7 @@ __global__ void k_level_smooth(const ProbDev* __restrict__ probs, int p, int l, 
   const float* t = L.r;
   if (HK == HK_JACOBI) {
     const float d = (SK == SK_CONST) ? s[4] : L.st[4 * (size_t)n * n + q];
-    u[q] += omega * t[q] / d;
+    u[q] += (omega / d) * t[q];
     return;
   }
   float acc = 0.f;
@@ -461,6 +275,7 @@ static cudaError_t set_tail_attrs(size_t smem) {
 }
 
 cudaError_t prepare_tail(const CycleArgs& a) {
+  if (a.ctail) return prepare_ctail(a);
   const size_t smem = tail_smem_bytes(a.nl, a.lstar, a.L, a.hk);
   cudaError_t e;
   MG_DISPATCH(a.sk, a.hk, (e = set_tail_attrs<SK_, HK_>(smem)));
@@ -468,6 +283,7 @@ cudaError_t prepare_tail(const CycleArgs& a) {
 }
 
 cudaError_t launch_tail(const CycleArgs& a) {
+  if (a.ctail) return launch_ctail(a);
   const int ls = a.lstar, L = a.L;
   const size_t smem = tail_smem_bytes(a.nl, ls, L, a.hk);
   cudaError_t e;

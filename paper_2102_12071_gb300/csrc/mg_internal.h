@@ -67,12 +67,17 @@ struct Profiler {
 struct ResMaps {
   CUtensorMap xh, xl, b;
 };
+struct DownMaps {
+  CUtensorMap r;   // load: r_l with halo
+  CUtensorMap e;   // store: e_l on the tile
+  CUtensorMap rc;  // store: r_{l+1} on the coarse tile
+};
 struct UpMaps {
   CUtensorMap e, r, ec, xh, xl;
 };
 struct TileMaps {
   ResMaps res;
-  CUtensorMap down[MG_MAXL];
+  DownMaps down[MG_MAXL];
   UpMaps up[MG_MAXL];
 };
 
@@ -100,6 +105,7 @@ struct CycleArgs {
   const TileMaps* maps;  // host copy of the tensor maps (tiled levels)
   float *xh0, *xl0;      // pitched iterate pair of the tiled path
   bool pdl;              // launch the cycle chain with programmatic dependencies
+  int ctail;             // levels >= lstar in one CTA cluster per problem (mg_ctail.cu)
 };
 
 // one network evaluation: a stencil field (st) or a constant stencil (s) on an n x n grid
@@ -149,12 +155,17 @@ cudaError_t launch_cycle(const CycleArgs& a);
 bool build_tile_maps(TileMaps& maps, const LevelArrays& arrays, int nprob, int lstar);
 cudaError_t launch_pack(const float* src, float* dst, int n, int pitch, int nprob, cudaStream_t s);
 cudaError_t launch_unpack(const float* src, float* dst, int n, int pitch, int nprob, cudaStream_t s);
-// one-CTA coarse tail from level a.lstar (mg_cycle.cu); prepare_tail sets its launch
-// attributes (call it outside stream capture)
+// coarse tail from level a.lstar: one CTA per problem (mg_cycle.cu), or the cluster tail
+// when a.ctail is set; prepare_tail sets launch attributes (call it outside stream capture)
 cudaError_t launch_tail(const CycleArgs& a);
 cudaError_t prepare_tail(const CycleArgs& a);
 cudaError_t launch_tail_solve(const CycleArgs& a, const float* b, float* xhi, float* xlo, float rtol, int max_cycles,
                               int budget, int final_residual);
+// cluster tail (mg_ctail.cu): levels lstar .. L-1 in one MG_CT_C-CTA cluster per problem
+size_t ctail_smem_bytes(const int* nl, int ls, int L, int hk);
+bool ctail_supported(int sk, int hk, size_t smem);
+cudaError_t prepare_ctail(const CycleArgs& a);
+cudaError_t launch_ctail(const CycleArgs& a);
 cudaError_t launch_smoother(const CycleArgs& a, int p, int l, const float* f, float* u, int nsteps);
 
 cudaError_t launch_varcoef5(int n, int nprob, const float* cells, size_t cells_stride, float* field,

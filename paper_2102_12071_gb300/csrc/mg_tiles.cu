@@ -1,11 +1,15 @@
-// mg_tiles.cu -- the tiled level kernels of the batched V-cycle (levels n_l > MG_TAIL_N).
+// mg_tiles.cu -- the tiled level kernels of the batched V-cycle (the levels above the
+// coarse tail).
 //
 // Each CTA owns a 32 x 32 block of fine points of one problem.  All its inputs, halos
 // included, arrive as TMA bulk tensor copies issued by one thread into shared memory
 // (one mbarrier per CTA); the copy engine zero-fills everything outside the grid, which is
 // exactly the homogeneous Dirichlet exterior.  Level vectors use a row pitch that is a
 // multiple of 32 floats (128-byte rows) and all problems of a level are one 3-D tensor
-// {x, y, problem}, so one tensor map serves the whole batch.
+// {x, y, problem}, so one tensor map serves the whole batch.  Threads walk vertical strips
+// of a region with the 3x3 neighbourhood in registers (three shared-memory loads per
+// point); tiles away from the edges skip all masking, and k_down writes its outputs back
+// with TMA stores.
 //   k_residual  r = b - A (x_hi + x_lo), compensated (float-float), ||r||^2, stopping test
 //   k_down(l)   e = H r, s = r - A e, r_{l+1} = P^T s         (Algorithm 1, pre-smoothing and restriction)
 //   k_up(l)     e1 = e + P e_{l+1}, e = e1 + H (r - A e1)      (Algorithm 1, correction and post-smoothing);
@@ -25,6 +29,7 @@ namespace mg {
 constexpr int TB = 32;           // fine tile side
 constexpr int NT = 256;          // threads per CTA (8 warps)
 constexpr int NW = NT / 32;
+constexpr int TC = TB / 2;       // coarse tile side
 constexpr int XW = TB + 8;       // box width: columns C0-4 .. C0+35 (x start 16-byte aligned)
 constexpr int RES_H = TB + 2;    // k_residual x boxes: rows R0-1 .. R0+32
 constexpr int DN_H = TB + 5;     // k_down r box: rows R0-2 .. R0+34
@@ -32,50 +37,95 @@ constexpr int UPE_H = TB + 4;    // k_up e box: rows R0-2 .. R0+33
 constexpr int UPR_H = TB + 2;    // k_up r box: rows R0-1 .. R0+32
 constexpr int EC_W = TB / 2 + 8; // k_up coarse box: columns C0/2-4 .. C0/2+19
 constexpr int EC_H = TB / 2 + 3; //                  rows    R0/2-2 .. R0/2+16
-constexpr int ES_DN = TB + 3;    // k_down e buffer side (rows/cols R0-1 .. R0+33)
+constexpr int ES = TB + 3;       // k_down e buffer side (rows/cols R0-1 .. R0+33)
+// a tile is "inner" when every point its kernels evaluate lies inside the grid and at
+// least MG_NET_MARGIN from the edges: no masking, interior network kernel in registers
+constexpr int INNER = 8;
 
-template <int SK>
-__device__ __forceinline__ void load_stencil_t(const LevelDev& L, float (&s)[9]) {
-#pragma unroll
-  for (int k = 0; k < 9; ++k) s[k] = (SK == SK_CONST) ? L.s[k] : 0.f;
+__device__ __forceinline__ bool inner_tile(int R0, int C0, int n) {
+  return R0 >= INNER && C0 >= INNER && R0 + TB + INNER <= n && C0 + TB + INNER <= n;
 }
 
-// Network kernels of a constant-stencil level for one tile.  If every point within two
-// of the tile is at least MG_NET_MARGIN from the edges, all of them use the interior class
-// and the 9 taps go to registers; otherwise the whole class table is copied to shared
-// memory.  Returns true for the interior case (uniform over the CTA).
-__device__ __forceinline__ bool load_table(const LevelDev& L, int R0, int C0, float* wtab, float (&wi)[9]) {
-  const int n = L.n, T = L.T, M = MG_NET_MARGIN;
-  const bool interior = T == MG_PROXY && R0 - 2 >= M && R0 + TB + 2 <= n - 1 - M && C0 - 2 >= M &&
-                        C0 + TB + 2 <= n - 1 - M;
-  if (interior) {
+// 3x3 neighbourhood of a point in registers: rows above (a), at (b) and below (c) it,
+// columns left (0), centre (1) and right (2); tap k = 3*(di+1) + (dj+1) of a stencil
+// multiplies a0 a1 a2 b0 b1 b2 c0 c1 c2 in that order.
+struct Win {
+  float a0, a1, a2, b0, b1, b2, c0, c1, c2;
+  __device__ __forceinline__ void load_ab(const float* c, int ts) {
+    a0 = c[-ts - 1]; a1 = c[-ts]; a2 = c[-ts + 1];
+    b0 = c[-1]; b1 = c[0]; b2 = c[1];
+  }
+  __device__ __forceinline__ void load_c(const float* c, int ts) {
+    c0 = c[ts - 1]; c1 = c[ts]; c2 = c[ts + 1];
+  }
+  __device__ __forceinline__ void shift() {
+    a0 = b0; a1 = b1; a2 = b2;
+    b0 = c0; b1 = c1; b2 = c2;
+  }
+};
+
+// sum of w_k v_k, centre first (the order of stencil_apply)
+__device__ __forceinline__ float dot9(const float (&w)[9], const Win& v) {
+  float acc = w[4] * v.b1;
+  acc = fmaf(w[0], v.a0, acc);
+  acc = fmaf(w[1], v.a1, acc);
+  acc = fmaf(w[2], v.a2, acc);
+  acc = fmaf(w[3], v.b0, acc);
+  acc = fmaf(w[5], v.b2, acc);
+  acc = fmaf(w[6], v.c0, acc);
+  acc = fmaf(w[7], v.c1, acc);
+  acc = fmaf(w[8], v.c2, acc);
+  return acc;
+}
+
+// A v at grid point (i, j)
+template <int SK>
+__device__ __forceinline__ float tapply_A(const LevelDev& L, const float (&s)[9], int i, int j, const Win& v) {
+  if (SK == SK_CONST) return dot9(s, v);
+  const size_t nn = (size_t)L.n * L.n;
+  const float* a = L.st + (size_t)i * L.n + j;
+  float w[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) w[k] = __ldg(a + k * nn);
+  return dot9(w, v);
+}
+
+// H v at grid point (i, j).  Jacobi: (omega / D) v; table: the interior kernel wi on inner
+// tiles, else the point's class from the shared-memory table; field: per-point kernels.
+template <int SK, int HK, bool IN>
+__device__ __forceinline__ float tapply_H(const LevelDev& L, const float (&s)[9], const float* wtab,
+                                          const float (&wi)[9], float omega, int i, int j, const Win& v) {
+  if (HK == HK_JACOBI) {
+    const float d = (SK == SK_CONST) ? s[4] : __ldg(L.st + 4 * (size_t)L.n * L.n + (size_t)i * L.n + j);
+    return (omega / d) * v.b1;
+  }
+  if (HK == HK_TABLE && IN) return dot9(wi, v);
+  float w[9];
+  if (HK == HK_TABLE) {
+    const int T = L.T;
+    const float* p = wtab + kclass(i, L.n, T) * T + kclass(j, L.n, T);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) w[k] = p[k * T * T];
+  } else {
+    const size_t nn = (size_t)L.n * L.n;
+    const float* p = L.W + (size_t)i * L.n + j;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) w[k] = __ldg(p + k * nn);
+  }
+  return dot9(w, v);
+}
+
+// Network kernels of a constant-stencil level for one tile: the interior kernel to
+// registers on inner tiles, else the whole class table to shared memory.
+__device__ __forceinline__ void load_table(const LevelDev& L, bool in, float* wtab, float (&wi)[9]) {
+  const int T = L.T, M = MG_NET_MARGIN;
+  if (in) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) wi[k] = L.W[k * T * T + M * T + M];
   } else {
     const int cnt = 9 * T * T;
     for (int t = threadIdx.x; t < cnt; t += NT) wtab[t] = L.W[t];
   }
-  return interior;
-}
-
-// H v at (i, j): the interior kernel from registers when the tile is interior
-template <int SK, int HK>
-__device__ __forceinline__ float smooth_at(const LevelDev& L, const float (&s)[9], const float* wtab,
-                                           const float (&wi)[9], bool interior, float omega, int i, int j,
-                                           const float* c, int ts) {
-  if (HK == HK_TABLE && interior) {
-    float acc = wi[4] * c[0];
-    acc = fmaf(wi[0], c[-ts - 1], acc);
-    acc = fmaf(wi[1], c[-ts], acc);
-    acc = fmaf(wi[2], c[-ts + 1], acc);
-    acc = fmaf(wi[3], c[-1], acc);
-    acc = fmaf(wi[5], c[1], acc);
-    acc = fmaf(wi[6], c[ts - 1], acc);
-    acc = fmaf(wi[7], c[ts], acc);
-    acc = fmaf(wi[8], c[ts + 1], acc);
-    return acc;
-  }
-  return smoother_apply<SK, HK>(L, s, wtab, omega, i, j, c, ts);
 }
 
 // Waits for the CTA's copies; on expiry marks the problem timed out (status 4) and waits
@@ -93,7 +143,72 @@ __device__ __forceinline__ bool tile_wait(uint64_t* bar, ProbState& st) {
   return true;
 }
 
+__device__ __forceinline__ bool inside(int i, int j, int n) { return (unsigned)i < (unsigned)n && (unsigned)j < (unsigned)n; }
+
+// r - A x with x = xh + xl (Dot2: exact products and error-free sums for xh, plain FP32
+// for the xl terms), taps in the order of dot9's index k
+__device__ __forceinline__ void dot2_sub(float a, float x, float xl, float& hi, float& lo) {
+  const float pr = a * x;
+  const float pe = fmaf(a, x, -pr);
+  float sum, err;
+  two_sum(hi, -pr, sum, err);
+  hi = sum;
+  lo += err - pe;
+  lo = fmaf(-a, xl, lo);
+}
+
 // ------------------------------------------------------------------ k_residual
+// Thread = column of the tile (lane) x strip of 4 rows (warp); 3x3 windows of x_hi and x_lo
+// slide down the strip in registers.
+template <int SK, bool IN>
+__device__ __forceinline__ float residual_tile(const LevelDev& L, const float (&s)[9], const float* XH,
+                                               const float* XL, const float* BB, int R0, int C0) {
+  constexpr int KS = TB / NW;
+  const int n = L.n, pitch = L.pitch;
+  const int tj = threadIdx.x & 31, t0 = (threadIdx.x >> 5) * KS, j = C0 + tj;
+  const float* ch = XH + (t0 + 1) * XW + tj + 4;
+  const float* cl = XL + (t0 + 1) * XW + tj + 4;
+  Win h, l;
+  h.load_ab(ch, XW);
+  l.load_ab(cl, XW);
+  float acc = 0.f;
+  float* rout = L.r + (size_t)(R0 + t0) * pitch + j;
+#pragma unroll
+  for (int k = 0; k < KS; ++k) {
+    h.load_c(ch + k * XW, XW);
+    l.load_c(cl + k * XW, XW);
+    const int i = R0 + t0 + k;
+    if (IN || inside(i, j, n)) {
+      float a[9];
+      if (SK == SK_CONST) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) a[q] = s[q];
+      } else {
+        const size_t nn = (size_t)n * n;
+        const float* ap = L.st + (size_t)i * n + j;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) a[q] = __ldg(ap + q * nn);
+      }
+      float hi = BB[(t0 + k) * TB + tj], lo = 0.f;
+      dot2_sub(a[0], h.a0, l.a0, hi, lo);
+      dot2_sub(a[1], h.a1, l.a1, hi, lo);
+      dot2_sub(a[2], h.a2, l.a2, hi, lo);
+      dot2_sub(a[3], h.b0, l.b0, hi, lo);
+      dot2_sub(a[4], h.b1, l.b1, hi, lo);
+      dot2_sub(a[5], h.b2, l.b2, hi, lo);
+      dot2_sub(a[6], h.c0, l.c0, hi, lo);
+      dot2_sub(a[7], h.c1, l.c1, hi, lo);
+      dot2_sub(a[8], h.c2, l.c2, hi, lo);
+      const float r = hi + lo;
+      rout[k * pitch] = r;
+      acc = fmaf(r, r, acc);
+    }
+    h.shift();
+    l.shift();
+  }
+  return acc;
+}
+
 template <int SK>
 __global__ void __launch_bounds__(NT) k_residual(const __grid_constant__ ResMaps M, const ProbDev* __restrict__ probs,
                                                  ProbState* __restrict__ state, float* __restrict__ partials,
@@ -102,7 +217,7 @@ __global__ void __launch_bounds__(NT) k_residual(const __grid_constant__ ResMaps
   pdl_trigger();
   const int p = act ? act[blockIdx.y] : blockIdx.y;
   const LevelDev L = probs[p].lv[0];
-  const int n = L.n, pitch = L.pitch;
+  const int n = L.n;
   const int ntx = (n + TB - 1) / TB, ntiles = ntx * ntx;
   const int tile = blockIdx.x;
   if (tile >= ntiles) return;
@@ -112,7 +227,8 @@ __global__ void __launch_bounds__(NT) k_residual(const __grid_constant__ ResMaps
   __shared__ __align__(128) float BB[TB * TB];
   __shared__ __align__(8) uint64_t bar;
   float s[9];
-  load_stencil_t<SK>(L, s);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) s[k] = (SK == SK_CONST) ? L.s[k] : 0.f;
   pdl_wait();
   if (!state[p].active) return;
   if (threadIdx.x == 0) {
@@ -125,31 +241,8 @@ __global__ void __launch_bounds__(NT) k_residual(const __grid_constant__ ResMaps
   }
   __syncthreads();
   if (!tile_wait(&bar, state[p])) return;
-  const size_t nn = (size_t)n * n;
-  float acc = 0.f;
-  const int tx = threadIdx.x & 31;
-  for (int ty = threadIdx.x >> 5; ty < TB; ty += NW) {
-    const int i = R0 + ty, j = C0 + tx;
-    if (!in_grid(i, j, n)) continue;
-    const int c = (ty + 1) * XW + tx + 4;
-    float hi = BB[ty * TB + tx], lo = 0.f;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      const int off = (k / 3 - 1) * XW + (k % 3 - 1);
-      const float a = (SK == SK_CONST) ? s[k] : __ldg(L.st + k * nn + (size_t)i * n + j);
-      const float x = XH[c + off];
-      const float pr = a * x;
-      const float pe = fmaf(a, x, -pr);
-      float sum, err;
-      two_sum(hi, -pr, sum, err);
-      hi = sum;
-      lo += err - pe;
-      lo = fmaf(-a, XL[c + off], lo);
-    }
-    const float r = hi + lo;
-    L.r[(size_t)i * pitch + j] = r;
-    acc = fmaf(r, r, acc);
-  }
+  const float acc = inner_tile(R0, C0, n) ? residual_tile<SK, true>(L, s, XH, XL, BB, R0, C0)
+                                          : residual_tile<SK, false>(L, s, XH, XL, BB, R0, C0);
   float rhi, rlo;
   if (block_partial_and_last<NT>(acc, partials + (size_t)p * ntiles_max, &state[p].counter, ntiles, tile, rhi, rlo)) {
     if (threadIdx.x == 0) decide(state[p], rhi, rlo, rtol, max_cycles);
@@ -157,68 +250,198 @@ __global__ void __launch_bounds__(NT) k_residual(const __grid_constant__ ResMaps
 }
 
 // ---------------------------------------------------------------------- k_down
+// e = H r (pre-smoothing from zero) on rows/cols R0-1 .. R0+33, s = r - A e on R0 .. R0+32
+// (over r in place), r_c = P^T s on the tile's 16 x 16 coarse points.  Threads walk
+// vertical strips of 5 rows with a 3x3 register window.
+template <int SK, int HK, bool IN>
+__device__ __forceinline__ void down_tile(const LevelDev& L, const float (&s)[9], const float* wtab,
+                                          const float (&wi)[9], float omega, float* rs, float* es, float* eo,
+                                          int R0, int C0) {
+  constexpr int KS = 5;
+  const int n = L.n, t = threadIdx.x;
+  {
+    constexpr int NS = (ES + KS - 1) / KS;
+    if (t < ES * NS) {
+      const int tj = t % ES, t0 = (t / ES) * KS, j = C0 - 1 + tj;
+      const bool own_col = (unsigned)(tj - 1) < (unsigned)TB;
+      const float* c = rs + (t0 + 1) * XW + tj + 3;
+      Win v;
+      if (HK != HK_JACOBI) v.load_ab(c, XW);
+#pragma unroll
+      for (int k = 0; k < KS; ++k) {
+        const int ti = t0 + k;
+        if (ES % KS == 0 || ti < ES) {
+          const int i = R0 - 1 + ti;
+          if (HK != HK_JACOBI) v.load_c(c + k * XW, XW);
+          else v.b1 = c[k * XW];
+          float e = 0.f;
+          if (IN || inside(i, j, n)) e = tapply_H<SK, HK, IN>(L, s, wtab, wi, omega, i, j, v);
+          es[ti * ES + tj] = e;
+          if (own_col && (unsigned)(ti - 1) < (unsigned)TB) eo[(ti - 1) * TB + tj - 1] = e;
+          if (HK != HK_JACOBI) v.shift();
+        }
+      }
+    }
+  }
+  fence_async_smem();
+  __syncthreads();
+  {
+    constexpr int W2 = TB + 1, NS = (W2 + KS - 1) / KS;
+    if (t < W2 * NS) {
+      const int tj = t % W2, t0 = (t / W2) * KS, j = C0 + tj;
+      const float* c = es + (t0 + 1) * ES + tj + 1;
+      float* rp = rs + (t0 + 2) * XW + tj + 4;
+      Win v;
+      v.load_ab(c, ES);
+#pragma unroll
+      for (int k = 0; k < KS; ++k) {
+        const int ti = t0 + k;
+        if (ti < W2) {
+          const int i = R0 + ti;
+          v.load_c(c + k * ES, ES);
+          float sv = 0.f;
+          if (IN || inside(i, j, n)) sv = rp[k * XW] - tapply_A<SK>(L, s, i, j, v);
+          rp[k * XW] = sv;
+          v.shift();
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
 template <int SK, int HK>
-__global__ void __launch_bounds__(NT) k_down(const __grid_constant__ CUtensorMap mr, const ProbDev* __restrict__ probs,
+__global__ void __launch_bounds__(NT) k_down(const __grid_constant__ DownMaps M, const ProbDev* __restrict__ probs,
                                              ProbState* __restrict__ state, int l, float omega,
                                              const int* __restrict__ act) {
   pdl_trigger();
   const int p = act ? act[blockIdx.y] : blockIdx.y;
   const LevelDev L = probs[p].lv[l];
-  const LevelDev Lc = probs[p].lv[l + 1];
-  const int n = L.n, nc = Lc.n, pitch = L.pitch, cpitch = Lc.pitch;
+  const int n = L.n;
   const int ntx = (n + TB - 1) / TB;
   const int tile = blockIdx.x;
   if (tile >= ntx * ntx) return;
   const int R0 = (tile / ntx) * TB, C0 = (tile % ntx) * TB;
   __shared__ __align__(128) float rs[DN_H * XW];  // r, then s = r - A e in place
-  __shared__ float es[ES_DN * ES_DN];
-  __shared__ float wtab[9 * MG_PROXY * MG_PROXY];
+  __shared__ __align__(128) float eo[TB * TB];    // e on the owned points (stored by TMA)
+  __shared__ __align__(128) float rco[TC * TC];   // r_c (stored by TMA)
+  __shared__ float es[ES * ES];
+  __shared__ float wtab[HK == HK_TABLE ? 9 * MG_PROXY * MG_PROXY : 1];
   __shared__ __align__(8) uint64_t bar;
+  const bool in = inner_tile(R0, C0, n);
   float s[9], wi[9];
-  load_stencil_t<SK>(L, s);
-  bool interior = false;
-  if (HK == HK_TABLE) interior = load_table(L, R0, C0, wtab, wi);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) s[k] = (SK == SK_CONST) ? L.s[k] : 0.f;
+  if (HK == HK_TABLE) load_table(L, in, wtab, wi);
   pdl_wait();
   if (!state[p].active) return;
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     fence_mbar_init();
     mbar_arrive_expect_tx(&bar, DN_H * XW * sizeof(float));
-    tma_load_3d(rs, &mr, &bar, C0 - 4, R0 - 2, p);
+    tma_load_3d(rs, &M.r, &bar, C0 - 4, R0 - 2, p);
   }
   __syncthreads();
   if (!tile_wait(&bar, state[p])) return;
-  // pre-smoothing from zero: e = H r on rows/cols R0-1 .. R0+33
-  for (int t = threadIdx.x; t < ES_DN * ES_DN; t += NT) {
-      const int ti = t / ES_DN, tj = t - ti * ES_DN;
-      const int i = R0 - 1 + ti, j = C0 - 1 + tj;
-      float v = 0.f;
-      if (in_grid(i, j, n)) {
-        v = smooth_at<SK, HK>(L, s, wtab, wi, interior, omega, i, j, rs + (ti + 1) * XW + tj + 3, XW);
-        if (ti >= 1 && ti <= TB && tj >= 1 && tj <= TB) L.e[(size_t)i * pitch + j] = v;
-      }
-      es[ti * ES_DN + tj] = v;
-    }
-  __syncthreads();
-  // s = r - A e on rows/cols R0 .. R0+32, written over r
-  for (int t = threadIdx.x; t < (TB + 1) * (TB + 1); t += NT) {
-      const int ti = t / (TB + 1), tj = t - ti * (TB + 1);
-      const int i = R0 + ti, j = C0 + tj;
-      float* rp = rs + (ti + 2) * XW + tj + 4;
-      float v = 0.f;
-      if (in_grid(i, j, n)) v = *rp - stencil_apply<SK>(L, s, i, j, es + (ti + 1) * ES_DN + tj + 1, ES_DN);
-      *rp = v;
-    }
-  __syncthreads();
-  // r_c = P^T s for the 16 x 16 coarse points centred in the tile
+  if (in) down_tile<SK, HK, true>(L, s, wtab, wi, omega, rs, es, eo, R0, C0);
+  else down_tile<SK, HK, false>(L, s, wtab, wi, omega, rs, es, eo, R0, C0);
+  if (threadIdx.x == 0) tma_store_3d(&M.e, eo, C0, R0, p);
   {
     const int a = threadIdx.x >> 4, b = threadIdx.x & 15;
-    const int I = R0 / 2 + a, J = C0 / 2 + b;
-    if (I < nc && J < nc) Lc.r[(size_t)I * cpitch + J] = restrict_at(rs + (2 * a + 3) * XW + 2 * b + 5, XW);
+    rco[a * TC + b] = restrict_at(rs + (2 * a + 3) * XW + 2 * b + 5, XW);
+  }
+  fence_async_smem();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tma_store_3d(&M.rc, rco, C0 / 2, R0 / 2, p);
+    tma_store_commit();
+    tma_store_wait();
   }
 }
 
 // ------------------------------------------------------------------------ k_up
+// e1 = e + P e_c on rows/cols R0-2 .. R0+33 (zero outside the grid without masking: e and
+// e_c are zero-filled there), t = r - A e1 on R0-1 .. R0+32, e = e1 + H t on the tile; on
+// level 0 e is added to the float-float iterate.
+template <int SK, int HK, bool UPDX, bool IN>
+__device__ __forceinline__ void up_tile(const LevelDev& L, const float (&s)[9], const float* wtab,
+                                        const float (&wi)[9], float omega, float* es, float* rs, const float* ecs,
+                                        const float* xhs, const float* xls, float* xhi, float* xlo, int p, int R0,
+                                        int C0) {
+  const int n = L.n, pitch = L.pitch, t = threadIdx.x;
+  {
+    // bilinear P: P e_c(i, j) = ((c(ia,ja) + c(ia,jb)) + (c(ib,ja) + c(ib,jb))) / 4 with
+    // ia = floor((i-1)/2), ib = floor(i/2) (equal for odd i), ja, jb likewise
+    constexpr int W1 = TB + 4, KS = 6, NS = W1 / KS;
+    if (t < W1 * NS) {
+      const int tj = t % W1, t0 = (t / W1) * KS, j = C0 - 2 + tj;
+      const int I0 = R0 / 2 - 2, J0 = C0 / 2 - 4;
+      const int ja = ((j - 1) >> 1) - J0, jb = (j >> 1) - J0;
+#pragma unroll
+      for (int k = 0; k < KS; ++k) {
+        const int ti = t0 + k, i = R0 - 2 + ti;
+        const float* ra = ecs + (((i - 1) >> 1) - I0) * EC_W;
+        const float* rb = ecs + ((i >> 1) - I0) * EC_W;
+        es[ti * XW + tj + 2] += 0.25f * ((ra[ja] + ra[jb]) + (rb[ja] + rb[jb]));
+      }
+    }
+  }
+  __syncthreads();
+  {
+    constexpr int W2 = TB + 2, KS = 5, NS = (W2 + KS - 1) / KS;
+    if (t < W2 * NS) {
+      const int tj = t % W2, t0 = (t / W2) * KS, j = C0 - 1 + tj;
+      const float* c = es + (t0 + 1) * XW + tj + 3;
+      float* rp = rs + t0 * XW + tj + 3;
+      Win v;
+      v.load_ab(c, XW);
+#pragma unroll
+      for (int k = 0; k < KS; ++k) {
+        const int ti = t0 + k;
+        if (ti < W2) {
+          const int i = R0 - 1 + ti;
+          v.load_c(c + k * XW, XW);
+          float tv = 0.f;
+          if (IN || inside(i, j, n)) tv = rp[k * XW] - tapply_A<SK>(L, s, i, j, v);
+          rp[k * XW] = tv;
+          v.shift();
+        }
+      }
+    }
+  }
+  __syncthreads();
+  {
+    constexpr int KS = TB / NW;
+    const int tj = threadIdx.x & 31, t0 = (threadIdx.x >> 5) * KS, j = C0 + tj;
+    const float* c = rs + (t0 + 1) * XW + tj + 4;
+    const float* e1 = es + (t0 + 2) * XW + tj + 4;
+    Win v;
+    if (HK != HK_JACOBI) v.load_ab(c, XW);
+    const size_t row0 = (size_t)(R0 + t0) * pitch + j;
+#pragma unroll
+    for (int k = 0; k < KS; ++k) {
+      const int i = R0 + t0 + k;
+      if (HK != HK_JACOBI) v.load_c(c + k * XW, XW);
+      else v.b1 = c[k * XW];
+      if (IN || inside(i, j, n)) {
+        const float e = e1[k * XW] + tapply_H<SK, HK, IN>(L, s, wtab, wi, omega, i, j, v);
+        if (UPDX) {
+          const size_t g = (size_t)p * n * pitch + row0 + (size_t)k * pitch;
+          float hi = xhs[(t0 + k) * TB + tj], lo = xls[(t0 + k) * TB + tj], sum, err;
+          two_sum(hi, e, sum, err);
+          err += lo;
+          fast_two_sum(sum, err, hi, lo);
+          xhi[g] = hi;
+          xlo[g] = lo;
+        } else {
+          L.e[row0 + (size_t)k * pitch] = e;
+        }
+      }
+      if (HK != HK_JACOBI) v.shift();
+    }
+  }
+}
+
 template <int SK, int HK, bool UPDX>
 __global__ void __launch_bounds__(NT) k_up(const __grid_constant__ UpMaps M, const ProbDev* __restrict__ probs,
                                            ProbState* __restrict__ state, int l, float omega, float* __restrict__ xhi,
@@ -226,7 +449,7 @@ __global__ void __launch_bounds__(NT) k_up(const __grid_constant__ UpMaps M, con
   pdl_trigger();
   const int p = act ? act[blockIdx.y] : blockIdx.y;
   const LevelDev L = probs[p].lv[l];
-  const int n = L.n, nc = probs[p].lv[l + 1].n, pitch = L.pitch;
+  const int n = L.n;
   const int ntx = (n + TB - 1) / TB;
   const int tile = blockIdx.x;
   if (tile >= ntx * ntx) return;
@@ -236,13 +459,13 @@ __global__ void __launch_bounds__(NT) k_up(const __grid_constant__ UpMaps M, con
   __shared__ __align__(128) float ecs[EC_H * EC_W];
   __shared__ __align__(128) float xhs[UPDX ? TB * TB : 4];
   __shared__ __align__(128) float xls[UPDX ? TB * TB : 4];
-  __shared__ float wtab[9 * MG_PROXY * MG_PROXY];
+  __shared__ float wtab[HK == HK_TABLE ? 9 * MG_PROXY * MG_PROXY : 1];
   __shared__ __align__(8) uint64_t bar;
-  const int I0 = R0 / 2 - 2, J0 = C0 / 2 - 4;
+  const bool in = inner_tile(R0, C0, n);
   float s[9], wi[9];
-  load_stencil_t<SK>(L, s);
-  bool interior = false;
-  if (HK == HK_TABLE) interior = load_table(L, R0, C0, wtab, wi);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) s[k] = (SK == SK_CONST) ? L.s[k] : 0.f;
+  if (HK == HK_TABLE) load_table(L, in, wtab, wi);
   pdl_wait();
   if (!state[p].active) return;
   if (threadIdx.x == 0) {
@@ -251,7 +474,7 @@ __global__ void __launch_bounds__(NT) k_up(const __grid_constant__ UpMaps M, con
     mbar_arrive_expect_tx(&bar, ((UPE_H + UPR_H) * XW + EC_H * EC_W + (UPDX ? 2 * TB * TB : 0)) * sizeof(float));
     tma_load_3d(es, &M.e, &bar, C0 - 4, R0 - 2, p);
     tma_load_3d(rs, &M.r, &bar, C0 - 4, R0 - 1, p);
-    tma_load_3d(ecs, &M.ec, &bar, J0, I0, p);
+    tma_load_3d(ecs, &M.ec, &bar, C0 / 2 - 4, R0 / 2 - 2, p);
     if (UPDX) {
       tma_load_3d(xhs, &M.xh, &bar, C0, R0, p);
       tma_load_3d(xls, &M.xl, &bar, C0, R0, p);
@@ -259,43 +482,8 @@ __global__ void __launch_bounds__(NT) k_up(const __grid_constant__ UpMaps M, con
   }
   __syncthreads();
   if (!tile_wait(&bar, state[p])) return;
-  (void)nc;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // e1 = e + P e_c on rows/cols R0-2 .. R0+33 (zero outside the grid)
-  for (int t = threadIdx.x; t < (TB + 4) * (TB + 4); t += NT) {
-      const int ti = t / (TB + 4), tj = t - ti * (TB + 4);
-      const int i = R0 - 2 + ti, j = C0 - 2 + tj;
-      float* ep = es + ti * XW + tj + 2;
-      *ep = in_grid(i, j, n) ? *ep + prolong_at(i, j, ecs, I0, J0, EC_W) : 0.f;
-    }
-  __syncthreads();
-  // t = r - A e1 on rows/cols R0-1 .. R0+32
-  for (int t = threadIdx.x; t < (TB + 2) * (TB + 2); t += NT) {
-      const int ti = t / (TB + 2), tj = t - ti * (TB + 2);
-      const int i = R0 - 1 + ti, j = C0 - 1 + tj;
-      float* rp = rs + ti * XW + tj + 3;
-      *rp = in_grid(i, j, n) ? *rp - stencil_apply<SK>(L, s, i, j, es + (ti + 1) * XW + tj + 3, XW) : 0.f;
-    }
-  __syncthreads();
-  // post-smoothing on the owned points: e = e1 + H t
-  const int tx = lane;
-  for (int ty = warp; ty < TB; ty += NW) {
-    const int i = R0 + ty, j = C0 + tx;
-    if (!in_grid(i, j, n)) continue;
-    const float e = es[(ty + 2) * XW + tx + 4] +
-                    smooth_at<SK, HK>(L, s, wtab, wi, interior, omega, i, j, rs + (ty + 1) * XW + tx + 4, XW);
-    const size_t g = (size_t)p * n * pitch + (size_t)i * pitch + j;
-    if (UPDX) {
-      float hi = xhs[ty * TB + tx], lo = xls[ty * TB + tx], sum, err;
-      two_sum(hi, e, sum, err);
-      err += lo;
-      fast_two_sum(sum, err, hi, lo);
-      xhi[g] = hi;
-      xlo[g] = lo;
-    } else {
-      L.e[(size_t)i * pitch + j] = e;
-    }
-  }
+  if (in) up_tile<SK, HK, UPDX, true>(L, s, wtab, wi, omega, es, rs, ecs, xhs, xls, xhi, xlo, p, R0, C0);
+  else up_tile<SK, HK, UPDX, false>(L, s, wtab, wi, omega, es, rs, ecs, xhs, xls, xhi, xlo, p, R0, C0);
 }
 
 // -------------------------------------------------------------- pack / unpack
@@ -361,7 +549,9 @@ bool build_tile_maps(TileMaps& T, const LevelArrays& A, int nprob, int lstar) {
             make_map(&T.res.xl, A.xl0, A.n[0], A.pitch[0], nprob, XW, RES_H) &&
             make_map(&T.res.b, A.b0, A.n[0], A.pitch[0], nprob, TB, TB);
   for (int l = 0; ok && l < lstar; ++l) {
-    ok = make_map(&T.down[l], A.r[l], A.n[l], A.pitch[l], nprob, XW, DN_H) &&
+    ok = make_map(&T.down[l].r, A.r[l], A.n[l], A.pitch[l], nprob, XW, DN_H) &&
+         make_map(&T.down[l].e, A.e[l], A.n[l], A.pitch[l], nprob, TB, TB) &&
+         make_map(&T.down[l].rc, A.r[l + 1], A.n[l + 1], A.pitch[l + 1], nprob, TC, TC) &&
          make_map(&T.up[l].e, A.e[l], A.n[l], A.pitch[l], nprob, XW, UPE_H) &&
          make_map(&T.up[l].r, A.r[l], A.n[l], A.pitch[l], nprob, XW, UPR_H) &&
          make_map(&T.up[l].ec, A.e[l + 1], A.n[l + 1], A.pitch[l + 1], nprob, EC_W, EC_H);
@@ -415,15 +605,19 @@ cudaError_t launch_cycle(const CycleArgs& a) {
   for (int l = ls - 1; l >= 0 && e == cudaSuccess; --l) {
     const int nt = tiles_per_side(a.nl[l]);
     dim3 grid(nt * nt, np);
+    // The kernel after the cluster tail waits for it by plain stream order: launched with
+    // programmatic serialisation it was seen to read the tail's e before all of it was
+    // written (run-to-run differences in 16-problem batches, none with plain ordering).
+    const bool pdl = a.pdl && !(a.ctail && l == ls - 1);
     a.prof->launches++;
     a.prof->begin(l == 0 ? PK_UP0 : PK_UP, a.stream);
     if (l == 0)
       MG_DISPATCH(a.sk, a.hk,
-                  (e = launch_pdl(a.pdl, k_up<SK_, HK_, true>, grid, dim3(NT), 0, a.stream, a.maps->up[0], probs, a.state, 0,
+                  (e = launch_pdl(pdl, k_up<SK_, HK_, true>, grid, dim3(NT), 0, a.stream, a.maps->up[0], probs, a.state, 0,
                                   a.omega, a.xh0, a.xl0, a.active)));
     else
       MG_DISPATCH(a.sk, a.hk,
-                  (e = launch_pdl(a.pdl, k_up<SK_, HK_, false>, grid, dim3(NT), 0, a.stream, a.maps->up[l], probs, a.state,
+                  (e = launch_pdl(pdl, k_up<SK_, HK_, false>, grid, dim3(NT), 0, a.stream, a.maps->up[l], probs, a.state,
                                   l, a.omega, nul, nul, a.active)));
     a.prof->end(a.stream);
   }

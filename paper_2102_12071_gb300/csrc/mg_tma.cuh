@@ -61,6 +61,21 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+// shared memory -> box of the tensor map at (x, y, z) (bulk async-group of this thread);
+// elements outside the tensor are not written.  The source must stay unchanged until
+// tma_store_wait() has returned.
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, const void* src, int x, int y, int z) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(smem_u32(src)), "r"(x), "r"(y), "r"(z)
+               : "memory");
+}
+__device__ __forceinline__ void tma_store_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// until every committed store of this thread has been performed
+__device__ __forceinline__ void tma_store_wait() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// orders this thread's earlier shared-memory writes before later copy-engine reads
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 // Programmatic dependent launch: let the next kernel on the stream be scheduled now (its
 // CTAs run their prologue), and wait here until the previous kernel has completed and its
 // memory operations are visible.

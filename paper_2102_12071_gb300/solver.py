@@ -34,14 +34,14 @@ class MultigridSolver:
 
     def __init__(self, problems: list[dict], smoother: str = "jacobi", net_params: torch.Tensor | None = None,
                  omega: float = 2.0 / 3.0, conv_bf16: bool = False, coarsest_n: int = 3, device="cuda",
-                 stream=None):
+                 stream=None, cluster_tail: bool = True):
         self.nprob = len(problems)
         self.n = problems[0]["n"]
         self.device = torch.device(device)
         self.stream = stream
         self._probs, self._keep = B.problems_array(problems)
         kind = B.MG_SMOOTH_CNN if smoother == "cnn" else B.MG_SMOOTH_JACOBI
-        self.opts = B.options(kind, omega, coarsest_n, int(conv_bf16))
+        self.opts = B.options(kind, omega, coarsest_n, int(conv_bf16), int(cluster_tail))
         size = B.mg_workspace_size(self._probs, self.nprob, self.opts)
         if size == 0:
             raise B.MGError(B.MG_ERR_INVALID_ARG, "mg_workspace_size", B.lib().mg_last_error().decode())

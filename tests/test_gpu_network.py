@@ -77,12 +77,13 @@ def test_cnn_kernels_match_oracle_on_every_level(n):
         np.testing.assert_allclose(Wg, Wo, rtol=2e-5, atol=2e-6 * np.abs(Wo).max())
 
 
-@pytest.mark.parametrize("n,cycles", [(63, 60), (255, 25)])
-def test_cnn_solve_history_matches_oracle(n, cycles):
+@pytest.mark.parametrize("n,cycles,ct", [(63, 60, True), (255, 25, True), (255, 25, False), (511, 8, True)])
+def test_cnn_solve_history_matches_oracle(n, cycles, ct):
+    """ct: coarse levels in one CTA cluster per problem (True) or one CTA (False)."""
     eps, theta = 0.05, 0.7
     p = small_net(3)
     b = inputs.rhs_uniform(7, n)
-    mg = S.MultigridSolver([S.rotated(n, eps, theta)], "cnn", torch.from_numpy(p).cuda())
+    mg = S.MultigridSolver([S.rotated(n, eps, theta)], "cnn", torch.from_numpy(p).cuda(), cluster_tail=ct)
     _, _, gh, cyc, _ = mg.solve(torch.from_numpy(b).cuda()[None].contiguous(), rtol=0.0, max_cycles=cycles)
     om = O.Multigrid(O.const_field(n, f32(O.q1_rotated_stencil(eps, theta))))
     om.set_cnn(f32(p))
@@ -92,12 +93,14 @@ def test_cnn_solve_history_matches_oracle(n, cycles):
     assert rel.max() <= 1e-5, rel.max()
 
 
-def test_cnn_solve_varcoef_field_path():
+@pytest.mark.parametrize("ct", [True, False])
+def test_cnn_solve_varcoef_field_path(ct):
     """Per-point kernels (variable coefficients): setup, RAP fields and the CNN solve."""
     n = 127
     a = inputs.grf_cells(11, n)
     p = small_net(4)
-    mg = S.MultigridSolver([S.varcoef5(n, torch.from_numpy(a).cuda())], "cnn", torch.from_numpy(p).cuda())
+    mg = S.MultigridSolver([S.varcoef5(n, torch.from_numpy(a).cuda())], "cnn", torch.from_numpy(p).cuda(),
+                           cluster_tail=ct)
     st0 = O.varcoef5_field(n, f32(a))
     om = O.Multigrid(f32(st0))
     for l in range(mg.levels):

@@ -89,12 +89,14 @@ def test_c1_jacobi_solve_matches_oracle(n):
         assert abs(fg - fo) <= 1e-3 * fo
 
 
-@pytest.mark.parametrize("n,cycles", [(127, 40), (255, 60), (1023, 4)])
-def test_large_grid_jacobi_history_matches_oracle(n, cycles):
-    """Tiled kernels (k_residual/k_down/k_up) plus the one-CTA tail; 1023 is the bench size."""
+@pytest.mark.parametrize("n,cycles,ct", [(127, 40, True), (255, 60, True), (1023, 4, True), (127, 40, False),
+                                         (255, 60, False), (1023, 4, False)])
+def test_large_grid_jacobi_history_matches_oracle(n, cycles, ct):
+    """Tiled kernels (k_residual/k_down/k_up) plus the coarse levels in one CTA cluster per
+    problem (ct) or in one CTA (levels <= 63, tiled above); 1023 is the bench size."""
     eps, theta = 0.05, 1.1
     b = inputs.rhs_uniform(1000, n)
-    mg = S.MultigridSolver([S.rotated(n, eps, theta)])
+    mg = S.MultigridSolver([S.rotated(n, eps, theta)], cluster_tail=ct)
     _, _, gh, cyc, st = mg.solve(torch.from_numpy(b).cuda()[None].contiguous(), rtol=0.0, max_cycles=cycles)
     assert st == B.MG_ERR_NOT_CONVERGED and cyc[0] == cycles
     om = O.Multigrid(oracle_rotated(n, eps, theta))
@@ -211,3 +213,22 @@ def test_vcycle_without_low_part_on_tiled_path():
     for _ in range(3):
         x = om.vcycle(f32(b), x)
     assert np.abs(xh[0].double().cpu().numpy() - x).max() <= 1e-5 * np.abs(x).max()
+
+
+def test_cluster_and_one_cta_tails_agree_on_a_batch():
+    """16 problems of the bench family at 511^2 (CNN-free, Jacobi): the cycle laid out as
+    one CTA cluster per problem for levels <= 127 and as tiled kernels plus a one-CTA tail
+    for levels <= 63 computes the same histories."""
+    n = 511
+    params = inputs.rotated_params(inputs.SEED_PARAMS, 16)
+    b = torch.from_numpy(np.stack([inputs.rhs_uniform(inputs.SEED_RHS + i, n) for i in range(16)])).cuda()
+    hs = []
+    for ct in (True, False):
+        mg = S.MultigridSolver([S.rotated(n, e, t) for e, t in params], cluster_tail=ct)
+        _, _, gh, cyc, _ = mg.solve(b.contiguous(), rtol=1e-8, max_cycles=30)
+        hs.append((gh, cyc))
+        mg.close()
+    np.testing.assert_array_equal(hs[0][1], hs[1][1])
+    for p in range(16):
+        k = int(hs[0][1][p]) + 1
+        np.testing.assert_allclose(hs[0][0][p][:k], hs[1][0][p][:k], rtol=1e-6)
