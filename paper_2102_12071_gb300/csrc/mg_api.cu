@@ -9,6 +9,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "mg_internal.h"
@@ -210,6 +211,29 @@ static mg_status cycle_graph(mg_ctx* ctx, const CycleArgs& a, float rtol, int ma
   *out = exec;
   *nodes = g.nodes;
   return MG_OK;
+}
+
+// Cycles of the next chunk of the solve loop.  Launches cover the problems active at the
+// start of a chunk, so a problem converging inside it keeps launching (idle) CTAs until
+// the chunk ends: the chunk is sized to end when the next problem is expected to reach
+// rtol at its recent convergence rate, as a multiple of the graph length and at most one
+// ring of residual history; without a rate estimate it doubles.
+static int next_chunk(const std::vector<ProbState>& st, int prev, double rtol, int max_cycles) {
+  int soonest = std::min(2 * prev, MG_HRING);
+  for (const ProbState& S : st) {
+    if (!S.active) continue;
+    const int it = S.iter;  // residual evaluations so far
+    int rem = max_cycles + 1 - it;
+    const int d = std::min(std::min(it - 1, prev), MG_HRING - 1);
+    if (rtol > 0.0 && d >= 4) {
+      const double r1 = S.hist[(it - 1) % MG_HRING], r0 = S.hist[(it - 1 - d) % MG_HRING];
+      const double rho = (r0 > 0.0 && r1 > 0.0) ? pow(r1 / r0, 1.0 / d) : 1.0;
+      if (rho < 0.9999) rem = std::min(rem, (int)std::min(1e6, ceil(log(rtol / r1) / log(rho))) + 1);
+    }
+    soonest = std::min(soonest, std::max(rem, 1));
+  }
+  const int G = (soonest + kGraphCycles - 1) / kGraphCycles * kGraphCycles;
+  return std::min(std::max(G, kGraphCycles), MG_HRING / kGraphCycles * kGraphCycles);
 }
 
 // row pitch of level vectors: a multiple of 32 floats (128-byte rows, TMA-aligned)
@@ -538,7 +562,7 @@ mg_status mg_solve(mg_ctx* ctx, const float* b, float* x_hi, float* x_lo, double
       a.active = ctx->d_active;
       a.nactive = active;
     }
-    G = G < 128 ? 2 * G : 128;
+    G = next_chunk(ctx->h_state, G, rtol, max_cycles);
   }
   if (!P.tail_solve) {
     CK(launch_unpack(A.xh0, x_hi, A.n[0], A.pitch[0], a.nprob, a.stream));

@@ -232,3 +232,17 @@ def test_cluster_and_one_cta_tails_agree_on_a_batch():
     for p in range(16):
         k = int(hs[0][1][p]) + 1
         np.testing.assert_allclose(hs[0][0][p][:k], hs[1][0][p][:k], rtol=1e-6)
+
+
+def test_batch_solve_is_deterministic():
+    """Two solves of a 16-problem 511^2 batch (CUDA-graph cycles with programmatic launches,
+    CNN-free) give bit-identical histories and iterates."""
+    n = 511
+    params = inputs.rotated_params(inputs.SEED_PARAMS, 16)
+    b = torch.from_numpy(np.stack([inputs.rhs_uniform(inputs.SEED_RHS + i, n) for i in range(16)])).cuda()
+    mg = S.MultigridSolver([S.rotated(n, e, t) for e, t in params])
+    runs = [mg.solve(b.contiguous(), rtol=1e-8, max_cycles=40) for _ in range(3)]
+    for xh, xl, gh, cyc, _ in runs[1:]:
+        np.testing.assert_array_equal(cyc, runs[0][3])
+        np.testing.assert_array_equal(np.nan_to_num(gh, nan=-1.0), np.nan_to_num(runs[0][2], nan=-1.0))
+        assert torch.equal(xh, runs[0][0]) and torch.equal(xl, runs[0][1])
