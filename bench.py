@@ -36,6 +36,9 @@ MAX_CYCLES = 20000
 WEIGHTS = os.path.join(ROOT, "paper_2102_12071_gb300", "weights", "cnn_rotated.npy")
 # algorithmic bytes per fine dof per launch (FP32, constant stencil)
 BYTES_PER_DOF = {0: 16.0, 1: 9.0, 2: 25.0}
+# dram bytes (read + write) per launch of the current kernel versions from one ncu capture
+# of the 16 x 1023^2 batch; None where the kernel changed since its last capture
+NCU_TRAFFIC = {0: 201.5e6 + 48.8e6, 1: None, 2: None}
 KERNEL_NAMES = {0: "k_residual", 1: "k_down(level 0)", 2: "k_up(level 0, x update)", 3: "k_tail", 4: "k_down(l>=1)",
                 5: "k_up(l>=1)"}
 
@@ -230,7 +233,8 @@ def run_varcoef(args, rank):
 
 
 def run_profile_case(args):
-    """Set up the benchmark batch and run a fixed number of cycles, nothing else."""
+    """Set up the benchmark batch and run a fixed number of single V-cycles (mg_vcycle:
+    residual, cycle, residual), nothing else: every launch does work (profiler captures)."""
     import torch
 
     import __graft_entry__
@@ -244,7 +248,9 @@ def run_profile_case(args):
     kind = args.smoother if args.smoother != "auto" else ("cnn" if w is not None else "jacobi")
     mg = S.MultigridSolver(problems, kind, net_params=w.cuda() if kind == "cnn" else None)
     b = torch.from_numpy(b_host).cuda().contiguous()
-    mg.solve(b, rtol=0.0, max_cycles=args.profile_cycles, history=False)
+    x_hi, x_lo = torch.zeros_like(b), torch.zeros_like(b)
+    for _ in range(args.profile_cycles):
+        mg.vcycle(b, x_hi, x_lo)
     torch.cuda.synchronize()
 
 
@@ -261,7 +267,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--roofline-cycles", type=int, default=20)
     ap.add_argument("--profile-cycles", type=int, default=0,
-                    help="only set up the batch and run this many V-cycles (for profiler captures)")
+                    help="only set up the batch and run this many single V-cycles (for profiler captures)")
     ap.add_argument("--smoother", default="auto", choices=["auto", "jacobi", "cnn"])
     ap.add_argument("--varcoef-n", type=int, default=1023, help="side of the GRF problem (0: skip)")
     args = ap.parse_args()
@@ -381,8 +387,9 @@ def main():
     algo_bytes = BYTES_PER_DOF[dom] * nprob * n * n
     achieved = algo_bytes / (dom_ms / dom_n / 1e3) / 1e9 if dom_n else None
     cycle_bytes = (16 + 9 + 25) * nprob * n * n + sum((9 + 13) * nprob * s * s for s in sizes[1:-1] if s > 127)
+    traffic = NCU_TRAFFIC.get(dom) if (n, nprob) == (N_DEFAULT, NPROB_DEFAULT) else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None, "traffic": None,
+                "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "kernel": KERNEL_NAMES[dom], "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": algo_bytes,
                 "launch_us": {KERNEL_NAMES[c]: round(1e3 * prof[c][0] / prof[c][1], 2) for c in prof if prof[c][1]},
