@@ -35,12 +35,14 @@ RTOL = 1e-8
 MAX_CYCLES = 20000
 WEIGHTS = os.path.join(ROOT, "paper_2102_12071_gb300", "weights", "cnn_rotated.npy")
 # algorithmic bytes per fine dof per launch (FP32, constant stencil)
-BYTES_PER_DOF = {0: 16.0, 1: 9.0, 2: 25.0}
+# k_residual: x_hi, x_lo, b in, r out; k_down level 0: r in, e out, r_c out (1/4);
+# k_up0: e, r, e_c (1/4), x_hi, x_lo, b in; x_hi, x_lo, r out
+BYTES_PER_DOF = {0: 16.0, 1: 9.0, 2: 33.0}
 # dram bytes (read + write) per launch of the current kernel versions from one ncu capture
 # of the 16 x 1023^2 batch; None where the kernel changed since its last capture
-NCU_TRAFFIC = {0: 201.5e6 + 48.8e6, 1: None, 2: None}
-KERNEL_NAMES = {0: "k_residual", 1: "k_down(level 0)", 2: "k_up(level 0, x update)", 3: "k_tail", 4: "k_down(l>=1)",
-                5: "k_up(l>=1)"}
+NCU_TRAFFIC = {1: None, 2: None}
+KERNEL_NAMES = {0: "k_residual (initial iterate)", 1: "k_down(level 0)", 2: "k_up0(level 0: up-sweep, x update, residual)",
+                3: "k_tail", 4: "k_down(l>=1)", 5: "k_up(l>=1)"}
 
 
 def peaks():
@@ -379,21 +381,22 @@ def main():
     solve_prof = {KERNEL_NAMES[c]: round(B.mg_profile_read(ctx, c)[0], 3) for c in range(6)}
     solve_launches = {KERNEL_NAMES[c]: B.mg_profile_read(ctx, c)[1] for c in range(6)}
     B.mg_profile_enable(ctx, False)
-    # kernel time of one solve cycle by class (mg_vcycle evaluates the residual twice)
-    per_cycle = {c: prof[c][0] / args.roofline_cycles / (2 if c == 0 else 1) for c in prof}
+    # kernel time of one solve cycle by class (each mg_vcycle call is the initial residual,
+    # which a solve evaluates once, and one cycle ending with the new residual)
+    per_cycle = {c: prof[c][0] / args.roofline_cycles for c in prof if c != 0}
     total_ms = sum(per_cycle.values())
-    dom = max((0, 1, 2), key=lambda c: per_cycle[c])
+    dom = max((1, 2), key=lambda c: per_cycle[c])
     dom_ms, dom_n = prof[dom]
     algo_bytes = BYTES_PER_DOF[dom] * nprob * n * n
     achieved = algo_bytes / (dom_ms / dom_n / 1e3) / 1e9 if dom_n else None
-    cycle_bytes = (16 + 9 + 25) * nprob * n * n + sum((9 + 13) * nprob * s * s for s in sizes[1:-1] if s > 127)
+    cycle_bytes = (9 + 33) * nprob * n * n + sum((9 + 13) * nprob * s * s for s in sizes[1:-1] if s > 127)
     traffic = NCU_TRAFFIC.get(dom) if (n, nprob) == (N_DEFAULT, NPROB_DEFAULT) else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "kernel": KERNEL_NAMES[dom], "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": algo_bytes,
                 "launch_us": {KERNEL_NAMES[c]: round(1e3 * prof[c][0] / prof[c][1], 2) for c in prof if prof[c][1]},
-                "kernel_share": {KERNEL_NAMES[c]: round(per_cycle[c] / total_ms, 4) for c in prof if total_ms},
+                "kernel_share": {KERNEL_NAMES[c]: round(per_cycle[c] / total_ms, 4) for c in per_cycle if total_ms},
                 "cycle_kernel_us": round(1e3 * total_ms, 2),
                 "cycle_hbm_frac": (cycle_bytes / (total_ms / 1e3) / 1e9) / peak,
                 "solve_breakdown": {"note": "the 1e-8 solve with every launch event-timed; launches include "

@@ -149,7 +149,8 @@ struct mg_ctx {
   LevelArrays arrays;
   TileMaps maps;
   Profiler prof;
-  // captured cycles (residual + every level kernel) per compacted launch size
+  // captured cycles (every level kernel; the last one ends with the new residual and the
+  // stopping test) per compacted launch size
   struct CycleGraph {
     int nactive, max_cycles;
     float rtol;
@@ -187,8 +188,7 @@ static mg_status cycle_graph(mg_ctx* ctx, const CycleArgs& a, float rtol, int ma
   CK(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e2 = cudaSuccess;
   for (int k = 0; k < kGraphCycles && e2 == cudaSuccess; ++k) {
-    e2 = launch_residual(c, rtol, max_cycles);
-    if (e2 == cudaSuccess) e2 = launch_cycle(c);
+    e2 = launch_cycle(c, rtol, max_cycles, k & 1);
   }
   cudaGraph_t graph = nullptr;
   cudaError_t e3 = cudaStreamEndCapture(c.stream, &graph);
@@ -259,12 +259,18 @@ static size_t carve(const Plan& P, const mg_options& o, void* base, mg_ctx* ctx)
     const size_t sz = (size_t)P.nprob * A.n[l] * A.pitch[l];
     A.r[l] = c.take<float>(sz);
     A.e[l] = c.take<float>(sz);
+    // tiled levels >= 1 of either coarse-level layout (the layout of the workspace does not
+    // depend on which one the device can run)
+    if (l >= 1 && l < P.lstar1) A.f[l] = c.take<float>(sz);
   }
-  if (P.lstar > 0) {
+  if (P.lstar1 > 0) {
     const size_t sz = (size_t)P.nprob * A.n[0] * A.pitch[0];
     A.xh0 = c.take<float>(sz);
     A.xl0 = c.take<float>(sz);
     A.b0 = c.take<float>(sz);
+    A.r0b = c.take<float>(sz);
+    A.xh0b = c.take<float>(sz);
+    A.xl0b = c.take<float>(sz);
   }
   std::vector<ProbDev> hp(ctx ? P.nprob : 0);
   for (int p = 0; p < P.nprob; ++p) {
@@ -279,6 +285,7 @@ static size_t carve(const Plan& P, const mg_options& o, void* base, mg_ctx* ctx)
       v.pitch = A.pitch[l];
       v.r = A.r[l] ? A.r[l] + (size_t)p * n * A.pitch[l] : nullptr;
       v.e = A.e[l] ? A.e[l] + (size_t)p * n * A.pitch[l] : nullptr;
+      v.f = (l >= 1 && l < P.lstar && A.f[l]) ? A.f[l] + (size_t)p * n * A.pitch[l] : v.e;
       if (P.sk == SK_FIELD) v.st = c.take<float>(9 * nn);
       if (l < P.L - 1) {
         if (P.hk == HK_FIELD) v.W = c.take<float>(9 * nn);
@@ -296,6 +303,10 @@ static size_t carve(const Plan& P, const mg_options& o, void* base, mg_ctx* ctx)
     ctx->args.partials = partials;
     ctx->args.xh0 = A.xh0;
     ctx->args.xl0 = A.xl0;
+    ctx->args.r0a = A.r[0];
+    ctx->args.r0b = A.r0b;
+    ctx->args.xh0b = A.xh0b;
+    ctx->args.xl0b = A.xl0b;
     ctx->arrays = A;
     ctx->xlo_ws = xlo;
     ctx->d_fail = fail_flag;
@@ -491,10 +502,9 @@ mg_status mg_vcycle(mg_ctx* ctx, const float* b, float* x_hi, float* x_lo, float
     CK(launch_pack(x_hi, A.xh0, A.n[0], A.pitch[0], a.nprob, a.stream));
     CK(launch_pack(x_lo, A.xl0, A.n[0], A.pitch[0], a.nprob, a.stream));
     CK(launch_residual(a, -1.f, big));
-    CK(launch_cycle(a));
-    CK(launch_residual(a, -1.f, big));
-    CK(launch_unpack(A.xh0, x_hi, A.n[0], A.pitch[0], a.nprob, a.stream));
-    if (x_lo) CK(launch_unpack(A.xl0, x_lo, A.n[0], A.pitch[0], a.nprob, a.stream));
+    CK(launch_cycle(a, -1.f, big, 0));  // ends with the residual of the new iterate
+    CK(launch_unpack(A.xh0, A.xh0b, a.state, x_hi, A.n[0], A.pitch[0], a.nprob, a.stream));
+    if (x_lo) CK(launch_unpack(A.xl0, A.xl0b, a.state, x_lo, A.n[0], A.pitch[0], a.nprob, a.stream));
   }
   if (rel_res) CK(launch_copy_rel(a.state, rel_res, a.nprob, a.stream));
   return MG_OK;
@@ -522,6 +532,8 @@ mg_status mg_solve(mg_ctx* ctx, const float* b, float* x_hi, float* x_lo, double
   }
   CK(cudaMemsetAsync(a.state, 0, sizeof(ProbState) * a.nprob, a.stream));
   CK(launch_bnorm(a, b));
+  // residual and stopping test of the initial iterate; every cycle ends with those of the new one
+  if (!P.tail_solve) CK(launch_residual(a, (float)rtol, max_cycles));
   std::vector<int> seen(P.nprob, 0);
   const float frtol = (float)rtol;
   int G = 16;
@@ -530,8 +542,7 @@ mg_status mg_solve(mg_ctx* ctx, const float* b, float* x_hi, float* x_lo, double
       CK(launch_tail_solve(a, b, x_hi, xlo, frtol, max_cycles, G, 0));
     } else if (ctx->prof.on) {  // event timing needs individual launches
       for (int c = 0; c < G; ++c) {
-        CK(launch_residual(a, frtol, max_cycles));
-        CK(launch_cycle(a));
+        CK(launch_cycle(a, frtol, max_cycles, c & 1));
       }
     } else {
       cudaGraphExec_t exec;
@@ -565,8 +576,8 @@ mg_status mg_solve(mg_ctx* ctx, const float* b, float* x_hi, float* x_lo, double
     G = next_chunk(ctx->h_state, G, rtol, max_cycles);
   }
   if (!P.tail_solve) {
-    CK(launch_unpack(A.xh0, x_hi, A.n[0], A.pitch[0], a.nprob, a.stream));
-    if (x_lo) CK(launch_unpack(A.xl0, x_lo, A.n[0], A.pitch[0], a.nprob, a.stream));
+    CK(launch_unpack(A.xh0, A.xh0b, a.state, x_hi, A.n[0], A.pitch[0], a.nprob, a.stream));
+    if (x_lo) CK(launch_unpack(A.xl0, A.xl0b, a.state, x_lo, A.n[0], A.pitch[0], a.nprob, a.stream));
     CK(cudaStreamSynchronize(a.stream));
   }
   mg_status rc = MG_OK;

@@ -35,8 +35,9 @@ struct LevelDev {
   float* st;           // SK_FIELD: stencil field [9][n][n]
   float* W;            // HK_TABLE: [9][T][T]; HK_FIELD: [9][n][n]
   float s[9];          // SK_CONST: stencil of this level (Galerkin product of the finer one)
-  int pitch;           // row pitch of r and e in floats (multiple of 32: 128-byte rows)
-  float pad_[2];
+  int pitch;           // row pitch of r, e and f in floats (multiple of 32: 128-byte rows)
+  float* f;            // final correction written by the up-sweep of a tiled level >= 1 (its
+                       // e is still read with halos in the same kernel); e elsewhere
 };
 
 #define MG_DISPATCH(SKv, HKv, CALL)                                                                        \

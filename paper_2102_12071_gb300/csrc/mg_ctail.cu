@@ -59,14 +59,7 @@ __host__ __device__ inline void ct_layout(const int* nl, int ls, int L, int hk, 
     t.off_p[l] = -1;
     if (l > ls && l < lsolo) { t.off_p[l] = o; o += sz; }
   }
-  for (int l = ls; l < L; ++l) {
-    t.a.off_w[l] = o;
-    if (hk == HK_TABLE && l < L - 1) {
-      const int T = nl[l] < MG_PROXY ? nl[l] : MG_PROXY;
-      o += 9 * T * T;
-    }
-  }
-  t.a.total = o;
+  tail_layout_tables(nl, ls, L, hk, o, t.a);
 }
 
 // ------------------------------------------------------------- cluster PTX
@@ -93,17 +86,21 @@ __device__ __forceinline__ float* cluster_map(float* p, int rank) {
 }
 
 // rows [a, b) of a level of side n: work items of one row and 32 columns spread over warps
-#define CT_FOR(a, b, n)                                                                                    \
-  for (int it_ = warp, nch_ = ((n) + 31) >> 5, end_ = ((b) - (a)) * nch_; it_ < end_; it_ += nwarps)   \
-    for (int i = (a) + it_ / nch_, j = (it_ % nch_) * 32 + lane; j < (n); j = (n))
+// (n + 1 is a power of two, so is the number of 32-column chunks per row: shifts, no division)
+#define CT_FOR(a, b, n)                                                                                \
+  for (int it_ = warp, sh_ = 31 - __clz(((n) + 31) >> 5), end_ = ((b) - (a)) << sh_; it_ < end_;        \
+       it_ += nwarps)                                                                                  \
+    for (int i = (a) + (it_ >> sh_), j = ((it_ & ((1 << sh_) - 1)) << 5) + lane; j < (n); j = (n))
 
 // Zero columns, rows outside the grid and solo-level rings; stencil constants, class
-// tables and interior kernels of levels ls .. L-1.
+// tables, interior kernels and the coarsest inverse of levels ls .. L-1.  Ends with a
+// barrier.
 template <int SK, int HK>
 __device__ void ct_prologue(const ProbDev& P, float* sm, const CtLayout& lay, float (*sc)[9], float (*wi)[9], int ls,
                             int L, int rank) {
+  load_level_data<SK, HK>(P, sm, lay.a, sc, ls, L);
   for (int l = ls; l < L; ++l) {
-    const int n = P.lv[l].n, m = n + 2;
+    const int n = lay.a.n[l], m = n + 2;
     const int offs[4] = {lay.a.off_r[l], lay.a.off_e[l], lay.a.off_t[l], lay.off_p[l]};
     if (l < lay.lsolo) {
       const int B = lay.band[l], R = B + 2 * MG_CT_HD, i0 = rank * B;
@@ -131,14 +128,9 @@ __device__ void ct_prologue(const ProbDev& P, float* sm, const CtLayout& lay, fl
         }
       }
     }
-    if (SK == SK_CONST && threadIdx.x < 9) sc[l][threadIdx.x] = P.lv[l].s[threadIdx.x];
-    if (HK == HK_TABLE && l < L - 1) {
-      const int T = P.lv[l].T, cnt = 9 * T * T;
-      for (int t = threadIdx.x; t < cnt; t += blockDim.x) sm[lay.a.off_w[l] + t] = P.lv[l].W[t];
-      if (threadIdx.x < 9 && T == MG_PROXY)
-        wi[l][threadIdx.x] = P.lv[l].W[threadIdx.x * T * T + MG_NET_MARGIN * T + MG_NET_MARGIN];
-    }
   }
+  __syncthreads();
+  load_interior_kernels<HK>(sm, lay.a, wi, ls, L);
   __syncthreads();
 }
 
@@ -148,7 +140,7 @@ __device__ void ct_down(const ProbDev& P, float* sm, const CtLayout& lay, const 
                         const float (*wi)[9], int l, int rank, float omega) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const LevelDev& V = P.lv[l];
-  const int n = V.n, m = n + 2, B = lay.band[l], i0 = rank * B, i1 = min(i0 + B, n);
+  const int n = lay.a.n[l], m = n + 2, B = lay.band[l], i0 = rank * B, i1 = min(i0 + B, n);
   const int o = MG_CT_HD - i0;  // local row of grid row i: i + o
   const float* r = sm + lay.a.off_r[l];
   float* e = sm + lay.a.off_e[l];
@@ -166,7 +158,7 @@ __device__ void ct_down(const ProbDev& P, float* sm, const CtLayout& lay, const 
   __syncthreads();
   // coarse rows [I0, I1) of this CTA: fine rows 2I .. 2I+2 lie in the band and its first
   // lower halo row
-  const int nc = P.lv[l + 1].n, mc = nc + 2, Bc = B >> 1, I0 = rank * Bc, I1 = min(I0 + Bc, nc);
+  const int nc = lay.a.n[l + 1], mc = nc + 2, Bc = B >> 1, I0 = rank * Bc, I1 = min(I0 + Bc, nc);
   float* rc = sm + lay.a.off_r[l + 1];
   if (l + 1 < lay.lsolo) {
     float* up = rank > 0 ? cluster_map(rc, rank - 1) : nullptr;
@@ -193,13 +185,13 @@ __device__ void ct_up(const ProbDev& P, float* sm, const CtLayout& lay, const fl
                       int l, int ls, int rank, float omega) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const LevelDev& V = P.lv[l];
-  const int n = V.n, m = n + 2, B = lay.band[l], i0 = rank * B, i1 = min(i0 + B, n);
+  const int n = lay.a.n[l], m = n + 2, B = lay.band[l], i0 = rank * B, i1 = min(i0 + B, n);
   const int o = MG_CT_HD - i0;
   const float* r = sm + lay.a.off_r[l];
   float* e = sm + lay.a.off_e[l];
   float* t = sm + lay.a.off_t[l];
   const float* w = sm + lay.a.off_w[l];
-  const int mc = P.lv[l + 1].n + 2;
+  const int mc = lay.a.n[l + 1] + 2;
   const bool solo_below = l + 1 == lay.lsolo;
   const float* ec;
   int Io;  // coarse grid row of the first stored row of ec
@@ -259,16 +251,17 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_ctail(const ProbDev* __restri
     ct_layout(nl, ls, L, HK, lay);
   }
   __syncthreads();
+  const float* rtop = P.lv[ls].r;  // before the wait: descriptors do not change
+  const int rpitch = P.lv[ls].pitch;
   ct_prologue<SK, HK>(P, sm, lay, sc, wi, ls, L, rank);
   pdl_wait();
   if (!state[p].active) return;  // the same decision in every CTA of the cluster
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   {
-    const LevelDev& V = P.lv[ls];
-    const int n = V.n, m = n + 2, i0 = rank * lay.band[ls];
+    const int n = lay.a.n[ls], m = n + 2, i0 = rank * lay.band[ls];
     const int a = max(0, i0 - MG_CT_HD), b = min(n, i0 + lay.band[ls] + MG_CT_HD);
     float* r = sm + lay.a.off_r[ls];
-    CT_FOR(a, b, n) r[(i - i0 + MG_CT_HD) * m + j + 1] = V.r[(size_t)i * V.pitch + j];
+    CT_FOR(a, b, n) r[(i - i0 + MG_CT_HD) * m + j + 1] = rtop[(size_t)i * rpitch + j];
   }
   cluster_sync();  // every CTA of the cluster is running with its exterior zeroed
   const int lsolo = lay.lsolo;

@@ -75,10 +75,18 @@ struct DownMaps {
 struct UpMaps {
   CUtensorMap e, r, ec, xh, xl;
 };
+// level 0: up-sweep, update of x and the residual of the new iterate in one kernel
+struct Up0Maps {
+  CUtensorMap e, r, ec;  // boxes one point wider than UpMaps' (the update covers a halo)
+  ResMaps x;             // x_hi, x_lo with a one-point halo, b
+};
 struct TileMaps {
   ResMaps res;
   DownMaps down[MG_MAXL];
   UpMaps up[MG_MAXL];
+  Up0Maps up0;
+  CUtensorMap down0_rb, up0_rb;  // level-0 residual loads of odd cycles (from r0b)
+  ResMaps resb;                  // x loads of odd cycles (from xh0b, xl0b)
 };
 
 // base pointers of the pitched level arrays (all problems of a level contiguous)
@@ -86,7 +94,10 @@ struct LevelArrays {
   int n[MG_MAXL], pitch[MG_MAXL];
   float* r[MG_MAXL];
   float* e[MG_MAXL];
+  float* f[MG_MAXL];      // final corrections of the tiled levels >= 1 (LevelDev::f)
   float *xh0, *xl0, *b0;  // the iterate pair and right-hand side, pitched like level 0
+  float *xh0b, *xl0b;     // second iterate pair: cycles alternate the two pairs
+  float* r0b;             // second level-0 residual: cycles alternate r[0] and r0b
 };
 
 struct CycleArgs {
@@ -103,7 +114,9 @@ struct CycleArgs {
   const int* active;  // device list of the problems cycle launches cover (nullptr: all)
   int nactive;
   const TileMaps* maps;  // host copy of the tensor maps (tiled levels)
-  float *xh0, *xl0;      // pitched iterate pair of the tiled path
+  float *xh0, *xl0;      // pitched iterate pair of the tiled path (read by even cycles)
+  float *xh0b, *xl0b;    // the second pair (read by odd cycles, written by even ones)
+  float *r0a, *r0b;      // the two level-0 residual arrays
   bool pdl;              // launch the cycle chain with programmatic dependencies
   int ctail;             // levels >= lstar in one CTA cluster per problem (mg_ctail.cu)
 };
@@ -149,12 +162,18 @@ int tiles_per_side(int n);
 size_t tail_smem_bytes(const int* nl, int l0, int L, int hk);
 
 cudaError_t launch_bnorm(const CycleArgs& a, const float* b);
-// tiled path (mg_tiles.cu): residual of the pitched iterate, and one V-cycle below it
+// tiled path (mg_tiles.cu): residual of the pitched iterate with the stopping test, and
+// one V-cycle below it ending with the same residual and test for the new iterate
 cudaError_t launch_residual(const CycleArgs& a, float rtol, int max_cycles);
-cudaError_t launch_cycle(const CycleArgs& a);
+// cycle `parity` reads the level-0 residual and the iterate from r[0], (xh0, xl0) (0) or
+// r0b, (xh0b, xl0b) (1) and writes the new ones to the other arrays: the fused level-0
+// kernel reads both with halos, so it must not overwrite them in place
+cudaError_t launch_cycle(const CycleArgs& a, float rtol, int max_cycles, int parity);
 bool build_tile_maps(TileMaps& maps, const LevelArrays& arrays, int nprob, int lstar);
 cudaError_t launch_pack(const float* src, float* dst, int n, int pitch, int nprob, cudaStream_t s);
-cudaError_t launch_unpack(const float* src, float* dst, int n, int pitch, int nprob, cudaStream_t s);
+// dst <- src_a, or src_b for the problems whose count of applied cycles is odd
+cudaError_t launch_unpack(const float* src_a, const float* src_b, const ProbState* state, float* dst, int n, int pitch,
+                          int nprob, cudaStream_t s);
 // coarse tail from level a.lstar: one CTA per problem (mg_cycle.cu), or the cluster tail
 // when a.ctail is set; prepare_tail sets launch attributes (call it outside stream capture)
 cudaError_t launch_tail(const CycleArgs& a);

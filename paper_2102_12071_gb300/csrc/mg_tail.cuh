@@ -11,9 +11,28 @@ namespace mg {
 // level vector is stored with a one-point ring of zeros (side n+2), so stencil, smoother
 // and transfer taps need no bounds checks: the ring is the Dirichlet exterior.
 struct TailLayout {
+  int n[MG_MAXL];  // level sides
   int off_r[MG_MAXL], off_e[MG_MAXL], off_t[MG_MAXL], off_w[MG_MAXL];
-  int total;
+  int off_inv;     // FP64 inverse of the coarsest operator (8-byte aligned)
+  int total;       // floats
 };
+
+// class tables and the coarsest inverse after the level vectors starting at float offset o
+__host__ __device__ inline void tail_layout_tables(const int* nl, int l0, int L, int hk, int o, TailLayout& t) {
+  for (int l = 0; l < L; ++l) t.n[l] = nl[l];
+  for (int l = l0; l < L; ++l) {
+    t.off_w[l] = o;
+    if (hk == HK_TABLE && l < L - 1) {
+      const int T = nl[l] < MG_PROXY ? nl[l] : MG_PROXY;
+      o += 9 * T * T;
+    }
+  }
+  o = (o + 1) & ~1;
+  t.off_inv = o;
+  const int mm = nl[L - 1] * nl[L - 1];
+  o += 2 * mm * mm;
+  t.total = o;
+}
 
 __host__ __device__ inline void tail_layout(const int* nl, int l0, int L, int hk, TailLayout& t) {
   int o = 0;
@@ -23,14 +42,7 @@ __host__ __device__ inline void tail_layout(const int* nl, int l0, int L, int hk
     t.off_e[l] = o; o += m * m;
     t.off_t[l] = o; o += m * m;
   }
-  for (int l = l0; l < L; ++l) {
-    t.off_w[l] = o;
-    if (hk == HK_TABLE && l < L - 1) {
-      const int T = nl[l] < MG_PROXY ? nl[l] : MG_PROXY;
-      o += 9 * T * T;
-    }
-  }
-  t.total = o;
+  tail_layout_tables(nl, l0, L, hk, o, t);
 }
 
 // A v at (i, j); c points at v(i, j) inside a ring-padded array of row stride m
@@ -110,7 +122,7 @@ __device__ void tail_cycle(const ProbDev& P, float* sm, const TailLayout& lay, c
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   for (int l = l0; l < L - 1; ++l) {
     const LevelDev& Lv = P.lv[l];
-    const int n = Lv.n, m = n + 2, nc = P.lv[l + 1].n, mc = nc + 2;
+    const int n = lay.n[l], m = n + 2, nc = lay.n[l + 1], mc = nc + 2;
     float* r = sm + lay.off_r[l];
     float* e = sm + lay.off_e[l];
     float* t = sm + lay.off_t[l];
@@ -131,11 +143,11 @@ __device__ void tail_cycle(const ProbDev& P, float* sm, const TailLayout& lay, c
     __syncthreads();
   }
   {
-    const int nL = P.lv[L - 1].n, mL = nL + 2, mm = P.m;
+    const int nL = lay.n[L - 1], mL = nL + 2, mm = nL * nL;
     const float* r = sm + lay.off_r[L - 1];
     float* e = sm + lay.off_e[L - 1];
     if ((int)threadIdx.x < mm) {
-      const double* Ai = P.chol + threadIdx.x * mm;
+      const double* Ai = reinterpret_cast<const double*>(sm + lay.off_inv) + threadIdx.x * mm;
       double acc = 0.0;
       for (int k = 0; k < mm; ++k) acc = fma(Ai[k], (double)r[(k / nL + 1) * mL + k % nL + 1], acc);
       e[(threadIdx.x / nL + 1) * mL + threadIdx.x % nL + 1] = (float)acc;
@@ -144,7 +156,7 @@ __device__ void tail_cycle(const ProbDev& P, float* sm, const TailLayout& lay, c
   }
   for (int l = L - 2; l >= l0; --l) {
     const LevelDev& Lv = P.lv[l];
-    const int n = Lv.n, m = n + 2, mc = P.lv[l + 1].n + 2;
+    const int n = lay.n[l], m = n + 2, mc = lay.n[l + 1] + 2;
     float* r = sm + lay.off_r[l];
     float* e = sm + lay.off_e[l];
     float* t = sm + lay.off_t[l];
@@ -165,12 +177,80 @@ __device__ void tail_cycle(const ProbDev& P, float* sm, const TailLayout& lay, c
   }
 }
 
-// Zero rings, stencil constants, class tables and interior kernels of levels l0 .. L-1.
+// Stencil constants, class tables of levels l0 .. L-2 and the coarsest inverse into shared
+// memory.  Every thread issues all of its global loads before its stores, so their
+// latencies overlap (copying level by level would wait on each level in turn).
+template <int SK, int HK>
+__device__ void load_level_data(const ProbDev& P, float* sm, const TailLayout& lay, float (*sc)[9], int l0, int L) {
+  __shared__ const float* src[MG_MAXL];
+  __shared__ int pre[MG_MAXL + 1], dst[MG_MAXL];
+  const int nq = L - l0;  // entries: the tables of levels l0 .. L-2, then the inverse
+  if ((int)threadIdx.x < nq) {
+    const int q = threadIdx.x, l = l0 + q;
+    src[q] = q < nq - 1 ? (HK == HK_TABLE ? P.lv[l].W : nullptr) : reinterpret_cast<const float*>(P.chol);
+    dst[q] = q < nq - 1 ? lay.off_w[l] : lay.off_inv;
+  }
+  if (SK == SK_CONST && (int)threadIdx.x < 9 * nq) sc[l0 + threadIdx.x / 9][threadIdx.x % 9] = P.lv[l0 + threadIdx.x / 9].s[threadIdx.x % 9];
+  if (threadIdx.x == 0) {
+    int o = 0;
+    for (int q = 0; q < nq; ++q) {
+      pre[q] = o;
+      const int l = l0 + q;
+      if (q < nq - 1) {
+        if (HK == HK_TABLE) {
+          const int T = lay.n[l] < MG_PROXY ? lay.n[l] : MG_PROXY;
+          o += 9 * T * T;
+        }
+      } else {
+        const int mm = lay.n[L - 1] * lay.n[L - 1];
+        o += 2 * mm * mm;
+      }
+    }
+    pre[nq] = o;
+  }
+  __syncthreads();
+  const int total = pre[nq];
+  constexpr int U = 4;
+  for (int base = threadIdx.x; base < total; base += U * blockDim.x) {
+    float v[U];
+    int d[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = base + u * blockDim.x;
+      d[u] = -1;
+      if (k < total) {
+        int q = 0;
+        while (k >= pre[q + 1]) ++q;
+        v[u] = __ldg(src[q] + (k - pre[q]));
+        d[u] = dst[q] + (k - pre[q]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (d[u] >= 0) sm[d[u]] = v[u];
+  }
+}
+
+// interior network kernel of each table level, from the shared-memory tables
+template <int HK>
+__device__ __forceinline__ void load_interior_kernels(const float* sm, const TailLayout& lay, float (*wi)[9], int l0,
+                                                      int L) {
+  if (HK != HK_TABLE) return;
+  const int q = threadIdx.x / 9, k = threadIdx.x % 9, l = l0 + q;
+  if (l < L - 1 && lay.n[l] >= MG_PROXY) {
+    const int T = MG_PROXY, M = MG_NET_MARGIN;
+    wi[l][k] = sm[lay.off_w[l] + k * T * T + M * T + M];
+  }
+}
+
+// Zero rings, stencil constants, class tables, interior kernels and the coarsest inverse of
+// levels l0 .. L-1; ends with a barrier.
 template <int SK, int HK>
 __device__ void tail_prologue(const ProbDev& P, float* sm, const TailLayout& lay, float (*sc)[9], float (*wi)[9],
                               int l0, int L) {
+  load_level_data<SK, HK>(P, sm, lay, sc, l0, L);
   for (int l = l0; l < L; ++l) {
-    const int m = P.lv[l].n + 2;
+    const int m = lay.n[l] + 2;
     const int offs[3] = {lay.off_r[l], lay.off_e[l], lay.off_t[l]};
     for (int a = 0; a < 3; ++a) {
       float* v = sm + offs[a];
@@ -181,18 +261,10 @@ __device__ void tail_prologue(const ProbDev& P, float* sm, const TailLayout& lay
         v[k * m + m - 1] = 0.f;
       }
     }
-    if (SK == SK_CONST && threadIdx.x < 9) sc[l][threadIdx.x] = P.lv[l].s[threadIdx.x];
-    if (HK == HK_TABLE && l < L - 1) {
-      const int T = P.lv[l].T;
-      const int cnt = 9 * T * T;
-      for (int t = threadIdx.x; t < cnt; t += blockDim.x) sm[lay.off_w[l] + t] = P.lv[l].W[t];
-      if (threadIdx.x < 9 && T == MG_PROXY) {
-        const int M = MG_NET_MARGIN;
-        wi[l][threadIdx.x] = P.lv[l].W[threadIdx.x * T * T + M * T + M];
-      }
-    }
   }
+  __syncthreads();
+  load_interior_kernels<HK>(sm, lay, wi, l0, L);
+  __syncthreads();
 }
-
 
 }  // namespace mg

@@ -38,6 +38,9 @@ constexpr int UPR_H = TB + 2;    // k_up r box: rows R0-1 .. R0+32
 constexpr int EC_W = TB / 2 + 8; // k_up coarse box: columns C0/2-4 .. C0/2+19
 constexpr int EC_H = TB / 2 + 3; //                  rows    R0/2-2 .. R0/2+16
 constexpr int ES = TB + 3;       // k_down e buffer side (rows/cols R0-1 .. R0+33)
+constexpr int UP0E_H = TB + 6;   // k_up0 e box: rows R0-3 .. R0+34
+constexpr int UP0R_H = TB + 4;   // k_up0 r box: rows R0-2 .. R0+33
+constexpr int EC0_H = TB / 2 + 4; // k_up0 coarse box: rows R0/2-2 .. R0/2+17
 // a tile is "inner" when every point its kernels evaluate lies inside the grid and at
 // least MG_NET_MARGIN from the edges: no masking, interior network kernel in registers
 constexpr int INNER = 8;
@@ -160,9 +163,12 @@ __device__ __forceinline__ void dot2_sub(float a, float x, float xl, float& hi, 
 // ------------------------------------------------------------------ k_residual
 // Thread = column of the tile (lane) x strip of 4 rows (warp); 3x3 windows of x_hi and x_lo
 // slide down the strip in registers.
+// With xo_hi/xo_lo (level-0 pitched arrays of problem p) it also stores the iterate of
+// the owned points.
 template <int SK, bool IN>
 __device__ __forceinline__ float residual_tile(const LevelDev& L, const float (&s)[9], const float* XH,
-                                               const float* XL, const float* BB, int R0, int C0) {
+                                               const float* XL, const float* BB, int R0, int C0, float* rdst,
+                                               float* xo_hi = nullptr, float* xo_lo = nullptr) {
   constexpr int KS = TB / NW;
   const int n = L.n, pitch = L.pitch;
   const int tj = threadIdx.x & 31, t0 = (threadIdx.x >> 5) * KS, j = C0 + tj;
@@ -172,7 +178,8 @@ __device__ __forceinline__ float residual_tile(const LevelDev& L, const float (&
   h.load_ab(ch, XW);
   l.load_ab(cl, XW);
   float acc = 0.f;
-  float* rout = L.r + (size_t)(R0 + t0) * pitch + j;
+  const size_t g0 = (size_t)(R0 + t0) * pitch + j;
+  float* rout = rdst + g0;
 #pragma unroll
   for (int k = 0; k < KS; ++k) {
     h.load_c(ch + k * XW, XW);
@@ -202,6 +209,10 @@ __device__ __forceinline__ float residual_tile(const LevelDev& L, const float (&
       const float r = hi + lo;
       rout[k * pitch] = r;
       acc = fmaf(r, r, acc);
+      if (xo_hi) {
+        xo_hi[g0 + (size_t)k * pitch] = h.b1;
+        xo_lo[g0 + (size_t)k * pitch] = l.b1;
+      }
     }
     h.shift();
     l.shift();
@@ -241,8 +252,8 @@ __global__ void __launch_bounds__(NT) k_residual(const __grid_constant__ ResMaps
   }
   __syncthreads();
   if (!tile_wait(&bar, state[p])) return;
-  const float acc = inner_tile(R0, C0, n) ? residual_tile<SK, true>(L, s, XH, XL, BB, R0, C0)
-                                          : residual_tile<SK, false>(L, s, XH, XL, BB, R0, C0);
+  const float acc = inner_tile(R0, C0, n) ? residual_tile<SK, true>(L, s, XH, XL, BB, R0, C0, L.r)
+                                          : residual_tile<SK, false>(L, s, XH, XL, BB, R0, C0, L.r);
   float rhi, rlo;
   if (block_partial_and_last<NT>(acc, partials + (size_t)p * ntiles_max, &state[p].counter, ntiles, tile, rhi, rlo)) {
     if (threadIdx.x == 0) decide(state[p], rhi, rlo, rtol, max_cycles);
@@ -434,7 +445,7 @@ __device__ __forceinline__ void up_tile(const LevelDev& L, const float (&s)[9], 
           xhi[g] = hi;
           xlo[g] = lo;
         } else {
-          L.e[row0 + (size_t)k * pitch] = e;
+          L.f[row0 + (size_t)k * pitch] = e;  // e is still read with halos by other CTAs
         }
       }
       if (HK != HK_JACOBI) v.shift();
@@ -486,6 +497,141 @@ __global__ void __launch_bounds__(NT) k_up(const __grid_constant__ UpMaps M, con
   else up_tile<SK, HK, UPDX, false>(L, s, wtab, wi, omega, es, rs, ecs, xhs, xls, xhi, xlo, p, R0, C0);
 }
 
+// ----------------------------------------------------------------- k_up0
+// Level 0: the up-sweep of k_up computed one point wider (e1 on rows/cols R0-3 .. R0+34,
+// t on R0-2 .. R0+33, e on R0-1 .. R0+32), the float-float update of x on the tile and its
+// halo in shared memory, then the compensated residual of the new iterate on the tile,
+// the norm partial and the stopping test: the residual of the next cycle without
+// re-reading x.
+template <int SK, int HK, bool IN>
+__device__ __forceinline__ void up0_tile(const LevelDev& L, const float (&s)[9], const float* wtab,
+                                         const float (&wi)[9], float omega, float* es, float* rs, const float* ecs,
+                                         float* xh, float* xl, int R0, int C0) {
+  const int n = L.n, t = threadIdx.x;
+  {
+    constexpr int W1 = TB + 6, KS = 7, NS = (W1 + KS - 1) / KS;
+    if (t < W1 * NS) {
+      const int tj = t % W1, t0 = (t / W1) * KS, j = C0 - 3 + tj;
+      const int I0 = R0 / 2 - 2, J0 = C0 / 2 - 4;
+      const int ja = ((j - 1) >> 1) - J0, jb = (j >> 1) - J0;
+#pragma unroll
+      for (int k = 0; k < KS; ++k) {
+        const int ti = t0 + k, i = R0 - 3 + ti;
+        if (ti < W1) {
+          const float* ra = ecs + (((i - 1) >> 1) - I0) * EC_W;
+          const float* rb = ecs + ((i >> 1) - I0) * EC_W;
+          es[ti * XW + tj + 1] += 0.25f * ((ra[ja] + ra[jb]) + (rb[ja] + rb[jb]));
+        }
+      }
+    }
+  }
+  __syncthreads();
+  {
+    constexpr int W2 = TB + 4, KS = 6, NS = W2 / KS;
+    if (t < W2 * NS) {
+      const int tj = t % W2, t0 = (t / W2) * KS, j = C0 - 2 + tj;
+      const float* c = es + (t0 + 1) * XW + tj + 2;
+      float* rp = rs + t0 * XW + tj + 2;
+      Win v;
+      v.load_ab(c, XW);
+#pragma unroll
+      for (int k = 0; k < KS; ++k) {
+        const int i = R0 - 2 + t0 + k;
+        v.load_c(c + k * XW, XW);
+        float tv = 0.f;
+        if (IN || inside(i, j, n)) tv = rp[k * XW] - tapply_A<SK>(L, s, i, j, v);
+        rp[k * XW] = tv;
+        v.shift();
+      }
+    }
+  }
+  __syncthreads();
+  {
+    constexpr int W3 = TB + 2, KS = 5, NS = (W3 + KS - 1) / KS;
+    if (t < W3 * NS) {
+      const int tj = t % W3, t0 = (t / W3) * KS, j = C0 - 1 + tj;
+      const float* c = rs + (t0 + 1) * XW + tj + 3;
+      const float* e1 = es + (t0 + 2) * XW + tj + 3;
+      float* ph = xh + t0 * XW + tj + 3;
+      float* pl = xl + t0 * XW + tj + 3;
+      Win v;
+      if (HK != HK_JACOBI) v.load_ab(c, XW);
+#pragma unroll
+      for (int k = 0; k < KS; ++k) {
+        const int ti = t0 + k, i = R0 - 1 + ti;
+        if (ti < W3) {
+          if (HK != HK_JACOBI) v.load_c(c + k * XW, XW);
+          else v.b1 = c[k * XW];
+          if (IN || inside(i, j, n)) {
+            const float e = e1[k * XW] + tapply_H<SK, HK, IN>(L, s, wtab, wi, omega, i, j, v);
+            float hi = ph[k * XW], lo = pl[k * XW], sum, err;
+            two_sum(hi, e, sum, err);
+            err += lo;
+            fast_two_sum(sum, err, hi, lo);
+            ph[k * XW] = hi;
+            pl[k * XW] = lo;
+          }
+          if (HK != HK_JACOBI) v.shift();
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <int SK, int HK>
+__global__ void __launch_bounds__(NT) k_up0(const __grid_constant__ Up0Maps M, const ProbDev* __restrict__ probs,
+                                            ProbState* __restrict__ state, float* __restrict__ partials,
+                                            int ntiles_max, float omega, float rtol, int max_cycles,
+                                            float* __restrict__ xhi, float* __restrict__ xlo,
+                                            float* __restrict__ rnew, const int* __restrict__ act) {
+  pdl_trigger();
+  const int p = act ? act[blockIdx.y] : blockIdx.y;
+  const LevelDev L = probs[p].lv[0];
+  const int n = L.n;
+  const int ntx = (n + TB - 1) / TB, ntiles = ntx * ntx;
+  const int tile = blockIdx.x;
+  if (tile >= ntiles) return;
+  const int R0 = (tile / ntx) * TB, C0 = (tile % ntx) * TB;
+  __shared__ __align__(128) float es[UP0E_H * XW];  // e, then e1 = e + P e_c in place
+  __shared__ __align__(128) float rs[UP0R_H * XW];  // r, then t = r - A e1 in place
+  __shared__ __align__(128) float ecs[EC0_H * EC_W];
+  __shared__ __align__(128) float xh[RES_H * XW];   // x on the tile and its halo, updated in place
+  __shared__ __align__(128) float xl[RES_H * XW];
+  __shared__ __align__(128) float bb[TB * TB];
+  __shared__ float wtab[HK == HK_TABLE ? 9 * MG_PROXY * MG_PROXY : 1];
+  __shared__ __align__(8) uint64_t bar;
+  const bool in = inner_tile(R0, C0, n);
+  float s[9], wi[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) s[k] = (SK == SK_CONST) ? L.s[k] : 0.f;
+  if (HK == HK_TABLE) load_table(L, in, wtab, wi);
+  pdl_wait();
+  if (!state[p].active) return;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    mbar_arrive_expect_tx(&bar, ((UP0E_H + UP0R_H + 2 * RES_H) * XW + EC0_H * EC_W + TB * TB) * sizeof(float));
+    tma_load_3d(es, &M.e, &bar, C0 - 4, R0 - 3, p);
+    tma_load_3d(rs, &M.r, &bar, C0 - 4, R0 - 2, p);
+    tma_load_3d(ecs, &M.ec, &bar, C0 / 2 - 4, R0 / 2 - 2, p);
+    tma_load_3d(xh, &M.x.xh, &bar, C0 - 4, R0 - 1, p);
+    tma_load_3d(xl, &M.x.xl, &bar, C0 - 4, R0 - 1, p);
+    tma_load_3d(bb, &M.x.b, &bar, C0, R0, p);
+  }
+  __syncthreads();
+  if (!tile_wait(&bar, state[p])) return;
+  if (in) up0_tile<SK, HK, true>(L, s, wtab, wi, omega, es, rs, ecs, xh, xl, R0, C0);
+  else up0_tile<SK, HK, false>(L, s, wtab, wi, omega, es, rs, ecs, xh, xl, R0, C0);
+  const size_t po = (size_t)p * n * L.pitch;
+  const float acc = in ? residual_tile<SK, true>(L, s, xh, xl, bb, R0, C0, rnew + po, xhi + po, xlo + po)
+                       : residual_tile<SK, false>(L, s, xh, xl, bb, R0, C0, rnew + po, xhi + po, xlo + po);
+  float rhi, rlo;
+  if (block_partial_and_last<NT>(acc, partials + (size_t)p * ntiles_max, &state[p].counter, ntiles, tile, rhi, rlo)) {
+    if (threadIdx.x == 0) decide(state[p], rhi, rlo, rtol, max_cycles);
+  }
+}
+
 // -------------------------------------------------------------- pack / unpack
 // dense [nprob][n][n] <-> pitched [nprob][n][pitch]; src == nullptr packs zeros
 __global__ void k_pack(const float* __restrict__ src, float* __restrict__ dst, int n, int pitch) {
@@ -496,11 +642,13 @@ __global__ void k_pack(const float* __restrict__ src, float* __restrict__ dst, i
   dst[(size_t)p * n * pitch + (size_t)i * pitch + j] = src ? src[(size_t)p * n * n + q] : 0.f;
 }
 
-__global__ void k_unpack(const float* __restrict__ src, float* __restrict__ dst, int n, int pitch) {
+__global__ void k_unpack(const float* __restrict__ src_a, const float* __restrict__ src_b,
+                         const ProbState* __restrict__ state, float* __restrict__ dst, int n, int pitch) {
   const int p = blockIdx.y;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n * n) return;
   const int i = q / n, j = q % n;
+  const float* src = (state[p].cycles & 1) ? src_b : src_a;
   dst[(size_t)p * n * n + q] = src[(size_t)p * n * pitch + (size_t)i * pitch + j];
 }
 
@@ -510,9 +658,10 @@ cudaError_t launch_pack(const float* src, float* dst, int n, int pitch, int npro
   return cudaGetLastError();
 }
 
-cudaError_t launch_unpack(const float* src, float* dst, int n, int pitch, int nprob, cudaStream_t s) {
+cudaError_t launch_unpack(const float* src_a, const float* src_b, const ProbState* state, float* dst, int n, int pitch,
+                          int nprob, cudaStream_t s) {
   dim3 grid((n * n + 255) / 256, nprob);
-  k_unpack<<<grid, 256, 0, s>>>(src, dst, n, pitch);
+  k_unpack<<<grid, 256, 0, s>>>(src_a, src_b, state, dst, n, pitch);
   return cudaGetLastError();
 }
 
@@ -554,14 +703,23 @@ bool build_tile_maps(TileMaps& T, const LevelArrays& A, int nprob, int lstar) {
          make_map(&T.down[l].rc, A.r[l + 1], A.n[l + 1], A.pitch[l + 1], nprob, TC, TC) &&
          make_map(&T.up[l].e, A.e[l], A.n[l], A.pitch[l], nprob, XW, UPE_H) &&
          make_map(&T.up[l].r, A.r[l], A.n[l], A.pitch[l], nprob, XW, UPR_H) &&
-         make_map(&T.up[l].ec, A.e[l + 1], A.n[l + 1], A.pitch[l + 1], nprob, EC_W, EC_H);
-    if (ok && l == 0)
-      ok = make_map(&T.up[0].xh, A.xh0, A.n[0], A.pitch[0], nprob, TB, TB) &&
-           make_map(&T.up[0].xl, A.xl0, A.n[0], A.pitch[0], nprob, TB, TB);
-    else if (ok) {
-      T.up[l].xh = T.up[l].e;  // unused on levels >= 1
+         make_map(&T.up[l].ec, l + 1 < lstar ? A.f[l + 1] : A.e[l + 1], A.n[l + 1], A.pitch[l + 1], nprob, EC_W,
+                  EC_H);
+    if (ok) {
+      T.up[l].xh = T.up[l].e;  // the x update is on level 0's fused kernel
       T.up[l].xl = T.up[l].e;
     }
+  }
+  if (ok) {
+    ok = make_map(&T.up0.e, A.e[0], A.n[0], A.pitch[0], nprob, XW, UP0E_H) &&
+         make_map(&T.up0.r, A.r[0], A.n[0], A.pitch[0], nprob, XW, UP0R_H) &&
+         make_map(&T.up0.ec, 1 < lstar ? A.f[1] : A.e[1], A.n[1], A.pitch[1], nprob, EC_W, EC0_H) &&
+         make_map(&T.down0_rb, A.r0b, A.n[0], A.pitch[0], nprob, XW, DN_H) &&
+         make_map(&T.up0_rb, A.r0b, A.n[0], A.pitch[0], nprob, XW, UP0R_H);
+    T.up0.x = T.res;
+    ok = ok && make_map(&T.resb.xh, A.xh0b, A.n[0], A.pitch[0], nprob, XW, RES_H) &&
+         make_map(&T.resb.xl, A.xl0b, A.n[0], A.pitch[0], nprob, XW, RES_H);
+    T.resb.b = T.res.b;
   }
   return ok;
 }
@@ -585,7 +743,7 @@ cudaError_t launch_residual(const CycleArgs& a, float rtol, int max_cycles) {
   return e;
 }
 
-cudaError_t launch_cycle(const CycleArgs& a) {
+cudaError_t launch_cycle(const CycleArgs& a, float rtol, int max_cycles, int parity) {
   const int ls = a.lstar, np = nlaunch(a);
   const ProbDev* probs = a.probs;
   float* const nul = nullptr;
@@ -595,9 +753,11 @@ cudaError_t launch_cycle(const CycleArgs& a) {
     dim3 grid(nt * nt, np);
     a.prof->launches++;
     a.prof->begin(l == 0 ? PK_DOWN0 : PK_DOWN, a.stream);
+    DownMaps dm = a.maps->down[l];
+    if (l == 0 && parity) dm.r = a.maps->down0_rb;
     MG_DISPATCH(a.sk, a.hk,
-                (e = launch_pdl(a.pdl, k_down<SK_, HK_>, grid, dim3(NT), 0, a.stream, a.maps->down[l], probs, a.state, l,
-                                a.omega, a.active)));
+                (e = launch_pdl(a.pdl, k_down<SK_, HK_>, grid, dim3(NT), 0, a.stream, dm, probs, a.state, l, a.omega,
+                                a.active)));
     a.prof->end(a.stream);
   }
   if (e != cudaSuccess) return e;
@@ -611,10 +771,19 @@ cudaError_t launch_cycle(const CycleArgs& a) {
     const bool pdl = a.pdl && !(a.ctail && l == ls - 1);
     a.prof->launches++;
     a.prof->begin(l == 0 ? PK_UP0 : PK_UP, a.stream);
-    if (l == 0)
+    if (l == 0) {
+      Up0Maps um = a.maps->up0;
+      if (parity) {
+        um.r = a.maps->up0_rb;
+        um.x = a.maps->resb;
+      }
+      float* rnew = parity ? a.r0a : a.r0b;
+      float* xhn = parity ? a.xh0 : a.xh0b;
+      float* xln = parity ? a.xl0 : a.xl0b;
       MG_DISPATCH(a.sk, a.hk,
-                  (e = launch_pdl(pdl, k_up<SK_, HK_, true>, grid, dim3(NT), 0, a.stream, a.maps->up[0], probs, a.state, 0,
-                                  a.omega, a.xh0, a.xl0, a.active)));
+                  (e = launch_pdl(pdl, k_up0<SK_, HK_>, grid, dim3(NT), 0, a.stream, um, probs, a.state, a.partials,
+                                  a.ntiles_max, a.omega, rtol, max_cycles, xhn, xln, rnew, a.active)));
+    }
     else
       MG_DISPATCH(a.sk, a.hk,
                   (e = launch_pdl(pdl, k_up<SK_, HK_, false>, grid, dim3(NT), 0, a.stream, a.maps->up[l], probs, a.state,

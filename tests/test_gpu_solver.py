@@ -246,3 +246,21 @@ def test_batch_solve_is_deterministic():
         np.testing.assert_array_equal(cyc, runs[0][3])
         np.testing.assert_array_equal(np.nan_to_num(gh, nan=-1.0), np.nan_to_num(runs[0][2], nan=-1.0))
         assert torch.equal(xh, runs[0][0]) and torch.equal(xl, runs[0][1])
+
+
+@pytest.mark.parametrize("ct", [True, False])
+def test_bench_batch_first_cycles_match_oracle(ct):
+    """The 16-problem 1023^2 bench batch: every tiled level runs in several waves of CTAs
+    (level 0: 16384 tiles, level 1: 4096), so a kernel that overwrote an array other CTAs
+    still read with halos would show here.  Problems 0 and 9 (the slowest Jacobi one)
+    against the oracle over the first cycles."""
+    n, cycles = 1023, 3
+    params = inputs.rotated_params(inputs.SEED_PARAMS, 16)
+    b = torch.from_numpy(np.stack([inputs.rhs_uniform(inputs.SEED_RHS + i, n) for i in range(16)])).cuda()
+    mg = S.MultigridSolver([S.rotated(n, e, t) for e, t in params], cluster_tail=ct)
+    _, _, gh, cyc, _ = mg.solve(b.contiguous(), rtol=0.0, max_cycles=cycles)
+    assert np.all(cyc == cycles)
+    for p in (0, 9):
+        om = O.Multigrid(oracle_rotated(n, *params[p]))
+        _, oh = om.solve(f32(b[p].cpu().numpy()), rtol=0.0, max_cycles=cycles)
+        assert _cmp_hist(gh[p], oh) == cycles + 1
