@@ -194,42 +194,203 @@ def cpu_baseline(n: int, budget_s: float = 12.0):
             "sample": f"{cycles} V(1,1) Jacobi cycles of one {n}^2 problem (FP64, single thread)"}
 
 
+def load_varcoef_weights():
+    """Network trained on the GRF family, else the rotated one (name, device tensor) or None."""
+    import numpy as np
+    import torch
+
+    for name in ("cnn_varcoef.npy", "cnn_rotated.npy"):
+        path = os.path.join(os.path.dirname(WEIGHTS), name)
+        if os.path.exists(path):
+            return name, torch.from_numpy(np.load(path).astype(np.float32)).cuda()
+    return None
+
+
+def timed_solve(mg, b, reps: int = 1):
+    """Event-timed solves to RTOL after two warm-up solves: (ms per solve, cycles, status)."""
+    import torch
+
+    for _ in range(2):
+        mg.solve(b, rtol=RTOL, max_cycles=MAX_CYCLES, history=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        _, _, _, cyc, st = mg.solve(b, rtol=RTOL, max_cycles=MAX_CYCLES, history=False)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, cyc, st
+
+
 def run_varcoef(args, rank):
     """Variable-coefficient diffusion -div(a grad u), a = exp(GRF), 5-point stencil: one
-    problem of side args.varcoef_n solved to 1e-8 with the CNN and with Jacobi (C4)."""
-    import numpy as np
+    problem per size in args.varcoef_n solved to 1e-8 with the CNN and with Jacobi (C4)."""
     import torch
 
     from paper_2102_12071_gb300 import inputs, solver as S
 
-    n = args.varcoef_n
-    cells = torch.from_numpy(inputs.grf_cells(inputs.SEED_GRF + rank, n)).cuda()
-    b = torch.from_numpy(inputs.rhs_uniform(inputs.SEED_RHS + 500 + rank, n)).cuda()[None].contiguous()
-    w = None
-    for name in ("cnn_varcoef.npy", "cnn_rotated.npy"):
-        path = os.path.join(os.path.dirname(WEIGHTS), name)
-        if os.path.exists(path):
-            w = torch.from_numpy(np.load(path).astype(np.float32)).cuda()
-            wname = name
-            break
-    out = {"n": n, "problem": "GRF a = exp(g), unit variance, correlation length 1/16, 5-point", "rtol": RTOL}
-    kinds = ["jacobi"] + (["cnn"] if w is not None else [])
-    for kind in kinds:
-        mg = S.MultigridSolver([S.varcoef5(n, cells)], kind, net_params=w if kind == "cnn" else None)
-        for _ in range(2):
-            mg.solve(b, rtol=RTOL, max_cycles=MAX_CYCLES, history=False)
+    wv = load_varcoef_weights()
+    out = {"problem": "GRF a = exp(g), unit variance, correlation length 1/16, 5-point", "rtol": RTOL}
+    if wv is not None:
+        out["weights"] = wv[0]
+    for n in [int(v) for v in str(args.varcoef_n).split(",") if int(v) > 0]:
+        cells = torch.from_numpy(inputs.grf_cells(inputs.SEED_GRF + rank, n)).cuda()
+        b = torch.from_numpy(inputs.rhs_uniform(inputs.SEED_RHS + 500 + rank, n)).cuda()[None].contiguous()
+        res = {}
+        for kind in ["jacobi"] + (["cnn"] if wv is not None else []):
+            mg = S.MultigridSolver([S.varcoef5(n, cells)], kind, net_params=wv[1] if kind == "cnn" else None)
+            ms, cyc, st = timed_solve(mg, b, reps=3 if n <= 2047 else 1)
+            res[kind] = {"ms": ms, "cycles": int(cyc[0]), "converged": int(st) == 0,
+                         "mdof_sweeps_per_s": sweeps_per_cycle(mg.sizes) * int(cyc[0]) / (ms / 1e3)}
+            mg.close()
+        if wv is not None:
+            res["cnn_vs_jacobi_time"] = res["jacobi"]["ms"] / res["cnn"]["ms"]
+        out[str(n)] = res
+        del cells, b
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_c1():
+    """63 x 63, eps = 0.01, theta = pi/6, V(1,1) Jacobi to 1e-8, rhs U[-1,1] seed 0 (C1):
+    one problem, the whole solve in one kernel (levels <= 63 live in one CTA)."""
+    import torch
+
+    from paper_2102_12071_gb300 import inputs, solver as S
+
+    n = 63
+    mg = S.MultigridSolver([S.rotated(n, 0.01, math.pi / 6)], "jacobi")
+    b = torch.from_numpy(inputs.rhs_uniform(0, n)).cuda()[None].contiguous()
+    ms, cyc, st = timed_solve(mg, b, reps=50)
+    mg.close()
+    return {"n": n, "eps": 0.01, "theta": "pi/6", "smoother": "jacobi", "ms_per_solve": ms, "cycles": int(cyc[0]),
+            "us_per_cycle": 1e3 * ms / max(int(cyc[0]), 1), "converged": int(st) == 0}
+
+
+def run_rotated_batch(n: int, nprob: int, weights, rank: int):
+    """nprob rotated problems of side n (the benchmark's recipe), CNN against Jacobi."""
+    import numpy as np
+    import torch
+
+    from paper_2102_12071_gb300 import solver as S
+
+    params, b_host = make_batch(rank, n, nprob)
+    problems = [S.rotated(n, e, t) for e, t in params]
+    b = torch.from_numpy(np.ascontiguousarray(b_host)).cuda()
+    out = {"n": n, "nprob": nprob}
+    for kind in ["jacobi"] + (["cnn"] if weights is not None else []):
+        mg = S.MultigridSolver(problems, kind, net_params=weights.cuda() if kind == "cnn" else None)
+        ms, cyc, st = timed_solve(mg, b, reps=3)
+        out[kind] = {"ms": ms, "max_cycles": int(cyc.max()), "mean_cycles": float(cyc.mean()),
+                     "converged": int(st) == 0,
+                     "mdof_sweeps_per_s": sum(sweeps_per_cycle(mg.sizes) * int(c) for c in cyc) / (ms / 1e3)}
+        mg.close()
+    if weights is not None:
+        out["cnn_vs_jacobi_time"] = out["jacobi"]["ms"] / out["cnn"]["ms"]
+    return out
+
+
+def run_train(steps: int = 5):
+    """One training step (C3): 32 rotated problems at 31^2 and 32 at 63^2, 32 Gaussian
+    vectors each; two-grid loss, its exact gradient and the Adam update.  A step includes
+    the batch setup of freshly drawn problems (stencils, Galerkin operator, banded
+    Cholesky factor); `loss_and_grad_ms` is the loss + gradient call alone on a set-up batch."""
+    import torch
+
+    from paper_2102_12071_gb300 import train as T
+
+    tr = T.Trainer(sizes=(31, 63), per_size=32, nvec=32)
+    for _ in range(3):
+        tr.step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        loss = tr.step()
+    torch.cuda.synchronize()
+    step_ms = 1e3 * (time.perf_counter() - t0) / steps
+    per = {}
+    for n in (31, 63):
+        batch = T.TwoGridBatch(tr.problems(0, n), 32, conv_bf16=True)
+        z = torch.randn((32, 32, n, n), device="cuda")
+        p = tr.params.detach()
+        for _ in range(3):
+            batch.loss_and_grad(p, z)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        _, _, _, cyc, st = mg.solve(b, rtol=RTOL, max_cycles=MAX_CYCLES, history=False)
+        for _ in range(20):
+            batch.loss_and_grad(p, z)
         e1.record()
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        out[kind] = {"ms": ms, "cycles": int(cyc[0]), "converged": int(st) == 0,
-                     "mdof_sweeps_per_s": sweeps_per_cycle(mg.sizes) * int(cyc[0]) / (ms / 1e3)}
-        mg.close()
-    if w is not None:
-        out["weights"] = wname
+        per[str(n)] = e0.elapsed_time(e1) / 20
+        batch.close()
+    return {"problems": "32 x 31^2 + 32 x 63^2 rotated, 32 vectors each", "step_ms": step_ms,
+            "loss_and_grad_ms": per, "last_loss": loss, "steps_timed": steps}
+
+
+def mixed_batch(count: int, rank: int):
+    """C5 workload: count problems, sizes log-uniform in [63, 2047] snapped to 2^m - 1, even
+    indices rotated anisotropic (eps log-U[1e-3,1], theta U[0,pi]), odd indices GRF
+    variable-coefficient; rhs U[-1,1]."""
+    import torch
+
+    from paper_2102_12071_gb300 import inputs, solver as S
+
+    sizes = inputs.grid_sizes_loguniform(inputs.SEED_PARAMS + 7 + rank, count)
+    params = inputs.rotated_params(inputs.SEED_PARAMS + 8 + rank, count)
+    problems, b = [], []
+    for i, n in enumerate(sizes):
+        if i % 2 == 0:
+            problems.append(S.rotated(n, *params[i]))
+        else:
+            cells = torch.from_numpy(inputs.grf_cells(inputs.SEED_GRF + 1000 * rank + 7 + i, n)).cuda()
+            problems.append(S.varcoef5(n, cells))
+        b.append(torch.from_numpy(inputs.rhs_uniform(inputs.SEED_RHS + 5000 + 1000 * rank + i, n)).cuda())
+    return problems, b
+
+
+def run_mixed(args, rank, weights):
+    """C5: one call solves the whole mixed batch (mg_solve_multi over one context per size
+    and stencil kind, each on its own stream); CNN against Jacobi."""
+    import numpy as np
+    import torch
+
+    from paper_2102_12071_gb300 import solver as S
+
+    t0 = time.perf_counter()
+    problems, b = mixed_batch(args.mixed_count, rank)
+    gen_s = time.perf_counter() - t0
+    wv = load_varcoef_weights()
+    out = {"count": len(problems), "input_generation_s": round(gen_s, 2)}
+    arms = ["jacobi"] + (["cnn"] if weights is not None else [])
+    for kind in arms:
+        net = {"const": weights.cuda(), "field": wv[1]} if kind == "cnn" else None
+        t0 = time.perf_counter()
+        mb = S.MixedBatchSolver(problems, kind, net_params=net, autotune=True)
+        mb.solve(b, rtol=RTOL, max_cycles=MAX_CYCLES)  # setup + autotune + first solve
+        setup_s = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.mixed_steps):
+            _, cyc, st = mb.solve(b, rtol=RTOL, max_cycles=MAX_CYCLES)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.mixed_steps
+        sweeps = 0.0
+        groups = {}
+        for key, idx in mb.groups.items():
+            sizes = mb.solvers[key].sizes
+            sweeps += sum(sweeps_per_cycle(sizes) * int(cyc[i]) for i in idx)
+            groups[f"{key[0]}/{key[1]}"] = {"problems": len(idx), "median_cycles": float(np.median(cyc[idx])),
+                                            "max_cycles": int(cyc[idx].max()),
+                                            "cluster_tail": bool(mb.layout.get(key, True))}
+        out[kind] = {"ms": ms, "ms_per_problem": ms / len(problems), "mdof_sweeps_per_s": sweeps / (ms / 1e3),
+                     "converged": int(st) == 0, "setup_and_first_solve_s": round(setup_s, 2), "groups": groups}
+        mb.close()
+        del mb
+        torch.cuda.empty_cache()
+    if weights is not None:
         out["cnn_vs_jacobi_time"] = out["jacobi"]["ms"] / out["cnn"]["ms"]
     return out
 
@@ -271,7 +432,10 @@ def main():
     ap.add_argument("--profile-cycles", type=int, default=0,
                     help="only set up the batch and run this many single V-cycles (for profiler captures)")
     ap.add_argument("--smoother", default="auto", choices=["auto", "jacobi", "cnn"])
-    ap.add_argument("--varcoef-n", type=int, default=1023, help="side of the GRF problem (0: skip)")
+    ap.add_argument("--varcoef-n", default="1023,4095", help="sides of the GRF problems, comma list (0: skip)")
+    ap.add_argument("--mixed-count", type=int, default=256, help="problems in the mixed batch (0: skip)")
+    ap.add_argument("--mixed-steps", type=int, default=2)
+    ap.add_argument("--no-extra", action="store_true", help="skip the 63^2, 255^2 and training sections")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -425,7 +589,13 @@ def main():
     e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps)
     e2e_val = sum(sweeps_per_cycle(sizes) * int(c) for c in cyc_e2e) * world / e2e_s
 
-    varcoef = run_varcoef(args, rank) if args.varcoef_n else None
+    varcoef = run_varcoef(args, rank) if str(args.varcoef_n) != "0" else None
+    extra = {}
+    if not args.no_extra and rank == 0:
+        extra["c1_63"] = run_c1()
+        extra["c2_255"] = run_rotated_batch(255, nprob, weights, rank)
+        extra["train"] = run_train()
+    mixed = run_mixed(args, rank, weights) if args.mixed_count else None
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -449,6 +619,8 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clocks,
         "varcoef": varcoef,
+        "mixed": mixed,
+        **extra,
     }
     if "cnn" in results:
         line["cnn_vs_jacobi_time"] = results["jacobi"]["ms_per_step"] / results["cnn"]["ms_per_step"]

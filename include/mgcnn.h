@@ -162,6 +162,22 @@ mg_status mg_vcycle(mg_ctx* ctx, const float* b, float* x_hi, float* x_lo, float
 mg_status mg_solve(mg_ctx* ctx, const float* b, float* x_hi, float* x_lo, double rtol,
                    int max_cycles, double* hist, int* cycles, void* stream);
 
+/* Solves of several independent batches at once (no counterpart in the paper; its
+   experiments solve problems one by one): the same as mg_solve on every context, for
+   batches of different sizes or stencil kinds, which one context cannot hold.  Context k
+   runs on streams[k] (NULL array or entry: the default stream) with its arrays b[k],
+   x_hi[k], x_lo[k] (x_lo NULL or an entry NULL: zero low parts) and cycles[k] (NULL array
+   or entry: not reported; else HOST int[nprob of context k]).  The host polls the
+   streams and issues a context's next chunk of cycles as soon as its previous chunk is
+   done, so the batches' kernels overlap on the GPU and no context waits for another.
+   The contexts must be distinct.  Blocks until all have finished.  The per-problem
+   outcomes (MG_ERR_NOT_CONVERGED, MG_ERR_NUMERIC, MG_ERR_TIMEOUT) stop no other context:
+   the first non-OK one in context order is returned.  A CUDA or argument error returns at
+   once, after waiting for every context's stream. */
+mg_status mg_solve_multi(mg_ctx* const* ctxs, int nctx, const float* const* b, float* const* x_hi,
+                         float* const* x_lo, double rtol, int max_cycles, int* const* cycles,
+                         void* const* streams);
+
 /* ------------------------------------------------------------ network (a3) ---- */
 
 /* Number of network parameters: 3x3 convolutions 9->7->5->3 (no bias) and the layer

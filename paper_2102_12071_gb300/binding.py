@@ -59,6 +59,7 @@ def lib() -> ctypes.CDLL:
         "mg_smoother_apply": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
         "mg_vcycle": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
         "mg_solve": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_double, ctypes.c_int, _P, _P, _P]),
+        "mg_solve_multi": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, ctypes.c_double, ctypes.c_int, _P, _P]),
         "mg_net_nparams": (ctypes.c_int, []),
         "mg_net_forward": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_float, ctypes.c_int, _P, _P]),
         "mg_train_workspace_size": (ctypes.c_size_t, [ctypes.POINTER(mg_problem), ctypes.c_int, ctypes.c_int,
@@ -180,6 +181,20 @@ def mg_solve(ctx, b, x_hi, x_lo, rtol, max_cycles, hist=None, cycles=None, strea
                         _stream(stream))
     if st not in (MG_OK, MG_ERR_NOT_CONVERGED):
         check(st, "mg_solve")
+    return st
+
+
+def mg_solve_multi(ctxs, b, x_hi, x_lo, rtol, max_cycles, cycles=None, streams=None) -> int:
+    """Per-context lists: b, x_hi, x_lo (tensors or None), cycles (numpy int32 or None),
+    streams (raw CUDA stream handles or None).  Returns MG_OK or MG_ERR_NOT_CONVERGED."""
+    k = len(ctxs)
+    arr = lambda vals: (ctypes.c_void_p * k)(*vals)
+    cyc = arr([c.ctypes.data if c is not None else None for c in cycles]) if cycles is not None else None
+    st = lib().mg_solve_multi(arr(ctxs), k, arr([_ptr(t) for t in b]), arr([_ptr(t) for t in x_hi]),
+                              arr([_ptr(t) for t in x_lo]) if x_lo is not None else None, float(rtol),
+                              int(max_cycles), cyc, arr(list(streams)) if streams is not None else None)
+    if st not in (MG_OK, MG_ERR_NOT_CONVERGED):
+        check(st, "mg_solve_multi")
     return st
 
 

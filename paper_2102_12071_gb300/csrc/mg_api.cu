@@ -10,6 +10,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <thread>
 #include <vector>
 
 #include "mg_internal.h"
@@ -140,7 +141,7 @@ struct mg_ctx {
   mg_options opts;
   CycleArgs args;
   std::vector<ProbDev> h_probs;
-  std::vector<ProbState> h_state;
+  ProbState* h_state = nullptr;  // pinned host copy of the control blocks (nprob entries)
   float* xlo_ws = nullptr;
   int* d_fail = nullptr;
   NetJob* d_jobs = nullptr;
@@ -161,6 +162,7 @@ struct mg_ctx {
   cudaStream_t capture_stream = nullptr;
   ~mg_ctx() {
     for (CycleGraph& g : graphs) cudaGraphExecDestroy(g.exec);
+    if (h_state) cudaFreeHost(h_state);
     if (capture_stream) cudaStreamDestroy(capture_stream);
   }
 };
@@ -218,9 +220,10 @@ static mg_status cycle_graph(mg_ctx* ctx, const CycleArgs& a, float rtol, int ma
 // the chunk ends: the chunk is sized to end when the next problem is expected to reach
 // rtol at its recent convergence rate, as a multiple of the graph length and at most one
 // ring of residual history; without a rate estimate it doubles.
-static int next_chunk(const std::vector<ProbState>& st, int prev, double rtol, int max_cycles) {
+static int next_chunk(const ProbState* st, int nprob, int prev, double rtol, int max_cycles) {
   int soonest = std::min(2 * prev, MG_HRING);
-  for (const ProbState& S : st) {
+  for (int p = 0; p < nprob; ++p) {
+    const ProbState& S = st[p];
     if (!S.active) continue;
     const int it = S.iter;  // residual evaluations so far
     int rem = max_cycles + 1 - it;
@@ -382,7 +385,12 @@ mg_status mg_setup(const mg_problem* problems, int nprob, const mg_options* opts
   a.nactive = 0;
   a.pdl = false;
   a.maps = &ctx->maps;
-  ctx->h_state.resize(P.nprob);
+  // pinned, so that the per-chunk read of the control blocks is asynchronous and several
+  // contexts can keep their streams busy at once
+  if (cudaMallocHost((void**)&ctx->h_state, sizeof(ProbState) * P.nprob) != cudaSuccess) {
+    delete ctx;
+    return fail(MG_ERR_CUDA, "cudaMallocHost of %d control blocks failed", P.nprob);
+  }
   if (P.lstar > 0 && !build_tile_maps(ctx->maps, ctx->arrays, P.nprob, P.lstar)) {
     delete ctx;
     return fail(MG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the level arrays");
@@ -510,19 +518,48 @@ mg_status mg_vcycle(mg_ctx* ctx, const float* b, float* x_hi, float* x_lo, float
   return MG_OK;
 }
 
-mg_status mg_solve(mg_ctx* ctx, const float* b, float* x_hi, float* x_lo, double rtol, int max_cycles, double* hist,
-                   int* cycles, void* stream) {
+}  // extern "C"
+
+// ------------------------------------------------------------ solve loop
+// One context's solve, split so that several contexts can interleave their chunks.
+struct SolveRun {
+  mg_ctx* ctx = nullptr;
+  CycleArgs a;
+  const float* b = nullptr;
+  float *x_hi = nullptr, *x_lo = nullptr, *xlo = nullptr;
+  double rtol = 0.0;
+  int max_cycles = 0;
+  double* hist = nullptr;
+  int* cycles = nullptr;
+  std::vector<int> seen;
+  int G = kGraphCycles;
+  bool done = false;
+};
+
+// copies into the pitched arrays, reset of the control blocks, ||b||, initial residual
+static mg_status run_begin(SolveRun& R, mg_ctx* ctx, const float* b, float* x_hi, float* x_lo, double rtol,
+                           int max_cycles, double* hist, int* cycles, cudaStream_t stream) {
   if (!ctx || !b || !x_hi) return fail(MG_ERR_INVALID_ARG, "mg_solve: ctx, b and x_hi are required");
   if (max_cycles < 0 || max_cycles > 100000000) return fail(MG_ERR_INVALID_ARG, "max_cycles out of range");
-  CycleArgs a = ctx->args;
-  a.stream = (cudaStream_t)stream;
+  R.ctx = ctx;
+  R.a = ctx->args;
+  R.a.stream = stream;
+  R.b = b;
+  R.x_hi = x_hi;
+  R.x_lo = x_lo;
+  R.xlo = x_lo;
+  R.rtol = rtol;
+  R.max_cycles = max_cycles;
+  R.hist = hist;
+  R.cycles = cycles;
   const Plan& P = ctx->plan;
-  float* xlo = x_lo;
+  CycleArgs& a = R.a;
   const LevelArrays& A = ctx->arrays;
+  R.seen.assign(P.nprob, 0);
   if (P.tail_solve) {
-    if (!xlo) {
-      xlo = ctx->xlo_ws;
-      CK(cudaMemsetAsync(xlo, 0, sizeof(float) * (size_t)P.nprob * P.n0 * P.n0, a.stream));
+    if (!R.xlo) {
+      R.xlo = ctx->xlo_ws;
+      CK(cudaMemsetAsync(R.xlo, 0, sizeof(float) * (size_t)P.nprob * P.n0 * P.n0, a.stream));
     }
   } else {
     // the tiled path iterates on pitched copies (TMA-aligned rows) and copies x back at the end
@@ -534,56 +571,76 @@ mg_status mg_solve(mg_ctx* ctx, const float* b, float* x_hi, float* x_lo, double
   CK(launch_bnorm(a, b));
   // residual and stopping test of the initial iterate; every cycle ends with those of the new one
   if (!P.tail_solve) CK(launch_residual(a, (float)rtol, max_cycles));
-  std::vector<int> seen(P.nprob, 0);
-  const float frtol = (float)rtol;
-  int G = 16;
-  for (;;) {
-    if (P.tail_solve) {
-      CK(launch_tail_solve(a, b, x_hi, xlo, frtol, max_cycles, G, 0));
-    } else if (ctx->prof.on) {  // event timing needs individual launches
-      for (int c = 0; c < G; ++c) {
-        CK(launch_cycle(a, frtol, max_cycles, c & 1));
-      }
-    } else {
-      cudaGraphExec_t exec;
-      long long nodes = 0;
-      mg_status gs = cycle_graph(ctx, a, frtol, max_cycles, &exec, &nodes);
-      if (gs != MG_OK) return gs;
-      for (int c = 0; c < G; c += kGraphCycles) CK(cudaGraphLaunch(exec, a.stream));
-      ctx->prof.launches += nodes * (G / kGraphCycles);
-    }
-    CK(cudaMemcpyAsync(ctx->h_state.data(), a.state, sizeof(ProbState) * P.nprob, cudaMemcpyDeviceToHost, a.stream));
-    CK(cudaStreamSynchronize(a.stream));
-    ctx->prof.collect();
-    int active = 0;
-    ctx->h_active.clear();
-    for (int p = 0; p < P.nprob; ++p) {
-      const ProbState& S = ctx->h_state[p];
-      if (hist)
-        for (int k = seen[p]; k < S.iter; ++k) hist[(size_t)p * (max_cycles + 1) + k] = S.hist[k % MG_HRING];
-      seen[p] = S.iter;
-      active += S.active;
-      if (S.active) ctx->h_active.push_back(p);
-    }
-    if (!active) break;
-    // later chunks launch CTAs only for the problems still iterating
-    if (active < a.nprob && active != a.nactive) {
-      CK(cudaMemcpyAsync(ctx->d_active, ctx->h_active.data(), sizeof(int) * active, cudaMemcpyHostToDevice,
-                         a.stream));
-      a.active = ctx->d_active;
-      a.nactive = active;
-    }
-    G = next_chunk(ctx->h_state, G, rtol, max_cycles);
+  return MG_OK;
+}
+
+// the next chunk of cycles and the asynchronous read of the control blocks
+static mg_status run_launch(SolveRun& R) {
+  mg_ctx* ctx = R.ctx;
+  const Plan& P = ctx->plan;
+  CycleArgs& a = R.a;
+  const float frtol = (float)R.rtol;
+  if (P.tail_solve) {
+    CK(launch_tail_solve(a, R.b, R.x_hi, R.xlo, frtol, R.max_cycles, R.G, 0));
+  } else if (ctx->prof.on) {  // event timing needs individual launches
+    for (int c = 0; c < R.G; ++c) CK(launch_cycle(a, frtol, R.max_cycles, c & 1));
+  } else {
+    cudaGraphExec_t exec;
+    long long nodes = 0;
+    mg_status gs = cycle_graph(ctx, a, frtol, R.max_cycles, &exec, &nodes);
+    if (gs != MG_OK) return gs;
+    for (int c = 0; c < R.G; c += kGraphCycles) CK(cudaGraphLaunch(exec, a.stream));
+    ctx->prof.launches += nodes * (R.G / kGraphCycles);
   }
+  CK(cudaMemcpyAsync(ctx->h_state, a.state, sizeof(ProbState) * P.nprob, cudaMemcpyDeviceToHost, a.stream));
+  return MG_OK;
+}
+
+// after the stream has been synchronised: history, compaction, next chunk length
+static mg_status run_collect(SolveRun& R) {
+  mg_ctx* ctx = R.ctx;
+  const Plan& P = ctx->plan;
+  CycleArgs& a = R.a;
+  ctx->prof.collect();
+  int active = 0;
+  ctx->h_active.clear();
+  for (int p = 0; p < P.nprob; ++p) {
+    const ProbState& S = ctx->h_state[p];
+    if (R.hist)
+      for (int k = R.seen[p]; k < S.iter; ++k) R.hist[(size_t)p * (R.max_cycles + 1) + k] = S.hist[k % MG_HRING];
+    R.seen[p] = S.iter;
+    active += S.active;
+    if (S.active) ctx->h_active.push_back(p);
+  }
+  if (!active) {
+    R.done = true;
+    return MG_OK;
+  }
+  // later chunks launch CTAs only for the problems still iterating
+  if (active < a.nprob && active != a.nactive) {
+    CK(cudaMemcpyAsync(ctx->d_active, ctx->h_active.data(), sizeof(int) * active, cudaMemcpyHostToDevice, a.stream));
+    a.active = ctx->d_active;
+    a.nactive = active;
+  }
+  R.G = next_chunk(ctx->h_state, P.nprob, R.G, R.rtol, R.max_cycles);
+  return MG_OK;
+}
+
+// copies x back, waits, and maps the problems' final states to a status
+static mg_status run_end(SolveRun& R) {
+  mg_ctx* ctx = R.ctx;
+  const Plan& P = ctx->plan;
+  CycleArgs& a = R.a;
+  const LevelArrays& A = ctx->arrays;
   if (!P.tail_solve) {
-    CK(launch_unpack(A.xh0, A.xh0b, a.state, x_hi, A.n[0], A.pitch[0], a.nprob, a.stream));
-    if (x_lo) CK(launch_unpack(A.xl0, A.xl0b, a.state, x_lo, A.n[0], A.pitch[0], a.nprob, a.stream));
+    CK(launch_unpack(A.xh0, A.xh0b, a.state, R.x_hi, A.n[0], A.pitch[0], a.nprob, a.stream));
+    if (R.x_lo) CK(launch_unpack(A.xl0, A.xl0b, a.state, R.x_lo, A.n[0], A.pitch[0], a.nprob, a.stream));
     CK(cudaStreamSynchronize(a.stream));
   }
   mg_status rc = MG_OK;
   for (int p = 0; p < P.nprob; ++p) {
     const ProbState& S = ctx->h_state[p];
-    if (cycles) cycles[p] = S.cycles;
+    if (R.cycles) R.cycles[p] = S.cycles;
     if (S.status == 4) rc = MG_ERR_TIMEOUT;
     else if (S.status == 3 && rc != MG_ERR_TIMEOUT) rc = MG_ERR_NUMERIC;
     else if (S.status == 2 && rc == MG_OK) rc = MG_ERR_NOT_CONVERGED;
@@ -591,6 +648,68 @@ mg_status mg_solve(mg_ctx* ctx, const float* b, float* x_hi, float* x_lo, double
   if (rc == MG_ERR_TIMEOUT) fail(rc, "a bounded wait for tile copies expired");
   else if (rc == MG_ERR_NUMERIC) fail(rc, "non-finite residual");
   else if (rc == MG_ERR_NOT_CONVERGED) fail(rc, "max_cycles reached before rtol");
+  return rc;
+}
+
+extern "C" {
+
+mg_status mg_solve(mg_ctx* ctx, const float* b, float* x_hi, float* x_lo, double rtol, int max_cycles, double* hist,
+                   int* cycles, void* stream) {
+  SolveRun R;
+  mg_status st = run_begin(R, ctx, b, x_hi, x_lo, rtol, max_cycles, hist, cycles, (cudaStream_t)stream);
+  if (st != MG_OK) return st;
+  while (!R.done) {
+    if ((st = run_launch(R)) != MG_OK) return st;
+    CK(cudaStreamSynchronize(R.a.stream));
+    if ((st = run_collect(R)) != MG_OK) return st;
+  }
+  return run_end(R);
+}
+
+mg_status mg_solve_multi(mg_ctx* const* ctxs, int nctx, const float* const* b, float* const* x_hi,
+                         float* const* x_lo, double rtol, int max_cycles, int* const* cycles, void* const* streams) {
+  if (!ctxs || nctx <= 0 || !b || !x_hi) return fail(MG_ERR_INVALID_ARG, "mg_solve_multi: contexts and arrays required");
+  for (int k = 0; k < nctx; ++k)
+    for (int q = 0; q < k; ++q)
+      if (ctxs[k] == ctxs[q]) return fail(MG_ERR_INVALID_ARG, "mg_solve_multi: context %d appears twice", k);
+  std::vector<SolveRun> runs(nctx);
+  for (int k = 0; k < nctx; ++k) {
+    mg_status st = run_begin(runs[k], ctxs[k], b[k], x_hi[k], x_lo ? x_lo[k] : nullptr, rtol, max_cycles, nullptr,
+                             cycles ? cycles[k] : nullptr, streams ? (cudaStream_t)streams[k] : nullptr);
+    if (st != MG_OK) return st;
+  }
+  // each context's next chunk goes out as soon as its previous one has been collected, so
+  // no stream waits for the slowest context
+  auto abort_all = [&](mg_status st) {
+    for (SolveRun& R : runs) cudaStreamSynchronize(R.a.stream);
+    return st;
+  };
+  int pending = 0;
+  for (SolveRun& R : runs) {
+    mg_status st = run_launch(R);
+    if (st != MG_OK) return abort_all(st);
+    ++pending;
+  }
+  while (pending) {
+    bool progressed = false;
+    for (SolveRun& R : runs) {
+      if (R.done) continue;
+      const cudaError_t q = cudaStreamQuery(R.a.stream);
+      if (q == cudaErrorNotReady) continue;
+      if (q != cudaSuccess) return abort_all(fail(MG_ERR_CUDA, "mg_solve_multi: %s", cudaGetErrorString(q)));
+      progressed = true;
+      mg_status st = run_collect(R);
+      if (st == MG_OK && !R.done) st = run_launch(R);
+      if (st != MG_OK) return abort_all(st);
+      if (R.done) --pending;
+    }
+    if (!progressed) std::this_thread::yield();
+  }
+  mg_status rc = MG_OK;
+  for (SolveRun& R : runs) {
+    const mg_status st = run_end(R);
+    if (rc == MG_OK) rc = st;
+  }
   return rc;
 }
 

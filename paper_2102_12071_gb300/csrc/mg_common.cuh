@@ -67,6 +67,14 @@ struct ProbState {
   float hist[MG_HRING];  // hist[k % MG_HRING] = relative residual after k cycles
 };
 
+// Control-block fields written by earlier kernels are read through L2 (ld.global.cg).  A
+// kernel launched with programmatic serialisation may be resident before those writes
+// happen, and a line of the block cached in its SM's L1 by an older kernel would then be
+// stale; L2 is the point of coherence, so a .cg load sees the latest value once
+// griddepcontrol.wait has returned.
+__device__ __forceinline__ int st_active(const ProbState* st) { return __ldcg(&st->active); }
+
+
 // ---------------------------------------------------------------- float-float
 // Error-free transformations (Knuth's TwoSum; FMA-based TwoProduct, Dekker 1971).
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {

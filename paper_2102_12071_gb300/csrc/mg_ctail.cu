@@ -79,10 +79,11 @@ __device__ __forceinline__ void cluster_sync() {
 }
 
 // generic address of the same shared-memory location in CTA `rank` of the cluster
-__device__ __forceinline__ float* cluster_map(float* p, int rank) {
+template <class T>
+__device__ __forceinline__ T* cluster_map(T* p, int rank) {
   uint64_t out;
   asm volatile("mapa.u64 %0, %1, %2;" : "=l"(out) : "l"(reinterpret_cast<uint64_t>(p)), "r"(rank));
-  return reinterpret_cast<float*>(out);
+  return reinterpret_cast<T*>(out);
 }
 
 // rows [a, b) of a level of side n: work items of one row and 32 columns spread over warps
@@ -255,15 +256,22 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_ctail(const ProbDev* __restri
   const int rpitch = P.lv[ls].pitch;
   ct_prologue<SK, HK>(P, sm, lay, sc, wi, ls, L, rank);
   pdl_wait();
-  if (!state[p].active) return;  // the same decision in every CTA of the cluster
+  __shared__ int live;
+  if (threadIdx.x == 0) live = st_active(state + p);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   {
     const int n = lay.a.n[ls], m = n + 2, i0 = rank * lay.band[ls];
     const int a = max(0, i0 - MG_CT_HD), b = min(n, i0 + lay.band[ls] + MG_CT_HD);
     float* r = sm + lay.a.off_r[ls];
-    CT_FOR(a, b, n) r[(i - i0 + MG_CT_HD) * m + j + 1] = rtop[(size_t)i * rpitch + j];
+    CT_FOR(a, b, n) r[(i - i0 + MG_CT_HD) * m + j + 1] = __ldcg(rtop + (size_t)i * rpitch + j);
   }
   cluster_sync();  // every CTA of the cluster is running with its exterior zeroed
+  // Leave or stay as a whole cluster, on CTA 0's reading of the flag: a CTA that left
+  // while the others went on would break their barriers and shared-memory pushes.
+  if (!*cluster_map(&live, 0)) {
+    cluster_sync();  // CTA 0 keeps `live` until every CTA has read it
+    return;
+  }
   const int lsolo = lay.lsolo;
   for (int l = ls; l < lsolo; ++l) ct_down<SK, HK>(P, sm, lay, sc, wi, l, rank, omega);
   if (rank == 0) tail_cycle<SK, HK>(P, sm, lay.a, sc, wi, lsolo, L, omega);

@@ -84,11 +84,11 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail(const ProbDev* __restrict
   __syncthreads();
   tail_prologue<SK, HK>(P, sm, lay, sc, wi, l0, L);
   pdl_wait();
-  if (!state[p].active) return;
+  if (!st_active(state + p)) return;
   const int n = P.lv[l0].n, m = n + 2, pitch = P.lv[l0].pitch;
   float* r = sm + lay.off_r[l0];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  TAIL_FOR(n) r[(i + 1) * m + j + 1] = P.lv[l0].r[(size_t)i * pitch + j];
+  TAIL_FOR(n) r[(i + 1) * m + j + 1] = __ldcg(P.lv[l0].r + (size_t)i * pitch + j);
   __syncthreads();
   tail_cycle<SK, HK>(P, sm, lay, sc, wi, l0, L, omega);
   const float* e = sm + lay.off_e[l0];
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_solve(const ProbDev* __re
   __shared__ TailLayout lay;
   __shared__ int go;
   const int p = act ? act[blockIdx.x] : blockIdx.x;
-  if (!state[p].active) return;
+  if (!st_active(state + p)) return;
   const ProbDev& P = probs[p];
   if (threadIdx.x == 0) {
     int nl[MG_MAXL];
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_solve(const ProbDev* __re
       float hi = 0.f, lo = 0.f;
       for (int k = 0; k < nwarps; ++k) ff_add(hi, lo, wh[k], wl[k]);
       decide(state[p], hi, lo, rtol, max_cycles);
-      go = state[p].active && it < budget;
+      go = st_active(state + p) && it < budget;
     }
     __syncthreads();
     if (!go) break;

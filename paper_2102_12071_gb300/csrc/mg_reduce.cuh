@@ -52,8 +52,8 @@ __device__ bool block_partial_and_last(float v, float* partials, unsigned int* c
 // Stopping test after residual evaluation number k = cycles applied so far (Sec. 6.1:
 // ||b - A x|| / ||b|| < rtol), with the cycle cap and non-finite residuals.
 __device__ __forceinline__ void decide(ProbState& st, float rr_hi, float rr_lo, float rtol, int max_cycles) {
-  const int k = st.iter;
-  const float rr = rr_hi + rr_lo, bb = st.bb_hi + st.bb_lo;
+  const int k = __ldcg(&st.iter);
+  const float rr = rr_hi + rr_lo, bb = __ldcg(&st.bb_hi) + __ldcg(&st.bb_lo);
   const float rel = sqrtf(rr / bb);
   st.rel = rel;
   st.hist[k % MG_HRING] = rel;

@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(NT) k_residual(const __grid_constant__ ResMaps
 #pragma unroll
   for (int k = 0; k < 9; ++k) s[k] = (SK == SK_CONST) ? L.s[k] : 0.f;
   pdl_wait();
-  if (!state[p].active) return;
+  if (!st_active(state + p)) return;
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     fence_mbar_init();
@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(NT) k_down(const __grid_constant__ DownMaps M,
   for (int k = 0; k < 9; ++k) s[k] = (SK == SK_CONST) ? L.s[k] : 0.f;
   if (HK == HK_TABLE) load_table(L, in, wtab, wi);
   pdl_wait();
-  if (!state[p].active) return;
+  if (!st_active(state + p)) return;
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     fence_mbar_init();
@@ -478,7 +478,7 @@ __global__ void __launch_bounds__(NT) k_up(const __grid_constant__ UpMaps M, con
   for (int k = 0; k < 9; ++k) s[k] = (SK == SK_CONST) ? L.s[k] : 0.f;
   if (HK == HK_TABLE) load_table(L, in, wtab, wi);
   pdl_wait();
-  if (!state[p].active) return;
+  if (!st_active(state + p)) return;
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     fence_mbar_init();
@@ -607,7 +607,7 @@ __global__ void __launch_bounds__(NT) k_up0(const __grid_constant__ Up0Maps M, c
   for (int k = 0; k < 9; ++k) s[k] = (SK == SK_CONST) ? L.s[k] : 0.f;
   if (HK == HK_TABLE) load_table(L, in, wtab, wi);
   pdl_wait();
-  if (!state[p].active) return;
+  if (!st_active(state + p)) return;
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     fence_mbar_init();
@@ -648,7 +648,7 @@ __global__ void k_unpack(const float* __restrict__ src_a, const float* __restric
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n * n) return;
   const int i = q / n, j = q % n;
-  const float* src = (state[p].cycles & 1) ? src_b : src_a;
+  const float* src = (__ldcg(&state[p].cycles) & 1) ? src_b : src_a;
   dst[(size_t)p * n * n + q] = src[(size_t)p * n * pitch + (size_t)i * pitch + j];
 }
 

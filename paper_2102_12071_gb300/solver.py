@@ -104,3 +104,89 @@ def net_forward(fields: torch.Tensor, params: torch.Tensor, omega: float = 2.0 /
     W = torch.empty_like(fields)
     B.mg_net_forward(n, nprob, fields.contiguous(), params.contiguous(), omega, int(conv_bf16), W)
     return W
+
+
+class MixedBatchSolver:
+    """Problems of different sizes and stencil storage in one solve.
+
+    A context holds problems of one size and one storage kind (constant stencils or per-point
+    fields), so the batch is split into such groups; every group gets its own context and
+    CUDA stream, and mg_solve_multi runs all groups' cycles at once.  net_params maps "const"
+    and "field" to the network parameters of each kind (CNN smoother).  With `autotune`, the
+    first solve times a few cycles of each coarse-level layout (one CTA cluster per problem
+    below 127, or one CTA below 63 with tiled kernels above) per group and keeps the faster.
+    """
+
+    def __init__(self, problems: list[dict], smoother: str = "jacobi", net_params: dict | None = None,
+                 autotune: bool = True, tune_cycles: int = 16):
+        self.problems = problems
+        self.smoother = smoother
+        self.net_params = net_params or {}
+        self.autotune = autotune
+        self.tune_cycles = tune_cycles
+        self.groups: dict[tuple, list[int]] = {}
+        for i, p in enumerate(problems):
+            field = p["kind"] in (B.MG_PROBLEM_VARCOEF5, B.MG_PROBLEM_FIELD)
+            self.groups.setdefault((p["n"], "field" if field else "const"), []).append(i)
+        self.solvers: dict[tuple, MultigridSolver] = {}
+        self.streams: dict[tuple, torch.cuda.Stream] = {key: torch.cuda.Stream() for key in self.groups}
+        self.layout: dict[tuple, bool] = {}
+
+    def _make(self, key, cluster_tail: bool) -> MultigridSolver:
+        params = self.net_params.get(key[1]) if self.smoother == "cnn" else None
+        return MultigridSolver([self.problems[i] for i in self.groups[key]], self.smoother, net_params=params,
+                               stream=self.streams[key].cuda_stream, cluster_tail=cluster_tail)
+
+    def _tune(self, key, b: torch.Tensor) -> MultigridSolver:
+        if not self.autotune or key[0] <= 63:  # <= 63: whole solves in one CTA, nothing to choose
+            return self._make(key, True)
+        best = None
+        for ct in (True, False):
+            mg = self._make(key, ct)
+            with torch.cuda.stream(self.streams[key]):
+                for _ in range(2):
+                    mg.solve(b, rtol=0.0, max_cycles=self.tune_cycles, history=False)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                mg.solve(b, rtol=0.0, max_cycles=self.tune_cycles, history=False)
+                e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            if best is None or ms < best[0]:
+                if best is not None:
+                    best[1].close()
+                best = (ms, mg, ct)
+            else:
+                mg.close()
+        self.layout[key] = best[2]
+        return best[1]
+
+    def group_b(self, b: list[torch.Tensor]) -> dict[tuple, torch.Tensor]:
+        return {key: torch.stack([b[i] for i in idx]).contiguous() for key, idx in self.groups.items()}
+
+    def solve(self, b: list[torch.Tensor], rtol: float = 1e-8, max_cycles: int = 20000):
+        """b: one [n, n] device tensor per problem.  Returns (x_hi list, cycles int32 array, status)."""
+        gb = self.group_b(b)
+        for key in self.groups:
+            if key not in self.solvers:
+                self.solvers[key] = self._tune(key, gb[key])
+        keys = list(self.groups)
+        torch.cuda.synchronize()
+        xh = {k: torch.zeros_like(gb[k]) for k in keys}
+        xl = {k: torch.zeros_like(gb[k]) for k in keys}
+        cyc = {k: np.zeros(len(self.groups[k]), dtype=np.int32) for k in keys}
+        st = B.mg_solve_multi([self.solvers[k].ctx for k in keys], [gb[k] for k in keys], [xh[k] for k in keys],
+                              [xl[k] for k in keys], rtol, max_cycles, [cyc[k] for k in keys],
+                              [self.streams[k].cuda_stream for k in keys])
+        x = [None] * len(self.problems)
+        cycles = np.zeros(len(self.problems), dtype=np.int32)
+        for k in keys:
+            for j, i in enumerate(self.groups[k]):
+                x[i] = xh[k][j]
+                cycles[i] = cyc[k][j]
+        return x, cycles, st
+
+    def close(self):
+        for mg in self.solvers.values():
+            mg.close()
+        self.solvers = {}

@@ -190,3 +190,40 @@ def test_autograd_function_and_adam_step_reduce_loss():
         tr.step()
     l1 = batch.loss_and_grad(tr.params.detach(), zt, False)[0].item()
     assert l1 < l0
+
+
+def test_trained_network_gains_over_jacobi():
+    """What training buys: the committed parameters (trained on the GPU by the two-grid loss
+    on 31^2 and 63^2 problems) against the same cycle with the network's starting point,
+    weighted Jacobi, on held-out problems of the bench family at 255^2: fewer V(1,1) cycles
+    to 1e-8 and a smaller asymptotic factor for every problem, and the CNN history of one
+    of them equal to the oracle's."""
+    import os
+
+    path = os.path.join(os.path.dirname(S.__file__), "weights", "cnn_rotated.npy")
+    w = torch.from_numpy(np.load(path).astype(np.float32)).cuda()
+    n = 255
+    params = inputs.rotated_params(inputs.SEED_PARAMS + 97, 6)  # not drawn by training or the bench
+    b = torch.from_numpy(np.stack([inputs.rhs_uniform(inputs.SEED_RHS + 300 + i, n) for i in range(6)])).cuda()
+    probs = [S.rotated(n, e, t) for e, t in params]
+    res = {}
+    for kind in ("jacobi", "cnn"):
+        mg = S.MultigridSolver(probs, kind, net_params=w if kind == "cnn" else None)
+        _, _, gh, cyc, st = mg.solve(b.contiguous(), rtol=1e-8, max_cycles=20000)
+        assert st == B.MG_OK
+        res[kind] = (gh, cyc)
+        mg.close()
+    for p in range(6):
+        cj, cc = int(res["jacobi"][1][p]), int(res["cnn"][1][p])
+        assert cc < cj, (p, params[p], cc, cj)
+        fj = (res["jacobi"][0][p][cj] / res["jacobi"][0][p][cj // 2]) ** (1.0 / (cj - cj // 2))
+        fc = (res["cnn"][0][p][cc] / res["cnn"][0][p][cc // 2]) ** (1.0 / (cc - cc // 2))
+        assert fc < fj, (p, fc, fj)
+    # the trained network's cycle is the oracle's cycle with the same network
+    p = 0
+    om = O.Multigrid(O.const_field(n, f32(O.q1_rotated_stencil(*params[p]))))
+    om.set_cnn(f32(w.cpu().numpy()))
+    k = min(30, int(res["cnn"][1][p]))
+    _, oh = om.solve(f32(b[p].cpu().numpy()), rtol=0.0, max_cycles=k)
+    rel = np.abs(res["cnn"][0][p][: k + 1] - oh) / oh
+    assert rel.max() <= 1e-5, rel.max()

@@ -264,3 +264,76 @@ def test_bench_batch_first_cycles_match_oracle(ct):
         om = O.Multigrid(oracle_rotated(n, *params[p]))
         _, oh = om.solve(f32(b[p].cpu().numpy()), rtol=0.0, max_cycles=cycles)
         assert _cmp_hist(gh[p], oh) == cycles + 1
+
+
+def _mixed_problems():
+    """Five problems in three groups: rotated 63 and 255 (two each, the second pair with
+    different eps/theta) and one GRF 5-point problem at 127."""
+    params = inputs.rotated_params(inputs.SEED_PARAMS + 31, 4)
+    probs = [S.rotated(63, *params[0]), S.rotated(255, *params[1]), S.rotated(63, *params[2]),
+             S.rotated(255, *params[3])]
+    cells = torch.from_numpy(inputs.grf_cells(inputs.SEED_GRF + 31, 127)).cuda()
+    probs.append(S.varcoef5(127, cells))
+    b = [torch.from_numpy(inputs.rhs_uniform(inputs.SEED_RHS + 300 + i, p["n"])).cuda() for i, p in enumerate(probs)]
+    return probs, b
+
+
+@pytest.mark.parametrize("autotune", [False, True])
+def test_solve_multi_matches_single_context_solves(autotune):
+    """mg_solve_multi over several contexts on their own streams gives, per problem, the
+    iterate and cycle count of a plain mg_solve of the same group (bit-identical)."""
+    probs, b = _mixed_problems()
+    mb = S.MixedBatchSolver(probs, "jacobi", autotune=autotune, tune_cycles=4)
+    assert sorted(mb.groups) == [(63, "const"), (127, "field"), (255, "const")]
+    x, cycles, st = mb.solve(b, rtol=1e-8, max_cycles=5000)
+    assert st == B.MG_OK, cycles
+    torch.cuda.synchronize()
+    for key, idx in mb.groups.items():
+        mg = S.MultigridSolver([probs[i] for i in idx], "jacobi", cluster_tail=mb.layout.get(key, True))
+        bb = torch.stack([b[i] for i in idx]).contiguous()
+        xh, _, _, cyc, st1 = mg.solve(bb, rtol=1e-8, max_cycles=5000, history=False)
+        assert st1 == B.MG_OK
+        for j, i in enumerate(idx):
+            assert cycles[i] == cyc[j], (key, i)
+            assert torch.equal(x[i], xh[j]), (key, i)
+        mg.close()
+    mb.close()
+    # and the 63 x 63 problem against the oracle
+    om = O.Multigrid(oracle_rotated(63, *inputs.rotated_params(inputs.SEED_PARAMS + 31, 4)[0]))
+    _, oh = om.solve(f32(b[0].cpu().numpy()), rtol=1e-8, max_cycles=5000)
+    assert abs(int(cycles[0]) - (len(oh) - 1)) <= 1
+
+
+def test_solve_multi_rejects_bad_arguments():
+    probs, b = _mixed_problems()
+    mg = S.MultigridSolver(probs[:1], "jacobi")
+    bb = b[0][None].contiguous()
+    xh, xl = torch.zeros_like(bb), torch.zeros_like(bb)
+    with pytest.raises(B.MGError):
+        B.mg_solve_multi([mg.ctx, mg.ctx], [bb, bb], [xh, xh], [xl, xl], 1e-8, 10)
+    with pytest.raises(B.MGError):
+        B.mg_solve_multi([], [], [], [], 1e-8, 10)
+    mg.close()
+
+
+@pytest.mark.parametrize("ct", [True, False])
+def test_small_tiled_batches_repeat_bit_identically(ct):
+    """Batches whose problems converge at different cycles at the smallest tiled sizes
+    (one tile level above the coarse tail): repeated solves give identical iterates and
+    cycle counts, and every problem reaches rtol.  Problems drop out of the launches one by
+    one here, so every kernel sees the stopping flags change between cycles."""
+    for n, count in ((127, 6), (255, 5)):
+        params = inputs.rotated_params(inputs.SEED_PARAMS + 41 + n, count, eps_lo=0.05)
+        mg = S.MultigridSolver([S.rotated(n, e, t) for e, t in params], cluster_tail=ct)
+        b = torch.from_numpy(np.stack([inputs.rhs_uniform(inputs.SEED_RHS + 700 + i, n) for i in range(count)]))
+        b = b.cuda().contiguous()
+        runs = []
+        for _ in range(3):
+            xh, xl, gh, cyc, st = mg.solve(b, rtol=1e-8, max_cycles=3000)
+            assert st == B.MG_OK
+            assert len(set(cyc.tolist())) > 1  # the problems stop at different cycles
+            runs.append((xh.clone(), cyc.copy()))
+        for xh, cyc in runs[1:]:
+            assert np.array_equal(cyc, runs[0][1])
+            assert torch.equal(xh, runs[0][0])
+        mg.close()
