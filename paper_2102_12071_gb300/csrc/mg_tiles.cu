@@ -765,9 +765,9 @@ cudaError_t launch_cycle(const CycleArgs& a, float rtol, int max_cycles, int par
   for (int l = ls - 1; l >= 0 && e == cudaSuccess; --l) {
     const int nt = tiles_per_side(a.nl[l]);
     dim3 grid(nt * nt, np);
-    // The kernel after the cluster tail waits for it by plain stream order: launched with
-    // programmatic serialisation it was seen to read the tail's e before all of it was
-    // written (run-to-run differences in 16-problem batches, none with plain ordering).
+    // The kernel after the cluster tail waits for it by plain stream order: with
+    // programmatic serialisation the cycle measured no faster (the tail's clusters hold
+    // whole SMs, so the next kernel has little room to start early).
     const bool pdl = a.pdl && !(a.ctail && l == ls - 1);
     a.prof->launches++;
     a.prof->begin(l == 0 ? PK_UP0 : PK_UP, a.stream);
