@@ -77,14 +77,18 @@ __device__ __forceinline__ int st_active(const ProbState* st) { return __ldcg(&s
 
 // ---------------------------------------------------------------- float-float
 // Error-free transformations (Knuth's TwoSum; FMA-based TwoProduct, Dekker 1971).
+// Error-free transformations.  Written with the _rn intrinsics, which the compiler never
+// contracts into a fused multiply-add: a product feeding one of these sums (a * x in a
+// compensated dot product) would otherwise be fused into it, and s + e would no longer
+// equal a + b exactly.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 __device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  e = b - (s - a);
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
 }
 __device__ __forceinline__ void ff_add(float& hi, float& lo, float bhi, float blo) {
   float s, e;

@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_solve(const ProbDev* __re
         if (!in_grid(ii, jj, n)) continue;
         const float a = (SK == SK_CONST) ? sc[0][k] : __ldg(L0.st + k * nn + q);
         const float x = xh[ii * n + jj];
-        const float pr = a * x, pe = fmaf(a, x, -pr);
+        const float pr = __fmul_rn(a, x), pe = fmaf(a, x, -pr);
         float sum, err;
         two_sum(hi, -pr, sum, err);
         hi = sum;
@@ -245,6 +245,9 @@ cudaError_t launch_bnorm(const CycleArgs& a, const float* b) {
   const int nt = tiles_per_side(a.n0);
   dim3 grid(nt * nt, a.nprob);
   a.prof->launches++;
+  // norm partial slots start empty (see block_partial_and_last)
+  cudaError_t e = cudaMemsetAsync(a.partials, 0xff, sizeof(float) * (size_t)a.nprob * a.ntiles_max, a.stream);
+  if (e != cudaSuccess) return e;
   k_bnorm<<<grid, NT, 0, a.stream>>>(a.probs, a.state, a.partials, a.ntiles_max, b);
   return cudaGetLastError();
 }

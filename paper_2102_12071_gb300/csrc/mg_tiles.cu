@@ -151,7 +151,7 @@ __device__ __forceinline__ bool inside(int i, int j, int n) { return (unsigned)i
 // r - A x with x = xh + xl (Dot2: exact products and error-free sums for xh, plain FP32
 // for the xl terms), taps in the order of dot9's index k
 __device__ __forceinline__ void dot2_sub(float a, float x, float xl, float& hi, float& lo) {
-  const float pr = a * x;
+  const float pr = __fmul_rn(a, x);
   const float pe = fmaf(a, x, -pr);
   float sum, err;
   two_sum(hi, -pr, sum, err);
