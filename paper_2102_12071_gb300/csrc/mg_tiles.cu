@@ -38,6 +38,10 @@ constexpr int UPR_H = TB + 2;    // k_up r box: rows R0-1 .. R0+32
 constexpr int EC_W = TB / 2 + 8; // k_up coarse box: columns C0/2-4 .. C0/2+19
 constexpr int EC_H = TB / 2 + 3; //                  rows    R0/2-2 .. R0/2+16
 constexpr int ES = TB + 3;       // k_down e buffer side (rows/cols R0-1 .. R0+33)
+// Row stride of that buffer.  The residual pass reads it in 5-row strips of 33 columns, so
+// a warp spans two strips; 5 * 45 = 1 (mod 32) puts the second strip's lanes exactly on
+// the banks the first strip's lanes leave free (a stride of 35 made most loads 2-way).
+constexpr int ESP = 45;
 constexpr int UP0E_H = TB + 6;   // k_up0 e box: rows R0-3 .. R0+34
 constexpr int UP0R_H = TB + 4;   // k_up0 r box: rows R0-2 .. R0+33
 constexpr int EC0_H = TB / 2 + 4; // k_up0 coarse box: rows R0/2-2 .. R0/2+17
@@ -287,7 +291,7 @@ __device__ __forceinline__ void down_tile(const LevelDev& L, const float (&s)[9]
           else v.b1 = c[k * XW];
           float e = 0.f;
           if (IN || inside(i, j, n)) e = tapply_H<SK, HK, IN>(L, s, wtab, wi, omega, i, j, v);
-          es[ti * ES + tj] = e;
+          es[ti * ESP + tj] = e;
           if (own_col && (unsigned)(ti - 1) < (unsigned)TB) eo[(ti - 1) * TB + tj - 1] = e;
           if (HK != HK_JACOBI) v.shift();
         }
@@ -300,16 +304,16 @@ __device__ __forceinline__ void down_tile(const LevelDev& L, const float (&s)[9]
     constexpr int W2 = TB + 1, NS = (W2 + KS - 1) / KS;
     if (t < W2 * NS) {
       const int tj = t % W2, t0 = (t / W2) * KS, j = C0 + tj;
-      const float* c = es + (t0 + 1) * ES + tj + 1;
+      const float* c = es + (t0 + 1) * ESP + tj + 1;
       float* rp = rs + (t0 + 2) * XW + tj + 4;
       Win v;
-      v.load_ab(c, ES);
+      v.load_ab(c, ESP);
 #pragma unroll
       for (int k = 0; k < KS; ++k) {
         const int ti = t0 + k;
         if (ti < W2) {
           const int i = R0 + ti;
-          v.load_c(c + k * ES, ES);
+          v.load_c(c + k * ESP, ESP);
           float sv = 0.f;
           if (IN || inside(i, j, n)) sv = rp[k * XW] - tapply_A<SK>(L, s, i, j, v);
           rp[k * XW] = sv;
@@ -336,7 +340,7 @@ __global__ void __launch_bounds__(NT) k_down(const __grid_constant__ DownMaps M,
   __shared__ __align__(128) float rs[DN_H * XW];  // r, then s = r - A e in place
   __shared__ __align__(128) float eo[TB * TB];    // e on the owned points (stored by TMA)
   __shared__ __align__(128) float rco[TC * TC];   // r_c (stored by TMA)
-  __shared__ float es[ES * ES];
+  __shared__ float es[ES * ESP];
   __shared__ float wtab[HK == HK_TABLE ? 9 * MG_PROXY * MG_PROXY : 1];
   __shared__ __align__(8) uint64_t bar;
   const bool in = inner_tile(R0, C0, n);
