@@ -758,3 +758,90 @@ double or_twogrid_loss(int n, const double* st, const double* W, int nz, const d
   free(tmp); free(tmp2); free(xc);
   return loss;
 }
+
+/*
+ * The same objective after k two-grid cycles (eq. overalltrain with u_* = 0 and k cycles
+ * of the solver, the form Algorithm 2 minimises over k): with E = S C S,
+ *   loss = (1/nz) sum_j ||E^k z_j||^2 / n^2.
+ * Forward: e_0 = z, e_{c+1} = E e_c, keeping A e_c and A (C S e_c) of every cycle.
+ * Adjoint, cycles in reverse: g = dloss/de_{c+1} gives the two dW terms of cycle c
+ * exactly as in or_twogrid_loss, and dloss/de_c = E^T g = S^T C^T S^T g feeds cycle c-1.
+ */
+double or_twogrid_loss_k(int n, const double* st, const double* W, int nz, const double* z, int ncycles,
+                         double* dW) {
+  const int nn = n * n, nc = (n - 1) / 2, nnc = nc * nc, K = ncycles;
+  double* stc = (double*)malloc(sizeof(double) * 9 * nnc);
+  or_rap(n, st, stc);
+  double* Lc = (double*)malloc(sizeof(double) * (size_t)nnc * nnc);
+  or_dense_matrix(nc, stc, Lc);
+  or_cholesky(nnc, Lc);
+  double* V0 = (double*)malloc(sizeof(double) * (size_t)K * nn); /* A e_c          */
+  double* V2 = (double*)malloc(sizeof(double) * (size_t)K * nn); /* A (C S e_c)    */
+  double *e = malloc(sizeof(double) * nn), *e1 = malloc(sizeof(double) * nn);
+  double *g = malloc(sizeof(double) * nn), *tmp = malloc(sizeof(double) * nn), *tmp2 = malloc(sizeof(double) * nn);
+  double* xc = malloc(sizeof(double) * nnc);
+  double loss = 0.0;
+  for (int s = 0; s < nz; ++s) {
+    memcpy(e, z + (size_t)s * nn, sizeof(double) * nn);
+    for (int c = 0; c < K; ++c) {
+      double* v0 = V0 + (size_t)c * nn;
+      double* v2 = V2 + (size_t)c * nn;
+      /* pre-smoothing: e1 = e - H A e */
+      or_apply(n, st, e, v0);
+      or_apply_H(n, W, v0, tmp);
+      for (int p = 0; p < nn; ++p) e1[p] = e[p] - tmp[p];
+      /* coarse correction: e = e1 - P Ac^{-1} P^T A e1 */
+      or_apply(n, st, e1, tmp);
+      or_restrict(n, tmp, xc);
+      or_cholesky_solve(nnc, Lc, xc);
+      for (int p = 0; p < nn; ++p) tmp[p] = 0.0;
+      or_prolong_add(n, xc, tmp);
+      for (int p = 0; p < nn; ++p) e[p] = e1[p] - tmp[p];
+      /* post-smoothing: e = e - H A e */
+      or_apply(n, st, e, v2);
+      or_apply_H(n, W, v2, tmp);
+      for (int p = 0; p < nn; ++p) e[p] -= tmp[p];
+    }
+    double sq = 0.0;
+    for (int p = 0; p < nn; ++p) sq += e[p] * e[p];
+    loss += sq / ((double)nz * nn);
+    if (!dW) continue;
+    for (int p = 0; p < nn; ++p) g[p] = 2.0 * e[p] / ((double)nz * nn);
+    for (int c = K - 1; c >= 0; --c) {
+      const double* v0 = V0 + (size_t)c * nn;
+      const double* v2 = V2 + (size_t)c * nn;
+      /* post-smoothing of cycle c */
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+          for (int k = 0; k < 9; ++k) {
+            const int ii = i + k / 3 - 1, jj = j + k % 3 - 1;
+            if (inside(n, ii, jj)) dW[k * nn + i * n + j] -= g[i * n + j] * v2[ii * n + jj];
+          }
+      or_apply_HT(n, W, g, tmp);
+      or_apply(n, st, tmp, tmp2);
+      for (int p = 0; p < nn; ++p) g[p] -= tmp2[p];
+      /* C^T = I - A P Ac^{-1} P^T */
+      or_restrict(n, g, xc);
+      or_cholesky_solve(nnc, Lc, xc);
+      for (int p = 0; p < nn; ++p) tmp[p] = 0.0;
+      or_prolong_add(n, xc, tmp);
+      or_apply(n, st, tmp, tmp2);
+      for (int p = 0; p < nn; ++p) g[p] -= tmp2[p];
+      /* pre-smoothing of cycle c */
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+          for (int k = 0; k < 9; ++k) {
+            const int ii = i + k / 3 - 1, jj = j + k % 3 - 1;
+            if (inside(n, ii, jj)) dW[k * nn + i * n + j] -= g[i * n + j] * v0[ii * n + jj];
+          }
+      /* dloss/de_c = S^T g for the cycle before */
+      if (c > 0) {
+        or_apply_HT(n, W, g, tmp);
+        or_apply(n, st, tmp, tmp2);
+        for (int p = 0; p < nn; ++p) g[p] -= tmp2[p];
+      }
+    }
+  }
+  free(stc); free(Lc); free(V0); free(V2); free(e); free(e1); free(g); free(tmp); free(tmp2); free(xc);
+  return loss;
+}

@@ -75,6 +75,9 @@ void or_hypernet_backward(int n, const double* st, const double* params, double 
 /* ---- convergence-theory loss (eq. twogrid, eq. overalltrain, Thm. sbound) ---- */
 double or_twogrid_loss(int n, const double* st, const double* W, int nz, const double* z,
                        double* dW);
+/* the same objective after ncycles >= 1 two-grid cycles: (1/nz) sum ||(S C S)^k z||^2 / n^2 */
+double or_twogrid_loss_k(int n, const double* st, const double* W, int nz, const double* z,
+                         int ncycles, double* dW);
 
 #ifdef __cplusplus
 }

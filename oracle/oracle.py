@@ -57,6 +57,8 @@ def lib():
         L.or_bf16.argtypes = [ctypes.c_double]
         L.or_twogrid_loss.restype = ctypes.c_double
         L.or_twogrid_loss.argtypes = [ctypes.c_int, _D, _D, ctypes.c_int, _D, _D]
+        L.or_twogrid_loss_k.restype = ctypes.c_double
+        L.or_twogrid_loss_k.argtypes = [ctypes.c_int, _D, _D, ctypes.c_int, _D, ctypes.c_int, _D]
         L.or_cholesky.argtypes = [ctypes.c_int, _D]
         L.or_cholesky_solve.argtypes = [ctypes.c_int, _D, _D]
         L.or_q1_rotated_stencil.argtypes = [ctypes.c_double, ctypes.c_double, _D]
@@ -286,18 +288,23 @@ def hypernet_backward(st, params, dW, omega: float = 2.0 / 3.0, bf16: bool = Fal
     return g
 
 
-def twogrid_loss(st, W, z, want_grad: bool = False):
-    """Loss (1/Z) sum_j ||S C S z_j||^2 / n and, optionally, dLoss/dW."""
+def twogrid_loss(st, W, z, want_grad: bool = False, cycles: int = 1):
+    """Loss (1/Z) sum_j ||(S C S)^k z_j||^2 / n^2 (k = cycles) and, optionally, dLoss/dW.
+    cycles = 1 is the two-grid objective of eq. twogrid; k > 1 the k-cycle form of eq.
+    overalltrain that Algorithm 2 minimises."""
     st, W, z = _f64(st), _f64(W), _f64(z)
     n = st.shape[1]
     nz = z.shape[0]
     dW = np.zeros((9, n, n)) if want_grad else None
-    loss = lib().or_twogrid_loss(n, _p(st), _p(W), nz, _p(z), _p(dW) if want_grad else None)
+    if cycles == 1:
+        loss = lib().or_twogrid_loss(n, _p(st), _p(W), nz, _p(z), _p(dW) if want_grad else None)
+    else:
+        loss = lib().or_twogrid_loss_k(n, _p(st), _p(W), nz, _p(z), int(cycles), _p(dW) if want_grad else None)
     return (loss, dW) if want_grad else loss
 
 
-def cnn_loss_and_grad(st, params, z, omega: float = 2.0 / 3.0, bf16: bool = False):
+def cnn_loss_and_grad(st, params, z, omega: float = 2.0 / 3.0, bf16: bool = False, cycles: int = 1):
     """Loss of one problem as a function of the network parameters, with its gradient."""
     W = hypernet_forward(st, params, omega, bf16)
-    loss, dW = twogrid_loss(st, W, z, want_grad=True)
+    loss, dW = twogrid_loss(st, W, z, want_grad=True, cycles=cycles)
     return loss, hypernet_backward(st, params, dW, omega, bf16)

@@ -163,3 +163,52 @@ def test_loss_estimates_frobenius_norm():
     # per-sample variance of ||E z||^2 is 2 ||E^T E||_F^2; 5 standard errors
     sd = math.sqrt(2 * np.sum((E.T @ E) ** 2)) / (n * n) / math.sqrt(Z)
     assert abs(est - fro) < 5 * sd
+
+
+@pytest.mark.parametrize("cycles", [2, 3])
+def test_k_cycle_loss_matches_dense_power(cycles):
+    """The k-cycle objective against the dense matrix power: (1/Z) sum ||E^k z||^2 / n^2."""
+    n = 15
+    st = O.const_field(n, O.q1_rotated_stencil(0.05, 1.0))
+    W = O.jacobi_kernels(st) * (1 + 0.1 * np.random.default_rng(12).standard_normal((9, n, n)))
+    z = np.random.default_rng(13).standard_normal((4, n, n))
+    Ek = np.linalg.matrix_power(_dense_E(st, W), cycles)
+    want = np.mean([np.sum((Ek @ zi.ravel()) ** 2) / (n * n) for zi in z])
+    assert abs(O.twogrid_loss(st, W, z, cycles=cycles) - want) < 1e-12 * want
+
+
+def test_k_cycle_loss_with_one_cycle_is_the_two_grid_loss():
+    n = 15
+    st = O.const_field(n, O.q1_rotated_stencil(0.3, 2.0))
+    W = O.jacobi_kernels(st) * (1 + 0.1 * np.random.default_rng(14).standard_normal((9, n, n)))
+    z = np.random.default_rng(15).standard_normal((3, n, n))
+    l1, g1 = O.twogrid_loss(st, W, z, want_grad=True)
+    # the k-cycle routine itself, called with k = 1
+    from oracle import oracle as OM
+
+    dW = np.zeros((9, n, n))
+    lk = OM.lib().or_twogrid_loss_k(n, OM._p(OM._f64(st)), OM._p(OM._f64(W)), 3, OM._p(OM._f64(z)), 1, OM._p(dW))
+    assert lk == l1
+    np.testing.assert_array_equal(dW, g1)
+
+
+def test_k_cycle_gradient_matches_finite_differences():
+    """dloss/dparams of the 3-cycle objective against FP64 central differences (h = 1e-6)."""
+    n = 15
+    rng = np.random.default_rng(16)
+    st = O.const_field(n, O.q1_rotated_stencil(10 ** rng.uniform(-3, 0), rng.uniform(0, math.pi)))
+    p = rng.standard_normal(NP) * 0.2
+    z = rng.standard_normal((2, n, n))
+    loss, g = O.cnn_loss_and_grad(st, p, z, cycles=3)
+    h = 1e-6
+    for i in list(rng.choice(NP, 10, replace=False)) + [NP - 1, 0]:
+        pp, pm = p.copy(), p.copy()
+        pp[i] += h
+        pm[i] -= h
+        fd = (O.twogrid_loss(st, O.hypernet_forward(st, pp), z, cycles=3)
+              - O.twogrid_loss(st, O.hypernet_forward(st, pm), z, cycles=3)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(abs(g).max(), 1e-12), (i, fd, g[i])
+    d = rng.standard_normal(NP)
+    lp = O.twogrid_loss(st, O.hypernet_forward(st, p + h * d), z, cycles=3)
+    lm = O.twogrid_loss(st, O.hypernet_forward(st, p - h * d), z, cycles=3)
+    assert abs((lp - lm) / (2 * h) - g @ d) <= 1e-6 * abs(g @ d)
