@@ -324,8 +324,28 @@ def run_train(steps: int = 5):
         torch.cuda.synchronize()
         per[str(n)] = e0.elapsed_time(e1) / 20
         batch.close()
+    # the loss after k = 4 two-grid cycles at 63^2 (adjoint through all four), with every
+    # cycle's products kept and with checkpointing (cycle inputs only, products recomputed)
+    kc = {}
+    for ckpt in (False, True):
+        batch = T.TwoGridBatch(tr.problems(0, 63), 32, conv_bf16=True, cycles=4, checkpoint=ckpt)
+        z = torch.randn((32, 32, 63, 63), device="cuda")
+        p = tr.params.detach()
+        for _ in range(3):
+            batch.loss_and_grad(p, z)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            batch.loss_and_grad(p, z)
+        e1.record()
+        torch.cuda.synchronize()
+        kc["checkpoint" if ckpt else "stored"] = {"ms": e0.elapsed_time(e1) / 10,
+                                                  "workspace_mb": round(batch.workspace.numel() / 2 ** 20, 1)}
+        batch.close()
     return {"problems": "32 x 31^2 + 32 x 63^2 rotated, 32 vectors each", "step_ms": step_ms,
-            "loss_and_grad_ms": per, "last_loss": loss, "steps_timed": steps}
+            "loss_and_grad_ms": per, "last_loss": loss, "steps_timed": steps,
+            "four_cycle_loss_63": kc}
 
 
 def mixed_batch(count: int, rank: int):

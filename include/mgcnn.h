@@ -96,6 +96,11 @@ typedef struct {
                        one CTA per problem and the levels above in tiled kernels.  Both
                        compute the same cycle; the choice only changes how it is laid out
                        on the GPU.  Problems of side <= 63 always run in one CTA each.   */
+  int train_cycles;     /* training only (mg_train_*): the most two-grid cycles k the loss
+                           may span, workspace reserved for (0 or 1: one cycle; <= 16)   */
+  int train_checkpoint; /* training only: 1 keeps just each cycle's input vectors and
+                           recomputes the cycle's operator products in the backward pass
+                           (one vector set per cycle instead of three)                   */
 } mg_options;
 
 typedef struct mg_ctx mg_ctx;
@@ -209,15 +214,20 @@ mg_status mg_train_setup(const mg_problem* problems, int nprob, int nvec,
 void mg_train_destroy(mg_train_ctx* ctx);
 
 /* Loss and gradient of the two-grid convergence objective (eq. twogrid with one pre- and
-   one post-smoothing step, eq. overalltrain with u_* = 0, Thm. sbound):
-     loss = (1/nprob) sum_b (1/nvec) sum_j || S C S z_bj ||^2 / n^2,
+   one post-smoothing step, eq. overalltrain with u_* = 0, Thm. sbound), after k cycles:
+     loss = (1/nprob) sum_b (1/nvec) sum_j || (S C S)^k z_bj ||^2 / n^2,
      S = I - H A,  C = I - P (P^T A P)^{-1} P^T A,
-   with H the network's per-point kernels for problem b.  z: DEVICE float[nprob][nvec][n][n]
-   (the random vectors, supplied by the caller), params: DEVICE float[mg_net_nparams()],
-   grad_out: DEVICE float[mg_net_nparams()] (overwritten with dloss/dparams; may be NULL),
-   loss_out: DEVICE float[1]. */
+   with H the network's per-point kernels for problem b and k set by mg_train_set_cycles
+   (default: train_cycles of the setup).  z: DEVICE float[nprob][nvec][n][n] (the random
+   vectors, supplied by the caller), params: DEVICE float[mg_net_nparams()], grad_out:
+   DEVICE float[mg_net_nparams()] (overwritten with dloss/dparams, the adjoint through all
+   k cycles; may be NULL), loss_out: DEVICE float[1]. */
 mg_status mg_train_step(mg_train_ctx* ctx, const float* params, const float* z,
                         float* grad_out, float* loss_out, void* stream);
+
+/* Number of two-grid cycles k of the following mg_train_step calls, 1 <= k <=
+   max(1, train_cycles of the setup); Algorithm 2 draws k uniformly per step.  Host-only. */
+mg_status mg_train_set_cycles(mg_train_ctx* ctx, int cycles);
 
 /* ------------------------------------------------- solving without a workspace ---- */
 

@@ -8,6 +8,10 @@
 // Adjoint: g3 = 2 e3 / (n^2 Z B); dW_p[k] -= g3(p) v2(p+d_k); g2 = g3 - A H^T g3;
 //          g1 = g2 - A P (P^T A P)^{-1} P^T g2; dW_p[k] -= g1(p) v0(p+d_k);
 // then dW -> d(params) through the network (mg_net.cu).
+// After k cycles (E = S C S, loss = ... ||E^k z||^2): the forward keeps A e and A (C S e)
+// of every cycle, or with checkpointing only each cycle's input e and recomputes the two
+// products when the adjoint reaches that cycle; the adjoint runs the cycles in reverse,
+// adds both dW terms of each, and passes E^T g = S^T C^T S^T g to the cycle before.
 //
 // All problems of a batch share n, so every kernel runs over (problem, vector, point) in
 // one launch; the data of a 64 x 32 batch at 63^2 (~16 MB per vector set) stays in L2.
@@ -178,7 +182,8 @@ __global__ void k_t_loss_total(const float* __restrict__ partial, int nvecs, flo
 
 // dW_p[k] = -sum_j ( g3_j(p) v2_j(p+d_k) + g1_j(p) v0_j(p+d_k) )   (one thread per (b, p))
 __global__ void k_t_dW(TrainDims D, const float* __restrict__ g3, const float* __restrict__ v2,
-                       const float* __restrict__ g1, const float* __restrict__ v0, float* __restrict__ dW) {
+                       const float* __restrict__ g1, const float* __restrict__ v0, float* __restrict__ dW,
+                       int accumulate) {
   const int b = blockIdx.y;
   const int q = blockIdx.x * TT + threadIdx.x;
   if (q >= (int)D.nn) return;
@@ -201,7 +206,7 @@ __global__ void k_t_dW(TrainDims D, const float* __restrict__ g3, const float* _
   }
   float* out = dW + (size_t)b * 9 * D.nn;
 #pragma unroll
-  for (int k = 0; k < 9; ++k) out[k * D.nn + q] = -acc[k];
+  for (int k = 0; k < 9; ++k) out[k * D.nn + q] = accumulate ? out[k * D.nn + q] - acc[k] : -acc[k];
 }
 
 // ---------------------------------------------------------------- coarse solve
@@ -373,14 +378,21 @@ struct mg_train_ctx {
   float* param_partial = nullptr;
   int* fail = nullptr;
   int ncta_bw = 0;
+  int kmax = 1, k = 1, ckpt = 0;   // cycles reserved / used by the loss; checkpointing
+  std::vector<float*> X;           // X[c]: input of cycle c >= 1
+  std::vector<float*> V0, V2;      // A e_c and A (C S e_c) of cycle c (V0[0] = v0, V2[0] = v2)
   std::vector<float> h_s9;
   std::vector<ProbDev> h_probs;
 };
 
 namespace {
 
+constexpr int kMaxTrainCycles = 16;
+
 mg_status train_dims(const mg_problem* probs, int nprob, int nvec, const mg_options* o, TrainDims& D, int& is_const) {
   if (!probs || nprob < 1 || nvec < 1 || !o) return (mg_status)api_fail(MG_ERR_INVALID_ARG, "training: bad arguments");
+  if (o->train_cycles < 0 || o->train_cycles > kMaxTrainCycles)
+    return (mg_status)api_fail(MG_ERR_INVALID_ARG, "train_cycles must be in [0, %d]", kMaxTrainCycles);
   if ((long long)nprob * nvec > 65535) return (mg_status)api_fail(MG_ERR_INVALID_ARG, "nprob * nvec must be <= 65535");
   if (!(o->omega > 0.f) || !(o->omega < 2.f)) return (mg_status)api_fail(MG_ERR_INVALID_ARG, "omega must be in (0, 2)");
   const int n = probs[0].n;
@@ -423,7 +435,7 @@ T* take(char* base, size_t& off, size_t count) {
   return p;
 }
 
-size_t train_carve(const TrainDims& D, void* basev, mg_train_ctx* c) {
+size_t train_carve(const TrainDims& D, int kmax, int ckpt, void* basev, mg_train_ctx* c) {
   char* base = (char*)basev;
   size_t off = 0;
   const size_t BZ = (size_t)D.B * D.Z, m = D.nnc, ld = D.w + 1;
@@ -440,6 +452,16 @@ size_t train_carve(const TrainDims& D, void* basev, mg_train_ctx* c) {
   x.ybuf = take<double>(base, off, m * BZ);
   float** vecs[] = {&x.v0, &x.e1, &x.e2, &x.v2, &x.g3, &x.t, &x.g2, &x.g1};
   for (float** v : vecs) *v = take<float>(base, off, D.nn * BZ);
+  x.X.assign(kmax, nullptr);
+  x.V0.assign(kmax, x.v0);
+  x.V2.assign(kmax, x.v2);
+  for (int c = 1; c < kmax; ++c) {
+    x.X[c] = take<float>(base, off, D.nn * BZ);
+    if (!ckpt) {
+      x.V0[c] = take<float>(base, off, D.nn * BZ);
+      x.V2[c] = take<float>(base, off, D.nn * BZ);
+    }
+  }
   x.rc = take<float>(base, off, D.nnc * BZ);
   x.xc = take<float>(base, off, D.nnc * BZ);
   x.loss_partial = take<float>(base, off, BZ);
@@ -463,7 +485,8 @@ size_t mg_train_workspace_size(const mg_problem* problems, int nprob, int nvec, 
   TrainDims D;
   int is_const = 0;
   if (train_dims(problems, nprob, nvec, opts, D, is_const) != MG_OK) return 0;
-  return train_carve(D, nullptr, nullptr);
+  return train_carve(D, opts->train_cycles > 1 ? opts->train_cycles : 1, opts->train_checkpoint != 0, nullptr,
+                     nullptr);
 }
 
 mg_status mg_train_setup(const mg_problem* problems, int nprob, int nvec, const mg_options* opts, void* workspace,
@@ -474,7 +497,8 @@ mg_status mg_train_setup(const mg_problem* problems, int nprob, int nvec, const 
   int is_const = 0;
   mg_status st = train_dims(problems, nprob, nvec, opts, D, is_const);
   if (st != MG_OK) return st;
-  const size_t need = train_carve(D, nullptr, nullptr);
+  const int kmax = opts->train_cycles > 1 ? opts->train_cycles : 1, ckpt = opts->train_checkpoint != 0;
+  const size_t need = train_carve(D, kmax, ckpt, nullptr, nullptr);
   if (!workspace || ws_bytes < need)
     return (mg_status)api_fail(MG_ERR_WORKSPACE, "training workspace needs %zu bytes, got %zu", need, ws_bytes);
   if (((uintptr_t)workspace & 255) != 0) return (mg_status)api_fail(MG_ERR_WORKSPACE, "workspace must be 256-byte aligned");
@@ -483,7 +507,9 @@ mg_status mg_train_setup(const mg_problem* problems, int nprob, int nvec, const 
   c->D = D;
   c->bf16 = opts->conv_bf16;
   c->omega = opts->omega;
-  train_carve(D, workspace, c);
+  c->kmax = c->k = kmax;
+  c->ckpt = ckpt;
+  train_carve(D, kmax, ckpt, workspace, c);
   auto run = [&]() -> mg_status {
     const dim3 gp((unsigned)((D.nn + TT - 1) / TT), D.B);
     if (is_const) {
@@ -536,6 +562,13 @@ mg_status mg_train_setup(const mg_problem* problems, int nprob, int nvec, const 
 
 void mg_train_destroy(mg_train_ctx* ctx) { delete ctx; }
 
+mg_status mg_train_set_cycles(mg_train_ctx* ctx, int cycles) {
+  if (!ctx || cycles < 1 || cycles > ctx->kmax)
+    return (mg_status)api_fail(MG_ERR_INVALID_ARG, "cycles must be in [1, train_cycles of the setup]");
+  ctx->k = cycles;
+  return MG_OK;
+}
+
 mg_status mg_train_step(mg_train_ctx* c, const float* params, const float* z, float* grad_out, float* loss_out,
                         void* stream) {
   if (!c || !params || !z || !loss_out) return (mg_status)api_fail(MG_ERR_INVALID_ARG, "mg_train_step: bad arguments");
@@ -552,26 +585,41 @@ mg_status mg_train_step(mg_train_ctx* c, const float* params, const float* z, fl
   nb.n = D.n;
   nb.pad_ = 0;
   TCK(launch_net_forward_batch(nb, D.B, params, c->omega, c->bf16, s));
-  // forward: e1 = S z, e2 = C e1, e3 = S e2
-  k_t_applyA<<<gv, TT, 0, s>>>(D, c->fields, z, c->v0);
-  k_t_xmHv<<<gv, TT, 0, s>>>(D, c->fields, c->W, z, c->v0, c->e1);
-  k_t_restrict<<<gc, TT, 0, s>>>(D, c->fields, c->e1, 1, c->rc);
-  k_t_band_solve<<<solve_blocks, 128, 0, s>>>(D, c->band, c->ut, c->rc, c->ybuf, c->xc, BZ);
-  k_t_xmP<<<gv, TT, 0, s>>>(D, c->e1, c->xc, c->e2);
-  k_t_applyA<<<gv, TT, 0, s>>>(D, c->fields, c->e2, c->v2);
-  k_t_xmHv<<<gv, TT, 0, s>>>(D, c->fields, c->W, c->e2, c->v2, c->g3);
+  const int K = c->k;
+  // one cycle e_out = S C S e_in, keeping v0 = A e_in and v2 = A (C S e_in); e_out may be
+  // NULL (recomputation of the products only)
+  auto cycle = [&](const float* ein, float* v0, float* v2, float* eout) {
+    k_t_applyA<<<gv, TT, 0, s>>>(D, c->fields, ein, v0);
+    k_t_xmHv<<<gv, TT, 0, s>>>(D, c->fields, c->W, ein, v0, c->e1);
+    k_t_restrict<<<gc, TT, 0, s>>>(D, c->fields, c->e1, 1, c->rc);
+    k_t_band_solve<<<solve_blocks, 128, 0, s>>>(D, c->band, c->ut, c->rc, c->ybuf, c->xc, BZ);
+    k_t_xmP<<<gv, TT, 0, s>>>(D, c->e1, c->xc, c->e2);
+    k_t_applyA<<<gv, TT, 0, s>>>(D, c->fields, c->e2, v2);
+    if (eout) k_t_xmHv<<<gv, TT, 0, s>>>(D, c->fields, c->W, c->e2, v2, eout);
+  };
+  // forward: e_{c+1} = S C S e_c; the last output goes to g3
+  for (int cc = 0; cc < K; ++cc)
+    cycle(cc == 0 ? z : c->X[cc], c->V0[cc], c->V2[cc], cc + 1 < K ? c->X[cc + 1] : c->g3);
   k_t_loss<<<BZ, TT, 0, s>>>(D, c->g3, 2.f * inv, c->g3, c->loss_partial);
   k_t_loss_total<<<1, 32, 0, s>>>(c->loss_partial, BZ, inv, loss_out);
   TCK(cudaGetLastError());
   if (!grad_out) return MG_OK;
-  // adjoint
-  k_t_HT<<<gv, TT, 0, s>>>(D, c->fields, c->W, c->g3, c->t);
-  k_t_xmAv<<<gv, TT, 0, s>>>(D, c->fields, c->g3, c->t, c->g2);
-  k_t_restrict<<<gc, TT, 0, s>>>(D, c->fields, c->g2, 0, c->rc);
-  k_t_band_solve<<<solve_blocks, 128, 0, s>>>(D, c->band, c->ut, c->rc, c->ybuf, c->xc, BZ);
-  k_t_P<<<gv, TT, 0, s>>>(D, c->xc, c->t);
-  k_t_xmAv<<<gv, TT, 0, s>>>(D, c->fields, c->g2, c->t, c->g1);
-  k_t_dW<<<dim3((unsigned)((D.nn + TT - 1) / TT), D.B), TT, 0, s>>>(D, c->g3, c->v2, c->g1, c->v0, c->dW);
+  // adjoint, cycles in reverse; g3 = dloss/d(output of cycle cc)
+  for (int cc = K - 1; cc >= 0; --cc) {
+    if (c->ckpt && cc + 1 < K) cycle(cc == 0 ? z : c->X[cc], c->V0[cc], c->V2[cc], nullptr);
+    k_t_HT<<<gv, TT, 0, s>>>(D, c->fields, c->W, c->g3, c->t);
+    k_t_xmAv<<<gv, TT, 0, s>>>(D, c->fields, c->g3, c->t, c->g2);
+    k_t_restrict<<<gc, TT, 0, s>>>(D, c->fields, c->g2, 0, c->rc);
+    k_t_band_solve<<<solve_blocks, 128, 0, s>>>(D, c->band, c->ut, c->rc, c->ybuf, c->xc, BZ);
+    k_t_P<<<gv, TT, 0, s>>>(D, c->xc, c->t);
+    k_t_xmAv<<<gv, TT, 0, s>>>(D, c->fields, c->g2, c->t, c->g1);
+    k_t_dW<<<dim3((unsigned)((D.nn + TT - 1) / TT), D.B), TT, 0, s>>>(D, c->g3, c->V2[cc], c->g1, c->V0[cc], c->dW,
+                                                                       cc + 1 < K);
+    if (cc > 0) {  // dloss/d(input of cycle cc) = S^T g1
+      k_t_HT<<<gv, TT, 0, s>>>(D, c->fields, c->W, c->g1, c->t);
+      k_t_xmAv<<<gv, TT, 0, s>>>(D, c->fields, c->g1, c->t, c->g3);
+    }
+  }
   TCK(cudaGetLastError());
   TCK(launch_net_backward(nb, D.B, c->dW, params, c->bf16, c->param_partial, 1.f, grad_out, s));
   return MG_OK;

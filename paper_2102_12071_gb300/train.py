@@ -43,12 +43,12 @@ class TwoGridBatch:
     """Device workspace + context for one training batch of same-size problems."""
 
     def __init__(self, problems: list[dict], nvec: int, omega: float = 2.0 / 3.0, conv_bf16: bool = False,
-                 workspace: torch.Tensor | None = None):
+                 workspace: torch.Tensor | None = None, cycles: int = 1, checkpoint: bool = False):
         self.n = problems[0]["n"]
         self.nprob = len(problems)
         self.nvec = nvec
         self._probs, self._keep = B.problems_array(problems)
-        self.opts = B.options(B.MG_SMOOTH_CNN, omega, 3, int(conv_bf16))
+        self.opts = B.options(B.MG_SMOOTH_CNN, omega, 3, int(conv_bf16), 1, int(cycles), int(checkpoint))
         size = B.mg_train_workspace_size(self._probs, self.nprob, nvec, self.opts)
         if size == 0:
             raise B.MGError(B.MG_ERR_INVALID_ARG, "mg_train_workspace_size", B.lib().mg_last_error().decode())
@@ -64,6 +64,10 @@ class TwoGridBatch:
 
     def __del__(self):
         self.close()
+
+    def set_cycles(self, cycles: int) -> None:
+        """Two-grid cycles k of the loss (at most the `cycles` given at construction)."""
+        B.mg_train_set_cycles(self.ctx, cycles)
 
     def loss_and_grad(self, params: torch.Tensor, z: torch.Tensor, want_grad: bool = True):
         assert z.shape == (self.nprob, self.nvec, self.n, self.n) and z.is_contiguous()
@@ -94,7 +98,10 @@ class Trainer:
 
     def __init__(self, sizes=(31, 63), per_size: int = 32, nvec: int = 32, omega: float = 2.0 / 3.0,
                  conv_bf16: bool = True, lr: float = 1e-3, seed: int = 0, eps_range=(1e-3, 1.0),
-                 families=("rotated",)):
+                 families=("rotated",), max_cycles: int = 1, checkpoint: bool = False):
+        """max_cycles = b of Algorithm 2: each step's loss spans k ~ U{1..b} two-grid cycles."""
+        self.max_cycles = max_cycles
+        self.checkpoint = checkpoint
         self.sizes = sizes
         self.per_size = per_size
         self.nvec = nvec
@@ -118,14 +125,23 @@ class Trainer:
                  "data": torch.from_numpy(inputs.grf_cells(seed * 64 + k, n)).cuda()}
                 for k in range(self.per_size)]
 
+    def cycles(self, step: int) -> int:
+        """k of this step, drawn uniformly from 1..max_cycles (seeded by the step)."""
+        if self.max_cycles <= 1:
+            return 1
+        return int(np.random.default_rng(inputs.SEED_TRAIN + 31 * step).integers(1, self.max_cycles + 1))
+
     def loss(self, step: int) -> torch.Tensor:
         total = 0.0
         count = 0
+        k = self.cycles(step)
         for family in self.families:
             for n in self.sizes:
                 probs = self.problems(step, n, family)
                 key = (family, n)
-                batch = TwoGridBatch(probs, self.nvec, self.omega, self.conv_bf16, self._ws.get(key))
+                batch = TwoGridBatch(probs, self.nvec, self.omega, self.conv_bf16, self._ws.get(key),
+                                     cycles=self.max_cycles, checkpoint=self.checkpoint)
+                batch.set_cycles(k)
                 self._ws[key] = batch.workspace
                 z = torch.randn((self.per_size, self.nvec, n, n), generator=self.gen, device="cuda")
                 total = total + TwoGridLoss.apply(self.params, z, batch)
@@ -157,12 +173,15 @@ def main():
                                                    "cnn_rotated.npy"))
     ap.add_argument("--fp32-conv", action="store_true")
     ap.add_argument("--families", default="rotated", help="comma list of rotated,varcoef")
+    ap.add_argument("--max-cycles", type=int, default=1, help="b: each step's loss spans k ~ U{1..b} cycles")
+    ap.add_argument("--checkpoint", action="store_true", help="recompute cycle products in the backward pass")
     args = ap.parse_args()
     from . import build
 
     build.build()
     tr = Trainer(lr=args.lr, seed=args.seed, conv_bf16=not args.fp32_conv,
-                 families=tuple(f.strip() for f in args.families.split(",")))
+                 families=tuple(f.strip() for f in args.families.split(",")), max_cycles=args.max_cycles,
+                 checkpoint=args.checkpoint)
     t0 = time.time()
     for s in range(args.steps):
         l = tr.step()

@@ -144,6 +144,54 @@ def test_train_step_matches_oracle_loss_and_gradient(n):
     np.testing.assert_allclose(g[big], go[big], rtol=1e-3)
 
 
+@pytest.mark.parametrize("n,cycles", [(15, 2), (15, 3), (31, 2)])
+def test_k_cycle_train_step_matches_oracle(n, cycles):
+    """The loss after k two-grid cycles and its adjoint through all k (north star line 3)
+    vs the FP64 oracle; with checkpointing the same numbers come out bit for bit."""
+    nprob, nvec = 3, 4
+    params = inputs.rotated_params(60 + n + cycles, nprob)
+    probs = [{"n": n, "kind": B.MG_PROBLEM_ROTATED, "eps": e, "theta": t} for e, t in params]
+    z = inputs.gaussian_vectors(61 + n, nprob * nvec, n).reshape(nprob, nvec, n, n)
+    zt = torch.from_numpy(z).cuda().contiguous()
+    p = small_net(7, 0.1)
+    pt = torch.from_numpy(p).cuda()
+    res = []
+    for ckpt in (False, True):
+        batch = T.TwoGridBatch(probs, nvec, 2.0 / 3.0, False, cycles=cycles, checkpoint=ckpt)
+        loss, grad = batch.loss_and_grad(pt, zt)
+        res.append((loss.item(), grad.double().cpu().numpy()))
+        batch.close()
+    assert res[0][0] == res[1][0]
+    np.testing.assert_array_equal(res[0][1], res[1][1])
+    lo, go = 0.0, np.zeros(p.size)
+    for k, (e, t) in enumerate(params):
+        st = O.const_field(n, f32(O.q1_rotated_stencil(e, t)))
+        l1, g1 = O.cnn_loss_and_grad(st, f32(p), f32(z[k]), cycles=cycles)
+        lo += l1 / nprob
+        go += g1 / nprob
+    loss, g = res[0]
+    assert abs(loss - lo) <= 1e-5 * lo
+    assert np.linalg.norm(g - go) <= 1e-4 * np.linalg.norm(go)
+
+
+def test_train_step_cycle_count_is_settable():
+    """A batch set up for k = 3 evaluates k = 1 exactly like a one-cycle batch."""
+    n, nprob, nvec = 15, 2, 3
+    params = inputs.rotated_params(90, nprob)
+    probs = [{"n": n, "kind": B.MG_PROBLEM_ROTATED, "eps": e, "theta": t} for e, t in params]
+    zt = torch.from_numpy(inputs.gaussian_vectors(91, nprob * nvec, n).reshape(nprob, nvec, n, n)).cuda().contiguous()
+    pt = torch.from_numpy(small_net(8, 0.1)).cuda()
+    one = T.TwoGridBatch(probs, nvec, 2.0 / 3.0, False)
+    three = T.TwoGridBatch(probs, nvec, 2.0 / 3.0, False, cycles=3)
+    three.set_cycles(1)
+    l1, g1 = one.loss_and_grad(pt, zt)
+    l3, g3 = three.loss_and_grad(pt, zt)
+    assert l1.item() == l3.item()
+    assert torch.equal(g1, g3)
+    with pytest.raises(B.MGError):
+        three.set_cycles(4)
+
+
 def test_train_step_gradient_matches_finite_differences_on_gpu_loss():
     """The library's adjoint against central differences of the library's own loss (FP32
     loss, so the step is large and the check loose); the FP64 FD check is the oracle's."""
