@@ -308,3 +308,86 @@ def cnn_loss_and_grad(st, params, z, omega: float = 2.0 / 3.0, bf16: bool = Fals
     W = hypernet_forward(st, params, omega, bf16)
     loss, dW = twogrid_loss(st, W, z, want_grad=True, cycles=cycles)
     return loss, hypernet_backward(st, params, dW, omega, bf16)
+
+
+# ------------------------------------------------ adaptive (level-by-level) training
+def transpose_kernels(W) -> np.ndarray:
+    """Per-point kernels of H^T.  (H v)(x) = sum_k W_x[k] v(x + d_k), so
+    (H^T v)(y) = sum_k W_{y - d_k}[k] v(y - d_k); as kernels at y with the offset
+    d_{8-k} = -d_k: WT[k][y] = W[8 - k][y + d_k], zero where y + d_k leaves the grid."""
+    W = _f64(W)
+    n = W.shape[1]
+    WT = np.zeros_like(W)
+    for k in range(9):
+        di, dj = k // 3 - 1, k % 3 - 1
+        i0, i1 = max(0, -di), min(n, n - di)
+        j0, j1 = max(0, -dj), min(n, n - dj)
+        WT[k, i0:i1, j0:j1] = W[8 - k, i0 + di:i1 + di, j0 + dj:j1 + dj]
+    return WT
+
+
+def _shift_outer(g, v, n):
+    """D[k][x] = g(x) v(x + d_k) (zero outside the grid): the weight gradient of H v."""
+    D = np.zeros((9, n, n))
+    for k in range(9):
+        di, dj = k // 3 - 1, k % 3 - 1
+        i0, i1 = max(0, -di), min(n, n - di)
+        j0, j1 = max(0, -dj), min(n, n - dj)
+        D[k, i0:i1, j0:j1] = g[i0:i1, j0:j1] * v[i0 + di:i1 + di, j0 + dj:j1 + dj]
+    return D
+
+
+def vcycle_loss(st, W, coarse, coarse_t, z, cycles: int = 1, want_grad: bool = False):
+    """The objective Algorithm 2 minimises at one level l: the two-grid error propagation
+    E = S (I - P M P^T A) S with S = I - H A, whose coarse solve is replaced by M, one
+    V-cycle of the hierarchy below (already trained); loss = (1/Z) sum_j ||E^k z_j||^2 / n^2.
+    coarse(r) applies M to a coarse vector, coarse_t(r) its transpose (the same V-cycle
+    with transposed smoothing kernels on every level).  Optionally dLoss/dW: the adjoint
+    runs the k cycles in reverse, C^T = I - A P M^T P^T."""
+    st, W, z = _f64(st), _f64(W), _f64(z)
+    n = st.shape[1]
+    nz = z.shape[0]
+    dW = np.zeros((9, n, n)) if want_grad else None
+    loss = 0.0
+    for zj in z:
+        e = zj.copy()
+        V0, V2 = [], []
+        for _ in range(cycles):
+            v0 = apply(st, e)                               # pre-smoothing e1 = e - H A e
+            e1 = e - apply_H(W, v0)
+            xc = coarse(restrict(apply(st, e1)))            # e2 = e1 - P M P^T A e1
+            e2 = e1 - prolong(xc, n)
+            v2 = apply(st, e2)                              # post-smoothing e = e2 - H A e2
+            e = e2 - apply_H(W, v2)
+            V0.append(v0)
+            V2.append(v2)
+        loss += np.sum(e * e) / (nz * n * n)
+        if not want_grad:
+            continue
+        g = 2.0 * e / (nz * n * n)
+        for c in range(cycles - 1, -1, -1):
+            dW -= _shift_outer(g, V2[c], n)
+            g = g - apply(st, apply_HT(W, g))
+            g = g - apply(st, prolong(coarse_t(restrict(g)), n))
+            dW -= _shift_outer(g, V0[c], n)
+            if c > 0:
+                g = g - apply(st, apply_HT(W, g))
+    return (loss, dW) if want_grad else loss
+
+
+def coarse_vcycle(st_c, kernels, transpose: bool = False):
+    """r -> one V(1,1) cycle from zero on the Galerkin hierarchy of st_c, with the given
+    per-level smoothing kernels (kernels[j] on level j of that hierarchy; transposed when
+    transpose is set), coarsest level solved exactly."""
+    mg = Multigrid(st_c)
+    for j, W in enumerate(kernels):
+        mg.set_kernels(j, transpose_kernels(W) if transpose else W)
+    return lambda r: mg.vcycle(r, np.zeros_like(_f64(r)))
+
+
+def vcycle_cnn_loss_and_grad(st, params, coarse, coarse_t, z, cycles: int = 1, omega: float = 2.0 / 3.0,
+                             bf16: bool = False):
+    """vcycle_loss as a function of the network parameters of this level, with its gradient."""
+    W = hypernet_forward(st, params, omega, bf16)
+    loss, dW = vcycle_loss(st, W, coarse, coarse_t, z, cycles, want_grad=True)
+    return loss, hypernet_backward(st, params, dW, omega, bf16)

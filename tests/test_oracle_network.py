@@ -212,3 +212,74 @@ def test_k_cycle_gradient_matches_finite_differences():
     lp = O.twogrid_loss(st, O.hypernet_forward(st, p + h * d), z, cycles=3)
     lm = O.twogrid_loss(st, O.hypernet_forward(st, p - h * d), z, cycles=3)
     assert abs((lp - lm) / (2 * h) - g @ d) <= 1e-6 * abs(g @ d)
+
+
+# ------------------------------------------------------------ adaptive training (Algorithm 2)
+def test_transposed_kernels_are_the_matrix_transpose():
+    n = 7
+    W = np.random.default_rng(20).standard_normal((9, n, n))
+    np.testing.assert_allclose(D.kernels_matrix(O.transpose_kernels(W)), D.kernels_matrix(W).T, rtol=0, atol=0)
+
+
+def _level_kernels(st_c, seed):
+    """Random smoothing kernels for every smoothed level of st_c's Galerkin hierarchy."""
+    mg = O.Multigrid(st_c)
+    rng = np.random.default_rng(seed)
+    return [O.jacobi_kernels(mg.field(j)) * (1 + 0.2 * rng.standard_normal((9, mg.n(j), mg.n(j))))
+            for j in range(mg.levels - 1)]
+
+
+def test_vcycle_loss_with_an_exact_coarse_solve_is_the_two_grid_loss():
+    n = 15
+    st = O.const_field(n, O.q1_rotated_stencil(0.1, 0.7))
+    W = O.jacobi_kernels(st) * (1 + 0.1 * np.random.default_rng(21).standard_normal((9, n, n)))
+    z = np.random.default_rng(22).standard_normal((3, n, n))
+    Ac = D.field_matrix(O.rap(st))
+    exact = lambda r: np.linalg.solve(Ac, r.ravel()).reshape(r.shape)
+    for k in (1, 2):
+        l0, g0 = O.twogrid_loss(st, W, z, want_grad=True, cycles=k)
+        l1, g1 = O.vcycle_loss(st, W, exact, exact, z, cycles=k, want_grad=True)
+        assert abs(l1 - l0) <= 1e-12 * l0
+        np.testing.assert_allclose(g1, g0, rtol=0, atol=1e-12 * np.abs(g0).max())
+
+
+@pytest.mark.parametrize("cycles", [1, 2])
+def test_vcycle_loss_matches_dense_operators(cycles):
+    """E = S (I - P M P^T A) S with M the dense matrix of the coarse V-cycle (applied to unit
+    vectors); the transposed-kernel cycle is M^T."""
+    n = 15
+    st = O.const_field(n, O.q1_rotated_stencil(0.03, 2.2))
+    W = O.jacobi_kernels(st) * (1 + 0.1 * np.random.default_rng(23).standard_normal((9, n, n)))
+    z = np.random.default_rng(24).standard_normal((3, n, n))
+    st_c = O.rap(st)
+    ker = _level_kernels(st_c, 25)
+    fwd, adj = O.coarse_vcycle(st_c, ker), O.coarse_vcycle(st_c, ker, transpose=True)
+    nc = st_c.shape[1]
+    M = np.stack([fwd(np.eye(nc * nc)[i].reshape(nc, nc)).ravel() for i in range(nc * nc)], axis=1)
+    MT = np.stack([adj(np.eye(nc * nc)[i].reshape(nc, nc)).ravel() for i in range(nc * nc)], axis=1)
+    np.testing.assert_allclose(MT, M.T, rtol=0, atol=1e-12 * np.abs(M).max())
+    A, H, P = D.field_matrix(st), D.kernels_matrix(W), D.prolongation(n)
+    S = np.eye(n * n) - H @ A
+    E = np.linalg.matrix_power(S @ (np.eye(n * n) - P @ M @ P.T @ A) @ S, cycles)
+    want = np.mean([np.sum((E @ zi.ravel()) ** 2) / (n * n) for zi in z])
+    assert abs(O.vcycle_loss(st, W, fwd, adj, z, cycles=cycles) - want) <= 1e-12 * want
+
+
+def test_vcycle_loss_gradient_matches_finite_differences():
+    n = 15
+    rng = np.random.default_rng(26)
+    st = O.const_field(n, O.q1_rotated_stencil(10 ** rng.uniform(-3, 0), rng.uniform(0, math.pi)))
+    st_c = O.rap(st)
+    ker = _level_kernels(st_c, 27)
+    fwd, adj = O.coarse_vcycle(st_c, ker), O.coarse_vcycle(st_c, ker, transpose=True)
+    p = rng.standard_normal(NP) * 0.2
+    z = rng.standard_normal((2, n, n))
+    loss, g = O.vcycle_cnn_loss_and_grad(st, p, fwd, adj, z, cycles=2)
+    h = 1e-6
+    for i in list(rng.choice(NP, 8, replace=False)) + [NP - 1]:
+        pp, pm = p.copy(), p.copy()
+        pp[i] += h
+        pm[i] -= h
+        fd = (O.vcycle_loss(st, O.hypernet_forward(st, pp), fwd, adj, z, cycles=2)
+              - O.vcycle_loss(st, O.hypernet_forward(st, pm), fwd, adj, z, cycles=2)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(abs(g).max(), 1e-12), (i, fd, g[i])
