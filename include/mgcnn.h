@@ -101,6 +101,13 @@ typedef struct {
   int train_checkpoint; /* training only: 1 keeps just each cycle's input vectors and
                            recomputes the cycle's operator products in the backward pass
                            (one vector set per cycle instead of three)                   */
+  int net_levels;       /* MG_SMOOTH_CNN: 0 or 1 -- one network for every level; k > 1 --
+                           net_params holds k parameter sets and level l uses set
+                           min(l, k - 1) (per-level smoothers H^(l), Algorithm 2)        */
+  int smoother_transpose; /* 1: every level smooths with H^T instead of H (per-point
+                           problems only), so a V-cycle of this context applies M^T when
+                           the context without it applies M: the adjoint coarse solve of
+                           mg_train_step_coarse                                          */
 } mg_options;
 
 typedef struct mg_ctx mg_ctx;
@@ -225,7 +232,22 @@ void mg_train_destroy(mg_train_ctx* ctx);
 mg_status mg_train_step(mg_train_ctx* ctx, const float* params, const float* z,
                         float* grad_out, float* loss_out, void* stream);
 
-/* Number of two-grid cycles k of the following mg_train_step calls, 1 <= k <=
+/* mg_train_step with the coarse solve of every cycle replaced by one V(1,1) cycle from
+   zero of an already-trained hierarchy below: the objective of Algorithm 2 at one level,
+     E = S (I - P M P^T A) S,  M = one V-cycle of `coarse` (its smoothers H^(l+1..)),
+   and the adjoint through M^T, one V-cycle of `coarse_t`.  coarse and coarse_t are
+   contexts of the nprob coarse operators P^T A P of this batch (mg_train_get_coarse_field),
+   in batch order, with (n - 1) / 2 <= 63 points per side, built with the same smoother
+   parameters; coarse_t with smoother_transpose = 1.  Other arguments as mg_train_step. */
+mg_status mg_train_step_coarse(mg_train_ctx* ctx, const float* params, const float* z,
+                               mg_ctx* coarse, mg_ctx* coarse_t, float* grad_out,
+                               float* loss_out, void* stream);
+
+/* The Galerkin coarse operator P^T A P of problem `prob` of the batch as a per-point
+   stencil field: out DEVICE float[9][nc][nc], nc = (n - 1) / 2. */
+mg_status mg_train_get_coarse_field(const mg_train_ctx* ctx, int prob, float* out, void* stream);
+
+/* Number of two-grid cycles k of the following mg_train_step calls, 1 <=
    max(1, train_cycles of the setup); Algorithm 2 draws k uniformly per step.  Host-only. */
 mg_status mg_train_set_cycles(mg_train_ctx* ctx, int cycles);
 

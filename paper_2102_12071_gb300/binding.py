@@ -26,7 +26,8 @@ class mg_problem(ctypes.Structure):
 class mg_options(ctypes.Structure):
     _fields_ = [("smoother", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("omega", ctypes.c_float), ("coarsest_n", ctypes.c_int), ("conv_bf16", ctypes.c_int),
-                ("cluster_tail", ctypes.c_int), ("train_cycles", ctypes.c_int), ("train_checkpoint", ctypes.c_int)]
+                ("cluster_tail", ctypes.c_int), ("train_cycles", ctypes.c_int), ("train_checkpoint", ctypes.c_int),
+                ("net_levels", ctypes.c_int), ("smoother_transpose", ctypes.c_int)]
 
 
 class MGError(RuntimeError):
@@ -69,6 +70,8 @@ def lib() -> ctypes.CDLL:
         "mg_train_destroy": (None, [_P]),
         "mg_train_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
         "mg_train_set_cycles": (ctypes.c_int, [_P, ctypes.c_int]),
+        "mg_train_step_coarse": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
+        "mg_train_get_coarse_field": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
         "mg_solve_small_static": (ctypes.c_int, [ctypes.POINTER(mg_problem), ctypes.c_int, ctypes.POINTER(mg_options),
                                                  _P, _P, _P, ctypes.c_double, ctypes.c_int, _P, _P, _P]),
         "mg_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -130,8 +133,10 @@ def problems_array(problems: list[dict]):
 
 
 def options(smoother: int = MG_SMOOTH_JACOBI, omega: float = 2.0 / 3.0, coarsest_n: int = 3,
-            conv_bf16: int = 0, cluster_tail: int = 1, train_cycles: int = 1, train_checkpoint: int = 0) -> mg_options:
-    return mg_options(smoother, 1, 1, omega, coarsest_n, conv_bf16, cluster_tail, train_cycles, train_checkpoint)
+            conv_bf16: int = 0, cluster_tail: int = 1, train_cycles: int = 1, train_checkpoint: int = 0,
+            net_levels: int = 0, smoother_transpose: int = 0) -> mg_options:
+    return mg_options(smoother, 1, 1, omega, coarsest_n, conv_bf16, cluster_tail, train_cycles, train_checkpoint,
+                      net_levels, smoother_transpose)
 
 
 def mg_workspace_size(probs, nprob: int, opts: mg_options) -> int:
@@ -238,6 +243,15 @@ def mg_train_destroy(ctx) -> None:
 def mg_train_step(ctx, params, z, grad_out, loss_out, stream=None):
     check(lib().mg_train_step(ctx, _ptr(params), _ptr(z), _ptr(grad_out), _ptr(loss_out), _stream(stream)),
           "mg_train_step")
+
+
+def mg_train_step_coarse(ctx, params, z, coarse, coarse_t, grad_out, loss_out, stream=None):
+    check(lib().mg_train_step_coarse(ctx, _ptr(params), _ptr(z), coarse, coarse_t, _ptr(grad_out), _ptr(loss_out),
+                                     _stream(stream)), "mg_train_step_coarse")
+
+
+def mg_train_get_coarse_field(ctx, prob: int, out, stream=None) -> None:
+    check(lib().mg_train_get_coarse_field(ctx, int(prob), _ptr(out), _stream(stream)), "mg_train_get_coarse_field")
 
 
 def mg_train_set_cycles(ctx, cycles: int) -> None:

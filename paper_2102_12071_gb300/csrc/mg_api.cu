@@ -64,6 +64,7 @@ mg_status make_plan(const mg_problem* probs, int nprob, const mg_options* o, Pla
   if (o->nu1 != 1 || o->nu2 != 1) return fail(MG_ERR_UNSUPPORTED, "only nu1 = nu2 = 1 is implemented");
   if (o->coarsest_n != 3 && o->coarsest_n != 7) return fail(MG_ERR_UNSUPPORTED, "coarsest_n must be 3 or 7");
   if (!(o->omega > 0.f) || !(o->omega < 2.f)) return fail(MG_ERR_INVALID_ARG, "omega must be in (0, 2)");
+  if (o->net_levels < 0 || o->net_levels > MG_MAXL) return fail(MG_ERR_INVALID_ARG, "net_levels out of range");
   const int n = probs[0].n;
   if (!is_pow2m1(n) || n < o->coarsest_n || n > 8191)
     return fail(MG_ERR_INVALID_ARG, "n = %d must be 2^m - 1 in [coarsest_n, 8191]", n);
@@ -94,6 +95,8 @@ mg_status make_plan(const mg_problem* probs, int nprob, const mg_options* o, Pla
   P.n0 = n;
   P.sk = nconst ? SK_CONST : SK_FIELD;
   P.hk = o->smoother == MG_SMOOTH_JACOBI ? HK_JACOBI : (P.sk == SK_CONST ? HK_TABLE : HK_FIELD);
+  if (o->smoother_transpose && P.hk == HK_TABLE)
+    return fail(MG_ERR_UNSUPPORTED, "smoother_transpose needs per-point problems (kinds VARCOEF5, FIELD)");
   int m = n, L = 0;
   P.nl[L++] = m;
   while (m > o->coarsest_n) {
@@ -146,6 +149,7 @@ struct mg_ctx {
   int* d_fail = nullptr;
   NetJob* d_jobs = nullptr;
   int* d_active = nullptr;      // compacted list of problems still iterating
+  float* tscratch = nullptr;    // kernel transposition scratch (smoother_transpose)
   std::vector<int> h_active;
   LevelArrays arrays;
   TileMaps maps;
@@ -254,6 +258,8 @@ static size_t carve(const Plan& P, const mg_options& o, void* base, mg_ctx* ctx)
   int* fail_flag = c.take<int>(4);
   int* active = c.take<int>(P.nprob);
   NetJob* jobs = c.take<NetJob>((size_t)P.nprob * P.L);
+  // scratch for the transposition of one problem's level-0 kernels (smoother_transpose)
+  float* tscr = (o.smoother_transpose && P.hk == HK_FIELD) ? c.take<float>((size_t)9 * P.n0 * P.n0) : nullptr;
   LevelArrays A;
   memset(&A, 0, sizeof(A));
   for (int l = 0; l < P.L; ++l) {
@@ -315,8 +321,8 @@ static size_t carve(const Plan& P, const mg_options& o, void* base, mg_ctx* ctx)
     ctx->d_fail = fail_flag;
     ctx->d_jobs = jobs;
     ctx->d_active = active;
+    ctx->tscratch = tscr;
   }
-  (void)o;
   return c.off + 256;
 }
 
@@ -428,10 +434,12 @@ mg_status mg_setup(const mg_problem* problems, int nprob, const mg_options* opts
     }
     CK(launch_coarsest_factor(a.probs, P.nprob, P.L, P.sk, ctx->d_fail, s));
     if (P.hk != HK_JACOBI && P.L > 1) {
+      // jobs level-major, so that every level can take its own parameter set
       std::vector<NetJob> jobs;
-      int nmax = 0;
-      for (int p = 0; p < nprob; ++p)
-        for (int l = 0; l + 1 < P.L; ++l) {
+      std::vector<int> first(P.L, 0), nmax(P.L, 0);
+      for (int l = 0; l + 1 < P.L; ++l) {
+        first[l] = (int)jobs.size();
+        for (int p = 0; p < nprob; ++p) {
           const LevelDev& v = ctx->h_probs[p].lv[l];
           NetJob J;
           J.st = P.sk == SK_FIELD ? v.st : nullptr;
@@ -439,11 +447,25 @@ mg_status mg_setup(const mg_problem* problems, int nprob, const mg_options* opts
           J.W = v.W;
           J.n = P.sk == SK_FIELD ? v.n : v.T;
           J.pad_ = 0;
-          nmax = J.n > nmax ? J.n : nmax;
+          nmax[l] = J.n > nmax[l] ? J.n : nmax[l];
           jobs.push_back(J);
         }
+      }
       CK(cudaMemcpyAsync(ctx->d_jobs, jobs.data(), sizeof(NetJob) * jobs.size(), cudaMemcpyHostToDevice, s));
-      CK(launch_net_forward(ctx->d_jobs, (int)jobs.size(), nmax, net_params, opts->omega, opts->conv_bf16, s));
+      if (opts->net_levels <= 1) {
+        int nm = 0;
+        for (int l = 0; l + 1 < P.L; ++l) nm = nmax[l] > nm ? nmax[l] : nm;
+        CK(launch_net_forward(ctx->d_jobs, (int)jobs.size(), nm, net_params, opts->omega, opts->conv_bf16, s));
+      } else {
+        for (int l = 0; l + 1 < P.L; ++l) {
+          const int set = l < opts->net_levels ? l : opts->net_levels - 1;
+          CK(launch_net_forward(ctx->d_jobs + first[l], nprob, nmax[l], net_params + (size_t)set * MG_NPARAMS,
+                                opts->omega, opts->conv_bf16, s));
+        }
+      }
+      if (opts->smoother_transpose)
+        for (int p = 0; p < nprob; ++p)
+          for (int l = 0; l + 1 < P.L; ++l) CK(launch_transpose_kernels(ctx->h_probs[p].lv[l].W, P.nl[l], ctx->tscratch, s));
       // the host vector must outlive the asynchronous copy
       CK(cudaStreamSynchronize(s));
     }
@@ -649,6 +671,14 @@ static mg_status run_end(SolveRun& R) {
   else if (rc == MG_ERR_NUMERIC) fail(rc, "non-finite residual");
   else if (rc == MG_ERR_NOT_CONVERGED) fail(rc, "max_cycles reached before rtol");
   return rc;
+}
+
+// the cycle arguments of a context whose whole hierarchy runs in one CTA per problem
+// (for the training step's coarse V-cycle); false for other contexts
+bool mg::ctx_tail_args(const mg_ctx* ctx, mg::CycleArgs* a) {
+  if (!ctx || !ctx->plan.tail_solve) return false;
+  *a = ctx->args;
+  return true;
 }
 
 extern "C" {

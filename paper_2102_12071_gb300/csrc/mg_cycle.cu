@@ -317,6 +317,66 @@ cudaError_t launch_tail_solve(const CycleArgs& a, const float* b, float* xhi, fl
   return cudaGetLastError();
 }
 
+// One V-cycle from zero of levels 0 .. L-1 on nvec right-hand sides per problem: the
+// coarse solve of Algorithm 2's training objective (one CTA per vector, every level in
+// shared memory).  rin, xout: dense [nprob * nvec][n0][n0].
+template <int SK, int HK>
+__global__ void __launch_bounds__(TAIL_THREADS) k_tail_vec(const ProbDev* __restrict__ probs, int L, float omega,
+                                                           const float* __restrict__ rin, float* __restrict__ xout,
+                                                           int nvec) {
+  extern __shared__ float sm[];
+  __shared__ float sc[MG_MAXL][9];
+  __shared__ float wi[MG_MAXL][9];
+  __shared__ TailLayout lay;
+  const int v = blockIdx.x, p = v / nvec;
+  const ProbDev& P = probs[p];
+  if (threadIdx.x == 0) {
+    int nl[MG_MAXL];
+    for (int l = 0; l < L; ++l) nl[l] = P.lv[l].n;
+    tail_layout(nl, 0, L, HK, lay);
+  }
+  __syncthreads();
+  tail_prologue<SK, HK>(P, sm, lay, sc, wi, 0, L);
+  const int n = P.lv[0].n, m = n + 2;
+  const size_t nn = (size_t)n * n;
+  const float* src = rin + (size_t)v * nn;
+  float* r = sm + lay.off_r[0];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  TAIL_FOR(n) r[(i + 1) * m + j + 1] = src[(size_t)i * n + j];
+  __syncthreads();
+  tail_cycle<SK, HK>(P, sm, lay, sc, wi, 0, L, omega);
+  const float* e = sm + lay.off_e[0];
+  float* dst = xout + (size_t)v * nn;
+  TAIL_FOR(n) dst[(size_t)i * n + j] = e[(i + 1) * m + j + 1];
+}
+
+cudaError_t launch_tail_vec(const CycleArgs& a, const float* rin, float* xout, int nvec) {
+  const size_t smem = tail_smem_bytes(a.nl, 0, a.L, a.hk);
+  cudaError_t e;
+  MG_DISPATCH(a.sk, a.hk, (e = set_tail_attrs<SK_, HK_>(smem)));
+  if (e != cudaSuccess) return e;
+  MG_DISPATCH(a.sk, a.hk, (k_tail_vec<SK_, HK_><<<a.nprob * nvec, TAIL_THREADS, smem, a.stream>>>(
+                              a.probs, a.L, a.omega, rin, xout, nvec)));
+  return cudaGetLastError();
+}
+
+// out[k][y] = W[8 - k][y + d_k] (zero outside): the kernels of H^T
+__global__ void k_transpose_kernels(const float* __restrict__ W, float* __restrict__ out, int n) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= 9 * n * n) return;
+  const int k = q / (n * n), y = q % (n * n), i = y / n, j = y % n;
+  const int ii = i + k / 3 - 1, jj = j + k % 3 - 1;
+  out[q] = in_grid(ii, jj, n) ? W[(size_t)(8 - k) * n * n + ii * n + jj] : 0.f;
+}
+
+cudaError_t launch_transpose_kernels(float* W, int n, float* scratch, cudaStream_t s) {
+  const int cnt = 9 * n * n;
+  k_transpose_kernels<<<(cnt + 255) / 256, 256, 0, s>>>(W, scratch, n);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyAsync(W, scratch, sizeof(float) * cnt, cudaMemcpyDeviceToDevice, s);
+}
+
 cudaError_t launch_smoother(const CycleArgs& a, int p, int l, const float* f, float* u, int nsteps) {
   const int n = a.nl[l];
   const int nb = (n * n + 255) / 256;

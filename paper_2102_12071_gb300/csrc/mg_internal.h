@@ -8,6 +8,8 @@
 
 #include "mg_common.cuh"
 
+struct mg_ctx;  // the library's context (mgcnn.h)
+
 namespace mg {
 
 // Kernel classes timed by the optional event profiler.
@@ -178,6 +180,12 @@ cudaError_t launch_unpack(const float* src_a, const float* src_b, const ProbStat
 // when a.ctail is set; prepare_tail sets launch attributes (call it outside stream capture)
 cudaError_t launch_tail(const CycleArgs& a);
 cudaError_t prepare_tail(const CycleArgs& a);
+// xout[v] = one V-cycle from zero of levels 0 .. L-1 applied to rin[v], v = p * nvec + j
+// (dense [nprob * nvec][n0][n0] arrays; contexts whose whole hierarchy runs in one CTA)
+cudaError_t launch_tail_vec(const CycleArgs& a, const float* rin, float* xout, int nvec);
+// W (9 x n x n per-point kernels) <- its transpose's kernels, through scratch (9 x n x n)
+cudaError_t launch_transpose_kernels(float* W, int n, float* scratch, cudaStream_t s);
+bool ctx_tail_args(const ::mg_ctx* ctx, CycleArgs* a);
 cudaError_t launch_tail_solve(const CycleArgs& a, const float* b, float* xhi, float* xlo, float rtol, int max_cycles,
                               int budget, int final_residual);
 // cluster tail (mg_ctail.cu): levels lstar .. L-1 in one MG_CT_C-CTA cluster per problem

@@ -569,8 +569,8 @@ mg_status mg_train_set_cycles(mg_train_ctx* ctx, int cycles) {
   return MG_OK;
 }
 
-mg_status mg_train_step(mg_train_ctx* c, const float* params, const float* z, float* grad_out, float* loss_out,
-                        void* stream) {
+static mg_status train_step(mg_train_ctx* c, const float* params, const float* z, const CycleArgs* cf,
+                            const CycleArgs* ct, float* grad_out, float* loss_out, void* stream) {
   if (!c || !params || !z || !loss_out) return (mg_status)api_fail(MG_ERR_INVALID_ARG, "mg_train_step: bad arguments");
   const TrainDims& D = c->D;
   cudaStream_t s = (cudaStream_t)stream;
@@ -586,13 +586,25 @@ mg_status mg_train_step(mg_train_ctx* c, const float* params, const float* z, fl
   nb.pad_ = 0;
   TCK(launch_net_forward_batch(nb, D.B, params, c->omega, c->bf16, s));
   const int K = c->k;
+  // xc = M rc: the exact coarse solve (banded Cholesky), or one V-cycle of the coarse
+  // context (cf), whose transpose ct serves the adjoint
+  auto coarse_solve = [&](const CycleArgs* ca) -> cudaError_t {
+    if (!ca) {
+      k_t_band_solve<<<solve_blocks, 128, 0, s>>>(D, c->band, c->ut, c->rc, c->ybuf, c->xc, BZ);
+      return cudaGetLastError();
+    }
+    CycleArgs a = *ca;
+    a.stream = s;
+    return launch_tail_vec(a, c->rc, c->xc, D.Z);
+  };
+  cudaError_t ce = cudaSuccess;
   // one cycle e_out = S C S e_in, keeping v0 = A e_in and v2 = A (C S e_in); e_out may be
   // NULL (recomputation of the products only)
   auto cycle = [&](const float* ein, float* v0, float* v2, float* eout) {
     k_t_applyA<<<gv, TT, 0, s>>>(D, c->fields, ein, v0);
     k_t_xmHv<<<gv, TT, 0, s>>>(D, c->fields, c->W, ein, v0, c->e1);
     k_t_restrict<<<gc, TT, 0, s>>>(D, c->fields, c->e1, 1, c->rc);
-    k_t_band_solve<<<solve_blocks, 128, 0, s>>>(D, c->band, c->ut, c->rc, c->ybuf, c->xc, BZ);
+    if (ce == cudaSuccess) ce = coarse_solve(cf);
     k_t_xmP<<<gv, TT, 0, s>>>(D, c->e1, c->xc, c->e2);
     k_t_applyA<<<gv, TT, 0, s>>>(D, c->fields, c->e2, v2);
     if (eout) k_t_xmHv<<<gv, TT, 0, s>>>(D, c->fields, c->W, c->e2, v2, eout);
@@ -602,6 +614,7 @@ mg_status mg_train_step(mg_train_ctx* c, const float* params, const float* z, fl
     cycle(cc == 0 ? z : c->X[cc], c->V0[cc], c->V2[cc], cc + 1 < K ? c->X[cc + 1] : c->g3);
   k_t_loss<<<BZ, TT, 0, s>>>(D, c->g3, 2.f * inv, c->g3, c->loss_partial);
   k_t_loss_total<<<1, 32, 0, s>>>(c->loss_partial, BZ, inv, loss_out);
+  TCK(ce);
   TCK(cudaGetLastError());
   if (!grad_out) return MG_OK;
   // adjoint, cycles in reverse; g3 = dloss/d(output of cycle cc)
@@ -610,7 +623,7 @@ mg_status mg_train_step(mg_train_ctx* c, const float* params, const float* z, fl
     k_t_HT<<<gv, TT, 0, s>>>(D, c->fields, c->W, c->g3, c->t);
     k_t_xmAv<<<gv, TT, 0, s>>>(D, c->fields, c->g3, c->t, c->g2);
     k_t_restrict<<<gc, TT, 0, s>>>(D, c->fields, c->g2, 0, c->rc);
-    k_t_band_solve<<<solve_blocks, 128, 0, s>>>(D, c->band, c->ut, c->rc, c->ybuf, c->xc, BZ);
+    TCK(coarse_solve(ct));
     k_t_P<<<gv, TT, 0, s>>>(D, c->xc, c->t);
     k_t_xmAv<<<gv, TT, 0, s>>>(D, c->fields, c->g2, c->t, c->g1);
     k_t_dW<<<dim3((unsigned)((D.nn + TT - 1) / TT), D.B), TT, 0, s>>>(D, c->g3, c->V2[cc], c->g1, c->V0[cc], c->dW,
@@ -620,8 +633,35 @@ mg_status mg_train_step(mg_train_ctx* c, const float* params, const float* z, fl
       k_t_xmAv<<<gv, TT, 0, s>>>(D, c->fields, c->g1, c->t, c->g3);
     }
   }
+  TCK(ce);
   TCK(cudaGetLastError());
   TCK(launch_net_backward(nb, D.B, c->dW, params, c->bf16, c->param_partial, 1.f, grad_out, s));
+  return MG_OK;
+}
+
+mg_status mg_train_step(mg_train_ctx* c, const float* params, const float* z, float* grad_out, float* loss_out,
+                        void* stream) {
+  return train_step(c, params, z, nullptr, nullptr, grad_out, loss_out, stream);
+}
+
+mg_status mg_train_step_coarse(mg_train_ctx* c, const float* params, const float* z, mg_ctx* coarse, mg_ctx* coarse_t,
+                               float* grad_out, float* loss_out, void* stream) {
+  if (!c) return (mg_status)api_fail(MG_ERR_INVALID_ARG, "mg_train_step_coarse: ctx is NULL");
+  CycleArgs af, at;
+  if (!ctx_tail_args(coarse, &af) || !ctx_tail_args(coarse_t, &at))
+    return (mg_status)api_fail(MG_ERR_INVALID_ARG, "coarse contexts must hold whole hierarchies of side <= 63");
+  const TrainDims& D = c->D;
+  if (af.n0 != D.nc || at.n0 != D.nc || af.nprob != D.B || at.nprob != D.B || af.L != at.L)
+    return (mg_status)api_fail(MG_ERR_INVALID_ARG, "coarse contexts must hold the %d coarse operators of side %d", D.B,
+                               D.nc);
+  return train_step(c, params, z, &af, &at, grad_out, loss_out, stream);
+}
+
+mg_status mg_train_get_coarse_field(const mg_train_ctx* c, int prob, float* out, void* stream) {
+  if (!c || !out || prob < 0 || prob >= c->D.B)
+    return (mg_status)api_fail(MG_ERR_INVALID_ARG, "mg_train_get_coarse_field: bad arguments");
+  TCK(cudaMemcpyAsync(out, c->cfields + (size_t)prob * 9 * c->D.nnc, sizeof(float) * 9 * c->D.nnc,
+                      cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
   return MG_OK;
 }
 

@@ -58,9 +58,42 @@ class TwoGridBatch:
         self.ctx = B.mg_train_setup(self._probs, self.nprob, nvec, self.opts, workspace, size)
 
     def close(self):
+        self.detach_coarse()
         if getattr(self, "ctx", None):
             B.mg_train_destroy(self.ctx)
             self.ctx = None
+
+    # ------------------------------------------------ Algorithm 2: V-cycle coarse solve
+    def coarse_fields(self) -> list[torch.Tensor]:
+        """The batch's Galerkin coarse operators P^T A P as per-point fields [9, nc, nc]."""
+        nc = (self.n - 1) // 2
+        out = []
+        for p in range(self.nprob):
+            f = torch.empty((9, nc, nc), dtype=torch.float32, device="cuda")
+            B.mg_train_get_coarse_field(self.ctx, p, f)
+            out.append(f)
+        return out
+
+    def attach_coarse(self, level_params: torch.Tensor | None, omega: float | None = None) -> None:
+        """Replace the exact coarse solve by one V-cycle of the hierarchy below, smoothed by
+        level_params ([k, nparams]: set j on level j of the coarse hierarchy, the last set
+        below that; None: weighted Jacobi), as Algorithm 2 does once those levels are trained."""
+        from . import solver as S
+
+        self.detach_coarse()
+        fields = self.coarse_fields()
+        nc = fields[0].shape[-1]
+        probs = [S.field(nc, f) for f in fields]
+        kind = "cnn" if level_params is not None else "jacobi"
+        om = self.opts.omega if omega is None else omega
+        self._coarse = [S.MultigridSolver(probs, kind, net_params=level_params, omega=om, conv_bf16=bool(self.opts.conv_bf16),
+                                          transpose=t) for t in (False, True)]
+        self._coarse_fields = fields
+
+    def detach_coarse(self) -> None:
+        for mg in getattr(self, "_coarse", []) or []:
+            mg.close()
+        self._coarse = None
 
     def __del__(self):
         self.close()
@@ -73,7 +106,10 @@ class TwoGridBatch:
         assert z.shape == (self.nprob, self.nvec, self.n, self.n) and z.is_contiguous()
         loss = torch.empty(1, device="cuda")
         grad = torch.empty(NPARAMS, device="cuda") if want_grad else None
-        B.mg_train_step(self.ctx, params.contiguous(), z, grad, loss)
+        if getattr(self, "_coarse", None):
+            B.mg_train_step_coarse(self.ctx, params.contiguous(), z, self._coarse[0].ctx, self._coarse[1].ctx, grad, loss)
+        else:
+            B.mg_train_step(self.ctx, params.contiguous(), z, grad, loss)
         return loss, grad
 
 
@@ -161,6 +197,80 @@ class Trainer:
         np.save(path, self.params.detach().cpu().numpy().astype(np.float32))
 
 
+class AdaptiveTrainer:
+    """Algorithm 2: one network per level of a hierarchy of side n_fine, trained from the
+    second-coarsest level up.  Level l's network minimises the two-grid objective of its own
+    operators with the coarse solve replaced by one V-cycle of the levels below, smoothed by
+    the networks already trained (the exact solve on the level above the coarsest).  The
+    operators of level l are rotated anisotropic problems of that level's size (constant
+    stencils are invariant under the Galerkin product, Sec. 6.1)."""
+
+    def __init__(self, n_fine: int = 63, per_size: int = 32, nvec: int = 32, steps_per_level: int = 300,
+                 lr: float = 1e-3, omega: float = 2.0 / 3.0, conv_bf16: bool = True, seed: int = 0,
+                 eps_range=(1e-3, 1.0), max_cycles: int = 1, init=None):
+        self.sizes = []
+        n = n_fine
+        while n > 3:
+            self.sizes.append(n)
+            n = (n - 1) // 2
+        self.per_size, self.nvec, self.steps = per_size, nvec, steps_per_level
+        self.lr, self.omega, self.conv_bf16, self.seed = lr, omega, conv_bf16, seed
+        self.eps_range, self.max_cycles = eps_range, max_cycles
+        self.init = init  # starting parameters of every level (None: the Jacobi-equivalent net)
+        self.params: dict[int, torch.Tensor] = {}
+        self.losses: dict[int, list[float]] = {}
+        self.gen = torch.Generator(device="cuda").manual_seed(inputs.SEED_TRAIN + 17 + seed)
+
+    def level_params(self, n: int) -> torch.Tensor | None:
+        """Stacked trained parameters of the levels below side n (finest first), or None."""
+        below = [m for m in self.sizes if m < n and m in self.params]
+        return torch.stack([self.params[m] for m in below]) if below else None
+
+    def problems(self, step: int, n: int) -> list[dict]:
+        params = inputs.rotated_params(inputs.SEED_TRAIN + 104729 * step + 7 * n + 1, self.per_size, *self.eps_range)
+        return [{"n": n, "kind": B.MG_PROBLEM_ROTATED, "eps": e, "theta": t} for e, t in params]
+
+    def train_level(self, n: int) -> torch.Tensor:
+        p = (init_params(self.seed) if self.init is None else self.init.detach().clone()).cuda().requires_grad_(True)
+        opt = torch.optim.Adam([p], lr=self.lr)
+        below = self.level_params(n)
+        ws = None
+        hist = []
+        for step in range(self.steps):
+            batch = TwoGridBatch(self.problems(step, n), self.nvec, self.omega, self.conv_bf16, ws,
+                                 cycles=self.max_cycles)
+            ws = batch.workspace
+            if (n - 1) // 2 > 3:  # the level above the coarsest keeps the exact coarse solve
+                batch.attach_coarse(below)
+            if self.max_cycles > 1:
+                batch.set_cycles(int(np.random.default_rng(inputs.SEED_TRAIN + 31 * step + n).integers(1, self.max_cycles + 1)))
+            z = torch.randn((self.per_size, self.nvec, n, n), generator=self.gen, device="cuda")
+            opt.zero_grad(set_to_none=True)
+            loss = TwoGridLoss.apply(p, z, batch)
+            loss.backward()
+            opt.step()
+            hist.append(float(loss.detach()))
+            batch.close()
+        self.losses[n] = hist
+        self.params[n] = p.detach().clone()
+        return self.params[n]
+
+    def train(self) -> None:
+        for n in reversed(self.sizes):
+            self.train_level(n)
+
+    def hierarchy_params(self, n_solve: int) -> torch.Tensor:
+        """Per-level parameter sets for a solver of side n_solve: each level takes the network
+        trained at its own side, levels finer than the finest trained side take that one."""
+        sets = []
+        n = n_solve
+        while n > 3:
+            m = n if n in self.params else max(self.params)
+            sets.append(self.params[m])
+            n = (n - 1) // 2
+        return torch.stack(sets)
+
+
 def main():
     import argparse
     import time
@@ -175,10 +285,27 @@ def main():
     ap.add_argument("--families", default="rotated", help="comma list of rotated,varcoef")
     ap.add_argument("--max-cycles", type=int, default=1, help="b: each step's loss spans k ~ U{1..b} cycles")
     ap.add_argument("--checkpoint", action="store_true", help="recompute cycle products in the backward pass")
+    ap.add_argument("--adaptive", type=int, default=0, metavar="N_FINE",
+                    help="Algorithm 2: one network per level of a hierarchy of this side, trained coarse to fine "
+                         "(--steps per level); saves [levels, nparams], finest first")
     args = ap.parse_args()
     from . import build
 
     build.build()
+    if args.adaptive:
+        t0 = time.time()
+        at = AdaptiveTrainer(n_fine=args.adaptive, steps_per_level=args.steps, lr=args.lr, seed=args.seed,
+                             conv_bf16=not args.fp32_conv, max_cycles=args.max_cycles)
+        for n in reversed(at.sizes):
+            at.train_level(n)
+            h = at.losses[n]
+            print(f"level n={n}: loss {np.mean(h[:10]):.5f} -> {np.mean(h[-10:]):.5f} ({time.time() - t0:.1f} s)",
+                  flush=True)
+        out = args.out if args.out.endswith("adaptive.npy") else args.out.replace(".npy", "_adaptive.npy")
+        os.makedirs(os.path.dirname(out), exist_ok=True)
+        np.save(out, torch.stack([at.params[n] for n in at.sizes]).cpu().numpy().astype(np.float32))
+        print("saved", out, "levels", at.sizes)
+        return
     tr = Trainer(lr=args.lr, seed=args.seed, conv_bf16=not args.fp32_conv,
                  families=tuple(f.strip() for f in args.families.split(",")), max_cycles=args.max_cycles,
                  checkpoint=args.checkpoint)

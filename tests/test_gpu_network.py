@@ -275,3 +275,67 @@ def test_trained_network_gains_over_jacobi():
     _, oh = om.solve(f32(b[p].cpu().numpy()), rtol=0.0, max_cycles=k)
     rel = np.abs(res["cnn"][0][p][: k + 1] - oh) / oh
     assert rel.max() <= 1e-5, rel.max()
+
+
+@pytest.mark.parametrize("n,smoother,cycles", [(15, "cnn", 1), (31, "cnn", 2), (31, "jacobi", 1)])
+def test_vcycle_coarse_train_step_matches_oracle(n, smoother, cycles):
+    """Algorithm 2's objective at one level: the two-grid error propagation whose coarse
+    solve is one V-cycle of the (already trained) hierarchy below, loss and gradient vs the
+    FP64 oracle (vcycle_cnn_loss_and_grad with coarse_vcycle and its transpose)."""
+    nprob, nvec = 3, 4
+    params = inputs.rotated_params(80 + n, nprob)
+    probs = [{"n": n, "kind": B.MG_PROBLEM_ROTATED, "eps": e, "theta": t} for e, t in params]
+    z = inputs.gaussian_vectors(81 + n, nprob * nvec, n).reshape(nprob, nvec, n, n)
+    p = small_net(9, 0.1)
+    nc = (n - 1) // 2
+    nsets = 0
+    m = nc
+    while m > 3:
+        nsets += 1
+        m = (m - 1) // 2
+    sets = [small_net(10 + j, 0.1) for j in range(nsets)]
+    batch = T.TwoGridBatch(probs, nvec, 2.0 / 3.0, False, cycles=cycles)
+    batch.attach_coarse(torch.from_numpy(np.stack(sets)).cuda() if smoother == "cnn" else None)
+    loss, grad = batch.loss_and_grad(torch.from_numpy(p).cuda(), torch.from_numpy(z).cuda().contiguous())
+    batch.close()
+    lo, go = 0.0, np.zeros(p.size)
+    for k, (e, t) in enumerate(params):
+        st = O.const_field(n, f32(O.q1_rotated_stencil(e, t)))
+        st_c = O.rap(st)
+        mgc = O.Multigrid(st_c)
+        ker = [O.hypernet_forward(mgc.field(j), f32(sets[j])) if smoother == "cnn" else O.jacobi_kernels(mgc.field(j))
+               for j in range(mgc.levels - 1)]
+        fwd, adj = O.coarse_vcycle(st_c, ker), O.coarse_vcycle(st_c, ker, transpose=True)
+        l1, g1 = O.vcycle_cnn_loss_and_grad(st, f32(p), fwd, adj, f32(z[k]), cycles=cycles)
+        lo += l1 / nprob
+        go += g1 / nprob
+    assert abs(loss.item() - lo) <= 1e-5 * lo, (loss.item(), lo)
+    g = grad.double().cpu().numpy()
+    assert np.linalg.norm(g - go) <= 1e-4 * np.linalg.norm(go), np.linalg.norm(g - go) / np.linalg.norm(go)
+
+
+def test_per_level_networks_and_transposed_smoothers_in_the_solver():
+    """net_params [k, nparams] gives level l the kernels of set min(l, k-1); transpose = 1
+    stores the kernels of H^T (per-point problems)."""
+    n = 31
+    cells = torch.from_numpy(inputs.grf_cells(inputs.SEED_GRF + 60, n)).cuda()
+    sets = np.stack([small_net(20 + j, 0.1) for j in range(2)])
+    mg = S.MultigridSolver([S.varcoef5(n, cells)], "cnn", torch.from_numpy(sets).cuda())
+    mgt = S.MultigridSolver([S.varcoef5(n, cells)], "cnn", torch.from_numpy(sets).cuda(), transpose=True)
+    om = O.Multigrid(f32(O.varcoef5_field(n, f32(cells.cpu().numpy()))))
+    for l in range(mg.levels - 1):
+        Wo = O.hypernet_forward(om.field(l), f32(sets[min(l, 1)]))
+        Wg = mg.kernels(0, l).double().cpu().numpy()
+        np.testing.assert_allclose(Wg, Wo, rtol=2e-5, atol=2e-6 * np.abs(Wo).max())
+        np.testing.assert_array_equal(mgt.kernels(0, l).cpu().numpy(), O.transpose_kernels(Wg).astype(np.float32))
+
+
+@pytest.mark.parametrize("n", [15])
+def test_adaptive_trainer_levels_train(n):
+    """Algorithm 2 end to end on a small hierarchy: every level's objective falls."""
+    tr = T.AdaptiveTrainer(n_fine=n, per_size=4, nvec=4, steps_per_level=40, lr=3e-3)
+    tr.train()
+    assert sorted(tr.params) == [7, 15]
+    for m, h in tr.losses.items():
+        assert np.mean(h[-5:]) < np.mean(h[:5]), (m, h[:5], h[-5:])
+    assert tr.hierarchy_params(63).shape == (4, T.NPARAMS)
