@@ -117,7 +117,8 @@ class MixedBatchSolver:
     A context holds problems of one size and one storage kind (constant stencils or per-point
     fields), so the batch is split into such groups; every group gets its own context and
     CUDA stream, and mg_solve_multi runs all groups' cycles at once.  net_params maps "const"
-    and "field" to the network parameters of each kind (CNN smoother).  With `autotune`, the
+    and "field" to the network parameters of each kind (CNN smoother): one set, per-level
+    sets, or a function of the group's side returning either.  With `autotune`, the
     first solve times a few cycles of each coarse-level layout (one CTA cluster per problem
     below 127, or one CTA below 63 with tiled kernels above) per group and keeps the faster.
     """
@@ -139,6 +140,8 @@ class MixedBatchSolver:
 
     def _make(self, key, cluster_tail: bool) -> MultigridSolver:
         params = self.net_params.get(key[1]) if self.smoother == "cnn" else None
+        if callable(params):  # per-level sets that depend on the hierarchy's size
+            params = params(key[0])
         return MultigridSolver([self.problems[i] for i in self.groups[key]], self.smoother, net_params=params,
                                stream=self.streams[key].cuda_stream, cluster_tail=cluster_tail)
 

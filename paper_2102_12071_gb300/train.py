@@ -271,6 +271,25 @@ class AdaptiveTrainer:
         return torch.stack(sets)
 
 
+def adaptive_params(W: np.ndarray | torch.Tensor, n_solve: int, n_fine: int = 63) -> torch.Tensor:
+    """Per-level parameter sets for a solver of side n_solve from networks trained by
+    AdaptiveTrainer for a hierarchy of side n_fine (W: [levels, nparams], finest first):
+    each level takes the network of its own side, finer levels the finest one."""
+    W = torch.as_tensor(np.asarray(W, dtype=np.float32))
+    sizes = []
+    n = n_fine
+    while n > 3:
+        sizes.append(n)
+        n = (n - 1) // 2
+    assert W.shape[0] == len(sizes)
+    sets = []
+    n = n_solve
+    while n > 3:
+        sets.append(W[sizes.index(n)] if n in sizes else W[0])
+        n = (n - 1) // 2
+    return torch.stack(sets)
+
+
 def main():
     import argparse
     import time
