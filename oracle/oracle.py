@@ -7,6 +7,7 @@ and stencil fields / per-point kernels are ``[9, n, n]`` with tap k = 3*(di+1)+(
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 
@@ -391,3 +392,62 @@ def vcycle_cnn_loss_and_grad(st, params, coarse, coarse_t, z, cycles: int = 1, o
     W = hypernet_forward(st, params, omega, bf16)
     loss, dW = vcycle_loss(st, W, coarse, coarse_t, z, cycles, want_grad=True)
     return loss, hypernet_backward(st, params, dW, omega, bf16)
+
+
+# ------------------------------------------------------------------- FGMRES (Sec. 6.4)
+def fgmres(apply_A, precond, b, x0=None, restart: int = 30, rtol: float = 1e-6, max_iters: int = 500):
+    """Right-preconditioned flexible GMRES(restart) (Sec. 6.4: multigrid as the
+    preconditioner; flexible because a network smoother need not be a fixed linear map).
+    Arnoldi on A M with the preconditioned directions z_j = M(v_j) kept, classical
+    Gram-Schmidt with one re-orthogonalisation, Givens rotations on the Hessenberg
+    matrix, x = x0 + Z y.  Stops when ||b - A x|| / ||b|| < rtol (the rotated least-squares
+    residual, which equals the true one in exact arithmetic).
+    Returns (x, history of relative residuals, iterations)."""
+    b = _f64(b)
+    shape = b.shape
+    bv = b.ravel()
+    x = np.zeros_like(bv) if x0 is None else _f64(x0).ravel().copy()
+    A = lambda v: _f64(apply_A(v.reshape(shape))).ravel()
+    M = lambda v: _f64(precond(v.reshape(shape))).ravel()
+    bnorm = np.linalg.norm(bv)
+    r = bv - A(x)
+    hist = [np.linalg.norm(r) / bnorm]
+    its = 0
+    while hist[-1] >= rtol and its < max_iters:
+        beta = np.linalg.norm(r)
+        V = [r / beta]
+        Z = []
+        H = np.zeros((restart + 1, restart))
+        cs, sn = np.zeros(restart), np.zeros(restart)
+        g = np.zeros(restart + 1)
+        g[0] = beta
+        j = 0
+        while j < restart and its < max_iters:
+            z = M(V[j])
+            Z.append(z)
+            w = A(z)
+            h = np.array([vi @ w for vi in V])
+            w = w - sum(hi * vi for hi, vi in zip(h, V))
+            h2 = np.array([vi @ w for vi in V])           # second Gram-Schmidt pass
+            w = w - sum(hi * vi for hi, vi in zip(h2, V))
+            H[: j + 1, j] = h + h2
+            H[j + 1, j] = np.linalg.norm(w)
+            V.append(w / H[j + 1, j])
+            for i in range(j):                             # earlier rotations
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            rho = math.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = H[j, j] / rho, H[j + 1, j] / rho
+            H[j, j], H[j + 1, j] = rho, 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            j += 1
+            its += 1
+            hist.append(abs(g[j]) / bnorm)
+            if hist[-1] < rtol:
+                break
+        y = np.linalg.solve(np.triu(H[:j, :j]), g[:j])
+        x = x + sum(yi * zi for yi, zi in zip(y, Z))
+        r = bv - A(x)
+    return x.reshape(shape), np.array(hist), its
