@@ -306,6 +306,42 @@ def run_rotated_batch(n: int, nprob: int, weights, rank: int):
     return out
 
 
+def run_fgmres(weights):
+    """Sec. 6.4: multigrid-preconditioned FGMRES(30) to 1e-6 on 511^2 rotated problems with
+    eps = 0.01 (the paper's xi = 100) and theta = pi/12 .. 5pi/12, one batch of five; V-cycle
+    preconditioner with Jacobi, the shared network or the per-level networks."""
+    import numpy as np
+    import torch
+
+    from paper_2102_12071_gb300 import inputs, solver as S, train as T
+
+    n = 511
+    thetas = [k * math.pi / 12 for k in (1, 2, 3, 4, 5)]
+    probs = [S.rotated(n, 0.01, t) for t in thetas]
+    b = torch.from_numpy(np.stack([inputs.rhs_uniform(inputs.SEED_RHS + 1700 + i, n) for i in range(5)]))
+    b = b.cuda().contiguous()
+    adaptive = load_adaptive()
+    arms = {"jacobi": None, "cnn": weights.cuda() if weights is not None else None,
+            "cnn_adaptive": T.adaptive_params(adaptive, n).cuda() if adaptive is not None else None}
+    out = {"n": n, "eps": 0.01, "thetas": "pi/12 .. 5pi/12", "rtol": 1e-6, "restart": 30,
+           "paper_iterations_511": {"jacobi": [37.0, 30.2, 28.0, 30.0, 37.0], "alpha_cnn": [11.0, 12.0, 13.0, 12.0, 11.0]}}
+    for name, net in arms.items():
+        if name != "jacobi" and net is None:
+            continue
+        mg = S.MultigridSolver(probs, "jacobi" if name == "jacobi" else "cnn", net_params=net)
+        S.fgmres(mg, b, rtol=1e-6, history=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, _, its, st = S.fgmres(mg, b, rtol=1e-6, history=False)
+        torch.cuda.synchronize()
+        ms = 1e3 * (time.perf_counter() - t0)
+        _, _, _, cyc, _ = mg.solve(b, rtol=1e-6, max_cycles=MAX_CYCLES, history=False)
+        out[name] = {"iterations": [int(i) for i in its], "ms_batch": ms, "converged": int(st) == 0,
+                     "vcycle_alone_cycles": [int(c) for c in cyc]}
+        mg.close()
+    return out
+
+
 def run_train(steps: int = 5):
     """One training step (C3): 32 rotated problems at 31^2 and 32 at 63^2, 32 Gaussian
     vectors each; two-grid loss, its exact gradient and the Adam update.  A step includes
@@ -647,6 +683,7 @@ def main():
         extra["c1_63"] = run_c1()
         extra["c2_255"] = run_rotated_batch(255, nprob, weights, rank)
         extra["train"] = run_train()
+        extra["fgmres_511"] = run_fgmres(weights)
     mixed = run_mixed(args, rank, weights) if args.mixed_count else None
     if rank != 0:
         if dist is not None:

@@ -190,6 +190,29 @@ mg_status mg_solve_multi(mg_ctx* const* ctxs, int nctx, const float* const* b, f
                          float* const* x_lo, double rtol, int max_cycles, int* const* cycles,
                          void* const* streams);
 
+/* ------------------------------------------------------- Krylov acceleration ---- */
+
+/* Bytes of device workspace mg_fgmres needs for this context and restart length
+   (1 <= restart <= 200; 0 on invalid arguments). */
+size_t mg_fgmres_workspace_size(const mg_ctx* ctx, int restart);
+
+/* Flexible GMRES(restart) with one V(1,1) cycle of ctx (its smoother) as the right
+   preconditioner (Sec. 6.4), for every problem of the batch: Arnoldi on A M keeping the
+   preconditioned directions z_j = M v_j, classical Gram-Schmidt with one
+   re-orthogonalisation, Givens rotations, x = x_0 + Z y.  A problem stops when the
+   least-squares residual estimate reaches ||b - A x|| / ||b|| < rtol or after max_iters
+   preconditioned steps in all.  b, x_hi, x_lo as for mg_solve (x_hi + x_lo the initial
+   guess in and the float-float solution out; x_lo NULL: zero low part kept in the
+   workspace); every restart evaluates b - A x in compensated arithmetic.  hist: HOST
+   double[nprob * (max_iters + 1)] or NULL, row p the relative residual estimate after
+   0, 1, ... steps; iters: HOST int[nprob] or NULL, steps per problem.  workspace: DEVICE,
+   >= mg_fgmres_workspace_size bytes, 256-byte aligned, caller-owned.  Returns
+   MG_ERR_NOT_CONVERGED if the final (compensated) residual of a problem is >= rtol.
+   Blocks the calling thread; uses ctx's workspace (no solve may run on ctx meanwhile). */
+mg_status mg_fgmres(mg_ctx* ctx, const float* b, float* x_hi, float* x_lo, int restart,
+                    double rtol, int max_iters, void* workspace, size_t ws_bytes,
+                    double* hist, int* iters, void* stream);
+
 /* ------------------------------------------------------------ network (a3) ---- */
 
 /* Number of network parameters: 3x3 convolutions 9->7->5->3 (no bias) and the layer

@@ -70,6 +70,9 @@ def lib() -> ctypes.CDLL:
         "mg_train_destroy": (None, [_P]),
         "mg_train_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
         "mg_train_set_cycles": (ctypes.c_int, [_P, ctypes.c_int]),
+        "mg_fgmres_workspace_size": (ctypes.c_size_t, [_P, ctypes.c_int]),
+        "mg_fgmres": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_int, _P, ctypes.c_size_t,
+                                     _P, _P, _P]),
         "mg_train_step_coarse": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
         "mg_train_get_coarse_field": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
         "mg_solve_small_static": (ctypes.c_int, [ctypes.POINTER(mg_problem), ctypes.c_int, ctypes.POINTER(mg_options),
@@ -252,6 +255,21 @@ def mg_train_step_coarse(ctx, params, z, coarse, coarse_t, grad_out, loss_out, s
 
 def mg_train_get_coarse_field(ctx, prob: int, out, stream=None) -> None:
     check(lib().mg_train_get_coarse_field(ctx, int(prob), _ptr(out), _stream(stream)), "mg_train_get_coarse_field")
+
+
+def mg_fgmres_workspace_size(ctx, restart: int) -> int:
+    return lib().mg_fgmres_workspace_size(ctx, int(restart))
+
+
+def mg_fgmres(ctx, b, x_hi, x_lo, restart, rtol, max_iters, workspace, ws_bytes, hist=None, iters=None,
+              stream=None) -> int:
+    hp = hist.ctypes.data if hist is not None else None
+    ip = iters.ctypes.data if iters is not None else None
+    st = lib().mg_fgmres(ctx, _ptr(b), _ptr(x_hi), _ptr(x_lo), int(restart), float(rtol), int(max_iters),
+                         _ptr(workspace), int(ws_bytes), hp, ip, _stream(stream))
+    if st not in (MG_OK, MG_ERR_NOT_CONVERGED):
+        check(st, "mg_fgmres")
+    return st
 
 
 def mg_train_set_cycles(ctx, cycles: int) -> None:

@@ -675,6 +675,8 @@ static mg_status run_end(SolveRun& R) {
 
 // the cycle arguments of a context whose whole hierarchy runs in one CTA per problem
 // (for the training step's coarse V-cycle); false for other contexts
+void mg::ctx_args(const mg_ctx* ctx, mg::CycleArgs* a) { *a = ctx->args; }
+
 bool mg::ctx_tail_args(const mg_ctx* ctx, mg::CycleArgs* a) {
   if (!ctx || !ctx->plan.tail_solve) return false;
   *a = ctx->args;

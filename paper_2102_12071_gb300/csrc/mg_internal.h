@@ -186,6 +186,7 @@ cudaError_t launch_tail_vec(const CycleArgs& a, const float* rin, float* xout, i
 // W (9 x n x n per-point kernels) <- its transpose's kernels, through scratch (9 x n x n)
 cudaError_t launch_transpose_kernels(float* W, int n, float* scratch, cudaStream_t s);
 bool ctx_tail_args(const ::mg_ctx* ctx, CycleArgs* a);
+void ctx_args(const ::mg_ctx* ctx, CycleArgs* a);
 cudaError_t launch_tail_solve(const CycleArgs& a, const float* b, float* xhi, float* xlo, float rtol, int max_cycles,
                               int budget, int final_residual);
 // cluster tail (mg_ctail.cu): levels lstar .. L-1 in one MG_CT_C-CTA cluster per problem

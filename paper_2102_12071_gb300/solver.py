@@ -101,6 +101,22 @@ class MultigridSolver:
         return x_hi, x_lo, hist, cycles, st
 
 
+def fgmres(mg: "MultigridSolver", b: torch.Tensor, x_hi: torch.Tensor | None = None, x_lo: torch.Tensor | None = None,
+           restart: int = 30, rtol: float = 1e-6, max_iters: int = 500, history: bool = True):
+    """Flexible GMRES with one V-cycle of `mg` as the preconditioner (Sec. 6.4).
+    Returns (x_hi, x_lo, hist [nprob, max_iters+1] (nan past the end), iterations, status)."""
+    shape = (mg.nprob, mg.n, mg.n)
+    assert b.shape == shape and b.dtype == torch.float32 and b.is_contiguous()
+    x_hi = torch.zeros(shape, dtype=torch.float32, device=mg.device) if x_hi is None else x_hi
+    x_lo = torch.zeros(shape, dtype=torch.float32, device=mg.device) if x_lo is None else x_lo
+    size = B.mg_fgmres_workspace_size(mg.ctx, restart)
+    ws = torch.empty(size, dtype=torch.uint8, device=mg.device)
+    hist = np.full((mg.nprob, max_iters + 1), np.nan) if history else None
+    iters = np.zeros(mg.nprob, dtype=np.int32)
+    st = B.mg_fgmres(mg.ctx, b, x_hi, x_lo, restart, rtol, max_iters, ws, size, hist, iters, mg.stream)
+    return x_hi, x_lo, hist, iters, st
+
+
 def net_forward(fields: torch.Tensor, params: torch.Tensor, omega: float = 2.0 / 3.0,
                 conv_bf16: bool = False) -> torch.Tensor:
     """Per-point smoothing kernels for a batch of stencil fields [nprob, 9, n, n]."""
