@@ -451,3 +451,98 @@ def fgmres(apply_A, precond, b, x0=None, restart: int = 30, rtol: float = 1e-6, 
         x = x + sum(yi * zi for yi, zi in zip(y, Z))
         r = bv - A(x)
     return x.reshape(shape), np.array(hist), its
+
+
+# ------------------------------------------- fully connected stencil-to-smoother network
+FC_LAYERS = [(40, 81), (40, 40), (40, 40), (9, 40)]  # (out, in): "4 fully connected layers" of Sec. 6.2
+FC_SLOPE = 0.01
+
+
+def fc_nparams() -> int:
+    return sum(o * i for o, i in FC_LAYERS)
+
+
+def _bf16_array(a):
+    return np.vectorize(bf16)(a) if a.size else a
+
+
+def fc_features(st, bf16_round: bool = False) -> np.ndarray:
+    """Sec. 4.2 (parameterisation with fully connected layers): the representation of a grid
+    point is the 81 stencil values of its 3x3 neighbourhood.  Feature 9 m + c is tap c of the
+    neighbour at offset d_m (m = 3 (di + 1) + (dj + 1)), divided by that neighbour's own
+    diagonal (the input normalisation of the convolutional network); zero outside the grid.
+    Returns [n*n, 81]."""
+    st = _f64(st)
+    n = st.shape[1]
+    a0 = st / st[4]
+    if bf16_round:
+        a0 = _bf16_array(a0)
+    X = np.zeros((n, n, 81))
+    for m in range(9):
+        di, dj = m // 3 - 1, m % 3 - 1
+        i0, i1 = max(0, -di), min(n, n - di)
+        j0, j1 = max(0, -dj), min(n, n - dj)
+        X[i0:i1, j0:j1, 9 * m:9 * m + 9] = np.moveaxis(a0[:, i0 + di:i1 + di, j0 + dj:j1 + dj], 0, -1)
+    return X.reshape(n * n, 81)
+
+
+def _fc_weights(params, bf16_round):
+    params = _f64(params)
+    assert params.size == fc_nparams()
+    out, o = [], 0
+    for co, ci in FC_LAYERS:
+        w = params[o:o + co * ci].reshape(co, ci)
+        out.append(_bf16_array(w) if bf16_round else w)
+        o += co * ci
+    return out
+
+
+def fc_forward(st, params, omega: float = 2.0 / 3.0, bf16: bool = False) -> np.ndarray:
+    """Per-point kernels W = (omega delta_4 + NN)/D from the fully connected network
+    81 -> 40 -> 40 -> 40 -> 9, LeakyReLU(0.01) after the hidden layers, no biases (6 800
+    parameters, Sec. 6.2); with bf16, weights, inputs and activations rounded to bfloat16."""
+    st = _f64(st)
+    n = st.shape[1]
+    Ws = _fc_weights(params, bf16)
+    a = fc_features(st, bf16)
+    for l, w in enumerate(Ws):
+        z = a @ w.T
+        if l < 3:
+            a = np.where(z > 0, z, FC_SLOPE * z)
+            if bf16:
+                a = _bf16_array(a)
+        else:
+            a = z
+    out = a.T.reshape(9, n, n)
+    W = out.copy()
+    W[4] += omega
+    return W / st[4]
+
+
+def fc_backward(st, params, dW, omega: float = 2.0 / 3.0, bf16: bool = False) -> np.ndarray:
+    """dLoss/dparams of fc_forward given dLoss/dW (rounding treated as the identity)."""
+    st, dW = _f64(st), _f64(dW)
+    n = st.shape[1]
+    Ws = _fc_weights(params, bf16)
+    acts, zs = [fc_features(st, bf16)], []
+    for l, w in enumerate(Ws):
+        z = acts[-1] @ w.T
+        zs.append(z)
+        if l < 3:
+            a = np.where(z > 0, z, FC_SLOPE * z)
+            acts.append(_bf16_array(a) if bf16 else a)
+    d = (dW / st[4]).reshape(9, n * n).T  # dLoss/dout, [P, 9]
+    grads = [None] * 4
+    for l in range(3, -1, -1):
+        grads[l] = d.T @ acts[l]
+        if l > 0:
+            da = d @ Ws[l]
+            d = da * np.where(zs[l - 1] > 0, 1.0, FC_SLOPE)
+    return np.concatenate([g.ravel() for g in grads])
+
+
+def fc_loss_and_grad(st, params, z, omega: float = 2.0 / 3.0, bf16: bool = False, cycles: int = 1):
+    """The two-grid objective (eq. twogrid) as a function of the FC network's parameters."""
+    W = fc_forward(st, params, omega, bf16)
+    loss, dW = twogrid_loss(st, W, z, want_grad=True, cycles=cycles)
+    return loss, fc_backward(st, params, dW, omega, bf16)

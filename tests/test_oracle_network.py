@@ -283,3 +283,71 @@ def test_vcycle_loss_gradient_matches_finite_differences():
         fd = (O.vcycle_loss(st, O.hypernet_forward(st, pp), fwd, adj, z, cycles=2)
               - O.vcycle_loss(st, O.hypernet_forward(st, pm), fwd, adj, z, cycles=2)) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 * max(abs(g).max(), 1e-12), (i, fd, g[i])
+
+
+# ------------------------------------------------------------ fully connected network
+NFC = 81 * 40 + 40 * 40 + 40 * 40 + 40 * 9
+
+
+def test_fc_parameter_count_is_the_papers():
+    assert O.fc_nparams() == NFC == 6800
+
+
+def test_fc_zero_last_layer_is_weighted_jacobi():
+    n = 7
+    st = O.const_field(n, O.q1_rotated_stencil(0.2, 0.3))
+    p = np.random.default_rng(30).standard_normal(NFC)
+    p[-360:] = 0.0
+    np.testing.assert_allclose(O.fc_forward(st, p), O.jacobi_kernels(st), rtol=1e-15, atol=0)
+
+
+def _torch_fc(st, p):
+    """The same network in torch (float64): unfold of the normalised stencil field gives the
+    3x3-neighbourhood features; linear layers and leaky_relu from torch.nn.functional."""
+    n = st.shape[1]
+    a0 = torch.from_numpy(st / st[4])[None]                      # [1, 9, n, n]
+    U = F.unfold(a0, 3, padding=1)[0]                            # [9*9, n*n]: (c, ky, kx) major
+    U = U.reshape(9, 9, n * n).permute(1, 0, 2).reshape(81, n * n)  # feature 9 m + c
+    x = U.T
+    pt = torch.from_numpy(p).requires_grad_(True)
+    o = 0
+    h = x
+    for l, (co, ci) in enumerate([(40, 81), (40, 40), (40, 40), (9, 40)]):
+        w = pt[o:o + co * ci].reshape(co, ci)
+        o += co * ci
+        h = F.linear(h, w)
+        if l < 3:
+            h = F.leaky_relu(h, 0.01)
+    out = h.T.reshape(9, n, n)
+    d = torch.from_numpy(st[4])
+    W = out.clone()
+    W[4] = W[4] + 2.0 / 3.0
+    return W / d, pt
+
+
+def test_fc_forward_and_backward_match_torch_autograd():
+    n = 9
+    rng = np.random.default_rng(31)
+    st = O.varcoef5_field(n, np.exp(rng.standard_normal((n + 1, n + 1))))
+    p = rng.standard_normal(NFC) * 0.1
+    Wt, pt = _torch_fc(st, p)
+    np.testing.assert_allclose(O.fc_forward(st, p), Wt.detach().numpy(), rtol=1e-12, atol=1e-14)
+    dW = rng.standard_normal((9, n, n))
+    (Wt * torch.from_numpy(dW)).sum().backward()
+    np.testing.assert_allclose(O.fc_backward(st, p, dW), pt.grad.numpy(), rtol=1e-10, atol=1e-12)
+
+
+def test_fc_loss_gradient_matches_finite_differences():
+    n = 15
+    rng = np.random.default_rng(32)
+    st = O.const_field(n, O.q1_rotated_stencil(0.05, 2.0))
+    p = rng.standard_normal(NFC) * 0.05
+    z = rng.standard_normal((2, n, n))
+    _, g = O.fc_loss_and_grad(st, p, z)
+    h = 1e-6
+    for i in list(rng.choice(NFC, 8, replace=False)) + [NFC - 1, 0]:
+        pp, pm = p.copy(), p.copy()
+        pp[i] += h
+        pm[i] -= h
+        fd = (O.twogrid_loss(st, O.fc_forward(st, pp), z) - O.twogrid_loss(st, O.fc_forward(st, pm), z)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(abs(g).max(), 1e-12), (i, fd, g[i])
