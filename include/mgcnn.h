@@ -108,7 +108,16 @@ typedef struct {
                            problems only), so a V-cycle of this context applies M^T when
                            the context without it applies M: the adjoint coarse solve of
                            mg_train_step_coarse                                          */
+  int net_arch;         /* MG_SMOOTH_CNN: mg_net_arch; parameter sets hold
+                           mg_net_param_count(net_arch) floats                           */
 } mg_options;
+
+typedef enum {
+  MG_NET_CONV = 0, /* 3x3 convolutions 9->7->5->3 and a 27->9 layer (Sec. 4.2, 1 260 params) */
+  MG_NET_FC = 1    /* fully connected 81->40->40->40->9 on the 3x3 neighbourhood's stencils
+                      (Sec. 4.2 parameterisation with fully connected layers, Sec. 6.2:
+                      6 800 params)                                                      */
+} mg_net_arch;
 
 typedef struct mg_ctx mg_ctx;
 typedef struct mg_train_ctx mg_train_ctx;
@@ -221,12 +230,23 @@ mg_status mg_fgmres(mg_ctx* ctx, const float* b, float* x_hi, float* x_lo, int r
    w3[3][5][3][3], wf[9][3][3][3]; LeakyReLU slope 0.01 after each convolution. */
 int mg_net_nparams(void);
 
+/* Parameters of a network architecture (mg_net_arch); 0 for an unknown one. */
+int mg_net_param_count(int arch);
+
 /* Network inference on nprob stencil fields (DEVICE float[nprob][9][n][n]): per point,
    input channel c = st[c]/st[4] (zero outside the grid), output kernel
    W = (omega*delta_4 + NN)/st[4] written to W (DEVICE float[nprob][9][n][n]).
    params: DEVICE float[mg_net_nparams()]. */
 mg_status mg_net_forward(int n, int nprob, const float* fields, const float* params,
                          float omega, int conv_bf16, float* W, void* stream);
+
+/* The same for the fully connected network (MG_NET_FC): per point the 81 values of its
+   3x3 neighbourhood, feature 9 m + c = tap c of the neighbour at offset m (row-major
+   3x3 offsets) divided by that neighbour's diagonal, zero outside the grid; layers
+   81->40->40->40->9 (weights [out][in] consecutively, no biases), LeakyReLU 0.01 after
+   the hidden layers, W = (omega*delta_4 + out)/diag.  params: DEVICE float[6800]. */
+mg_status mg_net_fc_forward(int n, int nprob, const float* fields, const float* params,
+                            float omega, int bf16, float* W, void* stream);
 
 /* --------------------------------------------------------- training (a11-a12) ---- */
 
@@ -249,9 +269,9 @@ void mg_train_destroy(mg_train_ctx* ctx);
      S = I - H A,  C = I - P (P^T A P)^{-1} P^T A,
    with H the network's per-point kernels for problem b and k set by mg_train_set_cycles
    (default: train_cycles of the setup).  z: DEVICE float[nprob][nvec][n][n] (the random
-   vectors, supplied by the caller), params: DEVICE float[mg_net_nparams()], grad_out:
-   DEVICE float[mg_net_nparams()] (overwritten with dloss/dparams, the adjoint through all
-   k cycles; may be NULL), loss_out: DEVICE float[1]. */
+   vectors, supplied by the caller), params and grad_out: DEVICE
+   float[mg_net_param_count(net_arch of the setup)] (grad_out overwritten with dloss/dparams,
+   the adjoint through all k cycles; may be NULL), loss_out: DEVICE float[1]. */
 mg_status mg_train_step(mg_train_ctx* ctx, const float* params, const float* z,
                         float* grad_out, float* loss_out, void* stream);
 

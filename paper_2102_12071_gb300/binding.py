@@ -27,7 +27,7 @@ class mg_options(ctypes.Structure):
     _fields_ = [("smoother", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("omega", ctypes.c_float), ("coarsest_n", ctypes.c_int), ("conv_bf16", ctypes.c_int),
                 ("cluster_tail", ctypes.c_int), ("train_cycles", ctypes.c_int), ("train_checkpoint", ctypes.c_int),
-                ("net_levels", ctypes.c_int), ("smoother_transpose", ctypes.c_int)]
+                ("net_levels", ctypes.c_int), ("smoother_transpose", ctypes.c_int), ("net_arch", ctypes.c_int)]
 
 
 class MGError(RuntimeError):
@@ -71,6 +71,8 @@ def lib() -> ctypes.CDLL:
         "mg_train_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
         "mg_train_set_cycles": (ctypes.c_int, [_P, ctypes.c_int]),
         "mg_fgmres_workspace_size": (ctypes.c_size_t, [_P, ctypes.c_int]),
+        "mg_net_param_count": (ctypes.c_int, [ctypes.c_int]),
+        "mg_net_fc_forward": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_float, ctypes.c_int, _P, _P]),
         "mg_fgmres": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_int, _P, ctypes.c_size_t,
                                      _P, _P, _P]),
         "mg_train_step_coarse": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
@@ -137,9 +139,9 @@ def problems_array(problems: list[dict]):
 
 def options(smoother: int = MG_SMOOTH_JACOBI, omega: float = 2.0 / 3.0, coarsest_n: int = 3,
             conv_bf16: int = 0, cluster_tail: int = 1, train_cycles: int = 1, train_checkpoint: int = 0,
-            net_levels: int = 0, smoother_transpose: int = 0) -> mg_options:
+            net_levels: int = 0, smoother_transpose: int = 0, net_arch: int = 0) -> mg_options:
     return mg_options(smoother, 1, 1, omega, coarsest_n, conv_bf16, cluster_tail, train_cycles, train_checkpoint,
-                      net_levels, smoother_transpose)
+                      net_levels, smoother_transpose, net_arch)
 
 
 def mg_workspace_size(probs, nprob: int, opts: mg_options) -> int:
@@ -255,6 +257,18 @@ def mg_train_step_coarse(ctx, params, z, coarse, coarse_t, grad_out, loss_out, s
 
 def mg_train_get_coarse_field(ctx, prob: int, out, stream=None) -> None:
     check(lib().mg_train_get_coarse_field(ctx, int(prob), _ptr(out), _stream(stream)), "mg_train_get_coarse_field")
+
+
+MG_NET_CONV, MG_NET_FC = 0, 1
+
+
+def mg_net_param_count(arch: int) -> int:
+    return lib().mg_net_param_count(int(arch))
+
+
+def mg_net_fc_forward(n, nprob, fields, params, omega, bf16, W, stream=None):
+    check(lib().mg_net_fc_forward(n, nprob, _ptr(fields), _ptr(params), float(omega), int(bf16), _ptr(W),
+                                  _stream(stream)), "mg_net_fc_forward")
 
 
 def mg_fgmres_workspace_size(ctx, restart: int) -> int:

@@ -65,6 +65,7 @@ mg_status make_plan(const mg_problem* probs, int nprob, const mg_options* o, Pla
   if (o->coarsest_n != 3 && o->coarsest_n != 7) return fail(MG_ERR_UNSUPPORTED, "coarsest_n must be 3 or 7");
   if (!(o->omega > 0.f) || !(o->omega < 2.f)) return fail(MG_ERR_INVALID_ARG, "omega must be in (0, 2)");
   if (o->net_levels < 0 || o->net_levels > MG_MAXL) return fail(MG_ERR_INVALID_ARG, "net_levels out of range");
+  if (o->net_arch != MG_NET_CONV && o->net_arch != MG_NET_FC) return fail(MG_ERR_INVALID_ARG, "unknown net_arch");
   const int n = probs[0].n;
   if (!is_pow2m1(n) || n < o->coarsest_n || n > 8191)
     return fail(MG_ERR_INVALID_ARG, "n = %d must be 2^m - 1 in [coarsest_n, 8191]", n);
@@ -354,6 +355,8 @@ size_t mg_workspace_size(const mg_problem* problems, int nprob, const mg_options
 
 int mg_net_nparams(void) { return MG_NPARAMS; }
 
+int mg_net_param_count(int arch) { return arch == MG_NET_CONV ? MG_NPARAMS : arch == MG_NET_FC ? MG_NPARAMS_FC : 0; }
+
 mg_status mg_setup(const mg_problem* problems, int nprob, const mg_options* opts, const float* net_params,
                    void* workspace, size_t ws_bytes, void* stream, mg_ctx** out) {
   if (!out) return fail(MG_ERR_INVALID_ARG, "out is NULL");
@@ -452,15 +455,20 @@ mg_status mg_setup(const mg_problem* problems, int nprob, const mg_options* opts
         }
       }
       CK(cudaMemcpyAsync(ctx->d_jobs, jobs.data(), sizeof(NetJob) * jobs.size(), cudaMemcpyHostToDevice, s));
+      const bool fc = opts->net_arch == MG_NET_FC;
+      const size_t np_set = fc ? MG_NPARAMS_FC : MG_NPARAMS;
+      auto net = [&](const NetJob* jobs_dev, int njobs, int nm, const float* prm) {
+        return fc ? launch_fc_forward(jobs_dev, njobs, nm, prm, opts->omega, opts->conv_bf16, s)
+                  : launch_net_forward(jobs_dev, njobs, nm, prm, opts->omega, opts->conv_bf16, s);
+      };
       if (opts->net_levels <= 1) {
         int nm = 0;
         for (int l = 0; l + 1 < P.L; ++l) nm = nmax[l] > nm ? nmax[l] : nm;
-        CK(launch_net_forward(ctx->d_jobs, (int)jobs.size(), nm, net_params, opts->omega, opts->conv_bf16, s));
+        CK(net(ctx->d_jobs, (int)jobs.size(), nm, net_params));
       } else {
         for (int l = 0; l + 1 < P.L; ++l) {
           const int set = l < opts->net_levels ? l : opts->net_levels - 1;
-          CK(launch_net_forward(ctx->d_jobs + first[l], nprob, nmax[l], net_params + (size_t)set * MG_NPARAMS,
-                                opts->omega, opts->conv_bf16, s));
+          CK(net(ctx->d_jobs + first[l], nprob, nmax[l], net_params + (size_t)set * np_set));
         }
       }
       if (opts->smoother_transpose)
@@ -743,6 +751,20 @@ mg_status mg_solve_multi(mg_ctx* const* ctxs, int nctx, const float* const* b, f
     if (rc == MG_OK) rc = st;
   }
   return rc;
+}
+
+mg_status mg_net_fc_forward(int n, int nprob, const float* fields, const float* params, float omega, int bf16,
+                            float* W, void* stream) {
+  if (n < 1 || n > 8191 || nprob < 1 || nprob > 65535 || !fields || !params || !W)
+    return fail(MG_ERR_INVALID_ARG, "mg_net_fc_forward: bad arguments");
+  NetBatch B;
+  B.st = fields;
+  B.W = W;
+  B.stride = 9 * (size_t)n * n;
+  B.n = n;
+  B.pad_ = 0;
+  CK(launch_fc_forward_batch(B, nprob, params, omega, bf16, (cudaStream_t)stream));
+  return MG_OK;
 }
 
 mg_status mg_net_forward(int n, int nprob, const float* fields, const float* params, float omega, int conv_bf16,

@@ -23,6 +23,7 @@
 #define MG_NET_MARGIN 5       // points closer than this to an edge get their own kernel class
 #define MG_PROXY (2 * MG_NET_MARGIN + 1)  // proxy grid side for constant-stencil inference
 #define MG_NPARAMS 1260
+#define MG_NPARAMS_FC 6800  // the fully connected network, 81 -> 40 -> 40 -> 40 -> 9
 
 enum { SK_CONST = 0, SK_FIELD = 1 };                 // stencil storage
 enum { HK_JACOBI = 0, HK_TABLE = 1, HK_FIELD = 2 };  // smoother storage

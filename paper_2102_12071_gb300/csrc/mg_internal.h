@@ -211,6 +211,14 @@ cudaError_t launch_net_forward_batch(const NetBatch& batch, int nfields, const f
                                      cudaStream_t s);
 cudaError_t launch_copy_rel(const ProbState* state, float* rel, int nprob, cudaStream_t s);
 int net_backward_ctas(int n, int nfields);
+// the fully connected network (mg_netfc.cu); the backward needs fc_backward_floats scratch
+cudaError_t launch_fc_forward(const NetJob* jobs_dev, int njobs, int nmax, const float* params, float omega, int bf16,
+                              cudaStream_t s);
+cudaError_t launch_fc_forward_batch(const NetBatch& batch, int nfields, const float* params, float omega, int bf16,
+                                    cudaStream_t s);
+size_t fc_backward_floats(int n, int nfields);
+cudaError_t launch_fc_backward(const NetBatch& batch, int nfields, const float* dW, const float* params, int bf16,
+                               float* scratch, float scale, float* grad, cudaStream_t s);
 cudaError_t launch_net_backward(const NetBatch& batch, int nfields, const float* dW, const float* params, int bf16,
                                 float* partials, float scale, float* grad, cudaStream_t s);
 

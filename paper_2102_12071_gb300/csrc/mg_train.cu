@@ -379,6 +379,8 @@ struct mg_train_ctx {
   int* fail = nullptr;
   int ncta_bw = 0;
   int kmax = 1, k = 1, ckpt = 0;   // cycles reserved / used by the loss; checkpointing
+  int arch = MG_NET_CONV;          // network architecture (mg_net_arch)
+  float* fc_scratch = nullptr;     // the fully connected network's backward tape
   std::vector<float*> X;           // X[c]: input of cycle c >= 1
   std::vector<float*> V0, V2;      // A e_c and A (C S e_c) of cycle c (V0[0] = v0, V2[0] = v2)
   std::vector<float> h_s9;
@@ -393,6 +395,8 @@ mg_status train_dims(const mg_problem* probs, int nprob, int nvec, const mg_opti
   if (!probs || nprob < 1 || nvec < 1 || !o) return (mg_status)api_fail(MG_ERR_INVALID_ARG, "training: bad arguments");
   if (o->train_cycles < 0 || o->train_cycles > kMaxTrainCycles)
     return (mg_status)api_fail(MG_ERR_INVALID_ARG, "train_cycles must be in [0, %d]", kMaxTrainCycles);
+  if (o->net_arch != MG_NET_CONV && o->net_arch != MG_NET_FC)
+    return (mg_status)api_fail(MG_ERR_INVALID_ARG, "unknown net_arch");
   if ((long long)nprob * nvec > 65535) return (mg_status)api_fail(MG_ERR_INVALID_ARG, "nprob * nvec must be <= 65535");
   if (!(o->omega > 0.f) || !(o->omega < 2.f)) return (mg_status)api_fail(MG_ERR_INVALID_ARG, "omega must be in (0, 2)");
   const int n = probs[0].n;
@@ -435,7 +439,7 @@ T* take(char* base, size_t& off, size_t count) {
   return p;
 }
 
-size_t train_carve(const TrainDims& D, int kmax, int ckpt, void* basev, mg_train_ctx* c) {
+size_t train_carve(const TrainDims& D, int kmax, int ckpt, int arch, void* basev, mg_train_ctx* c) {
   char* base = (char*)basev;
   size_t off = 0;
   const size_t BZ = (size_t)D.B * D.Z, m = D.nnc, ld = D.w + 1;
@@ -467,6 +471,7 @@ size_t train_carve(const TrainDims& D, int kmax, int ckpt, void* basev, mg_train
   x.loss_partial = take<float>(base, off, BZ);
   x.ncta_bw = net_backward_ctas(D.n, D.B);
   x.param_partial = take<float>(base, off, (size_t)x.ncta_bw * MG_NPARAMS);
+  x.fc_scratch = arch == MG_NET_FC ? take<float>(base, off, fc_backward_floats(D.n, D.B)) : nullptr;
   x.fail = take<int>(base, off, 4);
   return off + 256;
 }
@@ -485,8 +490,8 @@ size_t mg_train_workspace_size(const mg_problem* problems, int nprob, int nvec, 
   TrainDims D;
   int is_const = 0;
   if (train_dims(problems, nprob, nvec, opts, D, is_const) != MG_OK) return 0;
-  return train_carve(D, opts->train_cycles > 1 ? opts->train_cycles : 1, opts->train_checkpoint != 0, nullptr,
-                     nullptr);
+  return train_carve(D, opts->train_cycles > 1 ? opts->train_cycles : 1, opts->train_checkpoint != 0, opts->net_arch,
+                     nullptr, nullptr);
 }
 
 mg_status mg_train_setup(const mg_problem* problems, int nprob, int nvec, const mg_options* opts, void* workspace,
@@ -498,7 +503,7 @@ mg_status mg_train_setup(const mg_problem* problems, int nprob, int nvec, const 
   mg_status st = train_dims(problems, nprob, nvec, opts, D, is_const);
   if (st != MG_OK) return st;
   const int kmax = opts->train_cycles > 1 ? opts->train_cycles : 1, ckpt = opts->train_checkpoint != 0;
-  const size_t need = train_carve(D, kmax, ckpt, nullptr, nullptr);
+  const size_t need = train_carve(D, kmax, ckpt, opts->net_arch, nullptr, nullptr);
   if (!workspace || ws_bytes < need)
     return (mg_status)api_fail(MG_ERR_WORKSPACE, "training workspace needs %zu bytes, got %zu", need, ws_bytes);
   if (((uintptr_t)workspace & 255) != 0) return (mg_status)api_fail(MG_ERR_WORKSPACE, "workspace must be 256-byte aligned");
@@ -509,7 +514,8 @@ mg_status mg_train_setup(const mg_problem* problems, int nprob, int nvec, const 
   c->omega = opts->omega;
   c->kmax = c->k = kmax;
   c->ckpt = ckpt;
-  train_carve(D, kmax, ckpt, workspace, c);
+  c->arch = opts->net_arch;
+  train_carve(D, kmax, ckpt, opts->net_arch, workspace, c);
   auto run = [&]() -> mg_status {
     const dim3 gp((unsigned)((D.nn + TT - 1) / TT), D.B);
     if (is_const) {
@@ -584,7 +590,8 @@ static mg_status train_step(mg_train_ctx* c, const float* params, const float* z
   nb.stride = 9 * D.nn;
   nb.n = D.n;
   nb.pad_ = 0;
-  TCK(launch_net_forward_batch(nb, D.B, params, c->omega, c->bf16, s));
+  if (c->arch == MG_NET_FC) TCK(launch_fc_forward_batch(nb, D.B, params, c->omega, c->bf16, s));
+  else TCK(launch_net_forward_batch(nb, D.B, params, c->omega, c->bf16, s));
   const int K = c->k;
   // xc = M rc: the exact coarse solve (banded Cholesky), or one V-cycle of the coarse
   // context (cf), whose transpose ct serves the adjoint
@@ -635,7 +642,8 @@ static mg_status train_step(mg_train_ctx* c, const float* params, const float* z
   }
   TCK(ce);
   TCK(cudaGetLastError());
-  TCK(launch_net_backward(nb, D.B, c->dW, params, c->bf16, c->param_partial, 1.f, grad_out, s));
+  if (c->arch == MG_NET_FC) TCK(launch_fc_backward(nb, D.B, c->dW, params, c->bf16, c->fc_scratch, 1.f, grad_out, s));
+  else TCK(launch_net_backward(nb, D.B, c->dW, params, c->bf16, c->param_partial, 1.f, grad_out, s));
   return MG_OK;
 }
 

@@ -34,10 +34,11 @@ class MultigridSolver:
 
     def __init__(self, problems: list[dict], smoother: str = "jacobi", net_params: torch.Tensor | None = None,
                  omega: float = 2.0 / 3.0, conv_bf16: bool = False, coarsest_n: int = 3, device="cuda",
-                 stream=None, cluster_tail: bool = True, transpose: bool = False):
+                 stream=None, cluster_tail: bool = True, transpose: bool = False, net_arch: str = "conv"):
         """net_params: one parameter set [nparams] for every level, or per-level sets
         [k, nparams] (level l uses set min(l, k - 1)).  transpose: smooth with H^T (per-point
-        problems), so that a V-cycle applies the transpose of the cycle without it."""
+        problems), so that a V-cycle applies the transpose of the cycle without it.
+        net_arch: "conv" (the convolutional network) or "fc" (the fully connected one)."""
         self.nprob = len(problems)
         self.n = problems[0]["n"]
         self.device = torch.device(device)
@@ -45,8 +46,9 @@ class MultigridSolver:
         self._probs, self._keep = B.problems_array(problems)
         kind = B.MG_SMOOTH_CNN if smoother == "cnn" else B.MG_SMOOTH_JACOBI
         net_levels = int(net_params.shape[0]) if net_params is not None and net_params.dim() == 2 else 0
+        arch = B.MG_NET_FC if net_arch == "fc" else B.MG_NET_CONV
         self.opts = B.options(kind, omega, coarsest_n, int(conv_bf16), int(cluster_tail), 1, 0, net_levels,
-                              int(transpose))
+                              int(transpose), arch)
         size = B.mg_workspace_size(self._probs, self.nprob, self.opts)
         if size == 0:
             raise B.MGError(B.MG_ERR_INVALID_ARG, "mg_workspace_size", B.lib().mg_last_error().decode())

@@ -21,6 +21,26 @@ from . import inputs
 
 NPARAMS = 1260
 LAYERS = [(7, 9), (5, 7), (3, 5), (9, 3)]  # (out, in) channels of the 3x3 layers
+NPARAMS_FC = 6800
+FC_LAYERS = [(40, 81), (40, 40), (40, 40), (9, 40)]  # the fully connected network (out, in)
+
+
+def nparams(arch: str = "conv") -> int:
+    return NPARAMS_FC if arch == "fc" else NPARAMS
+
+
+def init_params_fc(seed: int = 0) -> torch.Tensor:
+    """The fully connected network: LeakyReLU Kaiming-uniform hidden layers, zero output
+    layer (the network starts at weighted Jacobi)."""
+    g = torch.Generator().manual_seed(seed)
+    parts = []
+    for k, (co, ci) in enumerate(FC_LAYERS):
+        if k == len(FC_LAYERS) - 1:
+            parts.append(torch.zeros(co * ci))
+        else:
+            bound = math.sqrt(6.0 / ((1 + 0.01 ** 2) * ci))
+            parts.append((torch.rand(co * ci, generator=g) * 2 - 1) * bound)
+    return torch.cat(parts)
 
 
 def init_params(seed: int = 0) -> torch.Tensor:
@@ -43,12 +63,15 @@ class TwoGridBatch:
     """Device workspace + context for one training batch of same-size problems."""
 
     def __init__(self, problems: list[dict], nvec: int, omega: float = 2.0 / 3.0, conv_bf16: bool = False,
-                 workspace: torch.Tensor | None = None, cycles: int = 1, checkpoint: bool = False):
+                 workspace: torch.Tensor | None = None, cycles: int = 1, checkpoint: bool = False,
+                 net_arch: str = "conv"):
         self.n = problems[0]["n"]
         self.nprob = len(problems)
         self.nvec = nvec
+        self.net_arch = net_arch
         self._probs, self._keep = B.problems_array(problems)
-        self.opts = B.options(B.MG_SMOOTH_CNN, omega, 3, int(conv_bf16), 1, int(cycles), int(checkpoint))
+        self.opts = B.options(B.MG_SMOOTH_CNN, omega, 3, int(conv_bf16), 1, int(cycles), int(checkpoint), 0, 0,
+                              B.MG_NET_FC if net_arch == "fc" else B.MG_NET_CONV)
         size = B.mg_train_workspace_size(self._probs, self.nprob, nvec, self.opts)
         if size == 0:
             raise B.MGError(B.MG_ERR_INVALID_ARG, "mg_train_workspace_size", B.lib().mg_last_error().decode())
@@ -105,7 +128,7 @@ class TwoGridBatch:
     def loss_and_grad(self, params: torch.Tensor, z: torch.Tensor, want_grad: bool = True):
         assert z.shape == (self.nprob, self.nvec, self.n, self.n) and z.is_contiguous()
         loss = torch.empty(1, device="cuda")
-        grad = torch.empty(NPARAMS, device="cuda") if want_grad else None
+        grad = torch.empty(nparams(self.net_arch), device="cuda") if want_grad else None
         if getattr(self, "_coarse", None):
             B.mg_train_step_coarse(self.ctx, params.contiguous(), z, self._coarse[0].ctx, self._coarse[1].ctx, grad, loss)
         else:
@@ -134,10 +157,12 @@ class Trainer:
 
     def __init__(self, sizes=(31, 63), per_size: int = 32, nvec: int = 32, omega: float = 2.0 / 3.0,
                  conv_bf16: bool = True, lr: float = 1e-3, seed: int = 0, eps_range=(1e-3, 1.0),
-                 families=("rotated",), max_cycles: int = 1, checkpoint: bool = False):
-        """max_cycles = b of Algorithm 2: each step's loss spans k ~ U{1..b} two-grid cycles."""
+                 families=("rotated",), max_cycles: int = 1, checkpoint: bool = False, net_arch: str = "conv"):
+        """max_cycles = b of Algorithm 2: each step's loss spans k ~ U{1..b} two-grid cycles.
+        net_arch: "conv" or "fc" (the fully connected network of Sec. 4.2)."""
         self.max_cycles = max_cycles
         self.checkpoint = checkpoint
+        self.net_arch = net_arch
         self.sizes = sizes
         self.per_size = per_size
         self.nvec = nvec
@@ -145,7 +170,7 @@ class Trainer:
         self.conv_bf16 = conv_bf16
         self.eps_range = eps_range
         self.families = families
-        self.params = init_params(seed).cuda().requires_grad_(True)
+        self.params = (init_params_fc(seed) if net_arch == "fc" else init_params(seed)).cuda().requires_grad_(True)
         self.opt = torch.optim.Adam([self.params], lr=lr)
         self.gen = torch.Generator(device="cuda").manual_seed(inputs.SEED_TRAIN + seed)
         self._ws = {}
@@ -176,7 +201,7 @@ class Trainer:
                 probs = self.problems(step, n, family)
                 key = (family, n)
                 batch = TwoGridBatch(probs, self.nvec, self.omega, self.conv_bf16, self._ws.get(key),
-                                     cycles=self.max_cycles, checkpoint=self.checkpoint)
+                                     cycles=self.max_cycles, checkpoint=self.checkpoint, net_arch=self.net_arch)
                 batch.set_cycles(k)
                 self._ws[key] = batch.workspace
                 z = torch.randn((self.per_size, self.nvec, n, n), generator=self.gen, device="cuda")
@@ -304,6 +329,7 @@ def main():
     ap.add_argument("--families", default="rotated", help="comma list of rotated,varcoef")
     ap.add_argument("--max-cycles", type=int, default=1, help="b: each step's loss spans k ~ U{1..b} cycles")
     ap.add_argument("--checkpoint", action="store_true", help="recompute cycle products in the backward pass")
+    ap.add_argument("--fc", action="store_true", help="train the fully connected network (Sec. 4.2)")
     ap.add_argument("--adaptive", type=int, default=0, metavar="N_FINE",
                     help="Algorithm 2: one network per level of a hierarchy of this side, trained coarse to fine "
                          "(--steps per level); saves [levels, nparams], finest first")
@@ -327,7 +353,7 @@ def main():
         return
     tr = Trainer(lr=args.lr, seed=args.seed, conv_bf16=not args.fp32_conv,
                  families=tuple(f.strip() for f in args.families.split(",")), max_cycles=args.max_cycles,
-                 checkpoint=args.checkpoint)
+                 checkpoint=args.checkpoint, net_arch="fc" if args.fc else "conv")
     t0 = time.time()
     for s in range(args.steps):
         l = tr.step()

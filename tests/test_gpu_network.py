@@ -376,3 +376,57 @@ def test_adaptive_per_level_networks_gain_over_shared_network_and_jacobi():
     k = min(41, int(np.count_nonzero(~np.isnan(hist0))))
     rel = np.abs(hist0[:k] - oh[:k]) / oh[:k]
     assert rel.max() <= 1e-5, rel.max()
+
+
+# ------------------------------------------------------------ fully connected network
+def _fc_params(seed, scale=0.1):
+    return (np.random.default_rng(seed).standard_normal(6800) * scale).astype(np.float32)
+
+
+@pytest.mark.parametrize("kind", ["rotated", "varcoef"])
+def test_fc_kernels_match_oracle_on_every_level(kind):
+    """The fully connected network's kernels in a solver context (class tables for constant
+    stencils, per-point for fields) against the oracle's network on every level's field."""
+    n = 31
+    p = _fc_params(40)
+    if kind == "rotated":
+        prob = S.rotated(n, 0.03, 2.0)
+        st0 = O.const_field(n, f32(O.q1_rotated_stencil(0.03, 2.0)))
+    else:
+        cells = inputs.grf_cells(inputs.SEED_GRF + 70, n)
+        prob = S.varcoef5(n, torch.from_numpy(cells).cuda())
+        st0 = f32(O.varcoef5_field(n, f32(cells)))
+    mg = S.MultigridSolver([prob], "cnn", torch.from_numpy(p).cuda(), net_arch="fc")
+    om = O.Multigrid(st0)
+    for l in range(mg.levels - 1):
+        Wg = mg.kernels(0, l).double().cpu().numpy()
+        Wo = O.fc_forward(om.field(l), f32(p))
+        np.testing.assert_allclose(Wg, Wo, rtol=2e-5, atol=2e-5 * np.abs(Wo).max())
+
+
+@pytest.mark.parametrize("n,bf16", [(15, False), (31, False), (15, True)])
+def test_fc_train_step_matches_oracle(n, bf16):
+    """Loss and gradient of the two-grid objective through the fully connected network."""
+    nprob, nvec = 3, 4
+    params = inputs.rotated_params(120 + n, nprob)
+    probs = [{"n": n, "kind": B.MG_PROBLEM_ROTATED, "eps": e, "theta": t} for e, t in params]
+    z = inputs.gaussian_vectors(121 + n, nprob * nvec, n).reshape(nprob, nvec, n, n)
+    p = _fc_params(41, 0.05)
+    batch = T.TwoGridBatch(probs, nvec, 2.0 / 3.0, bf16, net_arch="fc")
+    loss, grad = batch.loss_and_grad(torch.from_numpy(p).cuda(), torch.from_numpy(z).cuda().contiguous())
+    batch.close()
+    lo, go = 0.0, np.zeros(p.size)
+    for k, (e, t) in enumerate(params):
+        st = O.const_field(n, f32(O.q1_rotated_stencil(e, t)))
+        l1, g1 = O.fc_loss_and_grad(st, f32(p), f32(z[k]), bf16=bf16)
+        lo += l1 / nprob
+        go += g1 / nprob
+    assert abs(loss.item() - lo) <= 1e-5 * lo, (loss.item(), lo)
+    g = grad.double().cpu().numpy()
+    assert np.linalg.norm(g - go) <= 1e-4 * np.linalg.norm(go), np.linalg.norm(g - go) / np.linalg.norm(go)
+
+
+def test_fc_trainer_reduces_the_loss():
+    tr = T.Trainer(sizes=(15,), per_size=8, nvec=8, lr=1e-3, net_arch="fc")
+    losses = [tr.step() for _ in range(60)]
+    assert np.mean(losses[-10:]) < 0.8 * np.mean(losses[:10]), (losses[:5], losses[-5:])
