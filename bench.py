@@ -234,12 +234,16 @@ def timed_solve(mg, b, reps: int = 1):
 
 def run_varcoef(args, rank):
     """Variable-coefficient diffusion -div(a grad u), a = exp(GRF), 5-point stencil: one
-    problem per size in args.varcoef_n solved to 1e-8 with the CNN and with Jacobi (C4)."""
+    problem per size in args.varcoef_n solved to 1e-8 with the convolutional network, the
+    fully connected network (Sec. 4.2) and Jacobi (C4)."""
+    import numpy as np
     import torch
 
     from paper_2102_12071_gb300 import inputs, solver as S
 
     wv = load_varcoef_weights()
+    fc_path = os.path.join(os.path.dirname(WEIGHTS), "fc_varcoef.npy")
+    wfc = torch.from_numpy(np.load(fc_path).astype(np.float32)).cuda() if os.path.exists(fc_path) else None
     out = {"problem": "GRF a = exp(g), unit variance, correlation length 1/16, 5-point", "rtol": RTOL}
     if wv is not None:
         out["weights"] = wv[0]
@@ -247,8 +251,11 @@ def run_varcoef(args, rank):
         cells = torch.from_numpy(inputs.grf_cells(inputs.SEED_GRF + rank, n)).cuda()
         b = torch.from_numpy(inputs.rhs_uniform(inputs.SEED_RHS + 500 + rank, n)).cuda()[None].contiguous()
         res = {}
-        for kind in ["jacobi"] + (["cnn"] if wv is not None else []):
-            mg = S.MultigridSolver([S.varcoef5(n, cells)], kind, net_params=wv[1] if kind == "cnn" else None)
+        arms = ["jacobi"] + (["cnn"] if wv is not None else []) + (["fc"] if wfc is not None else [])
+        for kind in arms:
+            net = {"cnn": wv[1] if wv is not None else None, "fc": wfc}.get(kind)
+            mg = S.MultigridSolver([S.varcoef5(n, cells)], "jacobi" if kind == "jacobi" else "cnn", net_params=net,
+                                   net_arch="fc" if kind == "fc" else "conv")
             ms, cyc, st = timed_solve(mg, b, reps=3 if n <= 2047 else 1)
             res[kind] = {"ms": ms, "cycles": int(cyc[0]), "converged": int(st) == 0,
                          "mdof_sweeps_per_s": sweeps_per_cycle(mg.sizes) * int(cyc[0]) / (ms / 1e3)}
