@@ -323,8 +323,8 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights",
-                                                   "cnn_rotated.npy"))
+    ap.add_argument("--out", default=None,
+                    help="default: weights/<cnn|fc>_<first family>.npy next to this module")
     ap.add_argument("--fp32-conv", action="store_true")
     ap.add_argument("--families", default="rotated", help="comma list of rotated,varcoef")
     ap.add_argument("--max-cycles", type=int, default=1, help="b: each step's loss spans k ~ U{1..b} cycles")
@@ -346,7 +346,7 @@ def main():
             h = at.losses[n]
             print(f"level n={n}: loss {np.mean(h[:10]):.5f} -> {np.mean(h[-10:]):.5f} ({time.time() - t0:.1f} s)",
                   flush=True)
-        out = args.out if args.out.endswith("adaptive.npy") else args.out.replace(".npy", "_adaptive.npy")
+        out = args.out or os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "cnn_rotated_adaptive.npy")
         os.makedirs(os.path.dirname(out), exist_ok=True)
         np.save(out, torch.stack([at.params[n] for n in at.sizes]).cpu().numpy().astype(np.float32))
         print("saved", out, "levels", at.sizes)
@@ -359,8 +359,10 @@ def main():
         l = tr.step()
         if s % 50 == 0 or s == args.steps - 1:
             print(f"step {s:5d} loss {l:.6f} ({time.time() - t0:.1f} s)", flush=True)
-    tr.save(args.out)
-    print("saved", args.out)
+    out = args.out or os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights",
+                                   f"{'fc' if args.fc else 'cnn'}_{tr.families[0]}.npy")
+    tr.save(out)
+    print("saved", out)
 
 
 if __name__ == "__main__":
