@@ -23,7 +23,7 @@ namespace mg {
 constexpr int FC_IN = 81, FC_H = 40, FC_OUT = 9;
 constexpr int FC_O2 = FC_H * FC_IN, FC_O3 = FC_O2 + FC_H * FC_H, FC_O4 = FC_O3 + FC_H * FC_H;
 static_assert(FC_O4 + FC_OUT * FC_H == MG_NPARAMS_FC, "layer sizes");
-constexpr int FC_THREADS = 128;
+constexpr int FC_THREADS = 64;
 // tape rows per point (structure of arrays, point index fastest): x, a1, a2, a3, dz1, dz2,
 // dz3, dout
 constexpr int TP_X = 0, TP_A1 = TP_X + FC_IN, TP_A2 = TP_A1 + FC_H, TP_A3 = TP_A2 + FC_H, TP_D1 = TP_A3 + FC_H,
@@ -44,11 +44,19 @@ __device__ __forceinline__ void fc_load_weights(const float* params, int bf16, f
   __syncthreads();
 }
 
+// Layer outputs go to per-thread columns of two shared buffers (hidden unit o of thread t
+// at [o * FC_THREADS + t], conflict-free); the outer loops over units stay rolled and only
+// the inner products are unrolled, which keeps the code (and its compile time) small.
+struct FcSmem {
+  float w[MG_NPARAMS_FC];
+  float ha[FC_H * FC_THREADS], hb[FC_H * FC_THREADS];
+};
+
 // forward of one point to `out`; with a tape, every layer input is stored as it is made
 // (rows TP_X, TP_A1, TP_A2, TP_A3 at point column pt)
-__device__ __forceinline__ void fc_point(const float* w, const float* st, const float* s, int n, int i, int j,
-                                         int bf16, float (&out)[FC_OUT], float* tape, size_t P, size_t pt) {
-  float h[FC_H];
+__device__ __forceinline__ void fc_point(FcSmem& S, const float* st, const float* s, int n, int i, int j, int bf16,
+                                         float (&out)[FC_OUT], float* tape, size_t P, size_t pt) {
+  const int t = threadIdx.x;
   {
     float x[FC_IN];
 #pragma unroll
@@ -64,43 +72,48 @@ __device__ __forceinline__ void fc_point(const float* w, const float* st, const 
 #pragma unroll
       for (int f = 0; f < FC_IN; ++f, r += P) *r = x[f];
     }
-#pragma unroll
+#pragma unroll 1
     for (int o = 0; o < FC_H; ++o) {
+      const float* w = S.w + o * FC_IN;
       float acc = 0.f;
 #pragma unroll
-      for (int f = 0; f < FC_IN; ++f) acc = fmaf(w[o * FC_IN + f], x[f], acc);
-      h[o] = fc_rnd(fc_lrelu(acc), bf16);
+      for (int f = 0; f < FC_IN; ++f) acc = fmaf(w[f], x[f], acc);
+      S.ha[o * FC_THREADS + t] = fc_rnd(fc_lrelu(acc), bf16);
     }
   }
-  if (tape) {
-    float* r = tape + TP_A1 * P + pt;
-#pragma unroll
-    for (int f = 0; f < FC_H; ++f, r += P) *r = h[f];
-  }
-#pragma unroll
-  for (int l = 0; l < 2; ++l) {
-    const float* wl = w + (l == 0 ? FC_O2 : FC_O3);
-    float g[FC_H];
-#pragma unroll
-    for (int o = 0; o < FC_H; ++o) {
-      float acc = 0.f;
-#pragma unroll
-      for (int f = 0; f < FC_H; ++f) acc = fmaf(wl[o * FC_H + f], h[f], acc);
-      g[o] = fc_rnd(fc_lrelu(acc), bf16);
-    }
-#pragma unroll
-    for (int o = 0; o < FC_H; ++o) h[o] = g[o];
+  // hidden layers 2 and 3: ha -> hb -> ha
+#pragma unroll 1
+  for (int l = 0; l < 3; ++l) {
+    const float* src = (l == 1) ? S.hb : S.ha;
     if (tape) {
-      float* r = tape + (l == 0 ? TP_A2 : TP_A3) * P + pt;
+      float* r = tape + (TP_A1 + l * FC_H) * P + pt;
+#pragma unroll 1
+      for (int f = 0; f < FC_H; ++f, r += P) *r = src[f * FC_THREADS + t];
+    }
+    if (l == 2) break;
+    float* dst = (l == 0) ? S.hb : S.ha;
+    const float* wl = S.w + (l == 0 ? FC_O2 : FC_O3);
+    float h[FC_H];
 #pragma unroll
-      for (int f = 0; f < FC_H; ++f, r += P) *r = h[f];
+    for (int f = 0; f < FC_H; ++f) h[f] = src[f * FC_THREADS + t];
+#pragma unroll 1
+    for (int o = 0; o < FC_H; ++o) {
+      const float* w = wl + o * FC_H;
+      float acc = 0.f;
+#pragma unroll
+      for (int f = 0; f < FC_H; ++f) acc = fmaf(w[f], h[f], acc);
+      dst[o * FC_THREADS + t] = fc_rnd(fc_lrelu(acc), bf16);
     }
   }
+  float h[FC_H];
+#pragma unroll
+  for (int f = 0; f < FC_H; ++f) h[f] = S.ha[f * FC_THREADS + t];
 #pragma unroll
   for (int o = 0; o < FC_OUT; ++o) {
+    const float* w = S.w + FC_O4 + o * FC_H;
     float acc = 0.f;
 #pragma unroll
-    for (int f = 0; f < FC_H; ++f) acc = fmaf(w[FC_O4 + o * FC_H + f], h[f], acc);
+    for (int f = 0; f < FC_H; ++f) acc = fmaf(w[f], h[f], acc);
     out[o] = acc;
   }
 }
@@ -109,8 +122,8 @@ __device__ __forceinline__ void fc_point(const float* w, const float* st, const 
 // uniform batch of fields
 __global__ void __launch_bounds__(FC_THREADS) k_fc_forward(const NetJob* __restrict__ jobs, NetBatch batch,
                                                            const float* __restrict__ params, float omega, int bf16) {
-  __shared__ float w[MG_NPARAMS_FC];
-  fc_load_weights(params, bf16, w);
+  __shared__ FcSmem S;
+  fc_load_weights(params, bf16, S.w);
   const float *st, *s;
   float* W;
   int n;
@@ -127,10 +140,10 @@ __global__ void __launch_bounds__(FC_THREADS) k_fc_forward(const NetJob* __restr
     n = batch.n;
   }
   const int q = blockIdx.x * FC_THREADS + threadIdx.x;
-  if (q >= n * n) return;
+  if (q >= n * n) return;  // after the only barrier
   const int i = q / n, j = q % n;
   float out[FC_OUT];
-  fc_point(w, st, s, n, i, j, bf16, out, nullptr, 0, 0);
+  fc_point(S, st, s, n, i, j, bf16, out, nullptr, 0, 0);
   const size_t nn = (size_t)n * n;
   const float d = fc_tap(st, s, n, 4, i, j);
 #pragma unroll
@@ -141,20 +154,20 @@ __global__ void __launch_bounds__(FC_THREADS) k_fc_forward(const NetJob* __restr
 __global__ void __launch_bounds__(FC_THREADS) k_fc_tape(NetBatch batch, const float* __restrict__ dW,
                                                         const float* __restrict__ params, int bf16,
                                                         float* __restrict__ tape, size_t P) {
-  __shared__ float w[MG_NPARAMS_FC];
-  fc_load_weights(params, bf16, w);
+  __shared__ FcSmem S;
+  fc_load_weights(params, bf16, S.w);
   const int n = batch.n;
   const size_t nn = (size_t)n * n;
   const float* st = batch.st + blockIdx.y * batch.stride;
   const int q = blockIdx.x * FC_THREADS + threadIdx.x;
-  if (q >= (int)nn) return;
-  const int i = q / n, j = q % n;
+  if (q >= (int)nn) return;  // after the only barrier
+  const int i = q / n, j = q % n, t = threadIdx.x;
   const size_t pt = (size_t)blockIdx.y * nn + q;  // point index of the batch
   float out[FC_OUT];
-  fc_point(w, st, nullptr, n, i, j, bf16, out, tape, P, pt);
+  fc_point(S, st, nullptr, n, i, j, bf16, out, tape, P, pt);
   const float d = st[4 * nn + q];
   const float* g = dW + blockIdx.y * batch.stride;
-  float dout[FC_OUT], dz[FC_H];
+  float dout[FC_OUT];
   {
     float* r = tape + TP_DO * P + pt;
 #pragma unroll
@@ -163,36 +176,40 @@ __global__ void __launch_bounds__(FC_THREADS) k_fc_tape(NetBatch batch, const fl
       *r = dout[k];
     }
   }
-  // errors of the hidden layers, back from layer 4; the masks (LeakyReLU slopes) come from
-  // the stored activations (this thread's own stores)
+  // errors of the hidden layers, back from layer 4, through the thread's shared columns;
+  // the masks (LeakyReLU slopes) come from the stored activations (this thread's stores)
   {
     const float* a = tape + TP_A3 * P + pt;
     float* r = tape + TP_D3 * P + pt;
-#pragma unroll
+#pragma unroll 1
     for (int f = 0; f < FC_H; ++f, a += P, r += P) {
       float acc = 0.f;
 #pragma unroll
-      for (int o = 0; o < FC_OUT; ++o) acc = fmaf(w[FC_O4 + o * FC_H + f], dout[o], acc);
-      dz[f] = *a > 0.f ? acc : 0.01f * acc;
-      *r = dz[f];
+      for (int o = 0; o < FC_OUT; ++o) acc = fmaf(S.w[FC_O4 + o * FC_H + f], dout[o], acc);
+      const float e = *a > 0.f ? acc : 0.01f * acc;
+      S.ha[f * FC_THREADS + t] = e;
+      *r = e;
     }
   }
 #pragma unroll 1
   for (int l = 0; l < 2; ++l) {
-    const float* wl = w + (l == 0 ? FC_O3 : FC_O2);
+    const float* wl = S.w + (l == 0 ? FC_O3 : FC_O2);
     const float* a = tape + (l == 0 ? TP_A2 : TP_A1) * P + pt;
     float* r = tape + (l == 0 ? TP_D2 : TP_D1) * P + pt;
+    const float* src = l == 0 ? S.ha : S.hb;
+    float* dst = l == 0 ? S.hb : S.ha;
     float e[FC_H];
 #pragma unroll
+    for (int o = 0; o < FC_H; ++o) e[o] = src[o * FC_THREADS + t];
+#pragma unroll 1
     for (int f = 0; f < FC_H; ++f, a += P, r += P) {
       float acc = 0.f;
 #pragma unroll
-      for (int o = 0; o < FC_H; ++o) acc = fmaf(wl[o * FC_H + f], dz[o], acc);
-      e[f] = *a > 0.f ? acc : 0.01f * acc;
-      *r = e[f];
+      for (int o = 0; o < FC_H; ++o) acc = fmaf(wl[o * FC_H + f], e[o], acc);
+      const float v = *a > 0.f ? acc : 0.01f * acc;
+      dst[f * FC_THREADS + t] = v;
+      *r = v;
     }
-#pragma unroll
-    for (int f = 0; f < FC_H; ++f) dz[f] = e[f];
   }
 }
 
