@@ -314,6 +314,7 @@ static size_t carve(const Plan& P, const mg_options& o, void* base, mg_ctx* ctx)
     ctx->args.xh0 = A.xh0;
     ctx->args.xl0 = A.xl0;
     ctx->args.r0a = A.r[0];
+    ctx->args.b0 = A.b0;
     ctx->args.r0b = A.r0b;
     ctx->args.xh0b = A.xh0b;
     ctx->args.xl0b = A.xl0b;

@@ -119,6 +119,7 @@ struct CycleArgs {
   float *xh0, *xl0;      // pitched iterate pair of the tiled path (read by even cycles)
   float *xh0b, *xl0b;    // the second pair (read by odd cycles, written by even ones)
   float *r0a, *r0b;      // the two level-0 residual arrays
+  const float* b0;       // pitched level-0 right-hand sides (tiled path)
   bool pdl;              // launch the cycle chain with programmatic dependencies
   int ctail;             // levels >= lstar in one CTA cluster per problem (mg_ctail.cu)
 };

@@ -45,6 +45,10 @@ constexpr int ESP = 45;
 constexpr int UP0E_H = TB + 6;   // k_up0 e box: rows R0-3 .. R0+34
 constexpr int UP0R_H = TB + 4;   // k_up0 r box: rows R0-2 .. R0+33
 constexpr int EC0_H = TB / 2 + 4; // k_up0 coarse box: rows R0/2-2 .. R0/2+17
+// Constant-stencil kernels are bounded to 8 CTAs of 256 threads per SM (32 registers): the
+// tile kernels wait ~2.5 us for each tile's copies and more resident CTAs hide more of it.
+// The per-point-field variants hold more state and would spill at that bound; their
+// bounds (6 CTAs, 4 for k_up0) give the register counts they reach without spilling.
 // a tile is "inner" when every point its kernels evaluate lies inside the grid and at
 // least MG_NET_MARGIN from the edges: no masking, interior network kernel in registers
 constexpr int INNER = 8;
@@ -172,7 +176,8 @@ __device__ __forceinline__ void dot2_sub(float a, float x, float xl, float& hi, 
 template <int SK, bool IN>
 __device__ __forceinline__ float residual_tile(const LevelDev& L, const float (&s)[9], const float* XH,
                                                const float* XL, const float* BB, int R0, int C0, float* rdst,
-                                               float* xo_hi = nullptr, float* xo_lo = nullptr) {
+                                               float* xo_hi = nullptr, float* xo_lo = nullptr,
+                                               const float* bg = nullptr) {
   constexpr int KS = TB / NW;
   const int n = L.n, pitch = L.pitch;
   const int tj = threadIdx.x & 31, t0 = (threadIdx.x >> 5) * KS, j = C0 + tj;
@@ -200,7 +205,9 @@ __device__ __forceinline__ float residual_tile(const LevelDev& L, const float (&
 #pragma unroll
         for (int q = 0; q < 9; ++q) a[q] = __ldg(ap + q * nn);
       }
-      float hi = BB[(t0 + k) * TB + tj], lo = 0.f;
+      // b: the tile in shared memory, or (bg, the problem's pitched array) one coalesced
+      // global load per point
+      float hi = bg ? __ldg(bg + g0 + (size_t)k * pitch) : BB[(t0 + k) * TB + tj], lo = 0.f;
       dot2_sub(a[0], h.a0, l.a0, hi, lo);
       dot2_sub(a[1], h.a1, l.a1, hi, lo);
       dot2_sub(a[2], h.a2, l.a2, hi, lo);
@@ -326,7 +333,7 @@ __device__ __forceinline__ void down_tile(const LevelDev& L, const float (&s)[9]
 }
 
 template <int SK, int HK>
-__global__ void __launch_bounds__(NT) k_down(const __grid_constant__ DownMaps M, const ProbDev* __restrict__ probs,
+__global__ void __launch_bounds__(NT, SK == SK_CONST ? 8 : 6) k_down(const __grid_constant__ DownMaps M, const ProbDev* __restrict__ probs,
                                              ProbState* __restrict__ state, int l, float omega,
                                              const int* __restrict__ act) {
   pdl_trigger();
@@ -458,7 +465,7 @@ __device__ __forceinline__ void up_tile(const LevelDev& L, const float (&s)[9], 
 }
 
 template <int SK, int HK, bool UPDX>
-__global__ void __launch_bounds__(NT) k_up(const __grid_constant__ UpMaps M, const ProbDev* __restrict__ probs,
+__global__ void __launch_bounds__(NT, SK == SK_CONST ? 8 : 6) k_up(const __grid_constant__ UpMaps M, const ProbDev* __restrict__ probs,
                                            ProbState* __restrict__ state, int l, float omega, float* __restrict__ xhi,
                                            float* __restrict__ xlo, const int* __restrict__ act) {
   pdl_trigger();
@@ -584,11 +591,12 @@ __device__ __forceinline__ void up0_tile(const LevelDev& L, const float (&s)[9],
 }
 
 template <int SK, int HK>
-__global__ void __launch_bounds__(NT) k_up0(const __grid_constant__ Up0Maps M, const ProbDev* __restrict__ probs,
+__global__ void __launch_bounds__(NT, SK == SK_CONST ? 8 : 4) k_up0(const __grid_constant__ Up0Maps M, const ProbDev* __restrict__ probs,
                                             ProbState* __restrict__ state, float* __restrict__ partials,
                                             int ntiles_max, float omega, float rtol, int max_cycles,
                                             float* __restrict__ xhi, float* __restrict__ xlo,
-                                            float* __restrict__ rnew, const int* __restrict__ act) {
+                                            float* __restrict__ rnew, const float* __restrict__ b0,
+                                            const int* __restrict__ act) {
   pdl_trigger();
   const int p = act ? act[blockIdx.y] : blockIdx.y;
   const LevelDev L = probs[p].lv[0];
@@ -602,34 +610,37 @@ __global__ void __launch_bounds__(NT) k_up0(const __grid_constant__ Up0Maps M, c
   __shared__ __align__(128) float ecs[EC0_H * EC_W];
   __shared__ __align__(128) float xh[RES_H * XW];   // x on the tile and its halo, updated in place
   __shared__ __align__(128) float xl[RES_H * XW];
-  __shared__ __align__(128) float bb[TB * TB];
-  __shared__ float wtab[HK == HK_TABLE ? 9 * MG_PROXY * MG_PROXY : 1];
   __shared__ __align__(8) uint64_t bar;
   const bool in = inner_tile(R0, C0, n);
   float s[9], wi[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) s[k] = (SK == SK_CONST) ? L.s[k] : 0.f;
-  if (HK == HK_TABLE) load_table(L, in, wtab, wi);
+  // Edge tiles read the class table through L1 and the residual reads b from global memory
+  // (no shared copies: 28.7 KB per CTA, 8 CTAs fit on an SM)
+  const float* wtab = L.W;
+  if (HK == HK_TABLE && in) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) wi[k] = L.W[k * L.T * L.T + MG_NET_MARGIN * L.T + MG_NET_MARGIN];
+  }
   pdl_wait();
   if (!st_active(state + p)) return;
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     fence_mbar_init();
-    mbar_arrive_expect_tx(&bar, ((UP0E_H + UP0R_H + 2 * RES_H) * XW + EC0_H * EC_W + TB * TB) * sizeof(float));
+    mbar_arrive_expect_tx(&bar, ((UP0E_H + UP0R_H + 2 * RES_H) * XW + EC0_H * EC_W) * sizeof(float));
     tma_load_3d(es, &M.e, &bar, C0 - 4, R0 - 3, p);
     tma_load_3d(rs, &M.r, &bar, C0 - 4, R0 - 2, p);
     tma_load_3d(ecs, &M.ec, &bar, C0 / 2 - 4, R0 / 2 - 2, p);
     tma_load_3d(xh, &M.x.xh, &bar, C0 - 4, R0 - 1, p);
     tma_load_3d(xl, &M.x.xl, &bar, C0 - 4, R0 - 1, p);
-    tma_load_3d(bb, &M.x.b, &bar, C0, R0, p);
   }
   __syncthreads();
   if (!tile_wait(&bar, state[p])) return;
   if (in) up0_tile<SK, HK, true>(L, s, wtab, wi, omega, es, rs, ecs, xh, xl, R0, C0);
   else up0_tile<SK, HK, false>(L, s, wtab, wi, omega, es, rs, ecs, xh, xl, R0, C0);
   const size_t po = (size_t)p * n * L.pitch;
-  const float acc = in ? residual_tile<SK, true>(L, s, xh, xl, bb, R0, C0, rnew + po, xhi + po, xlo + po)
-                       : residual_tile<SK, false>(L, s, xh, xl, bb, R0, C0, rnew + po, xhi + po, xlo + po);
+  const float acc = in ? residual_tile<SK, true>(L, s, xh, xl, nullptr, R0, C0, rnew + po, xhi + po, xlo + po, b0 + po)
+                       : residual_tile<SK, false>(L, s, xh, xl, nullptr, R0, C0, rnew + po, xhi + po, xlo + po, b0 + po);
   float rhi, rlo;
   if (block_partial_and_last<NT>(acc, partials + (size_t)p * ntiles_max, &state[p].counter, ntiles, tile, rhi, rlo)) {
     if (threadIdx.x == 0) decide(state[p], rhi, rlo, rtol, max_cycles);
@@ -786,7 +797,7 @@ cudaError_t launch_cycle(const CycleArgs& a, float rtol, int max_cycles, int par
       float* xln = parity ? a.xl0 : a.xl0b;
       MG_DISPATCH(a.sk, a.hk,
                   (e = launch_pdl(pdl, k_up0<SK_, HK_>, grid, dim3(NT), 0, a.stream, um, probs, a.state, a.partials,
-                                  a.ntiles_max, a.omega, rtol, max_cycles, xhn, xln, rnew, a.active)));
+                                  a.ntiles_max, a.omega, rtol, max_cycles, xhn, xln, rnew, a.b0, a.active)));
     }
     else
       MG_DISPATCH(a.sk, a.hk,
