@@ -40,7 +40,7 @@ WEIGHTS = os.path.join(ROOT, "paper_2102_12071_gb300", "weights", "cnn_rotated.n
 BYTES_PER_DOF = {0: 16.0, 1: 9.0, 2: 33.0}
 # dram bytes (read + write) per launch of the current kernel versions from one ncu capture
 # of the 16 x 1023^2 batch; None where the kernel changed since its last capture
-NCU_TRAFFIC = {1: 67.15e6 + 41.10e6, 2: None}
+NCU_TRAFFIC = {1: 67.15e6 + 41.10e6, 2: 353.70e6 + 175.88e6}
 KERNEL_NAMES = {0: "k_residual (initial iterate)", 1: "k_down(level 0)", 2: "k_up0(level 0: up-sweep, x update, residual)",
                 3: "k_tail", 4: "k_down(l>=1)", 5: "k_up(l>=1)"}
 
