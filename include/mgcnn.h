@@ -105,8 +105,9 @@ typedef struct {
                            net_params holds k parameter sets and level l uses set
                            min(l, k - 1) (per-level smoothers H^(l), Algorithm 2)        */
   int smoother_transpose; /* 1: every level smooths with H^T instead of H (per-point
-                           problems only), so a V-cycle of this context applies M^T when
-                           the context without it applies M: the adjoint coarse solve of
+                           problems, or MG_NET_LINEAR: the chain reversed with mirrored
+                           kernels), so a V-cycle of this context applies M^T when the
+                           context without it applies M: the adjoint coarse solve of
                            mg_train_step_coarse                                          */
   int net_arch;         /* MG_SMOOTH_CNN: mg_net_arch; parameter sets hold
                            mg_net_param_count(net_arch) floats                           */
@@ -114,9 +115,17 @@ typedef struct {
 
 typedef enum {
   MG_NET_CONV = 0, /* 3x3 convolutions 9->7->5->3 and a 27->9 layer (Sec. 4.2, 1 260 params) */
-  MG_NET_FC = 1    /* fully connected 81->40->40->40->9 on the 3x3 neighbourhood's stencils
+  MG_NET_FC = 1,   /* fully connected 81->40->40->40->9 on the 3x3 neighbourhood's stencils
                       (Sec. 4.2 parameterisation with fully connected layers, Sec. 6.2:
                       6 800 params)                                                      */
+  MG_NET_LINEAR = 2 /* the shared-kernel linear smoother of Sec. 6 (eq.
+                      full-coarsening-smoother): H = f5(f4(f3(f2(f1(.))))) + f6, each f_k a
+                      3x3 convolution (tap layout above) whose input is zero outside the
+                      grid, the same six kernels at every point of every problem of a
+                      context.  A parameter set is float[6][9] = (f1 .. f5, f6), 54 params;
+                      the network has no input: its weights are the smoother.  Weighted
+                      Jacobi is f1..f4 = identity (tap 4 = 1), f5 = 0, f6 = omega/D at tap 4.
+                      Any stencil kind.                                                  */
 } mg_net_arch;
 
 typedef struct mg_ctx mg_ctx;
@@ -134,8 +143,9 @@ size_t mg_workspace_size(const mg_problem* problems, int nprob, const mg_options
    (Sec. 2.2) with full coarsening and bilinear P (Sec. 6.1, Fig. full_coarsening) down to
    coarsest_n, the FP64 inverse of the coarsest operator, and -- for
    MG_SMOOTH_CNN -- the per-point smoothing kernels of every smoothed level from the
-   network with parameters net_params (DEVICE float[mg_net_nparams()], read during this
-   call only; NULL for Jacobi).  workspace: DEVICE, >= mg_workspace_size bytes, 256-byte
+   network with parameters net_params (DEVICE, max(1, net_levels) sets of
+   mg_net_param_count(net_arch) floats, read during this call only; NULL for Jacobi;
+   MG_NET_LINEAR copies its sets as the levels' smoothers).  workspace: DEVICE, >= mg_workspace_size bytes, 256-byte
    aligned, owned by the caller and used exclusively by this context until mg_destroy.
    On success *out receives a host handle. */
 mg_status mg_setup(const mg_problem* problems, int nprob, const mg_options* opts,
@@ -152,7 +162,8 @@ int mg_level_n(const mg_ctx* ctx, int level);  /* side of level `level`, 0 if in
 mg_status mg_get_stencil(const mg_ctx* ctx, int prob, int level, float* out, void* stream);
 
 /* Copies the per-point smoothing kernels H of (prob, level) to out (DEVICE
-   float[9*n_l*n_l]), expanded to one 3x3 kernel per point (Jacobi: omega/D at tap 4). */
+   float[9*n_l*n_l]), expanded to one 3x3 kernel per point (Jacobi: omega/D at tap 4).
+   MG_NET_LINEAR has no such kernels: MG_ERR_UNSUPPORTED. */
 mg_status mg_get_kernels(const mg_ctx* ctx, int prob, int level, float* out, void* stream);
 
 /* Weighted-Jacobi or CNN smoothing on one level of one problem (eq. iteration):

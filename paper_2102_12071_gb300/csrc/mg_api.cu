@@ -65,7 +65,8 @@ mg_status make_plan(const mg_problem* probs, int nprob, const mg_options* o, Pla
   if (o->coarsest_n != 3 && o->coarsest_n != 7) return fail(MG_ERR_UNSUPPORTED, "coarsest_n must be 3 or 7");
   if (!(o->omega > 0.f) || !(o->omega < 2.f)) return fail(MG_ERR_INVALID_ARG, "omega must be in (0, 2)");
   if (o->net_levels < 0 || o->net_levels > MG_MAXL) return fail(MG_ERR_INVALID_ARG, "net_levels out of range");
-  if (o->net_arch != MG_NET_CONV && o->net_arch != MG_NET_FC) return fail(MG_ERR_INVALID_ARG, "unknown net_arch");
+  if (o->net_arch != MG_NET_CONV && o->net_arch != MG_NET_FC && o->net_arch != MG_NET_LINEAR)
+    return fail(MG_ERR_INVALID_ARG, "unknown net_arch");
   const int n = probs[0].n;
   if (!is_pow2m1(n) || n < o->coarsest_n || n > 8191)
     return fail(MG_ERR_INVALID_ARG, "n = %d must be 2^m - 1 in [coarsest_n, 8191]", n);
@@ -95,7 +96,9 @@ mg_status make_plan(const mg_problem* probs, int nprob, const mg_options* o, Pla
   P.nprob = nprob;
   P.n0 = n;
   P.sk = nconst ? SK_CONST : SK_FIELD;
-  P.hk = o->smoother == MG_SMOOTH_JACOBI ? HK_JACOBI : (P.sk == SK_CONST ? HK_TABLE : HK_FIELD);
+  P.hk = o->smoother == MG_SMOOTH_JACOBI ? HK_JACOBI
+         : o->net_arch == MG_NET_LINEAR  ? HK_LINEAR
+                                         : (P.sk == SK_CONST ? HK_TABLE : HK_FIELD);
   if (o->smoother_transpose && P.hk == HK_TABLE)
     return fail(MG_ERR_UNSUPPORTED, "smoother_transpose needs per-point problems (kinds VARCOEF5, FIELD)");
   int m = n, L = 0;
@@ -114,7 +117,7 @@ mg_status make_plan(const mg_problem* probs, int nprob, const mg_options* o, Pla
   P.ntiles_max = nt * nt;
   if (tail_smem_bytes(P.nl, P.lstar, L, P.hk) > MG_TAIL_SMEM_MAX)
     return fail(MG_ERR_UNSUPPORTED, "tail does not fit in shared memory");
-  if (!P.tail_solve && o->cluster_tail) {
+  if (!P.tail_solve && o->cluster_tail && P.hk != HK_LINEAR) {
     int ls = 1;  // the finest level stays tiled: it carries the outer residual and update
     while (ls < L && P.nl[ls] > MG_CT_N) ++ls;
     if (ls < L && P.nl[ls] > MG_CT_SOLO && ctail_smem_bytes(P.nl, ls, L, P.hk) <= MG_CT_SMEM_MAX) {
@@ -151,6 +154,7 @@ struct mg_ctx {
   NetJob* d_jobs = nullptr;
   int* d_active = nullptr;      // compacted list of problems still iterating
   float* tscratch = nullptr;    // kernel transposition scratch (smoother_transpose)
+  float* lin = nullptr;         // the linear smoother's weights, [L-1][MG_NPARAMS_LIN]
   std::vector<int> h_active;
   LevelArrays arrays;
   TileMaps maps;
@@ -261,6 +265,12 @@ static size_t carve(const Plan& P, const mg_options& o, void* base, mg_ctx* ctx)
   NetJob* jobs = c.take<NetJob>((size_t)P.nprob * P.L);
   // scratch for the transposition of one problem's level-0 kernels (smoother_transpose)
   float* tscr = (o.smoother_transpose && P.hk == HK_FIELD) ? c.take<float>((size_t)9 * P.n0 * P.n0) : nullptr;
+  // the linear smoother: its weights per level (shared by all problems) and three scratch
+  // vectors of level-0 size for the chain and the up-sweep residual
+  float* lin = P.hk == HK_LINEAR ? c.take<float>((size_t)MG_NPARAMS_LIN * (P.L > 1 ? P.L - 1 : 1)) : nullptr;
+  float* lin_s[3] = {nullptr, nullptr, nullptr};
+  if (P.hk == HK_LINEAR)
+    for (int k = 0; k < 3; ++k) lin_s[k] = c.take<float>((size_t)P.nprob * P.n0 * pitch_of(P.n0));
   LevelArrays A;
   memset(&A, 0, sizeof(A));
   for (int l = 0; l < P.L; ++l) {
@@ -300,6 +310,7 @@ static size_t carve(const Plan& P, const mg_options& o, void* base, mg_ctx* ctx)
       if (l < P.L - 1) {
         if (P.hk == HK_FIELD) v.W = c.take<float>(9 * nn);
         else if (P.hk == HK_TABLE) v.W = c.take<float>((size_t)9 * v.T * v.T);
+        else if (P.hk == HK_LINEAR) v.W = lin + (size_t)MG_NPARAMS_LIN * l;
       }
     }
     d.m = P.nl[P.L - 1] * P.nl[P.L - 1];
@@ -324,6 +335,11 @@ static size_t carve(const Plan& P, const mg_options& o, void* base, mg_ctx* ctx)
     ctx->d_jobs = jobs;
     ctx->d_active = active;
     ctx->tscratch = tscr;
+    ctx->lin = lin;
+    ctx->args.lin_wa = lin_s[0];
+    ctx->args.lin_wb = lin_s[1];
+    ctx->args.lin_t = lin_s[2];
+    for (int l = 0; l < MG_MAXL; ++l) ctx->args.lin_phi[l] = (lin && l + 1 < P.L) ? lin + (size_t)MG_NPARAMS_LIN * l : nullptr;
   }
   return c.off + 256;
 }
@@ -356,7 +372,9 @@ size_t mg_workspace_size(const mg_problem* problems, int nprob, const mg_options
 
 int mg_net_nparams(void) { return MG_NPARAMS; }
 
-int mg_net_param_count(int arch) { return arch == MG_NET_CONV ? MG_NPARAMS : arch == MG_NET_FC ? MG_NPARAMS_FC : 0; }
+int mg_net_param_count(int arch) {
+  return arch == MG_NET_CONV ? MG_NPARAMS : arch == MG_NET_FC ? MG_NPARAMS_FC : arch == MG_NET_LINEAR ? MG_NPARAMS_LIN : 0;
+}
 
 mg_status mg_setup(const mg_problem* problems, int nprob, const mg_options* opts, const float* net_params,
                    void* workspace, size_t ws_bytes, void* stream, mg_ctx** out) {
@@ -395,6 +413,7 @@ mg_status mg_setup(const mg_problem* problems, int nprob, const mg_options* opts
   a.nactive = 0;
   a.pdl = false;
   a.maps = &ctx->maps;
+  a.arrays = &ctx->arrays;
   // pinned, so that the per-chunk read of the control blocks is asynchronous and several
   // contexts can keep their streams busy at once
   if (cudaMallocHost((void**)&ctx->h_state, sizeof(ProbState) * P.nprob) != cudaSuccess) {
@@ -437,7 +456,15 @@ mg_status mg_setup(const mg_problem* problems, int nprob, const mg_options* opts
       CK(launch_rap_const(a.probs, P.nprob, P.L, s));
     }
     CK(launch_coarsest_factor(a.probs, P.nprob, P.L, P.sk, ctx->d_fail, s));
-    if (P.hk != HK_JACOBI && P.L > 1) {
+    if (P.hk == HK_LINEAR && P.L > 1) {
+      // the network is the chain itself: level l takes parameter set min(l, net_levels - 1)
+      for (int l = 0; l + 1 < P.L; ++l) {
+        const int set = opts->net_levels <= 1 ? 0 : (l < opts->net_levels ? l : opts->net_levels - 1);
+        CK(cudaMemcpyAsync(ctx->lin + (size_t)MG_NPARAMS_LIN * l, net_params + (size_t)set * MG_NPARAMS_LIN,
+                           MG_NPARAMS_LIN * sizeof(float), cudaMemcpyDeviceToDevice, s));
+      }
+      if (opts->smoother_transpose) CK(launch_transpose_linear(ctx->lin, P.L - 1, s));
+    } else if (P.hk != HK_JACOBI && P.L > 1) {
       // jobs level-major, so that every level can take its own parameter set
       std::vector<NetJob> jobs;
       std::vector<int> first(P.L, 0), nmax(P.L, 0);
@@ -512,6 +539,8 @@ mg_status mg_get_stencil(const mg_ctx* ctx, int prob, int level, float* out, voi
 mg_status mg_get_kernels(const mg_ctx* ctx, int prob, int level, float* out, void* stream) {
   if (!ctx || !out || prob < 0 || prob >= ctx->plan.nprob || level < 0 || level >= ctx->plan.L - 1)
     return fail(MG_ERR_INVALID_ARG, "mg_get_kernels: bad arguments (smoothed levels are 0..L-2)");
+  if (ctx->plan.hk == HK_LINEAR)
+    return fail(MG_ERR_UNSUPPORTED, "mg_get_kernels: the linear smoother is a chain of convolutions, not one 3x3 kernel per point");
   CK(launch_expand_kernels(ctx->args.probs, prob, level, ctx->plan.nl[level], ctx->plan.sk, ctx->plan.hk,
                            ctx->opts.omega, out, (cudaStream_t)stream));
   return MG_OK;

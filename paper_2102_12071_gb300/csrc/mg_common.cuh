@@ -24,9 +24,12 @@
 #define MG_PROXY (2 * MG_NET_MARGIN + 1)  // proxy grid side for constant-stencil inference
 #define MG_NPARAMS 1260
 #define MG_NPARAMS_FC 6800  // the fully connected network, 81 -> 40 -> 40 -> 40 -> 9
+#define MG_NPARAMS_LIN 54   // the shared-kernel linear smoother of one level: six 3x3 kernels
 
 enum { SK_CONST = 0, SK_FIELD = 1 };                 // stencil storage
-enum { HK_JACOBI = 0, HK_TABLE = 1, HK_FIELD = 2 };  // smoother storage
+// smoother storage: omega/D; per-point kernels of a constant stencil by boundary class;
+// per-point kernels of every point; the shared-kernel linear chain (MG_NPARAMS_LIN per level)
+enum { HK_JACOBI = 0, HK_TABLE = 1, HK_FIELD = 2, HK_LINEAR = 3 };
 
 struct LevelDev {
   int n;
@@ -34,7 +37,7 @@ struct LevelDev {
   float* r;            // residual / right-hand side of the error equation, [n][pitch]
   float* e;            // correction on this level, [n][pitch]
   float* st;           // SK_FIELD: stencil field [9][n][n]
-  float* W;            // HK_TABLE: [9][T][T]; HK_FIELD: [9][n][n]
+  float* W;            // HK_TABLE: [9][T][T]; HK_FIELD: [9][n][n]; HK_LINEAR: [6][9], shared
   float s[9];          // SK_CONST: stencil of this level (Galerkin product of the finer one)
   int pitch;           // row pitch of r, e and f in floats (multiple of 32: 128-byte rows)
   float* f;            // final correction written by the up-sweep of a tiled level >= 1 (its
@@ -47,6 +50,18 @@ struct LevelDev {
     else if ((SKv) == SK_CONST && (HKv) == HK_TABLE) { constexpr int SK_ = SK_CONST, HK_ = HK_TABLE; CALL; } \
     else if ((SKv) == SK_FIELD && (HKv) == HK_JACOBI) { constexpr int SK_ = SK_FIELD, HK_ = HK_JACOBI; CALL; } \
     else { constexpr int SK_ = SK_FIELD, HK_ = HK_FIELD; CALL; }                                           \
+  } while (0)
+
+// MG_DISPATCH plus the linear smoother: for the kernels that run every smoother kind (the
+// one-CTA coarse tail); the tiled and cluster kernels never see HK_LINEAR
+#define MG_DISPATCH_T(SKv, HKv, CALL)                                                   \
+  do {                                                                                  \
+    if ((HKv) == HK_LINEAR) {                                                           \
+      if ((SKv) == SK_CONST) { constexpr int SK_ = SK_CONST, HK_ = HK_LINEAR; CALL; }   \
+      else { constexpr int SK_ = SK_FIELD, HK_ = HK_LINEAR; CALL; }                     \
+    } else {                                                                            \
+      MG_DISPATCH(SKv, HKv, CALL);                                                      \
+    }                                                                                   \
   } while (0)
 
 struct ProbDev {
@@ -90,6 +105,17 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 __device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
   e = __fsub_rn(b, __fsub_rn(s, a));
+}
+// hi + lo -= a (x + xl): one tap of the compensated residual r = b - A x, x = x_hi + x_lo
+// (Dot2: exact product and error-free sum for x_hi, plain FP32 for the x_lo term)
+__device__ __forceinline__ void dot2_sub(float a, float x, float xl, float& hi, float& lo) {
+  const float pr = __fmul_rn(a, x);
+  const float pe = fmaf(a, x, -pr);
+  float sum, err;
+  two_sum(hi, -pr, sum, err);
+  hi = sum;
+  lo += err - pe;
+  lo = fmaf(-a, xl, lo);
 }
 __device__ __forceinline__ void ff_add(float& hi, float& lo, float bhi, float blo) {
   float s, e;

@@ -281,7 +281,7 @@ cudaError_t prepare_tail(const CycleArgs& a) {
   if (a.ctail) return prepare_ctail(a);
   const size_t smem = tail_smem_bytes(a.nl, a.lstar, a.L, a.hk);
   cudaError_t e;
-  MG_DISPATCH(a.sk, a.hk, (e = set_tail_attrs<SK_, HK_>(smem)));
+  MG_DISPATCH_T(a.sk, a.hk, (e = set_tail_attrs<SK_, HK_>(smem)));
   return e;
 }
 
@@ -290,13 +290,13 @@ cudaError_t launch_tail(const CycleArgs& a) {
   const int ls = a.lstar, L = a.L;
   const size_t smem = tail_smem_bytes(a.nl, ls, L, a.hk);
   cudaError_t e;
-  MG_DISPATCH(a.sk, a.hk, (e = set_tail_attrs<SK_, HK_>(smem)));
+  MG_DISPATCH_T(a.sk, a.hk, (e = set_tail_attrs<SK_, HK_>(smem)));
   if (e != cudaSuccess) return e;
   a.prof->launches++;
   a.prof->begin(PK_TAIL, a.stream);
   const ProbDev* probs = a.probs;
   const ProbState* state = a.state;
-  MG_DISPATCH(a.sk, a.hk, (e = launch_pdl(a.pdl, k_tail<SK_, HK_>, dim3(nlaunch(a)), dim3(TAIL_THREADS), smem,
+  MG_DISPATCH_T(a.sk, a.hk, (e = launch_pdl(a.pdl, k_tail<SK_, HK_>, dim3(nlaunch(a)), dim3(TAIL_THREADS), smem,
                                           a.stream, probs, state, ls, L, a.omega, a.active)));
   a.prof->end(a.stream);
   return e;
@@ -306,11 +306,11 @@ cudaError_t launch_tail_solve(const CycleArgs& a, const float* b, float* xhi, fl
                               int budget, int final_residual) {
   const size_t smem = tail_smem_bytes(a.nl, 0, a.L, a.hk);
   cudaError_t e;
-  MG_DISPATCH(a.sk, a.hk, (e = set_tail_attrs<SK_, HK_>(smem)));
+  MG_DISPATCH_T(a.sk, a.hk, (e = set_tail_attrs<SK_, HK_>(smem)));
   if (e != cudaSuccess) return e;
   a.prof->launches++;
   a.prof->begin(PK_TAIL, a.stream);
-  MG_DISPATCH(a.sk, a.hk, (k_tail_solve<SK_, HK_><<<nlaunch(a), TAIL_THREADS, smem, a.stream>>>(
+  MG_DISPATCH_T(a.sk, a.hk, (k_tail_solve<SK_, HK_><<<nlaunch(a), TAIL_THREADS, smem, a.stream>>>(
                               a.probs, a.state, a.L, a.omega, b, xhi, xlo, rtol, max_cycles, budget, final_residual,
                               a.active)));
   a.prof->end(a.stream);
@@ -353,9 +353,9 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_vec(const ProbDev* __rest
 cudaError_t launch_tail_vec(const CycleArgs& a, const float* rin, float* xout, int nvec) {
   const size_t smem = tail_smem_bytes(a.nl, 0, a.L, a.hk);
   cudaError_t e;
-  MG_DISPATCH(a.sk, a.hk, (e = set_tail_attrs<SK_, HK_>(smem)));
+  MG_DISPATCH_T(a.sk, a.hk, (e = set_tail_attrs<SK_, HK_>(smem)));
   if (e != cudaSuccess) return e;
-  MG_DISPATCH(a.sk, a.hk, (k_tail_vec<SK_, HK_><<<a.nprob * nvec, TAIL_THREADS, smem, a.stream>>>(
+  MG_DISPATCH_T(a.sk, a.hk, (k_tail_vec<SK_, HK_><<<a.nprob * nvec, TAIL_THREADS, smem, a.stream>>>(
                               a.probs, a.L, a.omega, rin, xout, nvec)));
   return cudaGetLastError();
 }
@@ -377,13 +377,23 @@ cudaError_t launch_transpose_kernels(float* W, int n, float* scratch, cudaStream
   return cudaMemcpyAsync(W, scratch, sizeof(float) * cnt, cudaMemcpyDeviceToDevice, s);
 }
 
+cudaError_t launch_level_residual(const CycleArgs& a, int p, int l, const float* f, const float* u) {
+  const int n = a.nl[l];
+  const int nb = (n * n + 255) / 256;
+  a.prof->launches++;
+  if (a.sk == SK_CONST) k_level_residual<SK_CONST><<<nb, 256, 0, a.stream>>>(a.probs, p, l, f, u);
+  else k_level_residual<SK_FIELD><<<nb, 256, 0, a.stream>>>(a.probs, p, l, f, u);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_smoother(const CycleArgs& a, int p, int l, const float* f, float* u, int nsteps) {
+  if (a.hk == HK_LINEAR) return launch_smoother_linear(a, p, l, f, u, nsteps);
   const int n = a.nl[l];
   const int nb = (n * n + 255) / 256;
   for (int s = 0; s < nsteps; ++s) {
-    a.prof->launches += 2;
-    if (a.sk == SK_CONST) k_level_residual<SK_CONST><<<nb, 256, 0, a.stream>>>(a.probs, p, l, f, u);
-    else k_level_residual<SK_FIELD><<<nb, 256, 0, a.stream>>>(a.probs, p, l, f, u);
+    cudaError_t e = launch_level_residual(a, p, l, f, u);
+    if (e != cudaSuccess) return e;
+    a.prof->launches++;
     MG_DISPATCH(a.sk, a.hk, (k_level_smooth<SK_, HK_><<<nb, 256, 0, a.stream>>>(a.probs, p, l, a.omega, u)));
   }
   return cudaGetLastError();

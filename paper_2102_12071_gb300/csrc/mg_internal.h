@@ -122,6 +122,11 @@ struct CycleArgs {
   const float* b0;       // pitched level-0 right-hand sides (tiled path)
   bool pdl;              // launch the cycle chain with programmatic dependencies
   int ctail;             // levels >= lstar in one CTA cluster per problem (mg_ctail.cu)
+  // HK_LINEAR: scratch vectors of the chain of convolutions and the up-sweep residual,
+  // each [nprob][n_l][pitch_l] on the level being processed (sized for level 0)
+  float *lin_wa, *lin_wb, *lin_t;
+  const float* lin_phi[MG_MAXL];  // HK_LINEAR: the 54 weights of each smoothed level
+  const LevelArrays* arrays;      // base pointers of the level arrays (host copy)
 };
 
 // one network evaluation: a stencil field (st) or a constant stencil (s) on an n x n grid
@@ -196,6 +201,14 @@ bool ctail_supported(int sk, int hk, size_t smem);
 cudaError_t prepare_ctail(const CycleArgs& a);
 cudaError_t launch_ctail(const CycleArgs& a);
 cudaError_t launch_smoother(const CycleArgs& a, int p, int l, const float* f, float* u, int nsteps);
+// t = f - A u of problem p on level l into the level's r vector (dense n_l x n_l)
+cudaError_t launch_level_residual(const CycleArgs& a, int p, int l, const float* f, const float* u);
+// the shared-kernel linear smoother (mg_linear.cu): the cycle's levels above a.lstar with
+// plain batched kernels, then the one-CTA tail; and the standalone smoother
+cudaError_t launch_cycle_linear(const CycleArgs& a, float rtol, int max_cycles, int parity);
+cudaError_t launch_smoother_linear(const CycleArgs& a, int p, int l, const float* f, float* u, int nsteps);
+// phi <- the parameters of H^T (chain reversed, kernels mirrored), nlev sets in place
+cudaError_t launch_transpose_linear(float* phi, int nlev, cudaStream_t s);
 
 cudaError_t launch_varcoef5(int n, int nprob, const float* cells, size_t cells_stride, float* field,
                             size_t field_stride, cudaStream_t s);

@@ -14,6 +14,7 @@ struct TailLayout {
   int n[MG_MAXL];  // level sides
   int off_r[MG_MAXL], off_e[MG_MAXL], off_t[MG_MAXL], off_w[MG_MAXL];
   int off_inv;     // FP64 inverse of the coarsest operator (8-byte aligned)
+  int off_s1, off_s2;  // HK_LINEAR: two ring-padded scratch arrays of the first level's size
   int total;       // floats
 };
 
@@ -25,7 +26,16 @@ __host__ __device__ inline void tail_layout_tables(const int* nl, int l0, int L,
     if (hk == HK_TABLE && l < L - 1) {
       const int T = nl[l] < MG_PROXY ? nl[l] : MG_PROXY;
       o += 9 * T * T;
+    } else if (hk == HK_LINEAR && l < L - 1) {
+      o += MG_NPARAMS_LIN;
     }
+  }
+  t.off_s1 = t.off_s2 = -1;
+  if (hk == HK_LINEAR) {
+    const int mm = (nl[l0] + 2) * (nl[l0] + 2);
+    t.off_s1 = o;
+    t.off_s2 = o + mm;
+    o += 2 * mm;
   }
   o = (o + 1) & ~1;
   t.off_inv = o;
@@ -114,6 +124,48 @@ __device__ __forceinline__ float pad_H(const LevelDev& L, const float* s, const 
   for (int i = warp; i < (nside); i += nwarps) \
     for (int j = lane; j < (nside); j += 32)
 
+// sum_t w[t] c[d_t] on a ring-padded array of row stride m, centre tap first (dot9's order)
+__device__ __forceinline__ float conv9(const float* w, const float* c, int m) {
+  float acc = w[4] * c[0];
+  acc = fmaf(w[0], c[-m - 1], acc);
+  acc = fmaf(w[1], c[-m], acc);
+  acc = fmaf(w[2], c[-m + 1], acc);
+  acc = fmaf(w[3], c[-1], acc);
+  acc = fmaf(w[5], c[1], acc);
+  acc = fmaf(w[6], c[m - 1], acc);
+  acc = fmaf(w[7], c[m], acc);
+  acc = fmaf(w[8], c[m + 1], acc);
+  return acc;
+}
+
+// The shared-kernel linear smoother (Sec. 6, eq. full-coarsening-smoother) on one level of
+// side n held ring-padded (stride m = n + 2, zero ring): w_k = f_k(w_{k-1}) for k = 1..4
+// from w_0 = u, ping-ponging between s1 and s2 (each pass also writes the zero ring, so the
+// scratch serves every level size), then dst (=, or += with acc) f_5(w_4) + f_6(u) on the
+// interior.  phi: the level's 54 weights (f_1 .. f_5, f_6).  Barriers between the passes;
+// the caller synchronises after the last one.
+__device__ inline void tail_linear_H(const float* phi, const float* u, float* dst, bool acc, float* s1, float* s2, int n,
+                              int m) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const float* src = u;
+  for (int k = 0; k < 4; ++k) {
+    float* out = (k & 1) ? s2 : s1;
+    const float* w = phi + 9 * k;
+    for (int i = warp - 1; i <= n; i += nwarps)
+      for (int j = lane - 1; j <= n; j += 32) {
+        const int q = (i + 1) * m + j + 1;
+        out[q] = (i >= 0 && i < n && j >= 0 && j < n) ? conv9(w, src + q, m) : 0.f;
+      }
+    __syncthreads();
+    src = out;
+  }
+  TAIL_FOR(n) {
+    const int q = (i + 1) * m + j + 1;
+    const float h = conv9(phi + 36, src + q, m) + conv9(phi + 45, u + q, m);
+    dst[q] = acc ? dst[q] + h : h;
+  }
+}
+
 // Down and up sweeps from level l0 with r_{l0} already in shared memory; leaves e_{l0}.
 // The coarsest level is one FP64 product with the precomputed inverse of A_L.
 template <int SK, int HK>
@@ -127,9 +179,13 @@ __device__ void tail_cycle(const ProbDev& P, float* sm, const TailLayout& lay, c
     float* e = sm + lay.off_e[l];
     float* t = sm + lay.off_t[l];
     const float* w = sm + lay.off_w[l];
-    TAIL_FOR(n) {
-      const int q = (i + 1) * m + j + 1;
-      e[q] = pad_H<SK, HK>(Lv, sc[l], w, wi[l], omega, r + q, m, n, i, j);
+    if (HK == HK_LINEAR) {
+      tail_linear_H(w, r, e, false, sm + lay.off_s1, sm + lay.off_s2, n, m);
+    } else {
+      TAIL_FOR(n) {
+        const int q = (i + 1) * m + j + 1;
+        e[q] = pad_H<SK, HK>(Lv, sc[l], w, wi[l], omega, r + q, m, n, i, j);
+      }
     }
     __syncthreads();
     TAIL_FOR(n) {
@@ -169,9 +225,13 @@ __device__ void tail_cycle(const ProbDev& P, float* sm, const TailLayout& lay, c
       t[q] = r[q] - pad_A<SK>(Lv, sc[l], e + q, m, n, i, j);
     }
     __syncthreads();
-    TAIL_FOR(n) {
-      const int q = (i + 1) * m + j + 1;
-      e[q] += pad_H<SK, HK>(Lv, sc[l], w, wi[l], omega, t + q, m, n, i, j);
+    if (HK == HK_LINEAR) {
+      tail_linear_H(w, t, e, true, sm + lay.off_s1, sm + lay.off_s2, n, m);
+    } else {
+      TAIL_FOR(n) {
+        const int q = (i + 1) * m + j + 1;
+        e[q] += pad_H<SK, HK>(Lv, sc[l], w, wi[l], omega, t + q, m, n, i, j);
+      }
     }
     __syncthreads();
   }
@@ -187,7 +247,8 @@ __device__ void load_level_data(const ProbDev& P, float* sm, const TailLayout& l
   const int nq = L - l0;  // entries: the tables of levels l0 .. L-2, then the inverse
   if ((int)threadIdx.x < nq) {
     const int q = threadIdx.x, l = l0 + q;
-    src[q] = q < nq - 1 ? (HK == HK_TABLE ? P.lv[l].W : nullptr) : reinterpret_cast<const float*>(P.chol);
+    src[q] = q < nq - 1 ? ((HK == HK_TABLE || HK == HK_LINEAR) ? P.lv[l].W : nullptr)
+                        : reinterpret_cast<const float*>(P.chol);
     dst[q] = q < nq - 1 ? lay.off_w[l] : lay.off_inv;
   }
   if (SK == SK_CONST && (int)threadIdx.x < 9 * nq) sc[l0 + threadIdx.x / 9][threadIdx.x % 9] = P.lv[l0 + threadIdx.x / 9].s[threadIdx.x % 9];
@@ -200,6 +261,8 @@ __device__ void load_level_data(const ProbDev& P, float* sm, const TailLayout& l
         if (HK == HK_TABLE) {
           const int T = lay.n[l] < MG_PROXY ? lay.n[l] : MG_PROXY;
           o += 9 * T * T;
+        } else if (HK == HK_LINEAR) {
+          o += MG_NPARAMS_LIN;
         }
       } else {
         const int mm = lay.n[L - 1] * lay.n[L - 1];

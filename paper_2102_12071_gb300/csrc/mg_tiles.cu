@@ -156,18 +156,6 @@ __device__ __forceinline__ bool tile_wait(uint64_t* bar, ProbState& st) {
 
 __device__ __forceinline__ bool inside(int i, int j, int n) { return (unsigned)i < (unsigned)n && (unsigned)j < (unsigned)n; }
 
-// r - A x with x = xh + xl (Dot2: exact products and error-free sums for xh, plain FP32
-// for the xl terms), taps in the order of dot9's index k
-__device__ __forceinline__ void dot2_sub(float a, float x, float xl, float& hi, float& lo) {
-  const float pr = __fmul_rn(a, x);
-  const float pe = fmaf(a, x, -pr);
-  float sum, err;
-  two_sum(hi, -pr, sum, err);
-  hi = sum;
-  lo += err - pe;
-  lo = fmaf(-a, xl, lo);
-}
-
 // ------------------------------------------------------------------ k_residual
 // Thread = column of the tile (lane) x strip of 4 rows (warp); 3x3 windows of x_hi and x_lo
 // slide down the strip in registers.
@@ -759,6 +747,7 @@ cudaError_t launch_residual(const CycleArgs& a, float rtol, int max_cycles) {
 }
 
 cudaError_t launch_cycle(const CycleArgs& a, float rtol, int max_cycles, int parity) {
+  if (a.hk == HK_LINEAR) return launch_cycle_linear(a, rtol, max_cycles, parity);
   const int ls = a.lstar, np = nlaunch(a);
   const ProbDev* probs = a.probs;
   float* const nul = nullptr;

@@ -29,6 +29,13 @@ def field(n: int, st: torch.Tensor) -> dict:
     return {"n": n, "kind": B.MG_PROBLEM_FIELD, "data": st.contiguous()}
 
 
+def net_arch_code(net_arch: str) -> int:
+    codes = {"conv": B.MG_NET_CONV, "fc": B.MG_NET_FC, "linear": B.MG_NET_LINEAR}
+    if net_arch not in codes:
+        raise ValueError(f"unknown net_arch {net_arch!r}")
+    return codes[net_arch]
+
+
 class MultigridSolver:
     """Hierarchy + V-cycle solver for a batch of same-size problems on one GPU."""
 
@@ -38,15 +45,19 @@ class MultigridSolver:
         """net_params: one parameter set [nparams] for every level, or per-level sets
         [k, nparams] (level l uses set min(l, k - 1)).  transpose: smooth with H^T (per-point
         problems), so that a V-cycle applies the transpose of the cycle without it.
-        net_arch: "conv" (the convolutional network) or "fc" (the fully connected one)."""
+        net_arch: "conv" (the convolutional network), "fc" (the fully connected one) or
+        "linear" (the shared-kernel linear smoother of Sec. 6: net_params are its six 3x3
+        kernels per level, [54] or [k, 54])."""
         self.nprob = len(problems)
         self.n = problems[0]["n"]
         self.device = torch.device(device)
         self.stream = stream
         self._probs, self._keep = B.problems_array(problems)
         kind = B.MG_SMOOTH_CNN if smoother == "cnn" else B.MG_SMOOTH_JACOBI
+        if net_params is not None and net_params.dim() > 2:  # e.g. linear sets given as [k, 6, 9]
+            net_params = net_params.reshape(net_params.shape[0], -1)
         net_levels = int(net_params.shape[0]) if net_params is not None and net_params.dim() == 2 else 0
-        arch = B.MG_NET_FC if net_arch == "fc" else B.MG_NET_CONV
+        arch = net_arch_code(net_arch)
         self.opts = B.options(kind, omega, coarsest_n, int(conv_bf16), int(cluster_tail), 1, 0, net_levels,
                               int(transpose), arch)
         size = B.mg_workspace_size(self._probs, self.nprob, self.opts)

@@ -1,0 +1,139 @@
+"""GPU parity of the shared-kernel linear smoother (Sec. 6, eq. full-coarsening-smoother):
+V-cycle solve histories, the standalone smoother and the transposed cycle, through the
+C ABI against the FP64 oracle (oracle/linear.py).
+
+Tolerance: the per-cycle relative residual within 1e-5 of the oracle's, the bar of every
+other solve path here (FP32 cycle, float-float outer iterate and residual).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from oracle import linear as OL
+from paper_2102_12071_gb300 import inputs
+from paper_2102_12071_gb300 import solver as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2102_12071_gb300 import build
+
+    build.build()
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def lin_params(nsets, d, seed, scale=0.01):
+    """Weighted Jacobi (omega/d) plus a small random chain: a convergent smoother whose
+    five chained kernels all act."""
+    rng = np.random.default_rng(seed)
+    return np.stack([OL.jacobi_params(d) + scale * rng.standard_normal((6, 9)) for _ in range(nsets)]).astype(
+        np.float32)
+
+
+def _solve_both(problems, fields, params, b, cycles, gpu_fields=False):
+    """gpu_fields: the oracle cycles on the GPU's own (FP32-rounded) Galerkin fields."""
+    mg = S.MultigridSolver(problems, "cnn", torch.from_numpy(params).cuda(), net_arch="linear")
+    bb = torch.from_numpy(np.stack(b).astype(np.float32)).cuda().contiguous()
+    _, _, gh, cyc, _ = mg.solve(bb, rtol=0.0, max_cycles=cycles)
+    out = []
+    for p, st in enumerate(fields):
+        lv = [mg.stencil_field(p, l).double().cpu().numpy() for l in range(mg.levels)] if gpu_fields else None
+        om = OL.LinearMultigrid(st, [f32(q) for q in params], fields=lv)
+        _, oh = om.solve(f32(b[p]), rtol=0.0, max_cycles=cycles)
+        assert cyc[p] == cycles
+        out.append((gh[p][: cycles + 1], oh))
+    return out
+
+
+@pytest.mark.parametrize("n,cycles,nsets", [(7, 6, 1), (63, 40, 1), (255, 20, 3), (511, 8, 2), (1023, 4, 4)])
+def test_linear_solve_history_matches_oracle(n, cycles, nsets):
+    """n <= 63: whole solves in one CTA; above: batched level kernels, then the tail."""
+    pe = [(0.05, 0.7), (0.01, 2.2)]
+    problems = [S.rotated(n, e, t) for e, t in pe]
+    fields = [O.const_field(n, f32(O.q1_rotated_stencil(e, t))) for e, t in pe]
+    d = fields[0][4, n // 2, n // 2]
+    params = lin_params(nsets, d, seed=n)
+    b = [inputs.rhs_uniform(20 + p, n) for p in range(len(pe))]
+    for gh, oh in _solve_both(problems, fields, params, b, cycles):
+        rel = np.abs(gh - oh) / oh
+        assert rel.max() <= 1e-5, rel.max()
+
+
+def test_linear_solve_per_point_field():
+    """Variable coefficients (per-point stencil fields).  One kernel set for every point
+    cannot follow a diagonal that varies by e^6: omega over the largest diagonal keeps it a
+    damped Jacobi that converges everywhere.  Such a weak smoother leans on the coarse
+    levels, so the oracle cycles on the GPU's FP32 Galerkin fields (their rounding against
+    the FP64 products is pinned by the CNN field-path test)."""
+    n = 127
+    a = inputs.grf_cells(12, n)
+    st0 = O.varcoef5_field(n, f32(a))
+    dmax = st0[4].max()
+    # the random chain stays small against omega / dmax: a perturbation that dominated the
+    # Jacobi part would make the cycle amplify some modes (and with them the rounding)
+    params = lin_params(2, dmax, seed=5, scale=0.02 * (2.0 / 3.0) / dmax)
+    problems = [S.varcoef5(n, torch.from_numpy(a).cuda())]
+    b = [inputs.rhs_uniform(31, n)]
+    for gh, oh in _solve_both(problems, [f32(st0)], params, b, 15, gpu_fields=True):
+        rel = np.abs(gh - oh) / oh
+        assert rel.max() <= 1e-5, rel.max()
+
+
+@pytest.mark.parametrize("n", [63, 255])
+def test_linear_at_the_jacobi_point_solves_like_jacobi(n):
+    eps, theta = 0.02, 1.0
+    s = O.q1_rotated_stencil(eps, theta).astype(np.float32).reshape(9)
+    params = OL.jacobi_params(float(s[4]))[None].astype(np.float32)
+    b = torch.from_numpy(inputs.rhs_uniform(3, n)).cuda()[None].contiguous()
+    lin = S.MultigridSolver([S.rotated(n, eps, theta)], "cnn", torch.from_numpy(params).cuda(), net_arch="linear")
+    jac = S.MultigridSolver([S.rotated(n, eps, theta)], "jacobi")
+    _, _, hl, cl, _ = lin.solve(b, rtol=1e-8, max_cycles=3000)
+    _, _, hj, cj, _ = jac.solve(b, rtol=1e-8, max_cycles=3000)
+    assert abs(int(cl[0]) - int(cj[0])) <= 1
+    k = min(cl[0], cj[0]) + 1
+    assert np.max(np.abs(hl[0][:k] - hj[0][:k]) / hj[0][:k]) < 1e-5
+
+
+def test_linear_standalone_smoother_matches_oracle():
+    n, level = 255, 1
+    eps, theta = 0.1, 0.3
+    params = lin_params(2, O.q1_rotated_stencil(eps, theta).reshape(9)[4], seed=9)
+    mg = S.MultigridSolver([S.rotated(n, eps, theta)], "cnn", torch.from_numpy(params).cuda(), net_arch="linear")
+    nl = mg.sizes[level]
+    st = mg.stencil_field(0, level).double().cpu().numpy()
+    rng = np.random.default_rng(4)
+    f = rng.standard_normal((nl, nl)).astype(np.float32)
+    u = rng.standard_normal((nl, nl)).astype(np.float32)
+    ug = torch.from_numpy(u).cuda()
+    mg.smooth(0, level, torch.from_numpy(f).cuda(), ug, nsteps=2)
+    uo = f32(u)
+    for _ in range(2):
+        uo = uo + OL.apply_H(f32(params[level]), f32(f) - O.apply(st, uo))
+    np.testing.assert_allclose(ug.double().cpu().numpy(), uo, rtol=0, atol=2e-5 * np.abs(uo).max())
+
+
+def test_transposed_linear_cycle_is_the_adjoint():
+    """With every level's chain transposed, one V-cycle from zero applies M^T (the adjoint
+    coarse solve of Algorithm 2's training objective)."""
+    n = 127
+    eps, theta = 0.05, 2.5
+    params = torch.from_numpy(lin_params(3, O.q1_rotated_stencil(eps, theta).reshape(9)[4], seed=2)).cuda()
+    M = S.MultigridSolver([S.rotated(n, eps, theta)], "cnn", params, net_arch="linear")
+    MT = S.MultigridSolver([S.rotated(n, eps, theta)], "cnn", params, net_arch="linear", transpose=True)
+    rng = np.random.default_rng(1)
+    r, s = (torch.from_numpy(v.astype(np.float32)).cuda()[None].contiguous() for v in rng.standard_normal((2, n, n)))
+    xr = torch.zeros_like(r)
+    xs = torch.zeros_like(s)
+    M.vcycle(r, xr)
+    MT.vcycle(s, xs)
+    lhs = float((xr.double() * s.double()).sum())
+    rhs = float((r.double() * xs.double()).sum())
+    assert math.isclose(lhs, rhs, rel_tol=1e-4), (lhs, rhs)
