@@ -71,6 +71,14 @@ struct TrainDims {
   const float* st = fields + (size_t)b * 9 * D.nn;           \
   (void)i; (void)j; (void)st;
 
+// the same for kernels that touch no stencil
+#define T_PROLOGUE_V                                         \
+  const int vec = blockIdx.y;                                \
+  const int q = blockIdx.x * TT + threadIdx.x;               \
+  if (q >= (int)D.nn) return;                                \
+  const int i = q / D.n, j = q % D.n;                        \
+  const size_t off = (size_t)vec * D.nn;
+
 // out = A in
 __global__ void k_t_applyA(TrainDims D, const float* __restrict__ fields, const float* __restrict__ in,
                            float* __restrict__ out) {
@@ -322,6 +330,123 @@ __global__ void k_t_band_solve(TrainDims D, const double* __restrict__ band, con
   }
 }
 
+// ------------------------------------------------- the shared-kernel linear smoother
+// H v = f5(f4(f3(f2(f1 v)))) + f6 v (Sec. 6, eq. full-coarsening-smoother), one 3x3
+// kernel per layer shared by every point of every vector, each layer's input zero outside
+// the grid.  Forward: four plain passes and x - (f5 w4 + f6 v).  Adjoint of one
+// application e_out = x - H v with output gradient g: the passes recomputed from v, then
+// back through the chain (transposed passes), the kernel gradients as correlations
+// sum_x lambda(x) w(x + d_t) reduced in a fixed order, and H^T g for the state adjoint.
+
+// sum_t w[t] v(i + di_t, j + dj_t) on one dense n x n vector, centre tap first
+__device__ __forceinline__ float tl_conv_at(const float* w, const float* v, int n, int i, int j) {
+  float acc = w[4] * v[i * n + j];
+#pragma unroll
+  for (int t = 0; t < 9; ++t) {
+    if (t == 4) continue;
+    const int ii = i + t / 3 - 1, jj = j + t % 3 - 1;
+    if (in_grid(ii, jj, n)) acc = fmaf(w[t], v[ii * n + jj], acc);
+  }
+  return acc;
+}
+
+// sum_t w[t] v(i - di_t, j - dj_t): the transposed pass
+__device__ __forceinline__ float tl_convT_at(const float* w, const float* v, int n, int i, int j) {
+  float acc = w[4] * v[i * n + j];
+#pragma unroll
+  for (int t = 0; t < 9; ++t) {
+    if (t == 4) continue;
+    const int ii = i - (t / 3 - 1), jj = j - (t % 3 - 1);
+    if (in_grid(ii, jj, n)) acc = fmaf(w[t], v[ii * n + jj], acc);
+  }
+  return acc;
+}
+
+// out = f(in), kernel w (9 floats), every vector
+__global__ void k_tl_conv(TrainDims D, const float* __restrict__ w, const float* __restrict__ in,
+                          float* __restrict__ out) {
+  T_PROLOGUE_V
+  out[off + q] = tl_conv_at(w, in + off, D.n, i, j);
+}
+
+// out = f^T(in)
+__global__ void k_tl_convT(TrainDims D, const float* __restrict__ w, const float* __restrict__ in,
+                           float* __restrict__ out) {
+  T_PROLOGUE_V
+  out[off + q] = tl_convT_at(w, in + off, D.n, i, j);
+}
+
+// out = x - (f5(w4) + f6(v))
+__global__ void k_tl_xmH(TrainDims D, const float* __restrict__ phi, const float* __restrict__ x,
+                         const float* __restrict__ w4, const float* __restrict__ v, float* __restrict__ out) {
+  T_PROLOGUE_V
+  const float h = tl_conv_at(phi + 36, w4 + off, D.n, i, j) + tl_conv_at(phi + 45, v + off, D.n, i, j);
+  out[off + q] = x[off + q] - h;
+}
+
+// out = H^T g = f1^T(l1) + f6^T(g)
+__global__ void k_tl_HT(TrainDims D, const float* __restrict__ phi, const float* __restrict__ l1,
+                        const float* __restrict__ g, float* __restrict__ out) {
+  T_PROLOGUE_V
+  out[off + q] = tl_convT_at(phi, l1 + off, D.n, i, j) + tl_convT_at(phi + 45, g + off, D.n, i, j);
+}
+
+// partial[(vec * gridDim.x + block) * 9 + t] = sum over the block's points x of g(x) u(x + d_t)
+__global__ void k_tl_corr(TrainDims D, const float* __restrict__ g, const float* __restrict__ u,
+                          float* __restrict__ partial) {
+  const int vec = blockIdx.y;
+  const int q = blockIdx.x * TT + threadIdx.x;
+  float c[9];
+#pragma unroll
+  for (int t = 0; t < 9; ++t) c[t] = 0.f;
+  if (q < (int)D.nn) {
+    const int i = q / D.n, j = q % D.n;
+    const size_t off = (size_t)vec * D.nn;
+    const float gv = g[off + q];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+      const int ii = i + t / 3 - 1, jj = j + t % 3 - 1;
+      if (in_grid(ii, jj, D.n)) c[t] = gv * u[off + ii * D.n + jj];
+    }
+  }
+  __shared__ float ws[9][TT / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int t = 0; t < 9; ++t) {
+    const float v = warp_sum(c[t]);
+    if (lane == 0) ws[t][w] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 9) {
+    float s = 0.f;
+    for (int k = 0; k < TT / 32; ++k) s += ws[threadIdx.x][k];
+    partial[((size_t)vec * gridDim.x + blockIdx.x) * 9 + threadIdx.x] = s;
+  }
+}
+
+// grad[slot * 9 + t] -= sum of the count partials of tap t (float-float, fixed order); 9 CTAs
+__global__ void k_tl_reduce(const float* __restrict__ partial, int count, float* __restrict__ grad, int slot) {
+  const int t = blockIdx.x;
+  float hi = 0.f, lo = 0.f;
+  for (int k = threadIdx.x; k < count; k += TT) ff_add(hi, lo, partial[(size_t)k * 9 + t], 0.f);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
+    ff_add(hi, lo, oh, ol);
+  }
+  __shared__ float sh[TT / 32], sl[TT / 32];
+  if ((threadIdx.x & 31) == 0) {
+    sh[threadIdx.x >> 5] = hi;
+    sl[threadIdx.x >> 5] = lo;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float h = 0.f, l = 0.f;
+    for (int k = 0; k < TT / 32; ++k) ff_add(h, l, sh[k], sl[k]);
+    grad[slot * 9 + t] -= h + l;
+  }
+}
+
 // constant stencils expanded to truncated fields
 __global__ void k_t_const_field(TrainDims D, const float* __restrict__ s9, float* __restrict__ fields) {
   const int b = blockIdx.y;
@@ -381,6 +506,9 @@ struct mg_train_ctx {
   int kmax = 1, k = 1, ckpt = 0;   // cycles reserved / used by the loss; checkpointing
   int arch = MG_NET_CONV;          // network architecture (mg_net_arch)
   float* fc_scratch = nullptr;     // the fully connected network's backward tape
+  float* lw[6] = {};               // the linear smoother: w1..w4 and two adjoint vectors
+  float* lpart = nullptr;          // its per-CTA correlation partials
+  float* lgrad = nullptr;          // its gradient accumulator [MG_NPARAMS_LIN]
   std::vector<float*> X;           // X[c]: input of cycle c >= 1
   std::vector<float*> V0, V2;      // A e_c and A (C S e_c) of cycle c (V0[0] = v0, V2[0] = v2)
   std::vector<float> h_s9;
@@ -395,7 +523,7 @@ mg_status train_dims(const mg_problem* probs, int nprob, int nvec, const mg_opti
   if (!probs || nprob < 1 || nvec < 1 || !o) return (mg_status)api_fail(MG_ERR_INVALID_ARG, "training: bad arguments");
   if (o->train_cycles < 0 || o->train_cycles > kMaxTrainCycles)
     return (mg_status)api_fail(MG_ERR_INVALID_ARG, "train_cycles must be in [0, %d]", kMaxTrainCycles);
-  if (o->net_arch != MG_NET_CONV && o->net_arch != MG_NET_FC)
+  if (o->net_arch != MG_NET_CONV && o->net_arch != MG_NET_FC && o->net_arch != MG_NET_LINEAR)
     return (mg_status)api_fail(MG_ERR_INVALID_ARG, "unknown net_arch");
   if ((long long)nprob * nvec > 65535) return (mg_status)api_fail(MG_ERR_INVALID_ARG, "nprob * nvec must be <= 65535");
   if (!(o->omega > 0.f) || !(o->omega < 2.f)) return (mg_status)api_fail(MG_ERR_INVALID_ARG, "omega must be in (0, 2)");
@@ -472,6 +600,11 @@ size_t train_carve(const TrainDims& D, int kmax, int ckpt, int arch, void* basev
   x.ncta_bw = net_backward_ctas(D.n, D.B);
   x.param_partial = take<float>(base, off, (size_t)x.ncta_bw * MG_NPARAMS);
   x.fc_scratch = arch == MG_NET_FC ? take<float>(base, off, fc_backward_floats(D.n, D.B)) : nullptr;
+  if (arch == MG_NET_LINEAR) {
+    for (int k = 0; k < 6; ++k) x.lw[k] = take<float>(base, off, D.nn * BZ);
+    x.lpart = take<float>(base, off, ((D.nn + TT - 1) / TT) * BZ * 9);
+    x.lgrad = take<float>(base, off, MG_NPARAMS_LIN);
+  }
   x.fail = take<int>(base, off, 4);
   return off + 256;
 }
@@ -590,9 +723,44 @@ static mg_status train_step(mg_train_ctx* c, const float* params, const float* z
   nb.stride = 9 * D.nn;
   nb.n = D.n;
   nb.pad_ = 0;
+  const bool lin = c->arch == MG_NET_LINEAR;  // params are the smoother's 54 weights
   if (c->arch == MG_NET_FC) TCK(launch_fc_forward_batch(nb, D.B, params, c->omega, c->bf16, s));
-  else TCK(launch_net_forward_batch(nb, D.B, params, c->omega, c->bf16, s));
+  else if (!lin) TCK(launch_net_forward_batch(nb, D.B, params, c->omega, c->bf16, s));
   const int K = c->k;
+  // out = x - H v
+  auto xmHv = [&](const float* x, const float* v, float* out) {
+    if (!lin) {
+      k_t_xmHv<<<gv, TT, 0, s>>>(D, c->fields, c->W, x, v, out);
+      return;
+    }
+    k_tl_conv<<<gv, TT, 0, s>>>(D, params, v, c->lw[4]);
+    k_tl_conv<<<gv, TT, 0, s>>>(D, params + 9, c->lw[4], c->lw[5]);
+    k_tl_conv<<<gv, TT, 0, s>>>(D, params + 18, c->lw[5], c->lw[4]);
+    k_tl_conv<<<gv, TT, 0, s>>>(D, params + 27, c->lw[4], c->lw[5]);
+    k_tl_xmH<<<gv, TT, 0, s>>>(D, params, x, c->lw[5], v, out);
+  };
+  // the linear smoother's part of the adjoint of e_out = x - H v with output gradient g:
+  // grad -= d<g, H v>/dphi, and t = H^T g
+  const int nblk = (int)((D.nn + TT - 1) / TT);
+  auto corr = [&](const float* g, const float* u, int slot) {
+    k_tl_corr<<<dim3(nblk, BZ), TT, 0, s>>>(D, g, u, c->lpart);
+    k_tl_reduce<<<9, TT, 0, s>>>(c->lpart, nblk * BZ, c->lgrad, slot);
+  };
+  auto lin_adjoint = [&](const float* v, const float* g, float* t) {
+    float* const* w = c->lw;  // w1..w4 in lw[0..3], adjoint vectors in lw[4], lw[5]
+    k_tl_conv<<<gv, TT, 0, s>>>(D, params, v, w[0]);
+    for (int k = 1; k < 4; ++k) k_tl_conv<<<gv, TT, 0, s>>>(D, params + 9 * k, w[k - 1], w[k]);
+    corr(g, w[3], 4);  // f5 reads w4
+    corr(g, v, 5);     // f6 reads v
+    const float* lam = g;
+    for (int k = 4; k >= 1; --k) {  // lam <- f_{k+1}^T lam: the gradient at w_k
+      float* out = c->lw[4 + (k & 1)];
+      k_tl_convT<<<gv, TT, 0, s>>>(D, params + 9 * k, lam, out);
+      lam = out;
+      corr(lam, k >= 2 ? w[k - 2] : v, k - 1);  // f_k reads w_{k-1} (w_0 = v)
+    }
+    k_tl_HT<<<gv, TT, 0, s>>>(D, params, lam, g, t);
+  };
   // xc = M rc: the exact coarse solve (banded Cholesky), or one V-cycle of the coarse
   // context (cf), whose transpose ct serves the adjoint
   auto coarse_solve = [&](const CycleArgs* ca) -> cudaError_t {
@@ -609,12 +777,12 @@ static mg_status train_step(mg_train_ctx* c, const float* params, const float* z
   // NULL (recomputation of the products only)
   auto cycle = [&](const float* ein, float* v0, float* v2, float* eout) {
     k_t_applyA<<<gv, TT, 0, s>>>(D, c->fields, ein, v0);
-    k_t_xmHv<<<gv, TT, 0, s>>>(D, c->fields, c->W, ein, v0, c->e1);
+    xmHv(ein, v0, c->e1);
     k_t_restrict<<<gc, TT, 0, s>>>(D, c->fields, c->e1, 1, c->rc);
     if (ce == cudaSuccess) ce = coarse_solve(cf);
     k_t_xmP<<<gv, TT, 0, s>>>(D, c->e1, c->xc, c->e2);
     k_t_applyA<<<gv, TT, 0, s>>>(D, c->fields, c->e2, v2);
-    if (eout) k_t_xmHv<<<gv, TT, 0, s>>>(D, c->fields, c->W, c->e2, v2, eout);
+    if (eout) xmHv(c->e2, v2, eout);
   };
   // forward: e_{c+1} = S C S e_c; the last output goes to g3
   for (int cc = 0; cc < K; ++cc)
@@ -625,14 +793,21 @@ static mg_status train_step(mg_train_ctx* c, const float* params, const float* z
   TCK(cudaGetLastError());
   if (!grad_out) return MG_OK;
   // adjoint, cycles in reverse; g3 = dloss/d(output of cycle cc)
+  if (lin) TCK(cudaMemsetAsync(c->lgrad, 0, MG_NPARAMS_LIN * sizeof(float), s));
   for (int cc = K - 1; cc >= 0; --cc) {
     if (c->ckpt && cc + 1 < K) cycle(cc == 0 ? z : c->X[cc], c->V0[cc], c->V2[cc], nullptr);
-    k_t_HT<<<gv, TT, 0, s>>>(D, c->fields, c->W, c->g3, c->t);
+    if (lin) lin_adjoint(c->V2[cc], c->g3, c->t);
+    else k_t_HT<<<gv, TT, 0, s>>>(D, c->fields, c->W, c->g3, c->t);
     k_t_xmAv<<<gv, TT, 0, s>>>(D, c->fields, c->g3, c->t, c->g2);
     k_t_restrict<<<gc, TT, 0, s>>>(D, c->fields, c->g2, 0, c->rc);
     TCK(coarse_solve(ct));
     k_t_P<<<gv, TT, 0, s>>>(D, c->xc, c->t);
     k_t_xmAv<<<gv, TT, 0, s>>>(D, c->fields, c->g2, c->t, c->g1);
+    if (lin) {
+      lin_adjoint(c->V0[cc], c->g1, c->t);
+      if (cc > 0) k_t_xmAv<<<gv, TT, 0, s>>>(D, c->fields, c->g1, c->t, c->g3);
+      continue;
+    }
     k_t_dW<<<dim3((unsigned)((D.nn + TT - 1) / TT), D.B), TT, 0, s>>>(D, c->g3, c->V2[cc], c->g1, c->V0[cc], c->dW,
                                                                        cc + 1 < K);
     if (cc > 0) {  // dloss/d(input of cycle cc) = S^T g1
@@ -642,6 +817,10 @@ static mg_status train_step(mg_train_ctx* c, const float* params, const float* z
   }
   TCK(ce);
   TCK(cudaGetLastError());
+  if (lin) {
+    TCK(cudaMemcpyAsync(grad_out, c->lgrad, MG_NPARAMS_LIN * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    return MG_OK;
+  }
   if (c->arch == MG_NET_FC) TCK(launch_fc_backward(nb, D.B, c->dW, params, c->bf16, c->fc_scratch, 1.f, grad_out, s));
   else TCK(launch_net_backward(nb, D.B, c->dW, params, c->bf16, c->param_partial, 1.f, grad_out, s));
   return MG_OK;

@@ -23,10 +23,21 @@ NPARAMS = 1260
 LAYERS = [(7, 9), (5, 7), (3, 5), (9, 3)]  # (out, in) channels of the 3x3 layers
 NPARAMS_FC = 6800
 FC_LAYERS = [(40, 81), (40, 40), (40, 40), (9, 40)]  # the fully connected network (out, in)
+NPARAMS_LIN = 54  # the shared-kernel linear smoother of one level: six 3x3 kernels
 
 
 def nparams(arch: str = "conv") -> int:
-    return NPARAMS_FC if arch == "fc" else NPARAMS
+    return {"fc": NPARAMS_FC, "linear": NPARAMS_LIN}.get(arch, NPARAMS)
+
+
+def init_params_linear(d: float, omega: float = 2.0 / 3.0) -> torch.Tensor:
+    """The linear smoother at weighted Jacobi for diagonal d: f1..f4 the identity kernel,
+    f5 zero, f6 = omega/d at the centre.  (Sec. 6 starts f1..f5 at zero, where the chain's
+    gradient vanishes identically; this start is Jacobi as well and lets the chain learn.)"""
+    p = torch.zeros(6, 9)
+    p[0:4, 4] = 1.0
+    p[5, 4] = omega / d
+    return p.reshape(-1)
 
 
 def init_params_fc(seed: int = 0) -> torch.Tensor:
@@ -70,8 +81,10 @@ class TwoGridBatch:
         self.nvec = nvec
         self.net_arch = net_arch
         self._probs, self._keep = B.problems_array(problems)
+        from .solver import net_arch_code
+
         self.opts = B.options(B.MG_SMOOTH_CNN, omega, 3, int(conv_bf16), 1, int(cycles), int(checkpoint), 0, 0,
-                              B.MG_NET_FC if net_arch == "fc" else B.MG_NET_CONV)
+                              net_arch_code(net_arch))
         size = B.mg_train_workspace_size(self._probs, self.nprob, nvec, self.opts)
         if size == 0:
             raise B.MGError(B.MG_ERR_INVALID_ARG, "mg_train_workspace_size", B.lib().mg_last_error().decode())
@@ -110,7 +123,7 @@ class TwoGridBatch:
         kind = "cnn" if level_params is not None else "jacobi"
         om = self.opts.omega if omega is None else omega
         self._coarse = [S.MultigridSolver(probs, kind, net_params=level_params, omega=om, conv_bf16=bool(self.opts.conv_bf16),
-                                          transpose=t) for t in (False, True)]
+                                          transpose=t, net_arch=self.net_arch) for t in (False, True)]
         self._coarse_fields = fields
 
     def detach_coarse(self) -> None:
@@ -232,7 +245,11 @@ class AdaptiveTrainer:
 
     def __init__(self, n_fine: int = 63, per_size: int = 32, nvec: int = 32, steps_per_level: int = 300,
                  lr: float = 1e-3, omega: float = 2.0 / 3.0, conv_bf16: bool = True, seed: int = 0,
-                 eps_range=(1e-3, 1.0), max_cycles: int = 1, init=None):
+                 eps_range=(1e-3, 1.0), max_cycles: int = 1, init=None, net_arch: str = "conv",
+                 problem: tuple[float, float] | None = None):
+        """net_arch "linear": the shared-kernel linear smoother of Sec. 6, trained for one
+        problem (eps, theta) = `problem` -- Sec. 6 trains each such smoother on instances of
+        its own problem: here `per_size` copies of it with nvec random vectors each."""
         self.sizes = []
         n = n_fine
         while n > 3:
@@ -242,6 +259,10 @@ class AdaptiveTrainer:
         self.lr, self.omega, self.conv_bf16, self.seed = lr, omega, conv_bf16, seed
         self.eps_range, self.max_cycles = eps_range, max_cycles
         self.init = init  # starting parameters of every level (None: the Jacobi-equivalent net)
+        self.net_arch = net_arch
+        self.problem = problem
+        if net_arch == "linear" and problem is None:
+            raise ValueError("the linear smoother is trained for one problem (eps, theta)")
         self.params: dict[int, torch.Tensor] = {}
         self.losses: dict[int, list[float]] = {}
         self.gen = torch.Generator(device="cuda").manual_seed(inputs.SEED_TRAIN + 17 + seed)
@@ -252,18 +273,29 @@ class AdaptiveTrainer:
         return torch.stack([self.params[m] for m in below]) if below else None
 
     def problems(self, step: int, n: int) -> list[dict]:
+        if self.problem is not None:
+            e, t = self.problem
+            return [{"n": n, "kind": B.MG_PROBLEM_ROTATED, "eps": e, "theta": t}] * self.per_size
         params = inputs.rotated_params(inputs.SEED_TRAIN + 104729 * step + 7 * n + 1, self.per_size, *self.eps_range)
         return [{"n": n, "kind": B.MG_PROBLEM_ROTATED, "eps": e, "theta": t} for e, t in params]
 
+    def _init(self) -> torch.Tensor:
+        if self.init is not None:
+            return self.init.detach().clone()
+        if self.net_arch == "linear":
+            s = B.mg_rotated_stencil(*self.problem)
+            return init_params_linear(float(s[4]), self.omega)
+        return init_params_fc(self.seed) if self.net_arch == "fc" else init_params(self.seed)
+
     def train_level(self, n: int) -> torch.Tensor:
-        p = (init_params(self.seed) if self.init is None else self.init.detach().clone()).cuda().requires_grad_(True)
+        p = self._init().cuda().requires_grad_(True)
         opt = torch.optim.Adam([p], lr=self.lr)
         below = self.level_params(n)
         ws = None
         hist = []
         for step in range(self.steps):
             batch = TwoGridBatch(self.problems(step, n), self.nvec, self.omega, self.conv_bf16, ws,
-                                 cycles=self.max_cycles)
+                                 cycles=self.max_cycles, net_arch=self.net_arch)
             ws = batch.workspace
             if (n - 1) // 2 > 3:  # the level above the coarsest keeps the exact coarse solve
                 batch.attach_coarse(below)

@@ -137,3 +137,80 @@ def test_transposed_linear_cycle_is_the_adjoint():
     lhs = float((xr.double() * s.double()).sum())
     rhs = float((r.double() * xs.double()).sum())
     assert math.isclose(lhs, rhs, rel_tol=1e-4), (lhs, rhs)
+
+
+# ------------------------------------------------------------------ training
+def _lin_batch(n, pe, nvec, seed, cycles=1, checkpoint=False):
+    from paper_2102_12071_gb300 import train as T
+
+    batch = T.TwoGridBatch([S.rotated(n, e, t) for e, t in pe], nvec, cycles=cycles, checkpoint=checkpoint,
+                           net_arch="linear")
+    z = np.random.default_rng(seed).standard_normal((len(pe), nvec, n, n)).astype(np.float32)
+    return batch, z
+
+
+@pytest.mark.parametrize("n,cycles,ckpt", [(15, 1, False), (31, 1, False), (15, 3, False), (15, 3, True)])
+def test_linear_train_step_matches_oracle(n, cycles, ckpt):
+    """Loss and gradient of the 54 weights (Sec. 3.2 objective, k cycles) against the oracle's
+    analytic adjoint; checkpointing recomputes the cycle products and changes nothing."""
+    pe = [(0.05, 0.7), (0.01, 2.0)]
+    phi = lin_params(1, O.q1_rotated_stencil(*pe[0]).reshape(9)[4], seed=n, scale=0.05)[0]
+    batch, z = _lin_batch(n, pe, 3, seed=1, cycles=cycles, checkpoint=ckpt)
+    loss, grad = batch.loss_and_grad(torch.from_numpy(phi.reshape(-1)).cuda(), torch.from_numpy(z).cuda())
+    lo, go = 0.0, np.zeros((6, 9))
+    for b, (e, t) in enumerate(pe):
+        st = O.const_field(n, f32(O.q1_rotated_stencil(e, t)))
+        l, g = OL.loss_and_grad(st, f32(phi), f32(z[b]), cycles=cycles)
+        lo += l / len(pe)
+        go += g / len(pe)
+    assert math.isclose(float(loss[0]), lo, rel_tol=2e-5), (float(loss[0]), lo)
+    g = grad.double().cpu().numpy().reshape(6, 9)
+    assert np.max(np.abs(g - go)) <= 1e-4 * np.max(np.abs(go)), np.max(np.abs(g - go)) / np.max(np.abs(go))
+
+
+def test_linear_vcycle_coarse_train_step_matches_oracle():
+    """Algorithm 2's objective: the coarse solve replaced by one V-cycle of the trained
+    linear smoothers below, its adjoint by the cycle with transposed chains."""
+    n = 31
+    pe = [(0.02, 1.2), (0.3, 0.4)]
+    d = O.q1_rotated_stencil(*pe[0]).reshape(9)[4]
+    lower = lin_params(2, d, seed=3, scale=0.02)
+    phi = lin_params(1, d, seed=4, scale=0.05)[0]
+    batch, z = _lin_batch(n, pe, 2, seed=2)
+    batch.attach_coarse(torch.from_numpy(lower.reshape(2, -1)).cuda())
+    loss, grad = batch.loss_and_grad(torch.from_numpy(phi.reshape(-1)).cuda(), torch.from_numpy(z).cuda())
+    coarse_fields = [f.double().cpu().numpy() for f in batch.coarse_fields()]
+    lo, go = 0.0, np.zeros((6, 9))
+    for b, (e, t) in enumerate(pe):
+        st = O.const_field(n, f32(O.q1_rotated_stencil(e, t)))
+        M = OL.coarse_vcycle(coarse_fields[b], [f32(q) for q in lower])
+        MT = OL.coarse_vcycle(coarse_fields[b], [f32(q) for q in lower], transpose=True)
+        l, g = OL.loss_and_grad(st, f32(phi), f32(z[b]), coarse=M, coarse_t=MT)
+        lo += l / len(pe)
+        go += g / len(pe)
+    batch.close()
+    assert math.isclose(float(loss[0]), lo, rel_tol=1e-4), (float(loss[0]), lo)
+    g = grad.double().cpu().numpy().reshape(6, 9)
+    assert np.max(np.abs(g - go)) <= 2e-4 * np.max(np.abs(go)), np.max(np.abs(g - go)) / np.max(np.abs(go))
+
+
+def test_adaptively_trained_linear_smoother_gains_over_jacobi():
+    """Sec. 6's alpha-CNN for one problem: per-level linear smoothers trained coarse to fine
+    (Algorithm 2) on a 31^2 hierarchy, then used on every level of a 255^2 solve.  The
+    objective falls on every level and the solve needs fewer cycles than weighted Jacobi."""
+    from paper_2102_12071_gb300 import train as T
+
+    eps, theta = 0.01, math.pi / 6
+    at = T.AdaptiveTrainer(n_fine=31, per_size=1, nvec=64, steps_per_level=150, lr=3e-3, conv_bf16=False,
+                           net_arch="linear", problem=(eps, theta))
+    at.train()
+    for n, h in at.losses.items():
+        assert np.mean(h[-10:]) < 0.9 * np.mean(h[:10]), (n, h[:3], h[-3:])
+    n = 255
+    b = torch.from_numpy(inputs.rhs_uniform(5, n)).cuda()[None].contiguous()
+    lin = S.MultigridSolver([S.rotated(n, eps, theta)], "cnn", at.hierarchy_params(n), net_arch="linear")
+    jac = S.MultigridSolver([S.rotated(n, eps, theta)], "jacobi")
+    _, _, _, cl, sl = lin.solve(b, rtol=1e-8, max_cycles=5000)
+    _, _, _, cj, sj = jac.solve(b, rtol=1e-8, max_cycles=5000)
+    assert sl == 0 and sj == 0
+    assert cl[0] < cj[0], (cl, cj)
