@@ -145,6 +145,18 @@ def load_adaptive():
     return np.load(path).astype(np.float32)
 
 
+def load_linear():
+    """Shared-kernel linear smoothers (Sec. 6) trained per problem by Algorithm 2: (params
+    [thetas, levels, 54], thetas, eps, n_fine) or None."""
+    path = os.path.join(os.path.dirname(WEIGHTS), "linear_eps0.01.npz")
+    if not os.path.exists(path):
+        return None
+    import numpy as np
+
+    z = np.load(path)
+    return z["params"].astype(np.float32), [float(t) for t in z["thetas"]], float(z["eps"]), int(z["n_fine"])
+
+
 # ------------------------------------------------------------------ reference arm
 def run_reference(args):
     """FP64 CPU oracle on a bounded sample: a fixed number of V(1,1) cycles on one problem."""
@@ -346,6 +358,28 @@ def run_fgmres(weights):
         out[name] = {"iterations": [int(i) for i in its], "ms_batch": ms, "converged": int(st) == 0,
                      "vcycle_alone_cycles": [int(c) for c in cyc]}
         mg.close()
+    # the paper's alpha-CNN of Sec. 6: one linear shared-kernel smoother per level and per
+    # problem, trained by Algorithm 2 for that problem -- one context per angle
+    lin = load_linear()
+    if lin is not None and abs(lin[2] - 0.01) < 1e-12 and all(abs(a - b) < 1e-9 for a, b in zip(lin[1], thetas)):
+        its, cycs, ms, ok = [], [], 0.0, True
+        for i, th in enumerate(thetas):
+            mg = S.MultigridSolver([probs[i]], "cnn", T.adaptive_params(lin[0][i], n, lin[3]).cuda(), net_arch="linear")
+            bi = b[i:i + 1].contiguous()
+            S.fgmres(mg, bi, rtol=1e-6, history=False)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, _, _, it, st = S.fgmres(mg, bi, rtol=1e-6, history=False)
+            torch.cuda.synchronize()
+            ms += 1e3 * (time.perf_counter() - t0)
+            _, _, _, cyc, _ = mg.solve(bi, rtol=1e-6, max_cycles=MAX_CYCLES, history=False)
+            its.append(int(it[0]))
+            cycs.append(int(cyc[0]))
+            ok = ok and int(st) == 0
+            mg.close()
+        out["linear_alpha"] = {"iterations": its, "ms_batch": ms, "converged": ok, "vcycle_alone_cycles": cycs,
+                               "smoother": "per-angle linear H = f5(..f1) + f6 per level (Sec. 6), Algorithm 2 on a "
+                                           f"{lin[3]}^2 hierarchy; one context per angle, run one after another"}
     return out
 
 

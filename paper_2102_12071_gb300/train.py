@@ -365,10 +365,35 @@ def main():
     ap.add_argument("--adaptive", type=int, default=0, metavar="N_FINE",
                     help="Algorithm 2: one network per level of a hierarchy of this side, trained coarse to fine "
                          "(--steps per level); saves [levels, nparams], finest first")
+    ap.add_argument("--linear", action="store_true",
+                    help="with --adaptive: the shared-kernel linear smoother of Sec. 6, one per problem "
+                         "(eps = --eps, theta in --thetas); saves an .npz of params [thetas, levels, 54]")
+    ap.add_argument("--eps", type=float, default=0.01)
+    ap.add_argument("--thetas", default="1,2,3,4,5", help="angles in units of pi/12")
     args = ap.parse_args()
     from . import build
 
     build.build()
+    if args.linear:
+        if not args.adaptive:
+            ap.error("--linear trains per level: give --adaptive N_FINE")
+        t0 = time.time()
+        thetas = [float(k) * math.pi / 12 for k in args.thetas.split(",")]
+        sets = []
+        for th in thetas:
+            at = AdaptiveTrainer(n_fine=args.adaptive, per_size=1, nvec=64, steps_per_level=args.steps, lr=args.lr,
+                                 seed=args.seed, conv_bf16=False, net_arch="linear", problem=(args.eps, th))
+            at.train()
+            sets.append(torch.stack([at.params[n] for n in at.sizes]).cpu().numpy().astype(np.float32))
+            h = at.losses[at.sizes[0]]
+            print(f"theta {th:.4f}: finest-level loss {np.mean(h[:10]):.5f} -> {np.mean(h[-10:]):.5f} "
+                  f"({time.time() - t0:.1f} s)", flush=True)
+        out = args.out or os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights",
+                                       f"linear_eps{args.eps:g}.npz")
+        os.makedirs(os.path.dirname(out), exist_ok=True)
+        np.savez(out, params=np.stack(sets), thetas=np.array(thetas), eps=args.eps, n_fine=args.adaptive)
+        print("saved", out, "levels", at.sizes)
+        return
     if args.adaptive:
         t0 = time.time()
         at = AdaptiveTrainer(n_fine=args.adaptive, steps_per_level=args.steps, lr=args.lr, seed=args.seed,

@@ -214,3 +214,28 @@ def test_adaptively_trained_linear_smoother_gains_over_jacobi():
     _, _, _, cj, sj = jac.solve(b, rtol=1e-8, max_cycles=5000)
     assert sl == 0 and sj == 0
     assert cl[0] < cj[0], (cl, cj)
+
+
+def test_fgmres_with_the_linear_smoother_matches_oracle():
+    """Sec. 6.4's solver with the linear smoother's V-cycle as the preconditioner: iterations
+    within two of the FP64 oracle's, first restart cycle's residual estimates within 1e-3,
+    true residual of the float-float solution below rtol."""
+    from paper_2102_12071_gb300 import binding as B
+
+    n, eps, theta = 255, 0.01, math.pi / 4
+    d = O.q1_rotated_stencil(eps, theta).reshape(9)[4]
+    params = lin_params(3, d, seed=8, scale=0.01)
+    b_np = inputs.rhs_uniform(inputs.SEED_RHS + 1600, n)
+    mg = S.MultigridSolver([S.rotated(n, eps, theta)], "cnn", torch.from_numpy(params).cuda(), net_arch="linear")
+    xh, xl, gh, its, st = S.fgmres(mg, torch.from_numpy(b_np).cuda()[None].contiguous(), restart=30, rtol=1e-6,
+                                   max_iters=300)
+    assert st == B.MG_OK
+    st0 = O.const_field(n, f32(O.q1_rotated_stencil(eps, theta)))
+    om = OL.LinearMultigrid(st0, [f32(q) for q in params])
+    xo, oh, oits = O.fgmres(lambda v: O.apply(st0, v), lambda v: om.vcycle(v, np.zeros_like(v)), f32(b_np),
+                            restart=30, rtol=1e-6, max_iters=300)
+    assert abs(int(its[0]) - oits) <= 2, (int(its[0]), oits)
+    k = min(int(its[0]), oits, 30) + 1
+    assert np.max(np.abs(gh[0][:k] - oh[:k]) / oh[:k]) <= 1e-3
+    x = xh[0].double().cpu().numpy() + xl[0].double().cpu().numpy()
+    assert np.linalg.norm(f32(b_np) - O.apply(st0, x)) / np.linalg.norm(f32(b_np)) < 1e-6
