@@ -359,27 +359,24 @@ def run_fgmres(weights):
                      "vcycle_alone_cycles": [int(c) for c in cyc]}
         mg.close()
     # the paper's alpha-CNN of Sec. 6: one linear shared-kernel smoother per level and per
-    # problem, trained by Algorithm 2 for that problem -- one context per angle
+    # problem, trained by Algorithm 2 for that problem -- one batched context, each problem
+    # with its own group of per-level sets
     lin = load_linear()
     if lin is not None and abs(lin[2] - 0.01) < 1e-12 and all(abs(a - b) < 1e-9 for a, b in zip(lin[1], thetas)):
-        its, cycs, ms, ok = [], [], 0.0, True
-        for i, th in enumerate(thetas):
-            mg = S.MultigridSolver([probs[i]], "cnn", T.adaptive_params(lin[0][i], n, lin[3]).cuda(), net_arch="linear")
-            bi = b[i:i + 1].contiguous()
-            S.fgmres(mg, bi, rtol=1e-6, history=False)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            _, _, _, it, st = S.fgmres(mg, bi, rtol=1e-6, history=False)
-            torch.cuda.synchronize()
-            ms += 1e3 * (time.perf_counter() - t0)
-            _, _, _, cyc, _ = mg.solve(bi, rtol=1e-6, max_cycles=MAX_CYCLES, history=False)
-            its.append(int(it[0]))
-            cycs.append(int(cyc[0]))
-            ok = ok and int(st) == 0
-            mg.close()
-        out["linear_alpha"] = {"iterations": its, "ms_batch": ms, "converged": ok, "vcycle_alone_cycles": cycs,
+        groups = torch.stack([T.adaptive_params(lin[0][i], n, lin[3]) for i in range(len(thetas))]).cuda()
+        mg = S.MultigridSolver(probs, "cnn", groups, net_arch="linear", per_problem=True)
+        S.fgmres(mg, b, rtol=1e-6, history=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, _, its, st = S.fgmres(mg, b, rtol=1e-6, history=False)
+        torch.cuda.synchronize()
+        ms = 1e3 * (time.perf_counter() - t0)
+        _, _, _, cyc, _ = mg.solve(b, rtol=1e-6, max_cycles=MAX_CYCLES, history=False)
+        out["linear_alpha"] = {"iterations": [int(i) for i in its], "ms_batch": ms, "converged": int(st) == 0,
+                               "vcycle_alone_cycles": [int(c) for c in cyc],
                                "smoother": "per-angle linear H = f5(..f1) + f6 per level (Sec. 6), Algorithm 2 on a "
-                                           f"{lin[3]}^2 hierarchy; one context per angle, run one after another"}
+                                           f"{lin[3]}^2 hierarchy; one batch, per-problem parameter groups"}
+        mg.close()
     return out
 
 

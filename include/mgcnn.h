@@ -111,6 +111,10 @@ typedef struct {
                            mg_train_step_coarse                                          */
   int net_arch;         /* MG_SMOOTH_CNN: mg_net_arch; parameter sets hold
                            mg_net_param_count(net_arch) floats                           */
+  int net_per_problem;  /* MG_NET_LINEAR only: 1 -- net_params holds max(1, net_levels)
+                           sets for each problem of the batch, [nprob][sets][54] in batch
+                           order (Sec. 6 trains one smoother per problem); 0 -- one group
+                           of sets shared by every problem                               */
 } mg_options;
 
 typedef enum {

@@ -27,7 +27,8 @@ class mg_options(ctypes.Structure):
     _fields_ = [("smoother", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("omega", ctypes.c_float), ("coarsest_n", ctypes.c_int), ("conv_bf16", ctypes.c_int),
                 ("cluster_tail", ctypes.c_int), ("train_cycles", ctypes.c_int), ("train_checkpoint", ctypes.c_int),
-                ("net_levels", ctypes.c_int), ("smoother_transpose", ctypes.c_int), ("net_arch", ctypes.c_int)]
+                ("net_levels", ctypes.c_int), ("smoother_transpose", ctypes.c_int), ("net_arch", ctypes.c_int),
+                ("net_per_problem", ctypes.c_int)]
 
 
 class MGError(RuntimeError):
@@ -139,9 +140,10 @@ def problems_array(problems: list[dict]):
 
 def options(smoother: int = MG_SMOOTH_JACOBI, omega: float = 2.0 / 3.0, coarsest_n: int = 3,
             conv_bf16: int = 0, cluster_tail: int = 1, train_cycles: int = 1, train_checkpoint: int = 0,
-            net_levels: int = 0, smoother_transpose: int = 0, net_arch: int = 0) -> mg_options:
+            net_levels: int = 0, smoother_transpose: int = 0, net_arch: int = 0,
+            net_per_problem: int = 0) -> mg_options:
     return mg_options(smoother, 1, 1, omega, coarsest_n, conv_bf16, cluster_tail, train_cycles, train_checkpoint,
-                      net_levels, smoother_transpose, net_arch)
+                      net_levels, smoother_transpose, net_arch, net_per_problem)
 
 
 def mg_workspace_size(probs, nprob: int, opts: mg_options) -> int:

@@ -67,6 +67,9 @@ mg_status make_plan(const mg_problem* probs, int nprob, const mg_options* o, Pla
   if (o->net_levels < 0 || o->net_levels > MG_MAXL) return fail(MG_ERR_INVALID_ARG, "net_levels out of range");
   if (o->net_arch != MG_NET_CONV && o->net_arch != MG_NET_FC && o->net_arch != MG_NET_LINEAR)
     return fail(MG_ERR_INVALID_ARG, "unknown net_arch");
+  if (o->net_per_problem != 0 && o->net_per_problem != 1) return fail(MG_ERR_INVALID_ARG, "net_per_problem must be 0 or 1");
+  if (o->net_per_problem && !(o->smoother == MG_SMOOTH_CNN && o->net_arch == MG_NET_LINEAR))
+    return fail(MG_ERR_UNSUPPORTED, "per-problem parameter sets need the linear smoother (MG_NET_LINEAR)");
   const int n = probs[0].n;
   if (!is_pow2m1(n) || n < o->coarsest_n || n > 8191)
     return fail(MG_ERR_INVALID_ARG, "n = %d must be 2^m - 1 in [coarsest_n, 8191]", n);
@@ -267,7 +270,8 @@ static size_t carve(const Plan& P, const mg_options& o, void* base, mg_ctx* ctx)
   float* tscr = (o.smoother_transpose && P.hk == HK_FIELD) ? c.take<float>((size_t)9 * P.n0 * P.n0) : nullptr;
   // the linear smoother: its weights per level (shared by all problems) and three scratch
   // vectors of level-0 size for the chain and the up-sweep residual
-  float* lin = P.hk == HK_LINEAR ? c.take<float>((size_t)MG_NPARAMS_LIN * (P.L > 1 ? P.L - 1 : 1)) : nullptr;
+  const int lin_lev = P.L > 1 ? P.L - 1 : 1, lin_groups = o.net_per_problem ? P.nprob : 1;
+  float* lin = P.hk == HK_LINEAR ? c.take<float>((size_t)MG_NPARAMS_LIN * lin_lev * lin_groups) : nullptr;
   float* lin_s[3] = {nullptr, nullptr, nullptr};
   if (P.hk == HK_LINEAR)
     for (int k = 0; k < 3; ++k) lin_s[k] = c.take<float>((size_t)P.nprob * P.n0 * pitch_of(P.n0));
@@ -310,7 +314,7 @@ static size_t carve(const Plan& P, const mg_options& o, void* base, mg_ctx* ctx)
       if (l < P.L - 1) {
         if (P.hk == HK_FIELD) v.W = c.take<float>(9 * nn);
         else if (P.hk == HK_TABLE) v.W = c.take<float>((size_t)9 * v.T * v.T);
-        else if (P.hk == HK_LINEAR) v.W = lin + (size_t)MG_NPARAMS_LIN * l;
+        else if (P.hk == HK_LINEAR) v.W = lin + (size_t)MG_NPARAMS_LIN * ((o.net_per_problem ? p * lin_lev : 0) + l);
       }
     }
     d.m = P.nl[P.L - 1] * P.nl[P.L - 1];
@@ -339,7 +343,6 @@ static size_t carve(const Plan& P, const mg_options& o, void* base, mg_ctx* ctx)
     ctx->args.lin_wa = lin_s[0];
     ctx->args.lin_wb = lin_s[1];
     ctx->args.lin_t = lin_s[2];
-    for (int l = 0; l < MG_MAXL; ++l) ctx->args.lin_phi[l] = (lin && l + 1 < P.L) ? lin + (size_t)MG_NPARAMS_LIN * l : nullptr;
   }
   return c.off + 256;
 }
@@ -458,12 +461,16 @@ mg_status mg_setup(const mg_problem* problems, int nprob, const mg_options* opts
     CK(launch_coarsest_factor(a.probs, P.nprob, P.L, P.sk, ctx->d_fail, s));
     if (P.hk == HK_LINEAR && P.L > 1) {
       // the network is the chain itself: level l takes parameter set min(l, net_levels - 1)
-      for (int l = 0; l + 1 < P.L; ++l) {
-        const int set = opts->net_levels <= 1 ? 0 : (l < opts->net_levels ? l : opts->net_levels - 1);
-        CK(cudaMemcpyAsync(ctx->lin + (size_t)MG_NPARAMS_LIN * l, net_params + (size_t)set * MG_NPARAMS_LIN,
-                           MG_NPARAMS_LIN * sizeof(float), cudaMemcpyDeviceToDevice, s));
-      }
-      if (opts->smoother_transpose) CK(launch_transpose_linear(ctx->lin, P.L - 1, s));
+      // of the context's group, or of its problem's group with net_per_problem
+      const int nsets = opts->net_levels > 1 ? opts->net_levels : 1, groups = opts->net_per_problem ? P.nprob : 1;
+      for (int g = 0; g < groups; ++g)
+        for (int l = 0; l + 1 < P.L; ++l) {
+          const int set = l < nsets ? l : nsets - 1;
+          CK(cudaMemcpyAsync(ctx->lin + (size_t)MG_NPARAMS_LIN * ((size_t)g * (P.L - 1) + l),
+                             net_params + (size_t)MG_NPARAMS_LIN * ((size_t)g * nsets + set),
+                             MG_NPARAMS_LIN * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        }
+      if (opts->smoother_transpose) CK(launch_transpose_linear(ctx->lin, groups * (P.L - 1), s));
     } else if (P.hk != HK_JACOBI && P.L > 1) {
       // jobs level-major, so that every level can take its own parameter set
       std::vector<NetJob> jobs;

@@ -125,7 +125,6 @@ struct CycleArgs {
   // HK_LINEAR: scratch vectors of the chain of convolutions and the up-sweep residual,
   // each [nprob][n_l][pitch_l] on the level being processed (sized for level 0)
   float *lin_wa, *lin_wb, *lin_t;
-  const float* lin_phi[MG_MAXL];  // HK_LINEAR: the 54 weights of each smoothed level
   const LevelArrays* arrays;      // base pointers of the level arrays (host copy)
 };
 

@@ -3,8 +3,8 @@
 //
 //   H v = f_5(f_4(f_3(f_2(f_1(v))))) + f_6(v),  f_k(u)(x) = sum_t phi_k[t] u(x + d_t),
 //
-// six 3x3 kernels per level shared by every point and every problem, each layer's input
-// zero outside the grid.  The levels of side > MG_TAIL_N run as plain batched kernels over
+// six 3x3 kernels per level shared by every point (and by every problem of a context, or
+// one group per problem with net_per_problem), each layer's input zero outside the grid.  The levels of side > MG_TAIL_N run as plain batched kernels over
 // the pitched level arrays, one thread per point with the neighbours through L1 (a pass of
 // the chain reads and writes 8 bytes per point; the level arrays of the batch are mostly
 // L2-resident at the sizes the paper uses); the levels below run in the one-CTA tail
@@ -65,14 +65,18 @@ __device__ __forceinline__ float apply_A_at(const LevelDev& L, const float (&s)[
 }
 
 // ------------------------------------------------------------------ chain passes
-// MODE 0: dst = f_k(src); 1: dst = f_5(src) + f_6(src2); 2: dst += f_5(src) + f_6(src2).
-// With pfix >= 0 the arrays are problem pfix's dense n x n vectors (pitch = n).
+// MODE 0: dst = f_k(src); 1: dst = f_5(src) + f_6(src2); 2: dst += f_5(src) + f_6(src2),
+// with the weights of level l of the CTA's problem.  With pfix >= 0 the arrays are problem
+// pfix's dense n x n vectors (pitch = n).
 template <int MODE>
-__global__ void __launch_bounds__(LT) k_lin_conv(const float* __restrict__ phi, int k, int n, int pitch,
+__global__ void __launch_bounds__(LT) k_lin_conv(const ProbDev* __restrict__ probs, int l, int k, int n, int pitch,
                                                  const ProbState* __restrict__ state, const int* __restrict__ act,
                                                  int pfix, const float* src, const float* src2, float* dst) {
   pdl_trigger();
   const int q = blockIdx.x * LT + threadIdx.x;
+  // the weights never change after setup, so they load before the wait
+  const int pw = pfix >= 0 ? pfix : (act ? act[blockIdx.y] : blockIdx.y);
+  const float* phi = probs[pw].lv[l].W;
   float w[9], w6[9];
 #pragma unroll
   for (int t = 0; t < 9; ++t) {
@@ -265,14 +269,14 @@ static inline int nlaunch(const CycleArgs& a) { return (a.active && a.nactive > 
 static cudaError_t lin_H(const CycleArgs& a, int l, const float* u, float* dst, bool acc, int cls) {
   const int n = a.nl[l], pitch = a.arrays->pitch[l];
   const dim3 grid((n * n + LT - 1) / LT, nlaunch(a));
-  const float* phi = a.lin_phi[l];
+  const ProbDev* probs = a.probs;
   const float* src = u;
   cudaError_t e = cudaSuccess;
   for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
     float* out = (k & 1) ? a.lin_wb : a.lin_wa;
     a.prof->launches++;
     a.prof->begin(cls, a.stream);
-    e = launch_pdl(a.pdl, k_lin_conv<0>, grid, dim3(LT), 0, a.stream, phi, k, n, pitch, (const ProbState*)a.state,
+    e = launch_pdl(a.pdl, k_lin_conv<0>, grid, dim3(LT), 0, a.stream, probs, l, k, n, pitch, (const ProbState*)a.state,
                    a.active, -1, src, (const float*)nullptr, out);
     a.prof->end(a.stream);
     src = out;
@@ -280,10 +284,10 @@ static cudaError_t lin_H(const CycleArgs& a, int l, const float* u, float* dst, 
   if (e != cudaSuccess) return e;
   a.prof->launches++;
   a.prof->begin(cls, a.stream);
-  e = acc ? launch_pdl(a.pdl, k_lin_conv<2>, grid, dim3(LT), 0, a.stream, phi, 4, n, pitch, (const ProbState*)a.state,
-                       a.active, -1, src, u, dst)
-          : launch_pdl(a.pdl, k_lin_conv<1>, grid, dim3(LT), 0, a.stream, phi, 4, n, pitch, (const ProbState*)a.state,
-                       a.active, -1, src, u, dst);
+  e = acc ? launch_pdl(a.pdl, k_lin_conv<2>, grid, dim3(LT), 0, a.stream, probs, l, 4, n, pitch,
+                       (const ProbState*)a.state, a.active, -1, src, u, dst)
+          : launch_pdl(a.pdl, k_lin_conv<1>, grid, dim3(LT), 0, a.stream, probs, l, 4, n, pitch,
+                       (const ProbState*)a.state, a.active, -1, src, u, dst);
   a.prof->end(a.stream);
   return e;
 }
@@ -364,7 +368,7 @@ cudaError_t launch_cycle_linear(const CycleArgs& a, float rtol, int max_cycles, 
 cudaError_t launch_smoother_linear(const CycleArgs& a, int p, int l, const float* f, float* u, int nsteps) {
   const int n = a.nl[l];
   const int nb = (n * n + LT - 1) / LT;
-  const float* phi = a.lin_phi[l];
+  const ProbDev* probs = a.probs;
   const float* t = a.arrays->r[l] + (size_t)p * n * a.arrays->pitch[l];
   for (int s = 0; s < nsteps; ++s) {
     cudaError_t e = launch_level_residual(a, p, l, f, u);
@@ -372,10 +376,10 @@ cudaError_t launch_smoother_linear(const CycleArgs& a, int p, int l, const float
     const float* src = t;
     for (int k = 0; k < 4; ++k) {
       float* out = (k & 1) ? a.lin_wb : a.lin_wa;
-      k_lin_conv<0><<<nb, LT, 0, a.stream>>>(phi, k, n, n, nullptr, nullptr, p, src, nullptr, out);
+      k_lin_conv<0><<<nb, LT, 0, a.stream>>>(probs, l, k, n, n, nullptr, nullptr, p, src, nullptr, out);
       src = out;
     }
-    k_lin_conv<2><<<nb, LT, 0, a.stream>>>(phi, 4, n, n, nullptr, nullptr, p, src, t, u);
+    k_lin_conv<2><<<nb, LT, 0, a.stream>>>(probs, l, 4, n, n, nullptr, nullptr, p, src, t, u);
     a.prof->launches += 5;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

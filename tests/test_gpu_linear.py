@@ -239,3 +239,22 @@ def test_fgmres_with_the_linear_smoother_matches_oracle():
     assert np.max(np.abs(gh[0][:k] - oh[:k]) / oh[:k]) <= 1e-3
     x = xh[0].double().cpu().numpy() + xl[0].double().cpu().numpy()
     assert np.linalg.norm(f32(b_np) - O.apply(st0, x)) / np.linalg.norm(f32(b_np)) < 1e-6
+
+
+def test_per_problem_linear_smoothers_batch_like_separate_contexts():
+    """net_per_problem: each problem of one context smooths with its own group of per-level
+    sets; the batched solve equals one context per problem (same kernels, same order)."""
+    n = 255
+    pe = [(0.01, math.pi / 12), (0.01, math.pi / 4), (0.2, 2.0)]
+    groups = np.stack([lin_params(3, O.q1_rotated_stencil(e, t).reshape(9)[4], seed=40 + i)
+                       for i, (e, t) in enumerate(pe)])
+    b = torch.from_numpy(np.stack([inputs.rhs_uniform(60 + i, n) for i in range(len(pe))])).cuda().contiguous()
+    mg = S.MultigridSolver([S.rotated(n, e, t) for e, t in pe], "cnn", torch.from_numpy(groups).cuda(),
+                           net_arch="linear", per_problem=True)
+    _, _, gh, gc, _ = mg.solve(b, rtol=1e-8, max_cycles=3000)
+    for i, (e, t) in enumerate(pe):
+        one = S.MultigridSolver([S.rotated(n, e, t)], "cnn", torch.from_numpy(groups[i]).cuda(), net_arch="linear")
+        _, _, h1, c1, _ = one.solve(b[i:i + 1].contiguous(), rtol=1e-8, max_cycles=3000)
+        assert int(gc[i]) == int(c1[0])
+        k = int(c1[0]) + 1
+        assert np.array_equal(gh[i][:k], h1[0][:k])
