@@ -158,6 +158,7 @@ struct mg_ctx {
   int* d_active = nullptr;      // compacted list of problems still iterating
   float* tscratch = nullptr;    // kernel transposition scratch (smoother_transpose)
   float* lin = nullptr;         // the linear smoother's weights, [L-1][MG_NPARAMS_LIN]
+  LinMaps lin_maps;             // its tensor maps (levels above the tail)
   std::vector<int> h_active;
   LevelArrays arrays;
   TileMaps maps;
@@ -426,6 +427,11 @@ mg_status mg_setup(const mg_problem* problems, int nprob, const mg_options* opts
   if (P.lstar > 0 && !build_tile_maps(ctx->maps, ctx->arrays, P.nprob, P.lstar)) {
     delete ctx;
     return fail(MG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the level arrays");
+  }
+  a.lin_maps = &ctx->lin_maps;
+  if (P.hk == HK_LINEAR && P.lstar > 0 && !build_lin_maps(ctx->lin_maps, ctx->arrays, a.lin_t, P.nprob, P.lstar)) {
+    delete ctx;
+    return fail(MG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the linear smoother's arrays");
   }
   // level-0 stencils
   for (int p = 0; p < nprob; ++p) {

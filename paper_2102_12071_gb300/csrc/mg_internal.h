@@ -102,6 +102,16 @@ struct LevelArrays {
   float* r0b;             // second level-0 residual: cycles alternate r[0] and r0b
 };
 
+// TMA maps of the linear smoother's tiled chain (mg_linear.cu): the vector a smoothing
+// applies H to, with the chain's five-point halo
+struct LinMaps {
+  CUtensorMap r0a, r0b;    // level 0: the two residual arrays (cycle parity)
+  CUtensorMap r[MG_MAXL];  // levels >= 1: r_l
+  CUtensorMap t[MG_MAXL];  // the up-sweep residual (scratch lin_t with level l's shape)
+  CUtensorMap e0;          // level 0's correction, boxed like the iterate (k_update_residual)
+};
+bool build_lin_maps(LinMaps& M, const LevelArrays& A, float* lin_t, int nprob, int lstar);
+
 struct CycleArgs {
   ProbDev* probs;
   ProbState* state;
@@ -126,7 +136,9 @@ struct CycleArgs {
   // each [nprob][n_l][pitch_l] on the level being processed (sized for level 0)
   float *lin_wa, *lin_wb, *lin_t;
   const LevelArrays* arrays;      // base pointers of the level arrays (host copy)
+  const LinMaps* lin_maps;        // HK_LINEAR: tensor maps of the tiled chain (host copy)
 };
+
 
 // one network evaluation: a stencil field (st) or a constant stencil (s) on an n x n grid
 struct NetJob {
@@ -177,6 +189,13 @@ cudaError_t launch_residual(const CycleArgs& a, float rtol, int max_cycles);
 // kernel reads both with halos, so it must not overwrite them in place
 cudaError_t launch_cycle(const CycleArgs& a, float rtol, int max_cycles, int parity);
 bool build_tile_maps(TileMaps& maps, const LevelArrays& arrays, int nprob, int lstar);
+// level 0 after an up-sweep run elsewhere: x += e_0 and the residual of the new iterate
+// with the stopping test, on the arrays of cycle `parity` (mg_tiles.cu); e0: tensor map of
+// e_0 with the iterate's box (tile_res_box)
+cudaError_t launch_update_residual(const CycleArgs& a, const CUtensorMap& e0, float rtol, int max_cycles, int parity);
+void tile_res_box(int* bw, int* bh);
+// 3-D tensor map {x, y, problem} of a pitched level array, box bw x bh x 1 (mg_tiles.cu)
+bool make_map(CUtensorMap* m, float* base, int n, int pitch, int nprob, int bw, int bh);
 cudaError_t launch_pack(const float* src, float* dst, int n, int pitch, int nprob, cudaStream_t s);
 // dst <- src_a, or src_b for the problems whose count of applied cycles is odd
 cudaError_t launch_unpack(const float* src_a, const float* src_b, const ProbState* state, float* dst, int n, int pitch,

@@ -4,28 +4,33 @@
 //   H v = f_5(f_4(f_3(f_2(f_1(v))))) + f_6(v),  f_k(u)(x) = sum_t phi_k[t] u(x + d_t),
 //
 // six 3x3 kernels per level shared by every point (and by every problem of a context, or
-// one group per problem with net_per_problem), each layer's input zero outside the grid.  The levels of side > MG_TAIL_N run as plain batched kernels over
-// the pitched level arrays, one thread per point with the neighbours through L1 (a pass of
-// the chain reads and writes 8 bytes per point; the level arrays of the batch are mostly
-// L2-resident at the sizes the paper uses); the levels below run in the one-CTA tail
-// (mg_tail.cuh), which holds the chain in shared memory.  The level-0 update and the
-// compensated residual with the stopping test follow the same conventions as the tiled
-// path (iterate and residual alternate between two arrays by cycle parity).
+// one group per problem with net_per_problem), each layer's input zero outside the grid.
+// On the levels of side > MG_TAIL_N every smoothing is one tiled kernel (k_lin_Htile): a
+// TMA copy brings the input tile with the chain's five-point halo into shared memory, the
+// five layers run there on shrinking regions (register windows, three shared loads per
+// point), and only H v leaves the SM -- 8 bytes per point instead of 8 per layer.  The
+// residual-and-restriction, prolongation, update and compensated residual are point
+// kernels on a 2-D grid (32 x 8 threads per CTA, problem in blockIdx.z).  The levels below
+// run in the one-CTA tail (mg_tail.cuh), which holds the chain in shared memory.  The
+// level-0 update and the compensated residual with the stopping test follow the same
+// conventions as the tiled path (iterate and residual alternate between two arrays by
+// cycle parity).
 #include "mg_common.cuh"
 #include "mg_internal.h"
 #include "mg_ops.cuh"
 #include "mg_reduce.cuh"
+#include "mg_tile.cuh"
 #include "mg_tma.cuh"
 
 namespace mg {
 
 constexpr int LT = 256;  // threads per CTA of the point kernels
-constexpr int TB = 32;   // tile side of the residual/norm kernel (matches the partial slots)
+constexpr int PX = 32, PY = 8, RY = 4;  // point kernels: 32 x 8 threads, 4 rows each (32 x 32 points)
 
-// problem of this CTA (-1: none) and the offset of its slice of a [nprob][n][pitch] array
-__device__ __forceinline__ int lin_problem(const ProbState* state, const int* act, int pfix) {
+// problem of this CTA (-1: none); the launch index is blockIdx.y or blockIdx.z
+__device__ __forceinline__ int lin_problem(const ProbState* state, const int* act, int pfix, int idx) {
   if (pfix >= 0) return pfix;
-  const int p = act ? act[blockIdx.y] : blockIdx.y;
+  const int p = act ? act[idx] : idx;
   return st_active(state + p) ? p : -1;
 }
 
@@ -84,7 +89,7 @@ __global__ void __launch_bounds__(LT) k_lin_conv(const ProbDev* __restrict__ pro
     w6[t] = MODE ? phi[45 + t] : 0.f;
   }
   pdl_wait();
-  const int p = lin_problem(state, act, pfix);
+  const int p = lin_problem(state, act, pfix, blockIdx.y);
   if (p < 0 || q >= n * n) return;
   const size_t off = pfix >= 0 ? 0 : (size_t)p * n * pitch;
   const int i = q / n, j = q % n;
@@ -94,158 +99,217 @@ __global__ void __launch_bounds__(LT) k_lin_conv(const ProbDev* __restrict__ pro
   dst[o] = MODE == 2 ? dst[o] + h : h;
 }
 
-// r_{l+1} = P^T (r - A e), one thread per coarse point: the residual on the 3 x 3 fine
-// points of its restriction stencil (fine 2I+1+d, all inside the grid) from e's 5 x 5
+// r_{l+1} = P^T (r - A e), a thread per coarse point of RY rows: the residual on the 3 x 3
+// fine points of its restriction stencil (fine 2I+1+d, all inside the grid) from e's 5 x 5
 // neighbourhood, then the restriction of Sec. 6.1 in the tile kernels' summation order.
 template <int SK>
 __global__ void __launch_bounds__(LT) k_lin_restrict(const ProbDev* __restrict__ probs,
                                                      const ProbState* __restrict__ state, const int* __restrict__ act,
                                                      int l, const float* r, const float* e, float* rc) {
   pdl_trigger();
-  const int Q = blockIdx.x * LT + threadIdx.x;
   pdl_wait();
-  const int p = lin_problem(state, act, -1);
+  const int p = lin_problem(state, act, -1, blockIdx.z);
   if (p < 0) return;
   const LevelDev L = probs[p].lv[l];
   const int n = L.n, pitch = L.pitch, nc = probs[p].lv[l + 1].n, pc = probs[p].lv[l + 1].pitch;
-  if (Q >= nc * nc) return;
+  const int J = blockIdx.x * PX + threadIdx.x;
+  if (J >= nc) return;
   float s[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) s[k] = (SK == SK_CONST) ? L.s[k] : 0.f;
-  const int I = Q / nc, J = Q % nc;
   const size_t off = (size_t)p * n * pitch;
   const float* rp = r + off;
   const float* ep = e + off;
-  float sv[9];
+  for (int y = 0; y < RY; ++y) {
+    const int I = blockIdx.y * PY * RY + y * PY + threadIdx.y;
+    if (I >= nc) break;
+    float sv[9];
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
+    for (int a = 0; a < 3; ++a)
 #pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const int fi = 2 * I + a, fj = 2 * J + b;
-      sv[3 * a + b] = rp[(size_t)fi * pitch + fj] - apply_A_at<SK>(L, s, ep, pitch, fi, fj);
-    }
-  rc[(size_t)p * nc * pc + (size_t)I * pc + J] = restrict_at(sv + 4, 3);
+      for (int b = 0; b < 3; ++b) {
+        const int fi = 2 * I + a, fj = 2 * J + b;
+        sv[3 * a + b] = rp[(size_t)fi * pitch + fj] - apply_A_at<SK>(L, s, ep, pitch, fi, fj);
+      }
+    rc[(size_t)p * nc * pc + (size_t)I * pc + J] = restrict_at(sv + 4, 3);
+  }
 }
 
-// e_l += P e_{l+1} (bilinear, Sec. 6.1), one thread per fine point, coarse values zero
-// outside the coarse grid; the arithmetic of prolong_at
+// e_l += P e_{l+1} (bilinear, Sec. 6.1), a thread per fine point of RY rows, coarse values
+// zero outside the coarse grid; the arithmetic of prolong_at
 __global__ void __launch_bounds__(LT) k_lin_prolong(const ProbDev* __restrict__ probs,
                                                     const ProbState* __restrict__ state, const int* __restrict__ act,
                                                     int l, float* e, const float* ec) {
   pdl_trigger();
-  const int q = blockIdx.x * LT + threadIdx.x;
   pdl_wait();
-  const int p = lin_problem(state, act, -1);
+  const int p = lin_problem(state, act, -1, blockIdx.z);
   if (p < 0) return;
   const int n = probs[p].lv[l].n, pitch = probs[p].lv[l].pitch;
   const int nc = probs[p].lv[l + 1].n, pc = probs[p].lv[l + 1].pitch;
-  if (q >= n * n) return;
-  const int i = q / n, j = q % n;
+  const int j = blockIdx.x * PX + threadIdx.x;
+  if (j >= n) return;
   const float* c = ec + (size_t)p * nc * pc;
-  const int Ia = (i - 1) >> 1, Ja = (j - 1) >> 1;
-  const float b00 = tap_at(c, pc, nc, Ia, Ja), b01 = tap_at(c, pc, nc, Ia, Ja + 1);
-  const float b10 = tap_at(c, pc, nc, Ia + 1, Ja), b11 = tap_at(c, pc, nc, Ia + 1, Ja + 1);
-  float v;
-  if (i & 1) v = (j & 1) ? b00 : 0.5f * (b00 + b01);
-  else v = (j & 1) ? 0.5f * (b00 + b10) : 0.25f * ((b00 + b01) + (b10 + b11));
-  e[(size_t)p * n * pitch + (size_t)i * pitch + j] += v;
+  float* ep = e + (size_t)p * n * pitch;
+  const int Ja = (j - 1) >> 1;
+  for (int y = 0; y < RY; ++y) {
+    const int i = blockIdx.y * PY * RY + y * PY + threadIdx.y;
+    if (i >= n) break;
+    const int Ia = (i - 1) >> 1;
+    const float b00 = tap_at(c, pc, nc, Ia, Ja), b01 = tap_at(c, pc, nc, Ia, Ja + 1);
+    const float b10 = tap_at(c, pc, nc, Ia + 1, Ja), b11 = tap_at(c, pc, nc, Ia + 1, Ja + 1);
+    float v;
+    if (i & 1) v = (j & 1) ? b00 : 0.5f * (b00 + b01);
+    else v = (j & 1) ? 0.5f * (b00 + b10) : 0.25f * ((b00 + b01) + (b10 + b11));
+    ep[(size_t)i * pitch + j] += v;
+  }
 }
 
-// t = r - A e on one level
+// t = r - A e on one level, a thread per point of RY rows
 template <int SK>
 __global__ void __launch_bounds__(LT) k_lin_residual(const ProbDev* __restrict__ probs,
                                                      const ProbState* __restrict__ state, const int* __restrict__ act,
                                                      int l, const float* r, const float* e, float* t) {
   pdl_trigger();
-  const int q = blockIdx.x * LT + threadIdx.x;
   pdl_wait();
-  const int p = lin_problem(state, act, -1);
+  const int p = lin_problem(state, act, -1, blockIdx.z);
   if (p < 0) return;
   const LevelDev L = probs[p].lv[l];
   const int n = L.n, pitch = L.pitch;
-  if (q >= n * n) return;
-  float s[9];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) s[k] = (SK == SK_CONST) ? L.s[k] : 0.f;
-  const int i = q / n, j = q % n;
-  const size_t off = (size_t)p * n * pitch, o = off + (size_t)i * pitch + j;
-  t[o] = r[o] - apply_A_at<SK>(L, s, e + off, pitch, i, j);
-}
-
-// x_out = x_in + e_0 in float-float (the update of the fused level-0 kernel)
-__global__ void __launch_bounds__(LT) k_lin_xupdate(const ProbDev* __restrict__ probs,
-                                                    const ProbState* __restrict__ state, const int* __restrict__ act,
-                                                    const float* e, const float* xh_in, const float* xl_in,
-                                                    float* xh_out, float* xl_out) {
-  pdl_trigger();
-  const int q = blockIdx.x * LT + threadIdx.x;
-  pdl_wait();
-  const int p = lin_problem(state, act, -1);
-  if (p < 0) return;
-  const int n = probs[p].lv[0].n, pitch = probs[p].lv[0].pitch;
-  if (q >= n * n) return;
-  const size_t o = (size_t)p * n * pitch + (size_t)(q / n) * pitch + q % n;
-  float hi = xh_in[o], lo = xl_in[o], sum, err;
-  two_sum(hi, e[o], sum, err);
-  err += lo;
-  fast_two_sum(sum, err, hi, lo);
-  xh_out[o] = hi;
-  xl_out[o] = lo;
-}
-
-// r = b - A (x_hi + x_lo) (Dot2, the taps in index order), ||r||^2 per 32 x 32 tile into
-// the partial slots and, in the last CTA of a problem, the stopping test
-template <int SK>
-__global__ void __launch_bounds__(LT) k_lin_residual0(const ProbDev* __restrict__ probs, ProbState* __restrict__ state,
-                                                      const int* __restrict__ act, float* __restrict__ partials,
-                                                      int ntiles_max, float rtol, int max_cycles, const float* xh,
-                                                      const float* xl, const float* b, float* rout) {
-  pdl_trigger();
-  pdl_wait();
-  const int p = lin_problem(state, act, -1);
-  if (p < 0) return;
-  const LevelDev L = probs[p].lv[0];
-  const int n = L.n, pitch = L.pitch;
-  const int ntx = (n + TB - 1) / TB, ntiles = ntx * ntx, tile = blockIdx.x;
-  if (tile >= ntiles) return;
-  const int R0 = (tile / ntx) * TB, C0 = (tile % ntx) * TB;
+  const int j = blockIdx.x * PX + threadIdx.x;
+  if (j >= n) return;
   float s[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) s[k] = (SK == SK_CONST) ? L.s[k] : 0.f;
   const size_t off = (size_t)p * n * pitch;
-  const float *xh_p = xh + off, *xl_p = xl + off;
-  const int j = C0 + (threadIdx.x & 31);
-  float acc = 0.f;
-  for (int k = 0; k < TB / (LT / 32); ++k) {
-    const int i = R0 + (threadIdx.x >> 5) * (TB / (LT / 32)) + k;
-    if (i >= n || j >= n) continue;
-    const size_t o = (size_t)i * pitch + j;
-    float a[9];
-    if (SK == SK_CONST) {
-#pragma unroll
-      for (int t = 0; t < 9; ++t) a[t] = s[t];
-    } else {
-      const size_t nn = (size_t)n * n, qq = (size_t)i * n + j;
-#pragma unroll
-      for (int t = 0; t < 9; ++t) a[t] = __ldg(L.st + t * nn + qq);
-    }
-    float hi = b[off + o], lo = 0.f;
-#pragma unroll
-    for (int t = 0; t < 9; ++t) {
-      const int ii = i + t / 3 - 1, jj = j + t % 3 - 1;
-      if ((unsigned)ii < (unsigned)n && (unsigned)jj < (unsigned)n) {
-        const size_t on = (size_t)ii * pitch + jj;
-        dot2_sub(a[t], xh_p[on], xl_p[on], hi, lo);
-      }
-    }
-    const float rv = hi + lo;
-    rout[off + o] = rv;
-    acc = fmaf(rv, rv, acc);
+  for (int y = 0; y < RY; ++y) {
+    const int i = blockIdx.y * PY * RY + y * PY + threadIdx.y;
+    if (i >= n) break;
+    const size_t o = off + (size_t)i * pitch + j;
+    t[o] = r[o] - apply_A_at<SK>(L, s, e + off, pitch, i, j);
   }
-  float rhi, rlo;
-  if (block_partial_and_last<LT>(acc, partials + (size_t)p * ntiles_max, &state[p].counter, ntiles, tile, rhi, rlo)) {
-    if (threadIdx.x == 0) decide(state[p], rhi, rlo, rtol, max_cycles);
+}
+
+// ------------------------------------------------------------------ the tiled chain
+// One CTA per 32 x 32 output tile.  Buffers share one origin, the tile's corner minus
+// (5 rows, 8 columns) -- the TMA box starts 8 columns left so that its x is 16-byte
+// aligned -- and a row stride of 48; layer k (k = 1..4) covers the tile grown by 5 - k
+// points, the output the tile itself.
+constexpr int HT = 32, HH = 5, HX = 48, HR = HT + 2 * HH;
+
+__device__ __forceinline__ bool lin_inside(int i, int j, int n) {
+  return (unsigned)i < (unsigned)n && (unsigned)j < (unsigned)n;
+}
+
+// out = f(in) on the region of side S centred on the tile (zero outside the grid when
+// MASK), K rows per thread walking down a column with a 3x3 register window
+template <int S, int K, bool MASK>
+__device__ __forceinline__ void lin_layer(const float* in, float* out, const float* wsm, int R0, int C0, int n) {
+  constexpr int NS = (S + K - 1) / K, o = (HR - S) / 2;
+  static_assert(S * NS <= LT, "layer needs more threads than the CTA has");
+  const int t = threadIdx.x;
+  if (t >= S * NS) return;
+  float w[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) w[k] = wsm[k];
+  const int tj = t % S, t0 = (t / S) * K, c = o + 3 + tj;
+  const float* src = in + (o + t0) * HX + c;
+  Win v;
+  v.load_ab(src, HX);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (t0 + k < S) {
+      v.load_c(src + k * HX, HX);
+      float val = dot9(w, v);
+      if (MASK && !lin_inside(R0 - HH + o + t0 + k, C0 - 8 + c, n)) val = 0.f;
+      out[(o + t0 + k) * HX + c] = val;
+      v.shift();
+    }
   }
+}
+
+// dst (=, or += with ACC) f_5(w_4) + f_6(u) on the tile's points inside the grid: one
+// window and one kernel live at a time (f_5 over w_4 first, then f_6 over u)
+template <bool ACC>
+__device__ __forceinline__ void lin_out(const float* w4, const float* u, const float* ph, int R0, int C0, int n,
+                                        float* dst, int pitch) {
+  constexpr int K = 4, o = HH;
+  const int tj = threadIdx.x % HT, t0 = (threadIdx.x / HT) * K, c = o + 3 + tj;
+  float h[K];
+  float w[9];
+  Win v;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) w[k] = ph[36 + k];
+  v.load_ab(w4 + (o + t0) * HX + c, HX);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    v.load_c(w4 + (o + t0 + k) * HX + c, HX);
+    h[k] = dot9(w, v);
+    v.shift();
+  }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) w[k] = ph[45 + k];
+  v.load_ab(u + (o + t0) * HX + c, HX);
+  const int j = C0 + tj;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    v.load_c(u + (o + t0 + k) * HX + c, HX);
+    const int i = R0 + t0 + k;
+    if (lin_inside(i, j, n)) {
+      const float hv = h[k] + dot9(w, v);
+      float* d = dst + (size_t)i * pitch + j;
+      *d = ACC ? *d + hv : hv;
+    }
+    v.shift();
+  }
+}
+
+template <bool MASK, bool ACC>
+__device__ __forceinline__ void lin_chain(float* U, float* A, float* Bf, const float* ph, int R0, int C0, int n,
+                                          float* dst, int pitch) {
+  lin_layer<40, 7, MASK>(U, A, ph, R0, C0, n);
+  __syncthreads();
+  lin_layer<38, 7, MASK>(A, Bf, ph + 9, R0, C0, n);
+  __syncthreads();
+  lin_layer<36, 6, MASK>(Bf, A, ph + 18, R0, C0, n);
+  __syncthreads();
+  lin_layer<34, 5, MASK>(A, Bf, ph + 27, R0, C0, n);
+  __syncthreads();
+  lin_out<ACC>(Bf, U, ph, R0, C0, n, dst, pitch);
+}
+
+// dst (=, or += with ACC) H u on level l; mu: the tensor map of u's level array
+template <bool ACC>
+__global__ void __launch_bounds__(LT, 6) k_lin_Htile(const __grid_constant__ CUtensorMap mu,
+                                                     const ProbDev* __restrict__ probs, ProbState* __restrict__ state,
+                                                     const int* __restrict__ act, int l, float* __restrict__ dst) {
+  pdl_trigger();
+  const int p = act ? act[blockIdx.y] : blockIdx.y;
+  const LevelDev L = probs[p].lv[l];
+  const int n = L.n, pitch = L.pitch, ntx = (n + HT - 1) / HT;
+  const int tile = blockIdx.x;
+  if (tile >= ntx * ntx) return;
+  const int R0 = (tile / ntx) * HT, C0 = (tile % ntx) * HT;
+  __shared__ __align__(128) float U[HR * HX];
+  __shared__ __align__(128) float A[HR * HX];
+  __shared__ __align__(128) float Bf[HR * HX];
+  __shared__ float ph[MG_NPARAMS_LIN];
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x < MG_NPARAMS_LIN) ph[threadIdx.x] = L.W[threadIdx.x];  // weights never change
+  pdl_wait();
+  if (!st_active(state + p)) return;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    mbar_arrive_expect_tx(&bar, HR * HX * sizeof(float));
+    tma_load_3d(U, &mu, &bar, C0 - 8, R0 - HH, p);
+  }
+  __syncthreads();
+  if (!tile_wait(&bar, state[p])) return;
+  float* d = dst + (size_t)p * n * pitch;
+  if (R0 >= HH && C0 >= HH && R0 + HT + HH <= n && C0 + HT + HH <= n)
+    lin_chain<false, ACC>(U, A, Bf, ph, R0, C0, n, d, pitch);
+  else
+    lin_chain<true, ACC>(U, A, Bf, ph, R0, C0, n, d, pitch);
 }
 
 // phi[l] <- the parameters of H^T: (f_5 .. f_1 f_6 reversed)^T = f_1^T .. f_5^T + f_6^T,
@@ -264,53 +328,43 @@ __global__ void k_lin_transpose(float* phi, int nlev) {
 // ---------------------------------------------------------------- launchers
 static inline int nlaunch(const CycleArgs& a) { return (a.active && a.nactive > 0) ? a.nactive : a.nprob; }
 
-// one application of H on level l over the launch set: dst (=, or += with acc) H u,
-// through the scratch vectors a.lin_wa / a.lin_wb
-static cudaError_t lin_H(const CycleArgs& a, int l, const float* u, float* dst, bool acc, int cls) {
-  const int n = a.nl[l], pitch = a.arrays->pitch[l];
-  const dim3 grid((n * n + LT - 1) / LT, nlaunch(a));
-  const ProbDev* probs = a.probs;
-  const float* src = u;
-  cudaError_t e = cudaSuccess;
-  for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
-    float* out = (k & 1) ? a.lin_wb : a.lin_wa;
-    a.prof->launches++;
-    a.prof->begin(cls, a.stream);
-    e = launch_pdl(a.pdl, k_lin_conv<0>, grid, dim3(LT), 0, a.stream, probs, l, k, n, pitch, (const ProbState*)a.state,
-                   a.active, -1, src, (const float*)nullptr, out);
-    a.prof->end(a.stream);
-    src = out;
-  }
-  if (e != cudaSuccess) return e;
+static dim3 point_grid(int n, int np) { return dim3((n + PX - 1) / PX, (n + PY * RY - 1) / (PY * RY), np); }
+
+// dst (=, or += with acc) H u on level l over the launch set: one tiled kernel
+static cudaError_t lin_H(const CycleArgs& a, int l, const CUtensorMap& mu, float* dst, bool acc, int cls) {
+  const int nt = (a.nl[l] + HT - 1) / HT;
+  const dim3 grid(nt * nt, nlaunch(a));
   a.prof->launches++;
   a.prof->begin(cls, a.stream);
-  e = acc ? launch_pdl(a.pdl, k_lin_conv<2>, grid, dim3(LT), 0, a.stream, probs, l, 4, n, pitch,
-                       (const ProbState*)a.state, a.active, -1, src, u, dst)
-          : launch_pdl(a.pdl, k_lin_conv<1>, grid, dim3(LT), 0, a.stream, probs, l, 4, n, pitch,
-                       (const ProbState*)a.state, a.active, -1, src, u, dst);
+  const cudaError_t e =
+      acc ? launch_pdl(a.pdl, k_lin_Htile<true>, grid, dim3(LT), 0, a.stream, mu, (const ProbDev*)a.probs, a.state,
+                       a.active, l, dst)
+          : launch_pdl(a.pdl, k_lin_Htile<false>, grid, dim3(LT), 0, a.stream, mu, (const ProbDev*)a.probs, a.state,
+                       a.active, l, dst);
   a.prof->end(a.stream);
   return e;
 }
 
 cudaError_t launch_cycle_linear(const CycleArgs& a, float rtol, int max_cycles, int parity) {
   const LevelArrays& A = *a.arrays;
+  const LinMaps& M = *a.lin_maps;
   const int ls = a.lstar, np = nlaunch(a);
   const ProbDev* probs = a.probs;
   const ProbState* cst = a.state;
   cudaError_t e = cudaSuccess;
   auto level_r = [&](int l) -> float* { return l == 0 ? (parity ? a.r0b : a.r0a) : A.r[l]; };
+  auto level_rmap = [&](int l) -> const CUtensorMap& { return l == 0 ? (parity ? M.r0b : M.r0a) : M.r[l]; };
   for (int l = 0; l < ls && e == cudaSuccess; ++l) {
     const int cls = l == 0 ? PK_DOWN0 : PK_DOWN;
-    e = lin_H(a, l, level_r(l), A.e[l], false, cls);  // pre-smoothing from e = 0
+    e = lin_H(a, l, level_rmap(l), A.e[l], false, cls);  // pre-smoothing from e = 0
     if (e != cudaSuccess) break;
-    const int nc = a.nl[l + 1];
-    const dim3 grid((nc * nc + LT - 1) / LT, np);
     a.prof->launches++;
     a.prof->begin(cls, a.stream);
+    const dim3 gc = point_grid(a.nl[l + 1], np);
     e = a.sk == SK_CONST
-            ? launch_pdl(a.pdl, k_lin_restrict<SK_CONST>, grid, dim3(LT), 0, a.stream, probs, cst, a.active, l,
+            ? launch_pdl(a.pdl, k_lin_restrict<SK_CONST>, gc, dim3(PX, PY), 0, a.stream, probs, cst, a.active, l,
                          (const float*)level_r(l), (const float*)A.e[l], A.r[l + 1])
-            : launch_pdl(a.pdl, k_lin_restrict<SK_FIELD>, grid, dim3(LT), 0, a.stream, probs, cst, a.active, l,
+            : launch_pdl(a.pdl, k_lin_restrict<SK_FIELD>, gc, dim3(PX, PY), 0, a.stream, probs, cst, a.active, l,
                          (const float*)level_r(l), (const float*)A.e[l], A.r[l + 1]);
     a.prof->end(a.stream);
   }
@@ -318,49 +372,40 @@ cudaError_t launch_cycle_linear(const CycleArgs& a, float rtol, int max_cycles, 
   e = launch_tail(a);
   for (int l = ls - 1; l >= 0 && e == cudaSuccess; --l) {
     const int cls = l == 0 ? PK_UP0 : PK_UP;
-    const int n = a.nl[l];
-    const dim3 grid((n * n + LT - 1) / LT, np);
+    const dim3 grid = point_grid(a.nl[l], np);
     a.prof->launches += 2;
     a.prof->begin(cls, a.stream);
-    e = launch_pdl(a.pdl, k_lin_prolong, grid, dim3(LT), 0, a.stream, probs, cst, a.active, l, A.e[l],
+    e = launch_pdl(a.pdl, k_lin_prolong, grid, dim3(PX, PY), 0, a.stream, probs, cst, a.active, l, A.e[l],
                    (const float*)A.e[l + 1]);
     a.prof->end(a.stream);
     if (e != cudaSuccess) break;
     a.prof->begin(cls, a.stream);
     e = a.sk == SK_CONST
-            ? launch_pdl(a.pdl, k_lin_residual<SK_CONST>, grid, dim3(LT), 0, a.stream, probs, cst, a.active, l,
+            ? launch_pdl(a.pdl, k_lin_residual<SK_CONST>, grid, dim3(PX, PY), 0, a.stream, probs, cst, a.active, l,
                          (const float*)level_r(l), (const float*)A.e[l], a.lin_t)
-            : launch_pdl(a.pdl, k_lin_residual<SK_FIELD>, grid, dim3(LT), 0, a.stream, probs, cst, a.active, l,
+            : launch_pdl(a.pdl, k_lin_residual<SK_FIELD>, grid, dim3(PX, PY), 0, a.stream, probs, cst, a.active, l,
                          (const float*)level_r(l), (const float*)A.e[l], a.lin_t);
     a.prof->end(a.stream);
     if (e != cudaSuccess) break;
-    e = lin_H(a, l, a.lin_t, A.e[l], true, cls);  // post-smoothing
+    e = lin_H(a, l, M.t[l], A.e[l], true, cls);  // post-smoothing
   }
   if (e != cudaSuccess || ls == 0) return e;
-  // level 0: the float-float update of the iterate, then its compensated residual
-  const int n = a.n0;
-  const float* xh_in = parity ? a.xh0b : a.xh0;
-  const float* xl_in = parity ? a.xl0b : a.xl0;
-  float* xh_out = parity ? a.xh0 : a.xh0b;
-  float* xl_out = parity ? a.xl0 : a.xl0b;
-  float* rnew = parity ? a.r0a : a.r0b;
-  a.prof->launches += 2;
-  a.prof->begin(PK_UP0, a.stream);
-  e = launch_pdl(a.pdl, k_lin_xupdate, dim3((n * n + LT - 1) / LT, np), dim3(LT), 0, a.stream, probs, cst, a.active,
-                 (const float*)A.e[0], xh_in, xl_in, xh_out, xl_out);
-  a.prof->end(a.stream);
-  if (e != cudaSuccess) return e;
-  const int nt = (n + TB - 1) / TB;
-  a.prof->begin(PK_UP0, a.stream);
-  e = a.sk == SK_CONST
-          ? launch_pdl(a.pdl, k_lin_residual0<SK_CONST>, dim3(nt * nt, np), dim3(LT), 0, a.stream, probs, a.state,
-                       a.active, a.partials, a.ntiles_max, rtol, max_cycles, (const float*)xh_out,
-                       (const float*)xl_out, a.b0, rnew)
-          : launch_pdl(a.pdl, k_lin_residual0<SK_FIELD>, dim3(nt * nt, np), dim3(LT), 0, a.stream, probs, a.state,
-                       a.active, a.partials, a.ntiles_max, rtol, max_cycles, (const float*)xh_out,
-                       (const float*)xl_out, a.b0, rnew);
-  a.prof->end(a.stream);
-  return e;
+  // level 0: the float-float update of the iterate and its compensated residual, one
+  // tiled kernel shared with the tiled path's conventions
+  return launch_update_residual(a, M.e0, rtol, max_cycles, parity);
+}
+
+bool build_lin_maps(LinMaps& M, const LevelArrays& A, float* lin_t, int nprob, int lstar) {
+  bool ok = make_map(&M.r0a, A.r[0], A.n[0], A.pitch[0], nprob, HX, HR) &&
+            make_map(&M.r0b, A.r0b, A.n[0], A.pitch[0], nprob, HX, HR);
+  int bw = 0, bh = 0;
+  tile_res_box(&bw, &bh);
+  ok = ok && make_map(&M.e0, A.e[0], A.n[0], A.pitch[0], nprob, bw, bh);
+  for (int l = 0; ok && l < lstar; ++l) {
+    ok = make_map(&M.t[l], lin_t, A.n[l], A.pitch[l], nprob, HX, HR);
+    if (ok && l >= 1) ok = make_map(&M.r[l], A.r[l], A.n[l], A.pitch[l], nprob, HX, HR);
+  }
+  return ok;
 }
 
 // nsteps times u += H (f - A u) on level l of problem p (dense n_l x n_l vectors): the

@@ -22,6 +22,7 @@
 #include "mg_internal.h"
 #include "mg_ops.cuh"
 #include "mg_reduce.cuh"
+#include "mg_tile.cuh"
 #include "mg_tma.cuh"
 
 namespace mg {
@@ -55,38 +56,6 @@ constexpr int INNER = 8;
 
 __device__ __forceinline__ bool inner_tile(int R0, int C0, int n) {
   return R0 >= INNER && C0 >= INNER && R0 + TB + INNER <= n && C0 + TB + INNER <= n;
-}
-
-// 3x3 neighbourhood of a point in registers: rows above (a), at (b) and below (c) it,
-// columns left (0), centre (1) and right (2); tap k = 3*(di+1) + (dj+1) of a stencil
-// multiplies a0 a1 a2 b0 b1 b2 c0 c1 c2 in that order.
-struct Win {
-  float a0, a1, a2, b0, b1, b2, c0, c1, c2;
-  __device__ __forceinline__ void load_ab(const float* c, int ts) {
-    a0 = c[-ts - 1]; a1 = c[-ts]; a2 = c[-ts + 1];
-    b0 = c[-1]; b1 = c[0]; b2 = c[1];
-  }
-  __device__ __forceinline__ void load_c(const float* c, int ts) {
-    c0 = c[ts - 1]; c1 = c[ts]; c2 = c[ts + 1];
-  }
-  __device__ __forceinline__ void shift() {
-    a0 = b0; a1 = b1; a2 = b2;
-    b0 = c0; b1 = c1; b2 = c2;
-  }
-};
-
-// sum of w_k v_k, centre first (the order of stencil_apply)
-__device__ __forceinline__ float dot9(const float (&w)[9], const Win& v) {
-  float acc = w[4] * v.b1;
-  acc = fmaf(w[0], v.a0, acc);
-  acc = fmaf(w[1], v.a1, acc);
-  acc = fmaf(w[2], v.a2, acc);
-  acc = fmaf(w[3], v.b0, acc);
-  acc = fmaf(w[5], v.b2, acc);
-  acc = fmaf(w[6], v.c0, acc);
-  acc = fmaf(w[7], v.c1, acc);
-  acc = fmaf(w[8], v.c2, acc);
-  return acc;
 }
 
 // A v at grid point (i, j)
@@ -137,21 +106,6 @@ __device__ __forceinline__ void load_table(const LevelDev& L, bool in, float* wt
     const int cnt = 9 * T * T;
     for (int t = threadIdx.x; t < cnt; t += NT) wtab[t] = L.W[t];
   }
-}
-
-// Waits for the CTA's copies; on expiry marks the problem timed out (status 4) and waits
-// once more, bounded, for copies still in flight.  Returns false in every thread then.
-__device__ __forceinline__ bool tile_wait(uint64_t* bar, ProbState& st) {
-  const bool ok = mbar_wait(bar, 0);
-  if (__syncthreads_or(!ok)) {
-    if (threadIdx.x == 0) {
-      st.status = 4;
-      st.active = 0;
-    }
-    mbar_wait(bar, 0);
-    return false;
-  }
-  return true;
 }
 
 __device__ __forceinline__ bool inside(int i, int j, int n) { return (unsigned)i < (unsigned)n && (unsigned)j < (unsigned)n; }
@@ -635,6 +589,66 @@ __global__ void __launch_bounds__(NT, SK == SK_CONST ? 8 : 4) k_up0(const __grid
   }
 }
 
+// ------------------------------------------------------- k_update_residual
+// The level-0 end of a cycle whose up-sweep ran in other kernels (the linear smoother's
+// path): x += e_0 in float-float on the tile and its one-point halo in shared memory, then
+// the compensated residual of the new iterate on the tile (storing the new iterate), its
+// norm partial and, in the last CTA of a problem, the stopping test.
+template <int SK>
+__global__ void __launch_bounds__(NT) k_update_residual(const __grid_constant__ ResMaps X,
+                                                        const __grid_constant__ CUtensorMap E,
+                                                        const ProbDev* __restrict__ probs, ProbState* __restrict__ state,
+                                                        float* __restrict__ partials, int ntiles_max, float rtol,
+                                                        int max_cycles, float* __restrict__ xhi, float* __restrict__ xlo,
+                                                        float* __restrict__ rnew, const float* __restrict__ b0,
+                                                        const int* __restrict__ act) {
+  pdl_trigger();
+  const int p = act ? act[blockIdx.y] : blockIdx.y;
+  const LevelDev L = probs[p].lv[0];
+  const int n = L.n;
+  const int ntx = (n + TB - 1) / TB, ntiles = ntx * ntx;
+  const int tile = blockIdx.x;
+  if (tile >= ntiles) return;
+  const int R0 = (tile / ntx) * TB, C0 = (tile % ntx) * TB;
+  __shared__ __align__(128) float xh[RES_H * XW];
+  __shared__ __align__(128) float xl[RES_H * XW];
+  __shared__ __align__(128) float es[RES_H * XW];
+  __shared__ __align__(8) uint64_t bar;
+  float s[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) s[k] = (SK == SK_CONST) ? L.s[k] : 0.f;
+  pdl_wait();
+  if (!st_active(state + p)) return;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    mbar_arrive_expect_tx(&bar, 3 * RES_H * XW * sizeof(float));
+    tma_load_3d(xh, &X.xh, &bar, C0 - 4, R0 - 1, p);
+    tma_load_3d(xl, &X.xl, &bar, C0 - 4, R0 - 1, p);
+    tma_load_3d(es, &E, &bar, C0 - 4, R0 - 1, p);
+  }
+  __syncthreads();
+  if (!tile_wait(&bar, state[p])) return;
+  // the box is zero outside the grid in all three arrays, so the update keeps it zero there
+  for (int q = threadIdx.x; q < RES_H * XW; q += NT) {
+    float hi = xh[q], lo = xl[q], sum, err;
+    two_sum(hi, es[q], sum, err);
+    err += lo;
+    fast_two_sum(sum, err, hi, lo);
+    xh[q] = hi;
+    xl[q] = lo;
+  }
+  __syncthreads();
+  const size_t po = (size_t)p * n * L.pitch;
+  const float acc = inner_tile(R0, C0, n)
+                        ? residual_tile<SK, true>(L, s, xh, xl, nullptr, R0, C0, rnew + po, xhi + po, xlo + po, b0 + po)
+                        : residual_tile<SK, false>(L, s, xh, xl, nullptr, R0, C0, rnew + po, xhi + po, xlo + po, b0 + po);
+  float rhi, rlo;
+  if (block_partial_and_last<NT>(acc, partials + (size_t)p * ntiles_max, &state[p].counter, ntiles, tile, rhi, rlo)) {
+    if (threadIdx.x == 0) decide(state[p], rhi, rlo, rtol, max_cycles);
+  }
+}
+
 // -------------------------------------------------------------- pack / unpack
 // dense [nprob][n][n] <-> pitched [nprob][n][pitch]; src == nullptr packs zeros
 __global__ void k_pack(const float* __restrict__ src, float* __restrict__ dst, int n, int pitch) {
@@ -683,7 +697,12 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // 3-D map {x = n, y = n, z = nprob} over a pitched level array, box bw x bh x 1
-static bool make_map(CUtensorMap* m, float* base, int n, int pitch, int nprob, int bw, int bh) {
+void tile_res_box(int* bw, int* bh) {
+  *bw = XW;
+  *bh = RES_H;
+}
+
+bool make_map(CUtensorMap* m, float* base, int n, int pitch, int nprob, int bw, int bh) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return false;
   const cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)nprob};
@@ -742,6 +761,26 @@ cudaError_t launch_residual(const CycleArgs& a, float rtol, int max_cycles) {
   else
     e = launch_pdl(a.pdl, k_residual<SK_FIELD>, grid, dim3(NT), 0, a.stream, a.maps->res, (const ProbDev*)a.probs, a.state,
                    a.partials, a.ntiles_max, rtol, max_cycles, a.active);
+  a.prof->end(a.stream);
+  return e;
+}
+
+cudaError_t launch_update_residual(const CycleArgs& a, const CUtensorMap& e0, float rtol, int max_cycles, int parity) {
+  const int nt = tiles_per_side(a.n0);
+  dim3 grid(nt * nt, nlaunch(a));
+  const ResMaps& X = parity ? a.maps->resb : a.maps->res;
+  float* rnew = parity ? a.r0a : a.r0b;
+  float* xhn = parity ? a.xh0 : a.xh0b;
+  float* xln = parity ? a.xl0 : a.xl0b;
+  a.prof->launches++;
+  a.prof->begin(PK_UP0, a.stream);
+  cudaError_t e;
+  if (a.sk == SK_CONST)
+    e = launch_pdl(a.pdl, k_update_residual<SK_CONST>, grid, dim3(NT), 0, a.stream, X, e0, (const ProbDev*)a.probs,
+                   a.state, a.partials, a.ntiles_max, rtol, max_cycles, xhn, xln, rnew, a.b0, a.active);
+  else
+    e = launch_pdl(a.pdl, k_update_residual<SK_FIELD>, grid, dim3(NT), 0, a.stream, X, e0, (const ProbDev*)a.probs,
+                   a.state, a.partials, a.ntiles_max, rtol, max_cycles, xhn, xln, rnew, a.b0, a.active);
   a.prof->end(a.stream);
   return e;
 }
