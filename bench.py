@@ -145,6 +145,25 @@ def load_adaptive():
     return np.load(path).astype(np.float32)
 
 
+def load_linear_batch(params, n: int):
+    """Per-problem linear smoothers trained for exactly this batch's (eps, theta) pairs
+    (train --linear --batch), as per-problem groups [nprob, levels(n) - 1, 54], or None."""
+    path = os.path.join(os.path.dirname(WEIGHTS), f"linear_batch{len(params)}.npz")
+    if not os.path.exists(path):
+        return None
+    import numpy as np
+    import torch
+
+    from paper_2102_12071_gb300 import train as T
+
+    z = np.load(path)
+    if len(z["eps"]) != len(params) or any(abs(float(z["eps"][i]) - e) > 1e-12 or abs(float(z["thetas"][i]) - t) > 1e-12
+                                           for i, (e, t) in enumerate(params)):
+        return None
+    W = z["params"].astype(np.float32)
+    return torch.stack([T.adaptive_params(W[i], n, int(z["n_fine"])) for i in range(len(params))])
+
+
 def load_linear():
     """Shared-kernel linear smoothers (Sec. 6) trained per problem by Algorithm 2: (params
     [thetas, levels, 54], thetas, eps, n_fine) or None."""
@@ -592,6 +611,13 @@ def main():
     if adaptive is not None:
         arms["cnn_adaptive"] = S.MultigridSolver(problems, "cnn", net_params=T.adaptive_params(adaptive, n).cuda())
     # the paper's method: per-level smoothers trained coarse to fine (Algorithm 2)
+    # the paper's alpha-CNN of Sec. 6: a linear shared-kernel smoother per problem and level,
+    # trained by Algorithm 2 for each (eps, theta) of this seeded batch
+    # (trained for rank 0's batch only: other ranks' batches differ, and every rank must
+    # time the same arms between its barriers)
+    lin = load_linear_batch(params, n) if world == 1 else None
+    if lin is not None:
+        arms["linear_alpha"] = S.MultigridSolver(problems, "cnn", lin.cuda(), net_arch="linear", per_problem=True)
     headline = "cnn_adaptive" if "cnn_adaptive" in arms else ("cnn" if "cnn" in arms else "jacobi")
     sizes = arms["jacobi"].sizes
     b = torch.from_numpy(b_host).cuda().contiguous()

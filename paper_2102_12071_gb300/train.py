@@ -370,6 +370,9 @@ def main():
                          "(eps = --eps, theta in --thetas); saves an .npz of params [thetas, levels, 54]")
     ap.add_argument("--eps", type=float, default=0.01)
     ap.add_argument("--thetas", default="1,2,3,4,5", help="angles in units of pi/12")
+    ap.add_argument("--batch", type=int, default=0, metavar="NPROB",
+                    help="with --linear: one smoother for each problem (eps, theta) of the seeded rotated batch of "
+                         "this size (inputs.rotated_params with the batch seed) instead of --eps / --thetas")
     args = ap.parse_args()
     from . import build
 
@@ -378,20 +381,24 @@ def main():
         if not args.adaptive:
             ap.error("--linear trains per level: give --adaptive N_FINE")
         t0 = time.time()
-        thetas = [float(k) * math.pi / 12 for k in args.thetas.split(",")]
+        if args.batch:
+            pairs = [(float(e), float(t)) for e, t in inputs.rotated_params(inputs.SEED_PARAMS, args.batch)]
+        else:
+            pairs = [(args.eps, float(k) * math.pi / 12) for k in args.thetas.split(",")]
         sets = []
-        for th in thetas:
+        for e, th in pairs:
             at = AdaptiveTrainer(n_fine=args.adaptive, per_size=1, nvec=64, steps_per_level=args.steps, lr=args.lr,
-                                 seed=args.seed, conv_bf16=False, net_arch="linear", problem=(args.eps, th))
+                                 seed=args.seed, conv_bf16=False, net_arch="linear", problem=(e, th))
             at.train()
             sets.append(torch.stack([at.params[n] for n in at.sizes]).cpu().numpy().astype(np.float32))
             h = at.losses[at.sizes[0]]
-            print(f"theta {th:.4f}: finest-level loss {np.mean(h[:10]):.5f} -> {np.mean(h[-10:]):.5f} "
+            print(f"eps {e:.4g} theta {th:.4f}: finest-level loss {np.mean(h[:10]):.5f} -> {np.mean(h[-10:]):.5f} "
                   f"({time.time() - t0:.1f} s)", flush=True)
-        out = args.out or os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights",
-                                       f"linear_eps{args.eps:g}.npz")
+        name = f"linear_batch{args.batch}.npz" if args.batch else f"linear_eps{args.eps:g}.npz"
+        out = args.out or os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", name)
         os.makedirs(os.path.dirname(out), exist_ok=True)
-        np.savez(out, params=np.stack(sets), thetas=np.array(thetas), eps=args.eps, n_fine=args.adaptive)
+        eps_out = np.array([e for e, _ in pairs]) if args.batch else args.eps
+        np.savez(out, params=np.stack(sets), thetas=np.array([t for _, t in pairs]), eps=eps_out, n_fine=args.adaptive)
         print("saved", out, "levels", at.sizes)
         return
     if args.adaptive:
