@@ -190,19 +190,26 @@ __global__ void __launch_bounds__(LT) k_lin_residual(const ProbDev* __restrict__
 }
 
 // ------------------------------------------------------------------ the tiled chain
-// One CTA per 32 x 32 output tile.  Buffers share one origin, the tile's corner minus
-// (5 rows, 8 columns) -- the TMA box starts 8 columns left so that its x is 16-byte
-// aligned -- and a row stride of 48; layer k (k = 1..4) covers the tile grown by 5 - k
-// points, the output the tile itself.
-constexpr int HT = 32, HH = 5, HX = 48, HR = HT + 2 * HH;
+// One CTA per 32 x 32 output tile.  Coordinates below are in the frame of the input tile
+// u: row 0 = grid row R0 - 5, column 0 = grid column C0 - 8 (the TMA box starts 8 columns
+// left so that its x is 16-byte aligned).  Layer k (k = 1..4) covers the tile grown by
+// 5 - k points, rows and columns [k, 42 - k) and [k + 3, 45 - k); the output covers rows
+// [5, 37), columns [8, 40).  Every layer writes a buffer of its own whose row stride makes
+// the next layer's reads conflict-free: a warp covers the end of one strip row and the
+// start of the row K below it, and K * stride = S (mod 32) puts the second run of lanes on
+// the banks right after the first.
+constexpr int HT = 32, HH = 5, HR = HT + 2 * HH;  // tile, halo, rows of u
+constexpr int HXU = 56;                            // u: 7 * 56 = 40 (mod 32), read by layer 1
+constexpr int HX1 = 42, HX2 = 38, HX3 = 43, HX4 = 34;  // layer outputs (7*42=38, 6*38=36, 6*43=34)
 
 __device__ __forceinline__ bool lin_inside(int i, int j, int n) {
   return (unsigned)i < (unsigned)n && (unsigned)j < (unsigned)n;
 }
 
-// out = f(in) on the region of side S centred on the tile (zero outside the grid when
-// MASK), K rows per thread walking down a column with a 3x3 register window
-template <int S, int K, bool MASK>
+// out = f(in) on the layer's region of side S (zero outside the grid when MASK), K rows
+// per thread walking down a column with a 3x3 register window; in / out: buffers of row
+// stride XI / XO whose element 0 sits at frame position (RI, CI) / (RO, CO)
+template <int S, int K, bool MASK, int XI, int RI, int CI, int XO, int RO, int CO>
 __device__ __forceinline__ void lin_layer(const float* in, float* out, const float* wsm, int R0, int C0, int n) {
   constexpr int NS = (S + K - 1) / K, o = (HR - S) / 2;
   static_assert(S * NS <= LT, "layer needs more threads than the CTA has");
@@ -211,17 +218,18 @@ __device__ __forceinline__ void lin_layer(const float* in, float* out, const flo
   float w[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) w[k] = wsm[k];
-  const int tj = t % S, t0 = (t / S) * K, c = o + 3 + tj;
-  const float* src = in + (o + t0) * HX + c;
+  const int tj = t % S, t0 = (t / S) * K, r = o + t0, c = o + 3 + tj;
+  const float* src = in + (r - RI) * XI + (c - CI);
+  float* dst = out + (r - RO) * XO + (c - CO);
   Win v;
-  v.load_ab(src, HX);
+  v.load_ab(src, XI);
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     if (t0 + k < S) {
-      v.load_c(src + k * HX, HX);
+      v.load_c(src + k * XI, XI);
       float val = dot9(w, v);
-      if (MASK && !lin_inside(R0 - HH + o + t0 + k, C0 - 8 + c, n)) val = 0.f;
-      out[(o + t0 + k) * HX + c] = val;
+      if (MASK && !lin_inside(R0 - HH + r + k, C0 - 8 + c, n)) val = 0.f;
+      dst[k * XO] = val;
       v.shift();
     }
   }
@@ -232,27 +240,29 @@ __device__ __forceinline__ void lin_layer(const float* in, float* out, const flo
 template <bool ACC>
 __device__ __forceinline__ void lin_out(const float* w4, const float* u, const float* ph, int R0, int C0, int n,
                                         float* dst, int pitch) {
-  constexpr int K = 4, o = HH;
-  const int tj = threadIdx.x % HT, t0 = (threadIdx.x / HT) * K, c = o + 3 + tj;
+  constexpr int K = 4;
+  const int tj = threadIdx.x % HT, t0 = (threadIdx.x / HT) * K, r = HH + t0, c = 8 + tj;
   float h[K];
   float w[9];
   Win v;
 #pragma unroll
   for (int k = 0; k < 9; ++k) w[k] = ph[36 + k];
-  v.load_ab(w4 + (o + t0) * HX + c, HX);
+  const float* a = w4 + (r - 4) * HX4 + (c - 7);
+  v.load_ab(a, HX4);
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    v.load_c(w4 + (o + t0 + k) * HX + c, HX);
+    v.load_c(a + k * HX4, HX4);
     h[k] = dot9(w, v);
     v.shift();
   }
 #pragma unroll
   for (int k = 0; k < 9; ++k) w[k] = ph[45 + k];
-  v.load_ab(u + (o + t0) * HX + c, HX);
+  const float* b = u + r * HXU + c;
+  v.load_ab(b, HXU);
   const int j = C0 + tj;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    v.load_c(u + (o + t0 + k) * HX + c, HX);
+    v.load_c(b + k * HXU, HXU);
     const int i = R0 + t0 + k;
     if (lin_inside(i, j, n)) {
       const float hv = h[k] + dot9(w, v);
@@ -264,17 +274,17 @@ __device__ __forceinline__ void lin_out(const float* w4, const float* u, const f
 }
 
 template <bool MASK, bool ACC>
-__device__ __forceinline__ void lin_chain(float* U, float* A, float* Bf, const float* ph, int R0, int C0, int n,
-                                          float* dst, int pitch) {
-  lin_layer<40, 7, MASK>(U, A, ph, R0, C0, n);
+__device__ __forceinline__ void lin_chain(const float* U, float* B1, float* B2, float* B3, float* B4, const float* ph,
+                                          int R0, int C0, int n, float* dst, int pitch) {
+  lin_layer<40, 7, MASK, HXU, 0, 0, HX1, 1, 4>(U, B1, ph, R0, C0, n);
   __syncthreads();
-  lin_layer<38, 7, MASK>(A, Bf, ph + 9, R0, C0, n);
+  lin_layer<38, 7, MASK, HX1, 1, 4, HX2, 2, 5>(B1, B2, ph + 9, R0, C0, n);
   __syncthreads();
-  lin_layer<36, 6, MASK>(Bf, A, ph + 18, R0, C0, n);
+  lin_layer<36, 6, MASK, HX2, 2, 5, HX3, 3, 6>(B2, B3, ph + 18, R0, C0, n);
   __syncthreads();
-  lin_layer<34, 5, MASK>(A, Bf, ph + 27, R0, C0, n);
+  lin_layer<34, 6, MASK, HX3, 3, 6, HX4, 4, 7>(B3, B4, ph + 27, R0, C0, n);
   __syncthreads();
-  lin_out<ACC>(Bf, U, ph, R0, C0, n, dst, pitch);
+  lin_out<ACC>(B4, U, ph, R0, C0, n, dst, pitch);
 }
 
 // dst (=, or += with ACC) H u on level l; mu: the tensor map of u's level array
@@ -289,9 +299,8 @@ __global__ void __launch_bounds__(LT, 6) k_lin_Htile(const __grid_constant__ CUt
   const int tile = blockIdx.x;
   if (tile >= ntx * ntx) return;
   const int R0 = (tile / ntx) * HT, C0 = (tile % ntx) * HT;
-  __shared__ __align__(128) float U[HR * HX];
-  __shared__ __align__(128) float A[HR * HX];
-  __shared__ __align__(128) float Bf[HR * HX];
+  __shared__ __align__(128) float U[HR * HXU];
+  __shared__ float B1[40 * HX1], B2[38 * HX2], B3[36 * HX3], B4[34 * HX4];
   __shared__ float ph[MG_NPARAMS_LIN];
   __shared__ __align__(8) uint64_t bar;
   if (threadIdx.x < MG_NPARAMS_LIN) ph[threadIdx.x] = L.W[threadIdx.x];  // weights never change
@@ -300,16 +309,16 @@ __global__ void __launch_bounds__(LT, 6) k_lin_Htile(const __grid_constant__ CUt
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     fence_mbar_init();
-    mbar_arrive_expect_tx(&bar, HR * HX * sizeof(float));
+    mbar_arrive_expect_tx(&bar, HR * HXU * sizeof(float));
     tma_load_3d(U, &mu, &bar, C0 - 8, R0 - HH, p);
   }
   __syncthreads();
   if (!tile_wait(&bar, state[p])) return;
   float* d = dst + (size_t)p * n * pitch;
   if (R0 >= HH && C0 >= HH && R0 + HT + HH <= n && C0 + HT + HH <= n)
-    lin_chain<false, ACC>(U, A, Bf, ph, R0, C0, n, d, pitch);
+    lin_chain<false, ACC>(U, B1, B2, B3, B4, ph, R0, C0, n, d, pitch);
   else
-    lin_chain<true, ACC>(U, A, Bf, ph, R0, C0, n, d, pitch);
+    lin_chain<true, ACC>(U, B1, B2, B3, B4, ph, R0, C0, n, d, pitch);
 }
 
 // phi[l] <- the parameters of H^T: (f_5 .. f_1 f_6 reversed)^T = f_1^T .. f_5^T + f_6^T,
@@ -396,14 +405,14 @@ cudaError_t launch_cycle_linear(const CycleArgs& a, float rtol, int max_cycles, 
 }
 
 bool build_lin_maps(LinMaps& M, const LevelArrays& A, float* lin_t, int nprob, int lstar) {
-  bool ok = make_map(&M.r0a, A.r[0], A.n[0], A.pitch[0], nprob, HX, HR) &&
-            make_map(&M.r0b, A.r0b, A.n[0], A.pitch[0], nprob, HX, HR);
+  bool ok = make_map(&M.r0a, A.r[0], A.n[0], A.pitch[0], nprob, HXU, HR) &&
+            make_map(&M.r0b, A.r0b, A.n[0], A.pitch[0], nprob, HXU, HR);
   int bw = 0, bh = 0;
   tile_res_box(&bw, &bh);
   ok = ok && make_map(&M.e0, A.e[0], A.n[0], A.pitch[0], nprob, bw, bh);
   for (int l = 0; ok && l < lstar; ++l) {
-    ok = make_map(&M.t[l], lin_t, A.n[l], A.pitch[l], nprob, HX, HR);
-    if (ok && l >= 1) ok = make_map(&M.r[l], A.r[l], A.n[l], A.pitch[l], nprob, HX, HR);
+    ok = make_map(&M.t[l], lin_t, A.n[l], A.pitch[l], nprob, HXU, HR);
+    if (ok && l >= 1) ok = make_map(&M.r[l], A.r[l], A.n[l], A.pitch[l], nprob, HXU, HR);
   }
   return ok;
 }
