@@ -547,8 +547,13 @@ def run_profile_case(args):
     w, ad = load_weights(), load_adaptive()
     if ad is not None:
         w = T.adaptive_params(ad, args.n)
-    kind = args.smoother if args.smoother != "auto" else ("cnn" if w is not None else "jacobi")
-    mg = S.MultigridSolver(problems, kind, net_params=w.cuda() if kind == "cnn" else None)
+    if args.smoother == "linear":
+        lin = load_linear_batch(params, args.n)
+        assert lin is not None, "no per-problem linear smoothers for this batch"
+        mg = S.MultigridSolver(problems, "cnn", lin.cuda(), net_arch="linear", per_problem=True)
+    else:
+        kind = args.smoother if args.smoother != "auto" else ("cnn" if w is not None else "jacobi")
+        mg = S.MultigridSolver(problems, kind, net_params=w.cuda() if kind == "cnn" else None)
     b = torch.from_numpy(b_host).cuda().contiguous()
     x_hi, x_lo = torch.zeros_like(b), torch.zeros_like(b)
     for _ in range(args.profile_cycles):
@@ -570,7 +575,8 @@ def main():
     ap.add_argument("--roofline-cycles", type=int, default=20)
     ap.add_argument("--profile-cycles", type=int, default=0,
                     help="only set up the batch and run this many single V-cycles (for profiler captures)")
-    ap.add_argument("--smoother", default="auto", choices=["auto", "jacobi", "cnn"])
+    ap.add_argument("--smoother", default="auto", choices=["auto", "jacobi", "cnn", "linear"],
+                    help="profile case: the smoother (linear: the per-problem linear smoothers of the batch)")
     ap.add_argument("--varcoef-n", default="1023,4095", help="sides of the GRF problems, comma list (0: skip)")
     ap.add_argument("--mixed-count", type=int, default=256, help="problems in the mixed batch (0: skip)")
     ap.add_argument("--mixed-steps", type=int, default=2)
