@@ -84,7 +84,13 @@ typedef enum {
 
 typedef struct {
   int smoother;     /* mg_smoother_kind                                               */
-  int nu1, nu2;     /* pre-/post-smoothing steps per level; this build supports 1, 1  */
+  int nu1, nu2;     /* pre-/post-smoothing steps per level (Algorithm 1), 1..8: the
+                       first pre-smoothing step is e = H r from e = 0, every further
+                       step e += H (r - A e).  Other than 1 only with MG_SMOOTH_JACOBI or
+                       MG_NET_LINEAR (MG_ERR_UNSUPPORTED otherwise); such contexts run the
+                       levels above 63 in batched level kernels, not the fused tiles
+                       (Sec. 6: six Jacobi steps per smoothing equal the six convolutions
+                       of the linear network in cost)                                   */
   float omega;      /* Jacobi weight (2/3 in the paper, Sec. 6.1); also the Jacobi part
                        of the network output W = (omega*delta + NN)/D                   */
   int coarsest_n;   /* stop coarsening at this size (this build: 3)                  */

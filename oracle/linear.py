@@ -132,9 +132,11 @@ class LinearMultigrid:
     """Galerkin hierarchy of st0 with the shared-kernel linear smoother on every level but
     the coarsest; phis[l] (or phis[-1] for deeper levels) smooths level l."""
 
-    def __init__(self, st0, phis, coarsest_n: int = 3, fields=None):
+    def __init__(self, st0, phis, coarsest_n: int = 3, fields=None, nu1: int = 1, nu2: int = 1):
         """fields: the level operators to use instead of the Galerkin products of st0 (a
-        caller that wants another implementation's rounded coarse fields)."""
+        caller that wants another implementation's rounded coarse fields); nu1, nu2: the
+        smoothing steps before and after the coarse correction."""
+        self.nu1, self.nu2 = nu1, nu2
         if fields is not None:
             self.st = [_f64(f) for f in fields]
         else:
@@ -153,7 +155,8 @@ class LinearMultigrid:
         return u + apply_H(self.phi[l], f - apply(self.st[l], u))
 
     def _level(self, l, f, u):
-        u = self._smooth(l, f, u)                          # pre-smoothing
+        for _ in range(self.nu1):                          # pre-smoothing
+            u = self._smooth(l, f, u)
         rc = restrict(f - apply(self.st[l], u))            # r^(l+1) = P^T (f - A u)
         if l + 1 == self.L - 1:
             nc = self.n(l + 1)
@@ -161,7 +164,9 @@ class LinearMultigrid:
         else:
             uc = self._level(l + 1, rc, np.zeros_like(rc))
         u = u + prolong(uc, self.n(l))                     # u += P u^(l+1)
-        return self._smooth(l, f, u)                       # post-smoothing
+        for _ in range(self.nu2):                          # post-smoothing
+            u = self._smooth(l, f, u)
+        return u
 
     def vcycle(self, b, x) -> np.ndarray:
         b, x = _f64(b), _f64(x)

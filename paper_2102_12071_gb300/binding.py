@@ -141,8 +141,8 @@ def problems_array(problems: list[dict]):
 def options(smoother: int = MG_SMOOTH_JACOBI, omega: float = 2.0 / 3.0, coarsest_n: int = 3,
             conv_bf16: int = 0, cluster_tail: int = 1, train_cycles: int = 1, train_checkpoint: int = 0,
             net_levels: int = 0, smoother_transpose: int = 0, net_arch: int = 0,
-            net_per_problem: int = 0) -> mg_options:
-    return mg_options(smoother, 1, 1, omega, coarsest_n, conv_bf16, cluster_tail, train_cycles, train_checkpoint,
+            net_per_problem: int = 0, nu1: int = 1, nu2: int = 1) -> mg_options:
+    return mg_options(smoother, nu1, nu2, omega, coarsest_n, conv_bf16, cluster_tail, train_cycles, train_checkpoint,
                       net_levels, smoother_transpose, net_arch, net_per_problem)
 
 

@@ -48,6 +48,8 @@ namespace {
 struct Plan {
   int nprob = 0, n0 = 0, L = 0, lstar = 0, sk = SK_CONST, hk = HK_JACOBI, tail_solve = 0;
   int ctail = 0;    // levels >= lstar in one CTA cluster per problem
+  int generic = 0;  // levels above the tail in batched level kernels (mg_linear.cu)
+  int nu1 = 1, nu2 = 1;
   int lstar1 = 0;   // first level of the one-CTA tail (the fallback of the cluster tail)
   int nl[MG_MAXL] = {0};
   int ntiles_max = 0;
@@ -61,7 +63,11 @@ mg_status make_plan(const mg_problem* probs, int nprob, const mg_options* o, Pla
   if (nprob > 65535) return fail(MG_ERR_INVALID_ARG, "nprob %d > 65535", nprob);
   if (o->smoother != MG_SMOOTH_JACOBI && o->smoother != MG_SMOOTH_CNN)
     return fail(MG_ERR_INVALID_ARG, "unknown smoother %d", o->smoother);
-  if (o->nu1 != 1 || o->nu2 != 1) return fail(MG_ERR_UNSUPPORTED, "only nu1 = nu2 = 1 is implemented");
+  if (o->nu1 < 1 || o->nu2 < 1 || o->nu1 > 8 || o->nu2 > 8)
+    return fail(MG_ERR_INVALID_ARG, "nu1 and nu2 must be in [1, 8]");
+  if ((o->nu1 != 1 || o->nu2 != 1) && !(o->smoother == MG_SMOOTH_JACOBI ||
+                                        (o->smoother == MG_SMOOTH_CNN && o->net_arch == MG_NET_LINEAR)))
+    return fail(MG_ERR_UNSUPPORTED, "nu1, nu2 > 1 need the Jacobi or the linear smoother");
   if (o->coarsest_n != 3 && o->coarsest_n != 7) return fail(MG_ERR_UNSUPPORTED, "coarsest_n must be 3 or 7");
   if (!(o->omega > 0.f) || !(o->omega < 2.f)) return fail(MG_ERR_INVALID_ARG, "omega must be in (0, 2)");
   if (o->net_levels < 0 || o->net_levels > MG_MAXL) return fail(MG_ERR_INVALID_ARG, "net_levels out of range");
@@ -116,11 +122,14 @@ mg_status make_plan(const mg_problem* probs, int nprob, const mg_options* o, Pla
   while (P.lstar < L && P.nl[P.lstar] > MG_TAIL_N) ++P.lstar;
   P.lstar1 = P.lstar;
   P.tail_solve = P.lstar == 0;
+  P.nu1 = o->nu1;
+  P.nu2 = o->nu2;
+  P.generic = P.hk == HK_LINEAR || P.nu1 != 1 || P.nu2 != 1;
   const int nt = tiles_per_side(n);
   P.ntiles_max = nt * nt;
   if (tail_smem_bytes(P.nl, P.lstar, L, P.hk) > MG_TAIL_SMEM_MAX)
     return fail(MG_ERR_UNSUPPORTED, "tail does not fit in shared memory");
-  if (!P.tail_solve && o->cluster_tail && P.hk != HK_LINEAR) {
+  if (!P.tail_solve && o->cluster_tail && !P.generic) {
     int ls = 1;  // the finest level stays tiled: it carries the outer residual and update
     while (ls < L && P.nl[ls] > MG_CT_N) ++ls;
     if (ls < L && P.nl[ls] > MG_CT_SOLO && ctail_smem_bytes(P.nl, ls, L, P.hk) <= MG_CT_SMEM_MAX) {
@@ -274,7 +283,7 @@ static size_t carve(const Plan& P, const mg_options& o, void* base, mg_ctx* ctx)
   const int lin_lev = P.L > 1 ? P.L - 1 : 1, lin_groups = o.net_per_problem ? P.nprob : 1;
   float* lin = P.hk == HK_LINEAR ? c.take<float>((size_t)MG_NPARAMS_LIN * lin_lev * lin_groups) : nullptr;
   float* lin_s[3] = {nullptr, nullptr, nullptr};
-  if (P.hk == HK_LINEAR)
+  if (P.generic)
     for (int k = 0; k < 3; ++k) lin_s[k] = c.take<float>((size_t)P.nprob * P.n0 * pitch_of(P.n0));
   LevelArrays A;
   memset(&A, 0, sizeof(A));
@@ -319,6 +328,8 @@ static size_t carve(const Plan& P, const mg_options& o, void* base, mg_ctx* ctx)
       }
     }
     d.m = P.nl[P.L - 1] * P.nl[P.L - 1];
+    d.nu1 = P.nu1;
+    d.nu2 = P.nu2;
     d.chol = c.take<double>((size_t)d.m * d.m);
     if (ctx) hp[p] = d;
   }
@@ -429,7 +440,9 @@ mg_status mg_setup(const mg_problem* problems, int nprob, const mg_options* opts
     return fail(MG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the level arrays");
   }
   a.lin_maps = &ctx->lin_maps;
-  if (P.hk == HK_LINEAR && P.lstar > 0 && !build_lin_maps(ctx->lin_maps, ctx->arrays, a.lin_t, P.nprob, P.lstar)) {
+  a.nu1 = P.nu1;
+  a.nu2 = P.nu2;
+  if (P.generic && P.lstar > 0 && !build_lin_maps(ctx->lin_maps, ctx->arrays, a.lin_t, P.nprob, P.lstar)) {
     delete ctx;
     return fail(MG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the linear smoother's arrays");
   }

@@ -68,7 +68,8 @@ struct ProbDev {
   LevelDev lv[MG_MAXL];
   double* chol;        // coarsest operator, dense FP64 inverse, m x m
   int m;               // n_L^2
-  int pad_[3];
+  int nu1, nu2;        // smoothing steps before and after the coarse correction (0 read as 1)
+  int pad_;
 };
 
 struct ProbState {

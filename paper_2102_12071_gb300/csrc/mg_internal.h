@@ -136,7 +136,8 @@ struct CycleArgs {
   // each [nprob][n_l][pitch_l] on the level being processed (sized for level 0)
   float *lin_wa, *lin_wb, *lin_t;
   const LevelArrays* arrays;      // base pointers of the level arrays (host copy)
-  const LinMaps* lin_maps;        // HK_LINEAR: tensor maps of the tiled chain (host copy)
+  const LinMaps* lin_maps;        // tensor maps of the batched level path (host copy)
+  int nu1, nu2;                   // smoothing steps; other than 1 only on the batched level path
 };
 
 
@@ -221,8 +222,9 @@ cudaError_t launch_ctail(const CycleArgs& a);
 cudaError_t launch_smoother(const CycleArgs& a, int p, int l, const float* f, float* u, int nsteps);
 // t = f - A u of problem p on level l into the level's r vector (dense n_l x n_l)
 cudaError_t launch_level_residual(const CycleArgs& a, int p, int l, const float* f, const float* u);
-// the shared-kernel linear smoother (mg_linear.cu): the cycle's levels above a.lstar with
-// plain batched kernels, then the one-CTA tail; and the standalone smoother
+// the batched level path (mg_linear.cu) -- the linear smoother, and nu1, nu2 > 1 with the
+// Jacobi or the linear smoother: the cycle's levels above a.lstar in batched level kernels,
+// then the one-CTA tail; and the linear smoother's standalone application
 cudaError_t launch_cycle_linear(const CycleArgs& a, float rtol, int max_cycles, int parity);
 cudaError_t launch_smoother_linear(const CycleArgs& a, int p, int l, const float* f, float* u, int nsteps);
 // phi <- the parameters of H^T (chain reversed, kernels mirrored), nlev sets in place

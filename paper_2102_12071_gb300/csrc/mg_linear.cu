@@ -189,6 +189,31 @@ __global__ void __launch_bounds__(LT) k_lin_residual(const ProbDev* __restrict__
   }
 }
 
+// dst (=, or += with ACC) (omega / D) u: weighted Jacobi (Sec. 2.1) on the batched level
+// path (smoothing with nu1, nu2 > 1), the arithmetic of the tiled kernels' Jacobi step
+template <int SK, bool ACC>
+__global__ void __launch_bounds__(LT) k_jac_H(const ProbDev* __restrict__ probs, const ProbState* __restrict__ state,
+                                              const int* __restrict__ act, int l, float omega, const float* u,
+                                              float* dst) {
+  pdl_trigger();
+  pdl_wait();
+  const int p = lin_problem(state, act, -1, blockIdx.z);
+  if (p < 0) return;
+  const LevelDev L = probs[p].lv[l];
+  const int n = L.n, pitch = L.pitch;
+  const int j = blockIdx.x * PX + threadIdx.x;
+  if (j >= n) return;
+  const size_t off = (size_t)p * n * pitch, nn = (size_t)n * n;
+  for (int y = 0; y < RY; ++y) {
+    const int i = blockIdx.y * PY * RY + y * PY + threadIdx.y;
+    if (i >= n) break;
+    const float d = (SK == SK_CONST) ? L.s[4] : __ldg(L.st + 4 * nn + (size_t)i * n + j);
+    const size_t o = off + (size_t)i * pitch + j;
+    const float h = (omega / d) * u[o];
+    dst[o] = ACC ? dst[o] + h : h;
+  }
+}
+
 // ------------------------------------------------------------------ the tiled chain
 // One CTA per 32 x 32 output tile.  Coordinates below are in the frame of the input tile
 // u: row 0 = grid row R0 - 5, column 0 = grid column C0 - 8 (the TMA box starts 8 columns
@@ -354,10 +379,56 @@ static cudaError_t lin_H(const CycleArgs& a, int l, const CUtensorMap& mu, float
   return e;
 }
 
+// dst (=, or += with acc) H u on level l: the tiled chain (linear smoother, u one of the
+// arrays of a tensor map in LinMaps) or weighted Jacobi
+static cudaError_t smooth_H(const CycleArgs& a, int l, const float* u, const CUtensorMap& mu, float* dst, bool acc,
+                            int cls) {
+  if (a.hk == HK_LINEAR) return lin_H(a, l, mu, dst, acc, cls);
+  a.prof->launches++;
+  a.prof->begin(cls, a.stream);
+  const dim3 grid = point_grid(a.nl[l], nlaunch(a));
+  const ProbDev* probs = a.probs;
+  const ProbState* cst = a.state;
+  cudaError_t e;
+  if (a.sk == SK_CONST)
+    e = acc ? launch_pdl(a.pdl, k_jac_H<SK_CONST, true>, grid, dim3(PX, PY), 0, a.stream, probs, cst, a.active, l,
+                         a.omega, u, dst)
+            : launch_pdl(a.pdl, k_jac_H<SK_CONST, false>, grid, dim3(PX, PY), 0, a.stream, probs, cst, a.active, l,
+                         a.omega, u, dst);
+  else
+    e = acc ? launch_pdl(a.pdl, k_jac_H<SK_FIELD, true>, grid, dim3(PX, PY), 0, a.stream, probs, cst, a.active, l,
+                         a.omega, u, dst)
+            : launch_pdl(a.pdl, k_jac_H<SK_FIELD, false>, grid, dim3(PX, PY), 0, a.stream, probs, cst, a.active, l,
+                         a.omega, u, dst);
+  a.prof->end(a.stream);
+  return e;
+}
+
+// t = r - A e on level l into the scratch vector a.lin_t
+static cudaError_t level_residual(const CycleArgs& a, int l, const float* r, const float* e, int cls) {
+  a.prof->launches++;
+  a.prof->begin(cls, a.stream);
+  const dim3 grid = point_grid(a.nl[l], nlaunch(a));
+  const ProbDev* probs = a.probs;
+  const ProbState* cst = a.state;
+  const cudaError_t err =
+      a.sk == SK_CONST
+          ? launch_pdl(a.pdl, k_lin_residual<SK_CONST>, grid, dim3(PX, PY), 0, a.stream, probs, cst, a.active, l, r, e,
+                       a.lin_t)
+          : launch_pdl(a.pdl, k_lin_residual<SK_FIELD>, grid, dim3(PX, PY), 0, a.stream, probs, cst, a.active, l, r, e,
+                       a.lin_t);
+  a.prof->end(a.stream);
+  return err;
+}
+
+// Algorithm 1 on the levels above the tail: nu1 steps of pre-smoothing from e = 0 (e = H r,
+// then e += H (r - A e)), the residual's restriction, the tail, then per level the
+// prolongation and nu2 steps e += H (r - A e); the level-0 update and residual at the end
 cudaError_t launch_cycle_linear(const CycleArgs& a, float rtol, int max_cycles, int parity) {
   const LevelArrays& A = *a.arrays;
   const LinMaps& M = *a.lin_maps;
   const int ls = a.lstar, np = nlaunch(a);
+  const int nu1 = a.nu1 > 1 ? a.nu1 : 1, nu2 = a.nu2 > 1 ? a.nu2 : 1;
   const ProbDev* probs = a.probs;
   const ProbState* cst = a.state;
   cudaError_t e = cudaSuccess;
@@ -365,38 +436,36 @@ cudaError_t launch_cycle_linear(const CycleArgs& a, float rtol, int max_cycles, 
   auto level_rmap = [&](int l) -> const CUtensorMap& { return l == 0 ? (parity ? M.r0b : M.r0a) : M.r[l]; };
   for (int l = 0; l < ls && e == cudaSuccess; ++l) {
     const int cls = l == 0 ? PK_DOWN0 : PK_DOWN;
-    e = lin_H(a, l, level_rmap(l), A.e[l], false, cls);  // pre-smoothing from e = 0
+    const float* r = level_r(l);
+    e = smooth_H(a, l, r, level_rmap(l), A.e[l], false, cls);  // pre-smoothing from e = 0
+    for (int k = 1; k < nu1 && e == cudaSuccess; ++k) {
+      e = level_residual(a, l, r, A.e[l], cls);
+      if (e == cudaSuccess) e = smooth_H(a, l, a.lin_t, M.t[l], A.e[l], true, cls);
+    }
     if (e != cudaSuccess) break;
     a.prof->launches++;
     a.prof->begin(cls, a.stream);
     const dim3 gc = point_grid(a.nl[l + 1], np);
     e = a.sk == SK_CONST
-            ? launch_pdl(a.pdl, k_lin_restrict<SK_CONST>, gc, dim3(PX, PY), 0, a.stream, probs, cst, a.active, l,
-                         (const float*)level_r(l), (const float*)A.e[l], A.r[l + 1])
-            : launch_pdl(a.pdl, k_lin_restrict<SK_FIELD>, gc, dim3(PX, PY), 0, a.stream, probs, cst, a.active, l,
-                         (const float*)level_r(l), (const float*)A.e[l], A.r[l + 1]);
+            ? launch_pdl(a.pdl, k_lin_restrict<SK_CONST>, gc, dim3(PX, PY), 0, a.stream, probs, cst, a.active, l, r,
+                         (const float*)A.e[l], A.r[l + 1])
+            : launch_pdl(a.pdl, k_lin_restrict<SK_FIELD>, gc, dim3(PX, PY), 0, a.stream, probs, cst, a.active, l, r,
+                         (const float*)A.e[l], A.r[l + 1]);
     a.prof->end(a.stream);
   }
   if (e != cudaSuccess) return e;
   e = launch_tail(a);
   for (int l = ls - 1; l >= 0 && e == cudaSuccess; --l) {
     const int cls = l == 0 ? PK_UP0 : PK_UP;
-    const dim3 grid = point_grid(a.nl[l], np);
-    a.prof->launches += 2;
+    a.prof->launches++;
     a.prof->begin(cls, a.stream);
-    e = launch_pdl(a.pdl, k_lin_prolong, grid, dim3(PX, PY), 0, a.stream, probs, cst, a.active, l, A.e[l],
-                   (const float*)A.e[l + 1]);
+    e = launch_pdl(a.pdl, k_lin_prolong, point_grid(a.nl[l], np), dim3(PX, PY), 0, a.stream, probs, cst, a.active, l,
+                   A.e[l], (const float*)A.e[l + 1]);
     a.prof->end(a.stream);
-    if (e != cudaSuccess) break;
-    a.prof->begin(cls, a.stream);
-    e = a.sk == SK_CONST
-            ? launch_pdl(a.pdl, k_lin_residual<SK_CONST>, grid, dim3(PX, PY), 0, a.stream, probs, cst, a.active, l,
-                         (const float*)level_r(l), (const float*)A.e[l], a.lin_t)
-            : launch_pdl(a.pdl, k_lin_residual<SK_FIELD>, grid, dim3(PX, PY), 0, a.stream, probs, cst, a.active, l,
-                         (const float*)level_r(l), (const float*)A.e[l], a.lin_t);
-    a.prof->end(a.stream);
-    if (e != cudaSuccess) break;
-    e = lin_H(a, l, M.t[l], A.e[l], true, cls);  // post-smoothing
+    for (int k = 0; k < nu2 && e == cudaSuccess; ++k) {  // post-smoothing
+      e = level_residual(a, l, level_r(l), A.e[l], cls);
+      if (e == cudaSuccess) e = smooth_H(a, l, a.lin_t, M.t[l], A.e[l], true, cls);
+    }
   }
   if (e != cudaSuccess || ls == 0) return e;
   // level 0: the float-float update of the iterate and its compensated residual, one

@@ -167,11 +167,43 @@ __device__ inline void tail_linear_H(const float* phi, const float* u, float* ds
 }
 
 // Down and up sweeps from level l0 with r_{l0} already in shared memory; leaves e_{l0}.
-// The coarsest level is one FP64 product with the precomputed inverse of A_L.
+// nu1 pre-smoothing steps from e = 0 (the first is e = H r, each further one e += H (r - A e))
+// and nu2 post-smoothing steps after the correction (Algorithm 1).  The coarsest level is
+// one FP64 product with the precomputed inverse of A_L.
 template <int SK, int HK>
 __device__ void tail_cycle(const ProbDev& P, float* sm, const TailLayout& lay, const float (*sc)[9],
                            const float (*wi)[9], int l0, int L, float omega) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int nu1 = P.nu1 > 1 ? P.nu1 : 1, nu2 = P.nu2 > 1 ? P.nu2 : 1;
+  // t = r - A e, then (with smooth) e += H t, on level l; both end with a barrier
+  auto residual = [&](int l) {
+    const LevelDev& Lv = P.lv[l];
+    const int n = lay.n[l], m = n + 2;
+    const float* r = sm + lay.off_r[l];
+    const float* e = sm + lay.off_e[l];
+    float* t = sm + lay.off_t[l];
+    TAIL_FOR(n) {
+      const int q = (i + 1) * m + j + 1;
+      t[q] = r[q] - pad_A<SK>(Lv, sc[l], e + q, m, n, i, j);
+    }
+    __syncthreads();
+  };
+  auto smooth_t = [&](int l) {
+    const LevelDev& Lv = P.lv[l];
+    const int n = lay.n[l], m = n + 2;
+    float* e = sm + lay.off_e[l];
+    const float* t = sm + lay.off_t[l];
+    const float* w = sm + lay.off_w[l];
+    if (HK == HK_LINEAR) {
+      tail_linear_H(w, t, e, true, sm + lay.off_s1, sm + lay.off_s2, n, m);
+    } else {
+      TAIL_FOR(n) {
+        const int q = (i + 1) * m + j + 1;
+        e[q] += pad_H<SK, HK>(Lv, sc[l], w, wi[l], omega, t + q, m, n, i, j);
+      }
+    }
+    __syncthreads();
+  };
   for (int l = l0; l < L - 1; ++l) {
     const LevelDev& Lv = P.lv[l];
     const int n = lay.n[l], m = n + 2, nc = lay.n[l + 1], mc = nc + 2;
@@ -188,11 +220,11 @@ __device__ void tail_cycle(const ProbDev& P, float* sm, const TailLayout& lay, c
       }
     }
     __syncthreads();
-    TAIL_FOR(n) {
-      const int q = (i + 1) * m + j + 1;
-      t[q] = r[q] - pad_A<SK>(Lv, sc[l], e + q, m, n, i, j);
+    for (int k = 1; k < nu1; ++k) {
+      residual(l);
+      smooth_t(l);
     }
-    __syncthreads();
+    residual(l);
     float* rc = sm + lay.off_r[l + 1];
     for (int I = warp; I < nc; I += nwarps)
       for (int J = lane; J < nc; J += 32) rc[(I + 1) * mc + J + 1] = restrict_at(t + (2 * I + 2) * m + 2 * J + 2, m);
@@ -211,29 +243,15 @@ __device__ void tail_cycle(const ProbDev& P, float* sm, const TailLayout& lay, c
     __syncthreads();
   }
   for (int l = L - 2; l >= l0; --l) {
-    const LevelDev& Lv = P.lv[l];
     const int n = lay.n[l], m = n + 2, mc = lay.n[l + 1] + 2;
-    float* r = sm + lay.off_r[l];
     float* e = sm + lay.off_e[l];
-    float* t = sm + lay.off_t[l];
     const float* ec = sm + lay.off_e[l + 1];
-    const float* w = sm + lay.off_w[l];
     TAIL_FOR(n) e[(i + 1) * m + j + 1] += prolong_at(i, j, ec, -1, -1, mc);
     __syncthreads();
-    TAIL_FOR(n) {
-      const int q = (i + 1) * m + j + 1;
-      t[q] = r[q] - pad_A<SK>(Lv, sc[l], e + q, m, n, i, j);
+    for (int k = 0; k < nu2; ++k) {
+      residual(l);
+      smooth_t(l);
     }
-    __syncthreads();
-    if (HK == HK_LINEAR) {
-      tail_linear_H(w, t, e, true, sm + lay.off_s1, sm + lay.off_s2, n, m);
-    } else {
-      TAIL_FOR(n) {
-        const int q = (i + 1) * m + j + 1;
-        e[q] += pad_H<SK, HK>(Lv, sc[l], w, wi[l], omega, t + q, m, n, i, j);
-      }
-    }
-    __syncthreads();
   }
 }
 

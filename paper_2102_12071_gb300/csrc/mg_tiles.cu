@@ -786,7 +786,7 @@ cudaError_t launch_update_residual(const CycleArgs& a, const CUtensorMap& e0, fl
 }
 
 cudaError_t launch_cycle(const CycleArgs& a, float rtol, int max_cycles, int parity) {
-  if (a.hk == HK_LINEAR) return launch_cycle_linear(a, rtol, max_cycles, parity);
+  if (a.hk == HK_LINEAR || a.nu1 != 1 || a.nu2 != 1) return launch_cycle_linear(a, rtol, max_cycles, parity);
   const int ls = a.lstar, np = nlaunch(a);
   const ProbDev* probs = a.probs;
   float* const nul = nullptr;

@@ -258,3 +258,44 @@ def test_per_problem_linear_smoothers_batch_like_separate_contexts():
         assert int(gc[i]) == int(c1[0])
         k = int(c1[0]) + 1
         assert np.array_equal(gh[i][:k], h1[0][:k])
+
+
+# ------------------------------------------------------------------ nu1, nu2 > 1
+@pytest.mark.parametrize("n,nu1,nu2,cycles", [(63, 2, 2, 20), (255, 3, 2, 12), (255, 6, 6, 8), (1023, 6, 6, 3)])
+def test_multistep_jacobi_matches_oracle(n, nu1, nu2, cycles):
+    """Algorithm 1 with nu1 pre- and nu2 post-smoothing Jacobi steps (the paper's cost-equalised
+    Jacobi takes six): batched level kernels above 63, the one-CTA tail below."""
+    eps, theta = 0.01, math.pi / 3
+    b = inputs.rhs_uniform(70, n)
+    mg = S.MultigridSolver([S.rotated(n, eps, theta)], "jacobi", nu1=nu1, nu2=nu2)
+    _, _, gh, cyc, _ = mg.solve(torch.from_numpy(b).cuda()[None].contiguous(), rtol=0.0, max_cycles=cycles)
+    om = O.Multigrid(O.const_field(n, f32(O.q1_rotated_stencil(eps, theta))), nu1=nu1, nu2=nu2)
+    _, oh = om.solve(f32(b), rtol=0.0, max_cycles=cycles)
+    rel = np.abs(gh[0][: cycles + 1] - oh) / oh
+    assert rel.max() <= 1e-5, rel.max()
+
+
+def test_multistep_linear_smoother_matches_oracle():
+    n, cycles = 255, 10
+    pe = [(0.05, 0.7), (0.01, 2.2)]
+    fields = [O.const_field(n, f32(O.q1_rotated_stencil(e, t))) for e, t in pe]
+    params = lin_params(3, fields[0][4, n // 2, n // 2], seed=77)
+    mg = S.MultigridSolver([S.rotated(n, e, t) for e, t in pe], "cnn", torch.from_numpy(params).cuda(),
+                           net_arch="linear", nu1=2, nu2=3)
+    b = [inputs.rhs_uniform(80 + p, n) for p in range(2)]
+    _, _, gh, _, _ = mg.solve(torch.from_numpy(np.stack(b).astype(np.float32)).cuda().contiguous(), rtol=0.0,
+                              max_cycles=cycles)
+    for p in range(2):
+        _, oh = OL.LinearMultigrid(fields[p], [f32(q) for q in params], nu1=2, nu2=3).solve(f32(b[p]), rtol=0.0,
+                                                                                            max_cycles=cycles)
+        rel = np.abs(gh[p][: cycles + 1] - oh) / oh
+        assert rel.max() <= 1e-5, rel.max()
+
+
+def test_multistep_smoothing_needs_jacobi_or_the_linear_smoother():
+    from paper_2102_12071_gb300 import binding as B
+
+    p = torch.zeros(1260, device="cuda")
+    with pytest.raises(B.MGError) as ei:  # refused while sizing the workspace
+        S.MultigridSolver([S.rotated(255, 0.1, 0.3)], "cnn", p, nu1=2)
+    assert "need the Jacobi or the linear smoother" in str(ei.value)

@@ -144,3 +144,17 @@ def test_coarse_vcycle_loss_gradient_matches_central_differences():
     z = rng.standard_normal((1, n, n))
     phi = OL.jacobi_params(st[4, 7, 7]) + 0.05 * rng.standard_normal((6, 9))
     _fd_check(lambda p: OL.loss_and_grad(st, p, z, cycles=1, coarse=coarse, coarse_t=coarse_t), phi)
+
+
+def test_multistep_smoothing_at_the_jacobi_point_equals_c_oracle():
+    """nu1, nu2 > 1 (Algorithm 1's smoothing steps): the linear oracle at the Jacobi point
+    against the C oracle's Jacobi multigrid with the same steps."""
+    n = 31
+    st = O.const_field(n, O.q1_rotated_stencil(0.05, 0.9))
+    b = _rng(9).uniform(-1, 1, (n, n))
+    base = OL.LinearMultigrid(st, [np.zeros((6, 9))])
+    for nu1, nu2 in ((2, 2), (3, 1), (6, 6)):
+        mgl = OL.LinearMultigrid(st, _jacobi_levels(base), nu1=nu1, nu2=nu2)
+        _, hl = mgl.solve(b, rtol=0.0, max_cycles=8)
+        _, hc = O.Multigrid(st, nu1=nu1, nu2=nu2).solve(b, rtol=0.0, max_cycles=8)
+        assert np.max(np.abs(hl - hc) / hc) < 1e-10
