@@ -40,7 +40,7 @@ WEIGHTS = os.path.join(ROOT, "paper_2102_12071_gb300", "weights", "cnn_rotated.n
 BYTES_PER_DOF = {0: 16.0, 1: 9.0, 2: 33.0}
 # dram bytes (read + write) per launch of the current kernel versions from one ncu capture
 # of the 16 x 1023^2 batch; None where the kernel changed since its last capture
-NCU_TRAFFIC = {1: 67.15e6 + 41.10e6, 2: 353.70e6 + 175.88e6}
+NCU_TRAFFIC = {1: 67.14e6 + 40.54e6, 2: 353.70e6 + 175.88e6}
 KERNEL_NAMES = {0: "k_residual (initial iterate)", 1: "k_down(level 0)", 2: "k_up0(level 0: up-sweep, x update, residual)",
                 3: "k_tail", 4: "k_down(l>=1)", 5: "k_up(l>=1)"}
 
@@ -54,9 +54,9 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def sweeps_per_cycle(sizes):
-    """Mdof-sweeps of one V(1,1) cycle: every smoothed level is swept twice."""
-    return sum(2 * s * s for s in sizes[:-1]) / 1e6
+def sweeps_per_cycle(sizes, nu1: int = 1, nu2: int = 1):
+    """Mdof-sweeps of one V(nu1, nu2) cycle: every smoothed level is swept nu1 + nu2 times."""
+    return sum((nu1 + nu2) * s * s for s in sizes[:-1]) / 1e6
 
 
 # ------------------------------------------------------------------ clocks
@@ -359,14 +359,17 @@ def run_fgmres(weights):
     b = torch.from_numpy(np.stack([inputs.rhs_uniform(inputs.SEED_RHS + 1700 + i, n) for i in range(5)]))
     b = b.cuda().contiguous()
     adaptive = load_adaptive()
-    arms = {"jacobi": None, "cnn": weights.cuda() if weights is not None else None,
+    arms = {"jacobi": None, "jacobi_nu6": None, "cnn": weights.cuda() if weights is not None else None,
             "cnn_adaptive": T.adaptive_params(adaptive, n).cuda() if adaptive is not None else None}
     out = {"n": n, "eps": 0.01, "thetas": "pi/12 .. 5pi/12", "rtol": 1e-6, "restart": 30,
            "paper_iterations_511": {"jacobi": [37.0, 30.2, 28.0, 30.0, 37.0], "alpha_cnn": [11.0, 12.0, 13.0, 12.0, 11.0]}}
     for name, net in arms.items():
-        if name != "jacobi" and net is None:
+        if not name.startswith("jacobi") and net is None:
             continue
-        mg = S.MultigridSolver(probs, "jacobi" if name == "jacobi" else "cnn", net_params=net)
+        # jacobi_nu6: six Jacobi steps per smoothing, the paper's cost-equalised baseline for
+        # the six-convolution linear smoother (Sec. 6)
+        nu = 6 if name == "jacobi_nu6" else 1
+        mg = S.MultigridSolver(probs, "cnn" if net is not None else "jacobi", net_params=net, nu1=nu, nu2=nu)
         S.fgmres(mg, b, rtol=1e-6, history=False)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -611,7 +614,9 @@ def main():
 
     weights = load_weights()
     adaptive = load_adaptive()
-    arms = {"jacobi": S.MultigridSolver(problems, "jacobi")}
+    arms = {"jacobi": S.MultigridSolver(problems, "jacobi"),
+            # six Jacobi steps per smoothing: the cost-equalised baseline of the linear smoother (Sec. 6)
+            "jacobi_nu6": S.MultigridSolver(problems, "jacobi", nu1=6, nu2=6)}
     if weights is not None:
         arms["cnn"] = S.MultigridSolver(problems, "cnn", net_params=weights.cuda())
     if adaptive is not None:
@@ -669,7 +674,8 @@ def main():
             barrier()
             ms = max_over_ranks(e0.elapsed_time(e1)) / args.steps
             cyc = cyc_all[-1]
-            sweeps = sum(sweeps_per_cycle(sizes) * int(c) for c in cyc)
+            spc = sweeps_per_cycle(sizes, arms[arm].opts.nu1, arms[arm].opts.nu2)
+            sweeps = sum(spc * int(c) for c in cyc)
             results[arm] = {"ms_per_step": ms, "cycles": [int(c) for c in cyc], "converged": int(st) == 0,
                             "mdof_sweeps_per_s": sweeps * world / (ms / 1e3)}
     clocks = clk.summary()
