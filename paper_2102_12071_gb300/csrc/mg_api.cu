@@ -442,7 +442,7 @@ mg_status mg_setup(const mg_problem* problems, int nprob, const mg_options* opts
   a.lin_maps = &ctx->lin_maps;
   a.nu1 = P.nu1;
   a.nu2 = P.nu2;
-  if (P.generic && P.lstar > 0 && !build_lin_maps(ctx->lin_maps, ctx->arrays, a.lin_t, P.nprob, P.lstar)) {
+  if (P.generic && P.lstar > 0 && !build_lin_maps(ctx->lin_maps, ctx->arrays, a.lin_t, a.lin_wa, P.nprob, P.lstar)) {
     delete ctx;
     return fail(MG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the linear smoother's arrays");
   }

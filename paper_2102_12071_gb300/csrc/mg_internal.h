@@ -109,8 +109,11 @@ struct LinMaps {
   CUtensorMap r[MG_MAXL];  // levels >= 1: r_l
   CUtensorMap t[MG_MAXL];  // the up-sweep residual (scratch lin_t with level l's shape)
   CUtensorMap e0;          // level 0's correction, boxed like the iterate (k_update_residual)
+  CUtensorMap eh[MG_MAXL]; // the linear up-sweep: e_l with its six-point halo
+  CUtensorMap ec[MG_MAXL]; // ... the coarse correction its prolongation reads
+  CUtensorMap e0f;         // ... level 0's final correction (scratch lin_wa), boxed like e0
 };
-bool build_lin_maps(LinMaps& M, const LevelArrays& A, float* lin_t, int nprob, int lstar);
+bool build_lin_maps(LinMaps& M, const LevelArrays& A, float* lin_t, float* lin_wa, int nprob, int lstar);
 
 struct CycleArgs {
   ProbDev* probs;

@@ -260,11 +260,12 @@ __device__ __forceinline__ void lin_layer(const float* in, float* out, const flo
   }
 }
 
-// dst (=, or += with ACC) f_5(w_4) + f_6(u) on the tile's points inside the grid: one
-// window and one kernel live at a time (f_5 over w_4 first, then f_6 over u)
+// dst (=, or += with ACC, or base + with base: four values per thread) f_5(w_4) + f_6(u)
+// on the tile's points inside the grid: one window and one kernel live at a time (f_5 over
+// w_4 first, then f_6 over u)
 template <bool ACC>
 __device__ __forceinline__ void lin_out(const float* w4, const float* u, const float* ph, int R0, int C0, int n,
-                                        float* dst, int pitch) {
+                                        float* dst, int pitch, const float* base) {
   constexpr int K = 4;
   const int tj = threadIdx.x % HT, t0 = (threadIdx.x / HT) * K, r = HH + t0, c = 8 + tj;
   float h[K];
@@ -292,7 +293,7 @@ __device__ __forceinline__ void lin_out(const float* w4, const float* u, const f
     if (lin_inside(i, j, n)) {
       const float hv = h[k] + dot9(w, v);
       float* d = dst + (size_t)i * pitch + j;
-      *d = ACC ? *d + hv : hv;
+      *d = base ? base[k] + hv : (ACC ? *d + hv : hv);
     }
     v.shift();
   }
@@ -300,7 +301,7 @@ __device__ __forceinline__ void lin_out(const float* w4, const float* u, const f
 
 template <bool MASK, bool ACC>
 __device__ __forceinline__ void lin_chain(const float* U, float* B1, float* B2, float* B3, float* B4, const float* ph,
-                                          int R0, int C0, int n, float* dst, int pitch) {
+                                          int R0, int C0, int n, float* dst, int pitch, const float* base = nullptr) {
   lin_layer<40, 7, MASK, HXU, 0, 0, HX1, 1, 4>(U, B1, ph, R0, C0, n);
   __syncthreads();
   lin_layer<38, 7, MASK, HX1, 1, 4, HX2, 2, 5>(B1, B2, ph + 9, R0, C0, n);
@@ -309,7 +310,121 @@ __device__ __forceinline__ void lin_chain(const float* U, float* B1, float* B2, 
   __syncthreads();
   lin_layer<34, 6, MASK, HX3, 3, 6, HX4, 4, 7>(B3, B4, ph + 27, R0, C0, n);
   __syncthreads();
-  lin_out<ACC>(B4, U, ph, R0, C0, n, dst, pitch);
+  lin_out<ACC>(B4, U, ph, R0, C0, n, dst, pitch, base);
+}
+
+// ------------------------------------------------------------- the fused up-sweep
+// Post-smoothing of a level in one kernel (the linear smoother's counterpart of k_up):
+// e1 = e + P e_c on the tile and a six-point halo, t = r - A e1 on the chain's input region
+// (zero outside the grid), then e1 + H t on the tile, written to an array of its own (other
+// CTAs still read e with halos).  Frames: e1 rows from R0 - 6, columns from C0 - 8 (stride
+// 48, 44 rows); t in the chain's input frame (rows from R0 - 5, stride 56), computed in
+// place over the TMA copy of r; the coarse tile from (R0/2 - 4, C0/2 - 4), 24 x 24.
+constexpr int UE_H = HR + 2, UE_X = 48, UC = 24;
+
+template <int SK, bool MASK>
+__device__ __forceinline__ void up_prepare(const LevelDev& L, const float (&s)[9], float* E1, float* U,
+                                           const float* ecs, int R0, int C0, int n) {
+  // e1 = e + P e_c on rows R0-6 .. R0+37, columns C0-6 .. C0+37 (e and e_c are zero outside
+  // their grids, so is P e_c outside the fine grid)
+  const int I0 = R0 / 2 - 4, J0 = C0 / 2 - 4;
+  for (int q = threadIdx.x; q < 44 * 44; q += LT) {
+    const int rr = q / 44, cc = 2 + q % 44;
+    const int i = R0 - 6 + rr, j = C0 - 8 + cc;
+    const float* b = ecs + (((i - 1) >> 1) - I0) * UC + (((j - 1) >> 1) - J0);
+    float v;
+    if (i & 1) v = (j & 1) ? b[0] : 0.5f * (b[0] + b[1]);
+    else v = (j & 1) ? 0.5f * (b[0] + b[UC]) : 0.25f * ((b[0] + b[1]) + (b[UC] + b[UC + 1]));
+    E1[rr * UE_X + cc] += v;
+  }
+  __syncthreads();
+  // t = r - A e1 on the chain's input region (frame rows 0..41, columns 3..44), K rows per
+  // thread with a register window over e1 (e1's row = t's row + 1)
+  constexpr int S = HR, K = 7, NS = (S + K - 1) / K;
+  static_assert(S * NS <= LT, "residual needs more threads than the CTA has");
+  const int t = threadIdx.x;
+  if (t < S * NS) {
+    const int tj = t % S, t0 = (t / S) * K, c = 3 + tj;
+    const float* src = E1 + (t0 + 1) * UE_X + c;
+    Win v;
+    v.load_ab(src, UE_X);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (t0 + k < S) {
+        v.load_c(src + k * UE_X, UE_X);
+        const int i = R0 - HH + t0 + k, j = C0 - 8 + c;
+        float* tp = U + (t0 + k) * HXU + c;
+        if (!MASK || lin_inside(i, j, n)) {
+          float a[9];
+          if (SK == SK_CONST) {
+#pragma unroll
+            for (int q = 0; q < 9; ++q) a[q] = s[q];
+          } else {
+            const size_t nn = (size_t)n * n, pq = (size_t)i * n + j;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) a[q] = __ldg(L.st + q * nn + pq);
+          }
+          *tp = *tp - dot9(a, v);
+        } else {
+          *tp = 0.f;
+        }
+        v.shift();
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// out = e1 + H t on level l (fused prolongation, residual and post-smoothing);
+// mE: e_l with the six-point halo, mR: r_l (the chain's input box), mC: the coarse tile
+template <int SK>
+__global__ void __launch_bounds__(LT, 5) k_lin_Uptile(const __grid_constant__ CUtensorMap mE,
+                                                      const __grid_constant__ CUtensorMap mR,
+                                                      const __grid_constant__ CUtensorMap mC,
+                                                      const ProbDev* __restrict__ probs, ProbState* __restrict__ state,
+                                                      const int* __restrict__ act, int l, float* __restrict__ out) {
+  pdl_trigger();
+  const int p = act ? act[blockIdx.y] : blockIdx.y;
+  const LevelDev L = probs[p].lv[l];
+  const int n = L.n, pitch = L.pitch, ntx = (n + HT - 1) / HT;
+  const int tile = blockIdx.x;
+  if (tile >= ntx * ntx) return;
+  const int R0 = (tile / ntx) * HT, C0 = (tile % ntx) * HT;
+  __shared__ __align__(128) float U[HR * HXU];
+  __shared__ __align__(128) float E1[UE_H * UE_X];
+  __shared__ __align__(128) float ecs[UC * UC];
+  __shared__ float B1[40 * HX1], B2[38 * HX2], B3[36 * HX3], B4[34 * HX4];
+  __shared__ float ph[MG_NPARAMS_LIN];
+  __shared__ __align__(8) uint64_t bar;
+  float s[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) s[k] = (SK == SK_CONST) ? L.s[k] : 0.f;
+  if (threadIdx.x < MG_NPARAMS_LIN) ph[threadIdx.x] = L.W[threadIdx.x];  // weights never change
+  pdl_wait();
+  if (!st_active(state + p)) return;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    mbar_arrive_expect_tx(&bar, (HR * HXU + UE_H * UE_X + UC * UC) * sizeof(float));
+    tma_load_3d(U, &mR, &bar, C0 - 8, R0 - HH, p);
+    tma_load_3d(E1, &mE, &bar, C0 - 8, R0 - HH - 1, p);
+    tma_load_3d(ecs, &mC, &bar, C0 / 2 - 4, R0 / 2 - 4, p);
+  }
+  __syncthreads();
+  if (!tile_wait(&bar, state[p])) return;
+  const bool inner = R0 >= HH + 1 && C0 >= HH + 1 && R0 + HT + HH + 1 <= n && C0 + HT + HH + 1 <= n;
+  if (inner) up_prepare<SK, false>(L, s, E1, U, ecs, R0, C0, n);
+  else up_prepare<SK, true>(L, s, E1, U, ecs, R0, C0, n);
+  // e1 on the output points of this thread (lin_out's mapping), then the chain on t
+  float e1c[4];
+  {
+    const int tj = threadIdx.x % HT, t0 = (threadIdx.x / HT) * 4;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) e1c[k] = E1[(t0 + k + HH + 1) * UE_X + tj + 8];
+  }
+  float* d = out + (size_t)p * n * pitch;
+  if (inner) lin_chain<false, false>(U, B1, B2, B3, B4, ph, R0, C0, n, d, pitch, e1c);
+  else lin_chain<true, false>(U, B1, B2, B3, B4, ph, R0, C0, n, d, pitch, e1c);
 }
 
 // dst (=, or += with ACC) H u on level l; mu: the tensor map of u's level array
@@ -455,32 +570,49 @@ cudaError_t launch_cycle_linear(const CycleArgs& a, float rtol, int max_cycles, 
   }
   if (e != cudaSuccess) return e;
   e = launch_tail(a);
+  const bool lin = a.hk == HK_LINEAR;
   for (int l = ls - 1; l >= 0 && e == cudaSuccess; --l) {
     const int cls = l == 0 ? PK_UP0 : PK_UP;
     a.prof->launches++;
     a.prof->begin(cls, a.stream);
-    e = launch_pdl(a.pdl, k_lin_prolong, point_grid(a.nl[l], np), dim3(PX, PY), 0, a.stream, probs, cst, a.active, l,
-                   A.e[l], (const float*)A.e[l + 1]);
+    // the linear smoother: prolongation, residual and the first post-smoothing step in one
+    // tiled kernel whose result goes to f_l (level 0: the scratch lin_wa); Jacobi: e_l += P e_c
+    float* ef = lin ? (l == 0 ? a.lin_wa : A.f[l]) : A.e[l];
+    if (lin) {
+      const int nt = (a.nl[l] + HT - 1) / HT;
+      e = a.sk == SK_CONST
+              ? launch_pdl(a.pdl, k_lin_Uptile<SK_CONST>, dim3(nt * nt, np), dim3(LT), 0, a.stream, M.eh[l],
+                           level_rmap(l), M.ec[l], probs, a.state, a.active, l, ef)
+              : launch_pdl(a.pdl, k_lin_Uptile<SK_FIELD>, dim3(nt * nt, np), dim3(LT), 0, a.stream, M.eh[l],
+                           level_rmap(l), M.ec[l], probs, a.state, a.active, l, ef);
+    } else {
+      e = launch_pdl(a.pdl, k_lin_prolong, point_grid(a.nl[l], np), dim3(PX, PY), 0, a.stream, probs, cst, a.active,
+                     l, A.e[l], (const float*)A.e[l + 1]);
+    }
     a.prof->end(a.stream);
-    for (int k = 0; k < nu2 && e == cudaSuccess; ++k) {  // post-smoothing
-      e = level_residual(a, l, level_r(l), A.e[l], cls);
-      if (e == cudaSuccess) e = smooth_H(a, l, a.lin_t, M.t[l], A.e[l], true, cls);
+    for (int k = lin ? 1 : 0; k < nu2 && e == cudaSuccess; ++k) {  // (further) post-smoothing steps
+      e = level_residual(a, l, level_r(l), ef, cls);
+      if (e == cudaSuccess) e = smooth_H(a, l, a.lin_t, M.t[l], ef, true, cls);
     }
   }
   if (e != cudaSuccess || ls == 0) return e;
   // level 0: the float-float update of the iterate and its compensated residual, one
   // tiled kernel shared with the tiled path's conventions
-  return launch_update_residual(a, M.e0, rtol, max_cycles, parity);
+  return launch_update_residual(a, lin ? M.e0f : M.e0, rtol, max_cycles, parity);
 }
 
-bool build_lin_maps(LinMaps& M, const LevelArrays& A, float* lin_t, int nprob, int lstar) {
+bool build_lin_maps(LinMaps& M, const LevelArrays& A, float* lin_t, float* lin_wa, int nprob, int lstar) {
   bool ok = make_map(&M.r0a, A.r[0], A.n[0], A.pitch[0], nprob, HXU, HR) &&
             make_map(&M.r0b, A.r0b, A.n[0], A.pitch[0], nprob, HXU, HR);
   int bw = 0, bh = 0;
   tile_res_box(&bw, &bh);
-  ok = ok && make_map(&M.e0, A.e[0], A.n[0], A.pitch[0], nprob, bw, bh);
+  ok = ok && make_map(&M.e0, A.e[0], A.n[0], A.pitch[0], nprob, bw, bh) &&
+       make_map(&M.e0f, lin_wa, A.n[0], A.pitch[0], nprob, bw, bh);
   for (int l = 0; ok && l < lstar; ++l) {
-    ok = make_map(&M.t[l], lin_t, A.n[l], A.pitch[l], nprob, HXU, HR);
+    ok = make_map(&M.t[l], lin_t, A.n[l], A.pitch[l], nprob, HXU, HR) &&
+         make_map(&M.eh[l], A.e[l], A.n[l], A.pitch[l], nprob, UE_X, UE_H) &&
+         // the correction level l's prolongation reads: f of a batched level, the tail's e
+         make_map(&M.ec[l], l + 1 < lstar ? A.f[l + 1] : A.e[l + 1], A.n[l + 1], A.pitch[l + 1], nprob, UC, UC);
     if (ok && l >= 1) ok = make_map(&M.r[l], A.r[l], A.n[l], A.pitch[l], nprob, HXU, HR);
   }
   return ok;
