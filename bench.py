@@ -116,6 +116,25 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ workload
+def reduce_over_ranks(v: float, dist, op: str = "max", device: str = "cpu") -> float:
+    """v combined over the ranks of the job ("max" or "sum"); v itself on one process."""
+    if dist is None:
+        return v
+    import torch
+
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_throughput(sweeps: float, ms: float, dist, device: str = "cpu"):
+    """Whole-job Mdof-sweeps/s and the job's time: every rank's sweeps (each rank solves its
+    own seeded batch, so the counts differ) over the slowest rank's milliseconds."""
+    total = reduce_over_ranks(sweeps, dist, "sum", device)
+    tmax = reduce_over_ranks(ms, dist, "max", device)
+    return total / (tmax / 1e3), tmax
+
+
 def make_batch(rank: int, n: int, nprob: int):
     from paper_2102_12071_gb300 import inputs
 
@@ -647,13 +666,6 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     results = {}
     for arm in arms:
         for _ in range(args.warmup):
@@ -672,14 +684,14 @@ def main():
             e1.record(stream)
             torch.cuda.synchronize()
             barrier()
-            ms = max_over_ranks(e0.elapsed_time(e1)) / args.steps
             cyc = cyc_all[-1]
             spc = sweeps_per_cycle(sizes, arms[arm].opts.nu1, arms[arm].opts.nu2)
-            sweeps = sum(spc * int(c) for c in cyc)
+            value, ms = job_throughput(sum(spc * int(c) for c in cyc), e0.elapsed_time(e1) / args.steps, dist, "cuda")
             results[arm] = {"ms_per_step": ms, "cycles": [int(c) for c in cyc], "converged": int(st) == 0,
-                            "mdof_sweeps_per_s": sweeps * world / (ms / 1e3)}
+                            "mdof_sweeps_per_s": value}
     clocks = clk.summary()
-    launches = sum(B.mg_profile_read(arms[a].ctx, -1)[1] - launches0[a] for a in arms)
+    launches = reduce_over_ranks(sum(B.mg_profile_read(arms[a].ctx, -1)[1] - launches0[a] for a in arms), dist,
+                                 "sum", "cuda")
 
     # ---- dominant-kernel roofline: single V-cycles of the whole batch (mg_vcycle: residual,
     # cycle, residual; every launch does work), each launch event-timed
@@ -750,8 +762,9 @@ def main():
         hout_hi.copy_(dxh, non_blocking=True)
         hout_lo.copy_(dxl, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps)
-    e2e_val = sum(sweeps_per_cycle(sizes) * int(c) for c in cyc_e2e) * world / e2e_s
+    e2e_val, e2e_ms = job_throughput(sum(sweeps_per_cycle(sizes) * int(c) for c in cyc_e2e),
+                                     1e3 * (time.perf_counter() - t0) / args.steps, dist, "cuda")
+    e2e_s = e2e_ms / 1e3
 
     varcoef = run_varcoef(args, rank) if str(args.varcoef_n) != "0" else None
     extra = {}
