@@ -63,9 +63,11 @@ class MultigridSolver:
             net_params = net_params.reshape(self.nprob, -1, 54)
             net_levels = int(net_params.shape[1])
             net_params = net_params.reshape(-1, 54)
+        elif net_arch == "linear" and net_params is not None:
+            # sets of six 3x3 kernels: [54], [6, 9], [k, 54] or [k, 6, 9] all mean k >= 1 sets
+            net_params = net_params.reshape(-1, 54)
+            net_levels = int(net_params.shape[0]) if net_params.shape[0] > 1 else 0
         else:
-            if net_params is not None and net_params.dim() > 2:  # e.g. linear sets given as [k, 6, 9]
-                net_params = net_params.reshape(net_params.shape[0], -1)
             net_levels = int(net_params.shape[0]) if net_params is not None and net_params.dim() == 2 else 0
         arch = net_arch_code(net_arch)
         self.opts = B.options(kind, omega, coarsest_n, int(conv_bf16), int(cluster_tail), 1, 0, net_levels,
