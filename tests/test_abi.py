@@ -83,3 +83,23 @@ def test_workspace_grows_with_batch(lib):
     assert s4 > 3 * s1 > 0
     # per problem: r and e on every level (4/3 n^2 floats each) dominate
     assert s1 >= 2 * 4 * 255 * 255
+
+
+def test_smoothing_steps_and_linear_smoother_options_are_checked_on_the_host(lib):
+    probs, _ = B.problems_array([{"n": 255, "kind": B.MG_PROBLEM_ROTATED, "eps": 0.1, "theta": 0.0}])
+    # nu1, nu2 in 1..8, other than 1 only for Jacobi and the linear smoother
+    assert B.mg_workspace_size(probs, 1, B.options(nu1=9)) == 0
+    assert b"[1, 8]" in lib.mg_last_error()
+    assert B.mg_workspace_size(probs, 1, B.options(nu1=0)) == 0
+    assert B.mg_workspace_size(probs, 1, B.options(B.MG_SMOOTH_CNN, nu1=2)) == 0
+    assert b"Jacobi or the linear smoother" in lib.mg_last_error()
+    jac6 = B.mg_workspace_size(probs, 1, B.options(nu1=6, nu2=6))
+    lin2 = B.mg_workspace_size(probs, 1, B.options(B.MG_SMOOTH_CNN, net_arch=B.MG_NET_LINEAR, nu1=2, nu2=3))
+    assert jac6 > B.mg_workspace_size(probs, 1, B.options()) > 0 and lin2 > 0  # scratch of the batched path
+    # per-problem parameter groups only for the linear smoother
+    assert B.mg_workspace_size(probs, 1, B.options(B.MG_SMOOTH_CNN, net_per_problem=1)) == 0
+    assert b"linear smoother" in lib.mg_last_error()
+    assert B.mg_workspace_size(probs, 1, B.options(B.MG_SMOOTH_CNN, net_arch=B.MG_NET_LINEAR,
+                                                   net_per_problem=1)) > 0
+    assert B.mg_workspace_size(probs, 1, B.options(B.MG_SMOOTH_CNN, net_arch=7)) == 0
+    assert lib.mg_net_param_count(B.MG_NET_LINEAR) == 54
