@@ -13,7 +13,10 @@
 //   k_residual  r = b - A (x_hi + x_lo), compensated (float-float), ||r||^2, stopping test
 //   k_down(l)   e = H r, s = r - A e, r_{l+1} = P^T s         (Algorithm 1, pre-smoothing and restriction)
 //   k_up(l)     e1 = e + P e_{l+1}, e = e1 + H (r - A e1)      (Algorithm 1, correction and post-smoothing);
-//               on level 0 the correction is added to the float-float iterate.
+//               on level 0 (k_up0) the correction is added to the float-float iterate and the
+//               next residual and stopping test follow in the same kernel.
+//   k_update_residual  x += e_0 and the compensated residual with the stopping test, for
+//               cycles whose up-sweep ran in the batched level kernels (mg_linear.cu).
 #include <cudaTypedefs.h>
 
 #include <atomic>
