@@ -1,0 +1,159 @@
+"""FP64 oracle of the stencil-to-smoother network with a stack of k = 3 output kernels.
+
+Test infrastructure only, like the rest of this package.  Plain PyTorch CPU operations in
+float64; the gradient of the loss is PyTorch's reverse mode over those operations.
+
+Sec. 4 maps each point's stencil neighbourhood to a stack of 3x3 convolution kernels
+(Sec. 4.2: three kernels per point, Fig. convolution).  The network is the one of the
+k = 1 oracle (9 input channels: the point's stencil over its diagonal; 3x3 convolutions
+9 -> 7 -> 5 -> 3 with LeakyReLU(0.01) and zero padding; a layer from the 3x3 window of the
+3-channel map) with 27 outputs instead of 9: out_1, out_2, out_3, one 3x3 kernel each.
+
+Readings of the paper:
+  - The three kernels act as a stack, H v = K3(K2(K1 v)), every K_k(u)(x) = sum_t
+    K_k[t](x) u(x + d_t) with u zero outside the grid (a stack of convolutions, Sec. 4).
+  - Scaling: K1 = (omega delta + out_1) / D, K2 = delta + out_2, K3 = delta + out_3
+    (delta the identity kernel).  A zero last layer is weighted Jacobi, as for k = 1, and
+    the stack reduces to the k = 1 network whenever out_2 = out_3 = 0.
+Parameters: w1[7][9][3][3], w2[5][7][3][3], w3[3][5][3][3], wf[27][3][3][3] (row 9k + t
+of wf: tap t of kernel k + 1): 1 746 values.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+import torch.nn.functional as F
+
+from .oracle import _f64
+
+NK = 3
+SIZES = [(7, 9), (5, 7), (3, 5), (9 * NK, 3)]
+NPARAMS = sum(co * ci * 9 for co, ci in SIZES)
+
+
+def _t(a):
+    return torch.as_tensor(np.asarray(a, dtype=np.float64))
+
+
+def _split(params: torch.Tensor):
+    out, o = [], 0
+    for co, ci in SIZES:
+        out.append(params[o:o + co * ci * 9].reshape(co, ci, 3, 3))
+        o += co * ci * 9
+    return out
+
+
+def network(st, params: torch.Tensor) -> torch.Tensor:
+    """out [27, n, n] of the network on one stencil field st [9, n, n]."""
+    st = _t(st)
+    w1, w2, w3, wf = _split(params)
+    a = (st / st[4]).unsqueeze(0)
+    for w in (w1, w2, w3):
+        z = F.conv2d(a, w, padding=1)
+        a = torch.where(z > 0, z, 0.01 * z)
+    return F.conv2d(a, wf, padding=1)[0]
+
+
+def kernels(st, params: torch.Tensor, omega: float = 2.0 / 3.0) -> torch.Tensor:
+    """The stack K [3, 9, n, n]: K1 = (omega delta + out_1)/D, K_k = delta + out_k (k = 2, 3)."""
+    st = _t(st)
+    out = network(st, params).reshape(NK, 9, *st.shape[1:])
+    delta = torch.zeros(9, 1, 1, dtype=torch.float64)
+    delta[4] = 1.0
+    k1 = (omega * delta + out[0]) / st[4]
+    return torch.stack([k1] + [delta + out[k] for k in range(1, NK)])
+
+
+def _shift(v: torch.Tensor, di: int, dj: int) -> torch.Tensor:
+    """u(x + (di, dj)) on the grid, zero where x + (di, dj) leaves it."""
+    p = F.pad(v, (1, 1, 1, 1))
+    n = v.shape[-1]
+    return p[..., 1 + di:1 + di + n, 1 + dj:1 + dj + n]
+
+
+def apply_kernel(K: torch.Tensor, v: torch.Tensor) -> torch.Tensor:
+    """(K v)(x) = sum_t K[t](x) v(x + d_t), v zero outside the grid."""
+    return sum(K[t] * _shift(v, t // 3 - 1, t % 3 - 1) for t in range(9))
+
+
+def apply_kernel_T(K: torch.Tensor, w: torch.Tensor) -> torch.Tensor:
+    """(K^T w)(y) = sum_t K[t](y - d_t) w(y - d_t)."""
+    return sum(_shift(K[t] * w, -(t // 3 - 1), -(t % 3 - 1)) for t in range(9))
+
+
+def apply_H(Ks: torch.Tensor, v: torch.Tensor) -> torch.Tensor:
+    for K in Ks:
+        v = apply_kernel(K, v)
+    return v
+
+
+def apply_HT(Ks: torch.Tensor, w: torch.Tensor) -> torch.Tensor:
+    for K in reversed(list(Ks)):
+        w = apply_kernel_T(K, w)
+    return w
+
+
+def apply_A(st, v: torch.Tensor) -> torch.Tensor:
+    return apply_kernel(_t(st), v)
+
+
+def restrict(r: torch.Tensor) -> torch.Tensor:
+    """P^T r: coarse point I sits at fine 2I+1, weights 1/4 [1 2 1; 2 4 2; 1 2 1] x 4."""
+    w = torch.tensor([[0.25, 0.5, 0.25], [0.5, 1.0, 0.5], [0.25, 0.5, 0.25]], dtype=torch.float64)
+    return F.conv2d(r[None, None], w[None, None], stride=2)[0, 0]
+
+
+def prolong(ec: torch.Tensor, n: int) -> torch.Tensor:
+    """P e_c (bilinear): the transpose of restrict."""
+    w = torch.tensor([[0.25, 0.5, 0.25], [0.5, 1.0, 0.5], [0.25, 0.5, 0.25]], dtype=torch.float64)
+    return F.conv_transpose2d(ec[None, None], w[None, None], stride=2)[0, 0][:n, :n]
+
+
+def loss(st, coarse_st, params: torch.Tensor, z, omega: float = 2.0 / 3.0, cycles: int = 1) -> torch.Tensor:
+    """(1/Z) sum_j ||E^k z_j||^2 / n^2 with E = S C S, S = I - H A, C = I - P A_c^{-1} P^T A
+    (Sec. 3.2, eq. twogrid; A_c = P^T A P is given as the coarse field coarse_st)."""
+    st = _t(st)
+    n = st.shape[-1]
+    nc = (n - 1) // 2
+    Ks = kernels(st, params, omega)
+    Ac = _dense(coarse_st)
+    total = torch.zeros((), dtype=torch.float64)
+    z = _t(z)
+    for zj in z:
+        e = zj
+        for _ in range(cycles):
+            e = e - apply_H(Ks, apply_A(st, e))
+            rc = restrict(apply_A(st, e))
+            e = e - prolong(torch.linalg.solve(Ac, rc.reshape(-1)).reshape(nc, nc), n)
+            e = e - apply_H(Ks, apply_A(st, e))
+        total = total + (e * e).sum()
+    return total / (z.shape[0] * n * n)
+
+
+def _dense(st) -> torch.Tensor:
+    st = _t(st)
+    n = st.shape[-1]
+    A = torch.zeros(n * n, n * n, dtype=torch.float64)
+    for t in range(9):
+        di, dj = t // 3 - 1, t % 3 - 1
+        for i in range(n):
+            for j in range(n):
+                ii, jj = i + di, j + dj
+                if 0 <= ii < n and 0 <= jj < n:
+                    A[i * n + j, ii * n + jj] = st[t, i, j]
+    return A
+
+
+def loss_and_grad(st, coarse_st, params, z, omega: float = 2.0 / 3.0, cycles: int = 1):
+    p = _t(params).clone().requires_grad_(True)
+    L = loss(st, coarse_st, p, z, omega, cycles)
+    (g,) = torch.autograd.grad(L, p)
+    return float(L.detach()), g.numpy()
+
+
+def k1_params(params) -> np.ndarray:
+    """The k = 1 network that the stack reduces to when out_2 = out_3 = 0: the same
+    convolutions and the first nine rows of the last layer."""
+    params = _f64(params)
+    conv = sum(co * ci * 9 for co, ci in SIZES[:3])
+    return np.concatenate([params[:conv], params[conv:conv + 9 * 27]])

@@ -1,0 +1,99 @@
+"""Pins of the k = 3 stack oracle (Sec. 4, Sec. 4.2: three output kernels per point).
+
+The stack reduces to the k = 1 network when the last layer's rows of kernels 2 and 3 are
+zero; there the oracle must agree with the independent C oracle (network, loss, gradient).
+Its operators are checked against the C oracle's, the stack's transpose by the adjoint
+identity, and the remaining gradient by central differences.
+"""
+import math
+
+import numpy as np
+import torch
+
+import oracle as O
+from oracle import stack as OS
+
+
+def _rng(seed):
+    return np.random.default_rng(seed)
+
+
+def _params(seed, scale=0.3, zero_rest=False):
+    p = _rng(seed).standard_normal(OS.NPARAMS) * scale
+    if zero_rest:
+        p[-18 * 27:] = 0.0  # rows of kernels 2 and 3 in the last layer
+    return p
+
+
+def test_parameter_count():
+    assert OS.NPARAMS == 1017 + 27 * 27 == 1746
+    assert OS.k1_params(np.zeros(OS.NPARAMS)).size == O.hypernet_nparams()
+
+
+def test_stack_reduces_to_the_k1_network_of_the_c_oracle():
+    n = 11
+    st = O.varcoef5_field(n, np.exp(_rng(1).standard_normal((n + 1, n + 1))))
+    p = _params(2, zero_rest=True)
+    K = OS.kernels(st, torch.from_numpy(p)).numpy()
+    W = O.hypernet_forward(st, OS.k1_params(p))
+    assert np.allclose(K[0], W, rtol=1e-12, atol=1e-14)
+    delta = np.zeros((9, n, n))
+    delta[4] = 1.0
+    assert np.array_equal(K[1], delta) and np.array_equal(K[2], delta)
+
+
+def test_operators_match_the_c_oracle():
+    rng = _rng(3)
+    n = 15
+    st = O.const_field(n, O.q1_rotated_stencil(0.05, 0.4))
+    v = rng.standard_normal((n, n))
+    W = rng.standard_normal((9, n, n))
+    tv = torch.from_numpy(v)
+    assert np.allclose(OS.apply_A(st, tv).numpy(), O.apply(st, v), rtol=0, atol=1e-12)
+    assert np.allclose(OS.apply_kernel(torch.from_numpy(W), tv).numpy(), O.apply_H(W, v), rtol=0, atol=1e-12)
+    assert np.allclose(OS.apply_kernel_T(torch.from_numpy(W), tv).numpy(), O.apply_HT(W, v), rtol=0, atol=1e-12)
+    assert np.allclose(OS.restrict(tv).numpy(), O.restrict(v), rtol=0, atol=1e-12)
+    ec = rng.standard_normal(((n - 1) // 2, (n - 1) // 2))
+    assert np.allclose(OS.prolong(torch.from_numpy(ec), n).numpy(), O.prolong(ec, n), rtol=0, atol=1e-12)
+
+
+def test_stack_is_three_chained_kernels_and_its_transpose_the_adjoint():
+    rng = _rng(4)
+    n = 9
+    Ks = torch.from_numpy(rng.standard_normal((3, 9, n, n)))
+    u, w = (torch.from_numpy(a) for a in rng.standard_normal((2, n, n)))
+    ref = O.apply_H(Ks[2].numpy(), O.apply_H(Ks[1].numpy(), O.apply_H(Ks[0].numpy(), u.numpy())))
+    assert np.allclose(OS.apply_H(Ks, u).numpy(), ref, rtol=0, atol=1e-11)
+    lhs = float((OS.apply_H(Ks, u) * w).sum())
+    assert math.isclose(lhs, float((u * OS.apply_HT(Ks, w)).sum()), rel_tol=1e-12)
+
+
+def test_loss_and_gradient_at_the_k1_point_equal_the_c_oracle():
+    n = 15
+    st = O.const_field(n, O.q1_rotated_stencil(0.05, 0.7))
+    z = _rng(5).standard_normal((2, n, n))
+    p = _params(6, scale=0.05, zero_rest=True)
+    L, g = OS.loss_and_grad(st, O.rap(st), p, z)
+    Lc, gc = O.cnn_loss_and_grad(st, OS.k1_params(p), z)
+    assert math.isclose(L, Lc, rel_tol=1e-11)
+    assert np.allclose(OS.k1_params(g), gc, rtol=1e-8, atol=1e-12 * np.abs(gc).max())
+
+
+def test_gradient_matches_central_differences():
+    n = 7
+    st = O.varcoef5_field(n, np.exp(0.5 * _rng(7).standard_normal((n + 1, n + 1))))
+    stc = O.rap(st)
+    z = _rng(8).standard_normal((2, n, n))
+    p = _params(9, scale=0.05)
+    _, g = OS.loss_and_grad(st, stc, p, z, cycles=2)
+    idx = _rng(10).choice(OS.NPARAMS, 40, replace=False)
+    idx = np.concatenate([idx, np.arange(OS.NPARAMS - 30, OS.NPARAMS)])  # include kernels 2, 3
+    h = 1e-6
+    for k in idx:
+        pp, pm = p.copy(), p.copy()
+        pp[k] += h
+        pm[k] -= h
+        lp = float(OS.loss(st, stc, torch.from_numpy(pp), z, cycles=2))
+        lm = float(OS.loss(st, stc, torch.from_numpy(pm), z, cycles=2))
+        fd = (lp - lm) / (2 * h)
+        assert abs(g[k] - fd) <= 1e-6 * np.abs(g).max() + 1e-10, (k, g[k], fd)
