@@ -349,9 +349,17 @@ def run_rotated_batch(n: int, nprob: int, weights, rank: int):
     adaptive = load_adaptive()
     nets = {"cnn": weights.cuda() if weights is not None else None,
             "cnn_adaptive": T.adaptive_params(adaptive, n).cuda() if adaptive is not None else None}
+    # the paper's alpha-CNN: the per-problem linear smoothers trained for these (eps, theta)
+    # (the batch seed gives the same pairs at every size), mapped onto this hierarchy
+    lin = load_linear_batch(params, n) if rank == 0 else None
+    if lin is not None:
+        nets["linear_alpha"] = lin.cuda()
     out = {"n": n, "nprob": nprob}
     for kind in ["jacobi"] + [k for k, v in nets.items() if v is not None]:
-        mg = S.MultigridSolver(problems, "jacobi" if kind == "jacobi" else "cnn", net_params=nets.get(kind))
+        if kind == "linear_alpha":
+            mg = S.MultigridSolver(problems, "cnn", nets[kind], net_arch="linear", per_problem=True)
+        else:
+            mg = S.MultigridSolver(problems, "jacobi" if kind == "jacobi" else "cnn", net_params=nets.get(kind))
         ms, cyc, st = timed_solve(mg, b, reps=3)
         out[kind] = {"ms": ms, "max_cycles": int(cyc.max()), "mean_cycles": float(cyc.mean()),
                      "converged": int(st) == 0,
