@@ -616,6 +616,7 @@ __global__ void __launch_bounds__(NT) k_update_residual(const __grid_constant__ 
   __shared__ __align__(128) float xh[RES_H * XW];
   __shared__ __align__(128) float xl[RES_H * XW];
   __shared__ __align__(128) float es[RES_H * XW];
+  __shared__ __align__(128) float bb[TB * TB];
   __shared__ __align__(8) uint64_t bar;
   float s[9];
 #pragma unroll
@@ -625,10 +626,11 @@ __global__ void __launch_bounds__(NT) k_update_residual(const __grid_constant__ 
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     fence_mbar_init();
-    mbar_arrive_expect_tx(&bar, 3 * RES_H * XW * sizeof(float));
+    mbar_arrive_expect_tx(&bar, (3 * RES_H * XW + TB * TB) * sizeof(float));
     tma_load_3d(xh, &X.xh, &bar, C0 - 4, R0 - 1, p);
     tma_load_3d(xl, &X.xl, &bar, C0 - 4, R0 - 1, p);
     tma_load_3d(es, &E, &bar, C0 - 4, R0 - 1, p);
+    tma_load_3d(bb, &X.b, &bar, C0, R0, p);
   }
   __syncthreads();
   if (!tile_wait(&bar, state[p])) return;
@@ -644,8 +646,8 @@ __global__ void __launch_bounds__(NT) k_update_residual(const __grid_constant__ 
   __syncthreads();
   const size_t po = (size_t)p * n * L.pitch;
   const float acc = inner_tile(R0, C0, n)
-                        ? residual_tile<SK, true>(L, s, xh, xl, nullptr, R0, C0, rnew + po, xhi + po, xlo + po, b0 + po)
-                        : residual_tile<SK, false>(L, s, xh, xl, nullptr, R0, C0, rnew + po, xhi + po, xlo + po, b0 + po);
+                        ? residual_tile<SK, true>(L, s, xh, xl, bb, R0, C0, rnew + po, xhi + po, xlo + po)
+                        : residual_tile<SK, false>(L, s, xh, xl, bb, R0, C0, rnew + po, xhi + po, xlo + po);
   float rhi, rlo;
   if (block_partial_and_last<NT>(acc, partials + (size_t)p * ntiles_max, &state[p].counter, ntiles, tile, rhi, rlo)) {
     if (threadIdx.x == 0) decide(state[p], rhi, rlo, rtol, max_cycles);
