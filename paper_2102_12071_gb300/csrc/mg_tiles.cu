@@ -603,8 +603,7 @@ __global__ void __launch_bounds__(NT) k_update_residual(const __grid_constant__ 
                                                         const ProbDev* __restrict__ probs, ProbState* __restrict__ state,
                                                         float* __restrict__ partials, int ntiles_max, float rtol,
                                                         int max_cycles, float* __restrict__ xhi, float* __restrict__ xlo,
-                                                        float* __restrict__ rnew, const float* __restrict__ b0,
-                                                        const int* __restrict__ act) {
+                                                        float* __restrict__ rnew, const int* __restrict__ act) {
   pdl_trigger();
   const int p = act ? act[blockIdx.y] : blockIdx.y;
   const LevelDev L = probs[p].lv[0];
@@ -782,10 +781,10 @@ cudaError_t launch_update_residual(const CycleArgs& a, const CUtensorMap& e0, fl
   cudaError_t e;
   if (a.sk == SK_CONST)
     e = launch_pdl(a.pdl, k_update_residual<SK_CONST>, grid, dim3(NT), 0, a.stream, X, e0, (const ProbDev*)a.probs,
-                   a.state, a.partials, a.ntiles_max, rtol, max_cycles, xhn, xln, rnew, a.b0, a.active);
+                   a.state, a.partials, a.ntiles_max, rtol, max_cycles, xhn, xln, rnew, a.active);
   else
     e = launch_pdl(a.pdl, k_update_residual<SK_FIELD>, grid, dim3(NT), 0, a.stream, X, e0, (const ProbDev*)a.probs,
-                   a.state, a.partials, a.ntiles_max, rtol, max_cycles, xhn, xln, rnew, a.b0, a.active);
+                   a.state, a.partials, a.ntiles_max, rtol, max_cycles, xhn, xln, rnew, a.active);
   a.prof->end(a.stream);
   return e;
 }
