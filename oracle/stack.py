@@ -157,3 +157,52 @@ def k1_params(params) -> np.ndarray:
     params = _f64(params)
     conv = sum(co * ci * 9 for co, ci in SIZES[:3])
     return np.concatenate([params[:conv], params[conv:conv + 9 * 27]])
+
+
+class StackMultigrid:
+    """Galerkin hierarchy of st0 (Algorithm 1, V(1,1)) smoothed on every level but the
+    coarsest by the stack of the one network evaluated on that level's own stencil field."""
+
+    def __init__(self, st0, params, omega: float = 2.0 / 3.0, coarsest_n: int = 3):
+        from .oracle import dense_matrix, rap
+
+        self.st = [_f64(st0)]
+        while self.st[-1].shape[1] > coarsest_n and (self.st[-1].shape[1] - 1) % 2 == 0:
+            self.st.append(rap(self.st[-1]))
+        p = _t(params)
+        with torch.no_grad():
+            self.K = [kernels(s, p, omega) for s in self.st[:-1]]
+        self.Ac = dense_matrix(self.st[-1])
+
+    def _smooth(self, l, f, u):
+        from .oracle import apply
+
+        with torch.no_grad():
+            h = apply_H(self.K[l], torch.from_numpy(f - apply(self.st[l], u))).numpy()
+        return u + h
+
+    def _level(self, l, f, u):
+        from .oracle import apply, prolong, restrict
+
+        u = self._smooth(l, f, u)
+        rc = restrict(f - apply(self.st[l], u))
+        if l + 1 == len(self.st) - 1:
+            nc = rc.shape[0]
+            uc = np.linalg.solve(self.Ac, rc.reshape(-1)).reshape(nc, nc)
+        else:
+            uc = self._level(l + 1, rc, np.zeros_like(rc))
+        u = u + prolong(uc, self.st[l].shape[1])
+        return self._smooth(l, f, u)
+
+    def solve(self, b, rtol: float = 1e-8, max_cycles: int = 1000):
+        """V-cycles from x = 0 until ||b - A x|| / ||b|| < rtol; (x, hist)."""
+        from .oracle import apply
+
+        b = _f64(b)
+        x = np.zeros_like(b)
+        bn = np.linalg.norm(b)
+        hist = [1.0]
+        while len(hist) - 1 < max_cycles and not hist[-1] < rtol:
+            x = self._level(0, b, x)
+            hist.append(np.linalg.norm(b - apply(self.st[0], x)) / bn)
+        return x, np.array(hist)
