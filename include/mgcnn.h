@@ -128,7 +128,7 @@ typedef enum {
   MG_NET_FC = 1,   /* fully connected 81->40->40->40->9 on the 3x3 neighbourhood's stencils
                       (Sec. 4.2 parameterisation with fully connected layers, Sec. 6.2:
                       6 800 params)                                                      */
-  MG_NET_LINEAR = 2 /* the shared-kernel linear smoother of Sec. 6 (eq.
+  MG_NET_LINEAR = 2, /* the shared-kernel linear smoother of Sec. 6 (eq.
                       full-coarsening-smoother): H = f5(f4(f3(f2(f1(.))))) + f6, each f_k a
                       3x3 convolution (tap layout above) whose input is zero outside the
                       grid, the same six kernels at every point of every problem of a
@@ -136,6 +136,14 @@ typedef enum {
                       the network has no input: its weights are the smoother.  Weighted
                       Jacobi is f1..f4 = identity (tap 4 = 1), f5 = 0, f6 = omega/D at tap 4.
                       Any stencil kind.                                                  */
+  MG_NET_CONV3 = 3  /* the convolutional network of MG_NET_CONV with 27 outputs per point:
+                      three 3x3 kernels applied as a stack H v = K3(K2(K1 v)), each
+                      layer's input zero outside the grid (Sec. 4, Sec. 4.2: k = 3),
+                      K1 = (omega delta + out_1)/D, K2 = delta + out_2, K3 = delta + out_3;
+                      last layer wf[27][3][3][3] (row 9k + t: tap t of kernel k+1), 1 746
+                      params.  Solve, V-cycle, smoother and FGMRES only (no training, no
+                      smoother_transpose); levels above 63 run in the batched level
+                      kernels.                                                           */
 } mg_net_arch;
 
 typedef struct mg_ctx mg_ctx;

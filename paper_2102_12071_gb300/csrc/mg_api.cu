@@ -71,8 +71,11 @@ mg_status make_plan(const mg_problem* probs, int nprob, const mg_options* o, Pla
   if (o->coarsest_n != 3 && o->coarsest_n != 7) return fail(MG_ERR_UNSUPPORTED, "coarsest_n must be 3 or 7");
   if (!(o->omega > 0.f) || !(o->omega < 2.f)) return fail(MG_ERR_INVALID_ARG, "omega must be in (0, 2)");
   if (o->net_levels < 0 || o->net_levels > MG_MAXL) return fail(MG_ERR_INVALID_ARG, "net_levels out of range");
-  if (o->net_arch != MG_NET_CONV && o->net_arch != MG_NET_FC && o->net_arch != MG_NET_LINEAR)
+  if (o->net_arch != MG_NET_CONV && o->net_arch != MG_NET_FC && o->net_arch != MG_NET_LINEAR &&
+      o->net_arch != MG_NET_CONV3)
     return fail(MG_ERR_INVALID_ARG, "unknown net_arch");
+  if (o->smoother == MG_SMOOTH_CNN && o->net_arch == MG_NET_CONV3 && (o->smoother_transpose || o->conv_bf16))
+    return fail(MG_ERR_UNSUPPORTED, "the three-kernel network runs in FP32 and without smoother_transpose");
   if (o->net_per_problem != 0 && o->net_per_problem != 1) return fail(MG_ERR_INVALID_ARG, "net_per_problem must be 0 or 1");
   if (o->net_per_problem && !(o->smoother == MG_SMOOTH_CNN && o->net_arch == MG_NET_LINEAR))
     return fail(MG_ERR_UNSUPPORTED, "per-problem parameter sets need the linear smoother (MG_NET_LINEAR)");
@@ -107,6 +110,7 @@ mg_status make_plan(const mg_problem* probs, int nprob, const mg_options* o, Pla
   P.sk = nconst ? SK_CONST : SK_FIELD;
   P.hk = o->smoother == MG_SMOOTH_JACOBI ? HK_JACOBI
          : o->net_arch == MG_NET_LINEAR  ? HK_LINEAR
+         : o->net_arch == MG_NET_CONV3   ? HK_STACK3
                                          : (P.sk == SK_CONST ? HK_TABLE : HK_FIELD);
   if (o->smoother_transpose && P.hk == HK_TABLE)
     return fail(MG_ERR_UNSUPPORTED, "smoother_transpose needs per-point problems (kinds VARCOEF5, FIELD)");
@@ -124,7 +128,7 @@ mg_status make_plan(const mg_problem* probs, int nprob, const mg_options* o, Pla
   P.tail_solve = P.lstar == 0;
   P.nu1 = o->nu1;
   P.nu2 = o->nu2;
-  P.generic = P.hk == HK_LINEAR || P.nu1 != 1 || P.nu2 != 1;
+  P.generic = P.hk == HK_LINEAR || P.hk == HK_STACK3 || P.nu1 != 1 || P.nu2 != 1;
   const int nt = tiles_per_side(n);
   P.ntiles_max = nt * nt;
   if (tail_smem_bytes(P.nl, P.lstar, L, P.hk) > MG_TAIL_SMEM_MAX)
@@ -325,6 +329,7 @@ static size_t carve(const Plan& P, const mg_options& o, void* base, mg_ctx* ctx)
         if (P.hk == HK_FIELD) v.W = c.take<float>(9 * nn);
         else if (P.hk == HK_TABLE) v.W = c.take<float>((size_t)9 * v.T * v.T);
         else if (P.hk == HK_LINEAR) v.W = lin + (size_t)MG_NPARAMS_LIN * ((o.net_per_problem ? p * lin_lev : 0) + l);
+        else if (P.hk == HK_STACK3) v.W = c.take<float>(27 * nn);
       }
     }
     d.m = P.nl[P.L - 1] * P.nl[P.L - 1];
@@ -388,7 +393,8 @@ size_t mg_workspace_size(const mg_problem* problems, int nprob, const mg_options
 int mg_net_nparams(void) { return MG_NPARAMS; }
 
 int mg_net_param_count(int arch) {
-  return arch == MG_NET_CONV ? MG_NPARAMS : arch == MG_NET_FC ? MG_NPARAMS_FC : arch == MG_NET_LINEAR ? MG_NPARAMS_LIN : 0;
+  return arch == MG_NET_CONV ? MG_NPARAMS : arch == MG_NET_FC ? MG_NPARAMS_FC : arch == MG_NET_LINEAR ? MG_NPARAMS_LIN
+         : arch == MG_NET_CONV3 ? MG_NPARAMS_K3 : 0;
 }
 
 mg_status mg_setup(const mg_problem* problems, int nprob, const mg_options* opts, const float* net_params,
@@ -442,6 +448,7 @@ mg_status mg_setup(const mg_problem* problems, int nprob, const mg_options* opts
   a.lin_maps = &ctx->lin_maps;
   a.nu1 = P.nu1;
   a.nu2 = P.nu2;
+  a.generic = P.generic;
   if (P.generic && P.lstar > 0 && !build_lin_maps(ctx->lin_maps, ctx->arrays, a.lin_t, a.lin_wa, P.nprob, P.lstar)) {
     delete ctx;
     return fail(MG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the linear smoother's arrays");
@@ -490,6 +497,32 @@ mg_status mg_setup(const mg_problem* problems, int nprob, const mg_options* opts
                              MG_NPARAMS_LIN * sizeof(float), cudaMemcpyDeviceToDevice, s));
         }
       if (opts->smoother_transpose) CK(launch_transpose_linear(ctx->lin, groups * (P.L - 1), s));
+    } else if (P.hk == HK_STACK3 && P.L > 1) {
+      // the three-kernel network on every point of every smoothed level (constant stencils
+      // included: its kernel fields are per point, not per boundary class)
+      std::vector<NetJob> jobs;
+      int nm = 0;
+      for (int l = 0; l + 1 < P.L; ++l)
+        for (int p = 0; p < nprob; ++p) {
+          const LevelDev& v = ctx->h_probs[p].lv[l];
+          NetJob J;
+          J.st = P.sk == SK_FIELD ? v.st : nullptr;
+          J.s = P.sk == SK_CONST ? &a.probs[p].lv[l].s[0] : nullptr;  // device address
+          J.W = v.W;
+          J.n = v.n;
+          J.pad_ = 0;
+          nm = J.n > nm ? J.n : nm;
+          jobs.push_back(J);
+        }
+      const int nsets = opts->net_levels > 1 ? opts->net_levels : 1;
+      if ((size_t)jobs.size() > (size_t)P.nprob * P.L) return fail(MG_ERR_INVALID_ARG, "too many network jobs");
+      CK(cudaMemcpyAsync(ctx->d_jobs, jobs.data(), sizeof(NetJob) * jobs.size(), cudaMemcpyHostToDevice, s));
+      for (int l = 0; l + 1 < P.L; ++l) {
+        const int set = l < nsets ? l : nsets - 1;
+        CK(launch_net_forward3(ctx->d_jobs + (size_t)l * nprob, nprob, P.nl[l], net_params + (size_t)set * MG_NPARAMS_K3,
+                               opts->omega, s));
+      }
+      CK(cudaStreamSynchronize(s));  // the host vector must outlive the asynchronous copy
     } else if (P.hk != HK_JACOBI && P.L > 1) {
       // jobs level-major, so that every level can take its own parameter set
       std::vector<NetJob> jobs;
@@ -565,8 +598,8 @@ mg_status mg_get_stencil(const mg_ctx* ctx, int prob, int level, float* out, voi
 mg_status mg_get_kernels(const mg_ctx* ctx, int prob, int level, float* out, void* stream) {
   if (!ctx || !out || prob < 0 || prob >= ctx->plan.nprob || level < 0 || level >= ctx->plan.L - 1)
     return fail(MG_ERR_INVALID_ARG, "mg_get_kernels: bad arguments (smoothed levels are 0..L-2)");
-  if (ctx->plan.hk == HK_LINEAR)
-    return fail(MG_ERR_UNSUPPORTED, "mg_get_kernels: the linear smoother is a chain of convolutions, not one 3x3 kernel per point");
+  if (ctx->plan.hk == HK_LINEAR || ctx->plan.hk == HK_STACK3)
+    return fail(MG_ERR_UNSUPPORTED, "mg_get_kernels: the smoother is a chain of convolutions, not one 3x3 kernel per point");
   CK(launch_expand_kernels(ctx->args.probs, prob, level, ctx->plan.nl[level], ctx->plan.sk, ctx->plan.hk,
                            ctx->opts.omega, out, (cudaStream_t)stream));
   return MG_OK;
@@ -575,6 +608,8 @@ mg_status mg_get_kernels(const mg_ctx* ctx, int prob, int level, float* out, voi
 mg_status mg_smoother_apply(mg_ctx* ctx, int prob, int level, const float* f, float* u, int nsteps, void* stream) {
   if (!ctx || !f || !u || prob < 0 || prob >= ctx->plan.nprob || level < 0 || level >= ctx->plan.L - 1 || nsteps < 0)
     return fail(MG_ERR_INVALID_ARG, "mg_smoother_apply: bad arguments (smoothed levels are 0..L-2)");
+  if (ctx->plan.hk == HK_STACK3)
+    return fail(MG_ERR_UNSUPPORTED, "mg_smoother_apply: not implemented for the three-kernel network");
   CycleArgs a = ctx->args;
   a.stream = (cudaStream_t)stream;
   CK(launch_smoother(a, prob, level, f, u, nsteps));

@@ -25,11 +25,13 @@
 #define MG_NPARAMS 1260
 #define MG_NPARAMS_FC 6800  // the fully connected network, 81 -> 40 -> 40 -> 40 -> 9
 #define MG_NPARAMS_LIN 54   // the shared-kernel linear smoother of one level: six 3x3 kernels
+#define MG_NPARAMS_K3 1746  // the convolutional network with three output kernels (27 outputs)
 
 enum { SK_CONST = 0, SK_FIELD = 1 };                 // stencil storage
 // smoother storage: omega/D; per-point kernels of a constant stencil by boundary class;
-// per-point kernels of every point; the shared-kernel linear chain (MG_NPARAMS_LIN per level)
-enum { HK_JACOBI = 0, HK_TABLE = 1, HK_FIELD = 2, HK_LINEAR = 3 };
+// per-point kernels of every point; the shared-kernel linear chain (MG_NPARAMS_LIN per level);
+// a stack of three per-point kernels of every point ([27][n][n], applied K3(K2(K1 v)))
+enum { HK_JACOBI = 0, HK_TABLE = 1, HK_FIELD = 2, HK_LINEAR = 3, HK_STACK3 = 4 };
 
 struct LevelDev {
   int n;
@@ -37,7 +39,8 @@ struct LevelDev {
   float* r;            // residual / right-hand side of the error equation, [n][pitch]
   float* e;            // correction on this level, [n][pitch]
   float* st;           // SK_FIELD: stencil field [9][n][n]
-  float* W;            // HK_TABLE: [9][T][T]; HK_FIELD: [9][n][n]; HK_LINEAR: [6][9], shared
+  float* W;            // HK_TABLE: [9][T][T]; HK_FIELD: [9][n][n]; HK_LINEAR: [6][9], shared;
+                       // HK_STACK3: [27][n][n]
   float s[9];          // SK_CONST: stencil of this level (Galerkin product of the finer one)
   int pitch;           // row pitch of r, e and f in floats (multiple of 32: 128-byte rows)
   float* f;            // final correction written by the up-sweep of a tiled level >= 1 (its
@@ -52,13 +55,16 @@ struct LevelDev {
     else { constexpr int SK_ = SK_FIELD, HK_ = HK_FIELD; CALL; }                                           \
   } while (0)
 
-// MG_DISPATCH plus the linear smoother: for the kernels that run every smoother kind (the
-// one-CTA coarse tail); the tiled and cluster kernels never see HK_LINEAR
+// MG_DISPATCH plus the linear smoother and the kernel stack: for the kernels that run every
+// smoother kind (the one-CTA coarse tail); the tiled and cluster kernels never see those
 #define MG_DISPATCH_T(SKv, HKv, CALL)                                                   \
   do {                                                                                  \
     if ((HKv) == HK_LINEAR) {                                                           \
       if ((SKv) == SK_CONST) { constexpr int SK_ = SK_CONST, HK_ = HK_LINEAR; CALL; }   \
       else { constexpr int SK_ = SK_FIELD, HK_ = HK_LINEAR; CALL; }                     \
+    } else if ((HKv) == HK_STACK3) {                                                    \
+      if ((SKv) == SK_CONST) { constexpr int SK_ = SK_CONST, HK_ = HK_STACK3; CALL; }   \
+      else { constexpr int SK_ = SK_FIELD, HK_ = HK_STACK3; CALL; }                     \
     } else {                                                                            \
       MG_DISPATCH(SKv, HKv, CALL);                                                      \
     }                                                                                   \

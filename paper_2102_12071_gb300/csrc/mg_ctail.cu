@@ -342,7 +342,7 @@ cudaError_t prepare_ctail(const CycleArgs& a) {
 }
 
 cudaError_t launch_ctail(const CycleArgs& a) {
-  if (a.hk == HK_LINEAR) return cudaErrorNotSupported;  // never planned with the linear smoother
+  if (a.hk == HK_LINEAR || a.hk == HK_STACK3) return cudaErrorNotSupported;  // never planned with these smoothers
   const int ls = a.lstar, L = a.L;
   const size_t smem = ctail_smem_bytes(a.nl, ls, L, a.hk);
   cudaError_t e = prepare_ctail(a);

@@ -388,6 +388,7 @@ cudaError_t launch_level_residual(const CycleArgs& a, int p, int l, const float*
 
 cudaError_t launch_smoother(const CycleArgs& a, int p, int l, const float* f, float* u, int nsteps) {
   if (a.hk == HK_LINEAR) return launch_smoother_linear(a, p, l, f, u, nsteps);
+  if (a.hk == HK_STACK3) return cudaErrorNotSupported;  // refused by mg_smoother_apply
   const int n = a.nl[l];
   const int nb = (n * n + 255) / 256;
   for (int s = 0; s < nsteps; ++s) {

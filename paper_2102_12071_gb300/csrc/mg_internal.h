@@ -141,6 +141,8 @@ struct CycleArgs {
   const LevelArrays* arrays;      // base pointers of the level arrays (host copy)
   const LinMaps* lin_maps;        // tensor maps of the batched level path (host copy)
   int nu1, nu2;                   // smoothing steps; other than 1 only on the batched level path
+  int generic;                    // levels above the tail on the batched level path (mg_linear.cu):
+                                  // the linear smoother, the kernel stack, or nu other than 1
 };
 
 
@@ -246,6 +248,9 @@ cudaError_t launch_net_forward(const NetJob* jobs_dev, int njobs, int nmax, cons
                                cudaStream_t s);
 cudaError_t launch_net_forward_batch(const NetBatch& batch, int nfields, const float* params, float omega, int bf16,
                                      cudaStream_t s);
+// the three-kernel network (MG_NET_CONV3): [27][n][n] per job, FP32
+cudaError_t launch_net_forward3(const NetJob* jobs_dev, int njobs, int nmax, const float* params, float omega,
+                                cudaStream_t s);
 cudaError_t launch_copy_rel(const ProbState* state, float* rel, int nprob, cudaStream_t s);
 int net_backward_ctas(int n, int nfields);
 // the fully connected network (mg_netfc.cu); the backward needs fc_backward_floats scratch

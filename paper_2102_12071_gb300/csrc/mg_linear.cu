@@ -214,6 +214,35 @@ __global__ void __launch_bounds__(LT) k_jac_H(const ProbDev* __restrict__ probs,
   }
 }
 
+// dst = K_k(src) (MODE 0) or dst += K_k(src) (MODE 2): one layer of the three-kernel stack
+// (MG_NET_CONV3), the kernel of point x is W[9k .. 9k+8](x) of the level's [27][n][n] field,
+// src zero outside the grid
+template <int MODE>
+__global__ void __launch_bounds__(LT) k_stack_conv(const ProbDev* __restrict__ probs,
+                                                   const ProbState* __restrict__ state, const int* __restrict__ act,
+                                                   int l, int k, const float* src, float* dst) {
+  pdl_trigger();
+  pdl_wait();
+  const int p = lin_problem(state, act, -1, blockIdx.z);
+  if (p < 0) return;
+  const LevelDev L = probs[p].lv[l];
+  const int n = L.n, pitch = L.pitch;
+  const int j = blockIdx.x * PX + threadIdx.x;
+  if (j >= n) return;
+  const size_t off = (size_t)p * n * pitch, nn = (size_t)n * n;
+  const float* Wk = L.W + (size_t)9 * k * nn;
+  for (int y = 0; y < RY; ++y) {
+    const int i = blockIdx.y * PY * RY + y * PY + threadIdx.y;
+    if (i >= n) break;
+    float w[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) w[t] = __ldg(Wk + t * nn + (size_t)i * n + j);
+    const float h = conv_at(w, src + off, pitch, n, i, j);
+    float* d = dst + off + (size_t)i * pitch + j;
+    *d = MODE == 2 ? *d + h : h;
+  }
+}
+
 // ------------------------------------------------------------------ the tiled chain
 // One CTA per 32 x 32 output tile.  Coordinates below are in the frame of the input tile
 // u: row 0 = grid row R0 - 5, column 0 = grid column C0 - 8 (the TMA box starts 8 columns
@@ -499,6 +528,27 @@ static cudaError_t lin_H(const CycleArgs& a, int l, const CUtensorMap& mu, float
 static cudaError_t smooth_H(const CycleArgs& a, int l, const float* u, const CUtensorMap& mu, float* dst, bool acc,
                             int cls) {
   if (a.hk == HK_LINEAR) return lin_H(a, l, mu, dst, acc, cls);
+  if (a.hk == HK_STACK3) {  // K3(K2(K1 u)) through the scratch vectors
+    const dim3 grid = point_grid(a.nl[l], nlaunch(a));
+    const ProbDev* probs = a.probs;
+    const ProbState* cst = a.state;
+    const float* src = u;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+      float* out = k == 2 ? dst : (k == 0 ? a.lin_wa : a.lin_wb);
+      a.prof->launches++;
+      a.prof->begin(cls, a.stream);
+      if (k < 2)
+        e = launch_pdl(a.pdl, k_stack_conv<0>, grid, dim3(PX, PY), 0, a.stream, probs, cst, a.active, l, k, src, out);
+      else if (acc)
+        e = launch_pdl(a.pdl, k_stack_conv<2>, grid, dim3(PX, PY), 0, a.stream, probs, cst, a.active, l, k, src, out);
+      else
+        e = launch_pdl(a.pdl, k_stack_conv<0>, grid, dim3(PX, PY), 0, a.stream, probs, cst, a.active, l, k, src, out);
+      a.prof->end(a.stream);
+      src = out;
+    }
+    return e;
+  }
   a.prof->launches++;
   a.prof->begin(cls, a.stream);
   const dim3 grid = point_grid(a.nl[l], nlaunch(a));

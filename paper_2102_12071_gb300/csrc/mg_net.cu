@@ -60,11 +60,16 @@ __device__ __forceinline__ void conv_layer(const float* __restrict__ w, const fl
   }
 }
 
-// jobs == nullptr: job y is field y of a uniform batch (batch.st/W + y * batch.stride)
+// jobs == nullptr: job y is field y of a uniform batch (batch.st/W + y * batch.stride).
+// NK output kernels per point: NK = 1 gives W = (omega delta + out) / D; NK = 3 the stack
+// K1 = (omega delta + out_1) / D, K2 = delta + out_2, K3 = delta + out_3 ([27][n][n] out).
+template <int NK>
 __global__ void __launch_bounds__(NET_THREADS) k_net_forward(const NetJob* __restrict__ jobs, NetBatch batch,
                                                              const float* __restrict__ params, float omega,
                                                              int bf16) {
-  __shared__ float w[MG_NPARAMS];
+  constexpr int NP = NK == 1 ? MG_NPARAMS : MG_NPARAMS_K3;
+  static_assert(NK == 1 || NP == OFF_WF + 27 * 27, "parameter layout of the three-kernel network");
+  __shared__ float w[NP];
   __shared__ float bufA[9 * S0 * S0];   // a0, later a2
   __shared__ float bufB[7 * S1 * S1];   // a1, later a3
   NetJob J;
@@ -80,7 +85,7 @@ __global__ void __launch_bounds__(NET_THREADS) k_net_forward(const NetJob* __res
   const int ntx = (n + OT - 1) / OT;
   if ((int)blockIdx.x >= ntx * ntx) return;
   const int oy = (blockIdx.x / ntx) * OT, ox = (blockIdx.x % ntx) * OT;
-  for (int t = threadIdx.x; t < MG_NPARAMS; t += NET_THREADS) w[t] = rnd_bf16(params[t], bf16);
+  for (int t = threadIdx.x; t < NP; t += NET_THREADS) w[t] = rnd_bf16(params[t], bf16);
   // a0: normalised stencil on rows/cols [oy-4, oy+OT+4)
   for (int t = threadIdx.x; t < S0 * S0; t += NET_THREADS) {
     const int i = oy - 4 + t / S0, j = ox - 4 + t % S0;
@@ -102,7 +107,7 @@ __global__ void __launch_bounds__(NET_THREADS) k_net_forward(const NetJob* __res
   __syncthreads();
   // output layer over the 3x3 window of the 3-channel map
   const size_t nn = (size_t)n * n;
-  for (int t = threadIdx.x; t < 9 * OT * OT; t += NET_THREADS) {
+  for (int t = threadIdx.x; t < 9 * NK * OT * OT; t += NET_THREADS) {
     const int o = t / (OT * OT), pos = t % (OT * OT);
     const int y = pos / OT, x = pos % OT;
     const int i = oy + y, j = ox + x;
@@ -115,8 +120,13 @@ __global__ void __launch_bounds__(NET_THREADS) k_net_forward(const NetJob* __res
 #pragma unroll
         for (int kx = 0; kx < 3; ++kx)
           acc = fmaf(w[OFF_WF + ((o * 3 + c) * 3 + ky) * 3 + kx], bufB[c * S3 * S3 + (y + ky) * S3 + x + kx], acc);
-    const float d = job_tap(J, 4, i, j);
-    J.W[o * nn + (size_t)i * n + j] = ((o == 4 ? omega : 0.f) + acc) / d;
+    float v;
+    if (o < 9) {
+      v = ((o == 4 ? omega : 0.f) + acc) / job_tap(J, 4, i, j);
+    } else {
+      v = (o % 9 == 4 ? 1.f : 0.f) + acc;
+    }
+    J.W[o * nn + (size_t)i * n + j] = v;
   }
 }
 
@@ -268,7 +278,16 @@ cudaError_t launch_net_forward(const NetJob* jobs_dev, int njobs, int nmax, cons
   const int ntx = (nmax + OT - 1) / OT;
   dim3 grid(ntx * ntx, njobs);
   NetBatch none{};
-  k_net_forward<<<grid, NET_THREADS, 0, s>>>(jobs_dev, none, params, omega, bf16);
+  k_net_forward<1><<<grid, NET_THREADS, 0, s>>>(jobs_dev, none, params, omega, bf16);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_net_forward3(const NetJob* jobs_dev, int njobs, int nmax, const float* params, float omega,
+                                cudaStream_t s) {
+  const int ntx = (nmax + OT - 1) / OT;
+  dim3 grid(ntx * ntx, njobs);
+  NetBatch none{};
+  k_net_forward<3><<<grid, NET_THREADS, 0, s>>>(jobs_dev, none, params, omega, 0);
   return cudaGetLastError();
 }
 
@@ -276,7 +295,7 @@ cudaError_t launch_net_forward_batch(const NetBatch& batch, int nfields, const f
                                      cudaStream_t s) {
   const int ntx = (batch.n + OT - 1) / OT;
   dim3 grid(ntx * ntx, nfields);
-  k_net_forward<<<grid, NET_THREADS, 0, s>>>(nullptr, batch, params, omega, bf16);
+  k_net_forward<1><<<grid, NET_THREADS, 0, s>>>(nullptr, batch, params, omega, bf16);
   return cudaGetLastError();
 }
 

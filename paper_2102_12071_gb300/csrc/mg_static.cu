@@ -135,6 +135,7 @@ extern "C" mg_status mg_solve_small_static(const mg_problem* problems, int nprob
   a.sk = SK_CONST;
   a.hk = HK_JACOBI;
   a.nu1 = a.nu2 = 1;
+  a.generic = 0;
   a.omega = opts->omega;
   a.stream = s;
   a.prof = &prof;

@@ -31,7 +31,7 @@ __host__ __device__ inline void tail_layout_tables(const int* nl, int l0, int L,
     }
   }
   t.off_s1 = t.off_s2 = -1;
-  if (hk == HK_LINEAR) {
+  if (hk == HK_LINEAR || hk == HK_STACK3) {
     const int mm = (nl[l0] + 2) * (nl[l0] + 2);
     t.off_s1 = o;
     t.off_s2 = o + mm;
@@ -166,6 +166,42 @@ __device__ inline void tail_linear_H(const float* phi, const float* u, float* ds
   }
 }
 
+// The three-kernel stack (MG_NET_CONV3) on one ring-padded level: K1 and K2 into the
+// scratch arrays (each pass writes the zero ring), then dst (=, or += with acc) K3 on the
+// interior; the per-point kernels come from the level's [27][n][n] field in global memory.
+// Barriers between the passes; the caller synchronises after the last one.
+__device__ inline void tail_stack_H(const float* W, const float* u, float* dst, bool acc, float* s1, float* s2, int n,
+                                   int m) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const size_t nn = (size_t)n * n;
+  const float* src = u;
+  for (int k = 0; k < 2; ++k) {
+    float* out = k ? s2 : s1;
+    for (int i = warp - 1; i <= n; i += nwarps)
+      for (int j = lane - 1; j <= n; j += 32) {
+        const int q = (i + 1) * m + j + 1;
+        float v = 0.f;
+        if (i >= 0 && i < n && j >= 0 && j < n) {
+          float w[9];
+#pragma unroll
+          for (int t = 0; t < 9; ++t) w[t] = __ldg(W + (size_t)(9 * k + t) * nn + (size_t)i * n + j);
+          v = conv9(w, src + q, m);
+        }
+        out[q] = v;
+      }
+    __syncthreads();
+    src = out;
+  }
+  TAIL_FOR(n) {
+    const int q = (i + 1) * m + j + 1;
+    float w[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) w[t] = __ldg(W + (size_t)(18 + t) * nn + (size_t)i * n + j);
+    const float h = conv9(w, src + q, m);
+    dst[q] = acc ? dst[q] + h : h;
+  }
+}
+
 // Down and up sweeps from level l0 with r_{l0} already in shared memory; leaves e_{l0}.
 // nu1 pre-smoothing steps from e = 0 (the first is e = H r, each further one e += H (r - A e))
 // and nu2 post-smoothing steps after the correction (Algorithm 1).  The coarsest level is
@@ -196,6 +232,8 @@ __device__ void tail_cycle(const ProbDev& P, float* sm, const TailLayout& lay, c
     const float* w = sm + lay.off_w[l];
     if (HK == HK_LINEAR) {
       tail_linear_H(w, t, e, true, sm + lay.off_s1, sm + lay.off_s2, n, m);
+    } else if (HK == HK_STACK3) {
+      tail_stack_H(Lv.W, t, e, true, sm + lay.off_s1, sm + lay.off_s2, n, m);
     } else {
       TAIL_FOR(n) {
         const int q = (i + 1) * m + j + 1;
@@ -213,6 +251,8 @@ __device__ void tail_cycle(const ProbDev& P, float* sm, const TailLayout& lay, c
     const float* w = sm + lay.off_w[l];
     if (HK == HK_LINEAR) {
       tail_linear_H(w, r, e, false, sm + lay.off_s1, sm + lay.off_s2, n, m);
+    } else if (HK == HK_STACK3) {
+      tail_stack_H(Lv.W, r, e, false, sm + lay.off_s1, sm + lay.off_s2, n, m);
     } else {
       TAIL_FOR(n) {
         const int q = (i + 1) * m + j + 1;

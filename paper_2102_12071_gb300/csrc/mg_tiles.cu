@@ -790,7 +790,9 @@ cudaError_t launch_update_residual(const CycleArgs& a, const CUtensorMap& e0, fl
 }
 
 cudaError_t launch_cycle(const CycleArgs& a, float rtol, int max_cycles, int parity) {
-  if (a.hk == HK_LINEAR || a.nu1 != 1 || a.nu2 != 1) return launch_cycle_linear(a, rtol, max_cycles, parity);
+  if (a.generic) return launch_cycle_linear(a, rtol, max_cycles, parity);
+  // the fused tile kernels exist for Jacobi and per-point 3x3 kernels only
+  if (a.hk != HK_JACOBI && a.hk != HK_TABLE && a.hk != HK_FIELD) return cudaErrorNotSupported;
   const int ls = a.lstar, np = nlaunch(a);
   const ProbDev* probs = a.probs;
   float* const nul = nullptr;

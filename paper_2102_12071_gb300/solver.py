@@ -30,7 +30,7 @@ def field(n: int, st: torch.Tensor) -> dict:
 
 
 def net_arch_code(net_arch: str) -> int:
-    codes = {"conv": B.MG_NET_CONV, "fc": B.MG_NET_FC, "linear": B.MG_NET_LINEAR}
+    codes = {"conv": B.MG_NET_CONV, "fc": B.MG_NET_FC, "linear": B.MG_NET_LINEAR, "conv3": B.MG_NET_CONV3}
     if net_arch not in codes:
         raise ValueError(f"unknown net_arch {net_arch!r}")
     return codes[net_arch]
@@ -46,7 +46,8 @@ class MultigridSolver:
         """net_params: one parameter set [nparams] for every level, or per-level sets
         [k, nparams] (level l uses set min(l, k - 1)).  transpose: smooth with H^T (per-point
         problems), so that a V-cycle applies the transpose of the cycle without it.
-        net_arch: "conv" (the convolutional network), "fc" (the fully connected one) or
+        net_arch: "conv" (the convolutional network), "conv3" (the same with three output
+        kernels applied as a stack, Sec. 4.2), "fc" (the fully connected one) or
         "linear" (the shared-kernel linear smoother of Sec. 6: net_params are its six 3x3
         kernels per level, [54] or [k, 54]; with per_problem, one group of k sets per
         problem, [nprob, k, 54], as Sec. 6 trains one smoother per problem).  nu1, nu2:

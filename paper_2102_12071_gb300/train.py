@@ -24,10 +24,11 @@ LAYERS = [(7, 9), (5, 7), (3, 5), (9, 3)]  # (out, in) channels of the 3x3 layer
 NPARAMS_FC = 6800
 FC_LAYERS = [(40, 81), (40, 40), (40, 40), (9, 40)]  # the fully connected network (out, in)
 NPARAMS_LIN = 54  # the shared-kernel linear smoother of one level: six 3x3 kernels
+NPARAMS_K3 = 1746  # the convolutional network with three output kernels (inference only)
 
 
 def nparams(arch: str = "conv") -> int:
-    return {"fc": NPARAMS_FC, "linear": NPARAMS_LIN}.get(arch, NPARAMS)
+    return {"fc": NPARAMS_FC, "linear": NPARAMS_LIN, "conv3": NPARAMS_K3}.get(arch, NPARAMS)
 
 
 def init_params_linear(d: float, omega: float = 2.0 / 3.0) -> torch.Tensor:
