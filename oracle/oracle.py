@@ -311,6 +311,53 @@ def cnn_loss_and_grad(st, params, z, omega: float = 2.0 / 3.0, bf16: bool = Fals
     return loss, hypernet_backward(st, params, dW, omega, bf16)
 
 
+# ------------------------------------------------ the shared-kernel network (Sec. 6.2)
+# Sec. 6.2 counts 378 parameters for the convolutional network with 7, 5 and 3 channels and
+# a 27 x 9 last layer: (7 + 5 + 3) * 9 + 27 * 9, one 3x3 kernel per output channel of each
+# convolution.  Reading: that kernel acts on every input channel of its layer, out_o =
+# k_o * (sum_c in_c).  This is the dense network with w[o][c] = k_o for every c, so the
+# forward is the dense one on the expanded parameters, and by the chain rule the gradient
+# of k_o is the sum over c of the dense gradient of w[o][c].
+SHARED_CONV = ((7, 9), (5, 7), (3, 5))  # (output, input) channels of the convolutions
+
+
+def shared_nparams() -> int:
+    return sum(co * 9 for co, _ in SHARED_CONV) + 9 * 27
+
+
+def shared_to_dense(params) -> np.ndarray:
+    """k1[7][9], k2[5][9], k3[3][9], wf[243] -> w1[7][9][9], w2[5][7][9], w3[3][5][9], wf."""
+    params = _f64(params)
+    assert params.size == shared_nparams()
+    out, o = [], 0
+    for co, ci in SHARED_CONV:
+        k = params[o:o + co * 9].reshape(co, 1, 9)
+        out.append(np.broadcast_to(k, (co, ci, 9)).reshape(-1))
+        o += co * 9
+    out.append(params[o:])
+    return np.concatenate(out)
+
+
+def shared_grad(dense_grad) -> np.ndarray:
+    """The gradient of the shared parameters from that of the expanded dense ones."""
+    g = _f64(dense_grad)
+    out, o = [], 0
+    for co, ci in SHARED_CONV:
+        out.append(g[o:o + co * ci * 9].reshape(co, ci, 9).sum(axis=1).reshape(-1))
+        o += co * ci * 9
+    out.append(g[o:])
+    return np.concatenate(out)
+
+
+def shared_forward(st, params, omega: float = 2.0 / 3.0, bf16: bool = False) -> np.ndarray:
+    return hypernet_forward(st, shared_to_dense(params), omega, bf16)
+
+
+def shared_loss_and_grad(st, params, z, omega: float = 2.0 / 3.0, bf16: bool = False, cycles: int = 1):
+    loss, g = cnn_loss_and_grad(st, shared_to_dense(params), z, omega, bf16, cycles)
+    return loss, shared_grad(g)
+
+
 # ------------------------------------------------ adaptive (level-by-level) training
 def transpose_kernels(W) -> np.ndarray:
     """Per-point kernels of H^T.  (H v)(x) = sum_k W_x[k] v(x + d_k), so
