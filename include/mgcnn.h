@@ -136,7 +136,7 @@ typedef enum {
                       the network has no input: its weights are the smoother.  Weighted
                       Jacobi is f1..f4 = identity (tap 4 = 1), f5 = 0, f6 = omega/D at tap 4.
                       Any stencil kind.                                                  */
-  MG_NET_CONV3 = 3  /* the convolutional network of MG_NET_CONV with 27 outputs per point:
+  MG_NET_CONV3 = 3, /* the convolutional network of MG_NET_CONV with 27 outputs per point:
                       three 3x3 kernels applied as a stack H v = K3(K2(K1 v)), each
                       layer's input zero outside the grid (Sec. 4, Sec. 4.2: k = 3),
                       K1 = (omega delta + out_1)/D, K2 = delta + out_2, K3 = delta + out_3;
@@ -144,6 +144,14 @@ typedef enum {
                       params.  Solve, V-cycle, smoother and FGMRES only (no training, no
                       smoother_transpose); levels above 63 run in the batched level
                       kernels.                                                           */
+  MG_NET_CONV_SHARED = 4 /* the network of MG_NET_CONV with one 3x3 kernel per output
+                      channel of each convolution, applied to every input channel of the
+                      layer (out_o = k_o * sum_c in_c): the 378-parameter count of
+                      Sec. 6.2, (7 + 5 + 3) * 9 + 27 * 9.  Layout: k1[7][3][3],
+                      k2[5][3][3], k3[3][3][3], wf[9][3][3][3].  It is MG_NET_CONV with
+                      w[o][c] = k_o for every c; the library expands each set on the
+                      device and sums the dense gradient over c.  Everything MG_NET_CONV
+                      supports.                                                          */
 } mg_net_arch;
 
 typedef struct mg_ctx mg_ctx;
@@ -259,7 +267,8 @@ mg_status mg_fgmres(mg_ctx* ctx, const float* b, float* x_hi, float* x_lo, int r
    w3[3][5][3][3], wf[9][3][3][3]; LeakyReLU slope 0.01 after each convolution. */
 int mg_net_nparams(void);
 
-/* Parameters of a network architecture (mg_net_arch); 0 for an unknown one. */
+/* Parameters of a network architecture (mg_net_arch); 0 for an unknown one.  The standalone
+   mg_net_forward below takes the MG_NET_CONV layout. */
 int mg_net_param_count(int arch);
 
 /* Network inference on nprob stencil fields (DEVICE float[nprob][9][n][n]): per point,

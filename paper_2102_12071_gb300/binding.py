@@ -261,7 +261,7 @@ def mg_train_get_coarse_field(ctx, prob: int, out, stream=None) -> None:
     check(lib().mg_train_get_coarse_field(ctx, int(prob), _ptr(out), _stream(stream)), "mg_train_get_coarse_field")
 
 
-MG_NET_CONV, MG_NET_FC, MG_NET_LINEAR, MG_NET_CONV3 = 0, 1, 2, 3
+MG_NET_CONV, MG_NET_FC, MG_NET_LINEAR, MG_NET_CONV3, MG_NET_CONV_SHARED = 0, 1, 2, 3, 4
 
 
 def mg_net_param_count(arch: int) -> int:

@@ -72,7 +72,7 @@ mg_status make_plan(const mg_problem* probs, int nprob, const mg_options* o, Pla
   if (!(o->omega > 0.f) || !(o->omega < 2.f)) return fail(MG_ERR_INVALID_ARG, "omega must be in (0, 2)");
   if (o->net_levels < 0 || o->net_levels > MG_MAXL) return fail(MG_ERR_INVALID_ARG, "net_levels out of range");
   if (o->net_arch != MG_NET_CONV && o->net_arch != MG_NET_FC && o->net_arch != MG_NET_LINEAR &&
-      o->net_arch != MG_NET_CONV3)
+      o->net_arch != MG_NET_CONV3 && o->net_arch != MG_NET_CONV_SHARED)
     return fail(MG_ERR_INVALID_ARG, "unknown net_arch");
   if (o->smoother == MG_SMOOTH_CNN && o->net_arch == MG_NET_CONV3 && (o->smoother_transpose || o->conv_bf16))
     return fail(MG_ERR_UNSUPPORTED, "the three-kernel network runs in FP32 and without smoother_transpose");
@@ -171,6 +171,7 @@ struct mg_ctx {
   int* d_active = nullptr;      // compacted list of problems still iterating
   float* tscratch = nullptr;    // kernel transposition scratch (smoother_transpose)
   float* lin = nullptr;         // the linear smoother's weights, [L-1][MG_NPARAMS_LIN]
+  float* net_dense = nullptr;   // MG_NET_CONV_SHARED: its sets in the dense layout
   LinMaps lin_maps;             // its tensor maps (levels above the tail)
   std::vector<int> h_active;
   LevelArrays arrays;
@@ -286,6 +287,9 @@ static size_t carve(const Plan& P, const mg_options& o, void* base, mg_ctx* ctx)
   // vectors of level-0 size for the chain and the up-sweep residual
   const int lin_lev = P.L > 1 ? P.L - 1 : 1, lin_groups = o.net_per_problem ? P.nprob : 1;
   float* lin = P.hk == HK_LINEAR ? c.take<float>((size_t)MG_NPARAMS_LIN * lin_lev * lin_groups) : nullptr;
+  // the shared-kernel network's parameter sets expanded to the dense layout
+  const bool shared_net = (P.hk == HK_TABLE || P.hk == HK_FIELD) && o.net_arch == MG_NET_CONV_SHARED;
+  float* net_dense = shared_net ? c.take<float>((size_t)MG_NPARAMS * (o.net_levels > 1 ? o.net_levels : 1)) : nullptr;
   float* lin_s[3] = {nullptr, nullptr, nullptr};
   if (P.generic)
     for (int k = 0; k < 3; ++k) lin_s[k] = c.take<float>((size_t)P.nprob * P.n0 * pitch_of(P.n0));
@@ -357,6 +361,7 @@ static size_t carve(const Plan& P, const mg_options& o, void* base, mg_ctx* ctx)
     ctx->d_active = active;
     ctx->tscratch = tscr;
     ctx->lin = lin;
+    ctx->net_dense = net_dense;
     ctx->args.lin_wa = lin_s[0];
     ctx->args.lin_wb = lin_s[1];
     ctx->args.lin_t = lin_s[2];
@@ -394,7 +399,7 @@ int mg_net_nparams(void) { return MG_NPARAMS; }
 
 int mg_net_param_count(int arch) {
   return arch == MG_NET_CONV ? MG_NPARAMS : arch == MG_NET_FC ? MG_NPARAMS_FC : arch == MG_NET_LINEAR ? MG_NPARAMS_LIN
-         : arch == MG_NET_CONV3 ? MG_NPARAMS_K3 : 0;
+         : arch == MG_NET_CONV3 ? MG_NPARAMS_K3 : arch == MG_NET_CONV_SHARED ? MG_NPARAMS_SHARED : 0;
 }
 
 mg_status mg_setup(const mg_problem* problems, int nprob, const mg_options* opts, const float* net_params,
@@ -544,6 +549,11 @@ mg_status mg_setup(const mg_problem* problems, int nprob, const mg_options* opts
       CK(cudaMemcpyAsync(ctx->d_jobs, jobs.data(), sizeof(NetJob) * jobs.size(), cudaMemcpyHostToDevice, s));
       const bool fc = opts->net_arch == MG_NET_FC;
       const size_t np_set = fc ? MG_NPARAMS_FC : MG_NPARAMS;
+      const float* prm_sets = net_params;
+      if (ctx->net_dense) {  // MG_NET_CONV_SHARED: expand every set, then the dense network
+        CK(launch_net_expand_shared(net_params, ctx->net_dense, opts->net_levels > 1 ? opts->net_levels : 1, s));
+        prm_sets = ctx->net_dense;
+      }
       auto net = [&](const NetJob* jobs_dev, int njobs, int nm, const float* prm) {
         return fc ? launch_fc_forward(jobs_dev, njobs, nm, prm, opts->omega, opts->conv_bf16, s)
                   : launch_net_forward(jobs_dev, njobs, nm, prm, opts->omega, opts->conv_bf16, s);
@@ -551,11 +561,11 @@ mg_status mg_setup(const mg_problem* problems, int nprob, const mg_options* opts
       if (opts->net_levels <= 1) {
         int nm = 0;
         for (int l = 0; l + 1 < P.L; ++l) nm = nmax[l] > nm ? nmax[l] : nm;
-        CK(net(ctx->d_jobs, (int)jobs.size(), nm, net_params));
+        CK(net(ctx->d_jobs, (int)jobs.size(), nm, prm_sets));
       } else {
         for (int l = 0; l + 1 < P.L; ++l) {
           const int set = l < opts->net_levels ? l : opts->net_levels - 1;
-          CK(net(ctx->d_jobs + first[l], nprob, nmax[l], net_params + (size_t)set * np_set));
+          CK(net(ctx->d_jobs + first[l], nprob, nmax[l], prm_sets + (size_t)set * np_set));
         }
       }
       if (opts->smoother_transpose)

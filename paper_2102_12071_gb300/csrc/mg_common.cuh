@@ -26,6 +26,7 @@
 #define MG_NPARAMS_FC 6800  // the fully connected network, 81 -> 40 -> 40 -> 40 -> 9
 #define MG_NPARAMS_LIN 54   // the shared-kernel linear smoother of one level: six 3x3 kernels
 #define MG_NPARAMS_K3 1746  // the convolutional network with three output kernels (27 outputs)
+#define MG_NPARAMS_SHARED 378  // one 3x3 kernel per convolution output channel, then wf
 
 enum { SK_CONST = 0, SK_FIELD = 1 };                 // stencil storage
 // smoother storage: omega/D; per-point kernels of a constant stencil by boundary class;

@@ -251,6 +251,10 @@ cudaError_t launch_net_forward_batch(const NetBatch& batch, int nfields, const f
 // the three-kernel network (MG_NET_CONV3): [27][n][n] per job, FP32
 cudaError_t launch_net_forward3(const NetJob* jobs_dev, int njobs, int nmax, const float* params, float omega,
                                 cudaStream_t s);
+// the shared-kernel network (MG_NET_CONV_SHARED): nsets parameter sets expanded to the dense
+// layout (w[o][c] = k_o), and one dense gradient summed back over the input channels
+cudaError_t launch_net_expand_shared(const float* shared, float* dense, int nsets, cudaStream_t s);
+cudaError_t launch_net_reduce_shared(const float* dense_grad, float* grad, cudaStream_t s);
 cudaError_t launch_copy_rel(const ProbState* state, float* rel, int nprob, cudaStream_t s);
 int net_backward_ctas(int n, int nfields);
 // the fully connected network (mg_netfc.cu); the backward needs fc_backward_floats scratch

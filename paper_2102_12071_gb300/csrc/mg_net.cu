@@ -282,6 +282,60 @@ cudaError_t launch_net_forward(const NetJob* jobs_dev, int njobs, int nmax, cons
   return cudaGetLastError();
 }
 
+// The shared-kernel network.  Dense index i of w_k[o][c][t] (k = 1..3) corresponds to the
+// shared k_k[o][t]; the last layer wf is common to both layouts.
+struct SharedMap {
+  int dense, shared, cin;  // start of the layer in each layout; input channels
+};
+__device__ __forceinline__ SharedMap shared_layer(int i) {
+  // dense layer starts: 0, 567, 882, 1017; shared: 0, 63, 108, 135
+  if (i < 567) return {0, 0, 9};
+  if (i < 882) return {567, 63, 7};
+  if (i < 1017) return {882, 108, 5};
+  return {1017, 135, 0};
+}
+
+__global__ void k_net_expand_shared(const float* __restrict__ shared, float* __restrict__ dense) {
+  const float* s = shared + (size_t)blockIdx.y * MG_NPARAMS_SHARED;
+  float* d = dense + (size_t)blockIdx.y * MG_NPARAMS;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < MG_NPARAMS; i += gridDim.x * blockDim.x) {
+    const SharedMap m = shared_layer(i);
+    const int j = i - m.dense;
+    // conv layers: j = (o * cin + c) * 9 + t  ->  o * 9 + t
+    d[i] = s[m.shared + (m.cin ? (j / (9 * m.cin)) * 9 + j % 9 : j)];
+  }
+}
+
+// grad[k_o[t]] = sum_c dense_grad[w[o][c][t]], c ascending (a fixed order: deterministic)
+__global__ void k_net_reduce_shared(const float* __restrict__ gd, float* __restrict__ g) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= MG_NPARAMS_SHARED) return;
+  int ds, ss, cin;
+  if (q < 63) ds = 0, ss = 0, cin = 9;
+  else if (q < 108) ds = 567, ss = 63, cin = 7;
+  else if (q < 135) ds = 882, ss = 108, cin = 5;
+  else ds = 1017, ss = 135, cin = 0;
+  const int j = q - ss;
+  if (!cin) {
+    g[q] = gd[ds + j];
+    return;
+  }
+  const int o = j / 9, t = j % 9;
+  float acc = 0.f;
+  for (int c = 0; c < cin; ++c) acc += gd[ds + (o * cin + c) * 9 + t];
+  g[q] = acc;
+}
+
+cudaError_t launch_net_expand_shared(const float* shared, float* dense, int nsets, cudaStream_t s) {
+  k_net_expand_shared<<<dim3((MG_NPARAMS + 255) / 256, nsets), 256, 0, s>>>(shared, dense);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_net_reduce_shared(const float* dense_grad, float* grad, cudaStream_t s) {
+  k_net_reduce_shared<<<(MG_NPARAMS_SHARED + 127) / 128, 128, 0, s>>>(dense_grad, grad);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_net_forward3(const NetJob* jobs_dev, int njobs, int nmax, const float* params, float omega,
                                 cudaStream_t s) {
   const int ntx = (nmax + OT - 1) / OT;

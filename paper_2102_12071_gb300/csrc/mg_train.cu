@@ -509,6 +509,8 @@ struct mg_train_ctx {
   float* lw[6] = {};               // the linear smoother: w1..w4 and two adjoint vectors
   float* lpart = nullptr;          // its per-CTA correlation partials
   float* lgrad = nullptr;          // its gradient accumulator [MG_NPARAMS_LIN]
+  float* sh_params = nullptr;      // MG_NET_CONV_SHARED: the set in the dense layout
+  float* sh_grad = nullptr;        // and the dense gradient
   std::vector<float*> X;           // X[c]: input of cycle c >= 1
   std::vector<float*> V0, V2;      // A e_c and A (C S e_c) of cycle c (V0[0] = v0, V2[0] = v2)
   std::vector<float> h_s9;
@@ -523,8 +525,11 @@ mg_status train_dims(const mg_problem* probs, int nprob, int nvec, const mg_opti
   if (!probs || nprob < 1 || nvec < 1 || !o) return (mg_status)api_fail(MG_ERR_INVALID_ARG, "training: bad arguments");
   if (o->train_cycles < 0 || o->train_cycles > kMaxTrainCycles)
     return (mg_status)api_fail(MG_ERR_INVALID_ARG, "train_cycles must be in [0, %d]", kMaxTrainCycles);
-  if (o->net_arch != MG_NET_CONV && o->net_arch != MG_NET_FC && o->net_arch != MG_NET_LINEAR)
-    return (mg_status)api_fail(MG_ERR_INVALID_ARG, "unknown net_arch");
+  if (o->net_arch != MG_NET_CONV && o->net_arch != MG_NET_FC && o->net_arch != MG_NET_LINEAR &&
+      o->net_arch != MG_NET_CONV_SHARED)
+    return (mg_status)api_fail(o->net_arch == MG_NET_CONV3 ? MG_ERR_UNSUPPORTED : MG_ERR_INVALID_ARG,
+                               o->net_arch == MG_NET_CONV3 ? "the three-kernel network is not trained here"
+                                                           : "unknown net_arch");
   if ((long long)nprob * nvec > 65535) return (mg_status)api_fail(MG_ERR_INVALID_ARG, "nprob * nvec must be <= 65535");
   if (!(o->omega > 0.f) || !(o->omega < 2.f)) return (mg_status)api_fail(MG_ERR_INVALID_ARG, "omega must be in (0, 2)");
   const int n = probs[0].n;
@@ -604,6 +609,10 @@ size_t train_carve(const TrainDims& D, int kmax, int ckpt, int arch, void* basev
     for (int k = 0; k < 6; ++k) x.lw[k] = take<float>(base, off, D.nn * BZ);
     x.lpart = take<float>(base, off, ((D.nn + TT - 1) / TT) * BZ * 9);
     x.lgrad = take<float>(base, off, MG_NPARAMS_LIN);
+  }
+  if (arch == MG_NET_CONV_SHARED) {
+    x.sh_params = take<float>(base, off, MG_NPARAMS);
+    x.sh_grad = take<float>(base, off, MG_NPARAMS);
   }
   x.fail = take<int>(base, off, 4);
   return off + 256;
@@ -724,8 +733,13 @@ static mg_status train_step(mg_train_ctx* c, const float* params, const float* z
   nb.n = D.n;
   nb.pad_ = 0;
   const bool lin = c->arch == MG_NET_LINEAR;  // params are the smoother's 54 weights
+  const float* net_prm = params;              // the convolutional network in the dense layout
+  if (c->arch == MG_NET_CONV_SHARED) {
+    TCK(launch_net_expand_shared(params, c->sh_params, 1, s));
+    net_prm = c->sh_params;
+  }
   if (c->arch == MG_NET_FC) TCK(launch_fc_forward_batch(nb, D.B, params, c->omega, c->bf16, s));
-  else if (!lin) TCK(launch_net_forward_batch(nb, D.B, params, c->omega, c->bf16, s));
+  else if (!lin) TCK(launch_net_forward_batch(nb, D.B, net_prm, c->omega, c->bf16, s));
   const int K = c->k;
   // out = x - H v
   auto xmHv = [&](const float* x, const float* v, float* out) {
@@ -822,7 +836,10 @@ static mg_status train_step(mg_train_ctx* c, const float* params, const float* z
     return MG_OK;
   }
   if (c->arch == MG_NET_FC) TCK(launch_fc_backward(nb, D.B, c->dW, params, c->bf16, c->fc_scratch, 1.f, grad_out, s));
-  else TCK(launch_net_backward(nb, D.B, c->dW, params, c->bf16, c->param_partial, 1.f, grad_out, s));
+  else if (c->arch == MG_NET_CONV_SHARED) {
+    TCK(launch_net_backward(nb, D.B, c->dW, net_prm, c->bf16, c->param_partial, 1.f, c->sh_grad, s));
+    TCK(launch_net_reduce_shared(c->sh_grad, grad_out, s));
+  } else TCK(launch_net_backward(nb, D.B, c->dW, params, c->bf16, c->param_partial, 1.f, grad_out, s));
   return MG_OK;
 }
 

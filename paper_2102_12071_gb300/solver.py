@@ -30,7 +30,8 @@ def field(n: int, st: torch.Tensor) -> dict:
 
 
 def net_arch_code(net_arch: str) -> int:
-    codes = {"conv": B.MG_NET_CONV, "fc": B.MG_NET_FC, "linear": B.MG_NET_LINEAR, "conv3": B.MG_NET_CONV3}
+    codes = {"conv": B.MG_NET_CONV, "fc": B.MG_NET_FC, "linear": B.MG_NET_LINEAR, "conv3": B.MG_NET_CONV3,
+             "conv_shared": B.MG_NET_CONV_SHARED}
     if net_arch not in codes:
         raise ValueError(f"unknown net_arch {net_arch!r}")
     return codes[net_arch]

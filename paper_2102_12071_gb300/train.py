@@ -25,10 +25,38 @@ NPARAMS_FC = 6800
 FC_LAYERS = [(40, 81), (40, 40), (40, 40), (9, 40)]  # the fully connected network (out, in)
 NPARAMS_LIN = 54  # the shared-kernel linear smoother of one level: six 3x3 kernels
 NPARAMS_K3 = 1746  # the convolutional network with three output kernels (inference only)
+NPARAMS_SHARED = 378  # one 3x3 kernel per convolution output channel (Sec. 6.2's count)
 
 
 def nparams(arch: str = "conv") -> int:
-    return {"fc": NPARAMS_FC, "linear": NPARAMS_LIN, "conv3": NPARAMS_K3}.get(arch, NPARAMS)
+    return {"fc": NPARAMS_FC, "linear": NPARAMS_LIN, "conv3": NPARAMS_K3,
+            "conv_shared": NPARAMS_SHARED}.get(arch, NPARAMS)
+
+
+def init_params_shared(seed: int = 0) -> torch.Tensor:
+    """The shared-kernel network: output channel o of a convolution is k_o applied to the sum
+    of the layer's ci input channels, so its fan-in is 9 ci as for the dense layer (same
+    Kaiming bound); the output layer is zero (the network starts at weighted Jacobi)."""
+    g = torch.Generator().manual_seed(seed)
+    parts = []
+    for k, (co, ci) in enumerate(LAYERS):
+        if k == len(LAYERS) - 1:
+            parts.append(torch.zeros(co * ci * 9))
+        else:
+            bound = math.sqrt(6.0 / ((1 + 0.01 ** 2) * ci * 9))
+            parts.append((torch.rand(co * 9, generator=g) * 2 - 1) * bound)
+    p = torch.cat(parts)
+    assert p.numel() == NPARAMS_SHARED
+    return p
+
+
+def init_for(arch: str, seed: int = 0) -> torch.Tensor:
+    """Starting parameters of a trainable architecture (all start at weighted Jacobi)."""
+    if arch == "fc":
+        return init_params_fc(seed)
+    if arch == "conv_shared":
+        return init_params_shared(seed)
+    return init_params(seed)
 
 
 def init_params_linear(d: float, omega: float = 2.0 / 3.0) -> torch.Tensor:
@@ -173,7 +201,8 @@ class Trainer:
                  conv_bf16: bool = True, lr: float = 1e-3, seed: int = 0, eps_range=(1e-3, 1.0),
                  families=("rotated",), max_cycles: int = 1, checkpoint: bool = False, net_arch: str = "conv"):
         """max_cycles = b of Algorithm 2: each step's loss spans k ~ U{1..b} two-grid cycles.
-        net_arch: "conv" or "fc" (the fully connected network of Sec. 4.2)."""
+        net_arch: "conv", "conv_shared" (one kernel per convolution output channel, Sec. 6.2's
+        378 parameters) or "fc" (the fully connected network of Sec. 4.2)."""
         self.max_cycles = max_cycles
         self.checkpoint = checkpoint
         self.net_arch = net_arch
@@ -184,7 +213,7 @@ class Trainer:
         self.conv_bf16 = conv_bf16
         self.eps_range = eps_range
         self.families = families
-        self.params = (init_params_fc(seed) if net_arch == "fc" else init_params(seed)).cuda().requires_grad_(True)
+        self.params = init_for(net_arch, seed).cuda().requires_grad_(True)
         self.opt = torch.optim.Adam([self.params], lr=lr)
         self.gen = torch.Generator(device="cuda").manual_seed(inputs.SEED_TRAIN + seed)
         self._ws = {}
@@ -286,7 +315,7 @@ class AdaptiveTrainer:
         if self.net_arch == "linear":
             s = B.mg_rotated_stencil(*self.problem)
             return init_params_linear(float(s[4]), self.omega)
-        return init_params_fc(self.seed) if self.net_arch == "fc" else init_params(self.seed)
+        return init_for(self.net_arch, self.seed)
 
     def train_level(self, n: int) -> torch.Tensor:
         p = self._init().cuda().requires_grad_(True)
