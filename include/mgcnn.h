@@ -141,9 +141,10 @@ typedef enum {
                       layer's input zero outside the grid (Sec. 4, Sec. 4.2: k = 3),
                       K1 = (omega delta + out_1)/D, K2 = delta + out_2, K3 = delta + out_3;
                       last layer wf[27][3][3][3] (row 9k + t: tap t of kernel k+1), 1 746
-                      params.  Solve, V-cycle, smoother and FGMRES only (no training, no
-                      smoother_transpose); levels above 63 run in the batched level
-                      kernels.                                                           */
+                      params.  FP32 only, without smoother_transpose (so no
+                      mg_train_step_coarse); solve, V-cycle, FGMRES and mg_train_step;
+                      mg_smoother_apply and mg_get_kernels refuse it.  Levels above 63
+                      run in the batched level kernels.                                  */
   MG_NET_CONV_SHARED = 4 /* the network of MG_NET_CONV with one 3x3 kernel per output
                       channel of each convolution, applied to every input channel of the
                       layer (out_o = k_o * sum_c in_c): the 378-parameter count of

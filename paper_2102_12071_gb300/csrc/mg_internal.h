@@ -251,6 +251,12 @@ cudaError_t launch_net_forward_batch(const NetBatch& batch, int nfields, const f
 // the three-kernel network (MG_NET_CONV3): [27][n][n] per job, FP32
 cudaError_t launch_net_forward3(const NetJob* jobs_dev, int njobs, int nmax, const float* params, float omega,
                                 cudaStream_t s);
+// the same on a uniform batch (kernels [27][n][n] of field y at batch.W + 3 y batch.stride)
+// and its backward (dW laid out like W; partials: net_backward_ctas x MG_NPARAMS_K3)
+cudaError_t launch_net_forward3_batch(const NetBatch& batch, int nfields, const float* params, float omega,
+                                      cudaStream_t s);
+cudaError_t launch_net_backward3(const NetBatch& batch, int nfields, const float* dW, const float* params,
+                                 float* partials, float scale, float* grad, cudaStream_t s);
 // the shared-kernel network (MG_NET_CONV_SHARED): nsets parameter sets expanded to the dense
 // layout (w[o][c] = k_o), and one dense gradient summed back over the input channels
 cudaError_t launch_net_expand_shared(const float* shared, float* dense, int nsets, cudaStream_t s);

@@ -60,7 +60,8 @@ __device__ __forceinline__ void conv_layer(const float* __restrict__ w, const fl
   }
 }
 
-// jobs == nullptr: job y is field y of a uniform batch (batch.st/W + y * batch.stride).
+// jobs == nullptr: job y is field y of a uniform batch (batch.st + y * batch.stride, its
+// NK kernels at batch.W + y * NK * batch.stride).
 // NK output kernels per point: NK = 1 gives W = (omega delta + out) / D; NK = 3 the stack
 // K1 = (omega delta + out_1) / D, K2 = delta + out_2, K3 = delta + out_3 ([27][n][n] out).
 template <int NK>
@@ -78,7 +79,7 @@ __global__ void __launch_bounds__(NET_THREADS) k_net_forward(const NetJob* __res
   } else {
     J.st = batch.st + blockIdx.y * batch.stride;
     J.s = nullptr;
-    J.W = batch.W + blockIdx.y * batch.stride;
+    J.W = batch.W + (size_t)blockIdx.y * batch.stride * NK;
     J.n = batch.n;
   }
   const int n = J.n;
@@ -135,9 +136,13 @@ __global__ void __launch_bounds__(NET_THREADS) k_net_forward(const NetJob* __res
 // batch of fields.  Each CTA recomputes the forward pass of its 16 x 16 output tile (with
 // halo) and back-propagates the paths that end in its own outputs; summed over tiles this
 // is the full gradient.  Rounding to bfloat16 is passed straight through.  Per-CTA
-// parameter gradients go to partials[cta][MG_NPARAMS] (deterministic reduction after).
-constexpr int BW_SMEM_FLOATS = 2 * MG_NPARAMS + 9 * S0 * S0 + 7 * S1 * S1 + 5 * S2 * S2 + 3 * S3 * S3 +
-                               9 * OT * OT + 3 * S3 * S3 + 5 * S2 * S2 + 7 * S1 * S1;
+// parameter gradients go to partials[cta][NP] (deterministic reduction after).  NK = 3:
+// the three-kernel network, dW [27][n][n] per field at dWall + y * 3 * batch.stride.
+template <int NK>
+constexpr int bw_smem_floats() {
+  return 2 * (NK == 1 ? MG_NPARAMS : MG_NPARAMS_K3) + 9 * S0 * S0 + 7 * S1 * S1 + 5 * S2 * S2 + 3 * S3 * S3 +
+         9 * NK * OT * OT + 3 * S3 * S3 + 5 * S2 * S2 + 7 * S1 * S1;
+}
 
 // weight gradient of a conv layer: gw[o][c][ky][kx] = sum_{y,x in so x so} dz[o][y][x] in[c][y+ky][x+kx]
 template <int CIN, int COUT>
@@ -180,35 +185,37 @@ __device__ __forceinline__ void conv_igrad(const float* w, const float* dz, int 
   }
 }
 
+template <int NK>
 __global__ void __launch_bounds__(NET_THREADS) k_net_backward(NetBatch batch, const float* __restrict__ dWall,
                                                               const float* __restrict__ params, int bf16,
                                                               float* __restrict__ partials) {
+  constexpr int NP = NK == 1 ? MG_NPARAMS : MG_NPARAMS_K3;
   extern __shared__ float sm[];
   float* w = sm;
-  float* gw = w + MG_NPARAMS;
-  float* a0 = gw + MG_NPARAMS;
+  float* gw = w + NP;
+  float* a0 = gw + NP;
   float* a1 = a0 + 9 * S0 * S0;
   float* a2 = a1 + 7 * S1 * S1;
   float* a3 = a2 + 5 * S2 * S2;
   float* dout = a3 + 3 * S3 * S3;
-  float* dz3 = dout + 9 * OT * OT;
+  float* dz3 = dout + 9 * NK * OT * OT;
   float* dz2 = dz3 + 3 * S3 * S3;
   float* dz1 = dz2 + 5 * S2 * S2;
   NetJob J;
   J.st = batch.st + blockIdx.y * batch.stride;
   J.s = nullptr;
   J.n = batch.n;
-  const float* dW = dWall + blockIdx.y * batch.stride;
+  const float* dW = dWall + (size_t)blockIdx.y * batch.stride * NK;
   const int n = J.n;
   const int ntx = (n + OT - 1) / OT;
   const int cta = blockIdx.y * gridDim.x + blockIdx.x;
-  float* out = partials + (size_t)cta * MG_NPARAMS;
+  float* out = partials + (size_t)cta * NP;
   if ((int)blockIdx.x >= ntx * ntx) {
-    for (int t = threadIdx.x; t < MG_NPARAMS; t += NET_THREADS) out[t] = 0.f;
+    for (int t = threadIdx.x; t < NP; t += NET_THREADS) out[t] = 0.f;
     return;
   }
   const int oy = (blockIdx.x / ntx) * OT, ox = (blockIdx.x % ntx) * OT;
-  for (int t = threadIdx.x; t < MG_NPARAMS; t += NET_THREADS) w[t] = rnd_bf16(params[t], bf16);
+  for (int t = threadIdx.x; t < NP; t += NET_THREADS) w[t] = rnd_bf16(params[t], bf16);
   for (int t = threadIdx.x; t < S0 * S0; t += NET_THREADS) {
     const int i = oy - 4 + t / S0, j = ox - 4 + t % S0;
     if (in_grid(i, j, n)) {
@@ -220,12 +227,17 @@ __global__ void __launch_bounds__(NET_THREADS) k_net_backward(NetBatch batch, co
       for (int c = 0; c < 9; ++c) a0[c * S0 * S0 + t] = 0.f;
     }
   }
-  // dL/d(out) = dW / diag on the tile's outputs
+  // dL/d(out) = dW / diag on the tile's outputs (the first kernel; K2, K3 = delta + out)
   const size_t nn = (size_t)n * n;
-  for (int t = threadIdx.x; t < 9 * OT * OT; t += NET_THREADS) {
+  for (int t = threadIdx.x; t < 9 * NK * OT * OT; t += NET_THREADS) {
     const int o = t / (OT * OT), pos = t % (OT * OT);
     const int i = oy + pos / OT, j = ox + pos % OT;
-    dout[t] = in_grid(i, j, n) ? dW[o * nn + (size_t)i * n + j] / job_tap(J, 4, i, j) : 0.f;
+    float d = 0.f;
+    if (in_grid(i, j, n)) {
+      d = dW[o * nn + (size_t)i * n + j];
+      if (o < 9) d /= job_tap(J, 4, i, j);
+    }
+    dout[t] = d;
   }
   __syncthreads();
   conv_layer<9, 7>(w + OFF_W1, a0, S0, a1, S1, oy - 3, ox - 3, n, bf16);
@@ -234,8 +246,8 @@ __global__ void __launch_bounds__(NET_THREADS) k_net_backward(NetBatch batch, co
   __syncthreads();
   conv_layer<5, 3>(w + OFF_W3, a2, S2, a3, S3, oy - 1, ox - 1, n, bf16);
   __syncthreads();
-  conv_wgrad<3, 9>(dout, OT, a3, S3, gw + OFF_WF);
-  conv_igrad<3, 9>(w + OFF_WF, dout, OT, a3, S3, dz3, oy - 1, ox - 1, n);
+  conv_wgrad<3, 9 * NK>(dout, OT, a3, S3, gw + OFF_WF);
+  conv_igrad<3, 9 * NK>(w + OFF_WF, dout, OT, a3, S3, dz3, oy - 1, ox - 1, n);
   __syncthreads();
   conv_wgrad<5, 3>(dz3, S3, a2, S2, gw + OFF_W3);
   conv_igrad<5, 3>(w + OFF_W3, dz3, S3, a2, S2, dz2, oy - 2, ox - 2, n);
@@ -245,14 +257,15 @@ __global__ void __launch_bounds__(NET_THREADS) k_net_backward(NetBatch batch, co
   __syncthreads();
   conv_wgrad<9, 7>(dz1, S1, a0, S0, gw + OFF_W1);
   __syncthreads();
-  for (int t = threadIdx.x; t < MG_NPARAMS; t += NET_THREADS) out[t] = gw[t];
+  for (int t = threadIdx.x; t < NP; t += NET_THREADS) out[t] = gw[t];
 }
 
+template <int NP>
 __global__ void k_reduce_params(const float* __restrict__ partials, int ncta, float scale, float* __restrict__ g) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= MG_NPARAMS) return;
+  if (t >= NP) return;
   float hi = 0.f, lo = 0.f;
-  for (int c = 0; c < ncta; ++c) ff_add(hi, lo, partials[(size_t)c * MG_NPARAMS + t], 0.f);
+  for (int c = 0; c < ncta; ++c) ff_add(hi, lo, partials[(size_t)c * NP + t], 0.f);
   g[t] = scale * (hi + lo);
 }
 
@@ -265,11 +278,32 @@ cudaError_t launch_net_backward(const NetBatch& batch, int nfields, const float*
                                 float* partials, float scale, float* grad, cudaStream_t s) {
   const int ntx = (batch.n + OT - 1) / OT;
   dim3 grid(ntx * ntx, nfields);
-  const size_t smem = (size_t)BW_SMEM_FLOATS * sizeof(float);
-  cudaError_t e = cudaFuncSetAttribute(k_net_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = (size_t)bw_smem_floats<1>() * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(k_net_backward<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_net_backward<<<grid, NET_THREADS, smem, s>>>(batch, dW, params, bf16, partials);
-  k_reduce_params<<<(MG_NPARAMS + 127) / 128, 128, 0, s>>>(partials, ntx * ntx * nfields, scale, grad);
+  k_net_backward<1><<<grid, NET_THREADS, smem, s>>>(batch, dW, params, bf16, partials);
+  k_reduce_params<MG_NPARAMS><<<(MG_NPARAMS + 127) / 128, 128, 0, s>>>(partials, ntx * ntx * nfields, scale, grad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_net_backward3(const NetBatch& batch, int nfields, const float* dW, const float* params,
+                                 float* partials, float scale, float* grad, cudaStream_t s) {
+  const int ntx = (batch.n + OT - 1) / OT;
+  dim3 grid(ntx * ntx, nfields);
+  const size_t smem = (size_t)bw_smem_floats<3>() * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(k_net_backward<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_net_backward<3><<<grid, NET_THREADS, smem, s>>>(batch, dW, params, 0, partials);
+  k_reduce_params<MG_NPARAMS_K3><<<(MG_NPARAMS_K3 + 127) / 128, 128, 0, s>>>(partials, ntx * ntx * nfields, scale,
+                                                                              grad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_net_forward3_batch(const NetBatch& batch, int nfields, const float* params, float omega,
+                                      cudaStream_t s) {
+  const int ntx = (batch.n + OT - 1) / OT;
+  dim3 grid(ntx * ntx, nfields);
+  k_net_forward<3><<<grid, NET_THREADS, 0, s>>>(nullptr, batch, params, omega, 0);
   return cudaGetLastError();
 }
 

@@ -217,6 +217,59 @@ __global__ void k_t_dW(TrainDims D, const float* __restrict__ g3, const float* _
   for (int k = 0; k < 9; ++k) out[k * D.nn + q] = accumulate ? out[k * D.nn + q] - acc[k] : -acc[k];
 }
 
+// ------------------------------------------------- the three-kernel stack (MG_NET_CONV3)
+// H = K3 K2 K1, kernel k (0..2) of problem b at Wall + (27 b + 9 k) nn, tap t at + t nn.
+__device__ __forceinline__ const float* t3_kernel(const TrainDims& D, const float* Wall, int b, int k) {
+  return Wall + ((size_t)b * 27 + 9 * k) * D.nn;
+}
+
+// out = K_k in, or out = x - K_k in when x is given
+__global__ void k_t3_conv(TrainDims D, const float* __restrict__ Wall, int k, const float* __restrict__ x,
+                          const float* __restrict__ in, float* __restrict__ out) {
+  T_PROLOGUE_V
+  const float* W = t3_kernel(D, Wall, vec / D.Z, k);
+  const float* v = in + off;
+  float acc = 0.f;
+#pragma unroll
+  for (int t = 0; t < 9; ++t) {
+    const int ii = i + t / 3 - 1, jj = j + t % 3 - 1;
+    if (in_grid(ii, jj, D.n)) acc = fmaf(W[t * D.nn + q], v[ii * D.n + jj], acc);
+  }
+  out[off + q] = x ? x[off + q] - acc : acc;
+}
+
+// out = K_k^T in
+__global__ void k_t3_convT(TrainDims D, const float* __restrict__ Wall, int k, const float* __restrict__ in,
+                           float* __restrict__ out) {
+  T_PROLOGUE_V
+  out[off + q] = appHT(t3_kernel(D, Wall, vec / D.Z, k), in + off, D.n, i, j);
+}
+
+// dW[9k + t](p) -= sum_j g_j(p) u_j(p + d_t): the gradient of a term x - K_k u with output
+// gradient g (one thread per (b, p); dW is cleared before the adjoint)
+__global__ void k_t3_dW(TrainDims D, const float* __restrict__ g, const float* __restrict__ u,
+                        float* __restrict__ dW, int k) {
+  const int b = blockIdx.y;
+  const int q = blockIdx.x * TT + threadIdx.x;
+  if (q >= (int)D.nn) return;
+  const int i = q / D.n, j = q % D.n;
+  float acc[9];
+#pragma unroll
+  for (int t = 0; t < 9; ++t) acc[t] = 0.f;
+  for (int z = 0; z < D.Z; ++z) {
+    const size_t off = ((size_t)b * D.Z + z) * D.nn;
+    const float gv = g[off + q];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+      const int ii = i + t / 3 - 1, jj = j + t % 3 - 1;
+      if (in_grid(ii, jj, D.n)) acc[t] = fmaf(gv, u[off + ii * D.n + jj], acc[t]);
+    }
+  }
+  float* out = dW + ((size_t)b * 27 + 9 * k) * D.nn;
+#pragma unroll
+  for (int t = 0; t < 9; ++t) out[t * D.nn + q] -= acc[t];
+}
+
 // ---------------------------------------------------------------- coarse solve
 // Banded Cholesky of the Galerkin coarse operator, right-looking, one CTA per problem.
 // band[(r)*(w+1) + d] holds L(r, r-d), d = 0..w.  A(r, r-d) comes from the coarse field.
@@ -506,7 +559,8 @@ struct mg_train_ctx {
   int kmax = 1, k = 1, ckpt = 0;   // cycles reserved / used by the loss; checkpointing
   int arch = MG_NET_CONV;          // network architecture (mg_net_arch)
   float* fc_scratch = nullptr;     // the fully connected network's backward tape
-  float* lw[6] = {};               // the linear smoother: w1..w4 and two adjoint vectors
+  float* lw[6] = {};               // the linear smoother: w1..w4 and two adjoint vectors;
+                                   // the three-kernel stack: lw[0..3]
   float* lpart = nullptr;          // its per-CTA correlation partials
   float* lgrad = nullptr;          // its gradient accumulator [MG_NPARAMS_LIN]
   float* sh_params = nullptr;      // MG_NET_CONV_SHARED: the set in the dense layout
@@ -526,10 +580,10 @@ mg_status train_dims(const mg_problem* probs, int nprob, int nvec, const mg_opti
   if (o->train_cycles < 0 || o->train_cycles > kMaxTrainCycles)
     return (mg_status)api_fail(MG_ERR_INVALID_ARG, "train_cycles must be in [0, %d]", kMaxTrainCycles);
   if (o->net_arch != MG_NET_CONV && o->net_arch != MG_NET_FC && o->net_arch != MG_NET_LINEAR &&
-      o->net_arch != MG_NET_CONV_SHARED)
-    return (mg_status)api_fail(o->net_arch == MG_NET_CONV3 ? MG_ERR_UNSUPPORTED : MG_ERR_INVALID_ARG,
-                               o->net_arch == MG_NET_CONV3 ? "the three-kernel network is not trained here"
-                                                           : "unknown net_arch");
+      o->net_arch != MG_NET_CONV_SHARED && o->net_arch != MG_NET_CONV3)
+    return (mg_status)api_fail(MG_ERR_INVALID_ARG, "unknown net_arch");
+  if (o->net_arch == MG_NET_CONV3 && o->conv_bf16)
+    return (mg_status)api_fail(MG_ERR_UNSUPPORTED, "the three-kernel network trains in FP32 (conv_bf16 = 0)");
   if ((long long)nprob * nvec > 65535) return (mg_status)api_fail(MG_ERR_INVALID_ARG, "nprob * nvec must be <= 65535");
   if (!(o->omega > 0.f) || !(o->omega < 2.f)) return (mg_status)api_fail(MG_ERR_INVALID_ARG, "omega must be in (0, 2)");
   const int n = probs[0].n;
@@ -581,8 +635,9 @@ size_t train_carve(const TrainDims& D, int kmax, int ckpt, int arch, void* basev
   x.s9 = take<float>(base, off, 9 * (size_t)D.B);
   x.fields = take<float>(base, off, 9 * D.nn * D.B);
   x.cfields = take<float>(base, off, 9 * D.nnc * D.B);
-  x.W = take<float>(base, off, 9 * D.nn * D.B);
-  x.dW = take<float>(base, off, 9 * D.nn * D.B);
+  const size_t nk = arch == MG_NET_CONV3 ? 3 : 1;  // kernels per point
+  x.W = take<float>(base, off, 9 * nk * D.nn * D.B);
+  x.dW = take<float>(base, off, 9 * nk * D.nn * D.B);
   x.probs = take<ProbDev>(base, off, D.B);
   x.band = take<double>(base, off, m * ld * D.B);
   x.ut = take<double>(base, off, m * ld * D.B);
@@ -603,7 +658,9 @@ size_t train_carve(const TrainDims& D, int kmax, int ckpt, int arch, void* basev
   x.xc = take<float>(base, off, D.nnc * BZ);
   x.loss_partial = take<float>(base, off, BZ);
   x.ncta_bw = net_backward_ctas(D.n, D.B);
-  x.param_partial = take<float>(base, off, (size_t)x.ncta_bw * MG_NPARAMS);
+  x.param_partial = take<float>(base, off, (size_t)x.ncta_bw * (arch == MG_NET_CONV3 ? MG_NPARAMS_K3 : MG_NPARAMS));
+  if (arch == MG_NET_CONV3)  // K1 v, K2 K1 v and two adjoint vectors of the stack
+    for (int k = 0; k < 4; ++k) x.lw[k] = take<float>(base, off, D.nn * BZ);
   x.fc_scratch = arch == MG_NET_FC ? take<float>(base, off, fc_backward_floats(D.n, D.B)) : nullptr;
   if (arch == MG_NET_LINEAR) {
     for (int k = 0; k < 6; ++k) x.lw[k] = take<float>(base, off, D.nn * BZ);
@@ -738,11 +795,19 @@ static mg_status train_step(mg_train_ctx* c, const float* params, const float* z
     TCK(launch_net_expand_shared(params, c->sh_params, 1, s));
     net_prm = c->sh_params;
   }
+  const bool k3 = c->arch == MG_NET_CONV3;  // H = K3 K2 K1, c->W holds [27][n][n] per problem
   if (c->arch == MG_NET_FC) TCK(launch_fc_forward_batch(nb, D.B, params, c->omega, c->bf16, s));
+  else if (k3) TCK(launch_net_forward3_batch(nb, D.B, params, c->omega, s));
   else if (!lin) TCK(launch_net_forward_batch(nb, D.B, net_prm, c->omega, c->bf16, s));
   const int K = c->k;
   // out = x - H v
   auto xmHv = [&](const float* x, const float* v, float* out) {
+    if (k3) {
+      k_t3_conv<<<gv, TT, 0, s>>>(D, c->W, 0, nullptr, v, c->lw[0]);
+      k_t3_conv<<<gv, TT, 0, s>>>(D, c->W, 1, nullptr, c->lw[0], c->lw[1]);
+      k_t3_conv<<<gv, TT, 0, s>>>(D, c->W, 2, x, c->lw[1], out);
+      return;
+    }
     if (!lin) {
       k_t_xmHv<<<gv, TT, 0, s>>>(D, c->fields, c->W, x, v, out);
       return;
@@ -774,6 +839,20 @@ static mg_status train_step(mg_train_ctx* c, const float* params, const float* z
       corr(lam, k >= 2 ? w[k - 2] : v, k - 1);  // f_k reads w_{k-1} (w_0 = v)
     }
     k_tl_HT<<<gv, TT, 0, s>>>(D, params, lam, g, t);
+  };
+  // the stack's part of the adjoint of e_out = x - K3 K2 K1 v with output gradient g:
+  // dW -= g (x) K2 K1 v, (K3^T g) (x) K1 v, (K2^T K3^T g) (x) v; and t = H^T g
+  const dim3 gp3(nblk, D.B);
+  auto stack_adjoint = [&](const float* v, const float* g, float* t) {
+    float* const* w = c->lw;
+    k_t3_conv<<<gv, TT, 0, s>>>(D, c->W, 0, nullptr, v, w[0]);
+    k_t3_conv<<<gv, TT, 0, s>>>(D, c->W, 1, nullptr, w[0], w[1]);
+    k_t3_dW<<<gp3, TT, 0, s>>>(D, g, w[1], c->dW, 2);
+    k_t3_convT<<<gv, TT, 0, s>>>(D, c->W, 2, g, w[2]);
+    k_t3_dW<<<gp3, TT, 0, s>>>(D, w[2], w[0], c->dW, 1);
+    k_t3_convT<<<gv, TT, 0, s>>>(D, c->W, 1, w[2], w[3]);
+    k_t3_dW<<<gp3, TT, 0, s>>>(D, w[3], v, c->dW, 0);
+    k_t3_convT<<<gv, TT, 0, s>>>(D, c->W, 0, w[3], t);
   };
   // xc = M rc: the exact coarse solve (banded Cholesky), or one V-cycle of the coarse
   // context (cf), whose transpose ct serves the adjoint
@@ -808,17 +887,20 @@ static mg_status train_step(mg_train_ctx* c, const float* params, const float* z
   if (!grad_out) return MG_OK;
   // adjoint, cycles in reverse; g3 = dloss/d(output of cycle cc)
   if (lin) TCK(cudaMemsetAsync(c->lgrad, 0, MG_NPARAMS_LIN * sizeof(float), s));
+  if (k3) TCK(cudaMemsetAsync(c->dW, 0, 27 * D.nn * D.B * sizeof(float), s));
   for (int cc = K - 1; cc >= 0; --cc) {
     if (c->ckpt && cc + 1 < K) cycle(cc == 0 ? z : c->X[cc], c->V0[cc], c->V2[cc], nullptr);
     if (lin) lin_adjoint(c->V2[cc], c->g3, c->t);
+    else if (k3) stack_adjoint(c->V2[cc], c->g3, c->t);
     else k_t_HT<<<gv, TT, 0, s>>>(D, c->fields, c->W, c->g3, c->t);
     k_t_xmAv<<<gv, TT, 0, s>>>(D, c->fields, c->g3, c->t, c->g2);
     k_t_restrict<<<gc, TT, 0, s>>>(D, c->fields, c->g2, 0, c->rc);
     TCK(coarse_solve(ct));
     k_t_P<<<gv, TT, 0, s>>>(D, c->xc, c->t);
     k_t_xmAv<<<gv, TT, 0, s>>>(D, c->fields, c->g2, c->t, c->g1);
-    if (lin) {
-      lin_adjoint(c->V0[cc], c->g1, c->t);
+    if (lin || k3) {
+      if (lin) lin_adjoint(c->V0[cc], c->g1, c->t);
+      else stack_adjoint(c->V0[cc], c->g1, c->t);
       if (cc > 0) k_t_xmAv<<<gv, TT, 0, s>>>(D, c->fields, c->g1, c->t, c->g3);
       continue;
     }
@@ -836,6 +918,7 @@ static mg_status train_step(mg_train_ctx* c, const float* params, const float* z
     return MG_OK;
   }
   if (c->arch == MG_NET_FC) TCK(launch_fc_backward(nb, D.B, c->dW, params, c->bf16, c->fc_scratch, 1.f, grad_out, s));
+  else if (k3) TCK(launch_net_backward3(nb, D.B, c->dW, params, c->param_partial, 1.f, grad_out, s));
   else if (c->arch == MG_NET_CONV_SHARED) {
     TCK(launch_net_backward(nb, D.B, c->dW, net_prm, c->bf16, c->param_partial, 1.f, c->sh_grad, s));
     TCK(launch_net_reduce_shared(c->sh_grad, grad_out, s));

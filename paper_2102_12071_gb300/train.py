@@ -24,7 +24,7 @@ LAYERS = [(7, 9), (5, 7), (3, 5), (9, 3)]  # (out, in) channels of the 3x3 layer
 NPARAMS_FC = 6800
 FC_LAYERS = [(40, 81), (40, 40), (40, 40), (9, 40)]  # the fully connected network (out, in)
 NPARAMS_LIN = 54  # the shared-kernel linear smoother of one level: six 3x3 kernels
-NPARAMS_K3 = 1746  # the convolutional network with three output kernels (inference only)
+NPARAMS_K3 = 1746  # the convolutional network with three output kernels (FP32)
 NPARAMS_SHARED = 378  # one 3x3 kernel per convolution output channel (Sec. 6.2's count)
 
 
@@ -50,12 +50,22 @@ def init_params_shared(seed: int = 0) -> torch.Tensor:
     return p
 
 
+def init_params_conv3(seed: int = 0) -> torch.Tensor:
+    """The three-kernel network: the convolutions of init_params and a zero 27-output layer,
+    so K1 = omega/D, K2 = K3 = identity (the stack starts at weighted Jacobi)."""
+    p = torch.cat([init_params(seed)[: NPARAMS - 243], torch.zeros(27 * 27)])
+    assert p.numel() == NPARAMS_K3
+    return p
+
+
 def init_for(arch: str, seed: int = 0) -> torch.Tensor:
     """Starting parameters of a trainable architecture (all start at weighted Jacobi)."""
     if arch == "fc":
         return init_params_fc(seed)
     if arch == "conv_shared":
         return init_params_shared(seed)
+    if arch == "conv3":
+        return init_params_conv3(seed)
     return init_params(seed)
 
 

@@ -10,6 +10,7 @@ from oracle import stack as OS
 from paper_2102_12071_gb300 import binding as B
 from paper_2102_12071_gb300 import inputs
 from paper_2102_12071_gb300 import solver as S
+from paper_2102_12071_gb300 import train as T
 
 pytestmark = pytest.mark.gpu
 
@@ -79,8 +80,39 @@ def test_stack_with_identity_kernels_two_and_three_solves_like_the_k1_network():
     assert np.max(np.abs(h3[0][:k] - h1[0][:k]) / h1[0][:k]) < 1e-5
 
 
-def test_stack_network_is_not_trained_here():
-    from paper_2102_12071_gb300 import train as T
+@pytest.mark.parametrize("n,cycles", [(15, 1), (31, 1), (15, 2)])
+def test_stack_train_step_matches_oracle(n, cycles):
+    """The two-grid loss (k cycles) and its gradient through the stack and the 27-output
+    network against the oracle's reverse mode (FP64 autograd over the same operations)."""
+    nprob, nvec = 2, 3
+    params = inputs.rotated_params(150 + n + cycles, nprob)
+    probs = [{"n": n, "kind": B.MG_PROBLEM_ROTATED, "eps": e, "theta": t} for e, t in params]
+    z = inputs.gaussian_vectors(151 + n + cycles, nprob * nvec, n).reshape(nprob, nvec, n, n)
+    p = stack_params(9, last=0.05)
+    batch = T.TwoGridBatch(probs, nvec, 2.0 / 3.0, False, cycles=cycles, net_arch="conv3")
+    loss, grad = batch.loss_and_grad(torch.from_numpy(p).cuda(), torch.from_numpy(z).cuda().contiguous())
+    batch.close()
+    assert grad.numel() == OS.NPARAMS
+    lo, go = 0.0, np.zeros(p.size)
+    for k, (e, t) in enumerate(params):
+        st = O.const_field(n, f32(O.q1_rotated_stencil(e, t)))
+        l1, g1 = OS.loss_and_grad(st, O.rap(st), f32(p), f32(z[k]), cycles=cycles)
+        lo += l1 / nprob
+        go += g1 / nprob
+    assert abs(loss.item() - lo) <= 1e-5 * lo, (loss.item(), lo)
+    g = grad.double().cpu().numpy()
+    assert np.linalg.norm(g - go) <= 1e-4 * np.linalg.norm(go), np.linalg.norm(g - go) / np.linalg.norm(go)
+    # kernels 2 and 3 (the last 18 x 27 weights) carry gradient of their own
+    assert np.linalg.norm(g[-18 * 27:] - go[-18 * 27:]) <= 1e-4 * np.linalg.norm(go[-18 * 27:])
 
+
+def test_stack_trainer_reduces_the_loss():
+    tr = T.Trainer(sizes=(15,), per_size=8, nvec=8, lr=3e-3, net_arch="conv3", conv_bf16=False)
+    assert tr.params.numel() == OS.NPARAMS
+    losses = [tr.step() for _ in range(60)]
+    assert np.mean(losses[-10:]) < 0.9 * np.mean(losses[:10]), (losses[:5], losses[-5:])
+
+
+def test_stack_training_is_fp32_only():
     with pytest.raises(B.MGError):
-        T.TwoGridBatch([S.rotated(15, 0.1, 0.2)], 2, net_arch="conv3")
+        T.TwoGridBatch([S.rotated(15, 0.1, 0.2)], 2, 2.0 / 3.0, True, net_arch="conv3")
