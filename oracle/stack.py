@@ -194,6 +194,10 @@ class StackMultigrid:
         u = u + prolong(uc, self.st[l].shape[1])
         return self._smooth(l, f, u)
 
+    def vcycle(self, b, x) -> np.ndarray:
+        """One V(1,1) cycle of Algorithm 1 on A x = b from the iterate x."""
+        return self._level(0, _f64(b), _f64(x).copy())
+
     def solve(self, b, rtol: float = 1e-8, max_cycles: int = 1000):
         """V-cycles from x = 0 until ||b - A x|| / ||b|| < rtol; (x, hist)."""
         from .oracle import apply

@@ -106,11 +106,14 @@ def test_stack_vcycle_reduces_to_the_c_oracle_cnn_multigrid():
     st = O.const_field(n, O.q1_rotated_stencil(0.05, 1.2))
     b = _rng(11).uniform(-1, 1, (n, n))
     p = _params(12, scale=0.05, zero_rest=True)
-    _, hs = OS.StackMultigrid(st, p).solve(b, rtol=0.0, max_cycles=10)
+    sm = OS.StackMultigrid(st, p)
+    _, hs = sm.solve(b, rtol=0.0, max_cycles=10)
     mg = O.Multigrid(st)
     mg.set_cnn(OS.k1_params(p))
     _, hc = mg.solve(b, rtol=0.0, max_cycles=10)
     assert np.max(np.abs(hs - hc) / hc) < 1e-10
+    # one cycle from zero, the FGMRES preconditioner, is the C oracle's as well
+    np.testing.assert_allclose(sm.vcycle(b, np.zeros_like(b)), mg.vcycle(b, np.zeros_like(b)), rtol=0, atol=1e-12)
     # with the other two kernels in play the smoother differs, and the cycle still runs
     _, h3 = OS.StackMultigrid(st, _params(12, scale=0.05)).solve(b, rtol=0.0, max_cycles=3)
     assert np.all(np.isfinite(h3)) and abs(h3[1] - hc[1]) > 1e-6
