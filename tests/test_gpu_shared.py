@@ -106,3 +106,23 @@ def test_shared_trainer_reduces_the_loss():
     assert tr.params.numel() == 378
     losses = [tr.step() for _ in range(60)]
     assert np.mean(losses[-10:]) < 0.9 * np.mean(losses[:10]), (losses[:5], losses[-5:])
+
+
+def test_shared_preconditioned_fgmres_matches_oracle():
+    n, eps, theta = 255, 0.01, np.pi / 4
+    p = shared_net(22)
+    b_np = inputs.rhs_uniform(inputs.SEED_RHS + 1601, n)
+    mg = S.MultigridSolver([S.rotated(n, eps, theta)], "cnn", torch.from_numpy(p).cuda(), net_arch="conv_shared")
+    xh, xl, gh, its, st = S.fgmres(mg, torch.from_numpy(b_np).cuda()[None].contiguous(), restart=30, rtol=1e-6,
+                                   max_iters=200)
+    assert st == B.MG_OK
+    st0 = O.const_field(n, f32(O.q1_rotated_stencil(eps, theta)))
+    om = O.Multigrid(st0)
+    om.set_cnn(O.shared_to_dense(f32(p)))
+    _, oh, oits = O.fgmres(lambda v: O.apply(st0, v), lambda v: om.vcycle(v, np.zeros_like(v)), f32(b_np),
+                           restart=30, rtol=1e-6, max_iters=200)
+    assert abs(int(its[0]) - oits) <= 2, (int(its[0]), oits)
+    k = min(int(its[0]), oits, 30) + 1
+    assert np.max(np.abs(gh[0][:k] - oh[:k]) / oh[:k]) <= 1e-3
+    x = xh[0].double().cpu().numpy() + xl[0].double().cpu().numpy()
+    assert np.linalg.norm(f32(b_np) - O.apply(st0, x)) / np.linalg.norm(f32(b_np)) < 1e-6

@@ -116,3 +116,23 @@ def test_stack_trainer_reduces_the_loss():
 def test_stack_training_is_fp32_only():
     with pytest.raises(B.MGError):
         T.TwoGridBatch([S.rotated(15, 0.1, 0.2)], 2, 2.0 / 3.0, True, net_arch="conv3")
+
+
+def test_stack_preconditioned_fgmres_matches_oracle():
+    """Flexible GMRES (Sec. 6.4) with one V-cycle of the stack-smoothed hierarchy as M."""
+    n, eps, theta = 255, 0.01, np.pi / 12
+    p = stack_params(21)
+    b_np = inputs.rhs_uniform(inputs.SEED_RHS + 1600, n)
+    mg = S.MultigridSolver([S.rotated(n, eps, theta)], "cnn", torch.from_numpy(p).cuda(), net_arch="conv3")
+    xh, xl, gh, its, st = S.fgmres(mg, torch.from_numpy(b_np).cuda()[None].contiguous(), restart=30, rtol=1e-6,
+                                   max_iters=200)
+    assert st == B.MG_OK
+    st0 = O.const_field(n, f32(O.q1_rotated_stencil(eps, theta)))
+    sm = OS.StackMultigrid(st0, f32(p))
+    _, oh, oits = O.fgmres(lambda v: O.apply(st0, v), lambda v: sm.vcycle(v, np.zeros_like(v)), f32(b_np),
+                           restart=30, rtol=1e-6, max_iters=200)
+    assert abs(int(its[0]) - oits) <= 2, (int(its[0]), oits)
+    k = min(int(its[0]), oits, 30) + 1
+    assert np.max(np.abs(gh[0][:k] - oh[:k]) / oh[:k]) <= 1e-3
+    x = xh[0].double().cpu().numpy() + xl[0].double().cpu().numpy()
+    assert np.linalg.norm(f32(b_np) - O.apply(st0, x)) / np.linalg.norm(f32(b_np)) < 1e-6
