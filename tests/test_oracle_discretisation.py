@@ -178,3 +178,29 @@ def test_jacobi_eigenpairs_five_point():
     hi = np.maximum(abs(A_), abs(B_)) >= math.pi / 2
     lfa = np.abs(1 - omega * (1 - (np.cos(A_) + np.cos(B_)) / 2))[hi].max()
     assert abs(lfa - 2.0 / 3.0) < 1e-12 and mu <= lfa + 1e-12
+
+
+@pytest.mark.parametrize("eps,theta", [(0.01, math.pi / 6), (0.2, 1.1), (0.05, 2.7)])
+def test_orientation_mirror_and_transpose_symmetries(eps, theta):
+    """The orientation convention (row index = y, column = x) is immaterial: mirroring the
+    grid in x is K(theta) -> K(-theta) (the cross term changes sign) and swapping x and y is
+    theta -> pi/2 - theta, for the operator and for whole V-cycle solves (same histories,
+    mirrored or transposed iterates).  The parametrisation itself is pinned by the closed
+    form above."""
+    n = 31
+    rng = np.random.default_rng(40)
+    u = rng.standard_normal((n, n))
+    A = O.q1_rotated_stencil(eps, theta)
+    A_m = O.q1_rotated_stencil(eps, -theta)
+    A_t = O.q1_rotated_stencil(eps, math.pi / 2 - theta)
+    Au = O.apply(O.const_field(n, A), u)
+    np.testing.assert_allclose(O.apply(O.const_field(n, A_m), u[:, ::-1])[:, ::-1], Au, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(O.apply(O.const_field(n, A_t), u.T).T, Au, rtol=0, atol=1e-13)
+    b = rng.uniform(-1, 1, (n, n))
+    x, h = O.Multigrid(O.const_field(n, A)).solve(b, rtol=0.0, max_cycles=6)
+    x_m, h_m = O.Multigrid(O.const_field(n, A_m)).solve(np.ascontiguousarray(b[:, ::-1]), rtol=0.0, max_cycles=6)
+    x_t, h_t = O.Multigrid(O.const_field(n, A_t)).solve(np.ascontiguousarray(b.T), rtol=0.0, max_cycles=6)
+    np.testing.assert_allclose(h_m, h, rtol=1e-10)
+    np.testing.assert_allclose(h_t, h, rtol=1e-10)
+    np.testing.assert_allclose(x_m[:, ::-1], x, rtol=0, atol=1e-10 * np.abs(x).max())
+    np.testing.assert_allclose(x_t.T, x, rtol=0, atol=1e-10 * np.abs(x).max())
