@@ -60,11 +60,13 @@ def jacobi_matrix(Al: np.ndarray, omega: float = 2.0 / 3.0) -> np.ndarray:
     return omega * np.diag(1.0 / np.diag(Al))
 
 
-def vcycle_matrix(A: np.ndarray, ns: list[int], smoother=None, nu1: int = 1, nu2: int = 1) -> np.ndarray:
+def vcycle_matrix(A: np.ndarray, ns: list[int], smoother=None, nu1: int = 1, nu2: int = 1, rscale: float = 1.0,
+                  mixed: bool = False) -> np.ndarray:
     """Error propagation of the recursive V-cycle with Galerkin coarse operators.
 
-    E_l = S_l^nu2 (I - P_l (I - E_{l+1}) A_{l+1}^{-1} P_l^T A_l) S_l^nu1, E_last = 0,
-    S_l = I - H_l A_l with H_l = smoother(l, A_l) (default weighted Jacobi).
+    E_l = S_l^nu2 (I - P_l (I - E_{l+1}) A_{l+1}^{-1} R_l A_l) S_l^nu1, E_last = 0,
+    S_l = I - H_l A_l with H_l = smoother(l, A_l) (default weighted Jacobi), restriction
+    R_l = rscale P_l^T and A_{l+1} = R_l A_l P_l (mixed: P_l^T A_l P_l whatever rscale).
     """
     smoother = smoother or (lambda l, Al: jacobi_matrix(Al))
 
@@ -74,10 +76,11 @@ def vcycle_matrix(A: np.ndarray, ns: list[int], smoother=None, nu1: int = 1, nu2
         if l == len(ns) - 1:
             return np.zeros_like(Al)
         P = prolongation(n)
-        Ac = P.T @ Al @ P
+        R = rscale * P.T
+        Ac = (P.T if mixed else R) @ Al @ P
         Ec = rec(l + 1, Ac)
         S = I - smoother(l, Al) @ Al
-        C = I - P @ (np.eye(Ac.shape[0]) - Ec) @ np.linalg.solve(Ac, P.T @ Al)
+        C = I - P @ (np.eye(Ac.shape[0]) - Ec) @ np.linalg.solve(Ac, R @ Al)
         return np.linalg.matrix_power(S, nu2) @ C @ np.linalg.matrix_power(S, nu1)
 
     return rec(0, A)

@@ -35,6 +35,22 @@ def test_vcycle_equals_dense_recursion(coarsest, ns, eps, theta):
     np.testing.assert_allclose(E, Ed, atol=1e-12)
 
 
+def test_restriction_scaling_with_its_galerkin_operator_is_immaterial():
+    """Algorithm 1 restricts with P^T and coarsens with P^T A P; the paper's full-weighting
+    stencil is P^T / 4.  Scaling the restriction and the coarse operator together leaves
+    the cycle unchanged (Jacobi on a scaled operator is the same smoother); full weighting
+    with P^T A P instead under-corrects by 4 and converges visibly slower."""
+    n = 15
+    s = O.q1_rotated_stencil(0.05, 0.6)
+    mg = O.Multigrid(O.const_field(n, s), coarsest_n=3)
+    E = _cycle_matrix(mg, n)
+    A = D.const_matrix(s, n)
+    np.testing.assert_allclose(D.vcycle_matrix(A, [15, 7, 3], rscale=0.25), E, atol=1e-12)
+    Em = D.vcycle_matrix(A, [15, 7, 3], rscale=0.25, mixed=True)
+    rho = lambda M: np.abs(np.linalg.eigvals(M)).max()
+    assert np.abs(Em - E).max() > 1e-2 and rho(Em) > rho(E) + 0.1
+
+
 def test_vcycle_with_per_point_kernels_equals_dense():
     """Same check with arbitrary per-point 3x3 smoothing kernels H (the CNN smoother form)
     on a variable-coefficient operator, with two pre- and one post-smoothing step."""
