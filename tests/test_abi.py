@@ -103,3 +103,31 @@ def test_smoothing_steps_and_linear_smoother_options_are_checked_on_the_host(lib
                                                    net_per_problem=1)) > 0
     assert B.mg_workspace_size(probs, 1, B.options(B.MG_SMOOTH_CNN, net_arch=7)) == 0
     assert lib.mg_net_param_count(B.MG_NET_LINEAR) == 54
+
+
+def test_network_architectures_are_checked_on_the_host(lib):
+    """Parameter counts per architecture (Sec. 6.2's 6 800 and 378 among them) and which
+    architecture/option pairs the setup and the training accept, without a GPU."""
+    counts = {B.MG_NET_CONV: 1260, B.MG_NET_FC: 6800, B.MG_NET_LINEAR: 54, B.MG_NET_CONV3: 1746,
+              B.MG_NET_CONV_SHARED: 378}
+    for arch, count in counts.items():
+        assert lib.mg_net_param_count(arch) == count
+    assert lib.mg_net_param_count(5) == 0
+    rot, _ = B.problems_array([{"n": 63, "kind": B.MG_PROBLEM_ROTATED, "eps": 0.1, "theta": 0.4}])
+    cnn = lambda **kw: B.options(B.MG_SMOOTH_CNN, **kw)
+    dense = B.mg_workspace_size(rot, 1, cnn())
+    shared = B.mg_workspace_size(rot, 1, cnn(net_arch=B.MG_NET_CONV_SHARED))
+    assert shared > dense > 0  # plus the expanded dense set
+    assert B.mg_workspace_size(rot, 1, cnn(net_arch=B.MG_NET_CONV_SHARED, net_levels=3)) > shared
+    assert B.mg_workspace_size(rot, 1, cnn(net_arch=B.MG_NET_CONV3)) > 0
+    # the three-kernel stack: FP32, no transposed smoother, one smoothing step
+    assert B.mg_workspace_size(rot, 1, cnn(net_arch=B.MG_NET_CONV3, conv_bf16=1)) == 0
+    assert b"FP32" in lib.mg_last_error()
+    assert B.mg_workspace_size(rot, 1, cnn(net_arch=B.MG_NET_CONV3, nu1=2)) == 0
+    # training: every architecture but bf16 with the stack
+    for arch in counts:
+        assert B.mg_train_workspace_size(rot, 1, 4, cnn(net_arch=arch)) > 0, arch
+    assert B.mg_train_workspace_size(rot, 1, 4, cnn(net_arch=B.MG_NET_CONV3, conv_bf16=1)) == 0
+    assert b"FP32" in lib.mg_last_error()
+    t_dense = B.mg_train_workspace_size(rot, 1, 4, cnn())
+    assert B.mg_train_workspace_size(rot, 1, 4, cnn(net_arch=B.MG_NET_CONV3)) > t_dense  # 27 outputs, stack scratch
