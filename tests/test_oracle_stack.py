@@ -8,10 +8,12 @@ identity, and the remaining gradient by central differences.
 import math
 
 import numpy as np
+import pytest
 import torch
 
 import oracle as O
 from oracle import stack as OS
+from tests import dense_ref as D
 
 
 def _rng(seed):
@@ -117,3 +119,42 @@ def test_stack_vcycle_reduces_to_the_c_oracle_cnn_multigrid():
     # with the other two kernels in play the smoother differs, and the cycle still runs
     _, h3 = OS.StackMultigrid(st, _params(12, scale=0.05)).solve(b, rtol=0.0, max_cycles=3)
     assert np.all(np.isfinite(h3)) and abs(h3[1] - hc[1]) > 1e-6
+
+
+def test_kernels_two_and_three_are_the_k1_network_on_their_rows_of_the_last_layer():
+    """out_k (k = 2, 3) is the k = 1 network of the C oracle whose last layer is the stack's
+    rows 9(k-1) .. 9k-1: recovered from W = (omega delta + out)/D as out = D W - omega delta."""
+    n, omega = 11, 0.6
+    st = O.varcoef5_field(n, np.exp(_rng(20).standard_normal((n + 1, n + 1))))
+    p = _params(21)
+    K = OS.kernels(st, torch.from_numpy(p), omega).numpy()
+    conv = p[:1017]
+    wf = p[1017:].reshape(27, 27)
+    delta = np.zeros((9, 1, 1))
+    delta[4] = 1.0
+    for k in (1, 2):
+        W = O.hypernet_forward(st, np.concatenate([conv, wf[9 * k:9 * k + 9].ravel()]), omega)
+        out = W * st[4] - omega * delta
+        np.testing.assert_allclose(K[k], delta + out, rtol=1e-12, atol=1e-12 * np.abs(out).max())
+
+
+@pytest.mark.parametrize("cycles", [1, 2])
+def test_loss_is_the_dense_error_propagation_of_the_stack(cycles):
+    """The loss at a general point (all three kernels active) against dense matrices:
+    H = K3 K2 K1 from per-point kernel matrices, S = I - H A, C = I - P Ac^-1 P^T A."""
+    n = 7
+    st = O.varcoef5_field(n, np.exp(0.5 * _rng(22).standard_normal((n + 1, n + 1))))
+    stc = O.rap(st)
+    p = _params(23, scale=0.1)
+    z = _rng(24).standard_normal((3, n, n))
+    K = OS.kernels(st, torch.from_numpy(p)).numpy()
+    A = D.field_matrix(st)
+    H = D.kernels_matrix(K[2]) @ D.kernels_matrix(K[1]) @ D.kernels_matrix(K[0])
+    P = D.prolongation(n)
+    I = np.eye(n * n)
+    S = I - H @ A
+    C = I - P @ np.linalg.solve(P.T @ A @ P, P.T @ A)
+    E = np.linalg.matrix_power(S @ C @ S, cycles)
+    ref = np.mean([np.sum((E @ zj.ravel()) ** 2) for zj in z]) / (n * n)
+    L = float(OS.loss(st, stc, torch.from_numpy(p), z, cycles=cycles))
+    assert math.isclose(L, ref, rel_tol=1e-11), (L, ref)
