@@ -3,7 +3,9 @@
 The stack reduces to the k = 1 network when the last layer's rows of kernels 2 and 3 are
 zero; there the oracle must agree with the independent C oracle (network, loss, gradient).
 Its operators are checked against the C oracle's, the stack's transpose by the adjoint
-identity, and the remaining gradient by central differences.
+identity, kernels 2 and 3 against the C oracle's network on their rows of the last layer,
+the loss at a general point against dense error-propagation matrices, and the remaining
+gradient by central differences.
 """
 import math
 
