@@ -306,7 +306,9 @@ void mg_train_destroy(mg_train_ctx* ctx);
    one post-smoothing step, eq. overalltrain with u_* = 0, Thm. sbound), after k cycles:
      loss = (1/nprob) sum_b (1/nvec) sum_j || (S C S)^k z_bj ||^2 / n^2,
      S = I - H A,  C = I - P (P^T A P)^{-1} P^T A,
-   with H the network's per-point kernels for problem b and k set by mg_train_set_cycles
+   with H the network's per-point kernels for problem b (MG_NET_CONV, MG_NET_CONV_SHARED,
+   MG_NET_FC), the stack K3 K2 K1 of MG_NET_CONV3 (FP32 only) or the linear chain of
+   MG_NET_LINEAR, and k set by mg_train_set_cycles
    (default: train_cycles of the setup).  z: DEVICE float[nprob][nvec][n][n] (the random
    vectors, supplied by the caller), params and grad_out: DEVICE
    float[mg_net_param_count(net_arch of the setup)] (grad_out overwritten with dloss/dparams,
