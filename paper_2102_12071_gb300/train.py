@@ -209,10 +209,15 @@ class Trainer:
 
     def __init__(self, sizes=(31, 63), per_size: int = 32, nvec: int = 32, omega: float = 2.0 / 3.0,
                  conv_bf16: bool = True, lr: float = 1e-3, seed: int = 0, eps_range=(1e-3, 1.0),
-                 families=("rotated",), max_cycles: int = 1, checkpoint: bool = False, net_arch: str = "conv"):
+                 families=("rotated",), max_cycles: int = 1, checkpoint: bool = False, net_arch: str = "conv",
+                 device="cuda"):
         """max_cycles = b of Algorithm 2: each step's loss spans k ~ U{1..b} two-grid cycles.
         net_arch: "conv", "conv_shared" (one kernel per convolution output channel, Sec. 6.2's
-        378 parameters) or "fc" (the fully connected network of Sec. 4.2)."""
+        378 parameters), "conv3" (three stacked output kernels, FP32) or "fc" (the fully
+        connected network of Sec. 4.2).  A training step needs the library and a GPU; device
+        only places the parameters, the optimizer state and the generator of the random
+        vectors (checkpoints can be written and read without a GPU)."""
+        self.device = torch.device(device)
         self.max_cycles = max_cycles
         self.checkpoint = checkpoint
         self.net_arch = net_arch
@@ -223,9 +228,9 @@ class Trainer:
         self.conv_bf16 = conv_bf16
         self.eps_range = eps_range
         self.families = families
-        self.params = init_for(net_arch, seed).cuda().requires_grad_(True)
+        self.params = init_for(net_arch, seed).to(self.device).requires_grad_(True)
         self.opt = torch.optim.Adam([self.params], lr=lr)
-        self.gen = torch.Generator(device="cuda").manual_seed(inputs.SEED_TRAIN + seed)
+        self.gen = torch.Generator(device=self.device).manual_seed(inputs.SEED_TRAIN + seed)
         self._ws = {}
         self.step_count = 0
 
@@ -236,7 +241,7 @@ class Trainer:
             return [{"n": n, "kind": B.MG_PROBLEM_ROTATED, "eps": e, "theta": t} for e, t in params]
         # variable coefficients a = exp(g), g a unit-variance Gaussian random field (Sec. 6.2)
         return [{"n": n, "kind": B.MG_PROBLEM_VARCOEF5,
-                 "data": torch.from_numpy(inputs.grf_cells(seed * 64 + k, n)).cuda()}
+                 "data": torch.from_numpy(inputs.grf_cells(seed * 64 + k, n)).to(self.device)}
                 for k in range(self.per_size)]
 
     def cycles(self, step: int) -> int:
@@ -257,7 +262,7 @@ class Trainer:
                                      cycles=self.max_cycles, checkpoint=self.checkpoint, net_arch=self.net_arch)
                 batch.set_cycles(k)
                 self._ws[key] = batch.workspace
-                z = torch.randn((self.per_size, self.nvec, n, n), generator=self.gen, device="cuda")
+                z = torch.randn((self.per_size, self.nvec, n, n), generator=self.gen, device=self.device)
                 total = total + TwoGridLoss.apply(self.params, z, batch)
                 count += 1
         return total / count
@@ -273,6 +278,39 @@ class Trainer:
     def save(self, path: str) -> None:
         os.makedirs(os.path.dirname(path), exist_ok=True)
         np.save(path, self.params.detach().cpu().numpy().astype(np.float32))
+
+    # ---------------------------------------------------------------- checkpoint / resume
+    def config(self) -> dict:
+        """What fixes the sequence of batches and losses (a resume must match it)."""
+        return {"net_arch": self.net_arch, "sizes": list(self.sizes), "per_size": self.per_size, "nvec": self.nvec,
+                "omega": self.omega, "conv_bf16": bool(self.conv_bf16), "eps_range": list(self.eps_range),
+                "families": list(self.families), "max_cycles": self.max_cycles}
+
+    def state_dict(self) -> dict:
+        """Parameters, Adam state, the state of the random-vector generator and the step:
+        a run resumed from it draws the same problems and vectors and takes the same steps."""
+        return {"config": self.config(), "step": self.step_count, "params": self.params.detach().cpu().clone(),
+                "opt": self.opt.state_dict(), "gen": self.gen.get_state()}
+
+    def load_state_dict(self, state: dict) -> None:
+        if state["config"] != self.config():
+            raise ValueError(f"checkpoint of another training setup: {state['config']} vs {self.config()}")
+        with torch.no_grad():
+            self.params.copy_(state["params"].to(self.device))
+        self.opt.load_state_dict(state["opt"])
+        self.gen.set_state(state["gen"])
+        self.step_count = int(state["step"])
+
+    def save_checkpoint(self, path: str) -> None:
+        d = os.path.dirname(path)
+        if d:
+            os.makedirs(d, exist_ok=True)
+        tmp = f"{path}.tmp{os.getpid()}"
+        torch.save(self.state_dict(), tmp)
+        os.replace(tmp, path)  # a crash mid-write leaves the previous checkpoint intact
+
+    def load_checkpoint(self, path: str) -> None:
+        self.load_state_dict(torch.load(path, map_location="cpu", weights_only=True))
 
 
 class AdaptiveTrainer:
@@ -402,6 +440,10 @@ def main():
     ap.add_argument("--max-cycles", type=int, default=1, help="b: each step's loss spans k ~ U{1..b} cycles")
     ap.add_argument("--checkpoint", action="store_true", help="recompute cycle products in the backward pass")
     ap.add_argument("--fc", action="store_true", help="train the fully connected network (Sec. 4.2)")
+    ap.add_argument("--arch", default=None, choices=["conv", "conv_shared", "conv3", "fc"],
+                    help="network architecture (default conv; --fc is --arch fc)")
+    ap.add_argument("--state", default=None, metavar="PATH",
+                    help="checkpoint: resume from PATH if it exists, write it every 100 steps and at the end")
     ap.add_argument("--adaptive", type=int, default=0, metavar="N_FINE",
                     help="Algorithm 2: one network per level of a hierarchy of this side, trained coarse to fine "
                          "(--steps per level); saves [levels, nparams], finest first")
@@ -455,16 +497,24 @@ def main():
         np.save(out, torch.stack([at.params[n] for n in at.sizes]).cpu().numpy().astype(np.float32))
         print("saved", out, "levels", at.sizes)
         return
-    tr = Trainer(lr=args.lr, seed=args.seed, conv_bf16=not args.fp32_conv,
+    arch = args.arch or ("fc" if args.fc else "conv")
+    tr = Trainer(lr=args.lr, seed=args.seed, conv_bf16=not args.fp32_conv and arch != "conv3",
                  families=tuple(f.strip() for f in args.families.split(",")), max_cycles=args.max_cycles,
-                 checkpoint=args.checkpoint, net_arch="fc" if args.fc else "conv")
+                 checkpoint=args.checkpoint, net_arch=arch)
+    if args.state and os.path.exists(args.state):
+        tr.load_checkpoint(args.state)
+        print(f"resumed from {args.state} at step {tr.step_count}", flush=True)
     t0 = time.time()
-    for s in range(args.steps):
+    while tr.step_count < args.steps:
+        s = tr.step_count
         l = tr.step()
         if s % 50 == 0 or s == args.steps - 1:
             print(f"step {s:5d} loss {l:.6f} ({time.time() - t0:.1f} s)", flush=True)
+        if args.state and (tr.step_count % 100 == 0 or tr.step_count == args.steps):
+            tr.save_checkpoint(args.state)
+    prefix = {"conv": "cnn", "fc": "fc", "conv_shared": "cnn378", "conv3": "cnn3"}[arch]
     out = args.out or os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights",
-                                   f"{'fc' if args.fc else 'cnn'}_{tr.families[0]}.npy")
+                                   f"{prefix}_{tr.families[0]}.npy")
     tr.save(out)
     print("saved", out)
 
