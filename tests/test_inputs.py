@@ -1,0 +1,34 @@
+"""The seeded input recipes (no GPU): the Gaussian random field behind the variable
+coefficients a = exp(g) has unit variance and the squared-exponential correlation of
+length 1/16 on the unit square (statistics over 200 seeded fields of 64 x 64 cells), and
+the mixed-batch sizes are 2^m - 1 within the requested range."""
+import numpy as np
+import pytest
+
+from paper_2102_12071_gb300 import inputs
+
+
+@pytest.fixture(scope="module")
+def fields():
+    n = 63
+    return n + 1, np.stack([np.log(inputs.grf_cells(10_000 + s, n).astype(np.float64)) for s in range(200)])
+
+
+def test_grf_has_unit_variance_and_zero_mean(fields):
+    _, g = fields
+    assert abs(g.mean()) < 0.05
+    assert abs(g.var() - 1.0) < 0.05
+
+
+@pytest.mark.parametrize("lag", [1, 4, 8])
+def test_grf_correlation_is_squared_exponential_of_length_one_sixteenth(fields, lag):
+    m, g = fields
+    expect = np.exp(-((lag / m) ** 2) / (2.0 * (1.0 / 16.0) ** 2))
+    for axis in (1, 2):  # isotropic: rows and columns alike
+        assert abs(np.mean(g * np.roll(g, lag, axis=axis)) - expect) < 0.03
+
+
+def test_mixed_batch_sizes_are_admissible():
+    sizes = inputs.grid_sizes_loguniform(7, 256)
+    assert all(((s + 1) & s) == 0 and 63 <= s <= 2047 for s in sizes)
+    assert len(set(sizes)) >= 5  # log-uniform over the range, not one size
