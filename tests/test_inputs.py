@@ -32,3 +32,24 @@ def test_mixed_batch_sizes_are_admissible():
     sizes = inputs.grid_sizes_loguniform(7, 256)
     assert all(((s + 1) & s) == 0 and 63 <= s <= 2047 for s in sizes)
     assert len(set(sizes)) >= 5  # log-uniform over the range, not one size
+
+
+def test_rotated_parameters_are_log_uniform_eps_and_uniform_theta():
+    pairs = inputs.rotated_params(3, 4000)
+    le = np.log10([e for e, _ in pairs])
+    th = np.array([t for _, t in pairs])
+    assert le.min() >= -3.0 and le.max() <= 0.0 and th.min() >= 0.0 and th.max() <= np.pi
+    # uniform in log10(eps) and in theta: quartiles at a quarter of each range
+    np.testing.assert_allclose(np.quantile(le, [0.25, 0.5, 0.75]), [-2.25, -1.5, -0.75], atol=0.08)
+    np.testing.assert_allclose(np.quantile(th, [0.25, 0.5, 0.75]), np.pi * np.array([0.25, 0.5, 0.75]), atol=0.08)
+    assert inputs.rotated_params(3, 4000) == pairs  # seeded: reproducible
+
+
+def test_right_hand_sides_and_loss_vectors():
+    b = inputs.rhs_uniform(1, 255)
+    assert b.dtype == np.float32 and b.shape == (255, 255)
+    assert b.min() >= -1.0 and b.max() <= 1.0 and abs(b.var() - 1.0 / 3.0) < 0.01
+    z = inputs.gaussian_vectors(2, 8, 63)
+    assert z.dtype == np.float32 and z.shape == (8, 63, 63)
+    assert abs(z.mean()) < 0.02 and abs(z.var() - 1.0) < 0.03
+    assert np.array_equal(inputs.rhs_uniform(1, 255), b)  # reproducible
