@@ -1,7 +1,9 @@
 """The seeded input recipes (no GPU): the Gaussian random field behind the variable
 coefficients a = exp(g) has unit variance and the squared-exponential correlation of
-length 1/16 on the unit square (statistics over 200 seeded fields of 64 x 64 cells), and
-the mixed-batch sizes are 2^m - 1 within the requested range."""
+length 1/16 on the unit square (statistics over 200 seeded fields of 64 x 64 cells); the
+mixed-batch sizes are 2^m - 1 within the requested range; (eps, theta) are log-uniform
+and uniform over their ranges; right-hand sides are uniform[-1, 1] and the loss vectors
+standard normal."""
 import numpy as np
 import pytest
 
