@@ -154,9 +154,8 @@ __global__ void k_t_xmP(TrainDims D, const float* __restrict__ x, const float* _
   out[(size_t)vec * D.nn + q] = x[(size_t)vec * D.nn + q] - v;
 }
 
-// per-vector sum of squares (one CTA per vector) and g3 = scale * e3
-__global__ void k_t_loss(TrainDims D, const float* __restrict__ e3, float scale, float* __restrict__ g3,
-                         float* __restrict__ partial) {
+// per-vector sum of squares (one CTA per vector) and g3 = scale * e3 (g3 may be e3: in place)
+__global__ void k_t_loss(TrainDims D, const float* e3, float scale, float* g3, float* __restrict__ partial) {
   const int vec = blockIdx.x;
   const float* e = e3 + (size_t)vec * D.nn;
   float* g = g3 + (size_t)vec * D.nn;
