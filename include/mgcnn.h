@@ -357,11 +357,12 @@ mg_status mg_train_set_cycles(mg_train_ctx* ctx, int cycles);
    MG_ERR_INVALID_ARG (other smoothers or options: MG_ERR_UNSUPPORTED).
    Arguments, outputs and return codes are those of mg_solve (b, x_hi, x_lo DEVICE
    [nprob][n][n], x_lo may be NULL; hist, cycles HOST or NULL); opts must ask for
-   MG_SMOOTH_JACOBI, nu1 = nu2 = 1, coarsest_n = 3.  The first call on a device looks up
-   the array's device address on the current device, so make it before any stream
-   capture.  Every call reuses the same array and resets what must start from zero; calls
-   whose GPU work overlaps (two threads, or two streams) race on it and must be serialised
-   by the caller.  Blocks the calling thread until the solve has finished. */
+   MG_SMOOTH_JACOBI, nu1 = nu2 = 1, coarsest_n = 3.  Every call looks up the array's device
+   address on the current device (a host-side query).  Every call reuses the same array
+   and resets what must start from zero; calls whose GPU work overlaps (two threads, or two
+   streams) race on it and must be serialised by the caller.  Blocks the calling thread
+   until the solve has finished (it reads the control blocks back after each chunk of
+   cycles). */
 mg_status mg_solve_small_static(const mg_problem* problems, int nprob, const mg_options* opts,
                                 const float* b, float* x_hi, float* x_lo, double rtol,
                                 int max_cycles, double* hist, int* cycles, void* stream);
@@ -377,6 +378,14 @@ mg_status mg_solve_small_static(const mg_problem* problems, int nprob, const mg_
    5 up-sweeps of levels >= 1; -1 returns in *launches the number of kernels this context
    launched since the last reset (timing or not). */
 mg_status mg_profile_enable(mg_ctx* ctx, int enable);
+
+/* Test setting for failure detection (the paper has no counterpart): with on != 0 the
+   following solves and cycles of ctx make the first bounded wait for every tile's copies
+   give up at once, so the expiry path runs: the wait for the copies still in flight keeps
+   its full bound (they land before the CTA exits), the problem is marked timed out, and
+   mg_solve / mg_vcycle report MG_ERR_TIMEOUT.  It concerns the tiled levels only (n > 63);
+   on = 0 restores normal solves.  Host-only; takes effect at the next solve or cycle. */
+mg_status mg_debug_short_wait(mg_ctx* ctx, int on);
 mg_status mg_profile_read(mg_ctx* ctx, int kernel_class, double* total_ms, long long* launches);
 
 /* ------------------------------------------------------------------- misc ---- */

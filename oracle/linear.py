@@ -132,17 +132,12 @@ class LinearMultigrid:
     """Galerkin hierarchy of st0 with the shared-kernel linear smoother on every level but
     the coarsest; phis[l] (or phis[-1] for deeper levels) smooths level l."""
 
-    def __init__(self, st0, phis, coarsest_n: int = 3, fields=None, nu1: int = 1, nu2: int = 1):
-        """fields: the level operators to use instead of the Galerkin products of st0 (a
-        caller that wants another implementation's rounded coarse fields); nu1, nu2: the
-        smoothing steps before and after the coarse correction."""
+    def __init__(self, st0, phis, coarsest_n: int = 3, nu1: int = 1, nu2: int = 1):
+        """nu1, nu2: the smoothing steps before and after the coarse correction."""
         self.nu1, self.nu2 = nu1, nu2
-        if fields is not None:
-            self.st = [_f64(f) for f in fields]
-        else:
-            self.st = [_f64(st0)]
-            while self.st[-1].shape[1] > coarsest_n and (self.st[-1].shape[1] - 1) % 2 == 0:
-                self.st.append(rap(self.st[-1]))
+        self.st = [_f64(st0)]
+        while self.st[-1].shape[1] > coarsest_n and (self.st[-1].shape[1] - 1) % 2 == 0:
+            self.st.append(rap(self.st[-1]))
         self.L = len(self.st)
         phis = [_f64(p).reshape(NPHI, 9) for p in phis]
         self.phi = [phis[min(l, len(phis) - 1)] for l in range(self.L)]

@@ -81,6 +81,7 @@ def lib() -> ctypes.CDLL:
         "mg_solve_small_static": (ctypes.c_int, [ctypes.POINTER(mg_problem), ctypes.c_int, ctypes.POINTER(mg_options),
                                                  _P, _P, _P, ctypes.c_double, ctypes.c_int, _P, _P, _P]),
         "mg_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
+        "mg_debug_short_wait": (ctypes.c_int, [_P, ctypes.c_int]),
         "mg_profile_read": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_longlong)]),
         "mg_rotated_stencil": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_float)]),
@@ -290,6 +291,10 @@ def mg_fgmres(ctx, b, x_hi, x_lo, restart, rtol, max_iters, workspace, ws_bytes,
 
 def mg_train_set_cycles(ctx, cycles: int) -> None:
     check(lib().mg_train_set_cycles(ctx, int(cycles)), "mg_train_set_cycles")
+
+
+def mg_debug_short_wait(ctx, on: bool) -> None:
+    check(lib().mg_debug_short_wait(ctx, int(on)), "mg_debug_short_wait")
 
 
 def mg_profile_enable(ctx, enable: bool) -> None:

@@ -882,6 +882,12 @@ mg_status mg_net_forward(int n, int nprob, const float* fields, const float* par
   return MG_OK;
 }
 
+mg_status mg_debug_short_wait(mg_ctx* ctx, int on) {
+  if (!ctx) return fail(MG_ERR_INVALID_ARG, "mg_debug_short_wait: ctx is NULL");
+  ctx->args.short_wait = on != 0;
+  return MG_OK;
+}
+
 mg_status mg_profile_enable(mg_ctx* ctx, int enable) {
   if (!ctx) return fail(MG_ERR_INVALID_ARG, "mg_profile_enable: ctx is NULL");
   ctx->prof.reset();

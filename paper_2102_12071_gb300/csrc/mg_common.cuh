@@ -88,6 +88,8 @@ struct ProbState {
   int status;          // 0 running, 1 converged, 2 hit max cycles, 3 non-finite residual,
                        // 4 a bounded wait for tile copies expired
   unsigned int counter;  // last-CTA detection for the norm reduction
+  int short_wait;        // test setting: nonzero makes the first wait for a tile's copies
+                         // give up at once (mg_debug_short_wait); 0 in every normal solve
   float hist[MG_HRING];  // hist[k % MG_HRING] = relative residual after k cycles
 };
 

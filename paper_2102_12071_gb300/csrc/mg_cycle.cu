@@ -34,7 +34,7 @@ __device__ __forceinline__ void load_stencil(const LevelDev& L, float (&s)[9]) {
 // ------------------------------------------------------------------ norms
 __global__ void __launch_bounds__(NT) k_bnorm(const ProbDev* __restrict__ probs, ProbState* __restrict__ state,
                                               float* __restrict__ partials, int ntiles_max,
-                                              const float* __restrict__ b) {
+                                              const float* __restrict__ b, int short_wait) {
   const int p = blockIdx.y;
   const int n = probs[p].lv[0].n;
   const size_t nn = (size_t)n * n;
@@ -60,6 +60,7 @@ __global__ void __launch_bounds__(NT) k_bnorm(const ProbDev* __restrict__ probs,
       state[p].iter = 0;
       state[p].cycles = 0;
       state[p].status = 0;
+      state[p].short_wait = short_wait;
     }
   }
 }
@@ -248,7 +249,7 @@ cudaError_t launch_bnorm(const CycleArgs& a, const float* b) {
   // norm partial slots start empty (see block_partial_and_last)
   cudaError_t e = cudaMemsetAsync(a.partials, 0xff, sizeof(float) * (size_t)a.nprob * a.ntiles_max, a.stream);
   if (e != cudaSuccess) return e;
-  k_bnorm<<<grid, NT, 0, a.stream>>>(a.probs, a.state, a.partials, a.ntiles_max, b);
+  k_bnorm<<<grid, NT, 0, a.stream>>>(a.probs, a.state, a.partials, a.ntiles_max, b, a.short_wait);
   return cudaGetLastError();
 }
 

@@ -143,6 +143,7 @@ struct CycleArgs {
   int nu1, nu2;                   // smoothing steps; other than 1 only on the batched level path
   int generic;                    // levels above the tail on the batched level path (mg_linear.cu):
                                   // the linear smoother, the kernel stack, or nu other than 1
+  int short_wait;                 // test setting copied into the control blocks by launch_bnorm
 };
 
 

@@ -149,9 +149,9 @@ __global__ void k_kry_axpy(float* __restrict__ w, const float* __restrict__ V, s
   w[(size_t)p * nn + q] = fmaf(sign, acc, w[(size_t)p * nn + q]);
 }
 
-// out_p = s_p w_p
-__global__ void k_kry_scale(float* __restrict__ out, const float* __restrict__ w, size_t nn,
-                            const float* __restrict__ s) {
+// out_p = s_p w_p; out and w may be the same array (the restart scales V_0 in place), so
+// neither is declared restrict
+__global__ void k_kry_scale(float* out, const float* w, size_t nn, const float* __restrict__ s) {
   const int p = blockIdx.y;
   const size_t q = (size_t)blockIdx.x * KT + threadIdx.x;
   if (q >= nn) return;

@@ -9,11 +9,11 @@
 // V-cycles using only a fixed scratch array that is part of the library image.
 //
 // The scratch is one file-scope device array shared by every call on a device and kept
-// until the process exits.  Its device address is looked up once per device by the first
-// call on that device, so that first call should come before any stream capture.  Calls
-// that overlap on the GPU -- from two threads, or on two streams -- race on the array.
+// until the process exits.  Every call looks up its device address on the current device
+// (a host-side query, no allocation), so a context rebuilt by cudaDeviceReset between calls
+// is seen.  Every call waits for its stream and reads the control blocks back to the host.
+// Calls that overlap on the GPU -- from two threads, or on two streams -- race on the array.
 #include <math.h>
-#include <mutex>
 #include <string.h>
 
 #include "mg_internal.h"
@@ -23,7 +23,6 @@ using namespace mg;
 
 namespace {
 
-constexpr int kMaxDevices = 64;
 constexpr size_t kStaticBytes = (size_t)MG_STATIC_SCRATCH_BYTES;
 
 // every field below sits inside g_static_scratch, carved in this order
@@ -51,24 +50,17 @@ StaticLayout static_layout(int nprob, int n, int m) {
 
 static __device__ __align__(256) unsigned char g_static_scratch[MG_STATIC_SCRATCH_BYTES];
 
-static std::mutex g_static_mu;
-static void* g_static_ptr[kMaxDevices];
-
-// Device address of g_static_scratch on the current device, looked up once per device.
+// Device address of g_static_scratch on the current device.  In host code the array's
+// name is only a host-side stand-in, so the address comes from the runtime on every call.
 static mg_status static_scratch(void** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return (mg_status)api_fail(MG_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return (mg_status)api_fail(MG_ERR_UNSUPPORTED, "device %d out of range", dev);
-  std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_static_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress((void**)&p, g_static_scratch);
-    if (e != cudaSuccess || !p)
-      return (mg_status)api_fail(MG_ERR_CUDA, "cudaGetSymbolAddress(g_static_scratch): %s", cudaGetErrorString(e));
-    g_static_ptr[dev] = p;
-  }
-  *out = g_static_ptr[dev];
+  void* p = nullptr;
+  e = cudaGetSymbolAddress((void**)&p, g_static_scratch);
+  if (e != cudaSuccess || !p)
+    return (mg_status)api_fail(MG_ERR_CUDA, "cudaGetSymbolAddress(g_static_scratch): %s", cudaGetErrorString(e));
+  *out = p;
   return MG_OK;
 }
 

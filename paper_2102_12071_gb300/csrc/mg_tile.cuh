@@ -40,9 +40,11 @@ __device__ __forceinline__ float dot9(const float (&w)[9], const Win& v) {
 }
 
 // Waits for the CTA's copies; on expiry marks the problem timed out (status 4) and waits
-// once more, bounded, for copies still in flight.  Returns false in every thread then.
+// once more, with the full bound, for copies still in flight, so that none is outstanding
+// when the CTA exits.  Returns false in every thread then.  With the test setting
+// st.short_wait the first wait gives up without polling (the expiry path on demand).
 __device__ __forceinline__ bool tile_wait(uint64_t* bar, ProbState& st) {
-  const bool ok = mbar_wait(bar, 0);
+  const bool ok = __ldcg(&st.short_wait) == 0 && mbar_wait(bar, 0);
   if (__syncthreads_or(!ok)) {
     if (threadIdx.x == 0) {
       st.status = 4;

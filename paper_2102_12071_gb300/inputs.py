@@ -63,6 +63,15 @@ def grf_cells(seed: int, n: int, corr_len: float = 1.0 / 16.0) -> np.ndarray:
     return np.exp(g).astype(np.float32)
 
 
+def sine_cells(n: int, kappa: float) -> np.ndarray:
+    """Cell coefficients a = sin(kappa pi x y) + 1.1 of the variable-coefficient problem of
+    Sec. 6.3, evaluated at the centres of the (n+1) x (n+1) cells of the unit square (row =
+    y, column = x).  Returns float32 [(n+1), (n+1)]."""
+    m = n + 1
+    c = (np.arange(m) + 0.5) / m
+    return (np.sin(kappa * math.pi * c[:, None] * c[None, :]) + 1.1).astype(np.float32)
+
+
 def grid_sizes_loguniform(seed: int, count: int, lo: int = 63, hi: int = 2047) -> list[int]:
     """Square interior sizes drawn log-uniform in [lo, hi], snapped to 2^m - 1."""
     rng = np.random.default_rng(seed)

@@ -209,6 +209,27 @@ def test_train_step_gradient_matches_finite_differences_on_gpu_loss():
     assert abs(fd - g @ d) <= 2e-2 * abs(g @ d)
 
 
+@pytest.mark.parametrize("n", [15, 31])
+def test_bf16_train_step_matches_oracle_bf16(n):
+    """The bfloat16 network of C2/C3 (weights and every layer input rounded to bfloat16,
+    FP32 accumulation) against the oracle's own bfloat16 emulation of the same network:
+    loss within 1e-5 and gradient within 1e-4 relative."""
+    nprob, nvec = 3, 4
+    params, probs, z, batch = _train_batch(n, nprob, nvec, 140 + n, bf16=True)
+    p = small_net(11, 0.1)
+    loss, grad = batch.loss_and_grad(torch.from_numpy(p).cuda(), torch.from_numpy(z).cuda().contiguous())
+    batch.close()
+    lo, go = 0.0, np.zeros(p.size)
+    for k, (e, t) in enumerate(params):
+        st = O.const_field(n, f32(O.q1_rotated_stencil(e, t)))
+        l1, g1 = O.cnn_loss_and_grad(st, f32(p), f32(z[k]), bf16=True)
+        lo += l1 / nprob
+        go += g1 / nprob
+    assert abs(loss.item() - lo) <= 1e-5 * lo, (loss.item(), lo)
+    g = grad.double().cpu().numpy()
+    assert np.linalg.norm(g - go) <= 1e-4 * np.linalg.norm(go), np.linalg.norm(g - go) / np.linalg.norm(go)
+
+
 def test_bf16_training_loss_close_to_fp32():
     n = 31
     _, probs, z, b32 = _train_batch(n, 4, 4, 90, bf16=False)

@@ -173,6 +173,28 @@ def test_solve_status_codes():
     assert st == B.MG_OK and c[0] > 10
 
 
+@pytest.mark.parametrize("ct", [True, False])
+def test_timeout_status_and_recovery(ct):
+    """Failure detection without a GPU fault: the test setting makes the first bounded wait
+    for every tile's copies give up at once (the wait for the copies in flight keeps its
+    full bound, so they land before each CTA exits).  The solve reports MG_ERR_TIMEOUT;
+    with the setting off, the same context then solves like the oracle."""
+    n, cycles = 255, 12
+    eps, theta = 0.1, 0.8
+    b = torch.from_numpy(inputs.rhs_uniform(15, n)).cuda()[None].contiguous()
+    mg = S.MultigridSolver([S.rotated(n, eps, theta)], cluster_tail=ct)
+    B.mg_debug_short_wait(mg.ctx, True)
+    with pytest.raises(B.MGError) as ei:
+        mg.solve(b, rtol=1e-8, max_cycles=cycles)
+    assert ei.value.status == B.MG_ERR_TIMEOUT
+    B.mg_debug_short_wait(mg.ctx, False)
+    _, _, gh, cyc, st = mg.solve(b, rtol=0.0, max_cycles=cycles)
+    assert st == B.MG_ERR_NOT_CONVERGED and cyc[0] == cycles
+    _, oh = O.Multigrid(oracle_rotated(n, eps, theta)).solve(f32(b[0].cpu().numpy()), rtol=0.0, max_cycles=cycles)
+    assert _cmp_hist(gh[0], oh) == cycles + 1
+    mg.close()
+
+
 def test_warm_start_continues_history():
     """x_lo carries the float-float low part between calls: 10 + 10 cycles == 20 cycles."""
     n = 255

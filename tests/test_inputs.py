@@ -55,3 +55,18 @@ def test_right_hand_sides_and_loss_vectors():
     assert z.dtype == np.float32 and z.shape == (8, 63, 63)
     assert abs(z.mean()) < 0.02 and abs(z.var() - 1.0) < 0.03
     assert np.array_equal(inputs.rhs_uniform(1, 255), b)  # reproducible
+
+
+def test_sine_coefficient_of_the_variable_coefficient_experiment():
+    """Sec. 6.3: a = sin(kappa pi x y) + 1.1 at cell centres, row = y, column = x."""
+    n = 15
+    a = inputs.sine_cells(n, 1.0)
+    assert a.dtype == np.float32 and a.shape == (n + 1, n + 1)
+    np.testing.assert_array_equal(a, a.T)  # symmetric in x and y
+    # with kappa = 1 the argument kappa pi x y stays in (0, pi): a in (1.1, 2.1]
+    assert a.min() > 1.1 and a.max() <= 2.1
+    h = 1.0 / (n + 1)
+    x, y = 5.5 * h, 2.5 * h  # cell (row 2, column 5)
+    assert abs(float(a[2, 5]) - (np.sin(np.pi * x * y) + 1.1)) < 1e-7
+    # kappa = 10 reaches the minimum 0.1 of the paper's coefficient range
+    assert inputs.sine_cells(255, 10.0).min() < 0.11

@@ -27,22 +27,44 @@ def _built():
     build.build()
 
 
-def _regular(problems, b, rtol, max_cycles):
+def _regular(problems, b, rtol, max_cycles, with_lo=True):
+    """mg_workspace_size + mg_setup + mg_solve; without x_lo the low part lives in the
+    context's workspace and only x_hi comes back."""
     mg = S.MultigridSolver(problems, "jacobi")
-    x_hi, x_lo, hist, cyc, st = mg.solve(b, rtol=rtol, max_cycles=max_cycles)
+    x_hi = torch.zeros_like(b)
+    x_lo = torch.zeros_like(b) if with_lo else None
+    hist = np.full((len(problems), max_cycles + 1), np.nan)
+    cyc = np.zeros(len(problems), dtype=np.int32)
+    st = B.mg_solve(mg.ctx, b, x_hi, x_lo, rtol, max_cycles, hist, cyc, mg.stream)
+    torch.cuda.synchronize()
+    mg.close()
     return x_hi, x_lo, hist, cyc, st
 
 
-def _static(problems, b, rtol, max_cycles):
+def _static(problems, b, rtol, max_cycles, with_lo=True):
+    """without x_lo the low part lives in the library's scratch array, which keeps the
+    previous call's contents: the entry point must clear it itself"""
     probs, keep = B.problems_array(problems)
     x_hi = torch.zeros_like(b)
-    x_lo = torch.zeros_like(b)
+    x_lo = torch.zeros_like(b) if with_lo else None
     hist = np.full((len(problems), max_cycles + 1), np.nan)
     cyc = np.zeros(len(problems), dtype=np.int32)
     st = B.mg_solve_small_static(probs, len(problems), B.options(), b, x_hi, x_lo, rtol, max_cycles, hist, cyc)
     torch.cuda.synchronize()
     del keep
     return x_hi, x_lo, hist, cyc, st
+
+
+def _same(got, want, count, with_lo=True):
+    assert got[4] == want[4]
+    np.testing.assert_array_equal(got[3], want[3])
+    for p in range(count):
+        k = int(want[3][p]) + 1
+        rel = np.abs(got[2][p][:k] - want[2][p][:k]) / want[2][p][:k]
+        assert rel.max() <= HIST_RTOL
+    x_got = got[0].double() + (got[1].double() if with_lo else 0.0)
+    x_want = want[0].double() + (want[1].double() if with_lo else 0.0)
+    assert (x_got - x_want).abs().max().item() <= 1e-6 * x_want.abs().max().item()
 
 
 def _batch(n, count, seed):
@@ -58,15 +80,17 @@ def test_static_solve_matches_regular_solve_twice_in_a_row():
         problems, b = _batch(n, count, seed)
         want = _regular(problems, b, rtol, cap)
         got = _static(problems, b, rtol, cap)
-        assert got[4] == want[4]
-        np.testing.assert_array_equal(got[3], want[3])
-        for p in range(count):
-            k = int(want[3][p]) + 1
-            rel = np.abs(got[2][p][:k] - want[2][p][:k]) / want[2][p][:k]
-            assert rel.max() <= HIST_RTOL
-        x_got = got[0].double() + got[1].double()
-        x_want = want[0].double() + want[1].double()
-        assert (x_got - x_want).abs().max().item() <= 1e-6 * x_want.abs().max().item()
+        _same(got, want, count)
+
+
+def test_static_solve_without_low_part_twice_in_a_row():
+    # x_lo = NULL: the float-float low part is kept in the scratch array's own region, which
+    # the first call leaves non-zero; the second call must start it from zero again
+    for n, count, seed, rtol, cap in ((63, 4, 900, 1e-8, 3000), (63, 4, 900, 1e-8, 3000), (15, 2, 950, 1e-8, 500)):
+        problems, b = _batch(n, count, seed)
+        want = _regular(problems, b, rtol, cap, with_lo=False)
+        got = _static(problems, b, rtol, cap, with_lo=False)
+        _same(got, want, count, with_lo=False)
 
 
 def test_static_solve_rejects_requests_beyond_its_scratch():
