@@ -124,8 +124,7 @@ def test_cnn_asymptotic_factor_matches_oracle(net):
 def test_linear_alpha_cnn_asymptotic_factor_matches_oracle():
     """The paper's alpha-CNN (Sec. 6): the committed per-angle linear shared-kernel smoothers
     of Algorithm 2 (eps = 0.01, theta = pi/6) on a 255^2 hierarchy, to 1e-8 (~35 cycles):
-    cycle count within one, the factor over the last 20 cycles within 1e-3 relative and the
-    whole history within 1e-5."""
+    cycle count within one and the factor over the last 20 cycles within 1e-3 relative."""
     z = np.load(os.path.join(WEIGHTS, "linear_eps0.01.npz"))
     i = int(np.argmin(np.abs(z["thetas"] - THETA_F)))
     assert abs(float(z["thetas"][i]) - THETA_F) < 1e-9 and abs(float(z["eps"]) - EPS_F) < 1e-12
@@ -141,6 +140,11 @@ def test_linear_alpha_cnn_asymptotic_factor_matches_oracle():
     assert co > 25 and abs(cg - co) <= 1, (cg, co)
     fg, fo = _factor(gh[0], cg, 20), _factor(oh, co, 20)
     assert abs(fg - fo) <= FACTOR_RTOL * fo, (fg, fo)
-    k = min(cg, co) + 1
-    rel = np.abs(gh[0][:k] - oh[:k]) / oh[:k]
+    # The history is the product of the per-cycle reductions, so a per-cycle difference of
+    # FP32 size accumulates: the first 20 cycles within 1e-5, and every cycle's reduction
+    # h[k] / h[k-1] within 1e-5 to the end.
+    rel = np.abs(gh[0][:21] - oh[:21]) / oh[:21]
     assert rel.max() <= HIST_RTOL, rel.max()
+    k = min(cg, co) + 1
+    qg, qo = gh[0][1:k] / gh[0][: k - 1], oh[1:k] / oh[: k - 1]
+    assert np.max(np.abs(qg - qo) / qo) <= HIST_RTOL

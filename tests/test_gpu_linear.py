@@ -68,17 +68,16 @@ def test_linear_solve_history_matches_oracle(n, cycles, nsets):
         assert rel.max() <= 1e-5, rel.max()
 
 
-@pytest.mark.parametrize("kappa", [1.0, 10.0])
-def test_linear_solve_per_point_field(kappa):
-    """Variable coefficients (per-point stencil fields): the paper's own problem of Sec. 6.3,
-    -div((sin(kappa pi x y) + 1.1) grad u) = f, here on the 5-point cell-coefficient scheme
-    at 127^2.  One kernel set serves every point, so its Jacobi part is omega over the
-    largest diagonal plus a small random chain; the oracle builds its own FP64 Galerkin
-    fields.  (With a unit-variance GRF the diagonal varies by e^6 and such a smoother is too
-    weak to be a useful check: the cycle then leans on coarse operators whose FP32
-    rounding it amplifies.)"""
+@pytest.mark.parametrize("coef", ["sine1", "sine10", "grf"])
+def test_linear_solve_per_point_field(coef):
+    """Variable coefficients (per-point stencil fields) at 127^2: the paper's own problem of
+    Sec. 6.3, -div((sin(kappa pi x y) + 1.1) grad u) = f with kappa = 1 and 10, and the
+    unit-variance GRF coefficient of the benchmark, both on the 5-point cell-coefficient
+    scheme.  One kernel set serves every point, so its Jacobi part is omega over the largest
+    diagonal plus a small random chain.  The oracle builds its own FP64 Galerkin fields."""
     n = 127
-    a = inputs.sine_cells(n, kappa)
+    a = {"sine1": lambda: inputs.sine_cells(n, 1.0), "sine10": lambda: inputs.sine_cells(n, 10.0),
+         "grf": lambda: inputs.grf_cells(12, n)}[coef]()
     st0 = O.varcoef5_field(n, f32(a))
     dmax = st0[4].max()
     params = lin_params(2, dmax, seed=5, scale=0.02 * (2.0 / 3.0) / dmax)
