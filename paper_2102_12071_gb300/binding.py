@@ -16,6 +16,9 @@ MG_OK, MG_ERR_INVALID_ARG, MG_ERR_WORKSPACE, MG_ERR_CUDA, MG_ERR_NOT_CONVERGED, 
     MG_ERR_TIMEOUT, MG_ERR_UNSUPPORTED = range(8)
 MG_PROBLEM_ROTATED, MG_PROBLEM_STENCIL, MG_PROBLEM_VARCOEF5, MG_PROBLEM_FIELD = range(4)
 MG_SMOOTH_JACOBI, MG_SMOOTH_CNN = 0, 1
+MG_TILE_DEFAULT, MG_TILE_32x32, MG_TILE_STRIP4x32, MG_TILE_STRIP8x64, MG_TILE_STRIP8x32 = range(5)
+TILE_SHAPES = {"32x32": MG_TILE_32x32, "strip4x32": MG_TILE_STRIP4x32, "strip8x64": MG_TILE_STRIP8x64,
+               "strip8x32": MG_TILE_STRIP8x32}
 
 
 class mg_problem(ctypes.Structure):
@@ -28,7 +31,7 @@ class mg_options(ctypes.Structure):
                 ("omega", ctypes.c_float), ("coarsest_n", ctypes.c_int), ("conv_bf16", ctypes.c_int),
                 ("cluster_tail", ctypes.c_int), ("train_cycles", ctypes.c_int), ("train_checkpoint", ctypes.c_int),
                 ("net_levels", ctypes.c_int), ("smoother_transpose", ctypes.c_int), ("net_arch", ctypes.c_int),
-                ("net_per_problem", ctypes.c_int)]
+                ("net_per_problem", ctypes.c_int), ("tile_shape", ctypes.c_int)]
 
 
 class MGError(RuntimeError):
@@ -142,9 +145,9 @@ def problems_array(problems: list[dict]):
 def options(smoother: int = MG_SMOOTH_JACOBI, omega: float = 2.0 / 3.0, coarsest_n: int = 3,
             conv_bf16: int = 0, cluster_tail: int = 1, train_cycles: int = 1, train_checkpoint: int = 0,
             net_levels: int = 0, smoother_transpose: int = 0, net_arch: int = 0,
-            net_per_problem: int = 0, nu1: int = 1, nu2: int = 1) -> mg_options:
+            net_per_problem: int = 0, nu1: int = 1, nu2: int = 1, tile_shape: int = 0) -> mg_options:
     return mg_options(smoother, nu1, nu2, omega, coarsest_n, conv_bf16, cluster_tail, train_cycles, train_checkpoint,
-                      net_levels, smoother_transpose, net_arch, net_per_problem)
+                      net_levels, smoother_transpose, net_arch, net_per_problem, tile_shape)
 
 
 def mg_workspace_size(probs, nprob: int, opts: mg_options) -> int:

@@ -51,6 +51,7 @@ struct Plan {
   int generic = 0;  // levels above the tail in batched level kernels (mg_linear.cu)
   int nu1 = 1, nu2 = 1;
   int lstar1 = 0;   // first level of the one-CTA tail (the fallback of the cluster tail)
+  int shape = MG_SHAPE_STRIP8x32;  // layout of the tiled level kernels
   int nl[MG_MAXL] = {0};
   int ntiles_max = 0;
   size_t bytes = 0;
@@ -77,6 +78,9 @@ mg_status make_plan(const mg_problem* probs, int nprob, const mg_options* o, Pla
   if (o->smoother == MG_SMOOTH_CNN && o->net_arch == MG_NET_CONV3 && (o->smoother_transpose || o->conv_bf16))
     return fail(MG_ERR_UNSUPPORTED, "the three-kernel network runs in FP32 and without smoother_transpose");
   if (o->net_per_problem != 0 && o->net_per_problem != 1) return fail(MG_ERR_INVALID_ARG, "net_per_problem must be 0 or 1");
+  if (o->tile_shape < MG_TILE_DEFAULT || o->tile_shape > MG_TILE_STRIP8x32)
+    return fail(MG_ERR_INVALID_ARG, "unknown tile_shape %d", o->tile_shape);
+  P.shape = o->tile_shape == MG_TILE_DEFAULT ? MG_SHAPE_STRIP8x32 : o->tile_shape;
   if (o->net_per_problem && !(o->smoother == MG_SMOOTH_CNN && o->net_arch == MG_NET_LINEAR))
     return fail(MG_ERR_UNSUPPORTED, "per-problem parameter sets need the linear smoother (MG_NET_LINEAR)");
   const int n = probs[0].n;
@@ -446,7 +450,8 @@ mg_status mg_setup(const mg_problem* problems, int nprob, const mg_options* opts
     delete ctx;
     return fail(MG_ERR_CUDA, "cudaMallocHost of %d control blocks failed", P.nprob);
   }
-  if (P.lstar > 0 && !build_tile_maps(ctx->maps, ctx->arrays, P.nprob, P.lstar)) {
+  a.shape = P.shape;
+  if (P.lstar > 0 && !build_tile_maps(ctx->maps, ctx->arrays, P.nprob, P.lstar, P.shape)) {
     delete ctx;
     return fail(MG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the level arrays");
   }

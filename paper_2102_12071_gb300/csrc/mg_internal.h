@@ -89,6 +89,10 @@ struct TileMaps {
   Up0Maps up0;
   CUtensorMap down0_rb, up0_rb;  // level-0 residual loads of odd cycles (from r0b)
   ResMaps resb;                  // x loads of odd cycles (from xh0b, xl0b)
+  // strip layouts (mg_strip.cu): the down-sweep's r block of each tiled level, and level
+  // 0's from r0b on odd cycles
+  CUtensorMap sr[MG_MAXL];
+  CUtensorMap sr0b;
 };
 
 // base pointers of the pitched level arrays (all problems of a level contiguous)
@@ -144,6 +148,7 @@ struct CycleArgs {
   int generic;                    // levels above the tail on the batched level path (mg_linear.cu):
                                   // the linear smoother, the kernel stack, or nu other than 1
   int short_wait;                 // test setting copied into the control blocks by launch_bnorm
+  int shape;                      // layout of the tiled level kernels (MG_SHAPE_*)
 };
 
 
@@ -195,7 +200,11 @@ cudaError_t launch_residual(const CycleArgs& a, float rtol, int max_cycles);
 // r0b, (xh0b, xl0b) (1) and writes the new ones to the other arrays: the fused level-0
 // kernel reads both with halos, so it must not overwrite them in place
 cudaError_t launch_cycle(const CycleArgs& a, float rtol, int max_cycles, int parity);
-bool build_tile_maps(TileMaps& maps, const LevelArrays& arrays, int nprob, int lstar);
+bool build_tile_maps(TileMaps& maps, const LevelArrays& arrays, int nprob, int lstar, int shape);
+// strip layouts (mg_strip.cu): the r block (box) of the down-sweep, and its launch on level
+// l for np problems with the tensor map m of that level's r array
+void strip_box(int shape, int* bw, int* bh);
+cudaError_t launch_sdown(const CycleArgs& a, const CUtensorMap& m, int l, int np);
 // level 0 after an up-sweep run elsewhere: x += e_0 and the residual of the new iterate
 // with the stopping test, on the arrays of cycle `parity` (mg_tiles.cu); e0: tensor map of
 // e_0 with the iterate's box (tile_res_box)

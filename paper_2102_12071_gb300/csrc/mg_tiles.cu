@@ -718,8 +718,15 @@ bool make_map(CUtensorMap* m, float* base, int n, int pitch, int nprob, int bw, 
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool build_tile_maps(TileMaps& T, const LevelArrays& A, int nprob, int lstar) {
+bool build_tile_maps(TileMaps& T, const LevelArrays& A, int nprob, int lstar, int shape) {
   if (lstar == 0) return true;
+  if (shape != MG_SHAPE_TILE32) {
+    int bw, bh;
+    strip_box(shape, &bw, &bh);
+    for (int l = 0; l < lstar; ++l)
+      if (!make_map(&T.sr[l], A.r[l], A.n[l], A.pitch[l], nprob, bw, bh)) return false;
+    if (!make_map(&T.sr0b, A.r0b, A.n[0], A.pitch[0], nprob, bw, bh)) return false;
+  }
   bool ok = make_map(&T.res.xh, A.xh0, A.n[0], A.pitch[0], nprob, XW, RES_H) &&
             make_map(&T.res.xl, A.xl0, A.n[0], A.pitch[0], nprob, XW, RES_H) &&
             make_map(&T.res.b, A.b0, A.n[0], A.pitch[0], nprob, TB, TB);
@@ -802,11 +809,15 @@ cudaError_t launch_cycle(const CycleArgs& a, float rtol, int max_cycles, int par
     dim3 grid(nt * nt, np);
     a.prof->launches++;
     a.prof->begin(l == 0 ? PK_DOWN0 : PK_DOWN, a.stream);
-    DownMaps dm = a.maps->down[l];
-    if (l == 0 && parity) dm.r = a.maps->down0_rb;
-    MG_DISPATCH(a.sk, a.hk,
-                (e = launch_pdl(a.pdl, k_down<SK_, HK_>, grid, dim3(NT), 0, a.stream, dm, probs, a.state, l, a.omega,
-                                a.active)));
+    if (a.shape != MG_SHAPE_TILE32) {
+      e = launch_sdown(a, (l == 0 && parity) ? a.maps->sr0b : a.maps->sr[l], l, np);
+    } else {
+      DownMaps dm = a.maps->down[l];
+      if (l == 0 && parity) dm.r = a.maps->down0_rb;
+      MG_DISPATCH(a.sk, a.hk,
+                  (e = launch_pdl(a.pdl, k_down<SK_, HK_>, grid, dim3(NT), 0, a.stream, dm, probs, a.state, l,
+                                  a.omega, a.active)));
+    }
     a.prof->end(a.stream);
   }
   if (e != cudaSuccess) return e;

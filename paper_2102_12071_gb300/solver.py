@@ -43,7 +43,7 @@ class MultigridSolver:
     def __init__(self, problems: list[dict], smoother: str = "jacobi", net_params: torch.Tensor | None = None,
                  omega: float = 2.0 / 3.0, conv_bf16: bool = False, coarsest_n: int = 3, device="cuda",
                  stream=None, cluster_tail: bool = True, transpose: bool = False, net_arch: str = "conv",
-                 per_problem: bool = False, nu1: int = 1, nu2: int = 1):
+                 per_problem: bool = False, nu1: int = 1, nu2: int = 1, tile_shape: str | int = 0):
         """net_params: one parameter set [nparams] for every level, or per-level sets
         [k, nparams] (level l uses set min(l, k - 1)).  transpose: smooth with H^T (per-point
         problems), so that a V-cycle applies the transpose of the cycle without it.
@@ -53,7 +53,9 @@ class MultigridSolver:
         kernels per level, [54] or [k, 54]; with per_problem, one group of k sets per
         problem, [nprob, k, 54], as Sec. 6 trains one smoother per problem).  nu1, nu2:
         smoothing steps before / after the coarse correction (> 1 for Jacobi and the linear
-        smoother; the paper's cost-equalised Jacobi runs six)."""
+        smoother; the paper's cost-equalised Jacobi runs six).  tile_shape: layout of the
+        kernels of the levels above the coarse tail, a name of binding.TILE_SHAPES or 0 for
+        the library's default; it changes speed, not the cycle."""
         self.nprob = len(problems)
         self.n = problems[0]["n"]
         self.device = torch.device(device)
@@ -72,8 +74,9 @@ class MultigridSolver:
         else:
             net_levels = int(net_params.shape[0]) if net_params is not None and net_params.dim() == 2 else 0
         arch = net_arch_code(net_arch)
+        shape = B.TILE_SHAPES[tile_shape] if isinstance(tile_shape, str) else int(tile_shape)
         self.opts = B.options(kind, omega, coarsest_n, int(conv_bf16), int(cluster_tail), 1, 0, net_levels,
-                              int(transpose), arch, int(per_problem), int(nu1), int(nu2))
+                              int(transpose), arch, int(per_problem), int(nu1), int(nu2), shape)
         size = B.mg_workspace_size(self._probs, self.nprob, self.opts)
         if size == 0:
             raise B.MGError(B.MG_ERR_INVALID_ARG, "mg_workspace_size", B.lib().mg_last_error().decode())
