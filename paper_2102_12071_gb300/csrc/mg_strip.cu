@@ -101,11 +101,81 @@ __device__ __forceinline__ float strip_H(const LevelDev& L, const float (&s)[9],
 }
 
 // ---------------------------------------------------------------------- k_sdown
-// Box row q holds grid row R0 - 2 + q.  Walking q = 0 .. BH-1, the warp forms e = H r on
+// Box row q holds grid row R0 - 2 + q.  Walking q = 2 .. BH-1, the warp forms e = H r on
 // box row q-1 (grid rows R0-1 .. R0+H+1), s = r - A e on box row q-2 (R0 .. R0+H) and the
 // column sums v = s/2 + s + s/2 of the restriction over fine rows 2I+2, 2I+3, 2I+4 of box
 // coordinates; at each coarse row it finishes P^T s with the row sums of the neighbouring
 // lanes.  Correct values: e on lanes 1..30, s on 2..29, r_c on the odd lanes 3..27.
+// The walk is a loop over chunks of six rows (the periods of the three-row windows and of
+// the restriction's row parity), so the register windows rotate without copies and the
+// code stays small; MARGIN selects the variant for warps that touch points within
+// MG_NET_MARGIN of an edge (class-table kernels there).
+struct DownCtx {
+  float s[9], wi[9];
+  float omega;
+  int n, R0, j, nc, pitch, pc, Jc;
+  bool jin, own, cown, jmargin;
+  const float* col;
+  float* e_out;
+  float* rc_out;
+};
+
+template <int SK, int HK, int H, int BW, bool MARGIN>
+__device__ __forceinline__ void sdown_walk(const LevelDev& L, const DownCtx& c) {
+  constexpr int BH = H + 5;
+  Row3 ra = row3(c.col[0]), rb = row3(c.col[BW]);  // r on box rows q-2, q-1
+  Row3 ea, eb;                                       // e on box rows q-3, q-2
+  ea.l = ea.c = ea.r = 0.f;
+  eb = ea;
+  float v = 0.f;  // column sum of the current coarse row
+#pragma unroll 1
+  for (int q0 = 2; q0 < BH; q0 += 6) {
+#pragma unroll
+    for (int u = 0; u < 6; ++u) {
+      const int q = q0 + u;
+      if (q < BH) {
+        const Row3 rc = row3(c.col[q * BW]);
+        const int ie = c.R0 + q - 3;  // e on box row q-1
+        float e = 0.f;
+        if (c.jin && (unsigned)ie < (unsigned)c.n) {
+          const bool margin = MARGIN && (c.jmargin || ie < MG_NET_MARGIN || ie >= c.n - MG_NET_MARGIN);
+          e = strip_H<SK, HK>(L, c.s, c.wi, c.omega, ie, c.j, margin, ra, rb, rc);
+        }
+        const Row3 ec = row3(e);
+        if (q >= 3 && q < H + 3 && c.own && ie < c.n) c.e_out[(size_t)ie * c.pitch + c.j] = e;
+        if (q >= 4) {
+          const int is = c.R0 + q - 4;  // s on box row q-2 (needed inside the grid only)
+          float sv = 0.f;
+          if (c.jin && is < c.n) {
+            float a[9];
+            stencil_at<SK>(L, c.s, is, c.j, a);
+            sv = ra.c - dot9r(a, ea, eb, ec);
+          }
+          // box row qs = q-2 is fine row 2I+2 (even: ends coarse row I-1, starts I) or 2I+3
+          // (odd: centre of I) of the CTA's coarse rows I = 0 .. H/2-1; q0 - 2 is a
+          // multiple of 6, so the parity of qs is that of u
+          const int qs = q - 2;
+          if ((u & 1) == 0) {
+            if (qs >= 4) {
+              v = fmaf(0.5f, sv, v);
+              const float rcv = fmaf(0.5f, __shfl_up_sync(0xffffffffu, v, 1) + __shfl_down_sync(0xffffffffu, v, 1), v);
+              const int Ic = (c.R0 >> 1) + ((qs - 4) >> 1);
+              if (c.cown && Ic < c.nc) c.rc_out[(size_t)Ic * c.pc + c.Jc] = rcv;
+            }
+            v = 0.5f * sv;
+          } else {
+            v += sv;
+          }
+        }
+        ra = rb;
+        rb = rc;
+        ea = eb;
+        eb = ec;
+      }
+    }
+  }
+}
+
 template <int SK, int HK, int WPC, int H>
 __global__ void __launch_bounds__(32 * WPC, Strip<WPC, H>::MINB) k_sdown(const __grid_constant__ CUtensorMap Mr,
                                                     const ProbDev* __restrict__ probs, ProbState* __restrict__ state,
@@ -120,17 +190,20 @@ __global__ void __launch_bounds__(32 * WPC, Strip<WPC, H>::MINB) k_sdown(const _
   const int R0 = ((int)blockIdx.x / ncx) * H, C0 = ((int)blockIdx.x % ncx) * G::CW;
   __shared__ __align__(128) float rs[G::BH * G::BW];
   __shared__ __align__(8) uint64_t bar;
-  float s[9], wi[9];
+  DownCtx c;
 #pragma unroll
-  for (int k = 0; k < 9; ++k) s[k] = (SK == SK_CONST) ? L.s[k] : 0.f;
-  if (HK == HK_TABLE) {
-    const int T = L.T, M = MG_NET_MARGIN;
+  for (int k = 0; k < 9; ++k) c.s[k] = (SK == SK_CONST) ? L.s[k] : 0.f;
+  const int T = L.T, M = MG_NET_MARGIN;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) wi[k] = T == MG_PROXY ? L.W[k * T * T + M * T + M] : 0.f;
-  }
-  float* const rc_out = probs[p].lv[l + 1].r;  // per-problem pitched arrays
-  const int nc = probs[p].lv[l + 1].n, pc = probs[p].lv[l + 1].pitch, pitch = L.pitch;
-  float* const e_out = L.e;
+  for (int k = 0; k < 9; ++k) c.wi[k] = (HK == HK_TABLE && T == MG_PROXY) ? L.W[k * T * T + M * T + M] : 0.f;
+  c.omega = omega;
+  c.n = n;
+  c.R0 = R0;
+  c.rc_out = probs[p].lv[l + 1].r;  // per-problem pitched arrays
+  c.nc = probs[p].lv[l + 1].n;
+  c.pc = probs[p].lv[l + 1].pitch;
+  c.pitch = L.pitch;
+  c.e_out = L.e;
   pdl_wait();
   if (!st_active(state + p)) return;
   if (threadIdx.x == 0) {
@@ -143,63 +216,20 @@ __global__ void __launch_bounds__(32 * WPC, Strip<WPC, H>::MINB) k_sdown(const _
   if (!tile_wait(&bar, state[p])) return;
 
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int c0 = C0 + SW * w;            // first owned column of the warp
-  const int j = c0 - 2 + lane;           // this lane's column
-  const bool jin = (unsigned)j < (unsigned)n;
-  const bool own = lane >= 2 && lane < 2 + SW && jin;
-  // points within MG_NET_MARGIN of the left or right edge take their kernel from the table
-  const bool jmargin = HK == HK_TABLE && (L.T != MG_PROXY || j < MG_NET_MARGIN || j >= n - MG_NET_MARGIN);
-  const float* col = rs + SW * w + 2 + lane;
+  const int c0 = C0 + SW * w;  // first owned column of the warp
+  c.j = c0 - 2 + lane;         // this lane's column
+  c.jin = (unsigned)c.j < (unsigned)n;
+  c.own = lane >= 2 && lane < 2 + SW && c.jin;
+  c.jmargin = T != MG_PROXY || c.j < M || c.j >= n - M;
+  c.col = rs + SW * w + 2 + lane;
   // coarse output of the odd lanes 3 .. 27: column c0/2 + (lane - 3)/2
-  const int Jc = (c0 >> 1) + ((lane - 3) >> 1);
-  const bool cown = (lane & 1) && lane >= 3 && lane <= 27 && Jc < nc;
-
-  Row3 ra = row3(col[0]), rb = row3(col[G::BW]);  // r on box rows q-2, q-1
-  Row3 ea, eb;                                     // e on box rows q-3, q-2
-  ea.l = ea.c = ea.r = 0.f;
-  eb = ea;
-  float v = 0.f;                                   // column sum of the current coarse row
-#pragma unroll
-  for (int q = 2; q < G::BH; ++q) {
-    const Row3 rc = row3(col[q * G::BW]);
-    // e on box row q-1 = grid row ie
-    const int ie = R0 + q - 3;
-    float e = 0.f;
-    if (jin && (unsigned)ie < (unsigned)n) {
-      const bool margin = HK == HK_TABLE && (jmargin || ie < MG_NET_MARGIN || ie >= n - MG_NET_MARGIN);
-      e = strip_H<SK, HK>(L, s, wi, omega, ie, j, margin, ra, rb, rc);
-    }
-    const Row3 ec = row3(e);
-    if (q >= 3 && q < H + 3 && own && ie < n) e_out[(size_t)ie * pitch + j] = e;
-    if (q >= 4) {
-      // s on box row q-2 = grid row is (needed inside the grid only)
-      const int is = R0 + q - 4;
-      float sv = 0.f;
-      if (jin && is < n) {
-        float a[9];
-        stencil_at<SK>(L, s, is, j, a);
-        sv = ra.c - dot9r(a, ea, eb, ec);
-      }
-      // restriction: box row qs = q-2 is fine row 2I+2 (even: ends coarse row I-1, starts
-      // I) or 2I+3 (odd: centre of I) of the CTA's coarse rows I = 0 .. H/2-1
-      const int qs = q - 2;
-      if ((qs & 1) == 0) {
-        if (qs >= 4) {
-          v = fmaf(0.5f, sv, v);
-          const float rcv = fmaf(0.5f, __shfl_up_sync(0xffffffffu, v, 1) + __shfl_down_sync(0xffffffffu, v, 1), v);
-          const int Ic = (R0 >> 1) + (qs - 4) / 2;
-          if (cown && Ic < nc) rc_out[(size_t)Ic * pc + Jc] = rcv;
-        }
-        v = 0.5f * sv;
-      } else {
-        v += sv;
-      }
-    }
-    ra = rb;
-    rb = rc;
-    ea = eb;
-    eb = ec;
-  }
+  c.Jc = (c0 >> 1) + ((lane - 3) >> 1);
+  c.cown = (lane & 1) && lane >= 3 && lane <= 27 && c.Jc < c.nc;
+  // a warp away from the edges (every point it evaluates at least M from them) uses the
+  // interior kernel throughout
+  const bool inner = T == MG_PROXY && c0 - 2 >= M && c0 + 29 < n - M && R0 - 1 >= M && R0 + H + 1 < n - M;
+  if (HK != HK_TABLE || inner) sdown_walk<SK, HK, H, G::BW, false>(L, c);
+  else sdown_walk<SK, HK, H, G::BW, true>(L, c);
 }
 
 // ---------------------------------------------------------------- launchers
