@@ -13,6 +13,7 @@
 
 #include "mg_common.cuh"
 #include "mg_internal.h"
+#include "mg_reduce.cuh"
 #include "mg_tile.cuh"
 #include "mg_tma.cuh"
 
@@ -128,7 +129,7 @@ __device__ __forceinline__ void sdown_walk(const LevelDev& L, const DownCtx& c) 
   ea.l = ea.c = ea.r = 0.f;
   eb = ea;
   float v = 0.f;  // column sum of the current coarse row
-#pragma unroll 1
+#pragma unroll
   for (int q0 = 2; q0 < BH; q0 += 6) {
 #pragma unroll
     for (int u = 0; u < 6; ++u) {
@@ -232,6 +233,232 @@ __global__ void __launch_bounds__(32 * WPC, Strip<WPC, H>::MINB) k_sdown(const _
   else sdown_walk<SK, HK, H, G::BW, true>(L, c);
 }
 
+// ------------------------------------------------------------------------ k_sup
+// Up-sweep of a tiled level (Algorithm 1, correction and post-smoothing): e1 = e + P e_c,
+// t = r - A e1, e = e1 + H t on the CTA's rows R0 .. R0+H-1.  Box row q holds grid row
+// R0 - 2 + q of e; walking q = 0 .. H+3 the warp forms e1 on box row q, t on q-1 (zero
+// outside the grid: H sees the Dirichlet exterior) and the final correction on q-2.  On
+// levels >= 1 that correction goes to the level's f array (other CTAs still read e with
+// halos); on level 0 (UPDX) it is added to the float-float iterate, read from (xin_hi,
+// xin_lo) and written to (xout_hi, xout_lo), the pair of the other cycle parity.
+// Prolongation: coarse point I sits at fine 2I+1, so fine row i interpolates coarse rows
+// (i-1)>>1 and i>>1: box rows q/2 and q/2+1 of the coarse block for even q, row q/2+1 for
+// odd q; hp holds the horizontal interpolation of a coarse row at the lane's column.
+struct UpCtx {
+  float s[9], wi[9];
+  float omega;
+  int n, R0, j, pitch;
+  bool jin, own, jmargin;
+  const float* col;    // e block, this lane's column
+  const float* ca;     // coarse block, column (j - 1) >> 1 of row 0
+  const float* cb;     // ... column j >> 1
+  const float* rin;    // r of this problem (pitched)
+  float* fout;         // levels >= 1: final correction
+  const float *xin_hi, *xin_lo;
+  float *xout_hi, *xout_lo;
+};
+
+template <int SK, int HK, int H, int BW, int CBW, bool UPDX, bool MARGIN>
+__device__ __forceinline__ void sup_walk(const LevelDev& L, const UpCtx& c) {
+  Row3 ea, eb;  // e1 on box rows q-2, q-1
+  Row3 ta, tb;  // t on box rows q-3, q-2
+  ea.l = ea.c = ea.r = 0.f;
+  eb = ea;
+  ta = ea;
+  tb = ea;
+  float hP = 0.5f * (c.ca[0] + c.cb[0]);  // coarse box row 0
+#pragma unroll
+  for (int q0 = 0; q0 < H + 4; q0 += 6) {
+#pragma unroll
+    for (int u = 0; u < 6; ++u) {
+      const int q = q0 + u;
+      if (q < H + 4) {
+        float pe;
+        if ((u & 1) == 0) {  // q0 is even, so q has the parity of u
+          const float hN = 0.5f * (c.ca[(q / 2 + 1) * CBW] + c.cb[(q / 2 + 1) * CBW]);
+          pe = 0.5f * (hP + hN);
+          hP = hN;
+        } else {
+          pe = hP;
+        }
+        const Row3 ec = row3(c.col[q * BW] + pe);  // e1 on box row q (zero outside the grid)
+        if (q >= 2) {
+          const int it = c.R0 + q - 3;  // t on box row q-1
+          float tv = 0.f;
+          if (c.jin && (unsigned)it < (unsigned)c.n) {
+            float a[9];
+            stencil_at<SK>(L, c.s, it, c.j, a);
+            tv = __ldg(c.rin + (size_t)it * c.pitch + c.j) - dot9r(a, ea, eb, ec);
+          }
+          const Row3 tc = row3(tv);
+          if (q >= 4) {
+            const int i = c.R0 + q - 4;  // final correction on box row q-2 (the CTA's rows)
+            if (c.own && i < c.n) {
+              const bool margin = MARGIN && (c.jmargin || i < MG_NET_MARGIN || i >= c.n - MG_NET_MARGIN);
+              const float e = ea.c + strip_H<SK, HK>(L, c.s, c.wi, c.omega, i, c.j, margin, ta, tb, tc);
+              const size_t g = (size_t)i * c.pitch + c.j;
+              if (UPDX) {
+                float hi = c.xin_hi[g], lo = c.xin_lo[g], sum, err;
+                two_sum(hi, e, sum, err);
+                err += lo;
+                fast_two_sum(sum, err, hi, lo);
+                c.xout_hi[g] = hi;
+                c.xout_lo[g] = lo;
+              } else {
+                c.fout[g] = e;
+              }
+            }
+          }
+          ta = tb;
+          tb = tc;
+        }
+        ea = eb;
+        eb = ec;
+      }
+    }
+  }
+}
+
+template <int SK, int HK, int WPC, int H, bool UPDX>
+__global__ void __launch_bounds__(32 * WPC, Strip<WPC, H>::MINB)
+    k_sup(const __grid_constant__ CUtensorMap Me, const __grid_constant__ CUtensorMap Mec,
+          const ProbDev* __restrict__ probs, ProbState* __restrict__ state, int l, float omega,
+          const float* rin_base, const float* xin_hi, const float* xin_lo, float* xout_hi, float* xout_lo,
+          const int* __restrict__ act) {
+  using G = Strip<WPC, H>;
+  constexpr int CBW = G::CW / 2 + 8;  // coarse block: columns C0/2-4 .. C0/2+CW/2+3
+  constexpr int CBH = H / 2 + 3;      //               rows    R0/2-2 .. R0/2+H/2
+  pdl_trigger();
+  const int p = act ? act[blockIdx.y] : blockIdx.y;
+  const LevelDev L = probs[p].lv[l];
+  const int n = L.n;
+  const int ncx = (n + G::CW - 1) / G::CW, ncy = (n + H - 1) / H;
+  if ((int)blockIdx.x >= ncx * ncy) return;
+  const int R0 = ((int)blockIdx.x / ncx) * H, C0 = ((int)blockIdx.x % ncx) * G::CW;
+  __shared__ __align__(128) float es[G::BH * G::BW];
+  __shared__ __align__(128) float ecs[CBH * CBW];
+  __shared__ __align__(8) uint64_t bar;
+  UpCtx c;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) c.s[k] = (SK == SK_CONST) ? L.s[k] : 0.f;
+  const int T = L.T, M = MG_NET_MARGIN;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) c.wi[k] = (HK == HK_TABLE && T == MG_PROXY) ? L.W[k * T * T + M * T + M] : 0.f;
+  c.omega = omega;
+  c.n = n;
+  c.R0 = R0;
+  c.pitch = L.pitch;
+  const size_t po = (size_t)p * n * L.pitch;  // problem offset in the level's batch arrays
+  c.rin = UPDX ? rin_base + po : L.r;
+  c.fout = L.f;
+  if (UPDX) {
+    c.xin_hi = xin_hi + po;
+    c.xin_lo = xin_lo + po;
+    c.xout_hi = xout_hi + po;
+    c.xout_lo = xout_lo + po;
+  }
+  pdl_wait();
+  if (!st_active(state + p)) return;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    mbar_arrive_expect_tx(&bar, (G::BH * G::BW + CBH * CBW) * sizeof(float));
+    tma_load_3d(es, &Me, &bar, C0 - 4, R0 - 2, p);
+    tma_load_3d(ecs, &Mec, &bar, C0 / 2 - 4, R0 / 2 - 2, p);
+  }
+  __syncthreads();
+  if (!tile_wait(&bar, state[p])) return;
+
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int c0 = C0 + SW * w;
+  c.j = c0 - 2 + lane;
+  c.jin = (unsigned)c.j < (unsigned)n;
+  c.own = lane >= 2 && lane < 2 + SW && c.jin;
+  c.jmargin = T != MG_PROXY || c.j < M || c.j >= n - M;
+  c.col = es + SW * w + 2 + lane;
+  c.ca = ecs + (SW / 2) * w + ((lane - 3) >> 1) + 4;  // coarse column (j - 1) >> 1
+  c.cb = ecs + (SW / 2) * w + ((lane - 2) >> 1) + 4;  // coarse column j >> 1
+  const bool inner = T == MG_PROXY && c0 >= M && c0 + SW <= n - M && R0 >= M && R0 + H <= n - M;
+  if (HK != HK_TABLE || inner) sup_walk<SK, HK, H, G::BW, CBW, UPDX, false>(L, c);
+  else sup_walk<SK, HK, H, G::BW, CBW, UPDX, true>(L, c);
+}
+
+// ----------------------------------------------------------------------- k_sres
+// Residual of the float-float iterate, r = b - A (x_hi + x_lo) (Dot2: exact products and
+// sums for x_hi, plain FP32 for the x_lo terms), its norm partial per CTA and, in the last
+// CTA of a problem, the stopping test.  A warp owns 30 columns (lane k holds column
+// c0 - 1 + k) and walks the rows R0-1 .. R0+H of x; x and b come straight from global
+// memory, one coalesced row per load.
+template <int SK, int WPC, int H>
+__global__ void __launch_bounds__(32 * WPC, Strip<WPC, H>::MINB)
+    k_sres(const ProbDev* __restrict__ probs, ProbState* __restrict__ state, float* __restrict__ partials,
+           int ntiles_max, float rtol, int max_cycles, const float* __restrict__ xh_base,
+           const float* __restrict__ xl_base, const float* __restrict__ b_base, float* __restrict__ r_base,
+           const int* __restrict__ act) {
+  constexpr int NT = 32 * WPC, RW = 30, CW = RW * WPC;
+  pdl_trigger();
+  const int p = act ? act[blockIdx.y] : blockIdx.y;
+  const int n = probs[p].lv[0].n, pitch = probs[p].lv[0].pitch;
+  const int ncx = (n + CW - 1) / CW, ncy = (n + H - 1) / H, ntiles = ncx * ncy;
+  const int tile = blockIdx.x;
+  if (tile >= ntiles) return;
+  const int R0 = (tile / ncx) * H, C0 = (tile % ncx) * CW;
+  float s[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) s[k] = (SK == SK_CONST) ? probs[p].lv[0].s[k] : 0.f;
+  const LevelDev& L = probs[p].lv[0];
+  const size_t po = (size_t)p * n * pitch;
+  const float* xh = xh_base + po;
+  const float* xl = xl_base + po;
+  const float* bb = b_base + po;
+  float* rr = r_base + po;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int j = C0 + RW * w - 1 + lane;
+  const bool jin = (unsigned)j < (unsigned)n;
+  const bool own = lane >= 1 && lane < 1 + RW && jin;
+  pdl_wait();
+  if (!st_active(state + p)) return;
+  auto ld = [&](const float* a, int i) { return (jin && (unsigned)i < (unsigned)n) ? a[(size_t)i * pitch + j] : 0.f; };
+  Row3 ha = row3(ld(xh, R0 - 1)), la = row3(ld(xl, R0 - 1));  // rows i-1 and i of x
+  Row3 hb = row3(ld(xh, R0)), lb = row3(ld(xl, R0));
+  float acc = 0.f;
+#pragma unroll
+  for (int q0 = 0; q0 < H; q0 += 3) {
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const int q = q0 + u, i = R0 + q;  // residual on grid row i
+      if (q < H) {
+        const Row3 hc = row3(ld(xh, i + 1)), lc = row3(ld(xl, i + 1));
+        if (own && i < n) {
+          float a[9];
+          stencil_at<SK>(L, s, i, j, a);
+          float hi = bb[(size_t)i * pitch + j], lo = 0.f;
+          dot2_sub(a[0], ha.l, la.l, hi, lo);
+          dot2_sub(a[1], ha.c, la.c, hi, lo);
+          dot2_sub(a[2], ha.r, la.r, hi, lo);
+          dot2_sub(a[3], hb.l, lb.l, hi, lo);
+          dot2_sub(a[4], hb.c, lb.c, hi, lo);
+          dot2_sub(a[5], hb.r, lb.r, hi, lo);
+          dot2_sub(a[6], hc.l, lc.l, hi, lo);
+          dot2_sub(a[7], hc.c, lc.c, hi, lo);
+          dot2_sub(a[8], hc.r, lc.r, hi, lo);
+          const float r = hi + lo;
+          rr[(size_t)i * pitch + j] = r;
+          acc = fmaf(r, r, acc);
+        }
+        ha = hb;
+        la = lb;
+        hb = hc;
+        lb = lc;
+      }
+    }
+  }
+  float rhi, rlo;
+  if (block_partial_and_last<NT>(acc, partials + (size_t)p * ntiles_max, &state[p].counter, ntiles, tile, rhi, rlo)) {
+    if (threadIdx.x == 0) decide(state[p], rhi, rlo, rtol, max_cycles);
+  }
+}
+
 // ---------------------------------------------------------------- launchers
 template <int WPC, int H>
 static cudaError_t sdown_shape(const CycleArgs& a, const CUtensorMap& m, int l, dim3 grid) {
@@ -256,6 +483,76 @@ static void strip_cta(int shape, int* cw, int* h) {
     case MG_SHAPE_STRIP4x32: *cw = Strip<4, 32>::CW; *h = 32; return;
     case MG_SHAPE_STRIP8x64: *cw = Strip<8, 64>::CW; *h = 64; return;
     default: *cw = Strip<8, 32>::CW; *h = 32; return;
+  }
+}
+
+template <int WPC, int H>
+static cudaError_t sup_shape(const CycleArgs& a, int l, int parity, dim3 grid) {
+  using G = Strip<WPC, H>;
+  // the kernel after the cluster tail waits for it by plain stream order (the tail's
+  // clusters hold whole SMs; starting early buys nothing there)
+  const bool pdl = a.pdl && !(a.ctail && l == a.lstar - 1);
+  const CUtensorMap& me = a.maps->se[l];
+  const CUtensorMap& mec = a.maps->sec[l];
+  const ProbDev* probs = a.probs;
+  cudaError_t e = cudaSuccess;
+  if (l == 0) {
+    const float* rin = parity ? a.r0b : a.r0a;
+    const float* xih = parity ? a.xh0b : a.xh0;
+    const float* xil = parity ? a.xl0b : a.xl0;
+    float* xoh = parity ? a.xh0 : a.xh0b;
+    float* xol = parity ? a.xl0 : a.xl0b;
+    MG_DISPATCH(a.sk, a.hk,
+                (e = launch_pdl(pdl, k_sup<SK_, HK_, WPC, H, true>, grid, dim3(G::NT), 0, a.stream, me, mec, probs,
+                                a.state, l, a.omega, rin, xih, xil, xoh, xol, a.active)));
+  } else {
+    const float* nulc = nullptr;
+    float* nul = nullptr;
+    MG_DISPATCH(a.sk, a.hk,
+                (e = launch_pdl(pdl, k_sup<SK_, HK_, WPC, H, false>, grid, dim3(G::NT), 0, a.stream, me, mec, probs,
+                                a.state, l, a.omega, nulc, nulc, nulc, nul, nul, a.active)));
+  }
+  return e;
+}
+
+template <int WPC, int H>
+static cudaError_t sres_shape(const CycleArgs& a, const float* xh, const float* xl, float* r, float rtol,
+                              int max_cycles, int np) {
+  constexpr int CW = 30 * WPC;
+  const int n = a.n0;
+  const dim3 grid(((n + CW - 1) / CW) * ((n + H - 1) / H), np);
+  if (a.sk == SK_CONST)
+    return launch_pdl(a.pdl, k_sres<SK_CONST, WPC, H>, grid, dim3(32 * WPC), 0, a.stream, (const ProbDev*)a.probs,
+                      a.state, a.partials, a.ntiles_max, rtol, max_cycles, xh, xl, a.b0, r, a.active);
+  return launch_pdl(a.pdl, k_sres<SK_FIELD, WPC, H>, grid, dim3(32 * WPC), 0, a.stream, (const ProbDev*)a.probs,
+                    a.state, a.partials, a.ntiles_max, rtol, max_cycles, xh, xl, a.b0, r, a.active);
+}
+
+void strip_coarse_box(int shape, int* bw, int* bh) {
+  int cw, h;
+  strip_cta(shape, &cw, &h);
+  *bw = cw / 2 + 8;
+  *bh = h / 2 + 3;
+}
+
+cudaError_t launch_sup(const CycleArgs& a, int l, int parity, int np) {
+  int cw, h;
+  strip_cta(a.shape, &cw, &h);
+  const int n = a.nl[l];
+  const dim3 grid(((n + cw - 1) / cw) * ((n + h - 1) / h), np);
+  switch (a.shape) {
+    case MG_SHAPE_STRIP4x32: return sup_shape<4, 32>(a, l, parity, grid);
+    case MG_SHAPE_STRIP8x64: return sup_shape<8, 64>(a, l, parity, grid);
+    default: return sup_shape<8, 32>(a, l, parity, grid);
+  }
+}
+
+cudaError_t launch_sres(const CycleArgs& a, const float* xh, const float* xl, float* r, float rtol, int max_cycles,
+                        int np) {
+  switch (a.shape) {
+    case MG_SHAPE_STRIP4x32: return sres_shape<4, 32>(a, xh, xl, r, rtol, max_cycles, np);
+    case MG_SHAPE_STRIP8x64: return sres_shape<8, 64>(a, xh, xl, r, rtol, max_cycles, np);
+    default: return sres_shape<8, 32>(a, xh, xl, r, rtol, max_cycles, np);
   }
 }
 
