@@ -28,8 +28,8 @@ struct Strip {
   static constexpr int BW = CW + 8;    // box columns C0-4 .. C0+CW+3 (x start 16-byte aligned)
   static constexpr int BH = H + 5;     // box rows R0-2 .. R0+H+2
   // resident CTAs per SM the register bound aims at (shared memory allows as many): about
-  // 40 warps per SM on 32-row blocks, 24 on 64-row blocks
-  static constexpr int MINB = H == 32 ? 40 / WPC : 3;
+  // 32 warps per SM on 32-row blocks, 24 on 64-row blocks
+  static constexpr int MINB = H == 32 ? 32 / WPC : 3;
   static_assert(H % 2 == 0, "coarse rows need an even first row");
   static_assert(BW <= 256 && BH <= 256, "TMA box limit");
 };
@@ -107,10 +107,9 @@ __device__ __forceinline__ float strip_H(const LevelDev& L, const float (&s)[9],
 // column sums v = s/2 + s + s/2 of the restriction over fine rows 2I+2, 2I+3, 2I+4 of box
 // coordinates; at each coarse row it finishes P^T s with the row sums of the neighbouring
 // lanes.  Correct values: e on lanes 1..30, s on 2..29, r_c on the odd lanes 3..27.
-// The walk is a loop over chunks of six rows (the periods of the three-row windows and of
-// the restriction's row parity), so the register windows rotate without copies and the
-// code stays small; MARGIN selects the variant for warps that touch points within
-// MG_NET_MARGIN of an edge (class-table kernels there).
+// The walk is unrolled completely (the register windows rotate without copies).  EDGE
+// selects the variant for warps that touch the boundary: bounds checks, and class-table
+// kernels within MG_NET_MARGIN of an edge; warps away from it run without either.
 struct DownCtx {
   float s[9], wi[9];
   float omega;
@@ -121,7 +120,7 @@ struct DownCtx {
   float* rc_out;
 };
 
-template <int SK, int HK, int H, int BW, bool MARGIN>
+template <int SK, int HK, int H, int BW, bool EDGE>
 __device__ __forceinline__ void sdown_walk(const LevelDev& L, const DownCtx& c) {
   constexpr int BH = H + 5;
   Row3 ra = row3(c.col[0]), rb = row3(c.col[BW]);  // r on box rows q-2, q-1
@@ -138,16 +137,16 @@ __device__ __forceinline__ void sdown_walk(const LevelDev& L, const DownCtx& c) 
         const Row3 rc = row3(c.col[q * BW]);
         const int ie = c.R0 + q - 3;  // e on box row q-1
         float e = 0.f;
-        if (c.jin && (unsigned)ie < (unsigned)c.n) {
-          const bool margin = MARGIN && (c.jmargin || ie < MG_NET_MARGIN || ie >= c.n - MG_NET_MARGIN);
+        if (!EDGE || (c.jin && (unsigned)ie < (unsigned)c.n)) {
+          const bool margin = EDGE && (c.jmargin || ie < MG_NET_MARGIN || ie >= c.n - MG_NET_MARGIN);
           e = strip_H<SK, HK>(L, c.s, c.wi, c.omega, ie, c.j, margin, ra, rb, rc);
         }
         const Row3 ec = row3(e);
-        if (q >= 3 && q < H + 3 && c.own && ie < c.n) c.e_out[(size_t)ie * c.pitch + c.j] = e;
+        if (q >= 3 && q < H + 3 && c.own && (!EDGE || ie < c.n)) __stcg(c.e_out + (size_t)ie * c.pitch + c.j, e);
         if (q >= 4) {
           const int is = c.R0 + q - 4;  // s on box row q-2 (needed inside the grid only)
           float sv = 0.f;
-          if (c.jin && is < c.n) {
+          if (!EDGE || (c.jin && is < c.n)) {
             float a[9];
             stencil_at<SK>(L, c.s, is, c.j, a);
             sv = ra.c - dot9r(a, ea, eb, ec);
@@ -161,7 +160,7 @@ __device__ __forceinline__ void sdown_walk(const LevelDev& L, const DownCtx& c) 
               v = fmaf(0.5f, sv, v);
               const float rcv = fmaf(0.5f, __shfl_up_sync(0xffffffffu, v, 1) + __shfl_down_sync(0xffffffffu, v, 1), v);
               const int Ic = (c.R0 >> 1) + ((qs - 4) >> 1);
-              if (c.cown && Ic < c.nc) c.rc_out[(size_t)Ic * c.pc + c.Jc] = rcv;
+              if (c.cown && (!EDGE || Ic < c.nc)) __stcg(c.rc_out + (size_t)Ic * c.pc + c.Jc, rcv);
             }
             v = 0.5f * sv;
           } else {
@@ -226,10 +225,12 @@ __global__ void __launch_bounds__(32 * WPC, Strip<WPC, H>::MINB) k_sdown(const _
   // coarse output of the odd lanes 3 .. 27: column c0/2 + (lane - 3)/2
   c.Jc = (c0 >> 1) + ((lane - 3) >> 1);
   c.cown = (lane & 1) && lane >= 3 && lane <= 27 && c.Jc < c.nc;
-  // a warp away from the edges (every point it evaluates at least M from them) uses the
-  // interior kernel throughout
-  const bool inner = T == MG_PROXY && c0 - 2 >= M && c0 + 29 < n - M && R0 - 1 >= M && R0 + H + 1 < n - M;
-  if (HK != HK_TABLE || inner) sdown_walk<SK, HK, H, G::BW, false>(L, c);
+  // a warp whose points all lie inside the grid (and, for class tables, at least M from
+  // its edges) needs neither bounds checks nor table kernels
+  const int m = HK == HK_TABLE ? M : 0;
+  const bool inner = (HK != HK_TABLE || T == MG_PROXY) && c0 - 2 >= m && c0 + 29 < n - m && R0 - 1 >= m &&
+                     R0 + H + 1 < n - m;
+  if (inner) sdown_walk<SK, HK, H, G::BW, false>(L, c);
   else sdown_walk<SK, HK, H, G::BW, true>(L, c);
 }
 
@@ -258,7 +259,7 @@ struct UpCtx {
   float *xout_hi, *xout_lo;
 };
 
-template <int SK, int HK, int H, int BW, int CBW, bool UPDX, bool MARGIN>
+template <int SK, int HK, int H, int BW, int CBW, bool UPDX, bool EDGE>
 __device__ __forceinline__ void sup_walk(const LevelDev& L, const UpCtx& c) {
   Row3 ea, eb;  // e1 on box rows q-2, q-1
   Row3 ta, tb;  // t on box rows q-3, q-2
@@ -285,7 +286,7 @@ __device__ __forceinline__ void sup_walk(const LevelDev& L, const UpCtx& c) {
         if (q >= 2) {
           const int it = c.R0 + q - 3;  // t on box row q-1
           float tv = 0.f;
-          if (c.jin && (unsigned)it < (unsigned)c.n) {
+          if (!EDGE || (c.jin && (unsigned)it < (unsigned)c.n)) {
             float a[9];
             stencil_at<SK>(L, c.s, it, c.j, a);
             tv = __ldg(c.rin + (size_t)it * c.pitch + c.j) - dot9r(a, ea, eb, ec);
@@ -293,19 +294,19 @@ __device__ __forceinline__ void sup_walk(const LevelDev& L, const UpCtx& c) {
           const Row3 tc = row3(tv);
           if (q >= 4) {
             const int i = c.R0 + q - 4;  // final correction on box row q-2 (the CTA's rows)
-            if (c.own && i < c.n) {
-              const bool margin = MARGIN && (c.jmargin || i < MG_NET_MARGIN || i >= c.n - MG_NET_MARGIN);
+            if (c.own && (!EDGE || i < c.n)) {
+              const bool margin = EDGE && (c.jmargin || i < MG_NET_MARGIN || i >= c.n - MG_NET_MARGIN);
               const float e = ea.c + strip_H<SK, HK>(L, c.s, c.wi, c.omega, i, c.j, margin, ta, tb, tc);
               const size_t g = (size_t)i * c.pitch + c.j;
               if (UPDX) {
-                float hi = c.xin_hi[g], lo = c.xin_lo[g], sum, err;
+                float hi = __ldg(c.xin_hi + g), lo = __ldg(c.xin_lo + g), sum, err;
                 two_sum(hi, e, sum, err);
                 err += lo;
                 fast_two_sum(sum, err, hi, lo);
-                c.xout_hi[g] = hi;
-                c.xout_lo[g] = lo;
+                __stcg(c.xout_hi + g, hi);
+                __stcg(c.xout_lo + g, lo);
               } else {
-                c.fout[g] = e;
+                __stcg(c.fout + g, e);
               }
             }
           }
@@ -378,8 +379,11 @@ __global__ void __launch_bounds__(32 * WPC, Strip<WPC, H>::MINB)
   c.col = es + SW * w + 2 + lane;
   c.ca = ecs + (SW / 2) * w + ((lane - 3) >> 1) + 4;  // coarse column (j - 1) >> 1
   c.cb = ecs + (SW / 2) * w + ((lane - 2) >> 1) + 4;  // coarse column j >> 1
-  const bool inner = T == MG_PROXY && c0 >= M && c0 + SW <= n - M && R0 >= M && R0 + H <= n - M;
-  if (HK != HK_TABLE || inner) sup_walk<SK, HK, H, G::BW, CBW, UPDX, false>(L, c);
+  // inside the grid: t on rows R0-1 .. R0+H and columns c0-2 .. c0+29; for class tables the
+  // smoothed points (the owned ones) at least M from the edges
+  bool inner = c0 - 2 >= 0 && c0 + 29 < n && R0 - 1 >= 0 && R0 + H < n;
+  if (HK == HK_TABLE) inner = inner && T == MG_PROXY && c0 >= M && c0 + SW <= n - M && R0 >= M && R0 + H <= n - M;
+  if (inner) sup_walk<SK, HK, H, G::BW, CBW, UPDX, false>(L, c);
   else sup_walk<SK, HK, H, G::BW, CBW, UPDX, true>(L, c);
 }
 
@@ -389,6 +393,50 @@ __global__ void __launch_bounds__(32 * WPC, Strip<WPC, H>::MINB)
 // CTA of a problem, the stopping test.  A warp owns 30 columns (lane k holds column
 // c0 - 1 + k) and walks the rows R0-1 .. R0+H of x; x and b come straight from global
 // memory, one coalesced row per load.
+// The row walk of k_sres for one lane; EDGE: bounds checks (warps touching the boundary).
+// Away from it every lane evaluates its row (lanes 0 and 31 from wrong neighbours) and
+// only the owned lanes store and count theirs.
+template <int SK, int H, bool EDGE>
+__device__ __forceinline__ float sres_walk(const LevelDev& L, const float (&s)[9], const float* xh, const float* xl,
+                                           const float* bb, float* rr, int n, int pitch, int R0, int j, bool jin,
+                                           bool own) {
+  auto ld = [&](const float* a, int i) {
+    return (!EDGE || (jin && (unsigned)i < (unsigned)n)) ? __ldg(a + (size_t)i * pitch + j) : 0.f;
+  };
+  Row3 ha = row3(ld(xh, R0 - 1)), la = row3(ld(xl, R0 - 1));  // rows i-1 and i of x
+  Row3 hb = row3(ld(xh, R0)), lb = row3(ld(xl, R0));
+  float acc = 0.f;
+#pragma unroll
+  for (int q = 0; q < H; ++q) {
+    const int i = R0 + q;  // residual on grid row i
+    const Row3 hc = row3(ld(xh, i + 1)), lc = row3(ld(xl, i + 1));
+    if (!EDGE || (jin && i < n)) {
+      float a[9];
+      stencil_at<SK>(L, s, i, j, a);
+      float hi = __ldg(bb + (size_t)i * pitch + j), lo = 0.f;
+      dot2_sub(a[0], ha.l, la.l, hi, lo);
+      dot2_sub(a[1], ha.c, la.c, hi, lo);
+      dot2_sub(a[2], ha.r, la.r, hi, lo);
+      dot2_sub(a[3], hb.l, lb.l, hi, lo);
+      dot2_sub(a[4], hb.c, lb.c, hi, lo);
+      dot2_sub(a[5], hb.r, lb.r, hi, lo);
+      dot2_sub(a[6], hc.l, lc.l, hi, lo);
+      dot2_sub(a[7], hc.c, lc.c, hi, lo);
+      dot2_sub(a[8], hc.r, lc.r, hi, lo);
+      const float r = hi + lo;
+      if (own) {
+        __stcg(rr + (size_t)i * pitch + j, r);
+        acc = fmaf(r, r, acc);
+      }
+    }
+    ha = hb;
+    la = lb;
+    hb = hc;
+    lb = lc;
+  }
+  return acc;
+}
+
 template <int SK, int WPC, int H>
 __global__ void __launch_bounds__(32 * WPC, Strip<WPC, H>::MINB)
     k_sres(const ProbDev* __restrict__ probs, ProbState* __restrict__ state, float* __restrict__ partials,
@@ -408,51 +456,18 @@ __global__ void __launch_bounds__(32 * WPC, Strip<WPC, H>::MINB)
   for (int k = 0; k < 9; ++k) s[k] = (SK == SK_CONST) ? probs[p].lv[0].s[k] : 0.f;
   const LevelDev& L = probs[p].lv[0];
   const size_t po = (size_t)p * n * pitch;
-  const float* xh = xh_base + po;
-  const float* xl = xl_base + po;
-  const float* bb = b_base + po;
-  float* rr = r_base + po;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int j = C0 + RW * w - 1 + lane;
+  const int c0 = C0 + RW * w;  // first owned column of the warp
+  const int j = c0 - 1 + lane;
   const bool jin = (unsigned)j < (unsigned)n;
   const bool own = lane >= 1 && lane < 1 + RW && jin;
+  const bool inner = c0 - 1 >= 0 && c0 + 30 < n && R0 - 1 >= 0 && R0 + H < n;
   pdl_wait();
   if (!st_active(state + p)) return;
-  auto ld = [&](const float* a, int i) { return (jin && (unsigned)i < (unsigned)n) ? a[(size_t)i * pitch + j] : 0.f; };
-  Row3 ha = row3(ld(xh, R0 - 1)), la = row3(ld(xl, R0 - 1));  // rows i-1 and i of x
-  Row3 hb = row3(ld(xh, R0)), lb = row3(ld(xl, R0));
-  float acc = 0.f;
-#pragma unroll
-  for (int q0 = 0; q0 < H; q0 += 3) {
-#pragma unroll
-    for (int u = 0; u < 3; ++u) {
-      const int q = q0 + u, i = R0 + q;  // residual on grid row i
-      if (q < H) {
-        const Row3 hc = row3(ld(xh, i + 1)), lc = row3(ld(xl, i + 1));
-        if (own && i < n) {
-          float a[9];
-          stencil_at<SK>(L, s, i, j, a);
-          float hi = bb[(size_t)i * pitch + j], lo = 0.f;
-          dot2_sub(a[0], ha.l, la.l, hi, lo);
-          dot2_sub(a[1], ha.c, la.c, hi, lo);
-          dot2_sub(a[2], ha.r, la.r, hi, lo);
-          dot2_sub(a[3], hb.l, lb.l, hi, lo);
-          dot2_sub(a[4], hb.c, lb.c, hi, lo);
-          dot2_sub(a[5], hb.r, lb.r, hi, lo);
-          dot2_sub(a[6], hc.l, lc.l, hi, lo);
-          dot2_sub(a[7], hc.c, lc.c, hi, lo);
-          dot2_sub(a[8], hc.r, lc.r, hi, lo);
-          const float r = hi + lo;
-          rr[(size_t)i * pitch + j] = r;
-          acc = fmaf(r, r, acc);
-        }
-        ha = hb;
-        la = lb;
-        hb = hc;
-        lb = lc;
-      }
-    }
-  }
+  const float acc = inner ? sres_walk<SK, H, false>(L, s, xh_base + po, xl_base + po, b_base + po, r_base + po, n,
+                                                    pitch, R0, j, jin, own)
+                          : sres_walk<SK, H, true>(L, s, xh_base + po, xl_base + po, b_base + po, r_base + po, n,
+                                                   pitch, R0, j, jin, own);
   float rhi, rlo;
   if (block_partial_and_last<NT>(acc, partials + (size_t)p * ntiles_max, &state[p].counter, ntiles, tile, rhi, rlo)) {
     if (threadIdx.x == 0) decide(state[p], rhi, rlo, rtol, max_cycles);
