@@ -107,9 +107,11 @@ __device__ __forceinline__ float strip_H(const LevelDev& L, const float (&s)[9],
 // column sums v = s/2 + s + s/2 of the restriction over fine rows 2I+2, 2I+3, 2I+4 of box
 // coordinates; at each coarse row it finishes P^T s with the row sums of the neighbouring
 // lanes.  Correct values: e on lanes 1..30, s on 2..29, r_c on the odd lanes 3..27.
-// The walk is unrolled completely (the register windows rotate without copies).  EDGE
-// selects the variant for warps that touch the boundary: bounds checks, and class-table
-// kernels within MG_NET_MARGIN of an edge; warps away from it run without either.
+// The walk is a loop over chunks of six rows (the periods of the three-row windows and of
+// the restriction's row parity), so the register windows rotate without copies while the
+// code stays small enough for the instruction cache.  EDGE selects the variant for warps
+// that touch the boundary: bounds checks, and class-table kernels within MG_NET_MARGIN of
+// an edge; warps away from it run without either.
 struct DownCtx {
   float s[9], wi[9];
   float omega;
@@ -128,7 +130,7 @@ __device__ __forceinline__ void sdown_walk(const LevelDev& L, const DownCtx& c) 
   ea.l = ea.c = ea.r = 0.f;
   eb = ea;
   float v = 0.f;  // column sum of the current coarse row
-#pragma unroll
+#pragma unroll 1
   for (int q0 = 2; q0 < BH; q0 += 6) {
 #pragma unroll
     for (int u = 0; u < 6; ++u) {
@@ -268,7 +270,10 @@ __device__ __forceinline__ void sup_walk(const LevelDev& L, const UpCtx& c) {
   ta = ea;
   tb = ea;
   float hP = 0.5f * (c.ca[0] + c.cb[0]);  // coarse box row 0
-#pragma unroll
+  // global loads stay unconditional, so the compiler may issue a chunk's loads together:
+  // on boundary warps the address is clamped into the grid and the value discarded
+  const int jc = EDGE ? min(max(c.j, 0), c.n - 1) : c.j;
+#pragma unroll 1
   for (int q0 = 0; q0 < H + 4; q0 += 6) {
 #pragma unroll
     for (int u = 0; u < 6; ++u) {
@@ -285,21 +290,28 @@ __device__ __forceinline__ void sup_walk(const LevelDev& L, const UpCtx& c) {
         const Row3 ec = row3(c.col[q * BW] + pe);  // e1 on box row q (zero outside the grid)
         if (q >= 2) {
           const int it = c.R0 + q - 3;  // t on box row q-1
+          const int itc = EDGE ? min(max(it, 0), c.n - 1) : it;
+          const float rv = __ldg(c.rin + (size_t)itc * c.pitch + jc);
           float tv = 0.f;
           if (!EDGE || (c.jin && (unsigned)it < (unsigned)c.n)) {
             float a[9];
             stencil_at<SK>(L, c.s, it, c.j, a);
-            tv = __ldg(c.rin + (size_t)it * c.pitch + c.j) - dot9r(a, ea, eb, ec);
+            tv = rv - dot9r(a, ea, eb, ec);
           }
           const Row3 tc = row3(tv);
           if (q >= 4) {
             const int i = c.R0 + q - 4;  // final correction on box row q-2 (the CTA's rows)
+            const size_t g = (size_t)(EDGE ? min(i, c.n - 1) : i) * c.pitch + jc;
+            float xh = 0.f, xl = 0.f;
+            if (UPDX) {
+              xh = __ldg(c.xin_hi + g);
+              xl = __ldg(c.xin_lo + g);
+            }
             if (c.own && (!EDGE || i < c.n)) {
               const bool margin = EDGE && (c.jmargin || i < MG_NET_MARGIN || i >= c.n - MG_NET_MARGIN);
               const float e = ea.c + strip_H<SK, HK>(L, c.s, c.wi, c.omega, i, c.j, margin, ta, tb, tc);
-              const size_t g = (size_t)i * c.pitch + c.j;
               if (UPDX) {
-                float hi = __ldg(c.xin_hi + g), lo = __ldg(c.xin_lo + g), sum, err;
+                float hi = xh, lo = xl, sum, err;
                 two_sum(hi, e, sum, err);
                 err += lo;
                 fast_two_sum(sum, err, hi, lo);
@@ -400,20 +412,30 @@ template <int SK, int H, bool EDGE>
 __device__ __forceinline__ float sres_walk(const LevelDev& L, const float (&s)[9], const float* xh, const float* xl,
                                            const float* bb, float* rr, int n, int pitch, int R0, int j, bool jin,
                                            bool own) {
+  // unconditional loads (clamped into the grid on boundary warps, the value then
+  // discarded), so a chunk's loads can be issued together
+  const int jc = EDGE ? min(max(j, 0), n - 1) : j;
   auto ld = [&](const float* a, int i) {
-    return (!EDGE || (jin && (unsigned)i < (unsigned)n)) ? __ldg(a + (size_t)i * pitch + j) : 0.f;
+    if (!EDGE) return __ldg(a + (size_t)i * pitch + j);
+    const float v = __ldg(a + (size_t)min(max(i, 0), n - 1) * pitch + jc);
+    return (jin && (unsigned)i < (unsigned)n) ? v : 0.f;
   };
   Row3 ha = row3(ld(xh, R0 - 1)), la = row3(ld(xl, R0 - 1));  // rows i-1 and i of x
   Row3 hb = row3(ld(xh, R0)), lb = row3(ld(xl, R0));
   float acc = 0.f;
+#pragma unroll 1
+  for (int q0 = 0; q0 < H; q0 += 6) {
 #pragma unroll
-  for (int q = 0; q < H; ++q) {
+  for (int u = 0; u < 6; ++u) {
+    const int q = q0 + u;
+    if (q >= H) break;
     const int i = R0 + q;  // residual on grid row i
     const Row3 hc = row3(ld(xh, i + 1)), lc = row3(ld(xl, i + 1));
+    const float bv = ld(bb, i);
     if (!EDGE || (jin && i < n)) {
       float a[9];
       stencil_at<SK>(L, s, i, j, a);
-      float hi = __ldg(bb + (size_t)i * pitch + j), lo = 0.f;
+      float hi = bv, lo = 0.f;
       dot2_sub(a[0], ha.l, la.l, hi, lo);
       dot2_sub(a[1], ha.c, la.c, hi, lo);
       dot2_sub(a[2], ha.r, la.r, hi, lo);
@@ -433,6 +455,7 @@ __device__ __forceinline__ float sres_walk(const LevelDev& L, const float (&s)[9
     la = lb;
     hb = hc;
     lb = lc;
+  }
   }
   return acc;
 }
