@@ -389,8 +389,7 @@ mg_status mg_solve_small_static(const mg_problem* problems, int nprob, const mg_
    synchronises and by mg_profile_read (which requires the stream to be idle).
    kernel_class: 0 outer residual, 1 down-sweep of level 0, 2 up-sweep of level 0 (with the
    iterate update), 3 one-CTA coarse tail / small-problem solve, 4 down-sweeps of levels >= 1,
-   5 up-sweeps of levels >= 1, 6 the residual of the updated iterate with the stopping test
-   (a kernel of its own in the strip layouts; part of class 2 in MG_TILE_32x32); -1 returns in *launches the number of kernels this context
+   5 up-sweeps of levels >= 1; -1 returns in *launches the number of kernels this context
    launched since the last reset (timing or not). */
 mg_status mg_profile_enable(mg_ctx* ctx, int enable);
 

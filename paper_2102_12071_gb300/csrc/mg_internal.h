@@ -13,7 +13,7 @@ struct mg_ctx;  // the library's context (mgcnn.h)
 namespace mg {
 
 // Kernel classes timed by the optional event profiler.
-enum { PK_RESIDUAL = 0, PK_DOWN0 = 1, PK_UP0 = 2, PK_TAIL = 3, PK_DOWN = 4, PK_UP = 5, PK_RES0 = 6, PK_NCLASS = 7 };
+enum { PK_RESIDUAL = 0, PK_DOWN0 = 1, PK_UP0 = 2, PK_TAIL = 3, PK_DOWN = 4, PK_UP = 5, PK_NCLASS = 6 };
 
 // CUDA-event timing of individual launches on the launching stream; events are reused
 // after each collect() (called once the stream has been synchronised).
@@ -93,8 +93,6 @@ struct TileMaps {
   // 0's from r0b on odd cycles
   CUtensorMap sr[MG_MAXL];
   CUtensorMap sr0b;
-  // ... the up-sweep's e block and coarse-correction block of each tiled level
-  CUtensorMap se[MG_MAXL], sec[MG_MAXL];
 };
 
 // base pointers of the pitched level arrays (all problems of a level contiguous)
@@ -206,14 +204,7 @@ bool build_tile_maps(TileMaps& maps, const LevelArrays& arrays, int nprob, int l
 // strip layouts (mg_strip.cu): the r block (box) of the down-sweep, and its launch on level
 // l for np problems with the tensor map m of that level's r array
 void strip_box(int shape, int* bw, int* bh);
-void strip_coarse_box(int shape, int* bw, int* bh);
 cudaError_t launch_sdown(const CycleArgs& a, const CUtensorMap& m, int l, int np);
-// up-sweep of level l (level 0: with the float-float update of the iterate of cycle
-// `parity`, written to the other pair), and the residual of an iterate pair into r with
-// the norm and the stopping test
-cudaError_t launch_sup(const CycleArgs& a, int l, int parity, int np);
-cudaError_t launch_sres(const CycleArgs& a, const float* xh, const float* xl, float* r, float rtol, int max_cycles,
-                        int np);
 // level 0 after an up-sweep run elsewhere: x += e_0 and the residual of the new iterate
 // with the stopping test, on the arrays of cycle `parity` (mg_tiles.cu); e0: tensor map of
 // e_0 with the iterate's box (tile_res_box)

@@ -723,13 +723,8 @@ bool build_tile_maps(TileMaps& T, const LevelArrays& A, int nprob, int lstar, in
   if (shape != MG_SHAPE_TILE32) {
     int bw, bh;
     strip_box(shape, &bw, &bh);
-    int cbw, cbh;
-    strip_coarse_box(shape, &cbw, &cbh);
     for (int l = 0; l < lstar; ++l)
-      if (!make_map(&T.sr[l], A.r[l], A.n[l], A.pitch[l], nprob, bw, bh) ||
-          !make_map(&T.se[l], A.e[l], A.n[l], A.pitch[l], nprob, bw, bh) ||
-          !make_map(&T.sec[l], l + 1 < lstar ? A.f[l + 1] : A.e[l + 1], A.n[l + 1], A.pitch[l + 1], nprob, cbw, cbh))
-        return false;
+      if (!make_map(&T.sr[l], A.r[l], A.n[l], A.pitch[l], nprob, bw, bh)) return false;
     if (!make_map(&T.sr0b, A.r0b, A.n[0], A.pitch[0], nprob, bw, bh)) return false;
   }
   bool ok = make_map(&T.res.xh, A.xh0, A.n[0], A.pitch[0], nprob, XW, RES_H) &&
@@ -771,9 +766,7 @@ cudaError_t launch_residual(const CycleArgs& a, float rtol, int max_cycles) {
   a.prof->launches++;
   a.prof->begin(PK_RESIDUAL, a.stream);
   cudaError_t e;
-  if (a.shape != MG_SHAPE_TILE32)
-    e = launch_sres(a, a.xh0, a.xl0, a.r0a, rtol, max_cycles, nlaunch(a));
-  else if (a.sk == SK_CONST)
+  if (a.sk == SK_CONST)
     e = launch_pdl(a.pdl, k_residual<SK_CONST>, grid, dim3(NT), 0, a.stream, a.maps->res, (const ProbDev*)a.probs, a.state,
                    a.partials, a.ntiles_max, rtol, max_cycles, a.active);
   else
@@ -838,19 +831,6 @@ cudaError_t launch_cycle(const CycleArgs& a, float rtol, int max_cycles, int par
     const bool pdl = a.pdl && !(a.ctail && l == ls - 1);
     a.prof->launches++;
     a.prof->begin(l == 0 ? PK_UP0 : PK_UP, a.stream);
-    if (a.shape != MG_SHAPE_TILE32) {
-      e = launch_sup(a, l, parity, np);
-      a.prof->end(a.stream);
-      if (l == 0 && e == cudaSuccess) {
-        // the residual of the new iterate (the other pair) into the other r array
-        a.prof->launches++;
-        a.prof->begin(PK_RES0, a.stream);
-        e = launch_sres(a, parity ? a.xh0 : a.xh0b, parity ? a.xl0 : a.xl0b, parity ? a.r0a : a.r0b, rtol,
-                        max_cycles, np);
-        a.prof->end(a.stream);
-      }
-      continue;
-    }
     if (l == 0) {
       Up0Maps um = a.maps->up0;
       if (parity) {
