@@ -304,16 +304,87 @@ def run_varcoef(args, rank):
         arms = ["jacobi"] + (["cnn"] if wv is not None else []) + (["fc"] if wfc is not None else [])
         for kind in arms:
             net = {"cnn": wv[1] if wv is not None else None, "fc": wfc}.get(kind)
-            mg = S.MultigridSolver([S.varcoef5(n, cells)], "jacobi" if kind == "jacobi" else "cnn", net_params=net,
-                                   net_arch="fc" if kind == "fc" else "conv")
+            # mg_setup (stencils, Galerkin hierarchy, coarsest factor and, for the network
+            # arms, the per-point network on every smoothed level) timed on its own: the
+            # network's cost belongs to the learned smoother
+            setup_ms = []
+            for rep in range(2):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                mg = S.MultigridSolver([S.varcoef5(n, cells)], "jacobi" if kind == "jacobi" else "cnn",
+                                       net_params=net, net_arch="fc" if kind == "fc" else "conv")
+                torch.cuda.synchronize()
+                setup_ms.append(1e3 * (time.perf_counter() - t0))
+                if rep == 0:
+                    mg.close()
             ms, cyc, st = timed_solve(mg, b, reps=3 if n <= 2047 else 1)
-            res[kind] = {"ms": ms, "cycles": int(cyc[0]), "converged": int(st) == 0,
+            res[kind] = {"ms": ms, "setup_ms": setup_ms[-1], "setup_and_solve_ms": setup_ms[-1] + ms,
+                         "cycles": int(cyc[0]), "converged": int(st) == 0,
                          "mdof_sweeps_per_s": sweeps_per_cycle(mg.sizes) * int(cyc[0]) / (ms / 1e3)}
             mg.close()
         if wv is not None:
             res["cnn_vs_jacobi_time"] = res["jacobi"]["ms"] / res["cnn"]["ms"]
+            res["cnn_vs_jacobi_time_with_setup"] = res["jacobi"]["setup_and_solve_ms"] / res["cnn"]["setup_and_solve_ms"]
         out[str(n)] = res
         del cells, b
+        torch.cuda.empty_cache()
+    return out
+
+
+# FP32 pipe peak of the GPU (152 SMs x 128 FP32 lanes x 2 flops per FMA x clock): the ALU
+# roofline of the network kernels, which run on the FP32 pipes
+SMS, FP32_LANES = 152, 128
+NET_FLOPS = {"conv": 2 * 1260, "fc": 2 * 6800}  # multiply-adds per point x 2 (Sec. 6.2 layer sizes)
+NET_BYTES = 9 * 4 + 9 * 4  # per point: its stencil in, its 3x3 kernel out (FP32)
+
+
+def run_network(sizes, sm_mhz):
+    """Network inference of mg_setup on per-point fields (the GRF 5-point operator): the
+    convolutional network in FP32 and bfloat16 and the fully connected one, one launch per
+    field, event-timed; flops are the network's own (tile halos recomputed by the kernel are
+    not counted) against the FP32 pipe peak at the sampled clock."""
+    import numpy as np
+    import torch
+
+    from paper_2102_12071_gb300 import binding as B, inputs, solver as S
+
+    wv = load_varcoef_weights()
+    fc_path = os.path.join(os.path.dirname(WEIGHTS), "fc_varcoef.npy")
+    wfc = torch.from_numpy(np.load(fc_path).astype(np.float32)).cuda() if os.path.exists(fc_path) else None
+    peak = SMS * FP32_LANES * 2 * (sm_mhz or 2070.0) * 1e6 / 1e12
+    out = {"fp32_peak_tflops": peak, "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x sampled SM clock",
+           "flops_per_point": NET_FLOPS, "algorithmic_bytes_per_point": NET_BYTES}
+    for n in sizes:
+        cells = torch.from_numpy(inputs.grf_cells(inputs.SEED_GRF, n)).cuda()
+        mg = S.MultigridSolver([S.varcoef5(n, cells)], "jacobi")
+        field = mg.stencil_field(0, 0)[None].contiguous()
+        mg.close()
+        W = torch.empty_like(field)
+        res = {}
+        arms = ([("conv_fp32", "conv", 0), ("conv_bf16", "conv", 1)] if wv is not None else []) + \
+               ([("fc_fp32", "fc", 0)] if wfc is not None else [])
+        for name, arch, bf16 in arms:
+            prm = wv[1] if arch == "conv" else wfc
+            fwd = B.mg_net_forward if arch == "conv" else B.mg_net_fc_forward
+            for _ in range(2):
+                fwd(n, 1, field, prm, 2.0 / 3.0, bf16, W)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 5
+            e0.record()
+            for _ in range(reps):
+                fwd(n, 1, field, prm, 2.0 / 3.0, bf16, W)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            pts = n * n
+            tf = NET_FLOPS[arch] * pts / (ms / 1e3) / 1e12
+            res[name] = {"ms": ms, "mpoints_per_s": pts / (ms / 1e3) / 1e6,
+                         "roofline": {"bound": "alu", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
+                                      "frac": tf / peak},
+                         "hbm_gbs": NET_BYTES * pts / (ms / 1e3) / 1e9}
+        out[str(n)] = res
+        del field, W, cells
         torch.cuda.empty_cache()
     return out
 
@@ -775,6 +846,8 @@ def main():
     e2e_s = e2e_ms / 1e3
 
     varcoef = run_varcoef(args, rank) if str(args.varcoef_n) != "0" else None
+    network = run_network([int(v) for v in str(args.varcoef_n).split(",") if int(v) > 0], clocks.get("sm_mhz")) \
+        if str(args.varcoef_n) != "0" and rank == 0 else None
     extra = {}
     if not args.no_extra and rank == 0:
         extra["c1_63"] = run_c1()
@@ -805,6 +878,7 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clocks,
         "varcoef": varcoef,
+        "network": network,
         "mixed": mixed,
         **extra,
     }
