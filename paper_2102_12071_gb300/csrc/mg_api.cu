@@ -560,6 +560,8 @@ mg_status mg_setup(const mg_problem* problems, int nprob, const mg_options* opts
         prm_sets = ctx->net_dense;
       }
       auto net = [&](const NetJob* jobs_dev, int njobs, int nm, const float* prm) {
+        // the fully connected network's bfloat16 mode runs its GEMMs on the tensor cores
+        if (fc && opts->conv_bf16) return launch_fc_forward_tc(jobs_dev, njobs, nm, prm, opts->omega, s);
         return fc ? launch_fc_forward(jobs_dev, njobs, nm, prm, opts->omega, opts->conv_bf16, s)
                   : launch_net_forward(jobs_dev, njobs, nm, prm, opts->omega, opts->conv_bf16, s);
       };
@@ -869,7 +871,8 @@ mg_status mg_net_fc_forward(int n, int nprob, const float* fields, const float* 
   B.stride = 9 * (size_t)n * n;
   B.n = n;
   B.pad_ = 0;
-  CK(launch_fc_forward_batch(B, nprob, params, omega, bf16, (cudaStream_t)stream));
+  if (bf16) CK(launch_fc_forward_batch_tc(B, nprob, params, omega, (cudaStream_t)stream));
+  else CK(launch_fc_forward_batch(B, nprob, params, omega, bf16, (cudaStream_t)stream));
   return MG_OK;
 }
 

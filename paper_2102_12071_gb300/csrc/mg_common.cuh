@@ -17,7 +17,9 @@
 #define MG_TAIL_SMEM_MAX (200 * 1024)  // dynamic shared memory limit of the tail kernels
 #define MG_CT_N 127           // levels at or below this size run in one CTA cluster per problem
 #define MG_CT_SOLO 31         // ... and at or below this size in the cluster's first CTA alone
-#define MG_CT_C 8             // CTAs per cluster (each owns a band of (n + 1) / 8 rows)
+#ifndef MG_CT_C
+#define MG_CT_C 8             // CTAs per cluster (each owns a band of (n + 1) / MG_CT_C rows)
+#endif
 #define MG_CT_HD 3            // halo rows on each side of a band
 #define MG_CT_SMEM_MAX (220 * 1024)    // dynamic shared memory limit of the cluster tail
 #define MG_NET_MARGIN 5       // points closer than this to an edge get their own kernel class

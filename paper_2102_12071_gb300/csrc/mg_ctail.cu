@@ -29,7 +29,10 @@
 
 namespace mg {
 
-constexpr int CT_THREADS = 1024;
+#ifndef MG_CT_THREADS
+#define MG_CT_THREADS 1024
+#endif
+constexpr int CT_THREADS = MG_CT_THREADS;
 
 struct CtLayout {
   TailLayout a;         // r, e, t (band or whole arrays) and kernel tables of every level
@@ -235,7 +238,7 @@ __device__ void ct_up(const ProbDev& P, float* sm, const CtLayout& lay, const fl
 // One cycle of levels ls .. L-1 for problem act[blockIdx.y]; blockIdx.x is the rank in
 // the cluster.  Reads r_ls and writes e_ls (pitched level arrays).
 template <int SK, int HK>
-__global__ void __launch_bounds__(CT_THREADS, 1) k_ctail(const ProbDev* __restrict__ probs,
+__global__ void __launch_bounds__(CT_THREADS, CT_THREADS <= 512 ? 2 : 1) k_ctail(const ProbDev* __restrict__ probs,
                                                          const ProbState* __restrict__ state, int ls, int L,
                                                          float omega, const int* __restrict__ act) {
   extern __shared__ float sm[];

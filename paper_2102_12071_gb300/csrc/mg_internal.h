@@ -278,6 +278,11 @@ cudaError_t launch_fc_forward(const NetJob* jobs_dev, int njobs, int nmax, const
                               cudaStream_t s);
 cudaError_t launch_fc_forward_batch(const NetBatch& batch, int nfields, const float* params, float omega, int bf16,
                                     cudaStream_t s);
+// its bfloat16 inference on the tensor cores (mg_fctc.cu): the same jobs and batches
+cudaError_t launch_fc_forward_tc(const NetJob* jobs_dev, int njobs, int nmax, const float* params, float omega,
+                                 cudaStream_t s);
+cudaError_t launch_fc_forward_batch_tc(const NetBatch& batch, int nfields, const float* params, float omega,
+                                       cudaStream_t s);
 size_t fc_backward_floats(int n, int nfields);
 cudaError_t launch_fc_backward(const NetBatch& batch, int nfields, const float* dW, const float* params, int bf16,
                                float* scratch, float scale, float* grad, cudaStream_t s);

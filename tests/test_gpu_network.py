@@ -425,6 +425,59 @@ def test_fc_kernels_match_oracle_on_every_level(kind):
         np.testing.assert_allclose(Wg, Wo, rtol=2e-5, atol=2e-5 * np.abs(Wo).max())
 
 
+def _bf16_agree(Wg, Wo):
+    """Kernels from bfloat16 networks: the two sides round FP32 (tensor-core or FP32-pipe
+    sums) and FP64 (oracle) pre-activations to bfloat16 and agree except where a value lies
+    within an FP32 rounding of a bfloat16 boundary; there one activation moves by one
+    bfloat16 step.  Returns the fraction of outputs within 2e-5 of the scale and the
+    largest difference over the scale."""
+    scale = np.abs(Wo).max()
+    err = np.abs(Wg - Wo)
+    return float(np.mean(err <= 2e-5 * scale)), float(err.max() / scale)
+
+
+@pytest.mark.parametrize("n", [45, 70])
+def test_fc_bf16_tensor_core_forward_matches_oracle(n):
+    """The fully connected network in bfloat16 mode runs its four GEMMs on the tensor cores
+    (tcgen05.mma, M = 128 points per tile, FP32 accumulation in tensor memory): per-point
+    kernels of a GRF field and of a constant stencil (tiles of 8 x 16 points with ragged
+    edges) against the oracle's bfloat16 emulation of the same network."""
+    fields = np.stack([varcoef_field(n, 13), f32(O.const_field(n, O.q1_rotated_stencil(0.02, 0.9)))])
+    p = _fc_params(42, 0.1)
+    ft = torch.from_numpy(fields.astype(np.float32)).cuda().contiguous()
+    W = torch.empty_like(ft)
+    B.mg_net_fc_forward(n, 2, ft, torch.from_numpy(p).cuda(), 2.0 / 3.0, 1, W)
+    torch.cuda.synchronize()
+    Wg = W.double().cpu().numpy()
+    for k in range(2):
+        frac, mx = _bf16_agree(Wg[k], O.fc_forward(fields[k], f32(p), 2.0 / 3.0, bf16=True))
+        print("fc tc agreement", n, k, frac, mx)
+        assert frac > 0.95 and mx <= 2e-2, (frac, mx)
+
+
+@pytest.mark.parametrize("kind", ["rotated", "varcoef"])
+def test_fc_bf16_tensor_core_kernels_in_the_solver(kind):
+    """mg_setup with the fully connected network in bfloat16 (tensor cores): class tables of
+    a constant stencil and per-point kernels of a GRF field on every level, against the
+    oracle's bfloat16 network on that level's own FP64 field."""
+    n = 63
+    p = _fc_params(43, 0.1)
+    if kind == "rotated":
+        prob = S.rotated(n, 0.03, 2.0)
+        st0 = O.const_field(n, f32(O.q1_rotated_stencil(0.03, 2.0)))
+    else:
+        cells = inputs.grf_cells(inputs.SEED_GRF + 71, n)
+        prob = S.varcoef5(n, torch.from_numpy(cells).cuda())
+        st0 = f32(O.varcoef5_field(n, f32(cells)))
+    mg = S.MultigridSolver([prob], "cnn", torch.from_numpy(p).cuda(), net_arch="fc", conv_bf16=True)
+    om = O.Multigrid(st0)
+    for l in range(mg.levels - 1):
+        frac, mx = _bf16_agree(mg.kernels(0, l).double().cpu().numpy(), O.fc_forward(om.field(l), f32(p), bf16=True))
+        print("fc tc solver agreement", kind, l, frac, mx)
+        assert frac > 0.95 and mx <= 2e-2, (l, frac, mx)
+    mg.close()
+
+
 @pytest.mark.parametrize("n,bf16", [(15, False), (31, False), (15, True)])
 def test_fc_train_step_matches_oracle(n, bf16):
     """Loss and gradient of the two-grid objective through the fully connected network."""
