@@ -362,7 +362,7 @@ def run_network(sizes, sm_mhz):
         W = torch.empty_like(field)
         res = {}
         arms = ([("conv_fp32", "conv", 0), ("conv_bf16", "conv", 1)] if wv is not None else []) + \
-               ([("fc_fp32", "fc", 0)] if wfc is not None else [])
+               ([("fc_fp32", "fc", 0), ("fc_bf16_tensor_cores", "fc", 1)] if wfc is not None else [])
         for name, arch, bf16 in arms:
             prm = wv[1] if arch == "conv" else wfc
             fwd = B.mg_net_forward if arch == "conv" else B.mg_net_fc_forward

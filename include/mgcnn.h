@@ -121,14 +121,16 @@ typedef struct {
                            sets for each problem of the batch, [nprob][sets][54] in batch
                            order (Sec. 6 trains one smoother per problem); 0 -- one group
                            of sets shared by every problem                               */
-  int tile_shape;       /* mg_tile_shape: how the kernels of the levels above the coarse
-                           tail cover a level.  Every shape computes the same cycle (up to
-                           the order of FP32 roundings); it only changes the work per CTA,
-                           so the fastest one depends on the grid size and the batch.    */
+  int tile_shape;       /* mg_tile_shape: how the down-sweep kernels of the levels above
+                           the coarse tail cover a level (the up-sweeps always use 32 x 32
+                           tiles).  Every shape computes the same cycle (up to the order of
+                           FP32 roundings); it only changes the work per CTA, so the fastest
+                           one depends on the grid size, the smoother and the batch: strips
+                           pay off when many problems fill the GPU, tiles when few do.     */
 } mg_options;
 
 typedef enum {
-  MG_TILE_DEFAULT = 0,    /* MG_TILE_STRIP8x32                                          */
+  MG_TILE_DEFAULT = 0,    /* MG_TILE_32x32                                              */
   MG_TILE_32x32 = 1,      /* one 32 x 32 block of points per CTA, 3x3 windows in shared
                              memory                                                     */
   MG_TILE_STRIP4x32 = 2,  /* warp strips: a warp owns 26 columns and walks down the rows,

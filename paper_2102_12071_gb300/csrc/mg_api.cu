@@ -51,7 +51,7 @@ struct Plan {
   int generic = 0;  // levels above the tail in batched level kernels (mg_linear.cu)
   int nu1 = 1, nu2 = 1;
   int lstar1 = 0;   // first level of the one-CTA tail (the fallback of the cluster tail)
-  int shape = MG_SHAPE_STRIP8x32;  // layout of the tiled level kernels
+  int shape = MG_SHAPE_TILE32;  // layout of the tiled level kernels
   int nl[MG_MAXL] = {0};
   int ntiles_max = 0;
   size_t bytes = 0;
@@ -80,7 +80,7 @@ mg_status make_plan(const mg_problem* probs, int nprob, const mg_options* o, Pla
   if (o->net_per_problem != 0 && o->net_per_problem != 1) return fail(MG_ERR_INVALID_ARG, "net_per_problem must be 0 or 1");
   if (o->tile_shape < MG_TILE_DEFAULT || o->tile_shape > MG_TILE_STRIP8x32)
     return fail(MG_ERR_INVALID_ARG, "unknown tile_shape %d", o->tile_shape);
-  P.shape = o->tile_shape == MG_TILE_DEFAULT ? MG_SHAPE_STRIP8x32 : o->tile_shape;
+  P.shape = o->tile_shape == MG_TILE_DEFAULT ? MG_SHAPE_TILE32 : o->tile_shape;
   if (o->net_per_problem && !(o->smoother == MG_SMOOTH_CNN && o->net_arch == MG_NET_LINEAR))
     return fail(MG_ERR_UNSUPPORTED, "per-problem parameter sets need the linear smoother (MG_NET_LINEAR)");
   const int n = probs[0].n;

@@ -16,7 +16,9 @@
 #define MG_TAIL_N 63          // levels at or below this size run in one CTA per problem
 #define MG_TAIL_SMEM_MAX (200 * 1024)  // dynamic shared memory limit of the tail kernels
 #define MG_CT_N 127           // levels at or below this size run in one CTA cluster per problem
+#ifndef MG_CT_SOLO
 #define MG_CT_SOLO 31         // ... and at or below this size in the cluster's first CTA alone
+#endif
 #ifndef MG_CT_C
 #define MG_CT_C 8             // CTAs per cluster (each owns a band of (n + 1) / MG_CT_C rows)
 #endif

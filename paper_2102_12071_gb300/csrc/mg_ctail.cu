@@ -29,8 +29,11 @@
 
 namespace mg {
 
+// threads per CTA of the cluster tail: 512 lets two CTAs share an SM, so the clusters of a
+// 16-problem batch and more are resident at once (with 1024 threads at most 14 clusters of
+// eight CTAs fit on the GPU and a 16-problem tail ran in two waves)
 #ifndef MG_CT_THREADS
-#define MG_CT_THREADS 1024
+#define MG_CT_THREADS 512
 #endif
 constexpr int CT_THREADS = MG_CT_THREADS;
 
