@@ -615,14 +615,21 @@ def run_mixed(args, rank, weights):
         ms = e0.elapsed_time(e1) / args.mixed_steps
         sweeps = 0.0
         groups = {}
+        times = mb.last_times_ms  # per problem, from the last timed solve (GPU timer stamps)
         for key, idx in mb.groups.items():
             sizes = mb.solvers[key].sizes
             sweeps += sum(sweeps_per_cycle(sizes) * int(cyc[i]) for i in idx)
+            ct, shape = mb.layout[key]
             groups[f"{key[0]}/{key[1]}"] = {"problems": len(idx), "median_cycles": float(np.median(cyc[idx])),
-                                            "max_cycles": int(cyc[idx].max()),
-                                            "cluster_tail": bool(mb.layout.get(key, True))}
+                                            "max_cycles": int(cyc[idx].max()), "cluster_tail": bool(ct),
+                                            "tile_shape": shape,
+                                            "median_ms_to_rtol": float(np.median(times[idx])),
+                                            "max_ms_to_rtol": float(np.max(times[idx]))}
         out[kind] = {"ms": ms, "ms_per_problem": ms / len(problems), "mdof_sweeps_per_s": sweeps / (ms / 1e3),
-                     "converged": int(st) == 0, "setup_and_first_solve_s": round(setup_s, 2), "groups": groups}
+                     "converged": int(st) == 0, "setup_and_first_solve_s": round(setup_s, 2), "groups": groups,
+                     "per_problem_ms_to_rtol": [round(float(v), 3) for v in times],
+                     "per_problem_cycles": [int(c) for c in cyc],
+                     "per_problem": [f"{p['n']}/{'field' if p['kind'] in (2, 3) else 'const'}" for p in problems]}
         mb.close()
         del mb
         torch.cuda.empty_cache()

@@ -395,6 +395,14 @@ mg_status mg_solve_small_static(const mg_problem* problems, int nprob, const mg_
    launched since the last reset (timing or not). */
 mg_status mg_profile_enable(mg_ctx* ctx, int enable);
 
+/* Per-problem timing of the last mg_solve or mg_solve_multi of ctx (the paper has no
+   counterpart; used to report time to tolerance in mixed batches): start_ns[p], the GPU
+   global timer in nanoseconds when the norm of b_p was formed at the start of the solve,
+   and done_ns[p], when the stopping test that ended problem p ran (0 if it had not ended).
+   Both HOST arrays of nprob entries; the timer is common to all SMs of the device, so
+   stamps of several contexts solved together compare directly.  Host-only. */
+mg_status mg_solve_times(const mg_ctx* ctx, unsigned long long* start_ns, unsigned long long* done_ns);
+
 /* Test setting for failure detection (the paper has no counterpart): with on != 0 the
    following solves and cycles of ctx make the first bounded wait for every tile's copies
    give up at once, so the expiry path runs: the wait for the copies still in flight keeps

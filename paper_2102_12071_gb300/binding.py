@@ -85,6 +85,7 @@ def lib() -> ctypes.CDLL:
                                                  _P, _P, _P, ctypes.c_double, ctypes.c_int, _P, _P, _P]),
         "mg_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
         "mg_debug_short_wait": (ctypes.c_int, [_P, ctypes.c_int]),
+        "mg_solve_times": (ctypes.c_int, [_P, _P, _P]),
         "mg_profile_read": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_longlong)]),
         "mg_rotated_stencil": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_float)]),
@@ -294,6 +295,16 @@ def mg_fgmres(ctx, b, x_hi, x_lo, restart, rtol, max_iters, workspace, ws_bytes,
 
 def mg_train_set_cycles(ctx, cycles: int) -> None:
     check(lib().mg_train_set_cycles(ctx, int(cycles)), "mg_train_set_cycles")
+
+
+def mg_solve_times(ctx, nprob: int):
+    """(start_ns, done_ns) numpy uint64 arrays of the last solve of ctx (see include/mgcnn.h)."""
+    import numpy as np
+
+    start = np.zeros(nprob, dtype=np.uint64)
+    done = np.zeros(nprob, dtype=np.uint64)
+    check(lib().mg_solve_times(ctx, start.ctypes.data, done.ctypes.data), "mg_solve_times")
+    return start, done
 
 
 def mg_debug_short_wait(ctx, on: bool) -> None:

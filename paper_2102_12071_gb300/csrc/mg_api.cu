@@ -890,6 +890,15 @@ mg_status mg_net_forward(int n, int nprob, const float* fields, const float* par
   return MG_OK;
 }
 
+mg_status mg_solve_times(const mg_ctx* ctx, unsigned long long* start_ns, unsigned long long* done_ns) {
+  if (!ctx || !start_ns || !done_ns) return fail(MG_ERR_INVALID_ARG, "mg_solve_times: bad arguments");
+  for (int p = 0; p < ctx->plan.nprob; ++p) {
+    start_ns[p] = ctx->h_state[p].t_start;
+    done_ns[p] = ctx->h_state[p].status != 0 ? ctx->h_state[p].t_done : 0ull;
+  }
+  return MG_OK;
+}
+
 mg_status mg_debug_short_wait(mg_ctx* ctx, int on) {
   if (!ctx) return fail(MG_ERR_INVALID_ARG, "mg_debug_short_wait: ctx is NULL");
   ctx->args.short_wait = on != 0;

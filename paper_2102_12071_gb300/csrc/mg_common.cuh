@@ -97,6 +97,9 @@ struct ProbState {
   unsigned int counter;  // last-CTA detection for the norm reduction
   int short_wait;        // test setting: nonzero makes the first wait for a tile's copies
                          // give up at once (mg_debug_short_wait); 0 in every normal solve
+  int pad_;
+  unsigned long long t_start;  // GPU global timer (ns) when the solve's norm of b was formed
+  unsigned long long t_done;   // ... when the stopping test ended this problem's iteration
   float hist[MG_HRING];  // hist[k % MG_HRING] = relative residual after k cycles
 };
 
@@ -106,6 +109,13 @@ struct ProbState {
 // stale; L2 is the point of coherence, so a .cg load sees the latest value once
 // griddepcontrol.wait has returned.
 __device__ __forceinline__ int st_active(const ProbState* st) { return __ldcg(&st->active); }
+
+// the GPU's global nanosecond timer (common to all SMs)
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 
 // ---------------------------------------------------------------- float-float

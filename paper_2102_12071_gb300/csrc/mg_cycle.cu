@@ -61,6 +61,7 @@ __global__ void __launch_bounds__(NT) k_bnorm(const ProbDev* __restrict__ probs,
       state[p].cycles = 0;
       state[p].status = 0;
       state[p].short_wait = short_wait;
+      state[p].t_start = global_ns();
     }
   }
 }

@@ -236,6 +236,9 @@ static cudaError_t fctc_prepare(int* ctas_per_sm) {
   if (dev < 0 || dev >= 64 || !done[dev]) {
     e = cudaFuncSetAttribute(k_fc_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FcTcSmem));
     if (e != cudaSuccess) return e;
+    // the whole unified L1 as shared memory, so that three CTAs fit on an SM
+    e = cudaFuncSetAttribute(k_fc_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) done[dev] = 1;
   }
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_fc_tc, FCTC_THREADS, sizeof(FcTcSmem));

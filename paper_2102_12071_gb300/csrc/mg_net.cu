@@ -235,6 +235,7 @@ static cudaError_t fwd_prepare() {
   if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
   e = cudaFuncSetAttribute(k_net_forward<NK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(FwdLayout<NK>::TOTAL * sizeof(float)));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_net_forward<NK>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = 1;
   return e;
 }

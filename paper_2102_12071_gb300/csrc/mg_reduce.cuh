@@ -91,6 +91,7 @@ __device__ __forceinline__ void decide(ProbState& st, float rr_hi, float rr_lo, 
     st.status = 2;
     st.active = 0;
   }
+  if (st.status != 0) st.t_done = global_ns();
 }
 
 }  // namespace mg

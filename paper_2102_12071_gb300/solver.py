@@ -165,38 +165,49 @@ class MixedBatchSolver:
     CUDA stream, and mg_solve_multi runs all groups' cycles at once.  net_params maps "const"
     and "field" to the network parameters of each kind (CNN smoother): one set, per-level
     sets, or a function of the group's side returning either.  With `autotune`, the
-    first solve times a few cycles of each coarse-level layout (one CTA cluster per problem
-    below 127, or one CTA below 63 with tiled kernels above) per group and keeps the faster.
+    first solve times a few cycles of every candidate layout per group -- the coarse-level
+    layout (one CTA cluster per problem below 127, or one CTA below 63 with tiled kernels
+    above) crossed with the tile shape of the tiled down-sweeps (`shapes`, names of
+    binding.TILE_SHAPES) -- and keeps the fastest; without it the first candidate is used.
+    After a solve, `last_times_ms[i]` is problem i's time to its stopping test, from the
+    start of the earliest group (GPU timer stamps, mg_solve_times).
     """
 
+    SHAPES = ("32x32", "strip4x32", "strip8x32")
+
     def __init__(self, problems: list[dict], smoother: str = "jacobi", net_params: dict | None = None,
-                 autotune: bool = True, tune_cycles: int = 16):
+                 autotune: bool = True, tune_cycles: int = 16, shapes=None, layouts=(True, False)):
         self.problems = problems
         self.smoother = smoother
         self.net_params = net_params or {}
         self.autotune = autotune
         self.tune_cycles = tune_cycles
+        self.shapes = tuple(shapes) if shapes else self.SHAPES
+        self.layouts = tuple(layouts)
+        self.last_times_ms = None
         self.groups: dict[tuple, list[int]] = {}
         for i, p in enumerate(problems):
             field = p["kind"] in (B.MG_PROBLEM_VARCOEF5, B.MG_PROBLEM_FIELD)
             self.groups.setdefault((p["n"], "field" if field else "const"), []).append(i)
         self.solvers: dict[tuple, MultigridSolver] = {}
         self.streams: dict[tuple, torch.cuda.Stream] = {key: torch.cuda.Stream() for key in self.groups}
-        self.layout: dict[tuple, bool] = {}
+        self.layout: dict[tuple, tuple] = {}  # group -> (cluster_tail, tile shape) in use
 
-    def _make(self, key, cluster_tail: bool) -> MultigridSolver:
+    def _make(self, key, cluster_tail: bool, shape: str) -> MultigridSolver:
         params = self.net_params.get(key[1]) if self.smoother == "cnn" else None
         if callable(params):  # per-level sets that depend on the hierarchy's size
             params = params(key[0])
         return MultigridSolver([self.problems[i] for i in self.groups[key]], self.smoother, net_params=params,
-                               stream=self.streams[key].cuda_stream, cluster_tail=cluster_tail)
+                               stream=self.streams[key].cuda_stream, cluster_tail=cluster_tail, tile_shape=shape)
 
     def _tune(self, key, b: torch.Tensor) -> MultigridSolver:
+        cands = [(ct, sh) for ct in self.layouts for sh in self.shapes]
         if not self.autotune or key[0] <= 63:  # <= 63: whole solves in one CTA, nothing to choose
-            return self._make(key, True)
+            self.layout[key] = cands[0]
+            return self._make(key, *cands[0])
         best = None
-        for ct in (True, False):
-            mg = self._make(key, ct)
+        for ct, sh in cands:
+            mg = self._make(key, ct, sh)
             with torch.cuda.stream(self.streams[key]):
                 for _ in range(2):
                     mg.solve(b, rtol=0.0, max_cycles=self.tune_cycles, history=False)
@@ -209,7 +220,7 @@ class MixedBatchSolver:
             if best is None or ms < best[0]:
                 if best is not None:
                     best[1].close()
-                best = (ms, mg, ct)
+                best = (ms, mg, (ct, sh))
             else:
                 mg.close()
         self.layout[key] = best[2]
@@ -234,10 +245,15 @@ class MixedBatchSolver:
                               [self.streams[k].cuda_stream for k in keys])
         x = [None] * len(self.problems)
         cycles = np.zeros(len(self.problems), dtype=np.int32)
+        stamps = {k: B.mg_solve_times(self.solvers[k].ctx, len(self.groups[k])) for k in keys}
+        t0 = min(int(stamps[k][0].min()) for k in keys)
+        self.last_times_ms = np.full(len(self.problems), np.nan)
         for k in keys:
             for j, i in enumerate(self.groups[k]):
                 x[i] = xh[k][j]
                 cycles[i] = cyc[k][j]
+                if stamps[k][1][j]:
+                    self.last_times_ms[i] = (int(stamps[k][1][j]) - t0) / 1e6
         return x, cycles, st
 
     def close(self):

@@ -4,6 +4,7 @@ Tolerances: per-cycle relative residual within 1e-5 relative; asymptotic converg
 factor within 1e-3; element-wise FP32 results within a few ulps of the stencil width.
 """
 import math
+import time
 
 import numpy as np
 import pytest
@@ -300,18 +301,28 @@ def _mixed_problems():
     return probs, b
 
 
-@pytest.mark.parametrize("autotune", [False, True])
-def test_solve_multi_matches_single_context_solves(autotune):
+@pytest.mark.parametrize("autotune,shapes", [(False, ("32x32",)), (False, ("strip8x32",)), (False, ("strip4x32",)),
+                                             (True, None)])
+def test_solve_multi_matches_single_context_solves(autotune, shapes):
     """mg_solve_multi over several contexts on their own streams gives, per problem, the
-    iterate and cycle count of a plain mg_solve of the same group (bit-identical)."""
+    iterate and cycle count of a plain mg_solve of the same group (bit-identical), with the
+    tile shapes fixed or chosen by the autotuner; every problem's time to its stopping test
+    is reported and lies inside the solve."""
     probs, b = _mixed_problems()
-    mb = S.MixedBatchSolver(probs, "jacobi", autotune=autotune, tune_cycles=4)
+    mb = S.MixedBatchSolver(probs, "jacobi", autotune=autotune, tune_cycles=4, shapes=shapes)
     assert sorted(mb.groups) == [(63, "const"), (127, "field"), (255, "const")]
-    x, cycles, st = mb.solve(b, rtol=1e-8, max_cycles=5000)
-    assert st == B.MG_OK, cycles
     torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x, cycles, st = mb.solve(b, rtol=1e-8, max_cycles=5000)
+    torch.cuda.synchronize()
+    wall_ms = 1e3 * (time.perf_counter() - t0)
+    assert st == B.MG_OK, cycles
+    assert np.all(mb.last_times_ms > 0) and np.all(mb.last_times_ms <= wall_ms), (mb.last_times_ms, wall_ms)
     for key, idx in mb.groups.items():
-        mg = S.MultigridSolver([probs[i] for i in idx], "jacobi", cluster_tail=mb.layout.get(key, True))
+        ct, shape = mb.layout[key]
+        if shapes and key[0] > 63:
+            assert shape == shapes[0]
+        mg = S.MultigridSolver([probs[i] for i in idx], "jacobi", cluster_tail=ct, tile_shape=shape)
         bb = torch.stack([b[i] for i in idx]).contiguous()
         xh, _, _, cyc, st1 = mg.solve(bb, rtol=1e-8, max_cycles=5000, history=False)
         assert st1 == B.MG_OK
