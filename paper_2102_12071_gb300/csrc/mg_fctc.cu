@@ -253,7 +253,10 @@ static cudaError_t fctc_launch(const NetJob* jobs, const NetBatch& batch, int np
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   const int ntiles = ((nmax + TCL - 1) / TCL) * ((nmax + TRW - 1) / TRW);
-  // persistent CTAs: as many as stay resident, spread over the jobs
+  // persistent CTAs: as many as shared memory lets stay resident (three per SM), spread over
+  // the jobs
+  const int fit = (int)((227u * 1024u) / sizeof(FcTcSmem));
+  per_sm = per_sm > fit ? per_sm : fit;
   int gx = (per_sm > 0 ? per_sm : 1) * sms / (nprob > 0 ? nprob : 1);
   gx = gx < 1 ? 1 : (gx > ntiles ? ntiles : gx);
   k_fc_tc<<<dim3(gx, nprob), FCTC_THREADS, sizeof(FcTcSmem), s>>>(jobs, batch, params, omega);
