@@ -41,6 +41,7 @@ BYTES_PER_DOF = {0: 16.0, 1: 9.0, 2: 33.0}
 # dram bytes (read + write) per launch of the current kernel versions from one ncu capture
 # of the 16 x 1023^2 batch; None where the kernel changed since its last capture
 NCU_TRAFFIC = {1: 67.14e6 + 40.54e6, 2: 353.70e6 + 175.88e6}
+NCU_TRAFFIC_SOURCE = {1: "profiles/k_down_level0_rotated1023x16.md", 2: "profiles/k_up0_rotated1023x16.md"}
 KERNEL_NAMES = {0: "k_residual (initial iterate)", 1: "k_down(level 0)", 2: "k_up0(level 0: up-sweep, x update, residual)",
                 3: "k_tail", 4: "k_down(l>=1)", 5: "k_up(l>=1)"}
 
@@ -226,10 +227,32 @@ def run_reference(args):
         "config": {"workload": f"rotated anisotropic Q1, {args.n}x{args.n}, V(1,1) Jacobi, bounded sample "
                                f"of {cycles} cycles on 1 of {args.nprob} problems", "n": args.n},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{cycles} V(1,1) cycles of one {args.n}^2 problem per step"},
+                         "sample": f"{cycles} V(1,1) cycles of one {args.n}^2 problem per step", **cpu_info()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def cpu_info():
+    """The host CPU's model name (from /proc/cpuinfo or lscpu) and its logical core count."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu model")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"cpu_model": model or "unknown", "nproc": os.cpu_count()}
 
 
 def cpu_baseline(n: int, budget_s: float = 12.0):
@@ -251,7 +274,7 @@ def cpu_baseline(n: int, budget_s: float = 12.0):
     mg.solve(bb, rtol=0.0, max_cycles=cycles)
     dt = time.perf_counter() - t0
     return {"value": sweeps_per_cycle(sizes) * cycles / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{cycles} V(1,1) Jacobi cycles of one {n}^2 problem (FP64, single thread)"}
+            "sample": f"{cycles} V(1,1) Jacobi cycles of one {n}^2 problem (FP64, single thread)", **cpu_info()}
 
 
 def load_varcoef_weights():
@@ -819,6 +842,8 @@ def main():
     traffic = NCU_TRAFFIC.get(dom) if (n, nprob) == (N_DEFAULT, NPROB_DEFAULT) else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
+                "traffic_source": (f"dram bytes read + written per launch from the ncu capture of "
+                                   f"{NCU_TRAFFIC_SOURCE[dom]}" if traffic is not None else None),
                 "kernel": KERNEL_NAMES[dom], "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": algo_bytes,
                 "launch_us": {KERNEL_NAMES[c]: round(1e3 * prof[c][0] / prof[c][1], 2) for c in prof if prof[c][1]},
