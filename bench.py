@@ -324,9 +324,11 @@ def run_varcoef(args, rank):
         cells = torch.from_numpy(inputs.grf_cells(inputs.SEED_GRF + rank, n)).cuda()
         b = torch.from_numpy(inputs.rhs_uniform(inputs.SEED_RHS + 500 + rank, n)).cuda()[None].contiguous()
         res = {}
-        arms = ["jacobi"] + (["cnn"] if wv is not None else []) + (["fc"] if wfc is not None else [])
+        # fc: the fully connected network in FP32; fc_bf16: in bfloat16, its inference on the
+        # tensor cores
+        arms = ["jacobi"] + (["cnn"] if wv is not None else []) + (["fc", "fc_bf16"] if wfc is not None else [])
         for kind in arms:
-            net = {"cnn": wv[1] if wv is not None else None, "fc": wfc}.get(kind)
+            net = {"cnn": wv[1] if wv is not None else None, "fc": wfc, "fc_bf16": wfc}.get(kind)
             # mg_setup (stencils, Galerkin hierarchy, coarsest factor and, for the network
             # arms, the per-point network on every smoothed level) timed on its own: the
             # network's cost belongs to the learned smoother
@@ -335,7 +337,8 @@ def run_varcoef(args, rank):
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 mg = S.MultigridSolver([S.varcoef5(n, cells)], "jacobi" if kind == "jacobi" else "cnn",
-                                       net_params=net, net_arch="fc" if kind == "fc" else "conv")
+                                       net_params=net, net_arch="fc" if kind.startswith("fc") else "conv",
+                                       conv_bf16=kind == "fc_bf16")
                 torch.cuda.synchronize()
                 setup_ms.append(1e3 * (time.perf_counter() - t0))
                 if rep == 0:

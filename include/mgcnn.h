@@ -112,7 +112,8 @@ typedef struct {
                            min(l, k - 1) (per-level smoothers H^(l), Algorithm 2)        */
   int smoother_transpose; /* 1: every level smooths with H^T instead of H (per-point
                            problems, or MG_NET_LINEAR: the chain reversed with mirrored
-                           kernels), so a V-cycle of this context applies M^T when the
+                           kernels, or MG_NET_CONV3: the stack reversed with each kernel
+                           transposed), so a V-cycle of this context applies M^T when the
                            context without it applies M: the adjoint coarse solve of
                            mg_train_step_coarse                                          */
   int net_arch;         /* MG_SMOOTH_CNN: mg_net_arch; parameter sets hold
@@ -157,8 +158,8 @@ typedef enum {
                       layer's input zero outside the grid (Sec. 4, Sec. 4.2: k = 3),
                       K1 = (omega delta + out_1)/D, K2 = delta + out_2, K3 = delta + out_3;
                       last layer wf[27][3][3][3] (row 9k + t: tap t of kernel k+1), 1 746
-                      params.  FP32 only, without smoother_transpose (so no
-                      mg_train_step_coarse); solve, V-cycle, FGMRES and mg_train_step;
+                      params.  FP32 only; solve, V-cycle, FGMRES, mg_train_step and
+                      (with smoother_transpose for the adjoint) mg_train_step_coarse;
                       mg_smoother_apply and mg_get_kernels refuse it.  Levels above 63
                       run in the batched level kernels.                                  */
   MG_NET_CONV_SHARED = 4 /* the network of MG_NET_CONV with one 3x3 kernel per output

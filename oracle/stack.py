@@ -109,9 +109,40 @@ def prolong(ec: torch.Tensor, n: int) -> torch.Tensor:
     return F.conv_transpose2d(ec[None, None], w[None, None], stride=2)[0, 0][:n, :n]
 
 
-def loss(st, coarse_st, params: torch.Tensor, z, omega: float = 2.0 / 3.0, cycles: int = 1) -> torch.Tensor:
+def coarse_vcycle(st_c, level_params, omega: float = 2.0 / 3.0):
+    """Algorithm 2's coarse solve: M, one V(1,1) cycle from zero (Algorithm 1) of the
+    Galerkin hierarchy of st_c, level l smoothed by the stack of network level_params[l]
+    (the last set below that) on that level's own field, FP64 direct solve on the
+    coarsest.  Returns M as a function of a torch right-hand side; it is linear in it, so
+    the adjoint M^T of the loss gradient is what autograd takes through it."""
+    from .oracle import dense_matrix, rap
+
+    sts = [_f64(st_c)]
+    while sts[-1].shape[1] > 3 and (sts[-1].shape[1] - 1) % 2 == 0:
+        sts.append(rap(sts[-1]))
+    sets = [_t(p) for p in level_params]
+    with torch.no_grad():
+        Ks = [kernels(s, sets[min(l, len(sets) - 1)], omega) for l, s in enumerate(sts[:-1])]
+    Ac = torch.from_numpy(dense_matrix(sts[-1]))
+
+    def level(l, f):
+        n = sts[l].shape[1]
+        if l == len(sts) - 1:
+            return torch.linalg.solve(Ac, f.reshape(-1)).reshape(n, n)
+        u = apply_H(Ks[l], f)                                   # pre-smoothing from u = 0
+        uc = level(l + 1, restrict(f - apply_A(sts[l], u)))     # restriction, coarse cycle
+        u = u + prolong(uc, n)                                  # prolongation
+        return u + apply_H(Ks[l], f - apply_A(sts[l], u))       # post-smoothing
+
+    return lambda rc: level(0, rc)
+
+
+def loss(st, coarse_st, params: torch.Tensor, z, omega: float = 2.0 / 3.0, cycles: int = 1,
+         coarse=None) -> torch.Tensor:
     """(1/Z) sum_j ||E^k z_j||^2 / n^2 with E = S C S, S = I - H A, C = I - P A_c^{-1} P^T A
-    (Sec. 3.2, eq. twogrid; A_c = P^T A P is given as the coarse field coarse_st)."""
+    (Sec. 3.2, eq. twogrid; A_c = P^T A P is given as the coarse field coarse_st).  With
+    `coarse` (a function of the coarse right-hand side, e.g. coarse_vcycle) A_c^{-1} is
+    replaced by it: Algorithm 2's objective at one level."""
     st = _t(st)
     n = st.shape[-1]
     nc = (n - 1) // 2
@@ -124,7 +155,8 @@ def loss(st, coarse_st, params: torch.Tensor, z, omega: float = 2.0 / 3.0, cycle
         for _ in range(cycles):
             e = e - apply_H(Ks, apply_A(st, e))
             rc = restrict(apply_A(st, e))
-            e = e - prolong(torch.linalg.solve(Ac, rc.reshape(-1)).reshape(nc, nc), n)
+            ec = coarse(rc) if coarse is not None else torch.linalg.solve(Ac, rc.reshape(-1)).reshape(nc, nc)
+            e = e - prolong(ec, n)
             e = e - apply_H(Ks, apply_A(st, e))
         total = total + (e * e).sum()
     return total / (z.shape[0] * n * n)
@@ -144,9 +176,9 @@ def _dense(st) -> torch.Tensor:
     return A
 
 
-def loss_and_grad(st, coarse_st, params, z, omega: float = 2.0 / 3.0, cycles: int = 1):
+def loss_and_grad(st, coarse_st, params, z, omega: float = 2.0 / 3.0, cycles: int = 1, coarse=None):
     p = _t(params).clone().requires_grad_(True)
-    L = loss(st, coarse_st, p, z, omega, cycles)
+    L = loss(st, coarse_st, p, z, omega, cycles, coarse)
     (g,) = torch.autograd.grad(L, p)
     return float(L.detach()), g.numpy()
 

@@ -75,8 +75,8 @@ mg_status make_plan(const mg_problem* probs, int nprob, const mg_options* o, Pla
   if (o->net_arch != MG_NET_CONV && o->net_arch != MG_NET_FC && o->net_arch != MG_NET_LINEAR &&
       o->net_arch != MG_NET_CONV3 && o->net_arch != MG_NET_CONV_SHARED)
     return fail(MG_ERR_INVALID_ARG, "unknown net_arch");
-  if (o->smoother == MG_SMOOTH_CNN && o->net_arch == MG_NET_CONV3 && (o->smoother_transpose || o->conv_bf16))
-    return fail(MG_ERR_UNSUPPORTED, "the three-kernel network runs in FP32 and without smoother_transpose");
+  if (o->smoother == MG_SMOOTH_CNN && o->net_arch == MG_NET_CONV3 && o->conv_bf16)
+    return fail(MG_ERR_UNSUPPORTED, "the three-kernel network runs in FP32");
   if (o->net_per_problem != 0 && o->net_per_problem != 1) return fail(MG_ERR_INVALID_ARG, "net_per_problem must be 0 or 1");
   if (o->tile_shape < MG_TILE_DEFAULT || o->tile_shape > MG_TILE_STRIP8x32)
     return fail(MG_ERR_INVALID_ARG, "unknown tile_shape %d", o->tile_shape);
@@ -286,7 +286,9 @@ static size_t carve(const Plan& P, const mg_options& o, void* base, mg_ctx* ctx)
   int* active = c.take<int>(P.nprob);
   NetJob* jobs = c.take<NetJob>((size_t)P.nprob * P.L);
   // scratch for the transposition of one problem's level-0 kernels (smoother_transpose)
-  float* tscr = (o.smoother_transpose && P.hk == HK_FIELD) ? c.take<float>((size_t)9 * P.n0 * P.n0) : nullptr;
+  float* tscr = (o.smoother_transpose && (P.hk == HK_FIELD || P.hk == HK_STACK3))
+                    ? c.take<float>((size_t)(P.hk == HK_STACK3 ? 27 : 9) * P.n0 * P.n0)
+                    : nullptr;
   // the linear smoother: its weights per level (shared by all problems) and three scratch
   // vectors of level-0 size for the chain and the up-sweep residual
   const int lin_lev = P.L > 1 ? P.L - 1 : 1, lin_groups = o.net_per_problem ? P.nprob : 1;
@@ -532,6 +534,9 @@ mg_status mg_setup(const mg_problem* problems, int nprob, const mg_options* opts
         CK(launch_net_forward3(ctx->d_jobs + (size_t)l * nprob, nprob, P.nl[l], net_params + (size_t)set * MG_NPARAMS_K3,
                                opts->omega, s));
       }
+      if (opts->smoother_transpose)  // H^T = K1^T K2^T K3^T on every level
+        for (int p = 0; p < nprob; ++p)
+          for (int l = 0; l + 1 < P.L; ++l) CK(launch_transpose_stack(ctx->h_probs[p].lv[l].W, P.nl[l], ctx->tscratch, s));
       CK(cudaStreamSynchronize(s));  // the host vector must outlive the asynchronous copy
     } else if (P.hk != HK_JACOBI && P.L > 1) {
       // jobs level-major, so that every level can take its own parameter set

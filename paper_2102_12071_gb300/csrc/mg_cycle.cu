@@ -379,6 +379,26 @@ cudaError_t launch_transpose_kernels(float* W, int n, float* scratch, cudaStream
   return cudaMemcpyAsync(W, scratch, sizeof(float) * cnt, cudaMemcpyDeviceToDevice, s);
 }
 
+// The kernels of the stack H = K3 K2 K1 transposed: H^T = K1^T K2^T K3^T, stored in the
+// order the stack is applied (first block first), so out = (K3^T, K2^T, K1^T) with each
+// block transposed as above; W holds the three blocks [27][n][n].
+__global__ void k_transpose_stack(const float* __restrict__ W, float* __restrict__ out, int n) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nn = n * n;
+  if (q >= 27 * nn) return;
+  const int b = q / (9 * nn), r = q % (9 * nn), k = r / nn, y = r % nn, i = y / n, j = y % n;
+  const int ii = i + k / 3 - 1, jj = j + k % 3 - 1;
+  out[q] = in_grid(ii, jj, n) ? W[(size_t)(2 - b) * 9 * nn + (size_t)(8 - k) * nn + ii * n + jj] : 0.f;
+}
+
+cudaError_t launch_transpose_stack(float* W, int n, float* scratch, cudaStream_t s) {
+  const int cnt = 27 * n * n;
+  k_transpose_stack<<<(cnt + 255) / 256, 256, 0, s>>>(W, scratch, n);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyAsync(W, scratch, sizeof(float) * cnt, cudaMemcpyDeviceToDevice, s);
+}
+
 cudaError_t launch_level_residual(const CycleArgs& a, int p, int l, const float* f, const float* u) {
   const int n = a.nl[l];
   const int nb = (n * n + 255) / 256;

@@ -225,6 +225,9 @@ cudaError_t prepare_tail(const CycleArgs& a);
 cudaError_t launch_tail_vec(const CycleArgs& a, const float* rin, float* xout, int nvec);
 // W (9 x n x n per-point kernels) <- its transpose's kernels, through scratch (9 x n x n)
 cudaError_t launch_transpose_kernels(float* W, int n, float* scratch, cudaStream_t s);
+// the three-kernel stack's fields [27][n][n] <- those of its transpose (blocks reversed, each
+// transposed), through scratch (27 x n x n)
+cudaError_t launch_transpose_stack(float* W, int n, float* scratch, cudaStream_t s);
 bool ctx_tail_args(const ::mg_ctx* ctx, CycleArgs* a);
 void ctx_args(const ::mg_ctx* ctx, CycleArgs* a);
 cudaError_t launch_tail_solve(const CycleArgs& a, const float* b, float* xhi, float* xlo, float rtol, int max_cycles,

@@ -106,6 +106,59 @@ def test_stack_train_step_matches_oracle(n, cycles):
     assert np.linalg.norm(g[-18 * 27:] - go[-18 * 27:]) <= 1e-4 * np.linalg.norm(go[-18 * 27:])
 
 
+@pytest.mark.parametrize("n,cycles", [(15, 1), (31, 1), (31, 2)])
+def test_stack_vcycle_coarse_train_step_matches_oracle(n, cycles):
+    """Algorithm 2 with the three-kernel stack: the two-grid objective whose coarse solve is
+    one V-cycle of the hierarchy below smoothed by (already trained) stack networks, and
+    its adjoint through the cycle with every stack transposed (smoother_transpose: K1^T
+    K2^T K3^T) -- loss and gradient against the oracle, whose adjoint is FP64 autograd
+    through its own coarse cycle."""
+    nprob, nvec = 2, 3
+    params = inputs.rotated_params(170 + n + cycles, nprob)
+    probs = [{"n": n, "kind": B.MG_PROBLEM_ROTATED, "eps": e, "theta": t} for e, t in params]
+    z = inputs.gaussian_vectors(171 + n + cycles, nprob * nvec, n).reshape(nprob, nvec, n, n)
+    p = stack_params(25, last=0.05)
+    sets = np.stack([stack_params(26 + j, last=0.05) for j in range(2)])
+    batch = T.TwoGridBatch(probs, nvec, 2.0 / 3.0, False, cycles=cycles, net_arch="conv3")
+    batch.attach_coarse(torch.from_numpy(sets).cuda())
+    loss, grad = batch.loss_and_grad(torch.from_numpy(p).cuda(), torch.from_numpy(z).cuda().contiguous())
+    batch.close()
+    lo, go = 0.0, np.zeros(p.size)
+    for k, (e, t) in enumerate(params):
+        st = O.const_field(n, f32(O.q1_rotated_stencil(e, t)))
+        st_c = O.rap(st)
+        l1, g1 = OS.loss_and_grad(st, st_c, f32(p), f32(z[k]), cycles=cycles,
+                                  coarse=OS.coarse_vcycle(st_c, [f32(q) for q in sets]))
+        lo += l1 / nprob
+        go += g1 / nprob
+    assert abs(loss.item() - lo) <= 1e-5 * lo, (loss.item(), lo)
+    g = grad.double().cpu().numpy()
+    assert np.linalg.norm(g - go) <= 1e-4 * np.linalg.norm(go), np.linalg.norm(g - go) / np.linalg.norm(go)
+
+
+def test_stack_transposed_context_applies_the_adjoint_cycle():
+    """A context built with smoother_transpose applies M^T: <M u, v> = <u, M^T v> for one
+    V-cycle from zero of a 63^2 per-point problem with the stack smoother."""
+    n = 63
+    cells = torch.from_numpy(inputs.grf_cells(inputs.SEED_GRF + 90, n)).cuda()
+    p = torch.from_numpy(stack_params(27, last=0.05)).cuda()
+    mgs = [S.MultigridSolver([S.varcoef5(n, cells)], "cnn", p, net_arch="conv3", transpose=t) for t in (False, True)]
+    rng = np.random.default_rng(28)
+    u = torch.from_numpy(rng.standard_normal((1, n, n)).astype(np.float32)).cuda()
+    v = torch.from_numpy(rng.standard_normal((1, n, n)).astype(np.float32)).cuda()
+    outs = []
+    for mg, rhs in zip(mgs, (u, v)):
+        xh, xl = torch.zeros_like(rhs), torch.zeros_like(rhs)
+        mg.vcycle(rhs.contiguous(), xh, xl)
+        outs.append(xh.double() + xl.double())
+        mg.close()
+    lhs = (outs[0] * v.double()).sum().item()
+    rhs_ = (u.double() * outs[1]).sum().item()
+    # FP32 cycles: the two inner products agree to a few FP32 roundings of the vectors' size
+    scale = (outs[0].norm() * v.double().norm()).item()
+    assert abs(lhs - rhs_) <= 1e-5 * scale, (lhs, rhs_, scale)
+
+
 def test_stack_trainer_reduces_the_loss():
     tr = T.Trainer(sizes=(15,), per_size=8, nvec=8, lr=3e-3, net_arch="conv3", conv_bf16=False)
     assert tr.params.numel() == OS.NPARAMS

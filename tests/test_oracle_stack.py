@@ -160,3 +160,58 @@ def test_loss_is_the_dense_error_propagation_of_the_stack(cycles):
     ref = np.mean([np.sum((E @ zj.ravel()) ** 2) for zj in z]) / (n * n)
     L = float(OS.loss(st, stc, torch.from_numpy(p), z, cycles=cycles))
     assert math.isclose(L, ref, rel_tol=1e-11), (L, ref)
+
+
+def test_algorithm2_objective_at_the_k1_point_equals_the_c_oracle():
+    """Algorithm 2's objective with the stack (coarse solve = one V-cycle of stack smoothers
+    on the coarse hierarchy, its adjoint by autograd) at the k = 1 point, where every stack
+    is the k = 1 network's kernel: loss and gradient equal the C oracle's vcycle objective,
+    whose adjoint is the explicitly transposed-kernel cycle."""
+    n = 31
+    st = O.const_field(n, O.q1_rotated_stencil(0.1, 1.1))
+    st_c = O.rap(st)
+    z = _rng(11).standard_normal((2, n, n))
+    p = _params(12, scale=0.05, zero_rest=True)
+    sets = [_params(13 + j, scale=0.05, zero_rest=True) for j in range(2)]
+    L, g = OS.loss_and_grad(st, st_c, p, z, coarse=OS.coarse_vcycle(st_c, sets))
+    mgc = O.Multigrid(st_c)
+    ker = [O.hypernet_forward(mgc.field(j), OS.k1_params(sets[min(j, 1)])) for j in range(mgc.levels - 1)]
+    Lc, gc = O.vcycle_cnn_loss_and_grad(st, OS.k1_params(p), O.coarse_vcycle(st_c, ker),
+                                        O.coarse_vcycle(st_c, ker, transpose=True), z)
+    assert math.isclose(L, Lc, rel_tol=1e-10)
+    assert np.allclose(OS.k1_params(g), gc, rtol=1e-7, atol=1e-11 * np.abs(gc).max())
+
+
+def test_coarse_vcycle_is_the_stack_multigrid_cycle_and_exact_on_the_coarsest():
+    """The torch coarse V-cycle against the numpy StackMultigrid cycle from zero (general
+    stack), and, on a coarse grid that is the coarsest (side 3), the exact solve: there
+    Algorithm 2's objective is the two-grid one."""
+    nc = 15
+    st_c = O.varcoef5_field(nc, np.exp(_rng(14).standard_normal((nc + 1, nc + 1))))
+    p = _params(15, scale=0.1)
+    r = _rng(16).standard_normal((nc, nc))
+    got = OS.coarse_vcycle(st_c, [p])(torch.from_numpy(r)).numpy()
+    want = OS.StackMultigrid(st_c, p).vcycle(r, np.zeros_like(r))
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-12 * np.abs(want).max())
+    n = 7
+    st = O.const_field(n, O.q1_rotated_stencil(0.3, 0.4))
+    z = _rng(17).standard_normal((2, n, n))
+    q = _params(18, scale=0.1)
+    L1 = OS.loss(st, O.rap(st), torch.from_numpy(q), z, coarse=OS.coarse_vcycle(O.rap(st), [q])).item()
+    L0 = OS.loss(st, O.rap(st), torch.from_numpy(q), z).item()
+    assert math.isclose(L1, L0, rel_tol=1e-12)
+
+
+def test_algorithm2_gradient_matches_central_differences():
+    n = 15
+    st = O.varcoef5_field(n, np.exp(0.5 * _rng(19).standard_normal((n + 1, n + 1))))
+    st_c = O.rap(st)
+    z = _rng(20).standard_normal((2, n, n))
+    p = _params(21, scale=0.1)
+    cv = OS.coarse_vcycle(st_c, [_params(22, scale=0.1)])
+    _, g = OS.loss_and_grad(st, st_c, p, z, coarse=cv)
+    d = _rng(23).standard_normal(p.size)
+    h = 1e-6
+    lp = OS.loss(st, st_c, torch.from_numpy(p + h * d), z, coarse=cv).item()
+    lm = OS.loss(st, st_c, torch.from_numpy(p - h * d), z, coarse=cv).item()
+    assert math.isclose((lp - lm) / (2 * h), g @ d, rel_tol=1e-6)
