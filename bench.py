@@ -664,6 +664,32 @@ def run_mixed(args, rank, weights):
     return out
 
 
+def run_profile_network(args):
+    """Network inference only (for profiler captures): the convolutional network in FP32 and
+    the fully connected one in bfloat16 (tensor cores) on the GRF field of side
+    args.profile_network, three launches each."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2102_12071_gb300 import binding as B, inputs, solver as S
+
+    n = args.profile_network
+    cells = torch.from_numpy(inputs.grf_cells(inputs.SEED_GRF, n)).cuda()
+    mg = S.MultigridSolver([S.varcoef5(n, cells)], "jacobi")
+    field = mg.stencil_field(0, 0)[None].contiguous()
+    mg.close()
+    W = torch.empty_like(field)
+    wv = load_varcoef_weights()
+    wfc = torch.from_numpy(np.load(os.path.join(os.path.dirname(WEIGHTS), "fc_varcoef.npy")).astype(np.float32)).cuda()
+    for _ in range(3):
+        B.mg_net_forward(n, 1, field, wv[1], 2.0 / 3.0, 0, W)
+        B.mg_net_fc_forward(n, 1, field, wfc, 2.0 / 3.0, 1, W)
+    torch.cuda.synchronize()
+
+
 def run_profile_case(args):
     """Set up the benchmark batch and run a fixed number of single V-cycles (mg_vcycle:
     residual, cycle, residual), nothing else: every launch does work (profiler captures)."""
@@ -687,7 +713,8 @@ def run_profile_case(args):
         mg = S.MultigridSolver(problems, "cnn", lin.cuda(), net_arch="linear", per_problem=True)
     else:
         kind = args.smoother if args.smoother != "auto" else ("cnn" if w is not None else "jacobi")
-        mg = S.MultigridSolver(problems, kind, net_params=w.cuda() if kind == "cnn" else None)
+        mg = S.MultigridSolver(problems, kind, net_params=w.cuda() if kind == "cnn" else None,
+                               tile_shape=args.tile_shape)
     b = torch.from_numpy(b_host).cuda().contiguous()
     x_hi, x_lo = torch.zeros_like(b), torch.zeros_like(b)
     for _ in range(args.profile_cycles):
@@ -709,6 +736,9 @@ def main():
     ap.add_argument("--roofline-cycles", type=int, default=20)
     ap.add_argument("--profile-cycles", type=int, default=0,
                     help="only set up the batch and run this many single V-cycles (for profiler captures)")
+    ap.add_argument("--profile-network", type=int, default=0,
+                    help="only run the network inference kernels three times on a GRF field of this side")
+    ap.add_argument("--tile-shape", default="32x32", help="profile case: tile shape of the tiled down-sweeps")
     ap.add_argument("--smoother", default="auto", choices=["auto", "jacobi", "cnn", "linear"],
                     help="profile case: the smoother (linear: the per-problem linear smoothers of the batch)")
     ap.add_argument("--varcoef-n", default="1023,4095", help="sides of the GRF problems, comma list (0: skip)")
@@ -718,6 +748,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_network:
+        return run_profile_network(args)
     if args.profile_cycles:
         return run_profile_case(args)
 
