@@ -14,7 +14,8 @@
 //   k_down(l)   e = H r, s = r - A e, r_{l+1} = P^T s         (Algorithm 1, pre-smoothing and restriction)
 //   k_up(l)     e1 = e + P e_{l+1}, e = e1 + H (r - A e1)      (Algorithm 1, correction and post-smoothing);
 //               on level 0 (k_up0) the correction is added to the float-float iterate and the
-//               next residual and stopping test follow in the same kernel.
+//               next residual and stopping test follow in the same kernel; k_up0p does the
+//               same on constant stencils with two columns per thread in packed FP32.
 //   k_update_residual  x += e_0 and the compensated residual with the stopping test, for
 //               cycles whose up-sweep ran in the batched level kernels (mg_linear.cu).
 #include <cudaTypedefs.h>
@@ -465,18 +466,28 @@ __device__ __forceinline__ void up0_tile(const LevelDev& L, const float (&s)[9],
                                          float* xh, float* xl, int R0, int C0) {
   const int n = L.n, t = threadIdx.x;
   {
-    constexpr int W1 = TB + 6, KS = 7, NS = (W1 + KS - 1) / KS;
+    // e1 = e + P e_c in strips of 8 fine rows starting on even offsets: strip s8 reads
+    // coarse rows 4 s8 .. 4 s8 + 4, so every row index below is a compile-time constant
+    constexpr int W1 = TB + 6, KS = 8, NS = (W1 + KS - 1) / KS;
     if (t < W1 * NS) {
-      const int tj = t % W1, t0 = (t / W1) * KS, j = C0 - 3 + tj;
-      const int I0 = R0 / 2 - 2, J0 = C0 / 2 - 4;
+      const int tj = t % W1, s8 = t / W1, j = C0 - 3 + tj;
+      const int J0 = C0 / 2 - 4;
       const int ja = ((j - 1) >> 1) - J0, jb = (j >> 1) - J0;
+      const float* cb = ecs + 4 * s8 * EC_W;
+      float* ep = es + 8 * s8 * XW + tj + 1;
+      if (s8 < NS - 1) {
 #pragma unroll
-      for (int k = 0; k < KS; ++k) {
-        const int ti = t0 + k, i = R0 - 3 + ti;
-        if (ti < W1) {
-          const float* ra = ecs + (((i - 1) >> 1) - I0) * EC_W;
-          const float* rb = ecs + ((i >> 1) - I0) * EC_W;
-          es[ti * XW + tj + 1] += 0.25f * ((ra[ja] + ra[jb]) + (rb[ja] + rb[jb]));
+        for (int k = 0; k < KS; ++k) {
+          const float* ra = cb + (k >> 1) * EC_W;
+          const float* rb = cb + ((k + 1) >> 1) * EC_W;
+          ep[k * XW] += 0.25f * ((ra[ja] + ra[jb]) + (rb[ja] + rb[jb]));
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < W1 - KS * (NS - 1); ++k) {
+          const float* ra = cb + (k >> 1) * EC_W;
+          const float* rb = cb + ((k + 1) >> 1) * EC_W;
+          ep[k * XW] += 0.25f * ((ra[ja] + ra[jb]) + (rb[ja] + rb[jb]));
         }
       }
     }
@@ -588,6 +599,361 @@ __global__ void __launch_bounds__(NT, SK == SK_CONST ? 8 : 4) k_up0(const __grid
                        : residual_tile<SK, false>(L, s, xh, xl, nullptr, R0, C0, rnew + po, xhi + po, xlo + po, b0 + po);
   float rhi, rlo;
   if (block_partial_and_last<NT>(acc, partials + (size_t)p * ntiles_max, &state[p].counter, ntiles, tile, rhi, rlo)) {
+    if (threadIdx.x == 0) decide(state[p], rhi, rlo, rtol, max_cycles);
+  }
+}
+
+// ------------------------------------------------------------ k_up0 in pairs
+// The constant-stencil level-0 kernel with two adjacent columns per thread (128 threads per
+// 32 x 32 tile, the same copies and phases as k_up0).  A pair's two values share one
+// 64-bit register pair and every arithmetic step is one packed FP32 instruction (add, mul,
+// fma on .f32x2; each lane rounded exactly as the scalar instruction), and the four columns
+// c-1 .. c+2 of a window row around the pair (c, c+1) are two aligned 64-bit shared loads
+// when c is odd.  Half the threads with twice the registers each keep 8 CTAs per SM.
+constexpr int NTP = 128;
+
+__device__ __forceinline__ float2 p2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 ng2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, ng2(b)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+__device__ __forceinline__ void st2(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
+
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
+  s = add2(a, b);
+  const float2 bb = sub2(s, a);
+  e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum2(float2 a, float2 b, float2& s, float2& e) {
+  s = add2(a, b);
+  e = sub2(b, sub2(s, a));
+}
+// dot2_sub on a pair: hi + lo -= a (x + xl)
+__device__ __forceinline__ void dot2_sub2(float a, float2 x, float2 xl, float2& hi, float2& lo) {
+  const float2 pr = mul2(p2(a), x);
+  const float2 pe = fma2(p2(a), x, ng2(pr));
+  float2 sum, err;
+  two_sum2(hi, ng2(pr), sum, err);
+  hi = sum;
+  lo = add2(lo, sub2(err, pe));
+  lo = fma2(p2(-a), xl, lo);
+}
+
+// Three rows of the columns c-1 .. c+2 around the pair (c, c+1): l = (c-1, c), m = (c, c+1),
+// r = (c+1, c+2) of rows a, b, c, the left, centre and right operands of the pair's stencil.
+struct Win2 {
+  float2 la, ma, ra, lb, mb, rb, lc, mc, rc;
+  __device__ __forceinline__ void shift() {
+    la = lb; ma = mb; ra = rb;
+    lb = lc; mb = mc; rb = rc;
+  }
+};
+// one window row; p points at column c-1, which is even (c odd): two aligned loads
+__device__ __forceinline__ void row_odd(const float* p, float2& l, float2& m, float2& r) {
+  const float2 u = ld2(p), w = ld2(p + 2);
+  l = u;
+  r = w;
+  m = make_float2(u.y, w.x);
+}
+// one window row; p points at column c, which is even: one aligned and two single loads
+__device__ __forceinline__ void row_even(const float* p, float2& l, float2& m, float2& r) {
+  const float2 u = ld2(p);
+  const float a = p[-1], b = p[2];
+  l = make_float2(a, u.x);
+  m = u;
+  r = make_float2(u.y, b);
+}
+// sum of w_k v_k for both points, centre first (the order of dot9)
+__device__ __forceinline__ float2 dot9p(const float (&w)[9], const Win2& v) {
+  float2 acc = mul2(p2(w[4]), v.mb);
+  acc = fma2(p2(w[0]), v.la, acc);
+  acc = fma2(p2(w[1]), v.ma, acc);
+  acc = fma2(p2(w[2]), v.ra, acc);
+  acc = fma2(p2(w[3]), v.lb, acc);
+  acc = fma2(p2(w[5]), v.rb, acc);
+  acc = fma2(p2(w[6]), v.lc, acc);
+  acc = fma2(p2(w[7]), v.mc, acc);
+  acc = fma2(p2(w[8]), v.rc, acc);
+  return acc;
+}
+// the scalar window of one point of the pair (lane 0: column c, lane 1: column c+1)
+__device__ __forceinline__ Win lane_win(const Win2& v, int lane) {
+  Win w;
+  w.a0 = lane ? v.la.y : v.la.x; w.a1 = lane ? v.ma.y : v.ma.x; w.a2 = lane ? v.ra.y : v.ra.x;
+  w.b0 = lane ? v.lb.y : v.lb.x; w.b1 = lane ? v.mb.y : v.mb.x; w.b2 = lane ? v.rb.y : v.rb.x;
+  w.c0 = lane ? v.lc.y : v.lc.x; w.c1 = lane ? v.mc.y : v.mc.x; w.c2 = lane ? v.rc.y : v.rc.x;
+  return w;
+}
+// H v for the pair at (i, j), (i, j+1): Jacobi, or the interior kernel on inner tiles, else
+// each point's class kernel (points outside the grid have no class: 0 there)
+template <int HK, bool IN>
+__device__ __forceinline__ float2 tapply_H2(const LevelDev& L, const float (&s)[9], const float* wtab,
+                                            const float (&wi)[9], float omega, int i, int j, const Win2& v) {
+  if (HK == HK_JACOBI) return mul2(p2(omega / s[4]), v.mb);
+  if (IN) return dot9p(wi, v);
+  float2 h = p2(0.f);
+  if (inside(i, j, L.n)) h.x = tapply_H<SK_CONST, HK, false>(L, s, wtab, wi, omega, i, j, lane_win(v, 0));
+  if (inside(i, j + 1, L.n)) h.y = tapply_H<SK_CONST, HK, false>(L, s, wtab, wi, omega, i, j + 1, lane_win(v, 1));
+  return h;
+}
+
+// Work item of thread t in a phase over NQ pairs and NS row strips: pairs 0 .. 15 first, one
+// strip per half-warp (16 consecutive pairs of a row: conflict-free 64-bit shared accesses),
+// then pairs 16 .. NQ-1 of every strip; false for the threads left idle.
+template <int NQ, int NS>
+__device__ __forceinline__ bool chunk_item(int t, int& q, int& strip) {
+  if (t < 16 * NS) {
+    q = t & 15;
+    strip = t >> 4;
+    return true;
+  }
+  t -= 16 * NS;
+  if (t < (NQ - 16) * NS) {
+    q = 16 + t % (NQ - 16);
+    strip = t / (NQ - 16);
+    return true;
+  }
+  return false;
+}
+
+// zero the lanes of a pair that lie outside the grid (edge tiles)
+__device__ __forceinline__ float2 mask2(float2 v, int i, int j, int n) {
+  if (!inside(i, j, n)) v.x = 0.f;
+  if (!inside(i, j + 1, n)) v.y = 0.f;
+  return v;
+}
+
+template <int HK, bool IN>
+__device__ __forceinline__ void up0p_tile(const LevelDev& L, const float (&s)[9], const float* wtab,
+                                          const float (&wi)[9], float omega, float* es, float* rs, const float* ecs,
+                                          float* xh, float* xl, int R0, int C0) {
+  const int n = L.n, t = threadIdx.x;
+  {
+    // e1 = e + P e_c on rows R0-3 .. R0+34 and the whole box width: pair q is box columns
+    // 2q, 2q+1 (grid columns C0-4+2q, even, and the odd one after it), whose bilinear
+    // weights read coarse box columns (q+1, q+2) and (q+2, q+2).  Strips of 8 fine rows
+    // from even offsets read coarse rows 4 s .. 4 s + 4 (a coarse row pair sum serves two
+    // fine rows).
+    constexpr int NQ = XW / 2, KS = 8, NS = (UP0E_H + KS - 1) / KS, LAST = UP0E_H - KS * (NS - 1);
+    if (t < NQ * NS) {
+      const int q = t % NQ, s8 = t / NQ;
+      const float* cb = ecs + 4 * s8 * EC_W + q + 1;
+      float* ep = es + 8 * s8 * XW + 2 * q;
+      float2 S[KS / 2 + 1];
+      if (s8 < NS - 1) {
+#pragma unroll
+        for (int m = 0; m <= KS / 2; ++m) {
+          const float a = cb[m * EC_W], b = cb[m * EC_W + 1];
+          S[m] = add2(make_float2(a, b), p2(b));
+        }
+#pragma unroll
+        for (int k = 0; k < KS; ++k) st2(ep + k * XW, fma2(p2(0.25f), add2(S[k >> 1], S[(k + 1) >> 1]), ld2(ep + k * XW)));
+      } else {
+#pragma unroll
+        for (int m = 0; m <= LAST / 2; ++m) {
+          const float a = cb[m * EC_W], b = cb[m * EC_W + 1];
+          S[m] = add2(make_float2(a, b), p2(b));
+        }
+#pragma unroll
+        for (int k = 0; k < LAST; ++k) st2(ep + k * XW, fma2(p2(0.25f), add2(S[k >> 1], S[(k + 1) >> 1]), ld2(ep + k * XW)));
+      }
+    }
+  }
+  __syncthreads();
+  {
+    // t = r - A e1 on rows R0-2 .. R0+33, box columns 1 .. 38 (pair q: 2q+1, 2q+2), 9-row strips
+    constexpr int NQ = (XW - 2) / 2, KS = 9, NS = UP0R_H / KS;
+    static_assert(KS * NS == UP0R_H && 16 * NS + (NQ - 16) * NS <= NTP, "phase t");
+    int q, sb;
+    if (chunk_item<NQ, NS>(t, q, sb)) {
+      const int t0 = sb * KS, j = C0 - 3 + 2 * q;
+      const float* c = es + t0 * XW + 2 * q;  // column 2q = c-1 of row t0 (window row a)
+      float* rp = rs + t0 * XW + 2 * q + 1;
+      Win2 v;
+      row_odd(c, v.la, v.ma, v.ra);
+      row_odd(c + XW, v.lb, v.mb, v.rb);
+#pragma unroll
+      for (int k = 0; k < KS; ++k) {
+        row_odd(c + (k + 2) * XW, v.lc, v.mc, v.rc);
+        float2 tv = sub2(make_float2(rp[k * XW], rp[k * XW + 1]), dot9p(s, v));
+        if (!IN) tv = mask2(tv, R0 - 2 + t0 + k, j, n);
+        rp[k * XW] = tv.x;
+        rp[k * XW + 1] = tv.y;
+        v.shift();
+      }
+    }
+  }
+  __syncthreads();
+  {
+    // e = e1 + H t and the float-float update of x on rows R0-1 .. R0+32, box columns
+    // 2 .. 37 (pair q: 2q+2, 2q+3; the residual reads 3 .. 36), 5-row strips; outside the
+    // grid x keeps its zero
+    constexpr int NQ = (TB + 4) / 2, KS = 5, NS = (RES_H + KS - 1) / KS;
+    static_assert(16 * NS + (NQ - 16) * NS <= NTP, "phase e");
+    int q, sc;
+    if (chunk_item<NQ, NS>(t, q, sc)) {
+      const int t0 = sc * KS, j = C0 - 2 + 2 * q;
+      const float* c = rs + t0 * XW + 2 * q + 2;  // column c of window row a
+      const float* e1 = es + (t0 + 2) * XW + 2 * q + 2;
+      float* ph = xh + t0 * XW + 2 * q + 2;
+      float* pl = xl + t0 * XW + 2 * q + 2;
+      Win2 v;
+      if (HK != HK_JACOBI) {
+        row_even(c, v.la, v.ma, v.ra);
+        row_even(c + XW, v.lb, v.mb, v.rb);
+      }
+#pragma unroll
+      for (int k = 0; k < KS; ++k) {
+        const int ti = t0 + k, i = R0 - 1 + ti;
+        if (ti < RES_H) {
+          if (HK != HK_JACOBI) row_even(c + (k + 2) * XW, v.lc, v.mc, v.rc);
+          else v.mb = ld2(c + (k + 1) * XW);
+          const float2 e = add2(ld2(e1 + k * XW), tapply_H2<HK, IN>(L, s, wtab, wi, omega, i, j, v));
+          float2 sum, err, hi, lo;
+          two_sum2(ld2(ph + k * XW), e, sum, err);
+          err = add2(err, ld2(pl + k * XW));
+          fast_two_sum2(sum, err, hi, lo);
+          if (IN) {
+            st2(ph + k * XW, hi);
+            st2(pl + k * XW, lo);
+          } else {
+            if (inside(i, j, n)) {
+              ph[k * XW] = hi.x;
+              pl[k * XW] = lo.x;
+            }
+            if (inside(i, j + 1, n)) {
+              ph[k * XW + 1] = hi.y;
+              pl[k * XW + 1] = lo.y;
+            }
+          }
+          if (HK != HK_JACOBI) v.shift();
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// The compensated residual r = b - A (x_hi + x_lo) of the new iterate on the tile (pair q:
+// grid columns C0+2q, C0+2q+1; 4-row strips), stored with the iterate; returns this
+// thread's share of ||r||^2.
+template <bool IN>
+__device__ __forceinline__ float residual_pair(const LevelDev& L, const float (&s)[9], const float* XH,
+                                               const float* XL, int R0, int C0, float* rdst, float* xo_hi,
+                                               float* xo_lo, const float* bg) {
+  constexpr int NQ = TB / 2, KS = TB / (NTP / NQ);
+  const int n = L.n, pitch = L.pitch;
+  const int q = threadIdx.x % NQ, t0 = (threadIdx.x / NQ) * KS, j = C0 + 2 * q;
+  const float* ch = XH + t0 * XW + 2 * q + 4;  // column c of window row a
+  const float* cl = XL + t0 * XW + 2 * q + 4;
+  Win2 h, l;
+  row_even(ch, h.la, h.ma, h.ra);
+  row_even(cl, l.la, l.ma, l.ra);
+  row_even(ch + XW, h.lb, h.mb, h.rb);
+  row_even(cl + XW, l.lb, l.mb, l.rb);
+  float2 acc = p2(0.f);
+  const size_t g0 = (size_t)(R0 + t0) * pitch + j;
+#pragma unroll
+  for (int k = 0; k < KS; ++k) {
+    row_even(ch + (k + 2) * XW, h.lc, h.mc, h.rc);
+    row_even(cl + (k + 2) * XW, l.lc, l.mc, l.rc);
+    const int i = R0 + t0 + k;
+    const size_t g = g0 + (size_t)k * pitch;
+    const bool in0 = IN || inside(i, j, n), in1 = IN || inside(i, j + 1, n);
+    float2 hi;
+    if (IN) hi = __ldg(reinterpret_cast<const float2*>(bg + g));
+    else hi = make_float2(in0 ? __ldg(bg + g) : 0.f, in1 ? __ldg(bg + g + 1) : 0.f);
+    float2 lo = p2(0.f);
+    dot2_sub2(s[0], h.la, l.la, hi, lo);
+    dot2_sub2(s[1], h.ma, l.ma, hi, lo);
+    dot2_sub2(s[2], h.ra, l.ra, hi, lo);
+    dot2_sub2(s[3], h.lb, l.lb, hi, lo);
+    dot2_sub2(s[4], h.mb, l.mb, hi, lo);
+    dot2_sub2(s[5], h.rb, l.rb, hi, lo);
+    dot2_sub2(s[6], h.lc, l.lc, hi, lo);
+    dot2_sub2(s[7], h.mc, l.mc, hi, lo);
+    dot2_sub2(s[8], h.rc, l.rc, hi, lo);
+    float2 r = add2(hi, lo);
+    if (IN) {
+      st2(rdst + g, r);
+      st2(xo_hi + g, h.mb);
+      st2(xo_lo + g, l.mb);
+    } else {
+      if (in0) {
+        rdst[g] = r.x;
+        xo_hi[g] = h.mb.x;
+        xo_lo[g] = l.mb.x;
+      } else {
+        r.x = 0.f;
+      }
+      if (in1) {
+        rdst[g + 1] = r.y;
+        xo_hi[g + 1] = h.mb.y;
+        xo_lo[g + 1] = l.mb.y;
+      } else {
+        r.y = 0.f;
+      }
+    }
+    acc = fma2(r, r, acc);
+    h.shift();
+    l.shift();
+  }
+  return acc.x + acc.y;
+}
+
+template <int HK>
+__global__ void __launch_bounds__(NTP, 8) k_up0p(const __grid_constant__ Up0Maps M, const ProbDev* __restrict__ probs,
+                                                 ProbState* __restrict__ state, float* __restrict__ partials,
+                                                 int ntiles_max, float omega, float rtol, int max_cycles,
+                                                 float* __restrict__ xhi, float* __restrict__ xlo,
+                                                 float* __restrict__ rnew, const float* __restrict__ b0,
+                                                 const int* __restrict__ act) {
+  pdl_trigger();
+  const int p = act ? act[blockIdx.y] : blockIdx.y;
+  const LevelDev L = probs[p].lv[0];
+  const int n = L.n;
+  const int ntx = (n + TB - 1) / TB, ntiles = ntx * ntx;
+  const int tile = blockIdx.x;
+  if (tile >= ntiles) return;
+  const int R0 = (tile / ntx) * TB, C0 = (tile % ntx) * TB;
+  __shared__ __align__(128) float es[UP0E_H * XW];
+  __shared__ __align__(128) float rs[UP0R_H * XW];
+  __shared__ __align__(128) float ecs[EC0_H * EC_W];
+  __shared__ __align__(128) float xh[RES_H * XW];
+  __shared__ __align__(128) float xl[RES_H * XW];
+  __shared__ __align__(8) uint64_t bar;
+  const bool in = inner_tile(R0, C0, n);
+  float s[9], wi[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) s[k] = L.s[k];
+  const float* wtab = L.W;
+  if (HK == HK_TABLE && in) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) wi[k] = L.W[k * L.T * L.T + MG_NET_MARGIN * L.T + MG_NET_MARGIN];
+  }
+  pdl_wait();
+  if (!st_active(state + p)) return;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    mbar_arrive_expect_tx(&bar, ((UP0E_H + UP0R_H + 2 * RES_H) * XW + EC0_H * EC_W) * sizeof(float));
+    tma_load_3d(es, &M.e, &bar, C0 - 4, R0 - 3, p);
+    tma_load_3d(rs, &M.r, &bar, C0 - 4, R0 - 2, p);
+    tma_load_3d(ecs, &M.ec, &bar, C0 / 2 - 4, R0 / 2 - 2, p);
+    tma_load_3d(xh, &M.x.xh, &bar, C0 - 4, R0 - 1, p);
+    tma_load_3d(xl, &M.x.xl, &bar, C0 - 4, R0 - 1, p);
+  }
+  __syncthreads();
+  if (!tile_wait(&bar, state[p])) return;
+  if (in) up0p_tile<HK, true>(L, s, wtab, wi, omega, es, rs, ecs, xh, xl, R0, C0);
+  else up0p_tile<HK, false>(L, s, wtab, wi, omega, es, rs, ecs, xh, xl, R0, C0);
+  const size_t po = (size_t)p * n * L.pitch;
+  const float acc = in ? residual_pair<true>(L, s, xh, xl, R0, C0, rnew + po, xhi + po, xlo + po, b0 + po)
+                       : residual_pair<false>(L, s, xh, xl, R0, C0, rnew + po, xhi + po, xlo + po, b0 + po);
+  float rhi, rlo;
+  if (block_partial_and_last<NTP>(acc, partials + (size_t)p * ntiles_max, &state[p].counter, ntiles, tile, rhi, rlo)) {
     if (threadIdx.x == 0) decide(state[p], rhi, rlo, rtol, max_cycles);
   }
 }
@@ -796,6 +1162,19 @@ cudaError_t launch_update_residual(const CycleArgs& a, const CUtensorMap& e0, fl
   return e;
 }
 
+// level 0 of the up-sweep: the paired kernel on constant stencils, k_up0 on per-point fields
+template <int SK, int HK>
+static cudaError_t launch_up0(bool pdl, dim3 grid, cudaStream_t s, const Up0Maps& um, const ProbDev* probs,
+                              ProbState* state, float* partials, int ntiles_max, float omega, float rtol,
+                              int max_cycles, float* xhn, float* xln, float* rnew, const float* b0, const int* act) {
+  if constexpr (SK == SK_CONST)
+    return launch_pdl(pdl, k_up0p<HK>, grid, dim3(NTP), 0, s, um, probs, state, partials, ntiles_max, omega, rtol,
+                      max_cycles, xhn, xln, rnew, b0, act);
+  else
+    return launch_pdl(pdl, k_up0<SK, HK>, grid, dim3(NT), 0, s, um, probs, state, partials, ntiles_max, omega, rtol,
+                      max_cycles, xhn, xln, rnew, b0, act);
+}
+
 cudaError_t launch_cycle(const CycleArgs& a, float rtol, int max_cycles, int parity) {
   if (a.generic) return launch_cycle_linear(a, rtol, max_cycles, parity);
   // the fused tile kernels exist for Jacobi and per-point 3x3 kernels only
@@ -841,8 +1220,8 @@ cudaError_t launch_cycle(const CycleArgs& a, float rtol, int max_cycles, int par
       float* xhn = parity ? a.xh0 : a.xh0b;
       float* xln = parity ? a.xl0 : a.xl0b;
       MG_DISPATCH(a.sk, a.hk,
-                  (e = launch_pdl(pdl, k_up0<SK_, HK_>, grid, dim3(NT), 0, a.stream, um, probs, a.state, a.partials,
-                                  a.ntiles_max, a.omega, rtol, max_cycles, xhn, xln, rnew, a.b0, a.active)));
+                  (e = launch_up0<SK_, HK_>(pdl, grid, a.stream, um, probs, a.state, a.partials, a.ntiles_max, a.omega,
+                                            rtol, max_cycles, xhn, xln, rnew, a.b0, a.active)));
     }
     else
       MG_DISPATCH(a.sk, a.hk,
