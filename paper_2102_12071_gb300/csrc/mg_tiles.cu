@@ -958,6 +958,155 @@ __global__ void __launch_bounds__(NTP, 8) k_up0p(const __grid_constant__ Up0Maps
   }
 }
 
+// ------------------------------------------------------------ k_down in pairs
+// k_down on constant stencils with two columns per thread (128 threads per tile) in packed
+// FP32, like k_up0p.  e = H r goes to its own buffer with a column origin at box column 3,
+// so that the odd box columns of the pre-smoothing pairs and the window rows of the
+// residual pass are all aligned 64-bit shared accesses.
+constexpr int EPW = 36;  // e buffer: box columns 3 .. 38, rows R0-1 .. R0+33
+
+template <int HK, bool IN>
+__device__ __forceinline__ void downp_tile(const LevelDev& L, const float (&s)[9], const float* wtab,
+                                           const float (&wi)[9], float omega, float* rs, float* es, float* eo,
+                                           int R0, int C0) {
+  const int n = L.n, t = threadIdx.x;
+  {
+    // e = H r on rows R0-1 .. R0+33, box columns 3 .. 38 (pair q: 2q+3, 2q+4; the residual
+    // reads 3 .. 37); the tile's own points also go to eo for the store of e
+    constexpr int NQ = 18, KS = 5, NS = (ES + KS - 1) / KS;
+    static_assert(16 * NS + (NQ - 16) * NS <= NTP, "phase e");
+    int q, sa;
+    if (chunk_item<NQ, NS>(t, q, sa)) {
+      const int t0 = sa * KS, j = C0 - 1 + 2 * q;
+      const float* c = rs + t0 * XW + 2 * q + 2;  // column c-1 of window row a
+      Win2 v;
+      if (HK != HK_JACOBI) {
+        row_odd(c, v.la, v.ma, v.ra);
+        row_odd(c + XW, v.lb, v.mb, v.rb);
+      }
+#pragma unroll
+      for (int k = 0; k < KS; ++k) {
+        const int ti = t0 + k, i = R0 - 1 + ti;
+        if (ES % KS == 0 || ti < ES) {
+          if (HK != HK_JACOBI) row_odd(c + (k + 2) * XW, v.lc, v.mc, v.rc);
+          else v.mb = make_float2(c[(k + 1) * XW + 1], c[(k + 1) * XW + 2]);
+          float2 e = tapply_H2<HK, IN>(L, s, wtab, wi, omega, i, j, v);
+          if (!IN) e = mask2(e, i, j, n);
+          st2(es + ti * EPW + 2 * q, e);
+          if ((unsigned)(ti - 1) < (unsigned)TB) {
+            if (q >= 1 && q <= TB / 2) eo[(ti - 1) * TB + 2 * q - 1] = e.x;
+            if (q < TB / 2) eo[(ti - 1) * TB + 2 * q] = e.y;
+          }
+          if (HK != HK_JACOBI) v.shift();
+        }
+      }
+    }
+  }
+  fence_async_smem();
+  __syncthreads();
+  {
+    // s = r - A e on rows R0 .. R0+32, box columns 4 .. 37 (pair q: 2q+4, 2q+5; the
+    // restriction reads 4 .. 36), over r in place
+    constexpr int NQ = 17, KS = 5, NR = TB + 1, NS = (NR + KS - 1) / KS;
+    static_assert(16 * NS + (NQ - 16) * NS <= NTP, "phase s");
+    int q, sb;
+    if (chunk_item<NQ, NS>(t, q, sb)) {
+      const int t0 = sb * KS, j = C0 + 2 * q;
+      const float* c = es + t0 * EPW + 2 * q;  // e box column 2q+3 = c-1 of window row a
+      float* rp = rs + (t0 + 2) * XW + 2 * q + 4;
+      Win2 v;
+      row_odd(c, v.la, v.ma, v.ra);
+      row_odd(c + EPW, v.lb, v.mb, v.rb);
+#pragma unroll
+      for (int k = 0; k < KS; ++k) {
+        const int ti = t0 + k;
+        if (ti < NR) {
+          row_odd(c + (k + 2) * EPW, v.lc, v.mc, v.rc);
+          float2 sv = sub2(ld2(rp + k * XW), dot9p(s, v));
+          if (!IN) sv = mask2(sv, R0 + ti, j, n);
+          st2(rp + k * XW, sv);
+          v.shift();
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <int HK>
+__global__ void __launch_bounds__(NTP, 8) k_downp(const __grid_constant__ DownMaps M, const ProbDev* __restrict__ probs,
+                                                  ProbState* __restrict__ state, int l, float omega,
+                                                  const int* __restrict__ act) {
+  pdl_trigger();
+  const int p = act ? act[blockIdx.y] : blockIdx.y;
+  const LevelDev L = probs[p].lv[l];
+  const int n = L.n;
+  const int ntx = (n + TB - 1) / TB;
+  const int tile = blockIdx.x;
+  if (tile >= ntx * ntx) return;
+  const int R0 = (tile / ntx) * TB, C0 = (tile % ntx) * TB;
+  __shared__ __align__(128) float rs[DN_H * XW];  // r, then s = r - A e in place
+  __shared__ __align__(128) float eo[TB * TB];    // e on the owned points (stored by TMA)
+  __shared__ __align__(128) float rco[TC * TC];   // r_c (stored by TMA)
+  __shared__ __align__(16) float es[ES * EPW];
+  __shared__ float wtab[HK == HK_TABLE ? 9 * MG_PROXY * MG_PROXY : 1];
+  __shared__ __align__(8) uint64_t bar;
+  const bool in = inner_tile(R0, C0, n);
+  float s[9], wi[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) s[k] = L.s[k];
+  if (HK == HK_TABLE) {
+    const int T = L.T, Mg = MG_NET_MARGIN;
+    if (in) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) wi[k] = L.W[k * T * T + Mg * T + Mg];
+    } else {
+      for (int k = threadIdx.x; k < 9 * T * T; k += NTP) wtab[k] = L.W[k];
+    }
+  }
+  pdl_wait();
+  if (!st_active(state + p)) return;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    mbar_arrive_expect_tx(&bar, DN_H * XW * sizeof(float));
+    tma_load_3d(rs, &M.r, &bar, C0 - 4, R0 - 2, p);
+  }
+  __syncthreads();
+  if (!tile_wait(&bar, state[p])) return;
+  if (in) downp_tile<HK, true>(L, s, wtab, wi, omega, rs, es, eo, R0, C0);
+  else downp_tile<HK, false>(L, s, wtab, wi, omega, rs, es, eo, R0, C0);
+  if (threadIdx.x == 0) tma_store_3d(&M.e, eo, C0, R0, p);
+  {
+    // r_c = P^T s: coarse row a, coarse columns 2m, 2m+1 (fine rows 2a .. 2a+2, columns
+    // 4m .. 4m+4 of the tile), the order of restrict_at
+    const int a = threadIdx.x >> 3, m = threadIdx.x & 7;
+    const float* c = rs + (2 * a + 2) * XW + 4 * m + 4;
+    float2 u[3], w[3];
+    float z[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      u[r] = ld2(c + r * XW);
+      w[r] = ld2(c + r * XW + 2);
+      z[r] = c[r * XW + 4];
+    }
+    // centre, left, right columns of the two coarse points: (u.y, w.y), (u.x, w.x), (w.x, z)
+    const float2 cen1 = make_float2(u[1].y, w[1].y);
+    const float2 edge = add2(add2(make_float2(u[0].y, w[0].y), make_float2(u[2].y, w[2].y)),
+                             add2(make_float2(u[1].x, w[1].x), make_float2(w[1].x, z[1])));
+    const float2 corner = add2(add2(make_float2(u[0].x, w[0].x), make_float2(w[0].x, z[0])),
+                               add2(make_float2(u[2].x, w[2].x), make_float2(w[2].x, z[2])));
+    st2(rco + a * TC + 2 * m, fma2(p2(0.25f), corner, fma2(p2(0.5f), edge, cen1)));
+  }
+  fence_async_smem();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tma_store_3d(&M.rc, rco, C0 / 2, R0 / 2, p);
+    tma_store_commit();
+    tma_store_wait();
+  }
+}
+
 // ------------------------------------------------------- k_update_residual
 // The level-0 end of a cycle whose up-sweep ran in other kernels (the linear smoother's
 // path): x += e_0 in float-float on the tile and its one-point halo in shared memory, then
@@ -1162,6 +1311,16 @@ cudaError_t launch_update_residual(const CycleArgs& a, const CUtensorMap& e0, fl
   return e;
 }
 
+// the down-sweep of a tiled level: the paired kernel on constant stencils, k_down on fields
+template <int SK, int HK>
+static cudaError_t launch_down(bool pdl, dim3 grid, cudaStream_t s, const DownMaps& dm, const ProbDev* probs,
+                               ProbState* state, int l, float omega, const int* act) {
+  if constexpr (SK == SK_CONST)
+    return launch_pdl(pdl, k_downp<HK>, grid, dim3(NTP), 0, s, dm, probs, state, l, omega, act);
+  else
+    return launch_pdl(pdl, k_down<SK, HK>, grid, dim3(NT), 0, s, dm, probs, state, l, omega, act);
+}
+
 // level 0 of the up-sweep: the paired kernel on constant stencils, k_up0 on per-point fields
 template <int SK, int HK>
 static cudaError_t launch_up0(bool pdl, dim3 grid, cudaStream_t s, const Up0Maps& um, const ProbDev* probs,
@@ -1193,9 +1352,7 @@ cudaError_t launch_cycle(const CycleArgs& a, float rtol, int max_cycles, int par
     } else {
       DownMaps dm = a.maps->down[l];
       if (l == 0 && parity) dm.r = a.maps->down0_rb;
-      MG_DISPATCH(a.sk, a.hk,
-                  (e = launch_pdl(a.pdl, k_down<SK_, HK_>, grid, dim3(NT), 0, a.stream, dm, probs, a.state, l,
-                                  a.omega, a.active)));
+      MG_DISPATCH(a.sk, a.hk, (e = launch_down<SK_, HK_>(a.pdl, grid, a.stream, dm, probs, a.state, l, a.omega, a.active)));
     }
     a.prof->end(a.stream);
   }
