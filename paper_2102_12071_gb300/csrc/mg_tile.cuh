@@ -56,4 +56,21 @@ __device__ __forceinline__ bool tile_wait(uint64_t* bar, ProbState& st) {
   return true;
 }
 
+// tile_wait for a barrier in use more than once (the completion of phase `parity`); on
+// expiry it also drains the copies in flight on `other` (phase other_parity), if any
+__device__ __forceinline__ bool tile_wait_phase(uint64_t* bar, uint32_t parity, uint64_t* other, uint32_t other_parity,
+                                                ProbState& st) {
+  const bool ok = __ldcg(&st.short_wait) == 0 && mbar_wait(bar, parity);
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) {
+      st.status = 4;
+      st.active = 0;
+    }
+    mbar_wait(bar, parity);
+    if (other) mbar_wait(other, other_parity);
+    return false;
+  }
+  return true;
+}
+
 }  // namespace mg

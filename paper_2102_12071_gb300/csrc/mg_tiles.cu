@@ -933,6 +933,8 @@ __global__ void __launch_bounds__(NTP, 8) k_up0p(const __grid_constant__ Up0Maps
 #pragma unroll
     for (int k = 0; k < 9; ++k) wi[k] = L.W[k * L.T * L.T + MG_NET_MARGIN * L.T + MG_NET_MARGIN];
   }
+  // b is read from global memory in the residual at the end: bring its tile to L2 now
+  if (threadIdx.x == 0) tma_prefetch_3d(&M.x.b, C0, R0, p);
   pdl_wait();
   if (!st_active(state + p)) return;
   if (threadIdx.x == 0) {
@@ -1033,78 +1035,102 @@ __device__ __forceinline__ void downp_tile(const LevelDev& L, const float (&s)[9
   __syncthreads();
 }
 
+// A CTA takes `tpc` consecutive tiles of one problem through two r buffers: the copy of
+// tile u+1 is in flight while tile u is computed, and the copy of tile u+2 starts as soon as
+// tile u's buffer is free.
 template <int HK>
 __global__ void __launch_bounds__(NTP, 8) k_downp(const __grid_constant__ DownMaps M, const ProbDev* __restrict__ probs,
-                                                  ProbState* __restrict__ state, int l, float omega,
+                                                  ProbState* __restrict__ state, int l, float omega, int tpc,
                                                   const int* __restrict__ act) {
   pdl_trigger();
   const int p = act ? act[blockIdx.y] : blockIdx.y;
   const LevelDev L = probs[p].lv[l];
   const int n = L.n;
-  const int ntx = (n + TB - 1) / TB;
-  const int tile = blockIdx.x;
-  if (tile >= ntx * ntx) return;
-  const int R0 = (tile / ntx) * TB, C0 = (tile % ntx) * TB;
-  __shared__ __align__(128) float rs[DN_H * XW];  // r, then s = r - A e in place
-  __shared__ __align__(128) float eo[TB * TB];    // e on the owned points (stored by TMA)
-  __shared__ __align__(128) float rco[TC * TC];   // r_c (stored by TMA)
+  const int ntx = (n + TB - 1) / TB, ntiles = ntx * ntx;
+  const int first = blockIdx.x * tpc;
+  if (first >= ntiles) return;
+  const int count = min(tpc, ntiles - first);
+  // r, then s = r - A e in place; each buffer a whole number of 128-byte lines (the copy
+  // engine writes to 128-byte aligned shared memory)
+  constexpr int RSZ = (DN_H * XW + 31) / 32 * 32;
+  __shared__ __align__(128) float rs[2][RSZ];
+  __shared__ __align__(128) float eo[TB * TB];       // e on the owned points (stored by TMA)
+  __shared__ __align__(128) float rco[TC * TC];      // r_c (stored by TMA)
   __shared__ __align__(16) float es[ES * EPW];
   __shared__ float wtab[HK == HK_TABLE ? 9 * MG_PROXY * MG_PROXY : 1];
-  __shared__ __align__(8) uint64_t bar;
-  const bool in = inner_tile(R0, C0, n);
+  __shared__ __align__(8) uint64_t bar[2];
   float s[9], wi[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) s[k] = L.s[k];
   if (HK == HK_TABLE) {
     const int T = L.T, Mg = MG_NET_MARGIN;
-    if (in) {
 #pragma unroll
-      for (int k = 0; k < 9; ++k) wi[k] = L.W[k * T * T + Mg * T + Mg];
-    } else {
+    for (int k = 0; k < 9; ++k) wi[k] = L.W[k * T * T + Mg * T + Mg];
+    bool edge = false;
+    for (int u = 0; u < count; ++u) edge |= !inner_tile(((first + u) / ntx) * TB, ((first + u) % ntx) * TB, n);
+    if (edge)
       for (int k = threadIdx.x; k < 9 * T * T; k += NTP) wtab[k] = L.W[k];
-    }
   }
   pdl_wait();
   if (!st_active(state + p)) return;
+  // thread 0: the copy of tile u into buffer u & 1
+  auto issue = [&](int u) {
+    const int tt = first + u;
+    mbar_arrive_expect_tx(&bar[u & 1], DN_H * XW * sizeof(float));
+    tma_load_3d(rs[u & 1], &M.r, &bar[u & 1], (tt % ntx) * TB - 4, (tt / ntx) * TB - 2, p);
+  };
   if (threadIdx.x == 0) {
-    mbar_init(&bar, 1);
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
     fence_mbar_init();
-    mbar_arrive_expect_tx(&bar, DN_H * XW * sizeof(float));
-    tma_load_3d(rs, &M.r, &bar, C0 - 4, R0 - 2, p);
+    issue(0);
+    if (count > 1) issue(1);
   }
   __syncthreads();
-  if (!tile_wait(&bar, state[p])) return;
-  if (in) downp_tile<HK, true>(L, s, wtab, wi, omega, rs, es, eo, R0, C0);
-  else downp_tile<HK, false>(L, s, wtab, wi, omega, rs, es, eo, R0, C0);
-  if (threadIdx.x == 0) tma_store_3d(&M.e, eo, C0, R0, p);
-  {
-    // r_c = P^T s: coarse row a, coarse columns 2m, 2m+1 (fine rows 2a .. 2a+2, columns
-    // 4m .. 4m+4 of the tile), the order of restrict_at
-    const int a = threadIdx.x >> 3, m = threadIdx.x & 7;
-    const float* c = rs + (2 * a + 2) * XW + 4 * m + 4;
-    float2 u[3], w[3];
-    float z[3];
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      u[r] = ld2(c + r * XW);
-      w[r] = ld2(c + r * XW + 2);
-      z[r] = c[r * XW + 4];
+  for (int u = 0; u < count; ++u) {
+    const int tt = first + u, R0 = (tt / ntx) * TB, C0 = (tt % ntx) * TB;
+    const bool in = inner_tile(R0, C0, n);
+    float* r = rs[u & 1];
+    // the stores of the previous tile have read eo and rco before they are written again
+    if (u > 0 && threadIdx.x == 0) tma_store_wait_read();
+    const bool more = u + 1 < count;
+    if (!tile_wait_phase(&bar[u & 1], (u >> 1) & 1, more ? &bar[(u + 1) & 1] : nullptr, ((u + 1) >> 1) & 1, state[p])) {
+      if (threadIdx.x == 0) tma_store_wait();
+      return;
     }
-    // centre, left, right columns of the two coarse points: (u.y, w.y), (u.x, w.x), (w.x, z)
-    const float2 cen1 = make_float2(u[1].y, w[1].y);
-    const float2 edge = add2(add2(make_float2(u[0].y, w[0].y), make_float2(u[2].y, w[2].y)),
-                             add2(make_float2(u[1].x, w[1].x), make_float2(w[1].x, z[1])));
-    const float2 corner = add2(add2(make_float2(u[0].x, w[0].x), make_float2(w[0].x, z[0])),
-                               add2(make_float2(u[2].x, w[2].x), make_float2(w[2].x, z[2])));
-    st2(rco + a * TC + 2 * m, fma2(p2(0.25f), corner, fma2(p2(0.5f), edge, cen1)));
+    if (in) downp_tile<HK, true>(L, s, wtab, wi, omega, r, es, eo, R0, C0);
+    else downp_tile<HK, false>(L, s, wtab, wi, omega, r, es, eo, R0, C0);
+    if (threadIdx.x == 0) tma_store_3d(&M.e, eo, C0, R0, p);
+    {
+      // r_c = P^T s: coarse row a, coarse columns 2m, 2m+1 (fine rows 2a .. 2a+2, columns
+      // 4m .. 4m+4 of the tile), the order of restrict_at
+      const int a = threadIdx.x >> 3, m = threadIdx.x & 7;
+      const float* c = r + (2 * a + 2) * XW + 4 * m + 4;
+      float2 x0[3], x1[3];
+      float z[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        x0[q] = ld2(c + q * XW);
+        x1[q] = ld2(c + q * XW + 2);
+        z[q] = c[q * XW + 4];
+      }
+      // centre, left and right columns of the two coarse points: (x0.y, x1.y), (x0.x, x1.x), (x1.x, z)
+      const float2 cen = make_float2(x0[1].y, x1[1].y);
+      const float2 edge = add2(add2(make_float2(x0[0].y, x1[0].y), make_float2(x0[2].y, x1[2].y)),
+                               add2(make_float2(x0[1].x, x1[1].x), make_float2(x1[1].x, z[1])));
+      const float2 corner = add2(add2(make_float2(x0[0].x, x1[0].x), make_float2(x1[0].x, z[0])),
+                                 add2(make_float2(x0[2].x, x1[2].x), make_float2(x1[2].x, z[2])));
+      st2(rco + a * TC + 2 * m, fma2(p2(0.25f), corner, fma2(p2(0.5f), edge, cen)));
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tma_store_3d(&M.rc, rco, C0 / 2, R0 / 2, p);
+      tma_store_commit();
+      if (u + 2 < count) issue(u + 2);  // every thread is done with buffer u & 1
+    }
   }
-  fence_async_smem();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    tma_store_3d(&M.rc, rco, C0 / 2, R0 / 2, p);
-    tma_store_commit();
-    tma_store_wait();
-  }
+  if (threadIdx.x == 0) tma_store_wait();
 }
 
 // ------------------------------------------------------- k_update_residual
@@ -1315,8 +1341,15 @@ cudaError_t launch_update_residual(const CycleArgs& a, const CUtensorMap& e0, fl
 template <int SK, int HK>
 static cudaError_t launch_down(bool pdl, dim3 grid, cudaStream_t s, const DownMaps& dm, const ProbDev* probs,
                                ProbState* state, int l, float omega, const int* act) {
-  if constexpr (SK == SK_CONST)
-    return launch_pdl(pdl, k_downp<HK>, grid, dim3(NTP), 0, s, dm, probs, state, l, omega, act);
+  if constexpr (SK == SK_CONST) {
+    // two tiles per CTA once the launch is several waves deep (8 CTAs per SM)
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int tpc = (long long)grid.x * grid.y >= 4ll * 8 * (nsm > 0 ? nsm : 1) ? 2 : 1;
+    const dim3 g((grid.x + tpc - 1) / tpc, grid.y);
+    return launch_pdl(pdl, k_downp<HK>, g, dim3(NTP), 0, s, dm, probs, state, l, omega, tpc, act);
+  }
   else
     return launch_pdl(pdl, k_down<SK, HK>, grid, dim3(NT), 0, s, dm, probs, state, l, omega, act);
 }
