@@ -18,6 +18,7 @@
 #include "mg_common.cuh"
 #include "mg_internal.h"
 #include "mg_ops.cuh"
+#include "mg_pair.cuh"
 #include "mg_reduce.cuh"
 #include "mg_tile.cuh"
 #include "mg_tma.cuh"
@@ -247,99 +248,118 @@ __global__ void __launch_bounds__(LT) k_stack_conv(const ProbDev* __restrict__ p
 // One CTA per 32 x 32 output tile.  Coordinates below are in the frame of the input tile
 // u: row 0 = grid row R0 - 5, column 0 = grid column C0 - 8 (the TMA box starts 8 columns
 // left so that its x is 16-byte aligned).  Layer k (k = 1..4) covers the tile grown by
-// 5 - k points, rows and columns [k, 42 - k) and [k + 3, 45 - k); the output covers rows
-// [5, 37), columns [8, 40).  Every layer writes a buffer of its own whose row stride makes
-// the next layer's reads conflict-free: a warp covers the end of one strip row and the
-// start of the row K below it, and K * stride = S (mod 32) puts the second run of lanes on
-// the banks right after the first.
+// 5 - k points; the output covers rows [5, 37), columns [8, 40).
 constexpr int HT = 32, HH = 5, HR = HT + 2 * HH;  // tile, halo, rows of u
-constexpr int HXU = 56;                            // u: 7 * 56 = 40 (mod 32), read by layer 1
-constexpr int HX1 = 42, HX2 = 38, HX3 = 43, HX4 = 34;  // layer outputs (7*42=38, 6*38=36, 6*43=34)
+constexpr int HXU = 56;                            // u: row stride of the TMA box
 
 __device__ __forceinline__ bool lin_inside(int i, int j, int n) {
   return (unsigned)i < (unsigned)n && (unsigned)j < (unsigned)n;
 }
 
-// out = f(in) on the layer's region of side S (zero outside the grid when MASK), K rows
-// per thread walking down a column with a 3x3 register window; in / out: buffers of row
-// stride XI / XO whose element 0 sits at frame position (RI, CI) / (RO, CO)
-template <int S, int K, bool MASK, int XI, int RI, int CI, int XO, int RO, int CO>
-__device__ __forceinline__ void lin_layer(const float* in, float* out, const float* wsm, int R0, int C0, int n) {
-  constexpr int NS = (S + K - 1) / K, o = (HR - S) / 2;
-  static_assert(S * NS <= LT, "layer needs more threads than the CTA has");
-  const int t = threadIdx.x;
-  if (t >= S * NS) return;
+// The tiled chain runs with two adjacent columns per thread in packed FP32 (mg_pair.cuh),
+// 128 threads per tile.  Layer L (L = 1..4) covers frame rows [L, 42 - L) and columns
+// [L + 3, 45 - L) in pairs (c, c+1), c = L + 3 + 2q, and writes a buffer whose origin is
+// (L, L + 3): the pair's own store is an aligned 64-bit access, and so are the next
+// layer's window rows (its column c - 1 is even there).  Layer 1 reads u, whose frame is
+// the TMA box: its windows (and f6's) are one 64-bit and two 32-bit loads.  Layers 1 and
+// 3 write one buffer, 2 and 4 the other.
+constexpr int LTP = 128;  // threads per CTA of the tiled chain kernels
+constexpr int BX = 40;    // row stride of the layer buffers
+
+template <int L, int K, bool MASK>
+__device__ __forceinline__ void lin_layer2(const float* in, float* out, const float* wsm, int R0, int C0, int n) {
+  constexpr int S = HR - 2 * L, NQ = S / 2, NS = (S + K - 1) / K;
+  constexpr int XI = L == 1 ? HXU : BX, RI = L == 1 ? 0 : L - 1, CI = L == 1 ? 0 : L + 2;
+  static_assert(16 * NS + (NQ - 16) * NS <= LTP, "layer needs more threads than the CTA has");
+  int q, strip;
+  if (!chunk_item<NQ, NS>(threadIdx.x, q, strip)) return;
   float w[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) w[k] = wsm[k];
-  const int tj = t % S, t0 = (t / S) * K, r = o + t0, c = o + 3 + tj;
-  const float* src = in + (r - RI) * XI + (c - CI);
-  float* dst = out + (r - RO) * XO + (c - CO);
-  Win v;
-  v.load_ab(src, XI);
+  const int r0 = L + strip * K, c = L + 3 + 2 * q;
+  const float* src = in + (r0 - 1 - RI) * XI + (L == 1 ? c : c - 1 - CI);  // window row a
+  float* dst = out + (r0 - L) * BX + 2 * q;
+  Win2 v;
+  if (L == 1) {
+    row_even(src, v.la, v.ma, v.ra);
+    row_even(src + XI, v.lb, v.mb, v.rb);
+  } else {
+    row_odd(src, v.la, v.ma, v.ra);
+    row_odd(src + XI, v.lb, v.mb, v.rb);
+  }
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    if (t0 + k < S) {
-      v.load_c(src + k * XI, XI);
-      float val = dot9(w, v);
-      if (MASK && !lin_inside(R0 - HH + r + k, C0 - 8 + c, n)) val = 0.f;
-      dst[k * XO] = val;
+    if (S % K == 0 || strip * K + k < S) {
+      if (L == 1) row_even(src + (k + 2) * XI, v.lc, v.mc, v.rc);
+      else row_odd(src + (k + 2) * XI, v.lc, v.mc, v.rc);
+      float2 val = dot9w<L != 1>(w, v);
+      if (MASK) {
+        const int i = R0 - HH + r0 + k, j = C0 - 8 + c;
+        if (!lin_inside(i, j, n)) val.x = 0.f;
+        if (!lin_inside(i, j + 1, n)) val.y = 0.f;
+      }
+      st2(dst + k * BX, val);
       v.shift();
     }
   }
 }
 
-// dst (=, or += with ACC, or base + with base: four values per thread) f_5(w_4) + f_6(u)
-// on the tile's points inside the grid: one window and one kernel live at a time (f_5 over
-// w_4 first, then f_6 over u)
-template <bool ACC>
-__device__ __forceinline__ void lin_out(const float* w4, const float* u, const float* ph, int R0, int C0, int n,
-                                        float* dst, int pitch, const float* base) {
+// dst (=, or += with ACC, or base + with base: four rows per thread) f_5(w_4) + f_6(u) on
+// the tile's points inside the grid, pair q = grid columns C0 + 2q, C0 + 2q + 1: one window
+// and one kernel live at a time (f_5 over layer 4's buffer first, then f_6 over u)
+template <bool MASK, bool ACC>
+__device__ __forceinline__ void lin_out2(const float* w4, const float* u, const float* ph, int R0, int C0, int n,
+                                         float* dst, int pitch, const float2* base) {
   constexpr int K = 4;
-  const int tj = threadIdx.x % HT, t0 = (threadIdx.x / HT) * K, r = HH + t0, c = 8 + tj;
-  float h[K];
+  const int q = threadIdx.x & 15, t0 = (threadIdx.x >> 4) * K, r = HH + t0, c = 8 + 2 * q;
+  float2 h[K];
   float w[9];
-  Win v;
+  Win2 v;
 #pragma unroll
   for (int k = 0; k < 9; ++k) w[k] = ph[36 + k];
-  const float* a = w4 + (r - 4) * HX4 + (c - 7);
-  v.load_ab(a, HX4);
+  const float* a = w4 + (r - 1 - 4) * BX + 2 * q;  // layer 4's origin (4, 7): column c-1 is 2q
+  row_odd(a, v.la, v.ma, v.ra);
+  row_odd(a + BX, v.lb, v.mb, v.rb);
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    v.load_c(a + k * HX4, HX4);
-    h[k] = dot9(w, v);
+    row_odd(a + (k + 2) * BX, v.lc, v.mc, v.rc);
+    h[k] = dot9w<true>(w, v);
     v.shift();
   }
 #pragma unroll
   for (int k = 0; k < 9; ++k) w[k] = ph[45 + k];
-  const float* b = u + r * HXU + c;
-  v.load_ab(b, HXU);
-  const int j = C0 + tj;
+  const float* b = u + (r - 1) * HXU + c;
+  row_even(b, v.la, v.ma, v.ra);
+  row_even(b + HXU, v.lb, v.mb, v.rb);
+  const int j = C0 + 2 * q;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    v.load_c(b + k * HXU, HXU);
+    row_even(b + (k + 2) * HXU, v.lc, v.mc, v.rc);
     const int i = R0 + t0 + k;
-    if (lin_inside(i, j, n)) {
-      const float hv = h[k] + dot9(w, v);
-      float* d = dst + (size_t)i * pitch + j;
-      *d = base ? base[k] + hv : (ACC ? *d + hv : hv);
+    const float2 hv = add2(h[k], dot9w<false>(w, v));
+    float* d = dst + (size_t)i * pitch + j;
+    if (!MASK) {
+      st2(d, base ? add2(base[k], hv) : (ACC ? add2(ld2(d), hv) : hv));
+    } else {
+      if (lin_inside(i, j, n)) d[0] = base ? base[k].x + hv.x : (ACC ? d[0] + hv.x : hv.x);
+      if (lin_inside(i, j + 1, n)) d[1] = base ? base[k].y + hv.y : (ACC ? d[1] + hv.y : hv.y);
     }
     v.shift();
   }
 }
 
 template <bool MASK, bool ACC>
-__device__ __forceinline__ void lin_chain(const float* U, float* B1, float* B2, float* B3, float* B4, const float* ph,
-                                          int R0, int C0, int n, float* dst, int pitch, const float* base = nullptr) {
-  lin_layer<40, 7, MASK, HXU, 0, 0, HX1, 1, 4>(U, B1, ph, R0, C0, n);
+__device__ __forceinline__ void lin_chain(const float* U, float* BA, float* BB, const float* ph, int R0, int C0, int n,
+                                          float* dst, int pitch, const float2* base = nullptr) {
+  lin_layer2<1, 7, MASK>(U, BA, ph, R0, C0, n);
   __syncthreads();
-  lin_layer<38, 7, MASK, HX1, 1, 4, HX2, 2, 5>(B1, B2, ph + 9, R0, C0, n);
+  lin_layer2<2, 7, MASK>(BA, BB, ph + 9, R0, C0, n);
   __syncthreads();
-  lin_layer<36, 6, MASK, HX2, 2, 5, HX3, 3, 6>(B2, B3, ph + 18, R0, C0, n);
+  lin_layer2<3, 6, MASK>(BB, BA, ph + 18, R0, C0, n);
   __syncthreads();
-  lin_layer<34, 6, MASK, HX3, 3, 6, HX4, 4, 7>(B3, B4, ph + 27, R0, C0, n);
+  lin_layer2<4, 5, MASK>(BA, BB, ph + 27, R0, C0, n);
   __syncthreads();
-  lin_out<ACC>(B4, U, ph, R0, C0, n, dst, pitch, base);
+  lin_out2<MASK, ACC>(BB, U, ph, R0, C0, n, dst, pitch, base);
 }
 
 // ------------------------------------------------------------- the fused up-sweep
@@ -355,48 +375,73 @@ template <int SK, bool MASK>
 __device__ __forceinline__ void up_prepare(const LevelDev& L, const float (&s)[9], float* E1, float* U,
                                            const float* ecs, int R0, int C0, int n) {
   // e1 = e + P e_c on rows R0-6 .. R0+37, columns C0-6 .. C0+37 (e and e_c are zero outside
-  // their grids, so is P e_c outside the fine grid)
-  const int I0 = R0 / 2 - 4, J0 = C0 / 2 - 4;
-  for (int q = threadIdx.x; q < 44 * 44; q += LT) {
-    const int rr = q / 44, cc = 2 + q % 44;
-    const int i = R0 - 6 + rr, j = C0 - 8 + cc;
-    const float* b = ecs + (((i - 1) >> 1) - I0) * UC + (((j - 1) >> 1) - J0);
-    float v;
-    if (i & 1) v = (j & 1) ? b[0] : 0.5f * (b[0] + b[1]);
-    else v = (j & 1) ? 0.5f * (b[0] + b[UC]) : 0.25f * ((b[0] + b[1]) + (b[UC] + b[UC + 1]));
-    E1[rr * UE_X + cc] += v;
+  // their grids, so is P e_c outside the fine grid).  Pair q is e1's columns 2 + 2q (an even
+  // grid column) and 3 + 2q, whose bilinear weights read coarse box columns (q, q+1) and
+  // (q+1, q+1); strips of 10 rows from even offsets read coarse box rows 5 s .. 5 s + 5 (row
+  // 2m reads coarse rows m, m+1; row 2m+1 coarse row m+1 twice), and the sum of a coarse row's
+  // pair serves two fine rows.  P e_c = ((c_aa + c_ab) + (c_ba + c_bb)) / 4 with coincident
+  // indices repeated, which equals the one-, two- and four-point forms exactly.
+  {
+    constexpr int NQ = 22, KS = 10, NS = (UE_H + KS - 1) / KS;
+    static_assert(NQ * NS <= LTP, "prolongation needs more threads than the CTA has");
+    if ((int)threadIdx.x < NQ * NS) {
+      const int q = threadIdx.x % NQ, s5 = threadIdx.x / NQ;
+      const float* cb = ecs + 5 * s5 * UC + q;
+      float* ep = E1 + KS * s5 * UE_X + 2 + 2 * q;
+      float2 S[KS / 2 + 1];
+#pragma unroll
+      for (int m = 0; m <= KS / 2; ++m) {
+        if (5 * s5 + m < UC) {
+          const float a = cb[m * UC], b = cb[m * UC + 1];
+          S[m] = add2(make_float2(a, b), p2(b));
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < KS; ++k)
+        if (KS * s5 + k < UE_H)
+          st2(ep + k * UE_X, fma2(p2(0.25f), add2(S[(k + 1) >> 1], S[(k >> 1) + 1]), ld2(ep + k * UE_X)));
+    }
   }
   __syncthreads();
-  // t = r - A e1 on the chain's input region (frame rows 0..41, columns 3..44), K rows per
-  // thread with a register window over e1 (e1's row = t's row + 1)
-  constexpr int S = HR, K = 7, NS = (S + K - 1) / K;
-  static_assert(S * NS <= LT, "residual needs more threads than the CTA has");
-  const int t = threadIdx.x;
-  if (t < S * NS) {
-    const int tj = t % S, t0 = (t / S) * K, c = 3 + tj;
-    const float* src = E1 + (t0 + 1) * UE_X + c;
-    Win v;
-    v.load_ab(src, UE_X);
+  // t = r - A e1 on the chain's input region (frame rows 0..41, columns 3..44) in pairs
+  // (3 + 2q, 4 + 2q), K rows per thread with a register window over e1 (e1's row = t's
+  // row + 1; column c - 1 is even there)
+  constexpr int S = HR, NQ = S / 2, K = 7, NS = (S + K - 1) / K;
+  static_assert(16 * NS + (NQ - 16) * NS <= LTP, "residual needs more threads than the CTA has");
+  int q, strip;
+  if (chunk_item<NQ, NS>(threadIdx.x, q, strip)) {
+    const int t0 = strip * K, c = 3 + 2 * q;
+    const float* src = E1 + t0 * UE_X + c - 1;
+    Win2 v;
+    row_odd(src, v.la, v.ma, v.ra);
+    row_odd(src + UE_X, v.lb, v.mb, v.rb);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       if (t0 + k < S) {
-        v.load_c(src + k * UE_X, UE_X);
+        row_odd(src + (k + 2) * UE_X, v.lc, v.mc, v.rc);
         const int i = R0 - HH + t0 + k, j = C0 - 8 + c;
         float* tp = U + (t0 + k) * HXU + c;
-        if (!MASK || lin_inside(i, j, n)) {
-          float a[9];
-          if (SK == SK_CONST) {
-#pragma unroll
-            for (int q = 0; q < 9; ++q) a[q] = s[q];
-          } else {
-            const size_t nn = (size_t)n * n, pq = (size_t)i * n + j;
-#pragma unroll
-            for (int q = 0; q < 9; ++q) a[q] = __ldg(L.st + q * nn + pq);
-          }
-          *tp = *tp - dot9(a, v);
+        float2 av;
+        if (SK == SK_CONST) {
+          av = dot9w<true>(s, v);
         } else {
-          *tp = 0.f;
+          const size_t nn = (size_t)n * n;
+          float a0[9], a1[9];
+          const bool in0 = !MASK || lin_inside(i, j, n), in1 = !MASK || lin_inside(i, j + 1, n);
+#pragma unroll
+          for (int z = 0; z < 9; ++z) {
+            a0[z] = in0 ? __ldg(L.st + z * nn + (size_t)i * n + j) : 0.f;
+            a1[z] = in1 ? __ldg(L.st + z * nn + (size_t)i * n + j + 1) : 0.f;
+          }
+          av = make_float2(dot9(a0, lane_win(v, 0)), dot9(a1, lane_win(v, 1)));
         }
+        float2 tv = sub2(make_float2(tp[0], tp[1]), av);
+        if (MASK) {
+          if (!lin_inside(i, j, n)) tv.x = 0.f;
+          if (!lin_inside(i, j + 1, n)) tv.y = 0.f;
+        }
+        tp[0] = tv.x;
+        tp[1] = tv.y;
         v.shift();
       }
     }
@@ -407,11 +452,11 @@ __device__ __forceinline__ void up_prepare(const LevelDev& L, const float (&s)[9
 // out = e1 + H t on level l (fused prolongation, residual and post-smoothing);
 // mE: e_l with the six-point halo, mR: r_l (the chain's input box), mC: the coarse tile
 template <int SK>
-__global__ void __launch_bounds__(LT, 5) k_lin_Uptile(const __grid_constant__ CUtensorMap mE,
-                                                      const __grid_constant__ CUtensorMap mR,
-                                                      const __grid_constant__ CUtensorMap mC,
-                                                      const ProbDev* __restrict__ probs, ProbState* __restrict__ state,
-                                                      const int* __restrict__ act, int l, float* __restrict__ out) {
+__global__ void __launch_bounds__(LTP, 6) k_lin_Uptile(const __grid_constant__ CUtensorMap mE,
+                                                       const __grid_constant__ CUtensorMap mR,
+                                                       const __grid_constant__ CUtensorMap mC,
+                                                       const ProbDev* __restrict__ probs, ProbState* __restrict__ state,
+                                                       const int* __restrict__ act, int l, float* __restrict__ out) {
   pdl_trigger();
   const int p = act ? act[blockIdx.y] : blockIdx.y;
   const LevelDev L = probs[p].lv[l];
@@ -422,7 +467,8 @@ __global__ void __launch_bounds__(LT, 5) k_lin_Uptile(const __grid_constant__ CU
   __shared__ __align__(128) float U[HR * HXU];
   __shared__ __align__(128) float E1[UE_H * UE_X];
   __shared__ __align__(128) float ecs[UC * UC];
-  __shared__ float B1[40 * HX1], B2[38 * HX2], B3[36 * HX3], B4[34 * HX4];
+  __shared__ __align__(16) float BA[(HR - 2) * BX];
+  __shared__ __align__(16) float BB[(HR - 4) * BX];
   __shared__ float ph[MG_NPARAMS_LIN];
   __shared__ __align__(8) uint64_t bar;
   float s[9];
@@ -444,23 +490,23 @@ __global__ void __launch_bounds__(LT, 5) k_lin_Uptile(const __grid_constant__ CU
   const bool inner = R0 >= HH + 1 && C0 >= HH + 1 && R0 + HT + HH + 1 <= n && C0 + HT + HH + 1 <= n;
   if (inner) up_prepare<SK, false>(L, s, E1, U, ecs, R0, C0, n);
   else up_prepare<SK, true>(L, s, E1, U, ecs, R0, C0, n);
-  // e1 on the output points of this thread (lin_out's mapping), then the chain on t
-  float e1c[4];
+  // e1 on the output points of this thread (lin_out2's mapping), then the chain on t
+  float2 e1c[4];
   {
-    const int tj = threadIdx.x % HT, t0 = (threadIdx.x / HT) * 4;
+    const int q = threadIdx.x & 15, t0 = (threadIdx.x >> 4) * 4;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) e1c[k] = E1[(t0 + k + HH + 1) * UE_X + tj + 8];
+    for (int k = 0; k < 4; ++k) e1c[k] = ld2(E1 + (t0 + k + HH + 1) * UE_X + 8 + 2 * q);
   }
   float* d = out + (size_t)p * n * pitch;
-  if (inner) lin_chain<false, false>(U, B1, B2, B3, B4, ph, R0, C0, n, d, pitch, e1c);
-  else lin_chain<true, false>(U, B1, B2, B3, B4, ph, R0, C0, n, d, pitch, e1c);
+  if (inner) lin_chain<false, false>(U, BA, BB, ph, R0, C0, n, d, pitch, e1c);
+  else lin_chain<true, false>(U, BA, BB, ph, R0, C0, n, d, pitch, e1c);
 }
 
 // dst (=, or += with ACC) H u on level l; mu: the tensor map of u's level array
 template <bool ACC>
-__global__ void __launch_bounds__(LT, 6) k_lin_Htile(const __grid_constant__ CUtensorMap mu,
-                                                     const ProbDev* __restrict__ probs, ProbState* __restrict__ state,
-                                                     const int* __restrict__ act, int l, float* __restrict__ dst) {
+__global__ void __launch_bounds__(LTP, 8) k_lin_Htile(const __grid_constant__ CUtensorMap mu,
+                                                      const ProbDev* __restrict__ probs, ProbState* __restrict__ state,
+                                                      const int* __restrict__ act, int l, float* __restrict__ dst) {
   pdl_trigger();
   const int p = act ? act[blockIdx.y] : blockIdx.y;
   const LevelDev L = probs[p].lv[l];
@@ -469,7 +515,8 @@ __global__ void __launch_bounds__(LT, 6) k_lin_Htile(const __grid_constant__ CUt
   if (tile >= ntx * ntx) return;
   const int R0 = (tile / ntx) * HT, C0 = (tile % ntx) * HT;
   __shared__ __align__(128) float U[HR * HXU];
-  __shared__ float B1[40 * HX1], B2[38 * HX2], B3[36 * HX3], B4[34 * HX4];
+  __shared__ __align__(16) float BA[(HR - 2) * BX];
+  __shared__ __align__(16) float BB[(HR - 4) * BX];
   __shared__ float ph[MG_NPARAMS_LIN];
   __shared__ __align__(8) uint64_t bar;
   if (threadIdx.x < MG_NPARAMS_LIN) ph[threadIdx.x] = L.W[threadIdx.x];  // weights never change
@@ -485,9 +532,9 @@ __global__ void __launch_bounds__(LT, 6) k_lin_Htile(const __grid_constant__ CUt
   if (!tile_wait(&bar, state[p])) return;
   float* d = dst + (size_t)p * n * pitch;
   if (R0 >= HH && C0 >= HH && R0 + HT + HH <= n && C0 + HT + HH <= n)
-    lin_chain<false, ACC>(U, B1, B2, B3, B4, ph, R0, C0, n, d, pitch);
+    lin_chain<false, ACC>(U, BA, BB, ph, R0, C0, n, d, pitch);
   else
-    lin_chain<true, ACC>(U, B1, B2, B3, B4, ph, R0, C0, n, d, pitch);
+    lin_chain<true, ACC>(U, BA, BB, ph, R0, C0, n, d, pitch);
 }
 
 // phi[l] <- the parameters of H^T: (f_5 .. f_1 f_6 reversed)^T = f_1^T .. f_5^T + f_6^T,
@@ -515,9 +562,9 @@ static cudaError_t lin_H(const CycleArgs& a, int l, const CUtensorMap& mu, float
   a.prof->launches++;
   a.prof->begin(cls, a.stream);
   const cudaError_t e =
-      acc ? launch_pdl(a.pdl, k_lin_Htile<true>, grid, dim3(LT), 0, a.stream, mu, (const ProbDev*)a.probs, a.state,
+      acc ? launch_pdl(a.pdl, k_lin_Htile<true>, grid, dim3(LTP), 0, a.stream, mu, (const ProbDev*)a.probs, a.state,
                        a.active, l, dst)
-          : launch_pdl(a.pdl, k_lin_Htile<false>, grid, dim3(LT), 0, a.stream, mu, (const ProbDev*)a.probs, a.state,
+          : launch_pdl(a.pdl, k_lin_Htile<false>, grid, dim3(LTP), 0, a.stream, mu, (const ProbDev*)a.probs, a.state,
                        a.active, l, dst);
   a.prof->end(a.stream);
   return e;
@@ -631,9 +678,9 @@ cudaError_t launch_cycle_linear(const CycleArgs& a, float rtol, int max_cycles, 
     if (lin) {
       const int nt = (a.nl[l] + HT - 1) / HT;
       e = a.sk == SK_CONST
-              ? launch_pdl(a.pdl, k_lin_Uptile<SK_CONST>, dim3(nt * nt, np), dim3(LT), 0, a.stream, M.eh[l],
+              ? launch_pdl(a.pdl, k_lin_Uptile<SK_CONST>, dim3(nt * nt, np), dim3(LTP), 0, a.stream, M.eh[l],
                            level_rmap(l), M.ec[l], probs, a.state, a.active, l, ef)
-              : launch_pdl(a.pdl, k_lin_Uptile<SK_FIELD>, dim3(nt * nt, np), dim3(LT), 0, a.stream, M.eh[l],
+              : launch_pdl(a.pdl, k_lin_Uptile<SK_FIELD>, dim3(nt * nt, np), dim3(LTP), 0, a.stream, M.eh[l],
                            level_rmap(l), M.ec[l], probs, a.state, a.active, l, ef);
     } else {
       e = launch_pdl(a.pdl, k_lin_prolong, point_grid(a.nl[l], np), dim3(PX, PY), 0, a.stream, probs, cst, a.active,

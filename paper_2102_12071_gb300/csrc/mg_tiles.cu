@@ -25,6 +25,7 @@
 #include "mg_common.cuh"
 #include "mg_internal.h"
 #include "mg_ops.cuh"
+#include "mg_pair.cuh"
 #include "mg_reduce.cuh"
 #include "mg_tile.cuh"
 #include "mg_tma.cuh"
@@ -612,110 +613,17 @@ __global__ void __launch_bounds__(NT, SK == SK_CONST ? 8 : 4) k_up0(const __grid
 // when c is odd.  Half the threads with twice the registers each keep 8 CTAs per SM.
 constexpr int NTP = 128;
 
-__device__ __forceinline__ float2 p2(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 ng2(float2 a) { return make_float2(-a.x, -a.y); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, ng2(b)); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
-__device__ __forceinline__ void st2(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
-
-__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
-  s = add2(a, b);
-  const float2 bb = sub2(s, a);
-  e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
-}
-__device__ __forceinline__ void fast_two_sum2(float2 a, float2 b, float2& s, float2& e) {
-  s = add2(a, b);
-  e = sub2(b, sub2(s, a));
-}
-// dot2_sub on a pair: hi + lo -= a (x + xl)
-__device__ __forceinline__ void dot2_sub2(float a, float2 x, float2 xl, float2& hi, float2& lo) {
-  const float2 pr = mul2(p2(a), x);
-  const float2 pe = fma2(p2(a), x, ng2(pr));
-  float2 sum, err;
-  two_sum2(hi, ng2(pr), sum, err);
-  hi = sum;
-  lo = add2(lo, sub2(err, pe));
-  lo = fma2(p2(-a), xl, lo);
-}
-
-// Three rows of the columns c-1 .. c+2 around the pair (c, c+1): l = (c-1, c), m = (c, c+1),
-// r = (c+1, c+2) of rows a, b, c, the left, centre and right operands of the pair's stencil.
-struct Win2 {
-  float2 la, ma, ra, lb, mb, rb, lc, mc, rc;
-  __device__ __forceinline__ void shift() {
-    la = lb; ma = mb; ra = rb;
-    lb = lc; mb = mc; rb = rc;
-  }
-};
-// one window row; p points at column c-1, which is even (c odd): two aligned loads
-__device__ __forceinline__ void row_odd(const float* p, float2& l, float2& m, float2& r) {
-  const float2 u = ld2(p), w = ld2(p + 2);
-  l = u;
-  r = w;
-  m = make_float2(u.y, w.x);
-}
-// one window row; p points at column c, which is even: one aligned and two single loads
-__device__ __forceinline__ void row_even(const float* p, float2& l, float2& m, float2& r) {
-  const float2 u = ld2(p);
-  const float a = p[-1], b = p[2];
-  l = make_float2(a, u.x);
-  m = u;
-  r = make_float2(u.y, b);
-}
-// sum of w_k v_k for both points, centre first (the order of dot9)
-__device__ __forceinline__ float2 dot9p(const float (&w)[9], const Win2& v) {
-  float2 acc = mul2(p2(w[4]), v.mb);
-  acc = fma2(p2(w[0]), v.la, acc);
-  acc = fma2(p2(w[1]), v.ma, acc);
-  acc = fma2(p2(w[2]), v.ra, acc);
-  acc = fma2(p2(w[3]), v.lb, acc);
-  acc = fma2(p2(w[5]), v.rb, acc);
-  acc = fma2(p2(w[6]), v.lc, acc);
-  acc = fma2(p2(w[7]), v.mc, acc);
-  acc = fma2(p2(w[8]), v.rc, acc);
-  return acc;
-}
-// the scalar window of one point of the pair (lane 0: column c, lane 1: column c+1)
-__device__ __forceinline__ Win lane_win(const Win2& v, int lane) {
-  Win w;
-  w.a0 = lane ? v.la.y : v.la.x; w.a1 = lane ? v.ma.y : v.ma.x; w.a2 = lane ? v.ra.y : v.ra.x;
-  w.b0 = lane ? v.lb.y : v.lb.x; w.b1 = lane ? v.mb.y : v.mb.x; w.b2 = lane ? v.rb.y : v.rb.x;
-  w.c0 = lane ? v.lc.y : v.lc.x; w.c1 = lane ? v.mc.y : v.mc.x; w.c2 = lane ? v.rc.y : v.rc.x;
-  return w;
-}
 // H v for the pair at (i, j), (i, j+1): Jacobi, or the interior kernel on inner tiles, else
 // each point's class kernel (points outside the grid have no class: 0 there)
-template <int HK, bool IN>
+template <int HK, bool IN, bool ODD>
 __device__ __forceinline__ float2 tapply_H2(const LevelDev& L, const float (&s)[9], const float* wtab,
                                             const float (&wi)[9], float omega, int i, int j, const Win2& v) {
   if (HK == HK_JACOBI) return mul2(p2(omega / s[4]), v.mb);
-  if (IN) return dot9p(wi, v);
+  if (IN) return dot9w<ODD>(wi, v);
   float2 h = p2(0.f);
   if (inside(i, j, L.n)) h.x = tapply_H<SK_CONST, HK, false>(L, s, wtab, wi, omega, i, j, lane_win(v, 0));
   if (inside(i, j + 1, L.n)) h.y = tapply_H<SK_CONST, HK, false>(L, s, wtab, wi, omega, i, j + 1, lane_win(v, 1));
   return h;
-}
-
-// Work item of thread t in a phase over NQ pairs and NS row strips: pairs 0 .. 15 first, one
-// strip per half-warp (16 consecutive pairs of a row: conflict-free 64-bit shared accesses),
-// then pairs 16 .. NQ-1 of every strip; false for the threads left idle.
-template <int NQ, int NS>
-__device__ __forceinline__ bool chunk_item(int t, int& q, int& strip) {
-  if (t < 16 * NS) {
-    q = t & 15;
-    strip = t >> 4;
-    return true;
-  }
-  t -= 16 * NS;
-  if (t < (NQ - 16) * NS) {
-    q = 16 + t % (NQ - 16);
-    strip = t / (NQ - 16);
-    return true;
-  }
-  return false;
 }
 
 // zero the lanes of a pair that lie outside the grid (edge tiles)
@@ -777,7 +685,7 @@ __device__ __forceinline__ void up0p_tile(const LevelDev& L, const float (&s)[9]
 #pragma unroll
       for (int k = 0; k < KS; ++k) {
         row_odd(c + (k + 2) * XW, v.lc, v.mc, v.rc);
-        float2 tv = sub2(make_float2(rp[k * XW], rp[k * XW + 1]), dot9p(s, v));
+        float2 tv = sub2(make_float2(rp[k * XW], rp[k * XW + 1]), dot9w<true>(s, v));
         if (!IN) tv = mask2(tv, R0 - 2 + t0 + k, j, n);
         rp[k * XW] = tv.x;
         rp[k * XW + 1] = tv.y;
@@ -810,7 +718,7 @@ __device__ __forceinline__ void up0p_tile(const LevelDev& L, const float (&s)[9]
         if (ti < RES_H) {
           if (HK != HK_JACOBI) row_even(c + (k + 2) * XW, v.lc, v.mc, v.rc);
           else v.mb = ld2(c + (k + 1) * XW);
-          const float2 e = add2(ld2(e1 + k * XW), tapply_H2<HK, IN>(L, s, wtab, wi, omega, i, j, v));
+          const float2 e = add2(ld2(e1 + k * XW), tapply_H2<HK, IN, false>(L, s, wtab, wi, omega, i, j, v));
           float2 sum, err, hi, lo;
           two_sum2(ld2(ph + k * XW), e, sum, err);
           err = add2(err, ld2(pl + k * XW));
@@ -992,7 +900,7 @@ __device__ __forceinline__ void downp_tile(const LevelDev& L, const float (&s)[9
         if (ES % KS == 0 || ti < ES) {
           if (HK != HK_JACOBI) row_odd(c + (k + 2) * XW, v.lc, v.mc, v.rc);
           else v.mb = make_float2(c[(k + 1) * XW + 1], c[(k + 1) * XW + 2]);
-          float2 e = tapply_H2<HK, IN>(L, s, wtab, wi, omega, i, j, v);
+          float2 e = tapply_H2<HK, IN, true>(L, s, wtab, wi, omega, i, j, v);
           if (!IN) e = mask2(e, i, j, n);
           st2(es + ti * EPW + 2 * q, e);
           if ((unsigned)(ti - 1) < (unsigned)TB) {
@@ -1024,7 +932,7 @@ __device__ __forceinline__ void downp_tile(const LevelDev& L, const float (&s)[9
         const int ti = t0 + k;
         if (ti < NR) {
           row_odd(c + (k + 2) * EPW, v.lc, v.mc, v.rc);
-          float2 sv = sub2(ld2(rp + k * XW), dot9p(s, v));
+          float2 sv = sub2(ld2(rp + k * XW), dot9w<true>(s, v));
           if (!IN) sv = mask2(sv, R0 + ti, j, n);
           st2(rp + k * XW, sv);
           v.shift();
