@@ -1102,6 +1102,65 @@ __global__ void __launch_bounds__(NT) k_update_residual(const __grid_constant__ 
   }
 }
 
+// k_update_residual on constant stencils in pairs (128 threads): the update of the
+// iterate over the whole box as 64-bit pairs, then the paired compensated residual of
+// k_up0p with b read through L2 (prefetched when the CTA starts).
+__global__ void __launch_bounds__(NTP, 8) k_update_residualp(const __grid_constant__ ResMaps X,
+                                                             const __grid_constant__ CUtensorMap E,
+                                                             const ProbDev* __restrict__ probs,
+                                                             ProbState* __restrict__ state, float* __restrict__ partials,
+                                                             int ntiles_max, float rtol, int max_cycles,
+                                                             float* __restrict__ xhi, float* __restrict__ xlo,
+                                                             float* __restrict__ rnew, const float* __restrict__ b0,
+                                                             const int* __restrict__ act) {
+  pdl_trigger();
+  const int p = act ? act[blockIdx.y] : blockIdx.y;
+  const LevelDev L = probs[p].lv[0];
+  const int n = L.n;
+  const int ntx = (n + TB - 1) / TB, ntiles = ntx * ntx;
+  const int tile = blockIdx.x;
+  if (tile >= ntiles) return;
+  const int R0 = (tile / ntx) * TB, C0 = (tile % ntx) * TB;
+  __shared__ __align__(128) float xh[RES_H * XW];
+  __shared__ __align__(128) float xl[RES_H * XW];
+  __shared__ __align__(128) float es[RES_H * XW];
+  __shared__ __align__(8) uint64_t bar;
+  float s[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) s[k] = L.s[k];
+  if (threadIdx.x == 0) tma_prefetch_3d(&X.b, C0, R0, p);
+  pdl_wait();
+  if (!st_active(state + p)) return;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    mbar_arrive_expect_tx(&bar, 3 * RES_H * XW * sizeof(float));
+    tma_load_3d(xh, &X.xh, &bar, C0 - 4, R0 - 1, p);
+    tma_load_3d(xl, &X.xl, &bar, C0 - 4, R0 - 1, p);
+    tma_load_3d(es, &E, &bar, C0 - 4, R0 - 1, p);
+  }
+  __syncthreads();
+  if (!tile_wait(&bar, state[p])) return;
+  // the box is zero outside the grid in all three arrays, so the update keeps it zero there
+  for (int q = 2 * threadIdx.x; q < RES_H * XW; q += 2 * NTP) {
+    float2 sum, err, hi, lo;
+    two_sum2(ld2(xh + q), ld2(es + q), sum, err);
+    err = add2(err, ld2(xl + q));
+    fast_two_sum2(sum, err, hi, lo);
+    st2(xh + q, hi);
+    st2(xl + q, lo);
+  }
+  __syncthreads();
+  const size_t po = (size_t)p * n * L.pitch;
+  const float acc = inner_tile(R0, C0, n)
+                        ? residual_pair<true>(L, s, xh, xl, R0, C0, rnew + po, xhi + po, xlo + po, b0 + po)
+                        : residual_pair<false>(L, s, xh, xl, R0, C0, rnew + po, xhi + po, xlo + po, b0 + po);
+  float rhi, rlo;
+  if (block_partial_and_last<NTP>(acc, partials + (size_t)p * ntiles_max, &state[p].counter, ntiles, tile, rhi, rlo)) {
+    if (threadIdx.x == 0) decide(state[p], rhi, rlo, rtol, max_cycles);
+  }
+}
+
 // -------------------------------------------------------------- pack / unpack
 // dense [nprob][n][n] <-> pitched [nprob][n][pitch]; src == nullptr packs zeros
 __global__ void k_pack(const float* __restrict__ src, float* __restrict__ dst, int n, int pitch) {
@@ -1236,8 +1295,8 @@ cudaError_t launch_update_residual(const CycleArgs& a, const CUtensorMap& e0, fl
   a.prof->begin(PK_UP0, a.stream);
   cudaError_t e;
   if (a.sk == SK_CONST)
-    e = launch_pdl(a.pdl, k_update_residual<SK_CONST>, grid, dim3(NT), 0, a.stream, X, e0, (const ProbDev*)a.probs,
-                   a.state, a.partials, a.ntiles_max, rtol, max_cycles, xhn, xln, rnew, a.active);
+    e = launch_pdl(a.pdl, k_update_residualp, grid, dim3(NTP), 0, a.stream, X, e0, (const ProbDev*)a.probs, a.state,
+                   a.partials, a.ntiles_max, rtol, max_cycles, xhn, xln, rnew, (const float*)a.b0, a.active);
   else
     e = launch_pdl(a.pdl, k_update_residual<SK_FIELD>, grid, dim3(NT), 0, a.stream, X, e0, (const ProbDev*)a.probs,
                    a.state, a.partials, a.ntiles_max, rtol, max_cycles, xhn, xln, rnew, a.active);
