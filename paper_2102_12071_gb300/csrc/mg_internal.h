@@ -116,6 +116,9 @@ struct LinMaps {
   CUtensorMap eh[MG_MAXL]; // the linear up-sweep: e_l with its six-point halo
   CUtensorMap ec[MG_MAXL]; // ... the coarse correction its prolongation reads
   CUtensorMap e0f;         // ... level 0's final correction (scratch lin_wa), boxed like e0
+  // the tiled restriction (constant stencils): r_l and e_l of a 32 x 32 tile with the rows
+  // and columns the residual needs, and the 16 x 16 coarse tile of r_{l+1}
+  CUtensorMap rr0a, rr0b, rr[MG_MAXL], er[MG_MAXL], rc[MG_MAXL];
 };
 bool build_lin_maps(LinMaps& M, const LevelArrays& A, float* lin_t, float* lin_wa, int nprob, int lstar);
 

@@ -537,6 +537,98 @@ __global__ void __launch_bounds__(LTP, 8) k_lin_Htile(const __grid_constant__ CU
     lin_chain<true, ACC>(U, BA, BB, ph, R0, C0, n, d, pitch);
 }
 
+// ------------------------------------------------------------- tiled restriction
+// r_{l+1} = P^T (r - A e) after the pre-smoothing, on constant stencils: one 32 x 32 fine
+// tile (16 x 16 coarse points) per CTA of 128 threads.  TMA copies of r (rows R0 .. R0+32)
+// and e (rows R0-1 .. R0+33), both over columns C0-4 .. C0+35; s = r - A e on rows R0 ..
+// R0+32 and box columns 4 .. 37 in pairs (4 + 2q, 5 + 2q) over r in place (the pair's own
+// values are aligned 64-bit accesses, its window rows one 64-bit and two single loads); the
+// restriction two coarse points per thread (the order of restrict_at); r_c out by a TMA
+// store.  Every coarse point inside the grid reads fine points inside it only, and the store
+// drops coarse points outside, so no masking is needed.
+constexpr int RW = 40, RRH = HT + 1, REH = HT + 3, RCT = HT / 2;
+
+__global__ void __launch_bounds__(LTP, 8) k_lin_restrict_tile(const __grid_constant__ CUtensorMap mR,
+                                                              const __grid_constant__ CUtensorMap mE,
+                                                              const __grid_constant__ CUtensorMap mRc,
+                                                              const ProbDev* __restrict__ probs,
+                                                              ProbState* __restrict__ state,
+                                                              const int* __restrict__ act, int l) {
+  pdl_trigger();
+  const int p = act ? act[blockIdx.y] : blockIdx.y;
+  const LevelDev L = probs[p].lv[l];
+  const int n = L.n, ntx = (n + HT - 1) / HT;
+  const int tile = blockIdx.x;
+  if (tile >= ntx * ntx) return;
+  const int R0 = (tile / ntx) * HT, C0 = (tile % ntx) * HT;
+  __shared__ __align__(128) float rs[RRH * RW];
+  __shared__ __align__(128) float es[REH * RW];
+  __shared__ __align__(128) float rco[RCT * RCT];
+  __shared__ __align__(8) uint64_t bar;
+  float s[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) s[k] = L.s[k];
+  pdl_wait();
+  if (!st_active(state + p)) return;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    mbar_arrive_expect_tx(&bar, (RRH + REH) * RW * sizeof(float));
+    tma_load_3d(rs, &mR, &bar, C0 - 4, R0, p);
+    tma_load_3d(es, &mE, &bar, C0 - 4, R0 - 1, p);
+  }
+  __syncthreads();
+  if (!tile_wait(&bar, state[p])) return;
+  {
+    constexpr int NQ = 17, K = 5, NS = (RRH + K - 1) / K;
+    static_assert(16 * NS + (NQ - 16) * NS <= LTP, "residual needs more threads than the CTA has");
+    int q, strip;
+    if (chunk_item<NQ, NS>(threadIdx.x, q, strip)) {
+      const int t0 = strip * K, c = 4 + 2 * q;
+      const float* w = es + t0 * RW + c;  // window row a of s row t0 (e's row 0 is R0 - 1)
+      float* rp = rs + t0 * RW + c;
+      Win2 v;
+      row_even(w, v.la, v.ma, v.ra);
+      row_even(w + RW, v.lb, v.mb, v.rb);
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        if (t0 + k < RRH) {
+          row_even(w + (k + 2) * RW, v.lc, v.mc, v.rc);
+          st2(rp + k * RW, sub2(ld2(rp + k * RW), dot9w<false>(s, v)));
+          v.shift();
+        }
+      }
+    }
+  }
+  __syncthreads();
+  {
+    // coarse row a, coarse columns 2m, 2m+1: fine rows 2a .. 2a+2, columns 4m .. 4m+4 of the tile
+    const int a = threadIdx.x >> 3, m = threadIdx.x & 7;
+    const float* c = rs + 2 * a * RW + 4 * m + 4;
+    float2 x0[3], x1[3];
+    float z[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      x0[r] = ld2(c + r * RW);
+      x1[r] = ld2(c + r * RW + 2);
+      z[r] = c[r * RW + 4];
+    }
+    const float2 cen = make_float2(x0[1].y, x1[1].y);
+    const float2 edge = add2(add2(make_float2(x0[0].y, x1[0].y), make_float2(x0[2].y, x1[2].y)),
+                             add2(make_float2(x0[1].x, x1[1].x), make_float2(x1[1].x, z[1])));
+    const float2 corner = add2(add2(make_float2(x0[0].x, x1[0].x), make_float2(x1[0].x, z[0])),
+                               add2(make_float2(x0[2].x, x1[2].x), make_float2(x1[2].x, z[2])));
+    st2(rco + a * RCT + 2 * m, fma2(p2(0.25f), corner, fma2(p2(0.5f), edge, cen)));
+  }
+  fence_async_smem();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tma_store_3d(&mRc, rco, C0 / 2, R0 / 2, p);
+    tma_store_commit();
+    tma_store_wait();
+  }
+}
+
 // phi[l] <- the parameters of H^T: (f_5 .. f_1 f_6 reversed)^T = f_1^T .. f_5^T + f_6^T,
 // and f^T is the correlation with the mirrored kernel (tap 8 - t)
 __global__ void k_lin_transpose(float* phi, int nlev) {
@@ -657,12 +749,15 @@ cudaError_t launch_cycle_linear(const CycleArgs& a, float rtol, int max_cycles, 
     if (e != cudaSuccess) break;
     a.prof->launches++;
     a.prof->begin(cls, a.stream);
-    const dim3 gc = point_grid(a.nl[l + 1], np);
-    e = a.sk == SK_CONST
-            ? launch_pdl(a.pdl, k_lin_restrict<SK_CONST>, gc, dim3(PX, PY), 0, a.stream, probs, cst, a.active, l, r,
-                         (const float*)A.e[l], A.r[l + 1])
-            : launch_pdl(a.pdl, k_lin_restrict<SK_FIELD>, gc, dim3(PX, PY), 0, a.stream, probs, cst, a.active, l, r,
-                         (const float*)A.e[l], A.r[l + 1]);
+    if (a.sk == SK_CONST) {
+      const int nt = (a.nl[l] + HT - 1) / HT;
+      e = launch_pdl(a.pdl, k_lin_restrict_tile, dim3(nt * nt, np), dim3(LTP), 0, a.stream,
+                     l == 0 ? (parity ? M.rr0b : M.rr0a) : M.rr[l], M.er[l], M.rc[l], probs, a.state, a.active, l);
+    } else {
+      const dim3 gc = point_grid(a.nl[l + 1], np);
+      e = launch_pdl(a.pdl, k_lin_restrict<SK_FIELD>, gc, dim3(PX, PY), 0, a.stream, probs, cst, a.active, l, r,
+                     (const float*)A.e[l], A.r[l + 1]);
+    }
     a.prof->end(a.stream);
   }
   if (e != cudaSuccess) return e;
@@ -711,7 +806,12 @@ bool build_lin_maps(LinMaps& M, const LevelArrays& A, float* lin_t, float* lin_w
          // the correction level l's prolongation reads: f of a batched level, the tail's e
          make_map(&M.ec[l], l + 1 < lstar ? A.f[l + 1] : A.e[l + 1], A.n[l + 1], A.pitch[l + 1], nprob, UC, UC);
     if (ok && l >= 1) ok = make_map(&M.r[l], A.r[l], A.n[l], A.pitch[l], nprob, HXU, HR);
+    ok = ok && make_map(&M.er[l], A.e[l], A.n[l], A.pitch[l], nprob, RW, REH) &&
+         make_map(&M.rc[l], A.r[l + 1], A.n[l + 1], A.pitch[l + 1], nprob, RCT, RCT);
+    if (ok && l >= 1) ok = make_map(&M.rr[l], A.r[l], A.n[l], A.pitch[l], nprob, RW, RRH);
   }
+  ok = ok && make_map(&M.rr0a, A.r[0], A.n[0], A.pitch[0], nprob, RW, RRH) &&
+       make_map(&M.rr0b, A.r0b, A.n[0], A.pitch[0], nprob, RW, RRH);
   return ok;
 }
 
