@@ -153,14 +153,20 @@ __device__ void ct_down(const ProbDev& P, float* sm, const CtLayout& lay, const 
   float* e = sm + lay.a.off_e[l];
   float* t = sm + lay.a.off_t[l];
   const float* w = sm + lay.a.off_w[l];
+  float sr[9], wr[9];  // stencil and interior kernel in registers
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    sr[k] = sc[l][k];
+    wr[k] = wi[l][k];
+  }
   CT_FOR(max(0, i0 - 2), min(n, i1 + 2), n) {
     const int q = (i + o) * m + j + 1;
-    e[q] = pad_H<SK, HK>(V, sc[l], w, wi[l], omega, r + q, m, n, i, j);
+    e[q] = pad_H<SK, HK>(V, sr, w, wr, omega, r + q, m, n, i, j);
   }
   __syncthreads();
   CT_FOR(max(0, i0 - 1), min(n, i1 + 1), n) {
     const int q = (i + o) * m + j + 1;
-    t[q] = r[q] - pad_A<SK>(V, sc[l], e + q, m, n, i, j);
+    t[q] = r[q] - pad_A<SK>(V, sr, e + q, m, n, i, j);
   }
   __syncthreads();
   // coarse rows [I0, I1) of this CTA: fine rows 2I .. 2I+2 lie in the band and its first
@@ -210,11 +216,17 @@ __device__ void ct_up(const ProbDev& P, float* sm, const CtLayout& lay, const fl
     ec = rank == 0 ? e0 : cluster_map(e0, 0);
     Io = -1;
   }
+  float sr[9], wr[9];  // stencil and interior kernel in registers
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    sr[k] = sc[l][k];
+    wr[k] = wi[l][k];
+  }
   CT_FOR(max(0, i0 - 2), min(n, i1 + 2), n) e[(i + o) * m + j + 1] += prolong_at(i, j, ec, Io, -1, mc);
   __syncthreads();
   CT_FOR(max(0, i0 - 1), min(n, i1 + 1), n) {
     const int q = (i + o) * m + j + 1;
-    t[q] = r[q] - pad_A<SK>(V, sc[l], e + q, m, n, i, j);
+    t[q] = r[q] - pad_A<SK>(V, sr, e + q, m, n, i, j);
   }
   __syncthreads();
   if (l > ls) {
@@ -223,7 +235,7 @@ __device__ void ct_up(const ProbDev& P, float* sm, const CtLayout& lay, const fl
     float* dn = rank < MG_CT_C - 1 ? cluster_map(pl, rank + 1) : nullptr;
     CT_FOR(i0, i1, n) {
       const int q = (i + o) * m + j + 1;
-      const float v = e[q] + pad_H<SK, HK>(V, sc[l], w, wi[l], omega, t + q, m, n, i, j);
+      const float v = e[q] + pad_H<SK, HK>(V, sr, w, wr, omega, t + q, m, n, i, j);
       pl[q] = v;
       if (up && i == i0) up[q + B * m] = v;      // lower halo of the CTA above
       if (dn && i >= i1 - 2) dn[q - B * m] = v;  // upper halo of the CTA below
@@ -232,7 +244,7 @@ __device__ void ct_up(const ProbDev& P, float* sm, const CtLayout& lay, const fl
   } else {
     CT_FOR(i0, i1, n) {
       const int q = (i + o) * m + j + 1;
-      V.e[(size_t)i * V.pitch + j] = e[q] + pad_H<SK, HK>(V, sc[l], w, wi[l], omega, t + q, m, n, i, j);
+      V.e[(size_t)i * V.pitch + j] = e[q] + pad_H<SK, HK>(V, sr, w, wr, omega, t + q, m, n, i, j);
     }
     if (solo_below) cluster_sync();  // CTA 0 keeps its arrays until every CTA has read them
   }

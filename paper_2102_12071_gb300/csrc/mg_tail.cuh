@@ -4,6 +4,7 @@
 #pragma once
 #include "mg_common.cuh"
 #include "mg_ops.cuh"
+#include "mg_tma.cuh"
 
 namespace mg {
 
@@ -55,21 +56,26 @@ __host__ __device__ inline void tail_layout(const int* nl, int l0, int L, int hk
   tail_layout_tables(nl, l0, L, hk, o, t);
 }
 
-// A v at (i, j); c points at v(i, j) inside a ring-padded array of row stride m
+// sum_t w[t * stride] c[d_t] on a ring-padded array of row stride m, centre tap first
+__device__ __forceinline__ float tap9(const float* w, int stride, const float* c, int m) {
+  float acc = w[4 * stride] * c[0];
+  acc = fmaf(w[0], c[-m - 1], acc);
+  acc = fmaf(w[stride], c[-m], acc);
+  acc = fmaf(w[2 * stride], c[-m + 1], acc);
+  acc = fmaf(w[3 * stride], c[-1], acc);
+  acc = fmaf(w[5 * stride], c[1], acc);
+  acc = fmaf(w[6 * stride], c[m - 1], acc);
+  acc = fmaf(w[7 * stride], c[m], acc);
+  acc = fmaf(w[8 * stride], c[m + 1], acc);
+  return acc;
+}
+
+// A v at (i, j); c points at v(i, j) inside a ring-padded array of row stride m.  Callers
+// pass the constant stencil s as a copy in registers.
 template <int SK>
-__device__ __forceinline__ float pad_A(const LevelDev& L, const float* s, const float* c, int m, int n, int i, int j) {
-  if (SK == SK_CONST) {
-    float acc = s[4] * c[0];
-    acc = fmaf(s[0], c[-m - 1], acc);
-    acc = fmaf(s[1], c[-m], acc);
-    acc = fmaf(s[2], c[-m + 1], acc);
-    acc = fmaf(s[3], c[-1], acc);
-    acc = fmaf(s[5], c[1], acc);
-    acc = fmaf(s[6], c[m - 1], acc);
-    acc = fmaf(s[7], c[m], acc);
-    acc = fmaf(s[8], c[m + 1], acc);
-    return acc;
-  }
+__device__ __forceinline__ float pad_A(const LevelDev& L, const float (&s)[9], const float* c, int m, int n, int i,
+                                       int j) {
+  if (SK == SK_CONST) return tap9(s, 1, c, m);
   const size_t nn = (size_t)n * n;
   const float* a = L.st + (size_t)i * n + j;
   float acc = __ldg(a + 4 * nn) * c[0];
@@ -85,38 +91,20 @@ __device__ __forceinline__ float pad_A(const LevelDev& L, const float* s, const 
 }
 
 // H v at (i, j) on a ring-padded array; wi holds the interior network kernel of the level
+// (a copy in registers: interior points read no weights from memory)
 template <int SK, int HK>
-__device__ __forceinline__ float pad_H(const LevelDev& L, const float* s, const float* wtab, const float* wi,
+__device__ __forceinline__ float pad_H(const LevelDev& L, const float (&s)[9], const float* wtab, const float (&wi)[9],
                                        float omega, const float* c, int m, int n, int i, int j) {
   if (HK == HK_JACOBI) {
     const float d = (SK == SK_CONST) ? s[4] : __ldg(L.st + 4 * (size_t)n * n + (size_t)i * n + j);
     return (omega / d) * c[0];
   }
-  const float* w;
-  int stride;
   if (HK == HK_TABLE) {
     const int T = L.T, M = MG_NET_MARGIN;
-    if (T == MG_PROXY && i >= M && i < n - M && j >= M && j < n - M) {
-      w = wi;
-      stride = 1;
-    } else {
-      w = wtab + kclass(i, n, T) * T + kclass(j, n, T);
-      stride = T * T;
-    }
-  } else {
-    w = L.W + (size_t)i * n + j;
-    stride = n * n;
+    if (T == MG_PROXY && i >= M && i < n - M && j >= M && j < n - M) return tap9(wi, 1, c, m);
+    return tap9(wtab + kclass(i, n, T) * T + kclass(j, n, T), T * T, c, m);
   }
-  float acc = w[4 * stride] * c[0];
-  acc = fmaf(w[0], c[-m - 1], acc);
-  acc = fmaf(w[stride], c[-m], acc);
-  acc = fmaf(w[2 * stride], c[-m + 1], acc);
-  acc = fmaf(w[3 * stride], c[-1], acc);
-  acc = fmaf(w[5 * stride], c[1], acc);
-  acc = fmaf(w[6 * stride], c[m - 1], acc);
-  acc = fmaf(w[7 * stride], c[m], acc);
-  acc = fmaf(w[8 * stride], c[m + 1], acc);
-  return acc;
+  return tap9(L.W + (size_t)i * n + j, n * n, c, m);
 }
 
 // interior points of level side n, warp per row and lane per column (no integer division)
@@ -218,9 +206,12 @@ __device__ void tail_cycle(const ProbDev& P, float* sm, const TailLayout& lay, c
     const float* r = sm + lay.off_r[l];
     const float* e = sm + lay.off_e[l];
     float* t = sm + lay.off_t[l];
+    float sr[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) sr[k] = sc[l][k];
     TAIL_FOR(n) {
       const int q = (i + 1) * m + j + 1;
-      t[q] = r[q] - pad_A<SK>(Lv, sc[l], e + q, m, n, i, j);
+      t[q] = r[q] - pad_A<SK>(Lv, sr, e + q, m, n, i, j);
     }
     __syncthreads();
   };
@@ -235,9 +226,15 @@ __device__ void tail_cycle(const ProbDev& P, float* sm, const TailLayout& lay, c
     } else if (HK == HK_STACK3) {
       tail_stack_H(Lv.W, t, e, true, sm + lay.off_s1, sm + lay.off_s2, n, m);
     } else {
+      float sr[9], wr[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        sr[k] = sc[l][k];
+        wr[k] = wi[l][k];
+      }
       TAIL_FOR(n) {
         const int q = (i + 1) * m + j + 1;
-        e[q] += pad_H<SK, HK>(Lv, sc[l], w, wi[l], omega, t + q, m, n, i, j);
+        e[q] += pad_H<SK, HK>(Lv, sr, w, wr, omega, t + q, m, n, i, j);
       }
     }
     __syncthreads();
@@ -254,9 +251,15 @@ __device__ void tail_cycle(const ProbDev& P, float* sm, const TailLayout& lay, c
     } else if (HK == HK_STACK3) {
       tail_stack_H(Lv.W, r, e, false, sm + lay.off_s1, sm + lay.off_s2, n, m);
     } else {
+      float sr[9], wr[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        sr[k] = sc[l][k];
+        wr[k] = wi[l][k];
+      }
       TAIL_FOR(n) {
         const int q = (i + 1) * m + j + 1;
-        e[q] = pad_H<SK, HK>(Lv, sc[l], w, wi[l], omega, r + q, m, n, i, j);
+        e[q] = pad_H<SK, HK>(Lv, sr, w, wr, omega, r + q, m, n, i, j);
       }
     }
     __syncthreads();
@@ -296,8 +299,9 @@ __device__ void tail_cycle(const ProbDev& P, float* sm, const TailLayout& lay, c
 }
 
 // Stencil constants, class tables of levels l0 .. L-2 and the coarsest inverse into shared
-// memory.  Every thread issues all of its global loads before its stores, so their
-// latencies overlap (copying level by level would wait on each level in turn).
+// memory by asynchronous copies: every copy of every level is in flight at once (copying
+// level by level through registers would wait on each level in turn).  The caller's next
+// barrier makes them visible.
 template <int SK, int HK>
 __device__ void load_level_data(const ProbDev& P, float* sm, const TailLayout& lay, float (*sc)[9], int l0, int L) {
   __shared__ const float* src[MG_MAXL];
@@ -330,26 +334,16 @@ __device__ void load_level_data(const ProbDev& P, float* sm, const TailLayout& l
     pre[nq] = o;
   }
   __syncthreads();
-  const int total = pre[nq];
-  constexpr int U = 4;
-  for (int base = threadIdx.x; base < total; base += U * blockDim.x) {
-    float v[U];
-    int d[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int k = base + u * blockDim.x;
-      d[u] = -1;
-      if (k < total) {
-        int q = 0;
-        while (k >= pre[q + 1]) ++q;
-        v[u] = __ldg(src[q] + (k - pre[q]));
-        d[u] = dst[q] + (k - pre[q]);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (d[u] >= 0) sm[d[u]] = v[u];
+  // one 4-byte asynchronous copy per element: every copy of the thread is in flight at once
+  // and nothing is staged in registers; the caller's barrier after cp_async_wait_all makes
+  // them visible to the CTA
+  for (int q = 0; q < nq; ++q) {
+    const int cnt = pre[q + 1] - pre[q];
+    const float* sq = src[q];
+    float* dq = sm + dst[q];
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) cp_async4(dq + k, sq + k);
   }
+  cp_async_wait_all();
 }
 
 // interior network kernel of each table level, from the shared-memory tables

@@ -51,6 +51,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
+// 4 bytes global -> shared without register staging (cp.async); complete after
+// cp_async_wait_all() in the issuing thread
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // box of the tensor map at element coordinates (x, y, z) -> shared memory, completion
 // signalled on `bar` (transaction bytes = the whole box, zero-filled parts included)
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
