@@ -278,10 +278,20 @@ __device__ void tail_cycle(const ProbDev& P, float* sm, const TailLayout& lay, c
     const float* r = sm + lay.off_r[L - 1];
     float* e = sm + lay.off_e[L - 1];
     if ((int)threadIdx.x < mm) {
+      // row threadIdx.x of the inverse times r, one partial sum per row of r (independent
+      // chains; no division in the index arithmetic)
       const double* Ai = reinterpret_cast<const double*>(sm + lay.off_inv) + threadIdx.x * mm;
-      double acc = 0.0;
-      for (int k = 0; k < mm; ++k) acc = fma(Ai[k], (double)r[(k / nL + 1) * mL + k % nL + 1], acc);
-      e[(threadIdx.x / nL + 1) * mL + threadIdx.x % nL + 1] = (float)acc;
+      double acc0 = 0.0, acc1 = 0.0;
+#pragma unroll 4
+      for (int a = 0; a < nL; ++a) {
+        const float* ra = r + (a + 1) * mL + 1;
+        const double* Aa = Ai + a * nL;
+        double sa = 0.0;
+        for (int b = 0; b < nL; ++b) sa = fma(Aa[b], (double)ra[b], sa);
+        if (a & 1) acc1 += sa;
+        else acc0 += sa;
+      }
+      e[(threadIdx.x / nL + 1) * mL + threadIdx.x % nL + 1] = (float)(acc0 + acc1);
     }
     __syncthreads();
   }
