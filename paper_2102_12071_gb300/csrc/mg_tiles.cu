@@ -109,7 +109,7 @@ __device__ __forceinline__ void load_table(const LevelDev& L, bool in, float* wt
     for (int k = 0; k < 9; ++k) wi[k] = L.W[k * T * T + M * T + M];
   } else {
     const int cnt = 9 * T * T;
-    for (int t = threadIdx.x; t < cnt; t += NT) wtab[t] = L.W[t];
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) wtab[t] = L.W[t];
   }
 }
 
@@ -1102,6 +1102,141 @@ __global__ void __launch_bounds__(NT) k_update_residual(const __grid_constant__ 
   }
 }
 
+// ------------------------------------------------------------ k_up in pairs
+// k_up on constant stencils (levels >= 1) with two columns per thread (128 threads): e1 =
+// e + P e_c over the whole box width in 8-row strips of pairs (a coarse row's pair sum serves
+// two fine rows), t = r - A e1 on even pairs (the pair's r and t are 64-bit accesses), then
+// e1 + H t on the tile's pairs, written to the level's array of its own (f).
+template <int HK, bool IN>
+__device__ __forceinline__ void upp_tile(const LevelDev& L, const float (&s)[9], const float* wtab,
+                                         const float (&wi)[9], float omega, float* es, float* rs, const float* ecs,
+                                         int R0, int C0) {
+  const int n = L.n, t = threadIdx.x;
+  {
+    // e1 on rows R0-2 .. R0+33 (es row rr: fine row 2m reads coarse box rows m, m+1, row
+    // 2m+1 coarse row m+1 twice) and box columns 0 .. 39 (pair q: coarse box columns
+    // (q+1, q+2) and (q+2, q+2), as in k_up0p)
+    constexpr int NQ = XW / 2, KS = 8, NS = (UPE_H + KS - 1) / KS, LAST = UPE_H - KS * (NS - 1);
+    if (t < NQ * NS) {
+      const int q = t % NQ, s8 = t / NQ;
+      const float* cb = ecs + 4 * s8 * EC_W + q + 1;
+      float* ep = es + KS * s8 * XW + 2 * q;
+      float2 S[KS / 2 + 1];
+      if (s8 < NS - 1) {
+#pragma unroll
+        for (int m = 0; m <= KS / 2; ++m) {
+          const float a = cb[m * EC_W], b = cb[m * EC_W + 1];
+          S[m] = add2(make_float2(a, b), p2(b));
+        }
+#pragma unroll
+        for (int k = 0; k < KS; ++k)
+          st2(ep + k * XW, fma2(p2(0.25f), add2(S[(k + 1) >> 1], S[(k >> 1) + 1]), ld2(ep + k * XW)));
+      } else {
+#pragma unroll
+        for (int m = 0; m <= LAST / 2; ++m) {
+          const float a = cb[m * EC_W], b = cb[m * EC_W + 1];
+          S[m] = add2(make_float2(a, b), p2(b));
+        }
+#pragma unroll
+        for (int k = 0; k < LAST; ++k)
+          st2(ep + k * XW, fma2(p2(0.25f), add2(S[(k + 1) >> 1], S[(k >> 1) + 1]), ld2(ep + k * XW)));
+      }
+    }
+  }
+  __syncthreads();
+  {
+    // t = r - A e1 on rows R0-1 .. R0+32, box columns 2 .. 37 (pair q: 2q+2, 2q+3)
+    constexpr int NQ = (TB + 4) / 2, KS = 5, NS = (UPR_H + KS - 1) / KS;
+    static_assert(16 * NS + (NQ - 16) * NS <= NTP, "phase t");
+    int q, sb;
+    if (chunk_item<NQ, NS>(t, q, sb)) {
+      const int t0 = sb * KS, j = C0 - 2 + 2 * q;
+      const float* c = es + t0 * XW + 2 * q + 2;  // column c of window row a
+      float* rp = rs + t0 * XW + 2 * q + 2;
+      Win2 v;
+      row_even(c, v.la, v.ma, v.ra);
+      row_even(c + XW, v.lb, v.mb, v.rb);
+#pragma unroll
+      for (int k = 0; k < KS; ++k) {
+        if (UPR_H % KS == 0 || t0 + k < UPR_H) {
+          row_even(c + (k + 2) * XW, v.lc, v.mc, v.rc);
+          float2 tv = sub2(ld2(rp + k * XW), dot9w<false>(s, v));
+          if (!IN) tv = mask2(tv, R0 - 1 + t0 + k, j, n);
+          st2(rp + k * XW, tv);
+          v.shift();
+        }
+      }
+    }
+  }
+  __syncthreads();
+  {
+    // e1 + H t on the tile: pair q = grid columns C0 + 2q, C0 + 2q + 1, 4-row strips
+    constexpr int KS = 4;
+    const int q = t & 15, t0 = (t >> 4) * KS, j = C0 + 2 * q;
+    const float* c = rs + t0 * XW + 2 * q + 4;
+    const float* e1 = es + (t0 + 2) * XW + 2 * q + 4;
+    float* out = L.f + (size_t)(R0 + t0) * L.pitch + j;
+    Win2 v;
+    if (HK != HK_JACOBI) {
+      row_even(c, v.la, v.ma, v.ra);
+      row_even(c + XW, v.lb, v.mb, v.rb);
+    }
+#pragma unroll
+    for (int k = 0; k < KS; ++k) {
+      const int i = R0 + t0 + k;
+      if (HK != HK_JACOBI) row_even(c + (k + 2) * XW, v.lc, v.mc, v.rc);
+      else v.mb = ld2(c + (k + 1) * XW);
+      const float2 e = add2(ld2(e1 + k * XW), tapply_H2<HK, IN, false>(L, s, wtab, wi, omega, i, j, v));
+      float* d = out + (size_t)k * L.pitch;
+      if (IN) {
+        st2(d, e);  // e is still read with halos by other CTAs: f is an array of its own
+      } else {
+        if (inside(i, j, n)) d[0] = e.x;
+        if (inside(i, j + 1, n)) d[1] = e.y;
+      }
+      if (HK != HK_JACOBI) v.shift();
+    }
+  }
+}
+
+template <int HK>
+__global__ void __launch_bounds__(NTP, 8) k_upp(const __grid_constant__ UpMaps M, const ProbDev* __restrict__ probs,
+                                                ProbState* __restrict__ state, int l, float omega,
+                                                const int* __restrict__ act) {
+  pdl_trigger();
+  const int p = act ? act[blockIdx.y] : blockIdx.y;
+  const LevelDev L = probs[p].lv[l];
+  const int n = L.n;
+  const int ntx = (n + TB - 1) / TB;
+  const int tile = blockIdx.x;
+  if (tile >= ntx * ntx) return;
+  const int R0 = (tile / ntx) * TB, C0 = (tile % ntx) * TB;
+  __shared__ __align__(128) float es[UPE_H * XW];  // e, then e1 = e + P e_c in place
+  __shared__ __align__(128) float rs[UPR_H * XW];  // r, then t = r - A e1 in place
+  __shared__ __align__(128) float ecs[EC_H * EC_W];
+  __shared__ float wtab[HK == HK_TABLE ? 9 * MG_PROXY * MG_PROXY : 1];
+  __shared__ __align__(8) uint64_t bar;
+  const bool in = inner_tile(R0, C0, n);
+  float s[9], wi[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) s[k] = L.s[k];
+  if (HK == HK_TABLE) load_table(L, in, wtab, wi);
+  pdl_wait();
+  if (!st_active(state + p)) return;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    mbar_arrive_expect_tx(&bar, ((UPE_H + UPR_H) * XW + EC_H * EC_W) * sizeof(float));
+    tma_load_3d(es, &M.e, &bar, C0 - 4, R0 - 2, p);
+    tma_load_3d(rs, &M.r, &bar, C0 - 4, R0 - 1, p);
+    tma_load_3d(ecs, &M.ec, &bar, C0 / 2 - 4, R0 / 2 - 2, p);
+  }
+  __syncthreads();
+  if (!tile_wait(&bar, state[p])) return;
+  if (in) upp_tile<HK, true>(L, s, wtab, wi, omega, es, rs, ecs, R0, C0);
+  else upp_tile<HK, false>(L, s, wtab, wi, omega, es, rs, ecs, R0, C0);
+}
+
 // k_update_residual on constant stencils in pairs (128 threads): the update of the
 // iterate over the whole box as 64-bit pairs, then the paired compensated residual of
 // k_up0p with b read through L2 (prefetched when the CTA starts).
@@ -1304,6 +1439,17 @@ cudaError_t launch_update_residual(const CycleArgs& a, const CUtensorMap& e0, fl
   return e;
 }
 
+// the up-sweep of a tiled level >= 1: the paired kernel on constant stencils, k_up on fields
+template <int SK, int HK>
+static cudaError_t launch_up(bool pdl, dim3 grid, cudaStream_t s, const UpMaps& um, const ProbDev* probs,
+                             ProbState* state, int l, float omega, const int* act) {
+  if constexpr (SK == SK_CONST)
+    return launch_pdl(pdl, k_upp<HK>, grid, dim3(NTP), 0, s, um, probs, state, l, omega, act);
+  else
+    return launch_pdl(pdl, k_up<SK, HK, false>, grid, dim3(NT), 0, s, um, probs, state, l, omega, (float*)nullptr,
+                      (float*)nullptr, act);
+}
+
 // the down-sweep of a tiled level: the paired kernel on constant stencils, k_down on fields
 template <int SK, int HK>
 static cudaError_t launch_down(bool pdl, dim3 grid, cudaStream_t s, const DownMaps& dm, const ProbDev* probs,
@@ -1340,7 +1486,6 @@ cudaError_t launch_cycle(const CycleArgs& a, float rtol, int max_cycles, int par
   if (a.hk != HK_JACOBI && a.hk != HK_TABLE && a.hk != HK_FIELD) return cudaErrorNotSupported;
   const int ls = a.lstar, np = nlaunch(a);
   const ProbDev* probs = a.probs;
-  float* const nul = nullptr;
   cudaError_t e = cudaSuccess;
   for (int l = 0; l < ls && e == cudaSuccess; ++l) {
     const int nt = tiles_per_side(a.nl[l]);
@@ -1381,9 +1526,8 @@ cudaError_t launch_cycle(const CycleArgs& a, float rtol, int max_cycles, int par
                                             rtol, max_cycles, xhn, xln, rnew, a.b0, a.active)));
     }
     else
-      MG_DISPATCH(a.sk, a.hk,
-                  (e = launch_pdl(pdl, k_up<SK_, HK_, false>, grid, dim3(NT), 0, a.stream, a.maps->up[l], probs, a.state,
-                                  l, a.omega, nul, nul, a.active)));
+      MG_DISPATCH(a.sk, a.hk, (e = launch_up<SK_, HK_>(pdl, grid, a.stream, a.maps->up[l], probs, a.state, l, a.omega,
+                                                       a.active)));
     a.prof->end(a.stream);
   }
   return e;
