@@ -602,23 +602,25 @@ __global__ void __launch_bounds__(LTP, 8) k_lin_restrict_tile(const __grid_const
   }
   __syncthreads();
   {
-    // coarse row a, coarse columns 2m, 2m+1: fine rows 2a .. 2a+2, columns 4m .. 4m+4 of the tile
-    const int a = threadIdx.x >> 3, m = threadIdx.x & 7;
-    const float* c = rs + 2 * a * RW + 4 * m + 4;
-    float2 x0[3], x1[3];
-    float z[3];
+    // coarse column b = lane of a half-warp, coarse rows a and a + 8: fine rows 2a .. 2a+2
+    // and columns 2b .. 2b+2 of the tile (one 64-bit and one single load per row), the order
+    // of restrict_at
+    const int bq = threadIdx.x & 15, a0 = threadIdx.x >> 4;
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      x0[r] = ld2(c + r * RW);
-      x1[r] = ld2(c + r * RW + 2);
-      z[r] = c[r * RW + 4];
+    for (int h = 0; h < 2; ++h) {
+      const int a = a0 + 8 * h;
+      const float* c = rs + 2 * a * RW + 2 * bq + 4;
+      float2 u[3];
+      float z[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        u[q] = ld2(c + q * RW);
+        z[q] = c[q * RW + 2];
+      }
+      const float edge = (u[0].y + u[2].y) + (u[1].x + z[1]);
+      const float corner = (u[0].x + z[0]) + (u[2].x + z[2]);
+      rco[a * RCT + bq] = u[1].y + 0.5f * edge + 0.25f * corner;
     }
-    const float2 cen = make_float2(x0[1].y, x1[1].y);
-    const float2 edge = add2(add2(make_float2(x0[0].y, x1[0].y), make_float2(x0[2].y, x1[2].y)),
-                             add2(make_float2(x0[1].x, x1[1].x), make_float2(x1[1].x, z[1])));
-    const float2 corner = add2(add2(make_float2(x0[0].x, x1[0].x), make_float2(x1[0].x, z[0])),
-                               add2(make_float2(x0[2].x, x1[2].x), make_float2(x1[2].x, z[2])));
-    st2(rco + a * RCT + 2 * m, fma2(p2(0.25f), corner, fma2(p2(0.5f), edge, cen)));
   }
   fence_async_smem();
   __syncthreads();

@@ -882,7 +882,7 @@ __device__ __forceinline__ void downp_tile(const LevelDev& L, const float (&s)[9
   const int n = L.n, t = threadIdx.x;
   {
     // e = H r on rows R0-1 .. R0+33, box columns 3 .. 38 (pair q: 2q+3, 2q+4; the residual
-    // reads 3 .. 37); the tile's own points also go to eo for the store of e
+    // reads 3 .. 37)
     constexpr int NQ = 18, KS = 5, NS = (ES + KS - 1) / KS;
     static_assert(16 * NS + (NQ - 16) * NS <= NTP, "phase e");
     int q, sa;
@@ -903,20 +903,17 @@ __device__ __forceinline__ void downp_tile(const LevelDev& L, const float (&s)[9
           float2 e = tapply_H2<HK, IN, true>(L, s, wtab, wi, omega, i, j, v);
           if (!IN) e = mask2(e, i, j, n);
           st2(es + ti * EPW + 2 * q, e);
-          if ((unsigned)(ti - 1) < (unsigned)TB) {
-            if (q >= 1 && q <= TB / 2) eo[(ti - 1) * TB + 2 * q - 1] = e.x;
-            if (q < TB / 2) eo[(ti - 1) * TB + 2 * q] = e.y;
-          }
           if (HK != HK_JACOBI) v.shift();
         }
       }
     }
   }
-  fence_async_smem();
   __syncthreads();
   {
     // s = r - A e on rows R0 .. R0+32, box columns 4 .. 37 (pair q: 2q+4, 2q+5; the
-    // restriction reads 4 .. 36), over r in place
+    // restriction reads 4 .. 36), over r in place; the centre pair of each window row on
+    // the tile is e at the pair's own points, which goes to eo (an aligned 64-bit store)
+    // for the store of e
     constexpr int NQ = 17, KS = 5, NR = TB + 1, NS = (NR + KS - 1) / KS;
     static_assert(16 * NS + (NQ - 16) * NS <= NTP, "phase s");
     int q, sb;
@@ -935,11 +932,13 @@ __device__ __forceinline__ void downp_tile(const LevelDev& L, const float (&s)[9
           float2 sv = sub2(ld2(rp + k * XW), dot9w<true>(s, v));
           if (!IN) sv = mask2(sv, R0 + ti, j, n);
           st2(rp + k * XW, sv);
+          if (ti < TB && q < TB / 2) st2(eo + ti * TB + 2 * q, make_float2(v.lb.y, v.rb.x));
           v.shift();
         }
       }
     }
   }
+  fence_async_smem();
   __syncthreads();
 }
 
@@ -1010,25 +1009,25 @@ __global__ void __launch_bounds__(NTP, 8) k_downp(const __grid_constant__ DownMa
     else downp_tile<HK, false>(L, s, wtab, wi, omega, r, es, eo, R0, C0);
     if (threadIdx.x == 0) tma_store_3d(&M.e, eo, C0, R0, p);
     {
-      // r_c = P^T s: coarse row a, coarse columns 2m, 2m+1 (fine rows 2a .. 2a+2, columns
-      // 4m .. 4m+4 of the tile), the order of restrict_at
-      const int a = threadIdx.x >> 3, m = threadIdx.x & 7;
-      const float* c = r + (2 * a + 2) * XW + 4 * m + 4;
-      float2 x0[3], x1[3];
-      float z[3];
+      // r_c = P^T s: coarse column b = lane of a half-warp, coarse rows a and a + 8 (fine
+      // rows 2a .. 2a+2 and columns 2b .. 2b+2 of the tile: one 64-bit and one single load
+      // per row), the order of restrict_at
+      const int bq = threadIdx.x & 15, a0 = threadIdx.x >> 4;
 #pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        x0[q] = ld2(c + q * XW);
-        x1[q] = ld2(c + q * XW + 2);
-        z[q] = c[q * XW + 4];
+      for (int h = 0; h < 2; ++h) {
+        const int a = a0 + 8 * h;
+        const float* c = r + (2 * a + 2) * XW + 2 * bq + 4;
+        float2 u[3];
+        float z[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          u[q] = ld2(c + q * XW);
+          z[q] = c[q * XW + 2];
+        }
+        const float edge = (u[0].y + u[2].y) + (u[1].x + z[1]);
+        const float corner = (u[0].x + z[0]) + (u[2].x + z[2]);
+        rco[a * TC + bq] = u[1].y + 0.5f * edge + 0.25f * corner;
       }
-      // centre, left and right columns of the two coarse points: (x0.y, x1.y), (x0.x, x1.x), (x1.x, z)
-      const float2 cen = make_float2(x0[1].y, x1[1].y);
-      const float2 edge = add2(add2(make_float2(x0[0].y, x1[0].y), make_float2(x0[2].y, x1[2].y)),
-                               add2(make_float2(x0[1].x, x1[1].x), make_float2(x1[1].x, z[1])));
-      const float2 corner = add2(add2(make_float2(x0[0].x, x1[0].x), make_float2(x1[0].x, z[0])),
-                                 add2(make_float2(x0[2].x, x1[2].x), make_float2(x1[2].x, z[2])));
-      st2(rco + a * TC + 2 * m, fma2(p2(0.25f), corner, fma2(p2(0.5f), edge, cen)));
     }
     fence_async_smem();
     __syncthreads();
