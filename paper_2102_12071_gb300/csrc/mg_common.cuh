@@ -15,10 +15,16 @@
 #define MG_HRING 256          // ring of relative residuals per problem (>= cycles per chunk)
 #define MG_TAIL_N 63          // levels at or below this size run in one CTA per problem
 #define MG_TAIL_SMEM_MAX (200 * 1024)  // dynamic shared memory limit of the tail kernels
-#define MG_CT_N 127           // levels at or below this size run in one CTA cluster per problem
-#ifndef MG_CT_SOLO
-#define MG_CT_SOLO 31         // ... and at or below this size in the cluster's first CTA alone
-#endif
+// Levels at or below MG_CT_N run in one CTA cluster per problem, and those at or below
+// MG_CT_SOLO in the cluster's first CTA alone.  With the network's class tables a level's
+// phases cost more, and the levels from 63 down with solo levels from 15 measured fastest;
+// Jacobi's cheaper phases keep the band levels 127 and 63 with solo levels from 31.
+#define MG_CT_N_TABLE 63
+#define MG_CT_SOLO_TABLE 15
+#define MG_CT_N_JACOBI 127
+#define MG_CT_SOLO_JACOBI 31
+#define MG_CT_N(hk) ((hk) == HK_JACOBI ? MG_CT_N_JACOBI : MG_CT_N_TABLE)
+#define MG_CT_SOLO(hk) ((hk) == HK_JACOBI ? MG_CT_SOLO_JACOBI : MG_CT_SOLO_TABLE)
 #ifndef MG_CT_C
 #define MG_CT_C 8             // CTAs per cluster (each owns a band of (n + 1) / MG_CT_C rows)
 #endif

@@ -240,8 +240,8 @@ def test_vcycle_without_low_part_on_tiled_path():
 
 def test_cluster_and_one_cta_tails_agree_on_a_batch():
     """16 problems of the bench family at 511^2 (CNN-free, Jacobi): the cycle laid out as
-    one CTA cluster per problem for levels <= 127 and as tiled kernels plus a one-CTA tail
-    for levels <= 63 computes the same histories."""
+    one CTA cluster per problem for levels <= 127 (Jacobi's layout) and as tiled kernels
+    plus a one-CTA tail for levels <= 63 computes the same histories."""
     n = 511
     params = inputs.rotated_params(inputs.SEED_PARAMS, 16)
     b = torch.from_numpy(np.stack([inputs.rhs_uniform(inputs.SEED_RHS + i, n) for i in range(16)])).cuda()
