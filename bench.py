@@ -38,10 +38,10 @@ WEIGHTS = os.path.join(ROOT, "paper_2102_12071_gb300", "weights", "cnn_rotated.n
 # k_residual: x_hi, x_lo, b in, r out; k_down level 0: r in, e out, r_c out (1/4);
 # k_up0: e, r, e_c (1/4), x_hi, x_lo, b in; x_hi, x_lo, r out
 BYTES_PER_DOF = {0: 16.0, 1: 9.0, 2: 33.0}
-# dram bytes (read + write) per launch of the current kernel versions from one ncu capture
-# of the 16 x 1023^2 batch (dram__bytes.sum.per_second x gpu__time_duration.sum); None
-# where the kernel changed since its last capture
-NCU_TRAFFIC = {1: 104.1e6, 2: 527.5e6}
+# dram bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the current
+# kernel versions from one ncu capture of the 16 x 1023^2 batch; None where the kernel
+# changed since its last capture
+NCU_TRAFFIC = {1: 67.16e6 + 36.28e6, 2: 353.91e6 + 169.91e6}
 NCU_TRAFFIC_SOURCE = {1: "profiles/k_downp_level0_rotated1023x16.md", 2: "profiles/k_up0p_rotated1023x16.md"}
 KERNEL_NAMES = {0: "k_residual (initial iterate)", 1: "k_downp(level 0)", 2: "k_up0p(level 0: up-sweep, x update, residual)",
                 3: "k_tail", 4: "k_downp(l>=1)", 5: "k_up(l>=1)"}
