@@ -96,9 +96,10 @@ typedef struct {
   int coarsest_n;   /* stop coarsening at this size (this build: 3)                  */
   int conv_bf16;    /* 1: network weights and activations rounded to bfloat16, FP32
                        accumulation; 0: FP32 throughout                                 */
-  int cluster_tail; /* 1: the levels below the finest of side <= 63 (network smoothers;
-                       row bands on the levels above 15) or <= 127 (Jacobi; bands above
-                       31) run in one cluster of 8 CTAs per problem with every vector in
+  int cluster_tail; /* 1: the levels below the finest of side <= 63 (network smoothers
+                       on fine grids of side >= 1023; row bands on the levels above 15)
+                       or <= 127 (otherwise; bands above 31) run in one cluster of 8 CTAs
+                       per problem with every vector in
                        shared memory, where the device can hold such a cluster, and the
                        levels above in tiled kernels; 0: the levels of side <= 63 run in
                        one CTA per problem and the levels above in tiled kernels.  Both

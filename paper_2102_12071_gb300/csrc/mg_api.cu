@@ -139,8 +139,8 @@ mg_status make_plan(const mg_problem* probs, int nprob, const mg_options* o, Pla
     return fail(MG_ERR_UNSUPPORTED, "tail does not fit in shared memory");
   if (!P.tail_solve && o->cluster_tail && !P.generic) {
     int ls = 1;  // the finest level stays tiled: it carries the outer residual and update
-    while (ls < L && P.nl[ls] > MG_CT_N(P.hk)) ++ls;
-    if (ls < L && P.nl[ls] > MG_CT_SOLO(P.hk) && ctail_smem_bytes(P.nl, ls, L, P.hk) <= MG_CT_SMEM_MAX) {
+    while (ls < L && P.nl[ls] > MG_CT_N(P.hk, P.nl[0])) ++ls;
+    if (ls < L && P.nl[ls] > MG_CT_SOLO(P.hk, P.nl[0]) && ctail_smem_bytes(P.nl, ls, L, P.hk) <= MG_CT_SMEM_MAX) {
       P.lstar = ls;
       P.ctail = 1;
     }

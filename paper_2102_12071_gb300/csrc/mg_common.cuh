@@ -16,15 +16,18 @@
 #define MG_TAIL_N 63          // levels at or below this size run in one CTA per problem
 #define MG_TAIL_SMEM_MAX (200 * 1024)  // dynamic shared memory limit of the tail kernels
 // Levels at or below MG_CT_N run in one CTA cluster per problem, and those at or below
-// MG_CT_SOLO in the cluster's first CTA alone.  With the network's class tables a level's
-// phases cost more, and the levels from 63 down with solo levels from 15 measured fastest;
-// Jacobi's cheaper phases keep the band levels 127 and 63 with solo levels from 31.
-#define MG_CT_N_TABLE 63
-#define MG_CT_SOLO_TABLE 15
-#define MG_CT_N_JACOBI 127
-#define MG_CT_SOLO_JACOBI 31
-#define MG_CT_N(hk) ((hk) == HK_JACOBI ? MG_CT_N_JACOBI : MG_CT_N_TABLE)
-#define MG_CT_SOLO(hk) ((hk) == HK_JACOBI ? MG_CT_SOLO_JACOBI : MG_CT_SOLO_TABLE)
+// MG_CT_SOLO in the cluster's first CTA alone (hk: the smoother kind, n0: the finest side).
+// On fine grids of side >= 1023 with the network smoothers, whose phases cost more, the
+// levels from 63 down with solo levels from 15 measured fastest; Jacobi, and the network
+// smoothers on smaller grids (measured at 255), keep band levels from 127 with solo levels
+// from 31.
+#define MG_CT_N_SHORT 63
+#define MG_CT_SOLO_SHORT 15
+#define MG_CT_N_LONG 127
+#define MG_CT_SOLO_LONG 31
+#define MG_CT_SHORT(hk, n0) ((hk) != HK_JACOBI && (n0) >= 1023)
+#define MG_CT_N(hk, n0) (MG_CT_SHORT(hk, n0) ? MG_CT_N_SHORT : MG_CT_N_LONG)
+#define MG_CT_SOLO(hk, n0) (MG_CT_SHORT(hk, n0) ? MG_CT_SOLO_SHORT : MG_CT_SOLO_LONG)
 #ifndef MG_CT_C
 #define MG_CT_C 8             // CTAs per cluster (each owns a band of (n + 1) / MG_CT_C rows)
 #endif

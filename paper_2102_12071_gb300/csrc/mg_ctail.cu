@@ -1,11 +1,11 @@
 // mg_ctail.cu -- the coarse levels of the V-cycle (Algorithm 1) in one thread-block
 // cluster per problem, for sm_103a.
 //
-// Levels of side n_l <= MG_CT_N(hk) run in a cluster of MG_CT_C CTAs per problem, every
-// vector in shared memory.  On a band level (n_l > MG_CT_SOLO(hk)) CTA k owns the rows
+// Levels of side n_l <= MG_CT_N(hk, n_0) run in a cluster of MG_CT_C CTAs per problem, every
+// vector in shared memory.  On a band level (n_l > MG_CT_SOLO(hk, n_0)) CTA k owns the rows
 // [k B, k B + B), B = (n_l + 1) / MG_CT_C (the last CTA one row fewer), and keeps r, e and
 // t of its band with MG_CT_HD halo rows on each side, a zero column on each side and zero
-// rows outside the grid (the Dirichlet exterior).  Levels of side <= MG_CT_SOLO(hk) run in
+// rows outside the grid (the Dirichlet exterior).  Levels of side <= MG_CT_SOLO(hk, n_0) run in
 // CTA 0 alone on whole ring-padded arrays, down to the FP64 coarsest solve and back.
 //
 // Down step of a band level: e = H r on the band and two halo rows, t = r - A e on the
@@ -38,7 +38,7 @@ namespace mg {
 constexpr int CT_THREADS = MG_CT_THREADS;
 // A band of the smallest band level (side 2 MG_CT_SOLO + 1) must hold the MG_CT_HD rows it
 // pushes into each neighbour's halo.
-static_assert((2 * MG_CT_SOLO_TABLE + 2) / MG_CT_C >= MG_CT_HD && (2 * MG_CT_SOLO_JACOBI + 2) / MG_CT_C >= MG_CT_HD,
+static_assert((2 * MG_CT_SOLO_SHORT + 2) / MG_CT_C >= MG_CT_HD && (2 * MG_CT_SOLO_LONG + 2) / MG_CT_C >= MG_CT_HD,
               "band levels need at least MG_CT_HD rows per CTA");
 
 struct CtLayout {
@@ -50,7 +50,7 @@ struct CtLayout {
 
 __host__ __device__ inline void ct_layout(const int* nl, int ls, int L, int hk, CtLayout& t) {
   int lsolo = ls;
-  while (lsolo < L && nl[lsolo] > MG_CT_SOLO(hk)) ++lsolo;
+  while (lsolo < L && nl[lsolo] > MG_CT_SOLO(hk, nl[0])) ++lsolo;
   t.lsolo = lsolo;
   int o = 0;
   for (int l = ls; l < L; ++l) {

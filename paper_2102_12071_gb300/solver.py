@@ -167,7 +167,8 @@ class MixedBatchSolver:
     sets, or a function of the group's side returning either.  With `autotune`, the
     first solve times a few cycles of every candidate layout per group -- the coarse-level
     layout (the coarse levels in one CTA cluster per problem -- from 63 with the network
-    smoothers, from 127 with Jacobi -- or from 63 in one CTA, tiled kernels above) crossed with the tile shape of the tiled down-sweeps (`shapes`, names of
+    smoothers on grids of side >= 1023, else from 127 -- or from 63 in one CTA, tiled kernels
+    above) crossed with the tile shape of the tiled down-sweeps (`shapes`, names of
     binding.TILE_SHAPES) -- and keeps the fastest; without it the first candidate is used.
     After a solve, `last_times_ms[i]` is problem i's time to its stopping test, from the
     start of the earliest group (GPU timer stamps, mg_solve_times).
