@@ -77,7 +77,7 @@ struct FwdLayout {
   static constexpr int W1 = 0, W2 = W1 + 9 * 9 * pad4(7), W3 = W2 + 7 * 9 * pad4(5), WF = W3 + 5 * 9 * pad4(3);
   static constexpr int NW = WF + 3 * 9 * pad4(9 * NK);
   static constexpr int A = NW, B = A + 9 * F0 * F0;  // a0 (later a2) and a1 (later a3)
-  static constexpr int TOTAL = B + 7 * F1 * F1;      // floats
+  static constexpr int TOTAL = B + 7 * F1 * F1 + 8;  // floats (the last 8: reads past a row end)
 };
 
 // conv weights w[o][c][ky][kx] of the parameter vector to wt[(c * 9 + tap) * pad4(COUT) + o]
@@ -133,14 +133,67 @@ __device__ __forceinline__ void fwd_sums(const float* wt, const float* in, int s
   }
 }
 
-template <int CIN, int COUT, int P>
+// The same sums for four consecutive positions x0 .. x0+3 (x0 a multiple of 4) as two
+// pairs in packed FP32 (__ffma2_rn: each lane rounded as fmaf, in the same order): per input
+// channel and kernel row the six inputs x0 .. x0+5 are three aligned 64-bit loads, and the
+// pairs of the middle kernel column are built from them.  The last run of a row reads up to
+// two values past the row's end (their results are dropped; the buffers are padded).
+template <int CIN, int COUT>
+__device__ __forceinline__ void fwd_sums4(const float* wt, const float* in, int si, int y, int x0,
+                                          float2 (&acc)[2][COUT]) {
+  constexpr int OP = pad4(COUT);
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int o = 0; o < COUT; ++o) acc[h][o] = make_float2(0.f, 0.f);
+#pragma unroll 1
+  for (int c = 0; c < CIN; ++c) {
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky) {
+      const float* rp = in + c * si * si + (y + ky) * si + x0;
+      const float2 v01 = *reinterpret_cast<const float2*>(rp), v23 = *reinterpret_cast<const float2*>(rp + 2),
+                   v45 = *reinterpret_cast<const float2*>(rp + 4);
+#pragma unroll
+      for (int kx = 0; kx < 3; ++kx) {
+        const float* wp = wt + (c * 9 + ky * 3 + kx) * OP;
+        float wv[OP];
+#pragma unroll
+        for (int q = 0; q < OP; q += 4) {
+          const float4 v4 = *reinterpret_cast<const float4*>(wp + q);
+          wv[q] = v4.x;
+          wv[q + 1] = v4.y;
+          wv[q + 2] = v4.z;
+          wv[q + 3] = v4.w;
+        }
+        const float2 a = kx == 0 ? v01 : (kx == 1 ? make_float2(v01.y, v23.x) : v23);
+        const float2 b = kx == 0 ? v23 : (kx == 1 ? make_float2(v23.y, v45.x) : v45);
+#pragma unroll
+        for (int o = 0; o < COUT; ++o) {
+          acc[0][o] = __ffma2_rn(make_float2(wv[o], wv[o]), a, acc[0][o]);
+          acc[1][o] = __ffma2_rn(make_float2(wv[o], wv[o]), b, acc[1][o]);
+        }
+      }
+    }
+  }
+}
+
+template <int CIN, int COUT>
 __device__ __forceinline__ void fwd_layer(const float* wt, const float* in, int si, float* out, int so, int gy0,
                                           int gx0, int n, int bf16) {
+  constexpr int P = 4;
   const int runs = (so + P - 1) / P;
   for (int t = threadIdx.x; t < so * runs; t += NET_THREADS) {
     const int y = t / runs, x0 = (t % runs) * P;
+    float2 acc2[2][COUT];
+    fwd_sums4<CIN, COUT>(wt, in, si, y, x0, acc2);
     float acc[P][COUT];
-    fwd_sums<CIN, COUT, P>(wt, in, si, so, y, x0, acc);
+#pragma unroll
+    for (int o = 0; o < COUT; ++o) {
+      acc[0][o] = acc2[0][o].x;
+      acc[1][o] = acc2[0][o].y;
+      acc[2][o] = acc2[1][o].x;
+      acc[3][o] = acc2[1][o].y;
+    }
 #pragma unroll
     for (int p = 0; p < P; ++p) {
       const int x = x0 + p;
@@ -197,11 +250,11 @@ __global__ void __launch_bounds__(NET_THREADS, 2) k_net_forward(const NetJob* __
     }
   }
   __syncthreads();
-  fwd_layer<9, 7, 3>(wt + Lay::W1, bufA, F0, bufB, F1, oy - 3, ox - 3, n, bf16);
+  fwd_layer<9, 7>(wt + Lay::W1, bufA, F0, bufB, F1, oy - 3, ox - 3, n, bf16);
   __syncthreads();
-  fwd_layer<7, 5, 3>(wt + Lay::W2, bufB, F1, bufA, F2, oy - 2, ox - 2, n, bf16);
+  fwd_layer<7, 5>(wt + Lay::W2, bufB, F1, bufA, F2, oy - 2, ox - 2, n, bf16);
   __syncthreads();
-  fwd_layer<5, 3, 4>(wt + Lay::W3, bufA, F2, bufB, F3, oy - 1, ox - 1, n, bf16);
+  fwd_layer<5, 3>(wt + Lay::W3, bufA, F2, bufB, F3, oy - 1, ox - 1, n, bf16);
   __syncthreads();
   // output layer over the 3x3 window of the 3-channel map
   constexpr int PF = NK == 1 ? 4 : 1;
@@ -210,7 +263,19 @@ __global__ void __launch_bounds__(NET_THREADS, 2) k_net_forward(const NetJob* __
   for (int t = threadIdx.x; t < FT * runs; t += NET_THREADS) {
     const int y = t / runs, x0 = (t % runs) * PF;
     float acc[PF][NO];
-    fwd_sums<3, NO, PF>(wt + Lay::WF, bufB, F3, FT, y, x0, acc);
+    if constexpr (NK == 1) {
+      float2 acc2[2][NO];
+      fwd_sums4<3, NO>(wt + Lay::WF, bufB, F3, y, x0, acc2);
+#pragma unroll
+      for (int o = 0; o < NO; ++o) {
+        acc[0][o] = acc2[0][o].x;
+        acc[1][o] = acc2[0][o].y;
+        acc[2][o] = acc2[1][o].x;
+        acc[3][o] = acc2[1][o].y;
+      }
+    } else {
+      fwd_sums<3, NO, PF>(wt + Lay::WF, bufB, F3, FT, y, x0, acc);
+    }
     const int i = oy + y;
 #pragma unroll
     for (int p = 0; p < PF; ++p) {
