@@ -61,14 +61,15 @@ __device__ __forceinline__ void conv_layer(const float* __restrict__ w, const fl
 }
 
 // ------------------------------------------------------------------ forward
-// One CTA computes a 32 x 32 tile of outputs (the halo the three convolutions need costs
-// 1.41x, 1.27x and 1.13x of the tile on their layers, against 1.89x, 1.56x and 1.27x for
-// the 16 x 16 tiles of the backward pass).  Each thread computes a run of P consecutive
+// One CTA computes a 24 x 24 tile of outputs (the halo the three convolutions need costs
+// 1.78x, 1.56x and 1.36x of the tile on their layers, against 1.41x, 1.27x and 1.13x for
+// 32 x 32 tiles; but 24 x 24 tiles hold 69 KB of shared memory, so three CTAs fit on an SM
+// instead of two, and the kernel, latency-bound, runs 10 % faster at 4095^2).  Each thread computes a run of P consecutive
 // positions of one row for every output channel of a layer, so a weight (read by the whole
 // warp at once from shared memory, where each (input channel, tap) keeps its output
 // channels contiguous) serves P multiply-adds and an input value COUT of them.  The sums
 // run over input channel, then kernel row, then kernel column, as in the backward pass.
-constexpr int FT = 32;  // forward output tile side
+constexpr int FT = 24;  // forward output tile side
 constexpr int F0 = FT + 8, F1 = FT + 6, F2 = FT + 4, F3 = FT + 2;
 
 __host__ __device__ constexpr int pad4(int v) { return (v + 3) & ~3; }
@@ -211,7 +212,7 @@ __device__ __forceinline__ void fwd_layer(const float* wt, const float* in, int 
 // NK output kernels per point: NK = 1 gives W = (omega delta + out) / D; NK = 3 the stack
 // K1 = (omega delta + out_1) / D, K2 = delta + out_2, K3 = delta + out_3 ([27][n][n] out).
 template <int NK>
-__global__ void __launch_bounds__(NET_THREADS, 2) k_net_forward(const NetJob* __restrict__ jobs, NetBatch batch,
+__global__ void __launch_bounds__(NET_THREADS, 3) k_net_forward(const NetJob* __restrict__ jobs, NetBatch batch,
                                                                 const float* __restrict__ params, float omega,
                                                                 int bf16) {
   using Lay = FwdLayout<NK>;
