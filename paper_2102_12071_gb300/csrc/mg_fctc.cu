@@ -253,11 +253,13 @@ static cudaError_t fctc_launch(const NetJob* jobs, const NetBatch& batch, int np
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   const int ntiles = ((nmax + TCL - 1) / TCL) * ((nmax + TRW - 1) / TRW);
-  // persistent CTAs: as many as shared memory lets stay resident (three per SM), spread over
-  // the jobs
+  // persistent CTAs: per job as many as shared memory lets stay resident on the GPU (three
+  // per SM), at most one per tile of the largest job.  Jobs of different sizes (the levels
+  // of a hierarchy) each get that many: a job's CTAs beyond its own tiles exit at once, and
+  // the largest job is not left to a share of the GPU while the small ones finish.
   const int fit = (int)((227u * 1024u) / sizeof(FcTcSmem));
   per_sm = per_sm > fit ? per_sm : fit;
-  int gx = (per_sm > 0 ? per_sm : 1) * sms / (nprob > 0 ? nprob : 1);
+  int gx = (per_sm > 0 ? per_sm : 1) * sms;
   gx = gx < 1 ? 1 : (gx > ntiles ? ntiles : gx);
   k_fc_tc<<<dim3(gx, nprob), FCTC_THREADS, sizeof(FcTcSmem), s>>>(jobs, batch, params, omega);
   return cudaGetLastError();
