@@ -41,10 +41,11 @@ BYTES_PER_DOF = {0: 16.0, 1: 9.0, 2: 33.0}
 # dram bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the current
 # kernel versions from one ncu capture of the 16 x 1023^2 batch; None where the kernel
 # changed since its last capture
-NCU_TRAFFIC = {1: 67.16e6 + 36.28e6, 2: 353.91e6 + 169.91e6}
+NCU_TRAFFIC = {1: None, 2: 353.91e6 + 169.91e6}
 NCU_TRAFFIC_SOURCE = {1: "profiles/k_downp_level0_rotated1023x16.md", 2: "profiles/k_up0p_rotated1023x16.md"}
-KERNEL_NAMES = {0: "k_residual (initial iterate)", 1: "k_downp(level 0)", 2: "k_up0p(level 0: up-sweep, x update, residual)",
-                3: "k_tail", 4: "k_downp(l>=1)", 5: "k_up(l>=1)"}
+KERNEL_NAMES = {0: "k_residual (initial iterate)", 1: "k_pdown(level 0, paired strips)",
+                2: "k_up0p(level 0: up-sweep, x update, residual)", 3: "k_tail",
+                4: "down-sweep l>=1 (k_pdown strips, k_downp tiles on short walks)", 5: "k_up(l>=1)"}
 
 
 def peaks():
@@ -739,7 +740,7 @@ def main():
                     help="only set up the batch and run this many single V-cycles (for profiler captures)")
     ap.add_argument("--profile-network", type=int, default=0,
                     help="only run the network inference kernels three times on a GRF field of this side")
-    ap.add_argument("--tile-shape", default="32x32", help="profile case: tile shape of the tiled down-sweeps")
+    ap.add_argument("--tile-shape", default="pstrip", help="profile case: tile shape of the tiled down-sweeps")
     ap.add_argument("--smoother", default="auto", choices=["auto", "jacobi", "cnn", "linear"],
                     help="profile case: the smoother (linear: the per-problem linear smoothers of the batch)")
     ap.add_argument("--varcoef-n", default="1023,4095", help="sides of the GRF problems, comma list (0: skip)")

@@ -134,13 +134,20 @@ typedef struct {
 } mg_options;
 
 typedef enum {
-  MG_TILE_DEFAULT = 0,    /* MG_TILE_32x32                                              */
+  MG_TILE_DEFAULT = 0,    /* MG_TILE_PSTRIP (which leaves the batches it does not cover
+                             to MG_TILE_32x32)                                          */
   MG_TILE_32x32 = 1,      /* one 32 x 32 block of points per CTA, 3x3 windows in shared
                              memory                                                     */
   MG_TILE_STRIP4x32 = 2,  /* warp strips: a warp owns 26 columns and walks down the rows,
                              neighbours by warp shuffles; CTAs of 4 strips x 32 rows    */
   MG_TILE_STRIP8x64 = 3,  /* ... CTAs of 8 strips x 64 rows                             */
-  MG_TILE_STRIP8x32 = 4   /* ... CTAs of 8 strips x 32 rows                             */
+  MG_TILE_STRIP8x32 = 4,  /* ... CTAs of 8 strips x 32 rows                             */
+  MG_TILE_PSTRIP = 5      /* paired warp strips (constant stencils with the Jacobi or
+                             network smoother; other batches use 32 x 32 tiles): lane k
+                             holds a pair of adjacent columns in packed FP32, a warp owns
+                             60 columns and walks down a height chosen per launch so that
+                             all walks fill about one wave, its rows arriving in 8-row
+                             copies through a ring of its own; bit-identical to 32 x 32 */
 } mg_tile_shape;
 
 typedef enum {
@@ -414,6 +421,14 @@ mg_status mg_solve_times(const mg_ctx* ctx, unsigned long long* start_ns, unsign
    mg_solve / mg_vcycle report MG_ERR_TIMEOUT.  It concerns the tiled levels only (n > 63);
    on = 0 restores normal solves.  Host-only; takes effect at the next solve or cycle. */
 mg_status mg_debug_short_wait(mg_ctx* ctx, int on);
+
+/* Test setting for the paired strips (tile_shape MG_TILE_PSTRIP): the least number of rows
+   a warp's walk must have for the strips to take a level's down-sweep launch; launches
+   with shorter walks (few problems active, small levels) run the 32 x 32 tiles, whose
+   results are bit-identical.  Default 32; 0 sends every launch of a constant-stencil level
+   with the Jacobi or network smoother to the strips.  rows < 0: MG_ERR_INVALID_ARG.
+   Host-only; takes effect at the next solve or cycle. */
+mg_status mg_debug_strip_rows(mg_ctx* ctx, int rows);
 mg_status mg_profile_read(mg_ctx* ctx, int kernel_class, double* total_ms, long long* launches);
 
 /* ------------------------------------------------------------------- misc ---- */

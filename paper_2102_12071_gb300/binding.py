@@ -16,9 +16,9 @@ MG_OK, MG_ERR_INVALID_ARG, MG_ERR_WORKSPACE, MG_ERR_CUDA, MG_ERR_NOT_CONVERGED, 
     MG_ERR_TIMEOUT, MG_ERR_UNSUPPORTED = range(8)
 MG_PROBLEM_ROTATED, MG_PROBLEM_STENCIL, MG_PROBLEM_VARCOEF5, MG_PROBLEM_FIELD = range(4)
 MG_SMOOTH_JACOBI, MG_SMOOTH_CNN = 0, 1
-MG_TILE_DEFAULT, MG_TILE_32x32, MG_TILE_STRIP4x32, MG_TILE_STRIP8x64, MG_TILE_STRIP8x32 = range(5)
+MG_TILE_DEFAULT, MG_TILE_32x32, MG_TILE_STRIP4x32, MG_TILE_STRIP8x64, MG_TILE_STRIP8x32, MG_TILE_PSTRIP = range(6)
 TILE_SHAPES = {"32x32": MG_TILE_32x32, "strip4x32": MG_TILE_STRIP4x32, "strip8x64": MG_TILE_STRIP8x64,
-               "strip8x32": MG_TILE_STRIP8x32}
+               "strip8x32": MG_TILE_STRIP8x32, "pstrip": MG_TILE_PSTRIP}
 
 
 class mg_problem(ctypes.Structure):
@@ -85,6 +85,7 @@ def lib() -> ctypes.CDLL:
                                                  _P, _P, _P, ctypes.c_double, ctypes.c_int, _P, _P, _P]),
         "mg_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
         "mg_debug_short_wait": (ctypes.c_int, [_P, ctypes.c_int]),
+        "mg_debug_strip_rows": (ctypes.c_int, [_P, ctypes.c_int]),
         "mg_solve_times": (ctypes.c_int, [_P, _P, _P]),
         "mg_profile_read": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_longlong)]),
@@ -309,6 +310,10 @@ def mg_solve_times(ctx, nprob: int):
 
 def mg_debug_short_wait(ctx, on: bool) -> None:
     check(lib().mg_debug_short_wait(ctx, int(on)), "mg_debug_short_wait")
+
+
+def mg_debug_strip_rows(ctx, rows: int) -> None:
+    check(lib().mg_debug_strip_rows(ctx, int(rows)), "mg_debug_strip_rows")
 
 
 def mg_profile_enable(ctx, enable: bool) -> None:

@@ -51,7 +51,7 @@ struct Plan {
   int generic = 0;  // levels above the tail in batched level kernels (mg_linear.cu)
   int nu1 = 1, nu2 = 1;
   int lstar1 = 0;   // first level of the one-CTA tail (the fallback of the cluster tail)
-  int shape = MG_SHAPE_TILE32;  // layout of the tiled level kernels
+  int shape = MG_SHAPE_PSTRIP;  // layout of the tiled level kernels
   int nl[MG_MAXL] = {0};
   int ntiles_max = 0;
   size_t bytes = 0;
@@ -78,9 +78,9 @@ mg_status make_plan(const mg_problem* probs, int nprob, const mg_options* o, Pla
   if (o->smoother == MG_SMOOTH_CNN && o->net_arch == MG_NET_CONV3 && o->conv_bf16)
     return fail(MG_ERR_UNSUPPORTED, "the three-kernel network runs in FP32");
   if (o->net_per_problem != 0 && o->net_per_problem != 1) return fail(MG_ERR_INVALID_ARG, "net_per_problem must be 0 or 1");
-  if (o->tile_shape < MG_TILE_DEFAULT || o->tile_shape > MG_TILE_STRIP8x32)
+  if (o->tile_shape < MG_TILE_DEFAULT || o->tile_shape > MG_TILE_PSTRIP)
     return fail(MG_ERR_INVALID_ARG, "unknown tile_shape %d", o->tile_shape);
-  P.shape = o->tile_shape == MG_TILE_DEFAULT ? MG_SHAPE_TILE32 : o->tile_shape;
+  P.shape = o->tile_shape == MG_TILE_DEFAULT ? MG_SHAPE_PSTRIP : o->tile_shape;
   if (o->net_per_problem && !(o->smoother == MG_SMOOTH_CNN && o->net_arch == MG_NET_LINEAR))
     return fail(MG_ERR_UNSUPPORTED, "per-problem parameter sets need the linear smoother (MG_NET_LINEAR)");
   const int n = probs[0].n;
@@ -116,6 +116,10 @@ mg_status make_plan(const mg_problem* probs, int nprob, const mg_options* o, Pla
          : o->net_arch == MG_NET_LINEAR  ? HK_LINEAR
          : o->net_arch == MG_NET_CONV3   ? HK_STACK3
                                          : (P.sk == SK_CONST ? HK_TABLE : HK_FIELD);
+  // the paired strips cover constant stencils with Jacobi or network kernels; other
+  // smoothers keep the 32 x 32 tiles
+  if (P.shape == MG_SHAPE_PSTRIP && !(P.sk == SK_CONST && (P.hk == HK_JACOBI || P.hk == HK_TABLE)))
+    P.shape = MG_SHAPE_TILE32;
   if (o->smoother_transpose && P.hk == HK_TABLE)
     return fail(MG_ERR_UNSUPPORTED, "smoother_transpose needs per-point problems (kinds VARCOEF5, FIELD)");
   int m = n, L = 0;
@@ -453,6 +457,7 @@ mg_status mg_setup(const mg_problem* problems, int nprob, const mg_options* opts
     return fail(MG_ERR_CUDA, "cudaMallocHost of %d control blocks failed", P.nprob);
   }
   a.shape = P.shape;
+  a.strip_rows = 32;
   if (P.lstar > 0 && !build_tile_maps(ctx->maps, ctx->arrays, P.nprob, P.lstar, P.shape)) {
     delete ctx;
     return fail(MG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the level arrays");
@@ -907,6 +912,13 @@ mg_status mg_solve_times(const mg_ctx* ctx, unsigned long long* start_ns, unsign
 mg_status mg_debug_short_wait(mg_ctx* ctx, int on) {
   if (!ctx) return fail(MG_ERR_INVALID_ARG, "mg_debug_short_wait: ctx is NULL");
   ctx->args.short_wait = on != 0;
+  return MG_OK;
+}
+
+mg_status mg_debug_strip_rows(mg_ctx* ctx, int rows) {
+  if (!ctx) return fail(MG_ERR_INVALID_ARG, "mg_debug_strip_rows: ctx is NULL");
+  if (rows < 0) return fail(MG_ERR_INVALID_ARG, "mg_debug_strip_rows: rows %d < 0", rows);
+  ctx->args.strip_rows = rows;
   return MG_OK;
 }
 

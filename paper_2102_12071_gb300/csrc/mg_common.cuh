@@ -44,7 +44,7 @@
 enum { SK_CONST = 0, SK_FIELD = 1 };                 // stencil storage
 // layout of the tiled level kernels (mg_tile_shape of mgcnn.h): 32 x 32 tiles (mg_tiles.cu),
 // or CTAs of 8 or 4 warp strips of 26 columns over 32 or 64 rows (mg_strip.cu)
-enum { MG_SHAPE_TILE32 = 1, MG_SHAPE_STRIP4x32 = 2, MG_SHAPE_STRIP8x64 = 3, MG_SHAPE_STRIP8x32 = 4 };
+enum { MG_SHAPE_TILE32 = 1, MG_SHAPE_STRIP4x32 = 2, MG_SHAPE_STRIP8x64 = 3, MG_SHAPE_STRIP8x32 = 4, MG_SHAPE_PSTRIP = 5 };
 // smoother storage: omega/D; per-point kernels of a constant stencil by boundary class;
 // per-point kernels of every point; the shared-kernel linear chain (MG_NPARAMS_LIN per level);
 // a stack of three per-point kernels of every point ([27][n][n], applied K3(K2(K1 v)))

@@ -152,6 +152,7 @@ struct CycleArgs {
                                   // the linear smoother, the kernel stack, or nu other than 1
   int short_wait;                 // test setting copied into the control blocks by launch_bnorm
   int shape;                      // layout of the tiled level kernels (MG_SHAPE_*)
+  int strip_rows;                 // MG_SHAPE_PSTRIP: least walk height the strips take
 };
 
 
@@ -208,6 +209,9 @@ bool build_tile_maps(TileMaps& maps, const LevelArrays& arrays, int nprob, int l
 // l for np problems with the tensor map m of that level's r array
 void strip_box(int shape, int* bw, int* bh);
 cudaError_t launch_sdown(const CycleArgs& a, const CUtensorMap& m, int l, int np);
+// whether the paired strips take level l's down-sweep for np problems (shape MG_SHAPE_PSTRIP;
+// the launches they do not take run the 32 x 32 tiles, with bit-identical results)
+bool pdown_applies(const CycleArgs& a, int l, int np);
 // level 0 after an up-sweep run elsewhere: x += e_0 and the residual of the new iterate
 // with the stopping test, on the arrays of cycle `parity` (mg_tiles.cu); e0: tensor map of
 // e_0 with the iterate's box (tile_res_box)

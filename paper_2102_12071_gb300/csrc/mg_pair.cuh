@@ -107,6 +107,46 @@ __device__ __forceinline__ float2 dot9w(const float (&w)[9], const Win2& v) {
   tap(w[8], v.lc, v.mc, v.rc, 2);
   return acc;
 }
+// A window row around the pair (c, c+1) as the pair and its two outer columns: l = c-1,
+// m = (c, c+1), r = c+2 (a row of the warp-strip kernels, whose neighbours come from the
+// adjacent lanes).
+struct PRow {
+  float l;
+  float2 m;
+  float r;
+};
+// the window of three such rows in the form dot9w<false> reads (l.x, m, r.y)
+__device__ __forceinline__ Win2 win_rows(const PRow& a, const PRow& b, const PRow& c) {
+  Win2 v;
+  v.la = make_float2(a.l, a.m.x); v.ma = a.m; v.ra = make_float2(a.m.y, a.r);
+  v.lb = make_float2(b.l, b.m.x); v.mb = b.m; v.rb = make_float2(b.m.y, b.r);
+  v.lc = make_float2(c.l, c.m.x); v.mc = c.m; v.rc = make_float2(c.m.y, c.r);
+  return v;
+}
+// dot9w<false> with a kernel of its own for each column of the pair (w[k].x for column c,
+// w[k].y for c+1): each lane performs the operations of dot9 in its order
+__device__ __forceinline__ float2 dot9wp(const float2 (&w)[9], const Win2& v) {
+  float2 acc = mul2(w[4], v.mb);
+  auto tap = [&](const float2& wk, const float2& l, const float2& m, const float2& r, int col) {
+    if (col == 1) acc = fma2(wk, m, acc);
+    else if (col == 0) {
+      acc.x = fmaf(wk.x, l.x, acc.x);
+      acc.y = fmaf(wk.y, m.x, acc.y);
+    } else {
+      acc.x = fmaf(wk.x, m.y, acc.x);
+      acc.y = fmaf(wk.y, r.y, acc.y);
+    }
+  };
+  tap(w[0], v.la, v.ma, v.ra, 0);
+  tap(w[1], v.la, v.ma, v.ra, 1);
+  tap(w[2], v.la, v.ma, v.ra, 2);
+  tap(w[3], v.lb, v.mb, v.rb, 0);
+  tap(w[5], v.lb, v.mb, v.rb, 2);
+  tap(w[6], v.lc, v.mc, v.rc, 0);
+  tap(w[7], v.lc, v.mc, v.rc, 1);
+  tap(w[8], v.lc, v.mc, v.rc, 2);
+  return acc;
+}
 // the scalar window of one point of the pair (lane 0: column c, lane 1: column c+1)
 __device__ __forceinline__ Win lane_win(const Win2& v, int lane) {
   Win w;

@@ -13,6 +13,7 @@
 
 #include "mg_common.cuh"
 #include "mg_internal.h"
+#include "mg_pair.cuh"
 #include "mg_tile.cuh"
 #include "mg_tma.cuh"
 
@@ -202,6 +203,231 @@ __global__ void __launch_bounds__(32 * WPC, Strip<WPC, H>::MINB) k_sdown(const _
   }
 }
 
+// ---------------------------------------------------------------------- k_pdown
+// The down-sweep of a constant-stencil level in paired warp strips.  Lane k holds the
+// column pair (c0 - 2 + 2k, c0 - 1 + 2k), so a warp covers 64 columns, and lanes 1 .. 30
+// own the 60 from c0 (the outer lanes carry the halo); every arithmetic step is one packed
+// FP32 instruction for both columns, each lane rounded as the scalar instruction, in the
+// order of the tile kernels, so e and r_c equal theirs bit for bit.  A warp walks down H
+// rows on its own: its rows arrive as 8-row TMA copies (box columns c0-4 .. c0+63) into a
+// ring of four stages with one mbarrier each, the copy of a stage going out again as soon
+// as the warp has read its last row, and e and r_c leave by coalesced global stores, so no
+// CTA-wide barrier is taken.  The launch chooses H so that the walks of all problems fill
+// about one wave of resident warps.
+constexpr int PS_OWN = 60;               // owned columns per warp
+constexpr int PS_BW = 68;                // box columns c0-4 .. c0+63
+constexpr int PS_K = 8;                  // rows per copy
+constexpr int PS_S = 4;                  // stages per warp
+constexpr int PS_WPC = 4;                // warps per CTA
+constexpr int PS_MINB = 4;               // resident CTAs per SM the register bound aims at
+constexpr int PS_STAGE = PS_K * PS_BW;   // floats per stage
+static_assert(PS_STAGE * sizeof(float) % 128 == 0, "stages start 128-byte aligned");
+static_assert((PS_BW * sizeof(float)) % 16 == 0 && PS_OWN % 4 == 0, "TMA box and x start 16-byte multiples");
+
+// Box row b of the walk holds grid row R0 - 2 + b, and copy c box rows 8c .. 8c+7.  The
+// walk keeps r on rows i, i+1 and e on rows i-1, i; the step at box row b (i = R0 - 4 + b)
+// reads r on row i+2, forms e = H r on row i+1 (stored on the owned rows), s = r - A e on
+// row i and the row sums of the restriction: an even row 2A+2 ends coarse row A (its r_c is
+// stored) and starts A+1, an odd row 2A+1 is A's centre row.  Box rows 0 .. 3 start the
+// walk; a copy whose eight rows are all steps runs as one unrolled block between the wait
+// for it and the sending of its stage's next copy, and the rows before and after such
+// copies run one at a time.
+template <int HK>
+__global__ void __launch_bounds__(32 * PS_WPC, PS_MINB) k_pdown(const __grid_constant__ CUtensorMap Mr,
+                                                                const ProbDev* __restrict__ probs,
+                                                                ProbState* __restrict__ state, int l, float omega,
+                                                                int H, const int* __restrict__ act) {
+  __shared__ __align__(128) float rbuf[PS_WPC][PS_S][PS_STAGE];
+  __shared__ __align__(8) uint64_t bars[PS_WPC][PS_S];
+  pdl_trigger();
+  const int p = act ? act[blockIdx.y] : blockIdx.y;
+  const LevelDev L = probs[p].lv[l];
+  const int n = L.n;
+  const int nb = (n + PS_OWN - 1) / PS_OWN, ns = (n + H - 1) / H;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = (int)blockIdx.x * PS_WPC + w;
+  if (g >= nb * ns) return;  // the whole warp: nothing below waits for the CTA
+  const int R0 = (g / nb) * H, c0 = (g % nb) * PS_OWN;
+  const int nc = probs[p].lv[l + 1].n, pc = probs[p].lv[l + 1].pitch;
+  float* const rc_out = probs[p].lv[l + 1].r;
+  // coarse rows R0/2 .. R0/2 + kend - 1 lie in the coarse grid; the walk reads box rows
+  // 0 .. last, which arrive in C copies
+  const int kend = min(H / 2, nc - R0 / 2);
+  const int last = kend > 0 ? 2 * kend + 4 : 3;
+  const int C = last / PS_K + 1;
+  float s[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) s[k] = L.s[k];
+  const int j = c0 - 2 + 2 * lane;  // the lane's columns j, j+1
+  const bool inx = (unsigned)j < (unsigned)n, iny = (unsigned)(j + 1) < (unsigned)n;
+  // network kernels of the lane's two columns on the rows at least MG_NET_MARGIN from the top
+  // and bottom edges (row class MG_NET_MARGIN)
+  const int T = L.T, M = MG_NET_MARGIN;
+  const int cx = inx ? kclass(j, n, T) : M, cy = iny ? kclass(j + 1, n, T) : M;
+  float2 wp[9];
+  if (HK == HK_TABLE) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) wp[k] = make_float2(L.W[k * T * T + M * T + cx], L.W[k * T * T + M * T + cy]);
+  }
+  const float2 jw = p2(omega / s[4]);
+  float* const buf = rbuf[w][0];
+  uint64_t* const bar = bars[w];
+  pdl_wait();
+  if (!st_active(state + p)) return;
+  const bool short_wait = __ldcg(&state[p].short_wait) != 0;
+  auto issue = [&](int c) {
+    mbar_arrive_expect_tx(&bar[c % PS_S], PS_STAGE * sizeof(float));
+    tma_load_3d(buf + (c % PS_S) * PS_STAGE, &Mr, &bar[c % PS_S], c0 - 4, R0 - 2 + c * PS_K, p);
+  };
+  if (lane == 0) {
+#pragma unroll
+    for (int c = 0; c < PS_S; ++c) mbar_init(&bar[c], 1);
+    fence_mbar_init();
+    for (int c = 0; c < PS_S && c < C; ++c) issue(c);
+  }
+  __syncwarp();
+
+  const float* const lrow = buf + 2 + 2 * lane;  // the lane's pair on row 0 of stage 0
+  auto at = [&](int b) { return lrow + ((b / PS_K) % PS_S) * PS_STAGE + (b % PS_K) * PS_BW; };
+  // a wait that expires clears ok (stores and further copies stop) and records the copy
+  bool ok = true;
+  int failed = 0;
+  auto wait = [&](int c) {
+    if (!ok) return;
+    const bool got = !short_wait && mbar_wait(&bar[c % PS_S], (c / PS_S) & 1);
+    if (__any_sync(0xffffffffu, !got)) {
+      ok = false;
+      failed = c;
+    }
+  };
+  auto release = [&](int c) {
+    __syncwarp();
+    if (ok && lane == 0 && c + PS_S < C) issue(c + PS_S);
+  };
+  auto load = [&](const float* q) {
+    PRow o;
+    o.m = ld2(q);
+    o.l = q[-1];
+    o.r = q[2];
+    return o;
+  };
+  // e = H r on grid row ie from r on rows ie-1 .. ie+1: zero outside the grid; INNER: the
+  // row lies at least MG_NET_MARGIN inside the grid
+  auto e_row = [&](int ie, bool inner, const PRow& a, const PRow& b, const PRow& c) -> float2 {
+    if (HK == HK_JACOBI) return mul2(jw, b.m);  // r is zero outside the grid
+    float2 e;
+    const int ci = inner ? M : ((unsigned)ie < (unsigned)n ? kclass(ie, n, T) : -1);
+    if (ci == M) {
+      e = dot9wp(wp, win_rows(a, b, c));
+    } else if (ci < 0) {
+      e = make_float2(0.f, 0.f);
+    } else {
+      float2 wr[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k)
+        wr[k] = make_float2(__ldg(L.W + k * T * T + ci * T + cx), __ldg(L.W + k * T * T + ci * T + cy));
+      e = dot9wp(wr, win_rows(a, b, c));
+    }
+    e.x = inx ? e.x : 0.f;
+    e.y = iny ? e.y : 0.f;
+    return e;
+  };
+  auto halo = [&](float2 e) {
+    PRow o;
+    o.m = e;
+    o.l = __shfl_up_sync(0xffffffffu, e.y, 1);
+    o.r = __shfl_down_sync(0xffffffffu, e.x, 1);
+    return o;
+  };
+  // e is stored on rows R0 .. e_end-1 by lanes 1 .. 30 as pairs: n is odd and the row pitch
+  // a multiple of 32, so a pair that ends at column n writes its zero into the row's padding
+  const int e_end = min(R0 + H, n);
+  const bool own = lane >= 1 && lane <= 30 && inx;
+  float* const e_lane = L.e + (own ? j : 0);
+  const size_t epitch = L.pitch;
+  const int B = (c0 >> 1) - 1 + lane;  // coarse column of the lane's restriction
+  const bool cown = lane >= 1 && lane <= 30 && B < nc;
+  float* const rc_lane = rc_out + (cown ? B : 0);
+
+  PRow ra, rb, rc, ea, eb, ec;
+  float2 top = make_float2(0.f, 0.f), cen = top;
+  // the step at grid row i from box row q; FIRST: i == R0 (no coarse row ends there)
+  auto step = [&](const float* q, int i, bool even, bool first, bool inner) {
+    rc = load(q);
+    const float2 e = e_row(i + 1, inner, ra, rb, rc);
+    if (ok && own && i + 1 < e_end) st2(e_lane + (size_t)(i + 1) * epitch, e);
+    ec = halo(e);
+    const float2 sv = sub2(ra.m, dot9w<false>(s, win_rows(ea, eb, ec)));
+    const float z = __shfl_down_sync(0xffffffffu, sv.x, 1);  // s two columns right of the pair
+    if (even) {
+      const float2 bot = make_float2(sv.x + z, sv.y);
+      if (!first) {
+        const float edge = (top.y + bot.y) + cen.x;
+        const float corner = top.x + bot.x;
+        const float v = cen.y + 0.5f * edge + 0.25f * corner;
+        if (ok && cown) rc_lane[(size_t)((i >> 1) - 1) * pc] = v;
+      }
+      top = bot;
+    } else {
+      cen = make_float2(sv.x + z, sv.y);
+    }
+    ra = rb;
+    rb = rc;
+    ea = eb;
+    eb = ec;
+  };
+  // one step with its copy's wait and release
+  auto single = [&](int b) {
+    const int i = R0 - 4 + b;
+    if (b % PS_K == 0) wait(b / PS_K);
+    step(at(b), i, (i & 1) == 0, i == R0, false);
+    if (b % PS_K == PS_K - 1) release(b / PS_K);
+  };
+
+  wait(0);
+  ra = load(at(0));
+  rb = load(at(1));
+  rc = load(at(2));
+  ea = halo(e_row(R0 - 1, false, ra, rb, rc));
+  ra = rb;
+  rb = rc;
+  rc = load(at(3));
+  {
+    const float2 e = e_row(R0, false, ra, rb, rc);
+    if (ok && own) st2(e_lane + (size_t)R0 * epitch, e);
+    eb = halo(e);
+  }
+  ra = rb;
+  rb = rc;
+  int b = 4;
+  for (; ok && b < PS_K && b <= last; ++b) single(b);
+  for (int c = 1; ok && PS_K * c + PS_K - 1 <= last; ++c) {
+    wait(c);
+    if (!ok) break;
+    const float* q = lrow + (c % PS_S) * PS_STAGE;
+    const int i0 = R0 - 4 + PS_K * c;  // even
+    if (HK == HK_JACOBI || (i0 + 1 >= M && i0 + PS_K < n - M)) {
+#pragma unroll
+      for (int t = 0; t < PS_K; ++t) step(q + t * PS_BW, i0 + t, (t & 1) == 0, false, true);
+    } else {
+#pragma unroll
+      for (int t = 0; t < PS_K; ++t) step(q + t * PS_BW, i0 + t, (t & 1) == 0, false, false);
+    }
+    release(c);
+    b = PS_K * (c + 1);
+  }
+  for (; ok && b <= last; ++b) single(b);
+  if (!ok) {
+    // the wait for copy `failed` expired: mark the problem, then wait for the copies still
+    // in flight (those up to failed + PS_S - 1 were sent) before the warp exits
+    if (lane == 0) {
+      state[p].status = 4;
+      state[p].active = 0;
+    }
+    for (int c = failed; c < failed + PS_S && c < C; ++c) mbar_wait(&bar[c % PS_S], (c / PS_S) & 1);
+  }
+}
+
 // ---------------------------------------------------------------- launchers
 template <int WPC, int H>
 static cudaError_t sdown_shape(const CycleArgs& a, const CUtensorMap& m, int l, dim3 grid) {
@@ -213,8 +439,36 @@ static cudaError_t sdown_shape(const CycleArgs& a, const CUtensorMap& m, int l, 
   return e;
 }
 
+// Rows per warp of a k_pdown launch: the walks of all problems fill about one wave of
+// resident warps (at least 8 rows, a multiple of the copy height).
+template <int HK>
+static int pdown_rows(int n, int np) {
+  static int per_sm[64];  // resident CTAs per SM, by device (0 until asked)
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  int& b = per_sm[dev & 63];
+  if (b == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pdown<HK>, 32 * PS_WPC, 0) != cudaSuccess) b = 1;
+  const long long cap = (long long)(nsm > 0 ? nsm : 1) * (b > 0 ? b : 1) * PS_WPC;
+  const long long per_seg = (long long)((n + PS_OWN - 1) / PS_OWN) * (np > 0 ? np : 1);
+  const long long ns = cap / per_seg > 1 ? cap / per_seg : 1;
+  int H = (int)((n + ns - 1) / ns);
+  H = (H + PS_K - 1) / PS_K * PS_K;
+  return H < PS_K ? PS_K : H;
+}
+
+template <int HK>
+static cudaError_t pdown_launch(const CycleArgs& a, const CUtensorMap& m, int l, int np) {
+  const int n = a.nl[l], H = pdown_rows<HK>(n, np);
+  const int warps = ((n + PS_OWN - 1) / PS_OWN) * ((n + H - 1) / H);
+  const dim3 grid((warps + PS_WPC - 1) / PS_WPC, np);
+  return launch_pdl(a.pdl, k_pdown<HK>, grid, dim3(32 * PS_WPC), 0, a.stream, m, (const ProbDev*)a.probs, a.state, l,
+                    a.omega, H, a.active);
+}
+
 void strip_box(int shape, int* bw, int* bh) {
   switch (shape) {
+    case MG_SHAPE_PSTRIP: *bw = PS_BW; *bh = PS_K; return;
     case MG_SHAPE_STRIP4x32: *bw = Strip<4, 32>::BW; *bh = Strip<4, 32>::BH; return;
     case MG_SHAPE_STRIP8x64: *bw = Strip<8, 64>::BW; *bh = Strip<8, 64>::BH; return;
     default: *bw = Strip<8, 32>::BW; *bh = Strip<8, 32>::BH; return;
@@ -229,7 +483,20 @@ static void strip_cta(int shape, int* cw, int* h) {
   }
 }
 
+// Paired strips pay off when every walk of a one-wave launch is long (a.strip_rows, 32 rows
+// by default: four copies); shorter walks (few problems or small levels) spend their time
+// starting up, and the 32 x 32 tiles (bit-identical results) take those launches.
+bool pdown_applies(const CycleArgs& a, int l, int np) {
+  if (a.shape != MG_SHAPE_PSTRIP || a.sk != SK_CONST || (a.hk != HK_JACOBI && a.hk != HK_TABLE)) return false;
+  const int H = a.hk == HK_JACOBI ? pdown_rows<HK_JACOBI>(a.nl[l], np) : pdown_rows<HK_TABLE>(a.nl[l], np);
+  return H >= a.strip_rows;
+}
+
 cudaError_t launch_sdown(const CycleArgs& a, const CUtensorMap& m, int l, int np) {
+  if (a.shape == MG_SHAPE_PSTRIP) {
+    if (a.sk != SK_CONST) return cudaErrorNotSupported;
+    return a.hk == HK_JACOBI ? pdown_launch<HK_JACOBI>(a, m, l, np) : pdown_launch<HK_TABLE>(a, m, l, np);
+  }
   int cw, h;
   strip_cta(a.shape, &cw, &h);
   const int n = a.nl[l];

@@ -1491,7 +1491,7 @@ cudaError_t launch_cycle(const CycleArgs& a, float rtol, int max_cycles, int par
     dim3 grid(nt * nt, np);
     a.prof->launches++;
     a.prof->begin(l == 0 ? PK_DOWN0 : PK_DOWN, a.stream);
-    if (a.shape != MG_SHAPE_TILE32) {
+    if (a.shape == MG_SHAPE_PSTRIP ? pdown_applies(a, l, np) : a.shape != MG_SHAPE_TILE32) {
       e = launch_sdown(a, (l == 0 && parity) ? a.maps->sr0b : a.maps->sr[l], l, np);
     } else {
       DownMaps dm = a.maps->down[l];

@@ -174,7 +174,7 @@ class MixedBatchSolver:
     start of the earliest group (GPU timer stamps, mg_solve_times).
     """
 
-    SHAPES = ("32x32", "strip4x32", "strip8x32")
+    SHAPES = ("pstrip", "32x32", "strip4x32", "strip8x32")
 
     def __init__(self, problems: list[dict], smoother: str = "jacobi", net_params: dict | None = None,
                  autotune: bool = True, tune_cycles: int = 16, shapes=None, layouts=(True, False)):

@@ -71,6 +71,9 @@ def test_argument_validation_is_host_side(lib):
     st = lib.mg_setup(probs, 1, ctypes.byref(cnn), None, None, 0, None, ctypes.byref(out))
     assert st == B.MG_ERR_INVALID_ARG
     assert lib.mg_solve(None, None, None, None, 1e-8, 10, None, None, None) == B.MG_ERR_INVALID_ARG
+    assert lib.mg_debug_strip_rows(None, 0) == B.MG_ERR_INVALID_ARG
+    assert B.mg_workspace_size(probs, 1, B.options(tile_shape=B.MG_TILE_PSTRIP)) > 0
+    assert B.mg_workspace_size(probs, 1, B.options(tile_shape=B.MG_TILE_PSTRIP + 1)) == 0
     assert lib.mg_status_string(B.MG_ERR_NOT_CONVERGED) == b"not converged"
     assert lib.mg_net_nparams() == O.hypernet_nparams() == 1260
 
