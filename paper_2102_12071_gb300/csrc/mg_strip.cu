@@ -224,6 +224,16 @@ constexpr int PS_STAGE = PS_K * PS_BW;   // floats per stage
 static_assert(PS_STAGE * sizeof(float) % 128 == 0, "stages start 128-byte aligned");
 static_assert((PS_BW * sizeof(float)) % 16 == 0 && PS_OWN % 4 == 0, "TMA box and x start 16-byte multiples");
 
+// global stores under a predicate (one predicated instruction each, no branch)
+__device__ __forceinline__ void stg2_if(bool p, float* a, float2 v) {
+  asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %0, 0;\n @q st.global.v2.f32 [%1], {%2, %3};\n}" ::"r"((int)p),
+               "l"(a), "f"(v.x), "f"(v.y));
+}
+__device__ __forceinline__ void stg_if(bool p, float* a, float v) {
+  asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %0, 0;\n @q st.global.f32 [%1], %2;\n}" ::"r"((int)p), "l"(a),
+               "f"(v));
+}
+
 // Box row b of the walk holds grid row R0 - 2 + b, and copy c box rows 8c .. 8c+7.  The
 // walk keeps r on rows i, i+1 and e on rows i-1, i; the step at box row b (i = R0 - 4 + b)
 // reads r on row i+2, forms e = H r on row i+1 (stored on the owned rows), s = r - A e on
@@ -289,7 +299,7 @@ __global__ void __launch_bounds__(32 * PS_WPC, PS_MINB) k_pdown(const __grid_con
 
   const float* const lrow = buf + 2 + 2 * lane;  // the lane's pair on row 0 of stage 0
   auto at = [&](int b) { return lrow + ((b / PS_K) % PS_S) * PS_STAGE + (b % PS_K) * PS_BW; };
-  // a wait that expires clears ok (stores and further copies stop) and records the copy
+  // a wait that expires clears ok (the walk and further copies stop) and records the copy
   bool ok = true;
   int failed = 0;
   auto wait = [&](int c) {
@@ -351,11 +361,12 @@ __global__ void __launch_bounds__(32 * PS_WPC, PS_MINB) k_pdown(const __grid_con
 
   PRow ra, rb, rc, ea, eb, ec;
   float2 top = make_float2(0.f, 0.f), cen = top;
-  // the step at grid row i from box row q; FIRST: i == R0 (no coarse row ends there)
-  auto step = [&](const float* q, int i, bool even, bool first, bool inner) {
+  // the step at grid row i from box row q, storing e at er (row i+1) and r_c at cr (coarse
+  // row i/2 - 1 on even rows); FIRST: i == R0 (no coarse row ends there)
+  auto step = [&](const float* q, int i, bool even, bool first, bool inner, float* er, float* cr) {
     rc = load(q);
     const float2 e = e_row(i + 1, inner, ra, rb, rc);
-    if (ok && own && i + 1 < e_end) st2(e_lane + (size_t)(i + 1) * epitch, e);
+    stg2_if(own && i + 1 < e_end, er, e);
     ec = halo(e);
     const float2 sv = sub2(ra.m, dot9w<false>(s, win_rows(ea, eb, ec)));
     const float z = __shfl_down_sync(0xffffffffu, sv.x, 1);  // s two columns right of the pair
@@ -365,7 +376,7 @@ __global__ void __launch_bounds__(32 * PS_WPC, PS_MINB) k_pdown(const __grid_con
         const float edge = (top.y + bot.y) + cen.x;
         const float corner = top.x + bot.x;
         const float v = cen.y + 0.5f * edge + 0.25f * corner;
-        if (ok && cown) rc_lane[(size_t)((i >> 1) - 1) * pc] = v;
+        stg_if(cown, cr, v);
       }
       top = bot;
     } else {
@@ -380,7 +391,8 @@ __global__ void __launch_bounds__(32 * PS_WPC, PS_MINB) k_pdown(const __grid_con
   auto single = [&](int b) {
     const int i = R0 - 4 + b;
     if (b % PS_K == 0) wait(b / PS_K);
-    step(at(b), i, (i & 1) == 0, i == R0, false);
+    step(at(b), i, (i & 1) == 0, i == R0, false, e_lane + (size_t)(i + 1) * epitch,
+         rc_lane + (size_t)((i >> 1) - 1) * pc);
     if (b % PS_K == PS_K - 1) release(b / PS_K);
   };
 
@@ -394,7 +406,7 @@ __global__ void __launch_bounds__(32 * PS_WPC, PS_MINB) k_pdown(const __grid_con
   rc = load(at(3));
   {
     const float2 e = e_row(R0, false, ra, rb, rc);
-    if (ok && own) st2(e_lane + (size_t)R0 * epitch, e);
+    stg2_if(own, e_lane + (size_t)R0 * epitch, e);
     eb = halo(e);
   }
   ra = rb;
@@ -406,12 +418,22 @@ __global__ void __launch_bounds__(32 * PS_WPC, PS_MINB) k_pdown(const __grid_con
     if (!ok) break;
     const float* q = lrow + (c % PS_S) * PS_STAGE;
     const int i0 = R0 - 4 + PS_K * c;  // even
+    float* er = e_lane + (size_t)(i0 + 1) * epitch;
+    float* cr = rc_lane + (size_t)((i0 >> 1) - 1) * pc;
     if (HK == HK_JACOBI || (i0 + 1 >= M && i0 + PS_K < n - M)) {
 #pragma unroll
-      for (int t = 0; t < PS_K; ++t) step(q + t * PS_BW, i0 + t, (t & 1) == 0, false, true);
+      for (int t = 0; t < PS_K; ++t) {
+        step(q + t * PS_BW, i0 + t, (t & 1) == 0, false, true, er, cr);
+        er += epitch;
+        if (t & 1) cr += pc;
+      }
     } else {
 #pragma unroll
-      for (int t = 0; t < PS_K; ++t) step(q + t * PS_BW, i0 + t, (t & 1) == 0, false, false);
+      for (int t = 0; t < PS_K; ++t) {
+        step(q + t * PS_BW, i0 + t, (t & 1) == 0, false, false, er, cr);
+        er += epitch;
+        if (t & 1) cr += pc;
+      }
     }
     release(c);
     b = PS_K * (c + 1);
