@@ -763,6 +763,15 @@ __device__ __forceinline__ float residual_pair(const LevelDev& L, const float (&
   row_even(cl + XW, l.lb, l.mb, l.rb);
   float2 acc = p2(0.f);
   const size_t g0 = (size_t)(R0 + t0) * pitch + j;
+  // b of all the thread's rows first, so that their latencies overlap
+  float2 bv[KS];
+#pragma unroll
+  for (int k = 0; k < KS; ++k) {
+    const int i = R0 + t0 + k;
+    const size_t g = g0 + (size_t)k * pitch;
+    if (IN) bv[k] = __ldg(reinterpret_cast<const float2*>(bg + g));
+    else bv[k] = make_float2(inside(i, j, n) ? __ldg(bg + g) : 0.f, inside(i, j + 1, n) ? __ldg(bg + g + 1) : 0.f);
+  }
 #pragma unroll
   for (int k = 0; k < KS; ++k) {
     row_even(ch + (k + 2) * XW, h.lc, h.mc, h.rc);
@@ -770,9 +779,7 @@ __device__ __forceinline__ float residual_pair(const LevelDev& L, const float (&
     const int i = R0 + t0 + k;
     const size_t g = g0 + (size_t)k * pitch;
     const bool in0 = IN || inside(i, j, n), in1 = IN || inside(i, j + 1, n);
-    float2 hi;
-    if (IN) hi = __ldg(reinterpret_cast<const float2*>(bg + g));
-    else hi = make_float2(in0 ? __ldg(bg + g) : 0.f, in1 ? __ldg(bg + g + 1) : 0.f);
+    float2 hi = bv[k];
     float2 lo = p2(0.f);
     dot2_sub2(s[0], h.la, l.la, hi, lo);
     dot2_sub2(s[1], h.ma, l.ma, hi, lo);
