@@ -41,7 +41,7 @@ BYTES_PER_DOF = {0: 16.0, 1: 9.0, 2: 33.0}
 # dram bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the current
 # kernel versions from one ncu capture of the 16 x 1023^2 batch; None where the kernel
 # changed since its last capture
-NCU_TRAFFIC = {1: 70.27e6 + 28.27e6, 2: 353.91e6 + 169.91e6}
+NCU_TRAFFIC = {1: 70.27e6 + 28.27e6, 2: 353.84e6 + 165.23e6}
 NCU_TRAFFIC_SOURCE = {1: "profiles/k_pdown_level0_rotated1023x16.md", 2: "profiles/k_up0p_rotated1023x16.md"}
 KERNEL_NAMES = {0: "k_residual (initial iterate)", 1: "k_pdown(level 0, paired strips)",
                 2: "k_up0p(level 0: up-sweep, x update, residual)", 3: "k_tail",
