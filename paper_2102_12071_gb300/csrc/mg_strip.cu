@@ -9,6 +9,10 @@
 // A CTA of WPC warps owns WPC * 26 columns and H rows; its input block with halos arrives
 // as one TMA bulk tensor copy (zero-filled outside the grid: the Dirichlet exterior).
 //   k_sdown(l)  e = H r, s = r - A e, r_{l+1} = P^T s   (Algorithm 1, pre-smoothing and restriction)
+//   k_pdown(l)  the same on constant stencils with a column pair per lane in packed FP32 (60
+//               owned columns per warp), each warp walking its rows alone through a ring of
+//               8-row copies; bit-identical to the 32 x 32 tiles, the default layout for the
+//               launches whose walks are at least 32 rows high
 #include <cudaTypedefs.h>
 
 #include "mg_common.cuh"
