@@ -666,6 +666,23 @@ def run_mixed(args, rank, weights):
     return out
 
 
+def run_profile_train(args):
+    """Profiler case for the training kernels: the C3 trainer (32 rotated problems at 31^2
+    and 32 at 63^2, 32 Gaussian vectors each) performs args.profile_train Adam steps, each
+    with its batch setup, two-grid loss, exact gradient and update."""
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import torch
+
+    from paper_2102_12071_gb300 import train as T
+
+    tr = T.Trainer(sizes=(31, 63), per_size=32, nvec=32)
+    for _ in range(args.profile_train):
+        tr.step()
+    torch.cuda.synchronize()
+
+
 def run_profile_network(args):
     """Network inference only (for profiler captures): the convolutional network in FP32 and
     the fully connected one in bfloat16 (tensor cores) on the GRF field of side
@@ -740,6 +757,8 @@ def main():
                     help="only set up the batch and run this many single V-cycles (for profiler captures)")
     ap.add_argument("--profile-network", type=int, default=0,
                     help="only run the network inference kernels three times on a GRF field of this side")
+    ap.add_argument("--profile-train", type=int, default=0,
+                    help="only run this many training steps of the C3 trainer (for profiler captures)")
     ap.add_argument("--tile-shape", default="pstrip", help="profile case: tile shape of the tiled down-sweeps")
     ap.add_argument("--smoother", default="auto", choices=["auto", "jacobi", "cnn", "linear"],
                     help="profile case: the smoother (linear: the per-problem linear smoothers of the batch)")
@@ -752,6 +771,8 @@ def main():
         return run_reference(args)
     if args.profile_network:
         return run_profile_network(args)
+    if args.profile_train:
+        return run_profile_train(args)
     if args.profile_cycles:
         return run_profile_case(args)
 
