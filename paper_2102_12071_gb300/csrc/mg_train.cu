@@ -338,8 +338,11 @@ __global__ void k_t_band_invdiag(TrainDims D, double* __restrict__ band) {
 }
 
 // x = A_c^{-1} rhs, one warp per right-hand side: forward substitution with L, then
-// backward substitution with L^T, FP64 throughout; lane t keeps the (t+1)-th most recent
-// unknown so each step is one warp-wide dot product of length w <= 32.
+// backward substitution with L^T, FP64 throughout, right-looking: lane t keeps the pending
+// sum of the row t below (above) the current one, so a step is one product for the current
+// unknown, one multiply-add per lane with its column of L, and a one-lane shift of the
+// window, whose new last row takes its own update when the band reaches it (w = 32).  Each
+// step's band entries are loaded one step ahead.
 __global__ void k_t_band_solve(TrainDims D, const double* __restrict__ band, const double* __restrict__ ut,
                                const float* __restrict__ rhs, double* __restrict__ ybuf, float* __restrict__ x,
                                int nvecs) {
@@ -347,38 +350,58 @@ __global__ void k_t_band_solve(TrainDims D, const double* __restrict__ band, con
   if (warp >= nvecs) return;
   const int b = warp / D.Z;
   const int m = D.nc * D.nc, w = D.w, ld = w + 1;
-  const double* L = band + (size_t)b * m * ld;
-  const double* U = ut + (size_t)b * m * ld;
+  const double* L = band + (size_t)b * m * ld;  // L(r, r-d) at r*ld + d, 1/L(r,r) at r*ld
+  const double* U = ut + (size_t)b * m * ld;    // L(i+d, i) at i*ld + d, 1/L(i,i) at i*ld
   const float* r = rhs + (size_t)warp * D.nnc;
   double* y = ybuf + (size_t)warp * m;
   float* out = x + (size_t)warp * D.nnc;
-  const int d = lane + 1;
-  double hist = 0.0;
-  double lnext = (d <= w) ? L[d] : 0.0;
+  const bool upd = lane >= 1 && lane <= w;
+  const bool edge = w == 32;
+  // forward: lane t holds the pending sum of row i + t
+  double acc = lane < m ? (double)r[lane] : 0.0;
+  double cn = upd ? U[lane] : 0.0, dn = U[0], en = edge ? U[32] : 0.0;
+  double rn = 32 < m ? (double)r[32] : 0.0;
   for (int i = 0; i < m; ++i) {
-    const double lcur = lnext;
-    if (i + 1 < m) lnext = (d <= w) ? L[(size_t)(i + 1) * ld + d] : 0.0;
-    double p = (d <= w && i - d >= 0) ? lcur * hist : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
-    const double yi = ((double)r[i] - p) * L[(size_t)i * ld];
-    const double prev = __shfl_up_sync(0xffffffffu, hist, 1);
-    hist = lane == 0 ? yi : prev;
+    const double c = cn, dinv = dn, ce = en, rin = rn;
+    if (i + 1 < m) {
+      const double* Ui = U + (size_t)(i + 1) * ld;
+      cn = upd ? Ui[lane] : 0.0;
+      dn = Ui[0];
+      en = edge ? Ui[32] : 0.0;
+      rn = i + 33 < m ? (double)r[i + 33] : 0.0;
+    }
+    const double yi = __shfl_sync(0xffffffffu, acc, 0) * dinv;
     if (lane == 0) y[i] = yi;
+    acc = fma(-c, yi, acc);
+    const double enter = i + 32 < m ? fma(-ce, yi, rin) : 0.0;
+    acc = __shfl_down_sync(0xffffffffu, acc, 1);
+    if (lane == 31) acc = enter;
   }
   __syncwarp();
-  hist = 0.0;
-  double unext = (d <= w) ? U[(size_t)(m - 1) * ld + d] : 0.0;
+  // backward: lane t holds the pending sum of row i - t
+  acc = lane < m ? y[m - 1 - lane] : 0.0;
+  {
+    const double* Li = L + (size_t)(m - 1) * ld;
+    cn = upd ? Li[lane] : 0.0;
+    dn = Li[0];
+    en = edge ? Li[32] : 0.0;
+  }
+  double yn = m - 33 >= 0 ? y[m - 33] : 0.0;
   for (int i = m - 1; i >= 0; --i) {
-    const double ucur = unext;
-    if (i > 0) unext = (d <= w) ? U[(size_t)(i - 1) * ld + d] : 0.0;
-    double p = (d <= w && i + d < m) ? ucur * hist : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
-    const double xi = (y[i] - p) * U[(size_t)i * ld];
-    const double prev = __shfl_up_sync(0xffffffffu, hist, 1);
-    hist = lane == 0 ? xi : prev;
+    const double c = cn, dinv = dn, ce = en, yin = yn;
+    if (i > 0) {
+      const double* Li = L + (size_t)(i - 1) * ld;
+      cn = upd ? Li[lane] : 0.0;
+      dn = Li[0];
+      en = edge ? Li[32] : 0.0;
+      yn = i - 33 >= 0 ? y[i - 33] : 0.0;
+    }
+    const double xi = __shfl_sync(0xffffffffu, acc, 0) * dinv;
     if (lane == 0) out[i] = (float)xi;
+    acc = fma(-c, xi, acc);
+    const double enter = i - 32 >= 0 ? fma(-ce, xi, yin) : 0.0;
+    acc = __shfl_down_sync(0xffffffffu, acc, 1);
+    if (lane == 31) acc = enter;
   }
 }
 
